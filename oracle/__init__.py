@@ -1,0 +1,153 @@
+"""CPU oracle for the readability metrics -- TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  It wraps the plain C brute force in
+`gr_oracle.c` (compiled here with gcc + OpenMP, no CUDA) through ctypes and
+shares no code with the CUDA library.  Every function takes numpy arrays:
+``xy`` int32 [V, 2], ``edges`` int32 [E, 2].
+
+Each function follows a definition of arXiv 2411.09809:
+  node_occlusion          -- Sec. 2.1, Algorithm 1
+  crossings               -- Sec. 2.1, Algorithms 4 and 5
+  crossings_of_edges      -- the same, restricted to sampled edges
+  min_angle               -- Sec. 2.1, Algorithm 2
+  edge_length_variation   -- Sec. 2.1, Algorithm 3
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gr_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libgr_oracle.so")
+_lib = None
+
+DEFAULT_IDEAL = 7.0 * math.pi / 18.0  # 70 degrees (Sec. 2.1)
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle shared library with gcc (plain C, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(
+            ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
+             _SRC, "-o", tmp, "-lm"],
+            check=True,
+        )
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+        i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+        i64 = ctypes.c_int64
+        lib.oracle_validate.argtypes = [i32p, i64, i32p, i64]
+        lib.oracle_validate.restype = ctypes.c_int
+        lib.oracle_node_occlusion.argtypes = [i32p, i64, i64]
+        lib.oracle_node_occlusion.restype = i64
+        lib.oracle_crossings.argtypes = [i32p, i64, i32p, i64, ctypes.c_double, i64p, f64p]
+        lib.oracle_crossings.restype = ctypes.c_int
+        lib.oracle_crossings_of_edges.argtypes = [i32p, i64, i32p, i64, ctypes.c_double,
+                                                  i64p, i64, i64p, f64p]
+        lib.oracle_crossings_of_edges.restype = ctypes.c_int
+        lib.oracle_min_angle.argtypes = [i32p, i64, i32p, i64, f64p]
+        lib.oracle_min_angle.restype = ctypes.c_int
+        lib.oracle_edge_length_variation.argtypes = [i32p, i64, i32p, i64]
+        lib.oracle_edge_length_variation.restype = ctypes.c_double
+        lib.oracle_num_threads.argtypes = []
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _xy(xy) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
+    return a
+
+
+def _edges(edges) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def validate(xy, edges) -> int:
+    """0 = valid, 1 = bad vertex id or self-loop, 2 = coordinate outside [0, 65536)."""
+    xy, edges = _xy(xy), _edges(edges)
+    return int(_load().oracle_validate(xy, len(xy), edges, len(edges)))
+
+
+def node_occlusion(xy, d: int) -> int:
+    """N_c: unordered vertex pairs at squared distance < d^2 (d = 2r)."""
+    xy = _xy(xy)
+    r = int(_load().oracle_node_occlusion(xy, len(xy), int(d)))
+    if r < 0:
+        raise ValueError("d must be >= 0")
+    return r
+
+
+@dataclass
+class Crossings:
+    proper: int
+    touching: int
+    collinear: int
+    zero_length_edges: int
+    crossings: int          # E_c = proper + touching
+    angle_dev_sum: float    # sum over E_c pairs of |ideal - a_c| (radians)
+    E_ca: float
+
+
+def crossings(xy, edges, ideal: float = DEFAULT_IDEAL) -> Crossings:
+    xy, edges = _xy(xy), _edges(edges)
+    counts = np.zeros(5, np.int64)
+    fv = np.zeros(2, np.float64)
+    if _load().oracle_crossings(xy, len(xy), edges, len(edges), float(ideal), counts, fv) != 0:
+        raise ValueError("ideal angle must be in (0, pi/2]")
+    return Crossings(int(counts[0]), int(counts[1]), int(counts[2]), int(counts[3]),
+                     int(counts[4]), float(fv[0]), float(fv[1]))
+
+
+def crossings_of_edges(xy, edges, sample, ideal: float = DEFAULT_IDEAL):
+    """Per sampled edge: int64 [n, 3] (proper, touching, collinear) and float64 [n]
+    sum of |ideal - a_c| over that edge's E_c partners."""
+    xy, edges = _xy(xy), _edges(edges)
+    sample = np.ascontiguousarray(np.asarray(sample, dtype=np.int64))
+    out_c = np.zeros((len(sample), 3), np.int64)
+    out_d = np.zeros(len(sample), np.float64)
+    if _load().oracle_crossings_of_edges(xy, len(xy), edges, len(edges), float(ideal),
+                                         sample, len(sample), out_c, out_d) != 0:
+        raise ValueError("ideal angle must be in (0, pi/2]")
+    return out_c, out_d
+
+
+@dataclass
+class MinAngle:
+    M_a: float
+    sum_d: float
+    n_vertices: int
+
+
+def min_angle(xy, edges) -> MinAngle:
+    xy, edges = _xy(xy), _edges(edges)
+    out = np.zeros(3, np.float64)
+    _load().oracle_min_angle(xy, len(xy), edges, len(edges), out)
+    return MinAngle(float(out[0]), float(out[1]), int(out[2]))
+
+
+def edge_length_variation(xy, edges) -> float:
+    xy, edges = _xy(xy), _edges(edges)
+    return float(_load().oracle_edge_length_variation(xy, len(xy), edges, len(edges)))
