@@ -1,0 +1,191 @@
+/*
+ * gr.h -- C ABI of libgr, exact graph-layout readability metrics on one GPU.
+ *
+ * The five metrics are those of "Scalable Readability Evaluation for Graph
+ * Layouts: 2D Geometric Distributed Algorithms" (arXiv 2411.09809), Sec. 2.1:
+ *   node occlusion N_c          (Algorithm 1)
+ *   minimum angle M_a           (Algorithm 2)
+ *   edge length variation M_l   (Algorithm 3)
+ *   edge crossings E_c          (Algorithm 4)
+ *   edge crossing angle E_ca    (Algorithm 5)
+ * All of them are computed exactly (counts are exact integers; float metrics
+ * carry only rounding error), unlike the paper's approximate "enhanced"
+ * algorithms of Sec. 3.2.
+ *
+ * Conventions shared by every entry point
+ *   - Coordinates: int32 pairs [V][2] in [0, 65536) (GR_COORD_I32).
+ *   - Edges: int32 pairs [E][2] of vertex ids in [0, V); no self-loops.
+ *     Duplicate edges are allowed (they share endpoints, so never cross).
+ *   - Pointers to inputs may be device or host memory (pinned or pageable);
+ *     the library looks the kind up and copies host inputs to the device on
+ *     the layout's stream.  The library never keeps a caller pointer after a
+ *     call returns: it copies what it needs into memory it owns.
+ *   - Every call returns a gr_status; on error the outputs are left
+ *     untouched and gr_last_error() describes the failure (thread-local).
+ *   - Calls on one gr_layout must not run concurrently from several host
+ *     threads.  Work is issued on the layout's stream (gr_stream_t is the
+ *     same type as cudaStream_t; NULL selects the legacy default stream).
+ *
+ * Degenerate cases, where the paper is silent (the library's fixed reading):
+ *   - two edges that share a vertex id never cross;
+ *   - a zero-length edge (distinct ids, equal coordinates) takes part in no
+ *     crossing and no angle; it has length 0 for M_l;
+ *   - a collinear pair whose extents meet is counted once in
+ *     collinear_overlaps and is not part of E_c or E_ca;
+ *   - E_c counts proper crossings plus touching pairs (an endpoint of one
+ *     edge on the other edge), as Algorithm 4's "<= 0" predicate does;
+ *   - the crossing angle a_c is the acute angle between the two lines;
+ *   - E_ca = 1 when E_c = 0; M_a = 1 when no vertex has two non-zero-length
+ *     incident edges; M_l = 0 when |E| <= 1 or the mean length is 0.
+ */
+#ifndef GR_H
+#define GR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *gr_stream_t; /* identical to cudaStream_t */
+typedef struct gr_layout gr_layout;
+
+typedef enum {
+    GR_OK = 0,
+    GR_EINVAL = 1,   /* bad argument, vertex id out of range or self-loop */
+    GR_ERANGE = 2,   /* coordinate outside [0, 65536) */
+    GR_ENOMEM = 3,   /* device allocation failed */
+    GR_ECUDA = 4,    /* a CUDA call failed (message in gr_last_error) */
+    GR_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    GR_ENOTSUP = 6   /* feature not supported for this input */
+} gr_status;
+
+typedef enum { GR_COORD_I32 = 0, GR_COORD_F32 = 1 } gr_coord_type;
+
+/* Metric selection bits for gr_evaluate. */
+enum {
+    GR_METRIC_OCCLUSION = 1u,
+    GR_METRIC_MIN_ANGLE = 2u,
+    GR_METRIC_EDGE_LENGTH = 4u,
+    GR_METRIC_CROSSINGS = 8u, /* E_c and E_ca together */
+    GR_METRIC_ALL = 15u
+};
+
+/* Which pair kernel computes crossings. */
+typedef enum {
+    GR_PATH_AUTO = 0,     /* density heuristic picks */
+    GR_PATH_GRID = 1,     /* uniform grid + per-cell pair kernel */
+    GR_PATH_ALLPAIRS = 2  /* tiled brute force over all edge pairs */
+} gr_path;
+
+typedef struct {
+    int32_t crossing_path;  /* gr_path; 0 = auto */
+    int32_t cell_log2;      /* crossing grid cell side 2^k, k in [6, 16]; 0 = auto */
+    int32_t occlusion_path; /* gr_path for occlusion; 0 = auto */
+    int32_t reserved;
+} gr_options;
+
+typedef struct {
+    double ideal_rad;    /* ideal crossing angle in (0, pi/2]; <= 0 selects 70 deg */
+    int64_t occlusion_d; /* occlusion diameter d = 2r >= 0 (pairs with distance < d) */
+} gr_params;
+
+typedef struct {
+    int64_t crossings;          /* E_c = proper + touching */
+    int64_t proper;             /* the two segments cross at interior points */
+    int64_t touching;           /* an endpoint lies on the other segment */
+    int64_t collinear_overlaps; /* collinear pairs whose extents meet (not in E_c) */
+    int64_t zero_length_edges;  /* edges with equal endpoint coordinates */
+    int64_t pairs_tested;       /* candidate pairs the pair kernel evaluated */
+} gr_crossing_counts;
+
+typedef struct {
+    gr_crossing_counts c;
+    double angle_dev_sum; /* sum over the E_c pairs of |ideal - a_c|, radians */
+    double ideal_rad;     /* the ideal angle used */
+    double E_ca;          /* 1 - angle_dev_sum / (ideal * E_c); 1 if E_c = 0 */
+} gr_crossing_angle_result;
+
+typedef struct {
+    double M_a;                 /* 1 - sum_d / n_vertices_counted; 1 if none */
+    double sum_d;               /* sum of d_v over counted vertices */
+    int64_t n_vertices_counted; /* vertices with >= 2 non-zero-length edges */
+} gr_min_angle_result;
+
+typedef struct {
+    uint32_t metrics;       /* the metric bits that were evaluated */
+    int32_t crossing_path;  /* gr_path taken for crossings (1 grid, 2 all-pairs) */
+    int32_t cell_log2;      /* grid cell side used for crossings (0 if all-pairs) */
+    int32_t occlusion_path; /* gr_path taken for occlusion */
+    gr_crossing_angle_result crossing;
+    int64_t occlusion_pairs; /* N_c */
+    int64_t occlusion_d;
+    gr_min_angle_result min_angle;
+    double M_l;
+    int64_t grid_records;   /* (edge, cell) records binned by the grid path */
+} gr_result;
+
+/* Creates a layout from V vertex coordinates and E edges (Sec. 2.1 inputs;
+ * Algorithms 1-5 take the vertex table D_pos and the edge table D_e).
+ * `xy` is [V][2] of `coord_type` (only GR_COORD_I32 here), `edges` is [E][2]
+ * int32, device or host memory.  Validates the input on the device and
+ * synchronises the stream: GR_EINVAL for a vertex id outside [0, V) or a
+ * self-loop, GR_ERANGE for a coordinate outside [0, 65536).  `opt` may be
+ * NULL.  The layout owns device memory sized for V and E until destroyed.
+ * V >= 0, E >= 0, both < 2^31. */
+gr_status gr_layout_create(gr_layout **out, const void *xy, gr_coord_type coord_type,
+                           int64_t V, const int32_t *edges, int64_t E,
+                           const gr_options *opt, gr_stream_t stream);
+
+/* Replaces the coordinates (and, when `edges` is not NULL, the edge list) of
+ * an existing layout, keeping V and E.  Stream-ordered, no synchronisation:
+ * validation errors are reported by the next gr_evaluate. */
+gr_status gr_layout_update(gr_layout *layout, const void *xy, const int32_t *edges);
+
+gr_status gr_layout_destroy(gr_layout *layout);
+
+/* Evaluates the metrics selected by `metrics` (GR_METRIC_* bits) and writes
+ * them to the host struct `out`.  `params` may be NULL (ideal 70 deg, d 0).
+ * Synchronises the layout's stream.  GR_EINVAL for d < 0 or an ideal angle
+ * above pi/2, and for invalid input left by gr_layout_update. */
+gr_status gr_evaluate(gr_layout *layout, uint32_t metrics, const gr_params *params,
+                      gr_result *out);
+
+/* Node occlusion N_c (Sec. 2.1, Algorithm 1): unordered vertex pairs whose
+ * distance is < d, d = 2r.  Strict inequality; d = 0 gives 0. */
+gr_status gr_node_occlusion(gr_layout *layout, int64_t d, int64_t *out_pairs);
+
+/* Minimum angle M_a (Sec. 2.1, Algorithm 2), averaged over the vertices with
+ * at least two non-zero-length incident edges. */
+gr_status gr_min_angle(gr_layout *layout, gr_min_angle_result *out);
+
+/* Edge length variation M_l (Sec. 2.1, Algorithm 3), every edge counted once. */
+gr_status gr_edge_length_variation(gr_layout *layout, double *out_M_l);
+
+/* Edge crossings E_c and their classes (Sec. 2.1, Algorithm 4). */
+gr_status gr_edge_crossings(gr_layout *layout, gr_crossing_counts *out);
+
+/* Edge crossing angle E_ca (Sec. 2.1, Algorithm 5) with ideal angle
+ * `ideal_rad` in (0, pi/2]; <= 0 selects 70 deg = 7 pi / 18. */
+gr_status gr_crossing_angle(gr_layout *layout, double ideal_rad, gr_crossing_angle_result *out);
+
+/* Per-edge crossing data (the per-segment quantity of Sec. 3.2.3 / Eq. 1,
+ * computed exactly): for every edge e, the number of proper crossings,
+ * touching pairs and collinear overlaps it takes part in, and the sum of
+ * |ideal - a_c| over its E_c partners.  `d_counts` is DEVICE memory
+ * int64 [E][3], `d_dev` DEVICE memory double [E]; both caller-owned and
+ * overwritten.  Edges are indexed as passed to gr_layout_create. */
+gr_status gr_crossings_per_edge(gr_layout *layout, double ideal_rad, int64_t *d_counts,
+                                double *d_dev);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *gr_last_error(void);
+
+/* Library version string. */
+const char *gr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GR_H */

@@ -1,0 +1,163 @@
+// gr_internal.cuh -- types and launchers shared by the translation units of
+// libgr.  Not part of the public ABI (that is include/gr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gr.h"
+
+namespace gr {
+
+// ---------------------------------------------------------------- status bits
+// Raised by device-side validation into DevAcc::status.
+enum : uint32_t {
+    ST_BAD_ID = 1u,       // vertex id outside [0, V) or self-loop
+    ST_BAD_COORD = 2u,    // coordinate outside [0, 65536)
+    ST_OVERFLOW = 4u,     // a grid record buffer was too small
+    ST_SCAN_OVERFLOW = 8u // an exclusive scan total exceeded 2^32 - 1
+};
+
+// Scale of the fixed-point angle-deviation sums: each |ideal - a_c| is an
+// FP32 value; multiplied by 2^32 it is an exact integer, so the sum of all
+// terms is exact, associative and independent of the order pairs are visited.
+constexpr float kDevScale = 4294967296.0f;  // 2^32
+constexpr double kDevUnscale = 1.0 / 4294967296.0;
+
+// Device-global accumulators.  The first block is written by
+// gr_layout_create / gr_layout_update; the rest is zeroed by every
+// evaluation (from offsetof(DevAcc, eval_status)).
+struct DevAcc {
+    uint32_t status;           // ST_* bits raised by input validation
+    uint32_t n_seg;            // non-zero-length segments after compaction
+    uint64_t zero_len;         // zero-length edges
+    // ---- per evaluation
+    uint32_t eval_status;      // ST_* bits raised during an evaluation
+    uint32_t work_next;        // work-queue head of persistent kernels
+    uint64_t proper;
+    uint64_t touching;
+    uint64_t collinear;
+    uint64_t dev_lo, dev_hi;   // 128-bit sum of |ideal - a_c| * 2^32
+    uint64_t occlusion;
+    uint64_t records;          // grid (edge, cell) records
+    uint64_t grid_work;        // sum over cells of n (n - 1) / 2
+    uint64_t occl_work;
+    uint64_t scan_total;       // total of the last exclusive scan
+    uint64_t scan_total2;      // second scan total slot
+};
+
+// One compacted non-zero-length segment: endpoints packed as x | y << 16
+// (coordinates are < 2^16) and the two vertex ids.
+//   .x = a.x | a.y << 16, .y = b.x | b.y << 16, .z = id(a), .w = id(b)
+using SegRec = uint4;
+
+__host__ __device__ inline int px(uint32_t p) { return int(p & 0xffffu); }
+__host__ __device__ inline int py(uint32_t p) { return int(p >> 16); }
+
+// Device buffers of a layout (owned; see gr_api.cu).
+struct Buffers {
+    int32_t *xy = nullptr;        // [V][2]
+    int32_t *edges = nullptr;     // [E][2] staging copy of host edges
+    SegRec *seg = nullptr;        // [E] compacted segments
+    int32_t *seg_eid = nullptr;   // [E] original edge index of seg[i]
+    int64_t *len2 = nullptr;      // [E] squared length of every edge
+    DevAcc *acc = nullptr;        // accumulators
+    double *elv_part = nullptr;   // [kElvBlocks * 2] per-block FP64 partial sums
+    double *ma_part = nullptr;    // [ma blocks] per-block sums of d_v
+    uint32_t *ma_cnt = nullptr;   // [ma blocks] per-block vertex counts
+    uint32_t *deg = nullptr;      // [V + 1] degree, then CSR offsets (scan in place)
+    uint32_t *deg_fill = nullptr; // [V]
+    int2 *dirs = nullptr;         // [2 E] incident directions by vertex
+    uint64_t *scan_tmp = nullptr; // [kScanMaxBlocks] block sums
+    gr_result *result = nullptr;  // device copy of the result
+};
+
+constexpr int kElvBlocks = 512;
+constexpr int kScanItems = 4096;      // elements per scan block
+constexpr int kScanMaxBlocks = 16384; // => up to 2^26 elements per scan
+
+// ------------------------------------------------------------------ launchers
+// All launchers enqueue on `s` and never synchronise.
+
+// a1: gathers every edge's endpoints, validates ids and coordinates, stores
+// the squared length of every edge, compacts the non-zero-length segments.
+void launch_gather(const int32_t *xy, int64_t V, const int32_t *edges, int64_t E,
+                   Buffers &b, cudaStream_t s);
+// Validates every vertex coordinate (vertices in no edge included).
+void launch_check_vertices(const int32_t *xy, int64_t V, Buffers &b, cudaStream_t s);
+
+// Optional per-edge outputs of the crossing kernels (both nullable together):
+// counts [E][3] (proper, touching, collinear) and fixed-point dev sums [E].
+struct PerEdge {
+    uint64_t *counts = nullptr;
+    uint64_t *dev = nullptr;
+};
+
+// a7: tiled all-pairs crossing kernel over the compacted segments.
+// `n_seg` is the compacted segment count (read back from the device).
+void launch_crossings_allpairs(const Buffers &b, int64_t n_seg, float ideal, PerEdge pe,
+                               cudaStream_t s);
+
+// a8: all-pairs occlusion (small V or d large).
+void launch_occlusion_allpairs(const Buffers &b, int64_t V, int64_t d, cudaStream_t s);
+
+// a9: minimum angle.
+void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s);
+int min_angle_blocks(int64_t V);
+
+// a10: edge length variation, two passes of deterministic FP64 partials.
+void launch_elv(const Buffers &b, int64_t E, cudaStream_t s);
+
+// Exclusive scan of n uint32 values in place into out[0..n] (out[n] = total).
+// `in` and `out` may alias.  The total also goes to *total (device).
+void launch_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *block_tmp,
+                     uint64_t *total, uint32_t *status, cudaStream_t s);
+
+// a11: folds all accumulators into b.result (device).
+void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal,
+                     int64_t d, int ma_blocks, int32_t path, int32_t cell_log2,
+                     int32_t occl_path, int64_t pairs_tested, cudaStream_t s);
+
+// Per-edge output conversion: fixed-point dev sums to double, in place.
+void launch_per_edge_export(uint64_t *dev_fixed, int64_t E, cudaStream_t s);
+
+// ------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum; every thread gets the result.  `sh` holds >= 32 T.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T r = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+    if (wid == 0) r = warp_sum(r);
+    if (threadIdx.x == 0) sh[0] = r;
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Adds a 64-bit fixed-point partial to a 128-bit (lo, hi) accumulator.
+__device__ __forceinline__ void add_u128(uint64_t *lo, uint64_t *hi, uint64_t v) {
+    if (v == 0) return;
+    const unsigned long long old = atomicAdd((unsigned long long *)lo, (unsigned long long)v);
+    if (old + v < old) atomicAdd((unsigned long long *)hi, 1ull);
+}
+
+__device__ __forceinline__ void atomic_add_u64(uint64_t *p, uint64_t v) {
+    if (v) atomicAdd((unsigned long long *)p, (unsigned long long)v);
+}
+#endif
+
+}  // namespace gr

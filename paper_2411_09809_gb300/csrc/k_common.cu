@@ -1,0 +1,345 @@
+// k_common.cu -- gather + validation (a1), exclusive scan, edge length
+// variation (a10) and the final reducer (a11).
+#include <math.h>
+
+#include "gr_internal.cuh"
+
+namespace gr {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// a1 -- one thread per edge (grid-stride, warp-uniform trip count).  Reads the
+// edge's vertex ids and coordinates (the D_e x D_pos join of Algorithm 4),
+// checks them, stores the exact squared length of every edge and appends the
+// non-zero-length ones to the compacted segment array (warp-aggregated slot
+// reservation; the order of the compacted array does not affect any result).
+__global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int64_t V,
+                                                const int2 *__restrict__ edges, int64_t E,
+                                                SegRec *__restrict__ seg,
+                                                int32_t *__restrict__ seg_eid,
+                                                int64_t *__restrict__ len2, DevAcc *acc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        bool keep = false, zero = false;
+        SegRec r = make_uint4(0, 0, 0, 0);
+        if (e < E) {
+            const int2 ed = edges[e];
+            int64_t l2 = 0;
+            if (ed.x < 0 || ed.y < 0 || ed.x >= V || ed.y >= V || ed.x == ed.y) {
+                atomicOr(&acc->status, ST_BAD_ID);
+            } else {
+                const int2 a = xy[ed.x], b = xy[ed.y];
+                if ((unsigned)a.x >= 65536u || (unsigned)a.y >= 65536u ||
+                    (unsigned)b.x >= 65536u || (unsigned)b.y >= 65536u) {
+                    atomicOr(&acc->status, ST_BAD_COORD);
+                } else {
+                    const int64_t dx = b.x - a.x, dy = b.y - a.y;
+                    l2 = dx * dx + dy * dy;
+                    if (l2 != 0) {
+                        keep = true;
+                        r = make_uint4(uint32_t(a.x) | (uint32_t(a.y) << 16),
+                                       uint32_t(b.x) | (uint32_t(b.y) << 16),
+                                       uint32_t(ed.x), uint32_t(ed.y));
+                    } else {
+                        zero = true;
+                    }
+                }
+            }
+            len2[e] = l2;
+        }
+        const unsigned mk = __ballot_sync(FULL, keep);
+        const unsigned mz = __ballot_sync(FULL, zero);
+        uint32_t slot = 0;
+        if (lane == 0 && mk) slot = atomicAdd(&acc->n_seg, (uint32_t)__popc(mk));
+        if (lane == 0 && mz) atomicAdd((unsigned long long *)&acc->zero_len, (unsigned long long)__popc(mz));
+        slot = __shfl_sync(FULL, slot, 0);
+        if (keep) {
+            const uint32_t pos = slot + __popc(mk & lanemask_lt());
+            seg[pos] = r;
+            seg_eid[pos] = (int32_t)e;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_check_vertices(const int2 *__restrict__ xy, int64_t V,
+                                                        DevAcc *acc) {
+    bool bad = false;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = xy[v];
+        bad |= ((unsigned)p.x >= 65536u) | ((unsigned)p.y >= 65536u);
+    }
+    if (bad) atomicOr(&acc->status, ST_BAD_COORD);
+}
+
+// ------------------------------------------------------------------- scan
+// Three phases: per-block sums, one-block scan of the block sums, per-block
+// scan + offset.  kScanItems = 1024 threads x 4 items.
+
+__global__ void __launch_bounds__(1024) k_scan_sums(const uint32_t *__restrict__ in, int64_t n,
+                                                    uint64_t *__restrict__ block_sum_out) {
+    __shared__ uint64_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanItems + threadIdx.x * 4;
+    uint64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < n) s += in[base + k];
+    s = block_sum<uint64_t>(s, sh);
+    if (threadIdx.x == 0) block_sum_out[blockIdx.x] = s;
+}
+
+// Exclusive scan of the block sums in place (one block of 1024 threads,
+// 16 values per thread).
+__global__ void __launch_bounds__(1024) k_scan_top(uint64_t *__restrict__ bs, int nb,
+                                                   uint32_t *__restrict__ out, int64_t n,
+                                                   uint64_t *total, uint32_t *status) {
+    __shared__ uint64_t warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t v[16];
+    uint64_t t = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int i = threadIdx.x * 16 + k;
+        v[k] = i < nb ? bs[i] : 0;
+        t += v[k];
+    }
+    // inclusive warp scan of the thread totals
+    uint64_t inc = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t w = warp_tot[lane];
+        uint64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - w;  // exclusive
+    }
+    __syncthreads();
+    uint64_t run = warp_tot[wid] + inc - t;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int i = threadIdx.x * 16 + k;
+        if (i < nb) bs[i] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 1023) {
+        // run now holds the grand total
+        *total = run;
+        if (run > 0xffffffffull) atomicOr(status, ST_SCAN_OVERFLOW);
+        out[n] = (uint32_t)run;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
+                                                     const uint64_t *__restrict__ boff) {
+    __shared__ uint32_t warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kScanItems + threadIdx.x * 4;
+    uint32_t v[4];
+    uint32_t t = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        t += v[k];
+    }
+    uint32_t inc = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t w = warp_tot[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = (uint32_t)boff[blockIdx.x] + warp_tot[wid] + inc - t;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+// ------------------------------------------------------------------ ELV a10
+// Pass 1: per-block FP64 sum of edge lengths l_e = sqrt(len2_e) over a fixed
+// strided subset of edges (fixed order => deterministic).
+__global__ void __launch_bounds__(256) k_elv_sum(const int64_t *__restrict__ len2, int64_t E,
+                                                 double *__restrict__ part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)kElvBlocks * blockDim.x)
+        s += sqrt((double)len2[e]);
+    s = block_sum<double>(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Pass 2: every block recomputes the mean from the pass-1 partials in the
+// same fixed order, then sums (l_e - mean)^2 over its subset.
+__global__ void __launch_bounds__(256) k_elv_var(const int64_t *__restrict__ len2, int64_t E,
+                                                 double *__restrict__ part) {
+    __shared__ double sh[32];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < kElvBlocks; i += blockDim.x) m += part[i];
+    m = block_sum<double>(m, sh) / (double)E;
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)kElvBlocks * blockDim.x) {
+        const double t = sqrt((double)len2[e]) - m;
+        s += t * t;
+    }
+    s = block_sum<double>(s, sh);
+    if (threadIdx.x == 0) part[kElvBlocks + blockIdx.x] = s;
+}
+
+// ------------------------------------------------------------- finalize a11
+__global__ void __launch_bounds__(256) k_finalize(const DevAcc *__restrict__ acc,
+                                                  const double *__restrict__ elv_part,
+                                                  const double *__restrict__ ma_part,
+                                                  const uint32_t *__restrict__ ma_cnt, int ma_blocks,
+                                                  uint32_t metrics, int64_t E, double ideal, int64_t d,
+                                                  int32_t path, int32_t cell_log2, int32_t occl_path,
+                                                  int64_t pairs_tested, gr_result *__restrict__ out) {
+    __shared__ double shd[32];
+    __shared__ uint64_t shu[32];
+    // edge length variation (Algorithm 3)
+    double sl = 0.0, sv = 0.0;
+    if (metrics & GR_METRIC_EDGE_LENGTH) {
+        for (int i = threadIdx.x; i < kElvBlocks; i += blockDim.x) {
+            sl += elv_part[i];
+            sv += elv_part[kElvBlocks + i];
+        }
+    }
+    sl = block_sum<double>(sl, shd);
+    sv = block_sum<double>(sv, shd);
+    // minimum angle (Algorithm 2)
+    double ms = 0.0;
+    uint64_t mn = 0;
+    for (int i = threadIdx.x; i < ((metrics & GR_METRIC_MIN_ANGLE) ? ma_blocks : 0); i += blockDim.x) {
+        ms += ma_part[i];
+        mn += ma_cnt[i];
+    }
+    ms = block_sum<double>(ms, shd);
+    mn = block_sum<uint64_t>(mn, shu);
+    if (threadIdx.x != 0) return;
+
+    gr_result r;
+    memset(&r, 0, sizeof(r));
+    r.metrics = metrics;
+    r.crossing_path = path;
+    r.cell_log2 = cell_log2;
+    r.occlusion_path = occl_path;
+    // crossings (Algorithms 4 and 5)
+    const uint64_t ec = acc->proper + acc->touching;
+    r.crossing.c.crossings = (int64_t)ec;
+    r.crossing.c.proper = (int64_t)acc->proper;
+    r.crossing.c.touching = (int64_t)acc->touching;
+    r.crossing.c.collinear_overlaps = (int64_t)acc->collinear;
+    r.crossing.c.zero_length_edges = (int64_t)acc->zero_len;
+    const uint64_t ns = acc->n_seg;
+    r.crossing.c.pairs_tested = pairs_tested >= 0 ? pairs_tested : (int64_t)(ns * (ns - (ns > 0)) / 2);
+    const double dev = (double)acc->dev_hi * 4294967296.0 + (double)acc->dev_lo * kDevUnscale;
+    r.crossing.angle_dev_sum = dev;
+    r.crossing.ideal_rad = ideal;
+    r.crossing.E_ca = ec > 0 ? 1.0 - dev / (ideal * (double)ec) : 1.0;
+    r.occlusion_pairs = (int64_t)acc->occlusion;
+    r.occlusion_d = d;
+    r.min_angle.sum_d = ms;
+    r.min_angle.n_vertices_counted = (int64_t)mn;
+    r.min_angle.M_a = mn > 0 ? 1.0 - ms / (double)mn : 1.0;
+    if ((metrics & GR_METRIC_EDGE_LENGTH) && E > 1) {
+        const double mu = sl / (double)E;
+        r.M_l = mu > 0.0 ? sqrt(sv / ((double)E * mu * mu)) / sqrt((double)E - 1.0) : 0.0;
+    } else {
+        r.M_l = 0.0;
+    }
+    r.grid_records = (int64_t)acc->records;
+    *out = r;
+}
+
+__global__ void k_per_edge_export(uint64_t *dev_fixed, int64_t E) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)dev_fixed[e] * kDevUnscale;
+        reinterpret_cast<double *>(dev_fixed)[e] = v;
+    }
+}
+
+int grid_for(int64_t n, int threads, int max_blocks) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+}  // namespace
+
+void launch_gather(const int32_t *xy, int64_t V, const int32_t *edges, int64_t E, Buffers &b,
+                   cudaStream_t s) {
+    if (E <= 0) return;
+    k_gather<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>((const int2 *)xy, V, (const int2 *)edges, E,
+                                                        b.seg, b.seg_eid, b.len2, b.acc);
+}
+
+void launch_check_vertices(const int32_t *xy, int64_t V, Buffers &b, cudaStream_t s) {
+    if (V <= 0) return;
+    k_check_vertices<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const int2 *)xy, V, b.acc);
+}
+
+void launch_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *block_tmp,
+                     uint64_t *total, uint32_t *status, cudaStream_t s) {
+    const int nb = (int)((n + kScanItems - 1) / kScanItems);
+    if (nb > kScanMaxBlocks) {  // callers bound n; record it rather than overrun
+        k_scan_top<<<1, 1024, 0, s>>>(block_tmp, 0, out, 0, total, status);
+        return;
+    }
+    if (nb > 0) k_scan_sums<<<nb, 1024, 0, s>>>(in, n, block_tmp);
+    k_scan_top<<<1, 1024, 0, s>>>(block_tmp, nb, out, n, total, status);
+    if (nb > 0) k_scan_apply<<<nb, 1024, 0, s>>>(in, out, n, block_tmp);
+}
+
+void launch_elv(const Buffers &b, int64_t E, cudaStream_t s) {
+    k_elv_sum<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part);
+    k_elv_var<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part);
+}
+
+void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal, int64_t d,
+                     int ma_blocks, int32_t path, int32_t cell_log2, int32_t occl_path,
+                     int64_t pairs_tested, cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(b.acc, b.elv_part, b.ma_part, b.ma_cnt, ma_blocks, metrics, E, ideal,
+                                 d, path, cell_log2, occl_path, pairs_tested, b.result);
+}
+
+void launch_per_edge_export(uint64_t *dev_fixed, int64_t E, cudaStream_t s) {
+    if (E <= 0) return;
+    k_per_edge_export<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>(dev_fixed, E);
+}
+
+}  // namespace gr

@@ -1,0 +1,145 @@
+// k_minangle.cu -- minimum angle M_a (a9, Algorithm 2).
+//
+// The aggregateMessages step of Algorithm 2 (collect, per vertex, the angles
+// of its incident edges) becomes a CSR build: degree count, exclusive scan,
+// scatter of the incident direction vectors.  GetMinAngle (sort the angles,
+// take the smallest gap between neighbours, wrap-around included) becomes an
+// exact successor search: for every incident direction d_i, the next
+// direction counter-clockwise is found with exact integer comparisons (half
+// plane relative to d_i, then the sign of a cross product), and the gap to it
+// is the ccw angle between the two vectors.  The set of gaps is the set of
+// neighbour gaps of the sorted order, so its minimum is GetMinAngle's result.
+#include <math.h>
+
+#include "gr_internal.cuh"
+
+namespace gr {
+
+namespace {
+
+constexpr int MA_WARPS = 8;  // vertices in flight per block
+constexpr int MA_MAX_BLOCKS = 1024;
+
+__global__ void k_degree(const SegRec *__restrict__ seg, const DevAcc *__restrict__ acc,
+                         uint32_t *__restrict__ deg) {
+    const int64_t n = acc->n_seg;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const SegRec r = seg[s];
+        atomicAdd(&deg[r.z], 1u);
+        atomicAdd(&deg[r.w], 1u);
+    }
+}
+
+__global__ void k_fill_dirs(const SegRec *__restrict__ seg, const DevAcc *__restrict__ acc,
+                            const uint32_t *__restrict__ off, uint32_t *__restrict__ fill,
+                            int2 *__restrict__ dirs) {
+    const int64_t n = acc->n_seg;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const SegRec r = seg[s];
+        const int dx = px(r.y) - px(r.x), dy = py(r.y) - py(r.x);
+        const uint32_t ia = atomicAdd(&fill[r.z], 1u);
+        dirs[off[r.z] + ia] = make_int2(dx, dy);
+        const uint32_t ib = atomicAdd(&fill[r.w], 1u);
+        dirs[off[r.w] + ib] = make_int2(-dx, -dy);
+    }
+}
+
+__device__ __forceinline__ long long cross2(int2 a, int2 b) {
+    return (long long)a.x * b.y - (long long)a.y * b.x;
+}
+__device__ __forceinline__ long long dot2(int2 a, int2 b) {
+    return (long long)a.x * b.x + (long long)a.y * b.y;
+}
+
+// One warp per vertex (fixed vertex -> block mapping, so the per-block FP64
+// partial sums are deterministic).  d_v = (2 pi / deg - min) / (2 pi / deg)
+// for every vertex with deg >= 2 (deg = 1 has a single 2 pi gap, d_v = 0).
+__global__ void __launch_bounds__(MA_WARPS * 32) k_min_angle(const uint32_t *__restrict__ off,
+                                                             const int2 *__restrict__ dirs, int64_t V,
+                                                             double *__restrict__ part,
+                                                             uint32_t *__restrict__ cnt) {
+    __shared__ double shd[32];
+    __shared__ uint64_t shu[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t step = (int64_t)gridDim.x * MA_WARPS;
+    double dsum = 0.0;
+    uint32_t nv = 0;
+    for (int64_t v = (int64_t)blockIdx.x * MA_WARPS + wid; v < V; v += step) {
+        const uint32_t start = off[v];
+        const int k = (int)(off[v + 1] - start);
+        if (k < 2) continue;  // warp-uniform
+        float gmin = 1e30f;
+        int2 bi = make_int2(1, 0), bs = make_int2(1, 0);
+        for (int i = lane; i < k; i += 32) {
+            const int2 di = dirs[start + i];
+            int2 db = make_int2(0, 0);
+            int hb = 2;
+            for (int j = 0; j < k; ++j) {
+                if (j == i) continue;
+                const int2 dj = dirs[start + j];
+                const long long cr = cross2(di, dj), dt = dot2(di, dj);
+                const int hj = (cr > 0 || (cr == 0 && dt > 0)) ? 0 : 1;
+                if (hj < hb || (hj == hb && cross2(dj, db) > 0)) {
+                    db = dj;
+                    hb = hj;
+                }
+            }
+            float g = atan2f((float)cross2(di, db), (float)dot2(di, db));
+            if (g < 0.f) g += 6.28318530717958647692f;
+            if (g < gmin) {
+                gmin = g;
+                bi = di;
+                bs = db;
+            }
+        }
+        // warp argmin; the winning pair's gap is recomputed in FP64
+        float m = gmin;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const unsigned win = __ballot_sync(0xffffffffu, gmin == m);
+        if (lane == __ffs(win) - 1) {
+            double g = atan2((double)cross2(bi, bs), (double)dot2(bi, bs));
+            if (g < 0.0) g += 2.0 * M_PI;
+            const double ideal = 2.0 * M_PI / (double)k;
+            dsum += (ideal - g) / ideal;
+            nv += 1;
+        }
+    }
+    const double s = block_sum<double>(dsum, shd);
+    const uint64_t c = block_sum<uint64_t>(nv, shu);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s;
+        cnt[blockIdx.x] = (uint32_t)c;
+    }
+}
+
+int grid_for(int64_t n, int threads, int max_blocks) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+}  // namespace
+
+int min_angle_blocks(int64_t V) {
+    int64_t b = (V + MA_WARPS - 1) / MA_WARPS;
+    if (b < 1) b = 1;
+    if (b > MA_MAX_BLOCKS) b = MA_MAX_BLOCKS;
+    return (int)b;
+}
+
+void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
+    if (V <= 0) return;
+    cudaMemsetAsync(b.deg, 0, sizeof(uint32_t) * (V + 1), s);
+    cudaMemsetAsync(b.deg_fill, 0, sizeof(uint32_t) * V, s);
+    const int gb = grid_for(E, 256, 152 * 8);
+    if (E > 0) k_degree<<<gb, 256, 0, s>>>(b.seg, b.acc, b.deg);
+    launch_scan_u32(b.deg, b.deg, V, b.scan_tmp, &b.acc->scan_total2, &b.acc->eval_status, s);
+    if (E > 0) k_fill_dirs<<<gb, 256, 0, s>>>(b.seg, b.acc, b.deg, b.deg_fill, b.dirs);
+    k_min_angle<<<min_angle_blocks(V), MA_WARPS * 32, 0, s>>>(b.deg, b.dirs, V, b.ma_part, b.ma_cnt);
+}
+
+}  // namespace gr

@@ -1,0 +1,106 @@
+// pair_math.cuh -- exact classification of one edge pair, shared by the
+// all-pairs and per-cell crossing kernels.
+//
+// Algorithm 4 decides a crossing from four orientation signs.  With
+// integer coordinates in [0, 2^16) every orientation is an exact int64:
+//   orient(p, q, r) = (q - p) x (r - p) = u x r - u x p,   u = q - p,
+// so for a fixed segment (p, q) it is the linear form u x r - k with
+// k = u x p precomputed once per segment; each orientation then costs two
+// 32x32->64 multiply-adds.  Magnitudes stay below 2^35.
+#pragma once
+
+#include "gr_internal.cuh"
+
+namespace gr {
+
+enum { PAIR_NONE = 0, PAIR_PROPER = 1, PAIR_TOUCHING = 2, PAIR_COLLINEAR = 3 };
+
+// Segment held in registers by the thread that owns it.
+struct RowSeg {
+    int ax, ay, bx, by;
+    int ux, uy;
+    long long k;  // u x a
+    uint32_t ida, idb;
+};
+
+// Segment staged in shared memory and read by every thread of a tile.
+struct __align__(8) ColSeg {
+    int cx, cy, dx, dy;
+    int vx, vy;
+    uint32_t idc, idd;
+    long long k;  // v x c
+};
+
+__device__ __forceinline__ RowSeg make_row(SegRec s) {
+    RowSeg r;
+    r.ax = px(s.x); r.ay = py(s.x); r.bx = px(s.y); r.by = py(s.y);
+    r.ux = r.bx - r.ax; r.uy = r.by - r.ay;
+    r.k = (long long)r.ux * r.ay - (long long)r.uy * r.ax;
+    r.ida = s.z; r.idb = s.w;
+    return r;
+}
+
+__device__ __forceinline__ ColSeg make_col(SegRec s) {
+    ColSeg c;
+    c.cx = px(s.x); c.cy = py(s.x); c.dx = px(s.y); c.dy = py(s.y);
+    c.vx = c.dx - c.cx; c.vy = c.dy - c.cy;
+    c.k = (long long)c.vx * c.cy - (long long)c.vy * c.cx;
+    c.idc = s.z; c.idd = s.w;
+    return c;
+}
+
+// Lexicographic (x, then y) key of a point; for points on one line this is a
+// linear order along the line.
+__device__ __forceinline__ uint32_t lex_key(int x, int y) { return (uint32_t(x) << 16) | uint32_t(y); }
+
+// Classifies the unordered pair {r, c} under the library's reading of
+// Algorithm 4 (shared ids never cross; collinear pairs that meet are
+// reported separately; proper and touching pairs form E_c).  For an E_c pair
+// `dev` receives |ideal - a_c| with a_c = atan2(|u x v|, |u . v|), the acute
+// angle between the lines (Algorithm 5), in FP32 from the exact integer cross
+// and dot products.  `o` receives the four orientations when non-null.
+__device__ __forceinline__ int classify(const RowSeg &r, const ColSeg &c, float ideal, float &dev) {
+    if ((r.ida == c.idc) | (r.ida == c.idd) | (r.idb == c.idc) | (r.idb == c.idd)) return PAIR_NONE;
+    const long long o1 = (long long)r.ux * c.cy - (long long)r.uy * c.cx - r.k;  // orient(a, b, c)
+    const long long o2 = (long long)r.ux * c.dy - (long long)r.uy * c.dx - r.k;  // orient(a, b, d)
+    if ((o1 > 0 && o2 > 0) || (o1 < 0 && o2 < 0)) return PAIR_NONE;
+    const long long o3 = (long long)c.vx * r.ay - (long long)c.vy * r.ax - c.k;  // orient(c, d, a)
+    const long long o4 = (long long)c.vx * r.by - (long long)c.vy * r.bx - c.k;  // orient(c, d, b)
+    if ((o3 > 0 && o4 > 0) || (o3 < 0 && o4 < 0)) return PAIR_NONE;
+    if (o1 == 0 && o2 == 0) {
+        // collinear (for non-zero-length segments o1 = o2 = 0 implies o3 = o4 = 0)
+        const uint32_t ka = lex_key(r.ax, r.ay), kb = lex_key(r.bx, r.by);
+        const uint32_t kc = lex_key(c.cx, c.cy), kd = lex_key(c.dx, c.dy);
+        const uint32_t lo = max(min(ka, kb), min(kc, kd));
+        const uint32_t hi = min(max(ka, kb), max(kc, kd));
+        return lo <= hi ? PAIR_COLLINEAR : PAIR_NONE;
+    }
+    const int kind = (o1 != 0 && o2 != 0 && o3 != 0 && o4 != 0) ? PAIR_PROPER : PAIR_TOUCHING;
+    const float cr = (float)((long long)r.ux * c.vy - (long long)r.uy * c.vx);
+    const float dt = (float)((long long)r.ux * c.vx + (long long)r.uy * c.vy);
+    dev = fabsf(ideal - atan2f(fabsf(cr), fabsf(dt)));
+    return kind;
+}
+
+// Per-thread tallies of one crossing kernel.
+struct PairCounts {
+    uint32_t proper = 0, touching = 0, collinear = 0;
+    uint64_t dev = 0;  // fixed point, 2^32 scale
+};
+
+// Block-wide reduction of the tallies and one atomic per counter.  Every
+// thread of the block must call it.
+__device__ __forceinline__ void flush_counts(const PairCounts &pc, DevAcc *acc, uint64_t *sh) {
+    const uint64_t p = block_sum<uint64_t>(pc.proper, sh);
+    const uint64_t t = block_sum<uint64_t>(pc.touching, sh);
+    const uint64_t c = block_sum<uint64_t>(pc.collinear, sh);
+    const uint64_t d = block_sum<uint64_t>(pc.dev, sh);
+    if (threadIdx.x == 0) {
+        atomic_add_u64(&acc->proper, p);
+        atomic_add_u64(&acc->touching, t);
+        atomic_add_u64(&acc->collinear, c);
+        add_u128(&acc->dev_lo, &acc->dev_hi, d);
+    }
+}
+
+}  // namespace gr

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libgr (include/gr.h), with the C entry points' names.
+
+Argument marshalling only: every step of every metric runs in the CUDA
+library.  Inputs may be CUDA tensors (torch), CPU tensors or numpy arrays; the
+library copies host inputs to the device itself.  If libgr.so has not been
+built, loading raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import c_double, c_int32, c_int64, c_uint32, c_void_p
+
+from . import build as _build
+
+GR_OK, GR_EINVAL, GR_ERANGE, GR_ENOMEM, GR_ECUDA, GR_ETIMEOUT, GR_ENOTSUP = range(7)
+GR_COORD_I32, GR_COORD_F32 = 0, 1
+GR_METRIC_OCCLUSION, GR_METRIC_MIN_ANGLE, GR_METRIC_EDGE_LENGTH, GR_METRIC_CROSSINGS = 1, 2, 4, 8
+GR_METRIC_ALL = 15
+GR_PATH_AUTO, GR_PATH_GRID, GR_PATH_ALLPAIRS = 0, 1, 2
+DEFAULT_IDEAL = 7.0 * math.pi / 18.0
+
+_STATUS_NAMES = ["GR_OK", "GR_EINVAL", "GR_ERANGE", "GR_ENOMEM", "GR_ECUDA", "GR_ETIMEOUT", "GR_ENOTSUP"]
+
+
+class GrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = _STATUS_NAMES[status] if 0 <= status < len(_STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class gr_options(ctypes.Structure):
+    _fields_ = [("crossing_path", c_int32), ("cell_log2", c_int32),
+                ("occlusion_path", c_int32), ("reserved", c_int32)]
+
+
+class gr_params(ctypes.Structure):
+    _fields_ = [("ideal_rad", c_double), ("occlusion_d", c_int64)]
+
+
+class gr_crossing_counts(ctypes.Structure):
+    _fields_ = [("crossings", c_int64), ("proper", c_int64), ("touching", c_int64),
+                ("collinear_overlaps", c_int64), ("zero_length_edges", c_int64),
+                ("pairs_tested", c_int64)]
+
+
+class gr_crossing_angle_result(ctypes.Structure):
+    _fields_ = [("c", gr_crossing_counts), ("angle_dev_sum", c_double), ("ideal_rad", c_double),
+                ("E_ca", c_double)]
+
+
+class gr_min_angle_result(ctypes.Structure):
+    _fields_ = [("M_a", c_double), ("sum_d", c_double), ("n_vertices_counted", c_int64)]
+
+
+class gr_result(ctypes.Structure):
+    _fields_ = [("metrics", c_uint32), ("crossing_path", c_int32), ("cell_log2", c_int32),
+                ("occlusion_path", c_int32), ("crossing", gr_crossing_angle_result),
+                ("occlusion_pairs", c_int64), ("occlusion_d", c_int64),
+                ("min_angle", gr_min_angle_result), ("M_l", c_double), ("grid_records", c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Loads libgr.so (built by ``paper_2411_09809_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libgr.so is not built ({_build.LIB}); call build() first")
+    lib = ctypes.CDLL(_build.LIB)
+    P = c_void_p
+    sigs = {
+        "gr_layout_create": ([ctypes.POINTER(c_void_p), P, c_int32, c_int64, P, c_int64,
+                              ctypes.POINTER(gr_options), P], c_int32),
+        "gr_layout_update": ([P, P, P], c_int32),
+        "gr_layout_destroy": ([P], c_int32),
+        "gr_evaluate": ([P, c_uint32, ctypes.POINTER(gr_params), ctypes.POINTER(gr_result)], c_int32),
+        "gr_node_occlusion": ([P, c_int64, ctypes.POINTER(c_int64)], c_int32),
+        "gr_min_angle": ([P, ctypes.POINTER(gr_min_angle_result)], c_int32),
+        "gr_edge_length_variation": ([P, ctypes.POINTER(c_double)], c_int32),
+        "gr_edge_crossings": ([P, ctypes.POINTER(gr_crossing_counts)], c_int32),
+        "gr_crossing_angle": ([P, c_double, ctypes.POINTER(gr_crossing_angle_result)], c_int32),
+        "gr_crossings_per_edge": ([P, c_double, P, P], c_int32),
+        "gr_last_error": ([], ctypes.c_char_p),
+        "gr_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st: int) -> None:
+    if st != GR_OK:
+        raise GrError(st, load().gr_last_error().decode())
+
+
+def _buffer(x, dtype: str):
+    """(pointer, keepalive) for a torch tensor or numpy array of the given dtype."""
+    if x is None:
+        return None, None
+    try:
+        import torch  # noqa: F401
+        if isinstance(x, torch.Tensor):
+            want = {"int32": torch.int32, "float32": torch.float32, "int64": torch.int64,
+                    "float64": torch.float64}[dtype]
+            if x.dtype != want:
+                raise TypeError(f"expected a {dtype} tensor, got {x.dtype}")
+            if not x.is_contiguous():
+                x = x.contiguous()
+            return x.data_ptr(), x
+    except ImportError:
+        pass
+    import numpy as np
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a
+
+
+def _stream_of(*tensors):
+    try:
+        import torch
+        for t in tensors:
+            if isinstance(t, torch.Tensor) and t.is_cuda:
+                return torch.cuda.current_stream(t.device).cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _count(x) -> int:
+    return int(x.shape[0]) if hasattr(x, "shape") else len(x)
+
+
+# ------------------------------------------------------------ C entry points
+
+def gr_layout_create(xy, edges, coord_type: int = GR_COORD_I32, opt: gr_options | None = None,
+                     stream=None) -> c_void_p:
+    lib = load()
+    xp, xk = _buffer(xy, "int32" if coord_type == GR_COORD_I32 else "float32")
+    ep, ek = _buffer(edges, "int32")
+    if stream is None:
+        stream = _stream_of(xy, edges)
+    h = c_void_p()
+    st = lib.gr_layout_create(ctypes.byref(h), xp, coord_type, _count(xk), ep, _count(ek),
+                              ctypes.byref(opt) if opt is not None else None, stream)
+    _check(st)
+    return h
+
+
+def gr_layout_update(layout, xy, edges=None) -> None:
+    lib = load()
+    xp, xk = _buffer(xy, "int32")
+    ep, ek = _buffer(edges, "int32")
+    _check(lib.gr_layout_update(layout, xp, ep))
+
+
+def gr_layout_destroy(layout) -> None:
+    _check(load().gr_layout_destroy(layout))
+
+
+def gr_evaluate(layout, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+                occlusion_d: int = 0) -> gr_result:
+    r = gr_result()
+    p = gr_params(float(ideal_rad), int(occlusion_d))
+    _check(load().gr_evaluate(layout, metrics, ctypes.byref(p), ctypes.byref(r)))
+    return r
+
+
+def gr_node_occlusion(layout, d: int) -> int:
+    out = c_int64()
+    _check(load().gr_node_occlusion(layout, int(d), ctypes.byref(out)))
+    return out.value
+
+
+def gr_min_angle(layout) -> gr_min_angle_result:
+    out = gr_min_angle_result()
+    _check(load().gr_min_angle(layout, ctypes.byref(out)))
+    return out
+
+
+def gr_edge_length_variation(layout) -> float:
+    out = c_double()
+    _check(load().gr_edge_length_variation(layout, ctypes.byref(out)))
+    return out.value
+
+
+def gr_edge_crossings(layout) -> gr_crossing_counts:
+    out = gr_crossing_counts()
+    _check(load().gr_edge_crossings(layout, ctypes.byref(out)))
+    return out
+
+
+def gr_crossing_angle(layout, ideal_rad: float = 0.0) -> gr_crossing_angle_result:
+    out = gr_crossing_angle_result()
+    _check(load().gr_crossing_angle(layout, float(ideal_rad), ctypes.byref(out)))
+    return out
+
+
+def gr_crossings_per_edge(layout, ideal_rad: float, d_counts, d_dev) -> None:
+    """d_counts: CUDA int64 tensor [E, 3]; d_dev: CUDA float64 tensor [E] (overwritten)."""
+    cp, ck = _buffer(d_counts, "int64")
+    dp, dk = _buffer(d_dev, "float64")
+    _check(load().gr_crossings_per_edge(layout, float(ideal_rad), cp, dp))
+
+
+def gr_last_error() -> str:
+    return load().gr_last_error().decode()
+
+
+def gr_version() -> str:
+    return load().gr_version().decode()
+
+
+# ---------------------------------------------------------------- convenience
+
+class Layout:
+    """Owns a gr_layout handle: ``Layout(xy, edges).evaluate(...)``."""
+
+    def __init__(self, xy, edges, opt: gr_options | None = None, stream=None,
+                 coord_type: int = GR_COORD_I32):
+        self.E = _count(edges)
+        self.V = _count(xy)
+        self.handle = gr_layout_create(xy, edges, coord_type, opt, stream)
+
+    def update(self, xy, edges=None) -> None:
+        gr_layout_update(self.handle, xy, edges)
+
+    def evaluate(self, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0, occlusion_d: int = 0) -> gr_result:
+        return gr_evaluate(self.handle, metrics, ideal_rad, occlusion_d)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            gr_layout_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,84 @@
+"""C ABI checks that need no GPU: the library builds, loads, exports every
+entry point include/gr.h declares, its structs have the layout the binding
+assumes, and argument checks that precede any CUDA call report GR_EINVAL."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2411_09809_gb300 import build, gr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gr.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return gr.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gr_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["gr_layout_create", "gr_layout_update", "gr_layout_destroy", "gr_evaluate",
+              "gr_node_occlusion", "gr_min_angle", "gr_edge_length_variation",
+              "gr_edge_crossings", "gr_crossing_angle", "gr_crossings_per_edge",
+              "gr_last_error", "gr_version"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", gr.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (gr_[a-z0-9_]+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    src = tmp_path / "sizes.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "gr.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gr_options), sizeof(gr_params),
+         sizeof(gr_crossing_counts), sizeof(gr_crossing_angle_result),
+         sizeof(gr_min_angle_result), sizeof(gr_result));
+  printf("%zu %zu %zu %zu\\n", offsetof(gr_result, crossing), offsetof(gr_result, occlusion_pairs),
+         offsetof(gr_result, min_angle), offsetof(gr_result, grid_records));
+  return 0;
+}
+""")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    sizes = [int(v) for v in lines[0].split()]
+    offs = [int(v) for v in lines[1].split()]
+    assert sizes == [ctypes.sizeof(t) for t in (gr.gr_options, gr.gr_params, gr.gr_crossing_counts,
+                                                gr.gr_crossing_angle_result, gr.gr_min_angle_result,
+                                                gr.gr_result)]
+    assert offs == [gr.gr_result.crossing.offset, gr.gr_result.occlusion_pairs.offset,
+                    gr.gr_result.min_angle.offset, gr.gr_result.grid_records.offset]
+
+
+def test_argument_errors_need_no_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.gr_layout_create(None, None, 0, 0, None, 0, None, None) == gr.GR_EINVAL
+    assert lib.gr_layout_create(ctypes.byref(h), None, 0, -1, None, 0, None, None) == gr.GR_EINVAL
+    assert lib.gr_layout_create(ctypes.byref(h), None, 0, 10, None, 0, None, None) == gr.GR_EINVAL
+    assert "NULL" in gr.gr_last_error()
+    assert lib.gr_layout_create(ctypes.byref(h), None, 7, 0, None, 0, None, None) == gr.GR_ENOTSUP
+    assert lib.gr_evaluate(None, 15, None, None) == gr.GR_EINVAL
+    assert lib.gr_layout_destroy(None) == gr.GR_OK
+    assert gr.gr_version().startswith("gr ")
