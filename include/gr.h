@@ -82,7 +82,7 @@ typedef struct {
     int32_t crossing_path;  /* gr_path; 0 = auto */
     int32_t cell_log2;      /* crossing grid cell side 2^k, k in [6, 16]; 0 = auto */
     int32_t occlusion_path; /* gr_path for occlusion; 0 = auto */
-    int32_t reserved;
+    int32_t profile;        /* non-zero: enable phase timing at creation */
 } gr_options;
 
 typedef struct {
@@ -177,6 +177,37 @@ gr_status gr_crossing_angle(gr_layout *layout, double ideal_rad, gr_crossing_ang
  * overwritten.  Edges are indexed as passed to gr_layout_create. */
 gr_status gr_crossings_per_edge(gr_layout *layout, double ideal_rad, int64_t *d_counts,
                                 double *d_dev);
+
+/* ------------------------------------------------------------- tracing
+ * Phase timing: when enabled on a layout, every gr_layout_update and
+ * gr_evaluate records CUDA events around its phases on the layout's stream;
+ * gr_profile_read returns the accumulated device time and call count of each
+ * phase (optionally resetting them).  Events cost a few microseconds per
+ * phase, so leave profiling off when not reading it. */
+typedef enum {
+    GR_PHASE_GATHER = 0,     /* input copies, validation, gather (a1) */
+    GR_PHASE_EDGE_LENGTH,    /* a10 */
+    GR_PHASE_MIN_ANGLE,      /* a9 */
+    GR_PHASE_OCCL_BIN,       /* a8 binning: count, scan, stencil work */
+    GR_PHASE_OCCL_PAIRS,     /* a8 scatter + pair kernel, or all-pairs tiles */
+    GR_PHASE_CROSS_BIN,      /* a2-a3: DDA count, cell offsets, work items */
+    GR_PHASE_CROSS_SCATTER,  /* a4: records sorted by cell */
+    GR_PHASE_CROSS_PAIRS,    /* a6 per-cell pair kernel, or a7 all-pairs tiles */
+    GR_PHASE_FINALIZE,       /* a11 and the result copy */
+    GR_NUM_PHASES
+} gr_phase;
+
+typedef struct {
+    double ms[16];     /* accumulated device milliseconds per gr_phase */
+    int64_t calls[16]; /* number of times each phase ran */
+} gr_profile;
+
+gr_status gr_profile_enable(gr_layout *layout, int enable);
+gr_status gr_profile_read(gr_layout *layout, gr_profile *out, int reset);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all layouts, all threads). */
+int64_t gr_kernel_launches(void);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *gr_last_error(void);

@@ -3,6 +3,7 @@
 // enqueued.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -62,11 +63,28 @@ struct gr_layout {
     cudaStream_t stream = nullptr;
     gr_options opt{};
     Buffers b;
+    GridBuffers g;
     gr_result *h_result = nullptr;  // pinned
     DevAcc *h_acc = nullptr;        // pinned
+    bool stats_stale = true;        // h_acc's layout part predates the last update
+    // phase timing
+    bool profiling = false;
+    cudaEvent_t ev[2 * GR_NUM_PHASES] = {};
+    bool pending[GR_NUM_PHASES] = {};
+    double prof_ms[GR_NUM_PHASES] = {};
+    int64_t prof_calls[GR_NUM_PHASES] = {};
 };
 
 namespace {
+
+std::atomic<int64_t> g_launches{0};
+
+void free_grid(GridBuffers &g) {
+    void *ptrs[] = {g.cell_off, g.item_off, g.cell_fill, g.rec, g.rec_eid, g.ocell_off, g.ocell_fill, g.opts};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    g = GridBuffers{};
+}
 
 void free_layout(gr_layout *L) {
     if (!L) return;
@@ -75,6 +93,9 @@ void free_layout(gr_layout *L) {
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.result};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    free_grid(L->g);
+    for (auto &e : L->ev)
+        if (e) cudaEventDestroy(e);
     if (L->h_result) cudaFreeHost(L->h_result);
     if (L->h_acc) cudaFreeHost(L->h_acc);
     delete L;
@@ -107,11 +128,94 @@ gr_status alloc_layout(gr_layout *L) {
     return GR_OK;
 }
 
+// Grows the crossing-grid cell arrays to C cells.
+gr_status ensure_cells(gr_layout *L, int C) {
+    GridBuffers &g = L->g;
+    if (g.cells_cap >= C) return GR_OK;
+    if (g.cell_off) cudaFree(g.cell_off);
+    if (g.item_off) cudaFree(g.item_off);
+    if (g.cell_fill) cudaFree(g.cell_fill);
+    g.cell_off = g.item_off = g.cell_fill = nullptr;
+    g.cells_cap = 0;
+    gr_status st;
+    if ((st = dalloc(&g.cell_off, (size_t)C + 1)) != GR_OK) return st;
+    if ((st = dalloc(&g.item_off, (size_t)C + 1)) != GR_OK) return st;
+    if ((st = dalloc(&g.cell_fill, (size_t)C)) != GR_OK) return st;
+    g.cells_cap = C;
+    return GR_OK;
+}
+
+gr_status ensure_records(gr_layout *L, uint64_t R) {
+    GridBuffers &g = L->g;
+    if (g.rec_cap >= R && g.rec) return GR_OK;
+    if (g.rec) cudaFree(g.rec);
+    if (g.rec_eid) cudaFree(g.rec_eid);
+    g.rec = nullptr;
+    g.rec_eid = nullptr;
+    g.rec_cap = 0;
+    const uint64_t cap = R + R / 4 + 1024;
+    gr_status st;
+    if ((st = dalloc(&g.rec, (size_t)cap)) != GR_OK) return st;
+    if ((st = dalloc(&g.rec_eid, (size_t)cap)) != GR_OK) return st;
+    g.rec_cap = cap;
+    return GR_OK;
+}
+
+gr_status ensure_ocells(gr_layout *L, int C) {
+    GridBuffers &g = L->g;
+    gr_status st;
+    if (!g.opts && (st = dalloc(&g.opts, (size_t)L->V)) != GR_OK) return st;
+    if (g.ocells_cap >= C) return GR_OK;
+    if (g.ocell_off) cudaFree(g.ocell_off);
+    if (g.ocell_fill) cudaFree(g.ocell_fill);
+    g.ocell_off = g.ocell_fill = nullptr;
+    g.ocells_cap = 0;
+    if ((st = dalloc(&g.ocell_off, (size_t)C + 1)) != GR_OK) return st;
+    if ((st = dalloc(&g.ocell_fill, (size_t)C)) != GR_OK) return st;
+    g.ocells_cap = C;
+    return GR_OK;
+}
+
+// ------------------------------------------------------------ phase timing
+void phase_begin(gr_layout *L, int ph) {
+    if (L->profiling) cudaEventRecord(L->ev[2 * ph], L->stream);
+}
+void phase_end(gr_layout *L, int ph) {
+    if (L->profiling) {
+        cudaEventRecord(L->ev[2 * ph + 1], L->stream);
+        L->pending[ph] = true;
+    }
+}
+// After a stream synchronisation: folds the recorded phases into the totals.
+void phase_collect(gr_layout *L) {
+    if (!L->profiling) return;
+    for (int ph = 0; ph < GR_NUM_PHASES; ++ph) {
+        if (!L->pending[ph]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, L->ev[2 * ph], L->ev[2 * ph + 1]) == cudaSuccess) {
+            L->prof_ms[ph] += ms;
+            L->prof_calls[ph] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        L->pending[ph] = false;
+    }
+}
+
+gr_status set_profiling(gr_layout *L, bool on) {
+    if (on && !L->ev[0]) {
+        for (auto &e : L->ev) GR_CU(cudaEventCreate(&e));
+    }
+    L->profiling = on;
+    return GR_OK;
+}
+
 // Copies the inputs into the layout's own buffers and runs a1 (gather and
 // validation).  Stream-ordered.
 gr_status enqueue_inputs(gr_layout *L, const void *xy, const int32_t *edges) {
     cudaStream_t s = L->stream;
     const int64_t V = L->V, E = L->E;
+    phase_begin(L, GR_PHASE_GATHER);
     GR_CU(cudaMemsetAsync(L->b.acc, 0, offsetof(DevAcc, eval_status), s));
     if (V > 0) {
         const cudaMemcpyKind k = is_device_pointer(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -123,7 +227,9 @@ gr_status enqueue_inputs(gr_layout *L, const void *xy, const int32_t *edges) {
     }
     launch_check_vertices(L->b.xy, V, L->b, s);
     launch_gather(L->b.xy, V, L->b.edges, E, L->b, s);
+    phase_end(L, GR_PHASE_GATHER);
     GR_CU(cudaGetLastError());
+    L->stats_stale = true;
     return GR_OK;
 }
 
@@ -145,6 +251,59 @@ gr_status read_params(const gr_params *p, double *ideal, int64_t *d) {
     if (!(*ideal <= M_PI / 2 + 1e-15)) return fail(GR_EINVAL, "ideal angle must be in (0, pi/2]");
     if (*d < 0) return fail(GR_EINVAL, "occlusion diameter d must be >= 0");
     return GR_OK;
+}
+
+// Reads the layout part of the accumulators (compacted count, total L1
+// length, validation status) once after every update.
+gr_status refresh_stats(gr_layout *L) {
+    if (!L->stats_stale) return GR_OK;
+    GR_CU(cudaMemcpyAsync(L->h_acc, L->b.acc, offsetof(DevAcc, eval_status), cudaMemcpyDeviceToHost, L->stream));
+    GR_CU(cudaStreamSynchronize(L->stream));
+    L->stats_stale = false;
+    return GR_OK;
+}
+
+// ---------------------------------------------------------- density model
+// Cost units are "one all-pairs pair test".  A grid record costs about as
+// much as kRecordCost pair tests (two DDA walks, atomics, scattered stores)
+// and a candidate pair in a cell about kCellPairCost (lane efficiency,
+// owner tests).  Measured on GB300 with the workloads of the benchmark.
+constexpr double kRecordCost = 24.0;
+constexpr double kCellPairCost = 3.0;
+
+struct CrossPlan {
+    bool grid = false;
+    int k = 0;
+};
+
+double est_records(double n, double l1, int k) { return n + l1 / double(1 << k); }
+
+// Chooses the cell size from segment count and total L1 length: records
+// n + L1 / w, and a lower bound R^2 / (2 C) on the candidate pairs (equality
+// for evenly spread records).  Picks all-pairs when even that bound loses.
+CrossPlan plan_crossings(const gr_layout *L, uint64_t n_seg, uint64_t l1) {
+    CrossPlan p;
+    const double n = (double)n_seg, l = (double)l1;
+    const double allpairs = n * (n - 1) / 2;
+    int best_k = 8;
+    double best = 1e300;
+    for (int k = 6; k <= 14; ++k) {
+        const double R = est_records(n, l, k);
+        const double C = double(65536 >> k) * double(65536 >> k);
+        const double cost = kRecordCost * R + kCellPairCost * R * R / (2 * C);
+        if (cost < best) { best = cost; best_k = k; }
+    }
+    p.k = L->opt.cell_log2 >= 6 && L->opt.cell_log2 <= 16 ? L->opt.cell_log2 : best_k;
+    if (L->opt.crossing_path == GR_PATH_GRID) p.grid = true;
+    else if (L->opt.crossing_path == GR_PATH_ALLPAIRS) p.grid = false;
+    else p.grid = n_seg >= 2 && best < allpairs;
+    return p;
+}
+
+int occl_cell_log2(int64_t d) {
+    int k = 6;
+    while ((int64_t(1) << k) < d) ++k;
+    return k;
 }
 
 }  // namespace
@@ -171,12 +330,15 @@ gr_status gr_layout_create(gr_layout **out, const void *xy, gr_coord_type coord_
     L->stream = (cudaStream_t)stream;
     if (opt) L->opt = *opt;
     gr_status st = alloc_layout(L);
+    if (st == GR_OK && L->opt.profile) st = set_profiling(L, true);
     if (st == GR_OK) st = enqueue_inputs(L, xy, edges);
     if (st == GR_OK) {
         cudaError_t e = cudaMemcpyAsync(L->h_acc, L->b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, L->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "validating the layout");
         else st = status_to_error(L->h_acc->status);
+        L->stats_stale = false;
+        phase_collect(L);
     }
     if (st != GR_OK) {
         free_layout(L);
@@ -212,24 +374,113 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     cudaStream_t s = L->stream;
     Buffers &b = L->b;
     const int64_t V = L->V, E = L->E;
+    if ((st = refresh_stats(L)) != GR_OK) return st;
+    if ((st = status_to_error(L->h_acc->status)) != GR_OK) return st;
+    const uint64_t n_seg = L->h_acc->n_seg;
     GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
                           sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
-    int32_t path = 0, occl_path = 0;
-    if (metrics & GR_METRIC_EDGE_LENGTH) launch_elv(b, E, s);
-    if (metrics & GR_METRIC_MIN_ANGLE) launch_min_angle(b, V, E, s);
-    if (metrics & GR_METRIC_OCCLUSION) {
-        launch_occlusion_allpairs(b, V, d, s);
-        occl_path = GR_PATH_ALLPAIRS;
+
+    if (metrics & GR_METRIC_EDGE_LENGTH) {
+        phase_begin(L, GR_PHASE_EDGE_LENGTH);
+        launch_elv(b, E, s);
+        phase_end(L, GR_PHASE_EDGE_LENGTH);
     }
-    if (metrics & GR_METRIC_CROSSINGS) {
-        launch_crossings_allpairs(b, E, (float)ideal, PerEdge{}, s);
+    if (metrics & GR_METRIC_MIN_ANGLE) {
+        phase_begin(L, GR_PHASE_MIN_ANGLE);
+        launch_min_angle(b, V, E, s);
+        phase_end(L, GR_PHASE_MIN_ANGLE);
+    }
+
+    // binning passes whose sizes the host needs
+    CrossPlan cp;
+    bool need_sync = false;
+    if ((metrics & GR_METRIC_CROSSINGS) && n_seg >= 2) {
+        cp = plan_crossings(L, n_seg, L->h_acc->len_l1);
+        if (cp.grid) {
+            const int C = (65536 >> cp.k) * (65536 >> cp.k);
+            if ((st = ensure_cells(L, C)) != GR_OK) return st;
+            phase_begin(L, GR_PHASE_CROSS_BIN);
+            launch_grid_count(b, E, L->g, cp.k, s);
+            phase_end(L, GR_PHASE_CROSS_BIN);
+            need_sync = true;
+        }
+    }
+    bool occl_grid = false;
+    const int ko = occl_cell_log2(d);
+    if ((metrics & GR_METRIC_OCCLUSION) && V >= 2 && d > 0) {
+        if (L->opt.occlusion_path == GR_PATH_GRID) occl_grid = ko <= 16;
+        else if (L->opt.occlusion_path == GR_PATH_ALLPAIRS) occl_grid = false;
+        else occl_grid = V > 4096 && ko <= 14;
+        if (occl_grid) {
+            const int C = (65536 >> ko) * (65536 >> ko);
+            if ((st = ensure_ocells(L, C)) != GR_OK) return st;
+            phase_begin(L, GR_PHASE_OCCL_BIN);
+            launch_occlusion_grid_count(b, V, L->g, ko, s);
+            phase_end(L, GR_PHASE_OCCL_BIN);
+            need_sync = true;
+        }
+    }
+    if (need_sync) {
+        GR_CU(cudaGetLastError());
+        GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+        GR_CU(cudaStreamSynchronize(s));
+        if ((st = status_to_error(L->h_acc->eval_status)) != GR_OK) return st;
+    }
+
+    int32_t path = 0, occl_path = 0;
+    int64_t pairs_tested = -1;
+    if ((metrics & GR_METRIC_CROSSINGS) && n_seg >= 2) {
+        bool grid = cp.grid;
+        const DevAcc &a = *L->h_acc;
+        if (grid && (a.grid_flags & GF_ITEMS_OVERFLOW)) grid = false;
+        if (grid && L->opt.crossing_path == GR_PATH_AUTO) {
+            const double n = (double)n_seg;
+            grid = kRecordCost * (double)a.records + kCellPairCost * (double)a.grid_work < n * (n - 1) / 2;
+        }
+        if (grid) {
+            if ((st = ensure_records(L, a.records)) != GR_OK) return st;
+            phase_begin(L, GR_PHASE_CROSS_SCATTER);
+            launch_grid_scatter(b, E, L->g, cp.k, s);
+            phase_end(L, GR_PHASE_CROSS_SCATTER);
+            phase_begin(L, GR_PHASE_CROSS_PAIRS);
+            launch_grid_pairs(b, L->g, cp.k, a.grid_items, (float)ideal, PerEdge{}, s);
+            phase_end(L, GR_PHASE_CROSS_PAIRS);
+            path = GR_PATH_GRID;
+            pairs_tested = (int64_t)a.grid_work;
+        } else {
+            phase_begin(L, GR_PHASE_CROSS_PAIRS);
+            launch_crossings_allpairs(b, E, (float)ideal, PerEdge{}, s);
+            phase_end(L, GR_PHASE_CROSS_PAIRS);
+            path = GR_PATH_ALLPAIRS;
+        }
+    } else if (metrics & GR_METRIC_CROSSINGS) {
         path = GR_PATH_ALLPAIRS;
     }
-    launch_finalize(b, metrics, E, ideal, d, V > 0 ? min_angle_blocks(V) : 0, path, 0, occl_path, -1, s);
+    if (metrics & GR_METRIC_OCCLUSION) {
+        bool grid = occl_grid;
+        if (grid && L->opt.occlusion_path == GR_PATH_AUTO) {
+            const double v = (double)V;
+            grid = 4.0 * (double)L->h_acc->occl_work < v * (v - 1) / 2;
+        }
+        phase_begin(L, GR_PHASE_OCCL_PAIRS);
+        if (grid) {
+            launch_occlusion_grid_pairs(b, V, L->g, ko, d, s);
+            occl_path = GR_PATH_GRID;
+        } else {
+            launch_occlusion_allpairs(b, V, d, s);
+            occl_path = GR_PATH_ALLPAIRS;
+        }
+        phase_end(L, GR_PHASE_OCCL_PAIRS);
+    }
+    phase_begin(L, GR_PHASE_FINALIZE);
+    launch_finalize(b, metrics, E, ideal, d, V > 0 ? min_angle_blocks(V) : 0, path,
+                    path == GR_PATH_GRID ? cp.k : 0, occl_path, pairs_tested, s);
     GR_CU(cudaGetLastError());
     GR_CU(cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s));
     GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+    phase_end(L, GR_PHASE_FINALIZE);
     GR_CU(cudaStreamSynchronize(s));
+    phase_collect(L);
     st = status_to_error(L->h_acc->status | L->h_acc->eval_status);
     if (st != GR_OK) return st;
     *out = *L->h_result;
@@ -299,7 +550,26 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     PerEdge pe;
     pe.counts = (uint64_t *)d_counts;
     pe.dev = (uint64_t *)d_dev;
-    launch_crossings_allpairs(b, E, (float)ideal, pe, s);
+    gr_status st2 = refresh_stats(L);
+    if (st2 != GR_OK) return st2;
+    if ((st2 = status_to_error(L->h_acc->status)) != GR_OK) return st2;
+    CrossPlan cp = plan_crossings(L, L->h_acc->n_seg, L->h_acc->len_l1);
+    if (cp.grid && L->h_acc->n_seg >= 2) {
+        const int C = (65536 >> cp.k) * (65536 >> cp.k);
+        if ((st2 = ensure_cells(L, C)) != GR_OK) return st2;
+        launch_grid_count(b, E, L->g, cp.k, s);
+        GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+        GR_CU(cudaStreamSynchronize(s));
+        if ((st2 = status_to_error(L->h_acc->eval_status)) != GR_OK) return st2;
+        if (L->h_acc->grid_flags & GF_ITEMS_OVERFLOW) cp.grid = false;
+    }
+    if (cp.grid && L->h_acc->n_seg >= 2) {
+        if ((st2 = ensure_records(L, L->h_acc->records)) != GR_OK) return st2;
+        launch_grid_scatter(b, E, L->g, cp.k, s);
+        launch_grid_pairs(b, L->g, cp.k, L->h_acc->grid_items, (float)ideal, pe, s);
+    } else {
+        launch_crossings_allpairs(b, E, (float)ideal, pe, s);
+    }
     launch_per_edge_export(pe.dev, E, s);
     GR_CU(cudaGetLastError());
     GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
@@ -307,4 +577,31 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     return status_to_error(L->h_acc->status | L->h_acc->eval_status);
 }
 
+gr_status gr_profile_enable(gr_layout *L, int enable) {
+    g_err.clear();
+    if (!L) return fail(GR_EINVAL, "layout is NULL");
+    return set_profiling(L, enable != 0);
+}
+
+gr_status gr_profile_read(gr_layout *L, gr_profile *out, int reset) {
+    g_err.clear();
+    if (!L || !out) return fail(GR_EINVAL, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    for (int ph = 0; ph < GR_NUM_PHASES; ++ph) {
+        out->ms[ph] = L->prof_ms[ph];
+        out->calls[ph] = L->prof_calls[ph];
+        if (reset) {
+            L->prof_ms[ph] = 0.0;
+            L->prof_calls[ph] = 0;
+        }
+    }
+    return GR_OK;
+}
+
+int64_t gr_kernel_launches(void) { return g_launches.load(); }
+
 }  // extern "C"
+
+namespace gr {
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace gr

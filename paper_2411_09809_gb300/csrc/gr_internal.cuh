@@ -31,19 +31,24 @@ struct DevAcc {
     uint32_t status;           // ST_* bits raised by input validation
     uint32_t n_seg;            // non-zero-length segments after compaction
     uint64_t zero_len;         // zero-length edges
+    uint64_t len_l1;           // sum over segments of |dx| + |dy|
     // ---- per evaluation
     uint32_t eval_status;      // ST_* bits raised during an evaluation
-    uint32_t work_next;        // work-queue head of persistent kernels
+    uint32_t grid_flags;       // GF_* bits: the grid path cannot be used
     uint64_t proper;
     uint64_t touching;
     uint64_t collinear;
     uint64_t dev_lo, dev_hi;   // 128-bit sum of |ideal - a_c| * 2^32
     uint64_t occlusion;
     uint64_t records;          // grid (edge, cell) records
+    uint64_t grid_items;       // pair-kernel work items
     uint64_t grid_work;        // sum over cells of n (n - 1) / 2
-    uint64_t occl_work;
-    uint64_t scan_total;       // total of the last exclusive scan
-    uint64_t scan_total2;      // second scan total slot
+    uint64_t occl_work;        // candidate vertex pairs of the occlusion grid
+    uint64_t scan_sink;        // totals nobody reads
+};
+
+enum : uint32_t {
+    GF_ITEMS_OVERFLOW = 1u     // a cell has more than 2^31 tile pairs
 };
 
 // One compacted non-zero-length segment: endpoints packed as x | y << 16
@@ -72,12 +77,30 @@ struct Buffers {
     gr_result *result = nullptr;  // device copy of the result
 };
 
+// Buffers of the uniform grids (crossings and occlusion), grown on demand.
+struct GridBuffers {
+    uint32_t *cell_off = nullptr;  // [C + 1] counts, then offsets (scan in place)
+    uint32_t *item_off = nullptr;  // [C + 1] work items per cell, then offsets
+    uint32_t *cell_fill = nullptr; // [C]
+    SegRec *rec = nullptr;         // [rec_cap] segments sorted by cell
+    int32_t *rec_eid = nullptr;    // [rec_cap] their edge ids
+    uint64_t rec_cap = 0;
+    int cells_cap = 0;             // C the cell arrays are sized for
+    // occlusion grid
+    uint32_t *ocell_off = nullptr; // [OC + 1]
+    uint32_t *ocell_fill = nullptr;// [OC]
+    uint32_t *opts = nullptr;      // [V] packed points sorted by cell
+    int ocells_cap = 0;
+};
+
 constexpr int kElvBlocks = 512;
 constexpr int kScanItems = 4096;      // elements per scan block
 constexpr int kScanMaxBlocks = 16384; // => up to 2^26 elements per scan
 
 // ------------------------------------------------------------------ launchers
-// All launchers enqueue on `s` and never synchronise.
+// All launchers enqueue on `s` and never synchronise.  Each adds the number of
+// kernels it launched to the library-wide counter.
+void count_launches(int n);
 
 // a1: gathers every edge's endpoints, validates ids and coordinates, stores
 // the squared length of every edge, compacts the non-zero-length segments.
@@ -97,6 +120,22 @@ struct PerEdge {
 // `n_seg` is the compacted segment count (read back from the device).
 void launch_crossings_allpairs(const Buffers &b, int64_t n_seg, float ideal, PerEdge pe,
                                cudaStream_t s);
+
+// a2-a4: DDA count, cell offsets, work items (records -> acc->records,
+// items -> acc->grid_items, candidate pairs -> acc->grid_work).
+void launch_grid_count(const Buffers &b, int64_t E, const GridBuffers &g, int k, cudaStream_t s);
+// a4: scatter of the records into their cells (needs rec_cap >= records).
+void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int k, cudaStream_t s);
+// a6: per-cell pair kernel with the owner-cell test.
+void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items, float ideal,
+                       PerEdge pe, cudaStream_t s);
+
+// a8 occlusion grid: cell side 2^k >= d.  Count + scan + stencil work
+// (-> acc->occl_work), then scatter + pair kernel.
+void launch_occlusion_grid_count(const Buffers &b, int64_t V, const GridBuffers &g, int k,
+                                 cudaStream_t s);
+void launch_occlusion_grid_pairs(const Buffers &b, int64_t V, const GridBuffers &g, int k, int64_t d,
+                                 cudaStream_t s);
 
 // a8: all-pairs occlusion (small V or d large).
 void launch_occlusion_allpairs(const Buffers &b, int64_t V, int64_t d, cudaStream_t s);

@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride) {
         const int64_t e = base + threadIdx.x;
         bool keep = false, zero = false;
+        uint32_t l1 = 0;
         SegRec r = make_uint4(0, 0, 0, 0);
         if (e < E) {
             const int2 ed = edges[e];
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int
                     l2 = dx * dx + dy * dy;
                     if (l2 != 0) {
                         keep = true;
+                        l1 = (uint32_t)(abs(b.x - a.x) + abs(b.y - a.y));
                         r = make_uint4(uint32_t(a.x) | (uint32_t(a.y) << 16),
                                        uint32_t(b.x) | (uint32_t(b.y) << 16),
                                        uint32_t(ed.x), uint32_t(ed.y));
@@ -63,6 +65,8 @@ __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int
         if (lane == 0 && mk) slot = atomicAdd(&acc->n_seg, (uint32_t)__popc(mk));
         if (lane == 0 && mz) atomicAdd((unsigned long long *)&acc->zero_len, (unsigned long long)__popc(mz));
         slot = __shfl_sync(FULL, slot, 0);
+        const uint64_t l1w = warp_sum<uint64_t>(l1);
+        if (lane == 0 && l1w) atomicAdd((unsigned long long *)&acc->len_l1, (unsigned long long)l1w);
         if (keep) {
             const uint32_t pos = slot + __popc(mk & lanemask_lt());
             seg[pos] = r;
@@ -304,12 +308,14 @@ int grid_for(int64_t n, int threads, int max_blocks) {
 void launch_gather(const int32_t *xy, int64_t V, const int32_t *edges, int64_t E, Buffers &b,
                    cudaStream_t s) {
     if (E <= 0) return;
+    count_launches(1);
     k_gather<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>((const int2 *)xy, V, (const int2 *)edges, E,
                                                         b.seg, b.seg_eid, b.len2, b.acc);
 }
 
 void launch_check_vertices(const int32_t *xy, int64_t V, Buffers &b, cudaStream_t s) {
     if (V <= 0) return;
+    count_launches(1);
     k_check_vertices<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const int2 *)xy, V, b.acc);
 }
 
@@ -317,15 +323,18 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *blo
                      uint64_t *total, uint32_t *status, cudaStream_t s) {
     const int nb = (int)((n + kScanItems - 1) / kScanItems);
     if (nb > kScanMaxBlocks) {  // callers bound n; record it rather than overrun
+        count_launches(1);
         k_scan_top<<<1, 1024, 0, s>>>(block_tmp, 0, out, 0, total, status);
         return;
     }
+    count_launches(nb > 0 ? 3 : 1);
     if (nb > 0) k_scan_sums<<<nb, 1024, 0, s>>>(in, n, block_tmp);
     k_scan_top<<<1, 1024, 0, s>>>(block_tmp, nb, out, n, total, status);
     if (nb > 0) k_scan_apply<<<nb, 1024, 0, s>>>(in, out, n, block_tmp);
 }
 
 void launch_elv(const Buffers &b, int64_t E, cudaStream_t s) {
+    count_launches(2);
     k_elv_sum<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part);
     k_elv_var<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part);
 }
@@ -333,12 +342,14 @@ void launch_elv(const Buffers &b, int64_t E, cudaStream_t s) {
 void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal, int64_t d,
                      int ma_blocks, int32_t path, int32_t cell_log2, int32_t occl_path,
                      int64_t pairs_tested, cudaStream_t s) {
+    count_launches(1);
     k_finalize<<<1, 256, 0, s>>>(b.acc, b.elv_part, b.ma_part, b.ma_cnt, ma_blocks, metrics, E, ideal,
                                  d, path, cell_log2, occl_path, pairs_tested, b.result);
 }
 
 void launch_per_edge_export(uint64_t *dev_fixed, int64_t E, cudaStream_t s) {
     if (E <= 0) return;
+    count_launches(1);
     k_per_edge_export<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>(dev_fixed, E);
 }
 

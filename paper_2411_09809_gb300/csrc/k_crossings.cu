@@ -100,6 +100,7 @@ void launch_crossings_allpairs(const Buffers &b, int64_t n_seg, float ideal, Per
     const int64_t nb = (n_seg + AP_ROWS - 1) / AP_ROWS;
     const int64_t tiles = nb * (nb + 1) / 2;
     const unsigned grid = (unsigned)(tiles < (int64_t(1) << 30) ? tiles : (int64_t(1) << 30));
+    count_launches(1);
     if (pe.counts)
         k_cross_allpairs<true><<<grid, AP_ROWS, 0, s>>>(b.seg, b.seg_eid, b.acc, ideal, pe, tiles);
     else

@@ -45,7 +45,125 @@ __global__ void __launch_bounds__(OC_ROWS) k_occl_allpairs(const int2 *__restric
     if (threadIdx.x == 0) atomic_add_u64(&acc->occlusion, s);
 }
 
+// ------------------------------------------------------------ occlusion grid
+// Cells of side w = 2^k >= d: two vertices closer than d lie in the same or
+// in 8-adjacent cells (the 2r x 2r grid of Sec. 3.2.1).  Each vertex is put
+// in exactly one cell and each unordered pair of cells is visited once
+// through the half stencil {E, NE, N, NW}, so no pair is seen twice and the
+// paper's `distinct` step is not needed.
+
+__global__ void __launch_bounds__(256) k_occl_count(const int2 *__restrict__ xy, int64_t V, int k,
+                                                    uint32_t *__restrict__ cnt) {
+    const int G = 65536 >> k;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = xy[v];
+        atomicAdd(&cnt[(p.y >> k) * G + (p.x >> k)], 1u);
+    }
+}
+
+// Candidate pairs of the stencil (for the grid vs all-pairs decision).
+__global__ void __launch_bounds__(256) k_occl_work(const uint32_t *__restrict__ off, int G, DevAcc *acc) {
+    __shared__ uint64_t sh[32];
+    uint64_t w = 0;
+    const int C = G * G;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        const uint64_t n = off[c + 1] - off[c];
+        if (n == 0) continue;
+        const int cx = c % G, cy = c / G;
+        uint64_t nb = 0;
+        if (cx + 1 < G) nb += off[c + 2] - off[c + 1];
+        if (cy + 1 < G) {
+            const int up = c + G;
+            nb += off[up + 1] - off[up];
+            if (cx + 1 < G) nb += off[up + 2] - off[up + 1];
+            if (cx > 0) nb += off[up] - off[up - 1];
+        }
+        w += n * (n - 1) / 2 + n * nb;
+    }
+    w = block_sum<uint64_t>(w, sh);
+    if (threadIdx.x == 0) atomic_add_u64(&acc->occl_work, w);
+}
+
+__global__ void __launch_bounds__(256) k_occl_fill(const int2 *__restrict__ xy, int64_t V, int k,
+                                                   const uint32_t *__restrict__ off,
+                                                   uint32_t *__restrict__ fill, uint32_t *__restrict__ pts) {
+    const int G = 65536 >> k;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = xy[v];
+        const int c = (p.y >> k) * G + (p.x >> k);
+        const uint32_t slot = atomicAdd(&fill[c], 1u);
+        pts[off[c] + slot] = uint32_t(p.x) | (uint32_t(p.y) << 16);
+    }
+}
+
+__device__ __forceinline__ uint32_t count_close(uint32_t p, const uint32_t *__restrict__ pts, uint32_t b,
+                                                uint32_t e, long long d2) {
+    uint32_t n = 0;
+    const int x = px(p), y = py(p);
+    for (uint32_t q = b; q < e; ++q) {
+        const uint32_t o = pts[q];
+        const long long dx = x - px(o), dy = y - py(o);
+        n += (dx * dx + dy * dy < d2) ? 1u : 0u;
+    }
+    return n;
+}
+
+// One thread per vertex in cell order: later vertices of its own cell, then
+// every vertex of the E, NE, N and NW cells.
+__global__ void __launch_bounds__(256) k_occl_pairs(const uint32_t *__restrict__ pts,
+                                                    const uint32_t *__restrict__ off, int64_t V, int k,
+                                                    long long d2, DevAcc *acc) {
+    __shared__ uint64_t sh[32];
+    const int G = 65536 >> k;
+    uint64_t cnt = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = pts[i];
+        const int cx = px(p) >> k, cy = py(p) >> k;
+        const int c = cy * G + cx;
+        cnt += count_close(p, pts, (uint32_t)i + 1, off[c + 1], d2);
+        if (cx + 1 < G) cnt += count_close(p, pts, off[c + 1], off[c + 2], d2);
+        if (cy + 1 < G) {
+            const int up = c + G;
+            if (cx > 0) cnt += count_close(p, pts, off[up - 1], off[up], d2);
+            cnt += count_close(p, pts, off[up], off[up + 1], d2);
+            if (cx + 1 < G) cnt += count_close(p, pts, off[up + 1], off[up + 2], d2);
+        }
+    }
+    cnt = block_sum<uint64_t>(cnt, sh);
+    if (threadIdx.x == 0) atomic_add_u64(&acc->occlusion, cnt);
+}
+
+int grid_for(int64_t n, int threads, int max_blocks) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
 }  // namespace
+
+void launch_occlusion_grid_count(const Buffers &b, int64_t V, const GridBuffers &g, int k, cudaStream_t s) {
+    const int G = 65536 >> k, C = G * G;
+    cudaMemsetAsync(g.ocell_off, 0, sizeof(uint32_t) * (C + 1), s);
+    count_launches(V > 0 ? 2 : 1);
+    if (V > 0) k_occl_count<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.xy, V, k, g.ocell_off);
+    launch_scan_u32(g.ocell_off, g.ocell_off, C, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
+    k_occl_work<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.ocell_off, G, b.acc);
+}
+
+void launch_occlusion_grid_pairs(const Buffers &b, int64_t V, const GridBuffers &g, int k, int64_t d,
+                                 cudaStream_t s) {
+    const int G = 65536 >> k, C = G * G;
+    if (V < 2 || d <= 0) return;
+    cudaMemsetAsync(g.ocell_fill, 0, sizeof(uint32_t) * C, s);
+    count_launches(2);
+    k_occl_fill<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.xy, V, k, g.ocell_off, g.ocell_fill,
+                                                         g.opts);
+    k_occl_pairs<<<grid_for(V, 256, 152 * 16), 256, 0, s>>>(g.opts, g.ocell_off, V, k, (long long)d * d, b.acc);
+}
 
 void launch_occlusion_allpairs(const Buffers &b, int64_t V, int64_t d, cudaStream_t s) {
     if (V < 2 || d <= 0) return;
@@ -54,6 +172,7 @@ void launch_occlusion_allpairs(const Buffers &b, int64_t V, int64_t d, cudaStrea
     // any d beyond the largest possible distance counts every pair
     const long long d2 = d >= 100000 ? (long long)1e11 : (long long)d * d;
     const unsigned grid = (unsigned)(tiles < (int64_t(1) << 30) ? tiles : (int64_t(1) << 30));
+    count_launches(1);
     k_occl_allpairs<<<grid, OC_ROWS, 0, s>>>((const int2 *)b.xy, (int)V, d2, b.acc, tiles);
 }
 

@@ -33,7 +33,7 @@ class GrError(RuntimeError):
 
 class gr_options(ctypes.Structure):
     _fields_ = [("crossing_path", c_int32), ("cell_log2", c_int32),
-                ("occlusion_path", c_int32), ("reserved", c_int32)]
+                ("occlusion_path", c_int32), ("profile", c_int32)]
 
 
 class gr_params(ctypes.Structure):
@@ -60,6 +60,17 @@ class gr_result(ctypes.Structure):
                 ("occlusion_path", c_int32), ("crossing", gr_crossing_angle_result),
                 ("occlusion_pairs", c_int64), ("occlusion_d", c_int64),
                 ("min_angle", gr_min_angle_result), ("M_l", c_double), ("grid_records", c_int64)]
+
+
+GR_PHASE_NAMES = ["gather", "edge_length", "min_angle", "occl_bin", "occl_pairs", "cross_bin",
+                  "cross_scatter", "cross_pairs", "finalize"]
+
+
+class gr_profile(ctypes.Structure):
+    _fields_ = [("ms", c_double * 16), ("calls", c_int64 * 16)]
+
+    def as_dict(self) -> dict:
+        return {n: (self.ms[i], self.calls[i]) for i, n in enumerate(GR_PHASE_NAMES)}
 
 
 _lib = None
@@ -90,6 +101,9 @@ def load() -> ctypes.CDLL:
         "gr_edge_crossings": ([P, ctypes.POINTER(gr_crossing_counts)], c_int32),
         "gr_crossing_angle": ([P, c_double, ctypes.POINTER(gr_crossing_angle_result)], c_int32),
         "gr_crossings_per_edge": ([P, c_double, P, P], c_int32),
+        "gr_profile_enable": ([P, c_int32], c_int32),
+        "gr_profile_read": ([P, ctypes.POINTER(gr_profile), c_int32], c_int32),
+        "gr_kernel_launches": ([], c_int64),
         "gr_last_error": ([], ctypes.c_char_p),
         "gr_version": ([], ctypes.c_char_p),
     }
@@ -214,6 +228,20 @@ def gr_crossings_per_edge(layout, ideal_rad: float, d_counts, d_dev) -> None:
     _check(load().gr_crossings_per_edge(layout, float(ideal_rad), cp, dp))
 
 
+def gr_profile_enable(layout, enable: bool = True) -> None:
+    _check(load().gr_profile_enable(layout, 1 if enable else 0))
+
+
+def gr_profile_read(layout, reset: bool = False) -> gr_profile:
+    out = gr_profile()
+    _check(load().gr_profile_read(layout, ctypes.byref(out), 1 if reset else 0))
+    return out
+
+
+def gr_kernel_launches() -> int:
+    return int(load().gr_kernel_launches())
+
+
 def gr_last_error() -> str:
     return load().gr_last_error().decode()
 
@@ -238,6 +266,9 @@ class Layout:
 
     def evaluate(self, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0, occlusion_d: int = 0) -> gr_result:
         return gr_evaluate(self.handle, metrics, ideal_rad, occlusion_d)
+
+    def profile(self, reset: bool = False) -> dict:
+        return gr_profile_read(self.handle, reset).as_dict()
 
     def close(self) -> None:
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -31,7 +31,8 @@ def test_header_declares_the_boundary():
     for n in ["gr_layout_create", "gr_layout_update", "gr_layout_destroy", "gr_evaluate",
               "gr_node_occlusion", "gr_min_angle", "gr_edge_length_variation",
               "gr_edge_crossings", "gr_crossing_angle", "gr_crossings_per_edge",
-              "gr_last_error", "gr_version"]:
+              "gr_last_error", "gr_version", "gr_profile_enable", "gr_profile_read",
+              "gr_kernel_launches"]:
         assert n in names
 
 
@@ -52,9 +53,9 @@ def test_struct_layouts_match_the_header(tmp_path):
 #include <stddef.h>
 #include "gr.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gr_options), sizeof(gr_params),
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gr_options), sizeof(gr_params),
          sizeof(gr_crossing_counts), sizeof(gr_crossing_angle_result),
-         sizeof(gr_min_angle_result), sizeof(gr_result));
+         sizeof(gr_min_angle_result), sizeof(gr_result), sizeof(gr_profile));
   printf("%zu %zu %zu %zu\\n", offsetof(gr_result, crossing), offsetof(gr_result, occlusion_pairs),
          offsetof(gr_result, min_angle), offsetof(gr_result, grid_records));
   return 0;
@@ -67,7 +68,7 @@ int main(void) {
     offs = [int(v) for v in lines[1].split()]
     assert sizes == [ctypes.sizeof(t) for t in (gr.gr_options, gr.gr_params, gr.gr_crossing_counts,
                                                 gr.gr_crossing_angle_result, gr.gr_min_angle_result,
-                                                gr.gr_result)]
+                                                gr.gr_result, gr.gr_profile)]
     assert offs == [gr.gr_result.crossing.offset, gr.gr_result.occlusion_pairs.offset,
                     gr.gr_result.min_angle.offset, gr.gr_result.grid_records.offset]
 
@@ -82,3 +83,4 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.gr_evaluate(None, 15, None, None) == gr.GR_EINVAL
     assert lib.gr_layout_destroy(None) == gr.GR_OK
     assert gr.gr_version().startswith("gr ")
+    assert gr.gr_kernel_launches() == 0  # nothing launched in a process without a GPU call

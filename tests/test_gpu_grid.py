@@ -1,0 +1,142 @@
+"""GPU: the uniform-grid paths (crossings a2-a6, occlusion a8) agree with the
+all-pairs kernels and with the oracle for every cell size, including inputs
+built to put intersections and segments exactly on cell boundaries."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_09809_gb300 import build, gr, synth
+
+pytestmark = pytest.mark.gpu
+IDEAL = 7 * math.pi / 18
+REL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    gr.load()
+
+
+def run(xy, edges, d, path, k=0, occl_path=0):
+    opt = gr.gr_options(path, k, occl_path, 0)
+    with gr.Layout(np.ascontiguousarray(xy, np.int32), np.ascontiguousarray(edges, np.int32), opt) as L:
+        return L.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
+
+
+def counts(r):
+    c = r.crossing.c
+    return (c.proper, c.touching, c.collinear_overlaps, c.zero_length_edges)
+
+
+def same_crossings(a, b, label):
+    assert counts(a) == counts(b), label
+    assert a.crossing.angle_dev_sum == pytest.approx(b.crossing.angle_dev_sum, rel=1e-12, abs=1e-9), label
+
+
+def boundary_layout(rng, V, E, step, span_cells, offset_cells=0):
+    """Vertices on a lattice of `step` (a divisor of the cell side), so crossings,
+    endpoints and whole segments fall exactly on cell edges and corners."""
+    n = span_cells * (64 // step)
+    base = offset_cells * 64
+    xy = base + step * rng.integers(0, n + 1, size=(V, 2))
+    a = rng.integers(0, V, size=E)
+    b = (a + rng.integers(1, V, size=E)) % V
+    return np.clip(xy, 0, 65535).astype(np.int32), np.stack([a, b], 1).astype(np.int32)
+
+
+@pytest.mark.parametrize("k", [6, 7, 8, 9, 10, 12, 16])
+def test_grid_equals_allpairs_and_oracle_for_every_cell_size(k):
+    L = synth.plain_layout(V=800, knn_count=1600, random_count=500, seed=31)
+    ref = oracle.crossings(L.xy, L.edges)
+    ap = run(L.xy, L.edges, 300, gr.GR_PATH_ALLPAIRS)
+    g = run(L.xy, L.edges, 300, gr.GR_PATH_GRID, k)
+    assert g.crossing_path == gr.GR_PATH_GRID and g.cell_log2 == k
+    assert ap.crossing_path == gr.GR_PATH_ALLPAIRS
+    same_crossings(g, ap, f"k={k}")
+    assert counts(g) == (ref.proper, ref.touching, ref.collinear, ref.zero_length_edges)
+    assert g.crossing.E_ca == pytest.approx(ref.E_ca, rel=REL)
+    assert g.grid_records >= L.E - ref.zero_length_edges
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("k", [6, 7])
+def test_grid_on_cell_boundaries(seed, k):
+    rng = np.random.default_rng(500 + seed)
+    step = [8, 16, 32, 64][seed % 4]
+    xy, e = boundary_layout(rng, 120, 500, step, span_cells=6, offset_cells=int(rng.integers(0, 1000)))
+    # plus axis-parallel segments lying on grid lines, sharing no vertex
+    extra_pts, extra_e = [], []
+    for i in range(20):
+        x = 64 * int(rng.integers(0, 8)) + int(xy[:, 0].min() // 64 * 64)
+        y0, y1 = sorted(int(v) for v in rng.integers(0, 8, size=2) * 64 + int(xy[:, 1].min() // 64 * 64))
+        extra_pts += [(x, y0), (x, y1 + 64)]
+        extra_e.append((len(xy) + len(extra_pts) - 2, len(xy) + len(extra_pts) - 1))
+    xy = np.concatenate([xy, np.clip(np.array(extra_pts), 0, 65535).astype(np.int32)])
+    e = np.concatenate([e, np.array(extra_e, np.int32)])
+    ref = oracle.crossings(xy, e)
+    g = run(xy, e, 64, gr.GR_PATH_GRID, k)
+    assert counts(g) == (ref.proper, ref.touching, ref.collinear, ref.zero_length_edges), f"seed {seed}"
+    assert g.crossing.angle_dev_sum == pytest.approx(ref.angle_dev_sum, rel=REL, abs=1e-6)
+    assert ref.touching + ref.collinear > 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_grid_on_tiny_degenerate_layouts(seed):
+    rng = np.random.default_rng(900 + seed)
+    L = synth.tiny_degenerate_layout(rng, 50, 600, span=int(rng.integers(3, 40)),
+                                     offset=64 * int(rng.integers(1, 1000)) - int(rng.integers(0, 20)))
+    ref = oracle.crossings(L.xy, L.edges)
+    for k in (6, 8):
+        g = run(L.xy, L.edges, 3, gr.GR_PATH_GRID, k)
+        assert counts(g) == (ref.proper, ref.touching, ref.collinear, ref.zero_length_edges), (seed, k)
+
+
+def test_heavy_cell_spans_many_tiles():
+    # 3,000 segments in one 64-wide cell: about 94 tiles of 32, 4,465 tile pairs
+    rng = np.random.default_rng(2)
+    xy = (1024 + rng.integers(0, 64, size=(2500, 2))).astype(np.int32)
+    e = synth.add_random_edges(rng, 2500, np.zeros((0, 2), np.int32), 3000)
+    ref = oracle.crossings(xy, e)
+    g = run(xy, e, 5, gr.GR_PATH_GRID, 6)
+    assert counts(g) == (ref.proper, ref.touching, ref.collinear, ref.zero_length_edges)
+
+
+@pytest.mark.parametrize("d", [1, 2, 63, 64, 65, 100, 128, 129, 1000, 5000])
+def test_occlusion_grid_matches_oracle(d):
+    rng = np.random.default_rng(d)
+    pts = synth.gaussian_mixture_points(rng, 6000, 8, 400.0)
+    lattice = np.array([(20000 + 64 * i, 20000 + 64 * j) for i in range(30) for j in range(30)], np.int32)
+    xy = np.concatenate([pts, lattice, pts[:50]])  # coincident points too
+    e = np.array([[0, 1]], np.int32)
+    ref = oracle.node_occlusion(xy, d)
+    g = run(xy, e, d, gr.GR_PATH_ALLPAIRS, 0, gr.GR_PATH_GRID)
+    assert g.occlusion_path == gr.GR_PATH_GRID
+    assert g.occlusion_pairs == ref
+    a = run(xy, e, d, gr.GR_PATH_ALLPAIRS, 0, gr.GR_PATH_ALLPAIRS)
+    assert a.occlusion_pairs == ref
+
+
+def test_grid_per_edge_output_matches_oracle():
+    import torch
+    L = synth.plain_layout(V=600, knn_count=1200, random_count=300, seed=44)
+    xy = torch.from_numpy(L.xy).cuda()
+    ed = torch.from_numpy(L.edges).cuda()
+    c = torch.empty((L.E, 3), dtype=torch.int64, device="cuda")
+    dv = torch.empty(L.E, dtype=torch.float64, device="cuda")
+    with gr.Layout(xy, ed, gr.gr_options(gr.GR_PATH_GRID, 7, 0, 0)) as lay:
+        gr.gr_crossings_per_edge(lay.handle, IDEAL, c, dv)
+    ref_c, ref_d = oracle.crossings_of_edges(L.xy, L.edges, np.arange(L.E))
+    assert np.array_equal(c.cpu().numpy(), ref_c)
+    np.testing.assert_allclose(dv.cpu().numpy(), ref_d, rtol=REL, atol=1e-6)
+
+
+def test_auto_path_choices_on_the_workloads():
+    sparse = synth.large_sparse_layout()
+    r = run(sparse.xy, sparse.edges, 64, gr.GR_PATH_AUTO)
+    assert r.crossing_path == gr.GR_PATH_GRID and r.occlusion_path == gr.GR_PATH_GRID
+    dense = synth.dense_long_edge_layout(V=4000, E=40_000)
+    r = run(dense.xy, dense.edges, 256, gr.GR_PATH_AUTO)
+    assert r.crossing_path == gr.GR_PATH_ALLPAIRS
