@@ -1,0 +1,417 @@
+"""Benchmark: exact readability metrics of one synthetic layout per step on GB300.
+
+One step = one pass of the whole hot path over one layout: gather + validation
+of the inputs (gr_layout_update), then all five metrics (gr_evaluate: edge
+length variation, minimum angle, occlusion binning + pairs, crossing binning +
+scatter + pair kernel, final reduction).  The default workload is the large
+sparse layout (200,000 vertices from a 64-component Gaussian mixture, 500,000
+edges: rank 1-5 nearest-neighbour edges plus 1 % uniform long edges, d = 64,
+ideal angle 70 deg).
+
+metric  edge-pair tests/s, resolved: |E| (|E| - 1) / 2 pairs per step (the
+        all-pairs-equivalent rate, which credits the pairs the grid never
+        has to test); `issued_pairs_per_s` reports the pairs actually tested.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on
+the layout's stream, with a 256 MiB L2 flush between steps (outside the
+events; the inputs are smaller than L2).  Barrier + synchronize around the
+timed region; the max over ranks is reported.  With --gpus N > 1 (torchrun),
+every rank evaluates its own replica of the layout (no collective on the data
+path; weak scaling).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+IDEAL = 7.0 * math.pi / 18.0
+L2_FLUSH_BYTES = 256 << 20
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+WORKLOADS = {
+    "large_sparse": ("large_sparse_layout", 64),
+    "dense_long_edge": ("dense_long_edge_layout", 256),
+    "plain": ("plain_layout", 256),
+}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_workload(name):
+    from paper_2411_09809_gb300 import synth
+    fn, d = WORKLOADS[name]
+    return getattr(synth, fn)(), d
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={','.join(self.FIELDS)}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- roofline
+
+def load_peaks() -> tuple[dict, str]:
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def load_traffic(kernel: str, workload: str, src_hash: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None if
+    the kernel source changed since the capture."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(f"{kernel}/{workload}")
+    if not e or e.get("source_sha256") != src_hash:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def kernel_source_hash(files: list[str]) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2411_09809_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+# Algorithmic work per unit, the figures the roofline divides by time:
+#   grid pair kernel (a6): per candidate pair 25 integer ops for the shared-id
+#     skip, four orientations and the sign tests; per E_c pair 60 more for the
+#     angle (cross/dot, conversion, atan2, fixed-point add) and the owner test.
+#   all-pairs kernel (a7): the same per pair, without the owner test (45 more
+#     per E_c pair).
+#   scatter (a4): per record a 16-byte segment + 4-byte edge id write and per
+#     segment a 16 + 4 byte read.
+OPS_PER_PAIR = 25
+OPS_PER_CROSSING_GRID = 60
+OPS_PER_CROSSING_ALLPAIRS = 45
+SM_COUNT = 152
+LANES_PER_SM_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes, one warp instruction per clock each
+
+
+def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload: str) -> dict:
+    pairs_ms, pairs_calls = prof["cross_pairs"]
+    scat_ms, scat_calls = prof["cross_scatter"]
+    grid = res.crossing_path == 1
+    ec = res.crossing.c.crossings
+    if pairs_calls and (not scat_calls or pairs_ms >= scat_ms):
+        t = pairs_ms / pairs_calls / 1e3
+        pairs = res.crossing.c.pairs_tested
+        ops = pairs * OPS_PER_PAIR + ec * (OPS_PER_CROSSING_GRID if grid else OPS_PER_CROSSING_ALLPAIRS)
+        peak = SM_COUNT * LANES_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        kernel = "k_grid_pairs" if grid else "k_cross_allpairs"
+        src = ["k_grid.cu", "pair_math.cuh"] if grid else ["k_crossings.cu", "pair_math.cuh"]
+        achieved = ops / t / 1e12
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Tops/s (int32-equivalent lane ops)", "frac": achieved / peak,
+                "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
+                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
+                "traffic": load_traffic(kernel, workload, kernel_source_hash(src)),
+                "launch_ms": t * 1e3}
+    t = scat_ms / scat_calls / 1e3
+    nbytes = res.grid_records * 20 + n_seg * 20
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = nbytes / t / 1e9
+    return {"kernel": "k_grid_fill", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_kind})",
+            "traffic": load_traffic("k_grid_fill", workload, kernel_source_hash(["k_grid.cu"])),
+            "launch_ms": t * 1e3}
+
+
+# ------------------------------------------------------------- CPU baseline
+
+def cpu_oracle_step(L, d, budget_s: float, rng_seed: int = 0) -> dict:
+    """Times the oracle on a bounded sample of one step and scales it to the full
+    step: crossings of S sampled edges against all edges, occlusion on the first
+    V_s vertices, minimum angle and edge length variation in full."""
+    import numpy as np
+
+    import oracle
+    E, V = L.E, L.V
+    rng = np.random.default_rng(rng_seed)
+    t0 = time.perf_counter()
+    oracle.edge_length_variation(L.xy, L.edges)
+    oracle.min_angle(L.xy, L.edges)
+    t_lin = time.perf_counter() - t0
+    # calibrate crossings on growing samples, then take one of ~budget/2 seconds
+    S, t_small = 16, 0.0
+    for _ in range(2):
+        t0 = time.perf_counter()
+        oracle.crossings_of_edges(L.xy, L.edges, rng.choice(E, size=S, replace=False))
+        t_small = time.perf_counter() - t0
+        if t_small > 0.5 or S >= E:
+            break
+        S = int(min(E, S * 1.0 / max(t_small, 1e-4)))
+    S2 = int(max(16, min(E, S * (0.5 * budget_s) / max(t_small, 1e-6))))
+    sample = rng.choice(E, size=S2, replace=False)
+    t0 = time.perf_counter()
+    oracle.crossings_of_edges(L.xy, L.edges, sample)
+    t_cross = time.perf_counter() - t0
+    cross_full = t_cross * (E * (E - 1) / 2) / (S2 * (E - 1))
+    Vs = min(V, 20000)
+    t0 = time.perf_counter()
+    oracle.node_occlusion(L.xy[:Vs], d)
+    t_occ = time.perf_counter() - t0
+    occ_full = t_occ * (V * (V - 1) / 2) / max(1, Vs * (Vs - 1) / 2)
+    step_s = cross_full + occ_full + t_lin
+    return {"step_s": step_s, "cores": oracle.num_threads(),
+            "sample": f"crossings of {S2} sampled edges against all {E} edges "
+                      f"({S2 * (E - 1):.3g} pair tests, {t_cross:.1f} s), occlusion of the first {Vs} "
+                      f"vertices ({t_occ:.1f} s), minimum angle and edge length variation in full "
+                      f"({t_lin:.2f} s); scaled to one full step ({step_s:.1f} s)",
+            "measured_s": t_lin + t_small + t_cross + t_occ}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle (plain C brute force) on the host cores."""
+    if rank != 0:
+        return
+    L, d = make_workload(args.workload)
+    E = L.E
+    pairs = E * (E - 1) / 2
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_step(L, d, budget / 4)
+    steps = [cpu_oracle_step(L, d, budget, rng_seed=i + 1) for i in range(args.steps)]
+    step_s = statistics.mean(s["step_s"] for s in steps)
+    value = pairs / step_s
+    line = {
+        "impl": "reference", "metric": "edge-pair tests/s", "value": value, "unit": "pairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": workload_config(L, d, args.workload),
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": steps[0]["cores"], "kind": "oracle",
+                         "sample": steps[0]["sample"]},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(L, d, name):
+    return {"workload": L.name, "V": L.V, "E": L.E, "occlusion_d": d, "ideal_deg": 70.0,
+            "metrics": "all five (crossings, crossing angle, occlusion, minimum angle, edge length variation)",
+            "inputs": "seeded synthetic (paper_2411_09809_gb300.synth)",
+            "l2": "256 MiB write between timed steps (inputs are smaller than L2)"}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_09809_gb300 import build as gr_build, gr
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        if rank == 0:
+            gr_build.build()
+        dist.barrier()
+    else:
+        gr_build.build()
+    gr.load()
+    L, d = make_workload(args.workload)
+    dev = torch.device("cuda", local_rank)
+    xy = torch.from_numpy(L.xy).to(dev)
+    edges = torch.from_numpy(L.edges).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lay = gr.Layout(xy, edges, gr.gr_options(0, args.cell_log2, 0, 1), stream=stream.cuda_stream)
+
+    def step():
+        lay.update(xy)
+        return lay.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
+
+    for _ in range(args.warmup):
+        res = step()
+    lay.profile(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = gr.gr_kernel_launches()
+    for i in range(args.steps):
+        flush.fill_(i)
+        starts[i].record(stream)
+        res = step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    launches = gr.gr_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    prof = lay.profile()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    hxy = torch.from_numpy(L.xy).pin_memory()
+    hed = torch.from_numpy(L.edges).pin_memory()
+    io0 = gr.gr_io_bytes(lay.handle)
+    e2e_s = []
+    for i in range(args.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gr.gr_layout_update(lay.handle, hxy, hed)
+        gr.gr_evaluate(lay.handle, gr.GR_METRIC_ALL, IDEAL, d)
+        e2e_s.append(time.perf_counter() - t0)
+    io1 = gr.gr_io_bytes(lay.handle)
+    e2e_ms = statistics.mean(e2e_s) * 1e3
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    n_seg = L.E - res.crossing.c.zero_length_edges
+    peaks, peak_kind = load_peaks()
+    rf = roofline(res, prof, n_seg, peaks, peak_kind, args.workload)
+    lay.close()
+    if rank != 0:
+        return
+    E = L.E
+    pairs = E * (E - 1) / 2
+    value = world * pairs / (ms / 1e3)
+    line = {
+        "metric": "edge-pair tests/s", "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": dict(workload_config(L, d, args.workload),
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       crossing_path={1: "grid", 2: "all-pairs"}.get(res.crossing_path, "none"),
+                       cell_log2=res.cell_log2, grid_records=res.grid_records,
+                       occlusion_path={1: "grid", 2: "all-pairs"}.get(res.occlusion_path, "none")),
+        "issued_pairs_per_s": world * res.crossing.c.pairs_tested / (ms / 1e3),
+        "results": {"E_c": res.crossing.c.crossings, "E_ca": res.crossing.E_ca,
+                    "N_c": res.occlusion_pairs, "M_a": res.min_angle.M_a, "M_l": res.M_l},
+        "phase_ms": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]},
+        "roofline": rf,
+        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": (io1[0] - io0[0]) // args.steps,
+                "d2h_bytes_per_step": (io1[1] - io0[1]) // args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_step(L, d, args.cpu_budget)
+        line["cpu_baseline"] = {"value": pairs / cb["step_s"], "unit": "pairs/s", "cores": cb["cores"],
+                                "kind": "oracle", "sample": cb["sample"]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large_sparse")
+    ap.add_argument("--cell-log2", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)  # rank 0 only; no process group needed
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -205,6 +205,10 @@ typedef struct {
 gr_status gr_profile_enable(gr_layout *layout, int enable);
 gr_status gr_profile_read(gr_layout *layout, gr_profile *out, int reset);
 
+/* Bytes this layout has copied host->device and device->host since it was
+ * created (inputs given in host memory, result and status read-backs). */
+gr_status gr_io_bytes(gr_layout *layout, int64_t *h2d, int64_t *d2h);
+
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all layouts, all threads). */
 int64_t gr_kernel_launches(void);

@@ -67,6 +67,7 @@ struct gr_layout {
     gr_result *h_result = nullptr;  // pinned
     DevAcc *h_acc = nullptr;        // pinned
     bool stats_stale = true;        // h_acc's layout part predates the last update
+    int64_t io_h2d = 0, io_d2h = 0; // bytes copied between host and device
     // phase timing
     bool profiling = false;
     cudaEvent_t ev[2 * GR_NUM_PHASES] = {};
@@ -220,10 +221,12 @@ gr_status enqueue_inputs(gr_layout *L, const void *xy, const int32_t *edges) {
     if (V > 0) {
         const cudaMemcpyKind k = is_device_pointer(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         GR_CU(cudaMemcpyAsync(L->b.xy, xy, sizeof(int32_t) * 2 * V, k, s));
+        if (k == cudaMemcpyHostToDevice) L->io_h2d += (int64_t)sizeof(int32_t) * 2 * V;
     }
     if (E > 0 && edges) {
         const cudaMemcpyKind k = is_device_pointer(edges) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         GR_CU(cudaMemcpyAsync(L->b.edges, edges, sizeof(int32_t) * 2 * E, k, s));
+        if (k == cudaMemcpyHostToDevice) L->io_h2d += (int64_t)sizeof(int32_t) * 2 * E;
     }
     launch_check_vertices(L->b.xy, V, L->b, s);
     launch_gather(L->b.xy, V, L->b.edges, E, L->b, s);
@@ -258,6 +261,7 @@ gr_status read_params(const gr_params *p, double *ideal, int64_t *d) {
 gr_status refresh_stats(gr_layout *L) {
     if (!L->stats_stale) return GR_OK;
     GR_CU(cudaMemcpyAsync(L->h_acc, L->b.acc, offsetof(DevAcc, eval_status), cudaMemcpyDeviceToHost, L->stream));
+    L->io_d2h += (int64_t)offsetof(DevAcc, eval_status);
     GR_CU(cudaStreamSynchronize(L->stream));
     L->stats_stale = false;
     return GR_OK;
@@ -423,6 +427,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     if (need_sync) {
         GR_CU(cudaGetLastError());
         GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+        L->io_d2h += (int64_t)sizeof(DevAcc);
         GR_CU(cudaStreamSynchronize(s));
         if ((st = status_to_error(L->h_acc->eval_status)) != GR_OK) return st;
     }
@@ -478,6 +483,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     GR_CU(cudaGetLastError());
     GR_CU(cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s));
     GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+    L->io_d2h += (int64_t)(sizeof(gr_result) + sizeof(DevAcc));
     phase_end(L, GR_PHASE_FINALIZE);
     GR_CU(cudaStreamSynchronize(s));
     phase_collect(L);
@@ -595,6 +601,14 @@ gr_status gr_profile_read(gr_layout *L, gr_profile *out, int reset) {
             L->prof_calls[ph] = 0;
         }
     }
+    return GR_OK;
+}
+
+gr_status gr_io_bytes(gr_layout *L, int64_t *h2d, int64_t *d2h) {
+    g_err.clear();
+    if (!L || !h2d || !d2h) return fail(GR_EINVAL, "NULL argument");
+    *h2d = L->io_h2d;
+    *d2h = L->io_d2h;
     return GR_OK;
 }
 

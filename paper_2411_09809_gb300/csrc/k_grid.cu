@@ -36,31 +36,77 @@ __device__ __forceinline__ int floordiv_pos(long long num, int den) {
     return q;
 }
 
-// Calls f(cx, cy) for every cell of side 2^k met by the closed segment
-// (x0, y0)-(x1, y1), column by column.  In a column the rows span from the
-// row of the segment's y at the column's left x to the row at its right x
-// (closed at both ends: a superset of the half-open cells met).
+// A segment walked along its major axis: coordinates swapped when |dy| > |dx|
+// (tr), then ordered so that x0 <= x1; afterwards |y1 - y0| <= x1 - x0 and
+// x1 > x0 (zero-length segments never reach the grid).
+struct DdaSeg {
+    int x0, y0, x1, y1;
+    bool tr;
+};
+
+__device__ __forceinline__ DdaSeg dda_norm(SegRec r) {
+    int ax = px(r.x), ay = py(r.x), bx = px(r.y), by = py(r.y);
+    const bool tr = abs(by - ay) > abs(bx - ax);
+    if (tr) {
+        int t = ax; ax = ay; ay = t;
+        t = bx; bx = by; by = t;
+    }
+    if (ax > bx) {
+        int t = ax; ax = bx; bx = t;
+        t = ay; ay = by; by = t;
+    }
+    return DdaSeg{ax, ay, bx, by, tr};
+}
+
+// Minor-axis cell index of the segment at major coordinate X, x0 <= X <= x1:
+// floor(y(X) / 2^k) with y(X) = y0 + (X - x0) (y1 - y0) / (x1 - x0), exact.
+__device__ __forceinline__ int minor_at(const DdaSeg &s, int X, int k) {
+    if (X == s.x0) return s.y0 >> k;
+    if (X == s.x1) return s.y1 >> k;
+    const int dx = s.x1 - s.x0, dy = s.y1 - s.y0;
+    return floordiv_pos((long long)s.y0 * dx + (long long)(X - s.x0) * dy, dx) >> k;
+}
+
+// The cells of major line c: minor indices between those at the line's two
+// ends, closed at both (a superset of the half-open cells the segment meets;
+// the slope is at most 1, so there are at most three).
 template <class F>
-__device__ __forceinline__ void for_each_cell(int x0, int y0, int x1, int y1, int k, F &&f) {
-    if (x0 > x1) {
-        int t = x0; x0 = x1; x1 = t;
-        t = y0; y0 = y1; y1 = t;
+__device__ __forceinline__ void dda_line(const DdaSeg &s, int c, int k, SegRec r, int32_t eid, F &f) {
+    const int ra = minor_at(s, max(s.x0, c << k), k);
+    const int rb = minor_at(s, min(s.x1, (c + 1) << k), k);
+    for (int q = min(ra, rb); q <= max(ra, rb); ++q) {
+        if (s.tr) f(q, c, r, eid); else f(c, q, r, eid);
     }
-    const int c0 = x0 >> k, c1 = x1 >> k;
-    if (x0 == x1) {
-        const int ra = min(y0, y1) >> k, rb = max(y0, y1) >> k;
-        for (int r = ra; r <= rb; ++r) f(c0, r);
-        return;
+}
+
+constexpr int LONG_LINES = 8;  // segments spanning more lines are walked by a warp
+
+// Calls f(cx, cy, record, edge id) for every cell of side 2^k that the
+// segment held by this lane (valid if `ok`) meets.  Short segments are walked
+// by their own lane; long ones by the whole warp, one major line per lane, so
+// that a few long edges do not serialise their warp.  Every lane of the warp
+// must call it.  Both DDA passes use it, so they enumerate the same cells.
+template <class F>
+__device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, bool ok, int k, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const DdaSeg s = dda_norm(r);
+    const int nl = ok ? (s.x1 >> k) - (s.x0 >> k) + 1 : 0;
+    const bool is_long = nl > LONG_LINES;
+    if (ok && !is_long) {
+        for (int c = s.x0 >> k, e = s.x1 >> k; c <= e; ++c) dda_line(s, c, k, r, eid, f);
     }
-    const int dx = x1 - x0, dy = y1 - y0;
-    int rprev = y0 >> k;
-    for (int c = c0; c <= c1; ++c) {
-        const int xh = min(x1, (c + 1) << k);
-        const int rh = (xh == x1) ? (y1 >> k)
-                                  : (floordiv_pos((long long)y0 * dx + (long long)(xh - x0) * dy, dx) >> k);
-        const int ra = min(rprev, rh), rb = max(rprev, rh);
-        for (int r = ra; r <= rb; ++r) f(c, r);
-        rprev = rh;
+    unsigned m = __ballot_sync(0xffffffffu, is_long);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        SegRec q;
+        q.x = __shfl_sync(0xffffffffu, r.x, src);
+        q.y = __shfl_sync(0xffffffffu, r.y, src);
+        q.z = __shfl_sync(0xffffffffu, r.z, src);
+        q.w = __shfl_sync(0xffffffffu, r.w, src);
+        const int32_t qe = __shfl_sync(0xffffffffu, eid, src);
+        const DdaSeg t = dda_norm(q);
+        for (int c = (t.x0 >> k) + lane, e = t.x1 >> k; c <= e; c += 32) dda_line(t, c, k, q, qe, f);
     }
 }
 
@@ -70,11 +116,13 @@ __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ s
                                                     uint32_t *__restrict__ cell_cnt) {
     const int64_t n = acc->n_seg;
     const int G = 65536 >> k;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const SegRec r = seg[s];
-        for_each_cell(px(r.x), py(r.x), px(r.y), py(r.y), k,
-                      [&](int cx, int cy) { atomicAdd(&cell_cnt[cy * G + cx], 1u); });
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool ok = i < n;
+        const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
+        warp_for_each_cell(r, 0, ok, k, [&](int cx, int cy, SegRec, int32_t) {
+            atomicAdd(&cell_cnt[cy * G + cx], 1u);
+        });
     }
 }
 
@@ -97,7 +145,8 @@ __global__ void __launch_bounds__(256) k_cell_items(const uint32_t *__restrict__
     if (threadIdx.x == 0) atomic_add_u64(&acc->grid_work, w);
 }
 
-// a4 -- scatter of the records into their cells.
+// a4 -- scatter of the records into their cells: the segment record and its
+// edge id go to cell_off[c] + (running count of cell c).
 __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ seg,
                                                    const int32_t *__restrict__ seg_eid,
                                                    const DevAcc *__restrict__ acc, int k,
@@ -111,16 +160,16 @@ __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ se
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_OVERFLOW);
         return;
     }
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const SegRec r = seg[s];
-        const int32_t eid = seg_eid[s];
-        for_each_cell(px(r.x), py(r.x), px(r.y), py(r.y), k, [&](int cx, int cy) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool ok = i < n;
+        const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
+        const int32_t eid = ok ? seg_eid[i] : 0;
+        warp_for_each_cell(r, eid, ok, k, [&](int cx, int cy, SegRec q, int32_t qe) {
             const int c = cy * G + cx;
-            const uint32_t slot = atomicAdd(&cell_fill[c], 1u);
-            const uint32_t pos = cell_off[c] + slot;
-            rec[pos] = r;
-            rec_eid[pos] = eid;
+            const uint32_t pos = cell_off[c] + atomicAdd(&cell_fill[c], 1u);
+            rec[pos] = q;
+            rec_eid[pos] = qe;
         });
     }
 }

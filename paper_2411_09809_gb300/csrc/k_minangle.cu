@@ -17,7 +17,8 @@ namespace gr {
 
 namespace {
 
-constexpr int MA_WARPS = 8;  // vertices in flight per block
+constexpr int MA_THREADS = 256;  // vertices in flight per block
+constexpr int MA_HEAVY = 32;     // degree above which a warp shares one vertex
 constexpr int MA_MAX_BLOCKS = 1024;
 
 __global__ void k_degree(const SegRec *__restrict__ seg, const DevAcc *__restrict__ acc,
@@ -53,58 +54,98 @@ __device__ __forceinline__ long long dot2(int2 a, int2 b) {
     return (long long)a.x * b.x + (long long)a.y * b.y;
 }
 
-// One warp per vertex (fixed vertex -> block mapping, so the per-block FP64
-// partial sums are deterministic).  d_v = (2 pi / deg - min) / (2 pi / deg)
+// Exact successor of direction di among dirs[0..k) (index i excluded): the
+// direction reached first when turning counter-clockwise from di, a
+// direction equal to di being reached at angle 0.
+__device__ __forceinline__ int2 ccw_successor(const int2 *__restrict__ d, int k, int i, int2 di) {
+    int2 db = make_int2(0, 0);
+    int hb = 2;
+    for (int j = 0; j < k; ++j) {
+        if (j == i) continue;
+        const int2 dj = d[j];
+        const long long cr = cross2(di, dj), dt = dot2(di, dj);
+        const int hj = (cr > 0 || (cr == 0 && dt > 0)) ? 0 : 1;  // half plane relative to di
+        if (hj < hb || (hj == hb && cross2(dj, db) > 0)) {
+            db = dj;
+            hb = hj;
+        }
+    }
+    return db;
+}
+
+__device__ __forceinline__ float ccw_gap_f(int2 a, int2 b) {
+    float g = atan2f((float)cross2(a, b), (float)dot2(a, b));
+    return g < 0.f ? g + 6.28318530717958647692f : g;
+}
+
+__device__ __forceinline__ double ccw_gap_d(int2 a, int2 b) {
+    double g = atan2((double)cross2(a, b), (double)dot2(a, b));
+    return g < 0.0 ? g + 2.0 * M_PI : g;
+}
+
+// One thread per vertex (fixed vertex -> block mapping, so the per-block FP64
+// partial sums are deterministic); vertices of degree > 32 are taken by the
+// whole warp after the per-thread pass.  Gaps are compared in FP32 and the
+// smallest is recomputed in FP64.  d_v = (2 pi / deg - min) / (2 pi / deg)
 // for every vertex with deg >= 2 (deg = 1 has a single 2 pi gap, d_v = 0).
-__global__ void __launch_bounds__(MA_WARPS * 32) k_min_angle(const uint32_t *__restrict__ off,
-                                                             const int2 *__restrict__ dirs, int64_t V,
-                                                             double *__restrict__ part,
-                                                             uint32_t *__restrict__ cnt) {
+__global__ void __launch_bounds__(MA_THREADS) k_min_angle(const uint32_t *__restrict__ off,
+                                                          const int2 *__restrict__ dirs, int64_t V,
+                                                          double *__restrict__ part,
+                                                          uint32_t *__restrict__ cnt) {
     __shared__ double shd[32];
     __shared__ uint64_t shu[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t step = (int64_t)gridDim.x * MA_WARPS;
+    const int lane = threadIdx.x & 31;
+    const int64_t step = (int64_t)gridDim.x * MA_THREADS;
     double dsum = 0.0;
     uint32_t nv = 0;
-    for (int64_t v = (int64_t)blockIdx.x * MA_WARPS + wid; v < V; v += step) {
-        const uint32_t start = off[v];
-        const int k = (int)(off[v + 1] - start);
-        if (k < 2) continue;  // warp-uniform
-        float gmin = 1e30f;
-        int2 bi = make_int2(1, 0), bs = make_int2(1, 0);
-        for (int i = lane; i < k; i += 32) {
-            const int2 di = dirs[start + i];
-            int2 db = make_int2(0, 0);
-            int hb = 2;
-            for (int j = 0; j < k; ++j) {
-                if (j == i) continue;
-                const int2 dj = dirs[start + j];
-                const long long cr = cross2(di, dj), dt = dot2(di, dj);
-                const int hj = (cr > 0 || (cr == 0 && dt > 0)) ? 0 : 1;
-                if (hj < hb || (hj == hb && cross2(dj, db) > 0)) {
-                    db = dj;
-                    hb = hj;
-                }
-            }
-            float g = atan2f((float)cross2(di, db), (float)dot2(di, db));
-            if (g < 0.f) g += 6.28318530717958647692f;
-            if (g < gmin) {
-                gmin = g;
-                bi = di;
-                bs = db;
-            }
+    for (int64_t base = (int64_t)blockIdx.x * MA_THREADS; base < V; base += step) {
+        const int64_t v = base + threadIdx.x;
+        int k = 0;
+        uint32_t start = 0;
+        if (v < V) {
+            start = off[v];
+            k = (int)(off[v + 1] - start);
         }
-        // warp argmin; the winning pair's gap is recomputed in FP64
-        float m = gmin;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        const unsigned win = __ballot_sync(0xffffffffu, gmin == m);
-        if (lane == __ffs(win) - 1) {
-            double g = atan2((double)cross2(bi, bs), (double)dot2(bi, bs));
-            if (g < 0.0) g += 2.0 * M_PI;
+        const bool heavy = k > MA_HEAVY;
+        if (k >= 2 && !heavy) {
+            const int2 *d = dirs + start;
+            float gmin = 1e30f;
+            int2 bi = make_int2(1, 0), bs = make_int2(1, 0);
+            for (int i = 0; i < k; ++i) {
+                const int2 di = d[i];
+                const int2 db = ccw_successor(d, k, i, di);
+                const float g = ccw_gap_f(di, db);
+                if (g < gmin) { gmin = g; bi = di; bs = db; }
+            }
             const double ideal = 2.0 * M_PI / (double)k;
-            dsum += (ideal - g) / ideal;
+            dsum += (ideal - ccw_gap_d(bi, bs)) / ideal;
             nv += 1;
+        }
+        // heavy vertices: the whole warp splits the directions of one vertex
+        unsigned hm = __ballot_sync(0xffffffffu, heavy);
+        while (hm) {
+            const int src = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const uint32_t hs = __shfl_sync(0xffffffffu, start, src);
+            const int hk = __shfl_sync(0xffffffffu, k, src);
+            const int2 *d = dirs + hs;
+            float gmin = 1e30f;
+            int2 bi = make_int2(1, 0), bs = make_int2(1, 0);
+            for (int i = lane; i < hk; i += 32) {
+                const int2 di = d[i];
+                const int2 db = ccw_successor(d, hk, i, di);
+                const float g = ccw_gap_f(di, db);
+                if (g < gmin) { gmin = g; bi = di; bs = db; }
+            }
+            float m = gmin;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const unsigned win = __ballot_sync(0xffffffffu, gmin == m);
+            if (lane == __ffs(win) - 1) {
+                const double ideal = 2.0 * M_PI / (double)hk;
+                dsum += (ideal - ccw_gap_d(bi, bs)) / ideal;
+                nv += 1;
+            }
         }
     }
     const double s = block_sum<double>(dsum, shd);
@@ -125,7 +166,7 @@ int grid_for(int64_t n, int threads, int max_blocks) {
 }  // namespace
 
 int min_angle_blocks(int64_t V) {
-    int64_t b = (V + MA_WARPS - 1) / MA_WARPS;
+    int64_t b = (V + MA_THREADS - 1) / MA_THREADS;
     if (b < 1) b = 1;
     if (b > MA_MAX_BLOCKS) b = MA_MAX_BLOCKS;
     return (int)b;
@@ -140,7 +181,7 @@ void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
     if (E > 0) k_degree<<<gb, 256, 0, s>>>(b.seg, b.acc, b.deg);
     launch_scan_u32(b.deg, b.deg, V, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
     if (E > 0) k_fill_dirs<<<gb, 256, 0, s>>>(b.seg, b.acc, b.deg, b.deg_fill, b.dirs);
-    k_min_angle<<<min_angle_blocks(V), MA_WARPS * 32, 0, s>>>(b.deg, b.dirs, V, b.ma_part, b.ma_cnt);
+    k_min_angle<<<min_angle_blocks(V), MA_THREADS, 0, s>>>(b.deg, b.dirs, V, b.ma_part, b.ma_cnt);
 }
 
 }  // namespace gr

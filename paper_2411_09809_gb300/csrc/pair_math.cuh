@@ -9,6 +9,7 @@
 // 32x32->64 multiply-adds.  Magnitudes stay below 2^35.
 #pragma once
 
+#include "atan_poly.cuh"
 #include "gr_internal.cuh"
 
 namespace gr {
@@ -54,12 +55,11 @@ __device__ __forceinline__ ColSeg make_col(SegRec s) {
 __device__ __forceinline__ uint32_t lex_key(int x, int y) { return (uint32_t(x) << 16) | uint32_t(y); }
 
 // Classifies the unordered pair {r, c} under the library's reading of
-// Algorithm 4 (shared ids never cross; collinear pairs that meet are
-// reported separately; proper and touching pairs form E_c).  For an E_c pair
-// `dev` receives |ideal - a_c| with a_c = atan2(|u x v|, |u . v|), the acute
-// angle between the lines (Algorithm 5), in FP32 from the exact integer cross
-// and dot products.  `o` receives the four orientations when non-null.
-__device__ __forceinline__ int classify(const RowSeg &r, const ColSeg &c, float ideal, float &dev) {
+// Algorithm 4: shared vertex ids never cross; a collinear pair whose extents
+// meet is reported separately; otherwise the pair is in E_c when both
+// orientation products are <= 0 (PAIR_PROPER when both are < 0, else
+// PAIR_TOUCHING).
+__device__ __forceinline__ int classify_kind(const RowSeg &r, const ColSeg &c) {
     if ((r.ida == c.idc) | (r.ida == c.idd) | (r.idb == c.idc) | (r.idb == c.idd)) return PAIR_NONE;
     const long long o1 = (long long)r.ux * c.cy - (long long)r.uy * c.cx - r.k;  // orient(a, b, c)
     const long long o2 = (long long)r.ux * c.dy - (long long)r.uy * c.dx - r.k;  // orient(a, b, d)
@@ -75,10 +75,39 @@ __device__ __forceinline__ int classify(const RowSeg &r, const ColSeg &c, float 
         const uint32_t hi = min(max(ka, kb), max(kc, kd));
         return lo <= hi ? PAIR_COLLINEAR : PAIR_NONE;
     }
-    const int kind = (o1 != 0 && o2 != 0 && o3 != 0 && o4 != 0) ? PAIR_PROPER : PAIR_TOUCHING;
-    const float cr = (float)((long long)r.ux * c.vy - (long long)r.uy * c.vx);
-    const float dt = (float)((long long)r.ux * c.vx + (long long)r.uy * c.vy);
-    dev = fabsf(ideal - atan2f(fabsf(cr), fabsf(dt)));
+    return (o1 != 0 && o2 != 0 && o3 != 0 && o4 != 0) ? PAIR_PROPER : PAIR_TOUCHING;
+}
+
+// |u x v| and |u . v| of an E_c pair: exact in int64, then rounded once to
+// FP32.  Both are symmetric in the two segments, so every path that meets
+// the pair (in either role) derives the same angle, bit for bit.
+__device__ __forceinline__ float2 cross_dot_abs(const RowSeg &r, const ColSeg &c) {
+    const long long cr = (long long)r.ux * c.vy - (long long)r.uy * c.vx;
+    const long long dt = (long long)r.ux * c.vx + (long long)r.uy * c.vy;
+    return make_float2(fabsf((float)cr), fabsf((float)dt));
+}
+
+// The acute angle between two lines (Sec. 3.1.5, "intersecting angles" from
+// arctan) from y = |u x v| and x = |u . v|, not both zero:
+// atan(min / max), reflected about pi/4 when y > x.
+__device__ __forceinline__ float acute_angle(float y, float x) {
+    const float a = atan01(__fdividef(fminf(x, y), fmaxf(x, y)));
+    return y > x ? 1.57079632679489662f - a : a;
+}
+
+// |ideal - a_c| as a 2^32-scaled fixed-point integer (exact conversion of
+// the FP32 value).
+__device__ __forceinline__ uint64_t dev_fixed(float2 yx, float ideal) {
+    return (uint64_t)__float2ull_rn(fabsf(ideal - acute_angle(yx.x, yx.y)) * kDevScale);
+}
+
+// classify_kind plus |ideal - a_c| for E_c pairs.
+__device__ __forceinline__ int classify(const RowSeg &r, const ColSeg &c, float ideal, float &dev) {
+    const int kind = classify_kind(r, c);
+    if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) {
+        const float2 yx = cross_dot_abs(r, c);
+        dev = fabsf(ideal - acute_angle(yx.x, yx.y));
+    }
     return kind;
 }
 

@@ -104,6 +104,7 @@ def load() -> ctypes.CDLL:
         "gr_profile_enable": ([P, c_int32], c_int32),
         "gr_profile_read": ([P, ctypes.POINTER(gr_profile), c_int32], c_int32),
         "gr_kernel_launches": ([], c_int64),
+        "gr_io_bytes": ([P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)], c_int32),
         "gr_last_error": ([], ctypes.c_char_p),
         "gr_version": ([], ctypes.c_char_p),
     }
@@ -236,6 +237,12 @@ def gr_profile_read(layout, reset: bool = False) -> gr_profile:
     out = gr_profile()
     _check(load().gr_profile_read(layout, ctypes.byref(out), 1 if reset else 0))
     return out
+
+
+def gr_io_bytes(layout) -> tuple[int, int]:
+    h2d, d2h = c_int64(), c_int64()
+    _check(load().gr_io_bytes(layout, ctypes.byref(h2d), ctypes.byref(d2h)))
+    return h2d.value, d2h.value
 
 
 def gr_kernel_launches() -> int:
