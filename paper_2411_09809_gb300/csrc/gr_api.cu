@@ -36,6 +36,9 @@ gr_status cuda_fail(cudaError_t e, const char *what) {
 
 constexpr double kDefaultIdeal = 7.0 * M_PI / 18.0;  // 70 degrees (Sec. 2.1)
 
+// The ideal angle in the kernels' angle units (pi / 2^32), <= 2^31.
+uint32_t ideal_units(double ideal) { return (uint32_t)llrint(ideal / M_PI * 4294967296.0); }
+
 bool is_device_pointer(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -81,7 +84,8 @@ namespace {
 std::atomic<int64_t> g_launches{0};
 
 void free_grid(GridBuffers &g) {
-    void *ptrs[] = {g.cell_off, g.item_off, g.cell_fill, g.rec, g.rec_eid, g.ocell_off, g.ocell_fill, g.opts};
+    void *ptrs[] = {g.cell_off, g.item_off, g.cell_fill, g.rec, g.rec_eid, g.rec_theta, g.ocell_off, g.ocell_fill,
+                    g.opts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g = GridBuffers{};
@@ -90,7 +94,7 @@ void free_grid(GridBuffers &g) {
 void free_layout(gr_layout *L) {
     if (!L) return;
     Buffers &b = L->b;
-    void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.len2, b.acc, b.elv_part, b.ma_part,
+    void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.ma_part,
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.result};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -112,6 +116,7 @@ gr_status alloc_layout(gr_layout *L) {
     GR_TRY(dalloc(&b.edges, 2 * (size_t)E));
     GR_TRY(dalloc(&b.seg, (size_t)E));
     GR_TRY(dalloc(&b.seg_eid, (size_t)E));
+    GR_TRY(dalloc(&b.seg_theta, (size_t)E));
     GR_TRY(dalloc(&b.len2, (size_t)E));
     GR_TRY(dalloc(&b.acc, 1));
     GR_TRY(dalloc(&b.elv_part, 2 * (size_t)kElvBlocks));
@@ -151,13 +156,16 @@ gr_status ensure_records(gr_layout *L, uint64_t R) {
     if (g.rec_cap >= R && g.rec) return GR_OK;
     if (g.rec) cudaFree(g.rec);
     if (g.rec_eid) cudaFree(g.rec_eid);
+    if (g.rec_theta) cudaFree(g.rec_theta);
     g.rec = nullptr;
     g.rec_eid = nullptr;
+    g.rec_theta = nullptr;
     g.rec_cap = 0;
     const uint64_t cap = R + R / 4 + 1024;
     gr_status st;
     if ((st = dalloc(&g.rec, (size_t)cap)) != GR_OK) return st;
     if ((st = dalloc(&g.rec_eid, (size_t)cap)) != GR_OK) return st;
+    if ((st = dalloc(&g.rec_theta, (size_t)cap)) != GR_OK) return st;
     g.rec_cap = cap;
     return GR_OK;
 }
@@ -448,13 +456,13 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
             launch_grid_scatter(b, E, L->g, cp.k, s);
             phase_end(L, GR_PHASE_CROSS_SCATTER);
             phase_begin(L, GR_PHASE_CROSS_PAIRS);
-            launch_grid_pairs(b, L->g, cp.k, a.grid_items, (float)ideal, PerEdge{}, s);
+            launch_grid_pairs(b, L->g, cp.k, a.grid_items, ideal_units(ideal), PerEdge{}, s);
             phase_end(L, GR_PHASE_CROSS_PAIRS);
             path = GR_PATH_GRID;
             pairs_tested = (int64_t)a.grid_work;
         } else {
             phase_begin(L, GR_PHASE_CROSS_PAIRS);
-            launch_crossings_allpairs(b, E, (float)ideal, PerEdge{}, s);
+            launch_crossings_allpairs(b, E, ideal_units(ideal), PerEdge{}, s);
             phase_end(L, GR_PHASE_CROSS_PAIRS);
             path = GR_PATH_ALLPAIRS;
         }
@@ -572,9 +580,9 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     if (cp.grid && L->h_acc->n_seg >= 2) {
         if ((st2 = ensure_records(L, L->h_acc->records)) != GR_OK) return st2;
         launch_grid_scatter(b, E, L->g, cp.k, s);
-        launch_grid_pairs(b, L->g, cp.k, L->h_acc->grid_items, (float)ideal, pe, s);
+        launch_grid_pairs(b, L->g, cp.k, L->h_acc->grid_items, ideal_units(ideal), pe, s);
     } else {
-        launch_crossings_allpairs(b, E, (float)ideal, pe, s);
+        launch_crossings_allpairs(b, E, ideal_units(ideal), pe, s);
     }
     launch_per_edge_export(pe.dev, E, s);
     GR_CU(cudaGetLastError());

@@ -18,11 +18,13 @@ enum : uint32_t {
     ST_SCAN_OVERFLOW = 8u // an exclusive scan total exceeded 2^32 - 1
 };
 
-// Scale of the fixed-point angle-deviation sums: each |ideal - a_c| is an
-// FP32 value; multiplied by 2^32 it is an exact integer, so the sum of all
-// terms is exact, associative and independent of the order pairs are visited.
-constexpr float kDevScale = 4294967296.0f;  // 2^32
-constexpr double kDevUnscale = 1.0 / 4294967296.0;
+// Angles are held as uint32 in units of pi / 2^32: the direction of a line
+// (an angle mod pi) is a point of Z / 2^32, a difference of two directions
+// wraps correctly, and the acute angle between two lines is
+// min(d, 2^32 - d) <= 2^31.  Every |ideal - a_c| is an integer in these units,
+// so the sums over pairs are exact, associative and independent of the
+// order pairs are visited in; the quantisation of a direction is < 1e-9 rad.
+constexpr double kAngleUnit = 3.14159265358979323846 / 4294967296.0;
 
 // Device-global accumulators.  The first block is written by
 // gr_layout_create / gr_layout_update; the rest is zeroed by every
@@ -38,7 +40,7 @@ struct DevAcc {
     uint64_t proper;
     uint64_t touching;
     uint64_t collinear;
-    uint64_t dev_lo, dev_hi;   // 128-bit sum of |ideal - a_c| * 2^32
+    uint64_t dev_lo, dev_hi;   // 128-bit sum of |ideal - a_c| in units of pi / 2^32
     uint64_t occlusion;
     uint64_t records;          // grid (edge, cell) records
     uint64_t grid_items;       // pair-kernel work items
@@ -65,6 +67,7 @@ struct Buffers {
     int32_t *edges = nullptr;     // [E][2] staging copy of host edges
     SegRec *seg = nullptr;        // [E] compacted segments
     int32_t *seg_eid = nullptr;   // [E] original edge index of seg[i]
+    uint32_t *seg_theta = nullptr;// [E] line direction of seg[i] (units of pi / 2^32)
     int64_t *len2 = nullptr;      // [E] squared length of every edge
     DevAcc *acc = nullptr;        // accumulators
     double *elv_part = nullptr;   // [kElvBlocks * 2] per-block FP64 partial sums
@@ -84,6 +87,7 @@ struct GridBuffers {
     uint32_t *cell_fill = nullptr; // [C]
     SegRec *rec = nullptr;         // [rec_cap] segments sorted by cell
     int32_t *rec_eid = nullptr;    // [rec_cap] their edge ids
+    uint32_t *rec_theta = nullptr; // [rec_cap] their line directions
     uint64_t rec_cap = 0;
     int cells_cap = 0;             // C the cell arrays are sized for
     // occlusion grid
@@ -110,7 +114,8 @@ void launch_gather(const int32_t *xy, int64_t V, const int32_t *edges, int64_t E
 void launch_check_vertices(const int32_t *xy, int64_t V, Buffers &b, cudaStream_t s);
 
 // Optional per-edge outputs of the crossing kernels (both nullable together):
-// counts [E][3] (proper, touching, collinear) and fixed-point dev sums [E].
+// counts [E][3] (proper, touching, collinear) and integer dev sums [E] in
+// units of pi / 2^32.
 struct PerEdge {
     uint64_t *counts = nullptr;
     uint64_t *dev = nullptr;
@@ -118,7 +123,8 @@ struct PerEdge {
 
 // a7: tiled all-pairs crossing kernel over the compacted segments.
 // `n_seg` is the compacted segment count (read back from the device).
-void launch_crossings_allpairs(const Buffers &b, int64_t n_seg, float ideal, PerEdge pe,
+// `ideal` is the ideal crossing angle in units of pi / 2^32 (<= 2^31).
+void launch_crossings_allpairs(const Buffers &b, int64_t n_seg, uint32_t ideal, PerEdge pe,
                                cudaStream_t s);
 
 // a2-a4: DDA count, cell offsets, work items (records -> acc->records,
@@ -127,7 +133,7 @@ void launch_grid_count(const Buffers &b, int64_t E, const GridBuffers &g, int k,
 // a4: scatter of the records into their cells (needs rec_cap >= records).
 void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int k, cudaStream_t s);
 // a6: per-cell pair kernel with the owner-cell test.
-void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items, float ideal,
+void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items, uint32_t ideal,
                        PerEdge pe, cudaStream_t s);
 
 // a8 occlusion grid: cell side 2^k >= d.  Count + scan + stencil work
@@ -157,7 +163,7 @@ void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal
                      int64_t d, int ma_blocks, int32_t path, int32_t cell_log2,
                      int32_t occl_path, int64_t pairs_tested, cudaStream_t s);
 
-// Per-edge output conversion: fixed-point dev sums to double, in place.
+// Per-edge output conversion: integer dev sums to radians (double), in place.
 void launch_per_edge_export(uint64_t *dev_fixed, int64_t E, cudaStream_t s);
 
 // ------------------------------------------------------------- device helpers

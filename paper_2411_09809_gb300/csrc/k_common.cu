@@ -21,10 +21,20 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // checks them, stores the exact squared length of every edge and appends the
 // non-zero-length ones to the compacted segment array (warp-aggregated slot
 // reservation; the order of the compacted array does not affect any result).
+// Direction of the line through a segment with vector (dx, dy), as an angle
+// in [0, pi) in units of pi / 2^32 (FP64 atan2, rounded to the nearest unit).
+__device__ __forceinline__ uint32_t line_direction(int dx, int dy) {
+    double t = atan2((double)dy, (double)dx);  // (-pi, pi]
+    if (t < 0.0) t += 3.14159265358979323846;
+    const double u = rint(t * (4294967296.0 / 3.14159265358979323846));  // [0, 2^32]
+    return (uint32_t)(unsigned long long)u;  // 2^32 (angle pi) wraps to 0
+}
+
 __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int64_t V,
                                                 const int2 *__restrict__ edges, int64_t E,
                                                 SegRec *__restrict__ seg,
                                                 int32_t *__restrict__ seg_eid,
+                                                uint32_t *__restrict__ seg_theta,
                                                 int64_t *__restrict__ len2, DevAcc *acc) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -71,6 +81,7 @@ __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int
             const uint32_t pos = slot + __popc(mk & lanemask_lt());
             seg[pos] = r;
             seg_eid[pos] = (int32_t)e;
+            seg_theta[pos] = line_direction(px(r.y) - px(r.x), py(r.y) - py(r.x));
         }
     }
 }
@@ -269,7 +280,7 @@ __global__ void __launch_bounds__(256) k_finalize(const DevAcc *__restrict__ acc
     r.crossing.c.zero_length_edges = (int64_t)acc->zero_len;
     const uint64_t ns = acc->n_seg;
     r.crossing.c.pairs_tested = pairs_tested >= 0 ? pairs_tested : (int64_t)(ns * (ns - (ns > 0)) / 2);
-    const double dev = (double)acc->dev_hi * 4294967296.0 + (double)acc->dev_lo * kDevUnscale;
+    const double dev = ((double)acc->dev_hi * 18446744073709551616.0 + (double)acc->dev_lo) * kAngleUnit;
     r.crossing.angle_dev_sum = dev;
     r.crossing.ideal_rad = ideal;
     r.crossing.E_ca = ec > 0 ? 1.0 - dev / (ideal * (double)ec) : 1.0;
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(256) k_finalize(const DevAcc *__restrict__ acc
 __global__ void k_per_edge_export(uint64_t *dev_fixed, int64_t E) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (double)dev_fixed[e] * kDevUnscale;
+        const double v = (double)dev_fixed[e] * kAngleUnit;
         reinterpret_cast<double *>(dev_fixed)[e] = v;
     }
 }
@@ -310,7 +321,7 @@ void launch_gather(const int32_t *xy, int64_t V, const int32_t *edges, int64_t E
     if (E <= 0) return;
     count_launches(1);
     k_gather<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>((const int2 *)xy, V, (const int2 *)edges, E,
-                                                        b.seg, b.seg_eid, b.len2, b.acc);
+                                                        b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc);
 }
 
 void launch_check_vertices(const int32_t *xy, int64_t V, Buffers &b, cudaStream_t s) {

@@ -71,29 +71,30 @@ __device__ __forceinline__ int minor_at(const DdaSeg &s, int X, int k) {
 // ends, closed at both (a superset of the half-open cells the segment meets;
 // the slope is at most 1, so there are at most three).
 template <class F>
-__device__ __forceinline__ void dda_line(const DdaSeg &s, int c, int k, SegRec r, int32_t eid, F &f) {
+__device__ __forceinline__ void dda_line(const DdaSeg &s, int c, int k, SegRec r, int32_t eid, uint32_t th,
+                                         F &f) {
     const int ra = minor_at(s, max(s.x0, c << k), k);
     const int rb = minor_at(s, min(s.x1, (c + 1) << k), k);
     for (int q = min(ra, rb); q <= max(ra, rb); ++q) {
-        if (s.tr) f(q, c, r, eid); else f(c, q, r, eid);
+        if (s.tr) f(q, c, r, eid, th); else f(c, q, r, eid, th);
     }
 }
 
 constexpr int LONG_LINES = 8;  // segments spanning more lines are walked by a warp
 
-// Calls f(cx, cy, record, edge id) for every cell of side 2^k that the
+// Calls f(cx, cy, record, edge id, direction) for every cell of side 2^k that the
 // segment held by this lane (valid if `ok`) meets.  Short segments are walked
 // by their own lane; long ones by the whole warp, one major line per lane, so
 // that a few long edges do not serialise their warp.  Every lane of the warp
 // must call it.  Both DDA passes use it, so they enumerate the same cells.
 template <class F>
-__device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, bool ok, int k, F &&f) {
+__device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, uint32_t th, bool ok, int k, F &&f) {
     const int lane = threadIdx.x & 31;
     const DdaSeg s = dda_norm(r);
     const int nl = ok ? (s.x1 >> k) - (s.x0 >> k) + 1 : 0;
     const bool is_long = nl > LONG_LINES;
     if (ok && !is_long) {
-        for (int c = s.x0 >> k, e = s.x1 >> k; c <= e; ++c) dda_line(s, c, k, r, eid, f);
+        for (int c = s.x0 >> k, e = s.x1 >> k; c <= e; ++c) dda_line(s, c, k, r, eid, th, f);
     }
     unsigned m = __ballot_sync(0xffffffffu, is_long);
     while (m) {
@@ -105,8 +106,9 @@ __device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, bool o
         q.z = __shfl_sync(0xffffffffu, r.z, src);
         q.w = __shfl_sync(0xffffffffu, r.w, src);
         const int32_t qe = __shfl_sync(0xffffffffu, eid, src);
+        const uint32_t qt = __shfl_sync(0xffffffffu, th, src);
         const DdaSeg t = dda_norm(q);
-        for (int c = (t.x0 >> k) + lane, e = t.x1 >> k; c <= e; c += 32) dda_line(t, c, k, q, qe, f);
+        for (int c = (t.x0 >> k) + lane, e = t.x1 >> k; c <= e; c += 32) dda_line(t, c, k, q, qe, qt, f);
     }
 }
 
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ s
         const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
         const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
-        warp_for_each_cell(r, 0, ok, k, [&](int cx, int cy, SegRec, int32_t) {
+        warp_for_each_cell(r, 0, 0u, ok, k, [&](int cx, int cy, SegRec, int32_t, uint32_t) {
             atomicAdd(&cell_cnt[cy * G + cx], 1u);
         });
     }
@@ -149,11 +151,12 @@ __global__ void __launch_bounds__(256) k_cell_items(const uint32_t *__restrict__
 // edge id go to cell_off[c] + (running count of cell c).
 __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ seg,
                                                    const int32_t *__restrict__ seg_eid,
+                                                   const uint32_t *__restrict__ seg_theta,
                                                    const DevAcc *__restrict__ acc, int k,
                                                    const uint32_t *__restrict__ cell_off,
                                                    uint32_t *__restrict__ cell_fill, uint64_t cap,
                                                    SegRec *__restrict__ rec, int32_t *__restrict__ rec_eid,
-                                                   uint32_t *status) {
+                                                   uint32_t *__restrict__ rec_theta, uint32_t *status) {
     const int64_t n = acc->n_seg;
     const int G = 65536 >> k;
     if (acc->records > cap) {  // sized from the same counts; cannot happen unless inputs changed
@@ -165,11 +168,13 @@ __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ se
         const bool ok = i < n;
         const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
         const int32_t eid = ok ? seg_eid[i] : 0;
-        warp_for_each_cell(r, eid, ok, k, [&](int cx, int cy, SegRec q, int32_t qe) {
+        const uint32_t th = ok ? seg_theta[i] : 0u;
+        warp_for_each_cell(r, eid, th, ok, k, [&](int cx, int cy, SegRec q, int32_t qe, uint32_t qt) {
             const int c = cy * G + cx;
             const uint32_t pos = cell_off[c] + atomicAdd(&cell_fill[c], 1u);
             rec[pos] = q;
             rec_eid[pos] = qe;
+            rec_theta[pos] = qt;
         });
     }
 }
@@ -202,9 +207,9 @@ __device__ __forceinline__ bool owns_collinear(const RowSeg &r, const ColSeg &c,
 // (i + q) mod m) so that every lane has work in every round.
 template <bool PER_EDGE>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
-    const SegRec *__restrict__ rec, const int32_t *__restrict__ rec_eid,
+    const SegRec *__restrict__ rec, const int32_t *__restrict__ rec_eid, const uint32_t *__restrict__ rec_theta,
     const uint32_t *__restrict__ cell_off, const uint32_t *__restrict__ item_off, int C, int k,
-    DevAcc *acc, float ideal, PerEdge pe) {
+    DevAcc *acc, uint32_t ideal, PerEdge pe) {
     __shared__ ColSeg cs[GP_WARPS][TILE];
     __shared__ int32_t ceid[GP_WARPS][PER_EDGE ? TILE : 1];
     __shared__ uint64_t shu[32];
@@ -233,13 +238,13 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
 
         __syncwarp();
         if (lane < mc) {
-            cs[wid][lane] = make_col(rec[base + tj * TILE + lane]);
+            cs[wid][lane] = make_col(rec[base + tj * TILE + lane], rec_theta[base + tj * TILE + lane]);
             if (PER_EDGE) ceid[wid][lane] = rec_eid[base + tj * TILE + lane];
         }
         RowSeg rs;
         int32_t reid = 0;
         if (lane < mr) {
-            rs = make_row(rec[base + ti * TILE + lane]);
+            rs = make_row(rec[base + ti * TILE + lane], rec_theta[base + ti * TILE + lane]);
             if (PER_EDGE) reid = rec_eid[base + ti * TILE + lane];
         }
         __syncwarp();
@@ -258,8 +263,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
                 jj = s;
             }
             const ColSeg c = cs[wid][jj];
-            float dev;
-            const int kind = classify(rs, c, ideal, dev);
+            const int kind = classify_kind(rs, c);
             if (kind == PAIR_NONE) continue;
             if (kind == PAIR_COLLINEAR) {
                 if (!owns_collinear(rs, c, cx, cy, k)) continue;
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
                 continue;
             }
             if (!owns_crossing(rs, c, x0, y0, w)) continue;
-            const uint64_t qd = (uint64_t)__float2ull_rn(dev * kDevScale);
+            const uint32_t qd = dev_term(rs.th, c.th, ideal);
             pc.dev += qd;
             if (kind == PAIR_PROPER) ++pc.proper; else ++pc.touching;
             if (PER_EDGE) {
@@ -310,22 +314,23 @@ void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int 
     cudaMemsetAsync(g.cell_fill, 0, sizeof(uint32_t) * C, s);
     if (E <= 0) return;
     count_launches(1);
-    k_grid_fill<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.acc, k, g.cell_off, g.cell_fill,
-                                                           g.rec_cap, g.rec, g.rec_eid, &b.acc->eval_status);
+    k_grid_fill<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, b.acc, k, g.cell_off,
+                                                           g.cell_fill, g.rec_cap, g.rec, g.rec_eid, g.rec_theta,
+                                                           &b.acc->eval_status);
 }
 
-void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items, float ideal,
+void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items, uint32_t ideal,
                        PerEdge pe, cudaStream_t s) {
     const int C = (65536 >> k) * (65536 >> k);
     if (n_items == 0) return;
     const int blocks = grid_for((int64_t)n_items, GP_WARPS, 152 * 8);
     count_launches(1);
     if (pe.counts)
-        k_grid_pairs<true><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.rec_eid, g.cell_off, g.item_off, C, k,
-                                                           b.acc, ideal, pe);
+        k_grid_pairs<true><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.rec_eid, g.rec_theta, g.cell_off, g.item_off,
+                                                           C, k, b.acc, ideal, pe);
     else
-        k_grid_pairs<false><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.rec_eid, g.cell_off, g.item_off, C, k,
-                                                            b.acc, ideal, pe);
+        k_grid_pairs<false><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.rec_eid, g.rec_theta, g.cell_off,
+                                                            g.item_off, C, k, b.acc, ideal, pe);
 }
 
 }  // namespace gr

@@ -1,5 +1,5 @@
-// pair_math.cuh -- exact classification of one edge pair, shared by the
-// all-pairs and per-cell crossing kernels.
+// pair_math.cuh -- classification of one edge pair and its crossing-angle
+// term, shared by the all-pairs and per-cell crossing kernels.
 //
 // Algorithm 4 decides a crossing from four orientation signs.  With
 // integer coordinates in [0, 2^16) every orientation is an exact int64:
@@ -7,9 +7,13 @@
 // so for a fixed segment (p, q) it is the linear form u x r - k with
 // k = u x p precomputed once per segment; each orientation then costs two
 // 32x32->64 multiply-adds.  Magnitudes stay below 2^35.
+//
+// Algorithm 5's crossing angle a_c is the acute angle between the two lines.
+// Each segment carries the direction of its line, theta in [0, pi), as a
+// uint32 in units of pi / 2^32; then a_c = min(d, 2^32 - d) with
+// d = theta_e - theta_f (mod 2^32), and |ideal - a_c| is integer arithmetic.
 #pragma once
 
-#include "atan_poly.cuh"
 #include "gr_internal.cuh"
 
 namespace gr {
@@ -22,6 +26,7 @@ struct RowSeg {
     int ux, uy;
     long long k;  // u x a
     uint32_t ida, idb;
+    uint32_t th;  // line direction
 };
 
 // Segment staged in shared memory and read by every thread of a tile.
@@ -30,23 +35,26 @@ struct __align__(8) ColSeg {
     int vx, vy;
     uint32_t idc, idd;
     long long k;  // v x c
+    uint32_t th;
 };
 
-__device__ __forceinline__ RowSeg make_row(SegRec s) {
+__device__ __forceinline__ RowSeg make_row(SegRec s, uint32_t th) {
     RowSeg r;
     r.ax = px(s.x); r.ay = py(s.x); r.bx = px(s.y); r.by = py(s.y);
     r.ux = r.bx - r.ax; r.uy = r.by - r.ay;
     r.k = (long long)r.ux * r.ay - (long long)r.uy * r.ax;
     r.ida = s.z; r.idb = s.w;
+    r.th = th;
     return r;
 }
 
-__device__ __forceinline__ ColSeg make_col(SegRec s) {
+__device__ __forceinline__ ColSeg make_col(SegRec s, uint32_t th) {
     ColSeg c;
     c.cx = px(s.x); c.cy = py(s.x); c.dx = px(s.y); c.dy = py(s.y);
     c.vx = c.dx - c.cx; c.vy = c.dy - c.cy;
     c.k = (long long)c.vx * c.cy - (long long)c.vy * c.cx;
     c.idc = s.z; c.idd = s.w;
+    c.th = th;
     return c;
 }
 
@@ -58,7 +66,7 @@ __device__ __forceinline__ uint32_t lex_key(int x, int y) { return (uint32_t(x) 
 // Algorithm 4: shared vertex ids never cross; a collinear pair whose extents
 // meet is reported separately; otherwise the pair is in E_c when both
 // orientation products are <= 0 (PAIR_PROPER when both are < 0, else
-// PAIR_TOUCHING).
+// PAIR_TOUCHING).  Exact.
 __device__ __forceinline__ int classify_kind(const RowSeg &r, const ColSeg &c) {
     if ((r.ida == c.idc) | (r.ida == c.idd) | (r.idb == c.idc) | (r.idb == c.idd)) return PAIR_NONE;
     const long long o1 = (long long)r.ux * c.cy - (long long)r.uy * c.cx - r.k;  // orient(a, b, c)
@@ -78,43 +86,19 @@ __device__ __forceinline__ int classify_kind(const RowSeg &r, const ColSeg &c) {
     return (o1 != 0 && o2 != 0 && o3 != 0 && o4 != 0) ? PAIR_PROPER : PAIR_TOUCHING;
 }
 
-// |u x v| and |u . v| of an E_c pair: exact in int64, then rounded once to
-// FP32.  Both are symmetric in the two segments, so every path that meets
-// the pair (in either role) derives the same angle, bit for bit.
-__device__ __forceinline__ float2 cross_dot_abs(const RowSeg &r, const ColSeg &c) {
-    const long long cr = (long long)r.ux * c.vy - (long long)r.uy * c.vx;
-    const long long dt = (long long)r.ux * c.vx + (long long)r.uy * c.vy;
-    return make_float2(fabsf((float)cr), fabsf((float)dt));
-}
-
-// The acute angle between two lines (Sec. 3.1.5, "intersecting angles" from
-// arctan) from y = |u x v| and x = |u . v|, not both zero:
-// atan(min / max), reflected about pi/4 when y > x.
-__device__ __forceinline__ float acute_angle(float y, float x) {
-    const float a = atan01(__fdividef(fminf(x, y), fmaxf(x, y)));
-    return y > x ? 1.57079632679489662f - a : a;
-}
-
-// |ideal - a_c| as a 2^32-scaled fixed-point integer (exact conversion of
-// the FP32 value).
-__device__ __forceinline__ uint64_t dev_fixed(float2 yx, float ideal) {
-    return (uint64_t)__float2ull_rn(fabsf(ideal - acute_angle(yx.x, yx.y)) * kDevScale);
-}
-
-// classify_kind plus |ideal - a_c| for E_c pairs.
-__device__ __forceinline__ int classify(const RowSeg &r, const ColSeg &c, float ideal, float &dev) {
-    const int kind = classify_kind(r, c);
-    if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) {
-        const float2 yx = cross_dot_abs(r, c);
-        dev = fabsf(ideal - acute_angle(yx.x, yx.y));
-    }
-    return kind;
+// |ideal - a_c| in units of pi / 2^32 for lines of directions ta and tb.
+// Symmetric in (ta, tb), so every path that meets a pair derives the same
+// term.  At most 2^31.
+__device__ __forceinline__ uint32_t dev_term(uint32_t ta, uint32_t tb, uint32_t ideal) {
+    const uint32_t d = ta - tb;
+    const uint32_t a = min(d, 0u - d);  // acute angle between the lines
+    return max(a, ideal) - min(a, ideal);
 }
 
 // Per-thread tallies of one crossing kernel.
 struct PairCounts {
     uint32_t proper = 0, touching = 0, collinear = 0;
-    uint64_t dev = 0;  // fixed point, 2^32 scale
+    uint64_t dev = 0;  // sum of |ideal - a_c|, units of pi / 2^32
 };
 
 // Block-wide reduction of the tallies and one atomic per counter.  Every
