@@ -213,6 +213,30 @@ gr_status gr_io_bytes(gr_layout *layout, int64_t *h2d, int64_t *d2h);
  * (all layouts, all threads). */
 int64_t gr_kernel_launches(void);
 
+/* ------------------------------------------------- no device allocation
+ * Edge crossings and crossing angle of one layout of at most
+ * GR_NOALLOC_MAX_EDGES edges, computed without allocating anything: for
+ * callers that cannot call cudaMalloc -- a process whose device memory is
+ * already committed to its own pool allocator under a fixed budget, or a
+ * latency-critical caller that cannot afford cudaMalloc / cudaFree, which may
+ * block or synchronise the device.  The paper has no counterpart; the
+ * results equal gr_crossing_angle's on the same layout.
+ *
+ * `d_xy` [V][2] and `d_edges` [E][2] are DEVICE memory (int32, as for
+ * gr_layout_create); `out` is device or host memory.  Work runs on `stream`
+ * and the call synchronises it.  Scratch is a fixed array of about 1 MiB in
+ * the library's device image, held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture on the device.  Every call reuses the
+ * same array: calls whose GPU work overlaps (other streams or host threads)
+ * race and must be serialised by the caller.  GR_EINVAL for E above the
+ * limit, for host-memory inputs, bad ids or self-loops; GR_ERANGE for
+ * coordinates outside [0, 65536). */
+#define GR_NOALLOC_MAX_EDGES 32768
+gr_status gr_crossing_angle_noalloc(const int32_t *d_xy, int64_t V, const int32_t *d_edges, int64_t E,
+                                    double ideal_rad, gr_crossing_angle_result *out, gr_stream_t stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *gr_last_error(void);
 

@@ -626,4 +626,5 @@ int64_t gr_kernel_launches(void) { return g_launches.load(); }
 
 namespace gr {
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_last_error(const char *msg) { g_err = msg; }
 }  // namespace gr

@@ -105,6 +105,8 @@ constexpr int kScanMaxBlocks = 16384; // => up to 2^26 elements per scan
 // All launchers enqueue on `s` and never synchronise.  Each adds the number of
 // kernels it launched to the library-wide counter.
 void count_launches(int n);
+// Sets the message gr_last_error() returns on this host thread.
+void set_last_error(const char *msg);
 
 // a1: gathers every edge's endpoints, validates ids and coordinates, stores
 // the squared length of every edge, compacts the non-zero-length segments.

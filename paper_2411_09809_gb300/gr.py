@@ -105,6 +105,8 @@ def load() -> ctypes.CDLL:
         "gr_profile_read": ([P, ctypes.POINTER(gr_profile), c_int32], c_int32),
         "gr_kernel_launches": ([], c_int64),
         "gr_io_bytes": ([P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)], c_int32),
+        "gr_crossing_angle_noalloc": ([P, c_int64, P, c_int64, c_double,
+                                       ctypes.POINTER(gr_crossing_angle_result), P], c_int32),
         "gr_last_error": ([], ctypes.c_char_p),
         "gr_version": ([], ctypes.c_char_p),
     }
@@ -227,6 +229,22 @@ def gr_crossings_per_edge(layout, ideal_rad: float, d_counts, d_dev) -> None:
     cp, ck = _buffer(d_counts, "int64")
     dp, dk = _buffer(d_dev, "float64")
     _check(load().gr_crossings_per_edge(layout, float(ideal_rad), cp, dp))
+
+
+GR_NOALLOC_MAX_EDGES = 32768
+
+
+def gr_crossing_angle_noalloc(d_xy, d_edges, ideal_rad: float = 0.0, stream=None) -> gr_crossing_angle_result:
+    """Crossings and crossing angle without any device allocation (CUDA int32
+    tensors, at most GR_NOALLOC_MAX_EDGES edges); see include/gr.h."""
+    xp, xk = _buffer(d_xy, "int32")
+    ep, ek = _buffer(d_edges, "int32")
+    if stream is None:
+        stream = _stream_of(d_xy, d_edges)
+    out = gr_crossing_angle_result()
+    _check(load().gr_crossing_angle_noalloc(xp, _count(xk), ep, _count(ek), float(ideal_rad),
+                                            ctypes.byref(out), stream))
+    return out
 
 
 def gr_profile_enable(layout, enable: bool = True) -> None:

@@ -32,7 +32,7 @@ def test_header_declares_the_boundary():
               "gr_node_occlusion", "gr_min_angle", "gr_edge_length_variation",
               "gr_edge_crossings", "gr_crossing_angle", "gr_crossings_per_edge",
               "gr_last_error", "gr_version", "gr_profile_enable", "gr_profile_read",
-              "gr_kernel_launches", "gr_io_bytes"]:
+              "gr_kernel_launches", "gr_io_bytes", "gr_crossing_angle_noalloc"]:
         assert n in names
 
 
@@ -82,5 +82,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.gr_layout_create(ctypes.byref(h), None, 7, 0, None, 0, None, None) == gr.GR_ENOTSUP
     assert lib.gr_evaluate(None, 15, None, None) == gr.GR_EINVAL
     assert lib.gr_layout_destroy(None) == gr.GR_OK
+    out = gr.gr_crossing_angle_result()
+    assert lib.gr_crossing_angle_noalloc(None, 0, None, gr.GR_NOALLOC_MAX_EDGES + 1, 0.0,
+                                         ctypes.byref(out), None) == gr.GR_EINVAL
+    assert "limit" in gr.gr_last_error()
     assert gr.gr_version().startswith("gr ")
     assert gr.gr_kernel_launches() == 0  # nothing launched in a process without a GPU call
