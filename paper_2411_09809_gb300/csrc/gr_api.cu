@@ -84,8 +84,7 @@ namespace {
 std::atomic<int64_t> g_launches{0};
 
 void free_grid(GridBuffers &g) {
-    void *ptrs[] = {g.cell_off, g.item_off, g.cell_fill, g.rec, g.rec_eid, g.rec_theta, g.ocell_off, g.ocell_fill,
-                    g.opts};
+    void *ptrs[] = {g.cell_off, g.item_off, g.cell_fill, g.rec, g.item_cell, g.ocell_off, g.ocell_fill, g.opts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g = GridBuffers{};
@@ -151,22 +150,25 @@ gr_status ensure_cells(gr_layout *L, int C) {
     return GR_OK;
 }
 
-gr_status ensure_records(gr_layout *L, uint64_t R) {
+gr_status ensure_records(gr_layout *L, uint64_t R, uint64_t items) {
     GridBuffers &g = L->g;
-    if (g.rec_cap >= R && g.rec) return GR_OK;
-    if (g.rec) cudaFree(g.rec);
-    if (g.rec_eid) cudaFree(g.rec_eid);
-    if (g.rec_theta) cudaFree(g.rec_theta);
-    g.rec = nullptr;
-    g.rec_eid = nullptr;
-    g.rec_theta = nullptr;
-    g.rec_cap = 0;
-    const uint64_t cap = R + R / 4 + 1024;
     gr_status st;
-    if ((st = dalloc(&g.rec, (size_t)cap)) != GR_OK) return st;
-    if ((st = dalloc(&g.rec_eid, (size_t)cap)) != GR_OK) return st;
-    if ((st = dalloc(&g.rec_theta, (size_t)cap)) != GR_OK) return st;
-    g.rec_cap = cap;
+    if (g.rec_cap < R || !g.rec) {
+        if (g.rec) cudaFree(g.rec);
+        g.rec = nullptr;
+        g.rec_cap = 0;
+        const uint64_t cap = R + R / 4 + 1024;
+        if ((st = dalloc(&g.rec, (size_t)cap)) != GR_OK) return st;
+        g.rec_cap = cap;
+    }
+    if (g.items_cap < items || !g.item_cell) {
+        if (g.item_cell) cudaFree(g.item_cell);
+        g.item_cell = nullptr;
+        g.items_cap = 0;
+        const uint64_t cap = items + items / 4 + 1024;
+        if ((st = dalloc(&g.item_cell, (size_t)cap)) != GR_OK) return st;
+        g.items_cap = cap;
+    }
     return GR_OK;
 }
 
@@ -451,7 +453,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
             grid = kRecordCost * (double)a.records + kCellPairCost * (double)a.grid_work < n * (n - 1) / 2;
         }
         if (grid) {
-            if ((st = ensure_records(L, a.records)) != GR_OK) return st;
+            if ((st = ensure_records(L, a.records, a.grid_items)) != GR_OK) return st;
             phase_begin(L, GR_PHASE_CROSS_SCATTER);
             launch_grid_scatter(b, E, L->g, cp.k, s);
             phase_end(L, GR_PHASE_CROSS_SCATTER);
@@ -578,7 +580,7 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
         if (L->h_acc->grid_flags & GF_ITEMS_OVERFLOW) cp.grid = false;
     }
     if (cp.grid && L->h_acc->n_seg >= 2) {
-        if ((st2 = ensure_records(L, L->h_acc->records)) != GR_OK) return st2;
+        if ((st2 = ensure_records(L, L->h_acc->records, L->h_acc->grid_items)) != GR_OK) return st2;
         launch_grid_scatter(b, E, L->g, cp.k, s);
         launch_grid_pairs(b, L->g, cp.k, L->h_acc->grid_items, ideal_units(ideal), pe, s);
     } else {

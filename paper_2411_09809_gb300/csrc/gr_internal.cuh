@@ -80,15 +80,22 @@ struct Buffers {
     gr_result *result = nullptr;  // device copy of the result
 };
 
+// One (segment, cell) record of the crossing grid, 32 bytes (one sector):
+// .s = the segment (as SegRec), .x = {edge id, line direction, 0, 0}.
+struct __align__(32) GridRec {
+    uint4 s;
+    uint4 x;
+};
+
 // Buffers of the uniform grids (crossings and occlusion), grown on demand.
 struct GridBuffers {
     uint32_t *cell_off = nullptr;  // [C + 1] counts, then offsets (scan in place)
     uint32_t *item_off = nullptr;  // [C + 1] work items per cell, then offsets
     uint32_t *cell_fill = nullptr; // [C]
-    SegRec *rec = nullptr;         // [rec_cap] segments sorted by cell
-    int32_t *rec_eid = nullptr;    // [rec_cap] their edge ids
-    uint32_t *rec_theta = nullptr; // [rec_cap] their line directions
+    GridRec *rec = nullptr;        // [rec_cap] records sorted by cell
     uint64_t rec_cap = 0;
+    uint32_t *item_cell = nullptr; // [items_cap] cell of every work item
+    uint64_t items_cap = 0;
     int cells_cap = 0;             // C the cell arrays are sized for
     // occlusion grid
     uint32_t *ocell_off = nullptr; // [OC + 1]

@@ -68,33 +68,45 @@ __device__ __forceinline__ int minor_at(const DdaSeg &s, int X, int k) {
 }
 
 // The cells of major line c: minor indices between those at the line's two
-// ends, closed at both (a superset of the half-open cells the segment meets;
-// the slope is at most 1, so there are at most three).
-template <class F>
-__device__ __forceinline__ void dda_line(const DdaSeg &s, int c, int k, SegRec r, int32_t eid, uint32_t th,
-                                         F &f) {
+// ends, closed at both (a superset of the half-open cells the segment meets).
+// Along one line the major coordinate advances by at most w and the slope is
+// at most 1, so the minor index changes by at most one: at most two cells.
+// Writes their ids (cy * G + cx) and returns how many.
+__device__ __forceinline__ int line_cells(const DdaSeg &s, int c, int k, int G, int (&out)[2]) {
     const int ra = minor_at(s, max(s.x0, c << k), k);
     const int rb = minor_at(s, min(s.x1, (c + 1) << k), k);
-    for (int q = min(ra, rb); q <= max(ra, rb); ++q) {
-        if (s.tr) f(q, c, r, eid, th); else f(c, q, r, eid, th);
+    const int lo = min(ra, rb);
+    const int n = min(max(ra, rb) - lo + 1, 2);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int q = lo + i;
+        out[i] = s.tr ? (c * G + q) : (q * G + c);
     }
+    return n;
 }
 
-constexpr int LONG_LINES = 8;  // segments spanning more lines are walked by a warp
+constexpr int SHORT_LINES = 2;  // segments spanning more major lines are walked by a warp
 
-// Calls f(cx, cy, record, edge id, direction) for every cell of side 2^k that the
-// segment held by this lane (valid if `ok`) meets.  Short segments are walked
-// by their own lane; long ones by the whole warp, one major line per lane, so
-// that a few long edges do not serialise their warp.  Every lane of the warp
-// must call it.  Both DDA passes use it, so they enumerate the same cells.
+// Calls f(ids, n, record, edge id, direction) for the cells of side 2^k that
+// the segment held by this lane (valid if `ok`) meets, a batch of at most two
+// cells at a time (so a callback can issue its atomics before its stores).
+// Segments spanning at most SHORT_LINES major lines are walked by their own
+// lane; longer ones by the whole warp, one line per lane, so that a few long
+// edges do not serialise their warp.  Every lane of the warp must call it.
+// Both DDA passes use it, so they enumerate the same cells.
 template <class F>
 __device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, uint32_t th, bool ok, int k, F &&f) {
     const int lane = threadIdx.x & 31;
+    const int G = 65536 >> k;
     const DdaSeg s = dda_norm(r);
     const int nl = ok ? (s.x1 >> k) - (s.x0 >> k) + 1 : 0;
-    const bool is_long = nl > LONG_LINES;
+    const bool is_long = nl > SHORT_LINES;
     if (ok && !is_long) {
-        for (int c = s.x0 >> k, e = s.x1 >> k; c <= e; ++c) dda_line(s, c, k, r, eid, th, f);
+        for (int c = s.x0 >> k, e = s.x1 >> k; c <= e; ++c) {
+            int ids[2];
+            const int n = line_cells(s, c, k, G, ids);
+            f(ids, n, r, eid, th);
+        }
     }
     unsigned m = __ballot_sync(0xffffffffu, is_long);
     while (m) {
@@ -108,7 +120,11 @@ __device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, uint32
         const int32_t qe = __shfl_sync(0xffffffffu, eid, src);
         const uint32_t qt = __shfl_sync(0xffffffffu, th, src);
         const DdaSeg t = dda_norm(q);
-        for (int c = (t.x0 >> k) + lane, e = t.x1 >> k; c <= e; c += 32) dda_line(t, c, k, q, qe, qt, f);
+        for (int c = (t.x0 >> k) + lane, e = t.x1 >> k; c <= e; c += 32) {
+            int ids[2];
+            const int n = line_cells(t, c, k, G, ids);
+            f(ids, n, q, qe, qt);
+        }
     }
 }
 
@@ -117,13 +133,13 @@ __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ s
                                                     const DevAcc *__restrict__ acc, int k,
                                                     uint32_t *__restrict__ cell_cnt) {
     const int64_t n = acc->n_seg;
-    const int G = 65536 >> k;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
         const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
-        warp_for_each_cell(r, 0, 0u, ok, k, [&](int cx, int cy, SegRec, int32_t, uint32_t) {
-            atomicAdd(&cell_cnt[cy * G + cx], 1u);
+        warp_for_each_cell(r, 0, 0u, ok, k, [&](const int (&ids)[2], int nc, SegRec, int32_t, uint32_t) {
+            atomicAdd(&cell_cnt[ids[0]], 1u);
+            if (nc > 1) atomicAdd(&cell_cnt[ids[1]], 1u);
         });
     }
 }
@@ -147,18 +163,25 @@ __global__ void __launch_bounds__(256) k_cell_items(const uint32_t *__restrict__
     if (threadIdx.x == 0) atomic_add_u64(&acc->grid_work, w);
 }
 
-// a4 -- scatter of the records into their cells: the segment record and its
-// edge id go to cell_off[c] + (running count of cell c).
+// The cell of every work item (replaces a search over the item offsets).
+__global__ void __launch_bounds__(256) k_item_cells(const uint32_t *__restrict__ item_off, int C,
+                                                    uint32_t *__restrict__ item_cell) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        for (uint32_t q = item_off[c], e = item_off[c + 1]; q < e; ++q) item_cell[q] = (uint32_t)c;
+    }
+}
+
+// a4 -- scatter of the records into their cells: segment, edge id and line
+// direction go as one 32-byte record to cell_off[c] + (running count of c).
+// A batch's atomics are issued before its stores.
 __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ seg,
                                                    const int32_t *__restrict__ seg_eid,
                                                    const uint32_t *__restrict__ seg_theta,
                                                    const DevAcc *__restrict__ acc, int k,
                                                    const uint32_t *__restrict__ cell_off,
                                                    uint32_t *__restrict__ cell_fill, uint64_t cap,
-                                                   SegRec *__restrict__ rec, int32_t *__restrict__ rec_eid,
-                                                   uint32_t *__restrict__ rec_theta, uint32_t *status) {
+                                                   GridRec *__restrict__ rec, uint32_t *status) {
     const int64_t n = acc->n_seg;
-    const int G = 65536 >> k;
     if (acc->records > cap) {  // sized from the same counts; cannot happen unless inputs changed
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_OVERFLOW);
         return;
@@ -169,62 +192,111 @@ __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ se
         const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
         const int32_t eid = ok ? seg_eid[i] : 0;
         const uint32_t th = ok ? seg_theta[i] : 0u;
-        warp_for_each_cell(r, eid, th, ok, k, [&](int cx, int cy, SegRec q, int32_t qe, uint32_t qt) {
-            const int c = cy * G + cx;
-            const uint32_t pos = cell_off[c] + atomicAdd(&cell_fill[c], 1u);
-            rec[pos] = q;
-            rec_eid[pos] = qe;
-            rec_theta[pos] = qt;
+        warp_for_each_cell(r, eid, th, ok, k, [&](const int (&ids)[2], int nc, SegRec q, int32_t qe, uint32_t qt) {
+            const uint32_t s0 = atomicAdd(&cell_fill[ids[0]], 1u);
+            const uint32_t s1 = nc > 1 ? atomicAdd(&cell_fill[ids[1]], 1u) : 0u;
+            const uint32_t o0 = cell_off[ids[0]];
+            const uint32_t o1 = nc > 1 ? cell_off[ids[1]] : 0u;
+            GridRec g;
+            g.s = q;
+            g.x = make_uint4((uint32_t)qe, qt, 0u, 0u);
+            rec[o0 + s0] = g;
+            if (nc > 1) rec[o1 + s1] = g;
         });
     }
 }
 
-// Owner test of an E_c pair: the intersection point P = a + u t with
-// t = ((c - a) x v) / (u x v) lies in the half-open cell [x0, x0 + w) x
-// [y0, y0 + w).  All products are exact in int64 (|P_x * den| < 2^52).
-__device__ __forceinline__ bool owns_crossing(const RowSeg &r, const ColSeg &c, int x0, int y0, int w) {
-    long long den = (long long)r.ux * c.vy - (long long)r.uy * c.vx;
-    long long num = (long long)(c.cx - r.ax) * c.vy - (long long)(c.cy - r.ay) * c.vx;
+// Owner test of an E_c pair in cell-relative integer coordinates (the cell
+// spans [0, w)^2): the intersection point P = a + u t with
+// t = ((c - a) x v) / (u x v) lies in the half-open cell.  Exact in int64
+// (|P_x * den| < 2^51).
+__device__ __forceinline__ bool owns_crossing(int ax, int ay, int ux, int uy, int cx, int cy, int vx, int vy,
+                                              int w) {
+    long long den = (long long)ux * vy - (long long)uy * vx;
+    long long num = (long long)(cx - ax) * vy - (long long)(cy - ay) * vx;
     if (den < 0) { den = -den; num = -num; }
-    const long long X = (long long)r.ax * den + (long long)r.ux * num;
-    const long long Y = (long long)r.ay * den + (long long)r.uy * num;
-    return (long long)x0 * den <= X && X < (long long)(x0 + w) * den &&
-           (long long)y0 * den <= Y && Y < (long long)(y0 + w) * den;
+    const long long X = (long long)ax * den + (long long)ux * num;
+    const long long Y = (long long)ay * den + (long long)uy * num;
+    const long long W = (long long)w * den;
+    return 0 <= X && X < W && 0 <= Y && Y < W;
 }
 
-// Owner of a collinear overlap: the cell of the lexicographically smallest
-// point of the overlap, which is an endpoint of one of the segments.
-__device__ __forceinline__ bool owns_collinear(const RowSeg &r, const ColSeg &c, int cx, int cy, int k) {
-    const uint32_t ka = lex_key(r.ax, r.ay), kb = lex_key(r.bx, r.by);
-    const uint32_t kc = lex_key(c.cx, c.cy), kd = lex_key(c.dx, c.dy);
-    const uint32_t lo = max(min(ka, kb), min(kc, kd));
-    return (int(lo >> 16) >> k) == cx && (int(lo & 0xffffu) >> k) == cy;
+// A segment in the coordinates of the cell being processed (origin at the
+// cell's lower-left corner), in the FP32 form the pair test uses.  When
+// |u_x|, |u_y| <= 2^10 and every coordinate is within 2^12 of the origin,
+// u x p - k and all its partial sums are integers of magnitude <= 2^24, so
+// the FP32 evaluation is exact ("exact" below); otherwise (relative
+// coordinates still below 2^16 in magnitude) its error is below 1,792, under
+// the filter bound kOrientFilter.
+struct __align__(16) GSeg {
+    float ax, ay, bx, by;
+    float ux, uy, nk;  // nk = -(u x a), rounded
+    uint32_t th;
+    uint32_t ida, idb;
+    int exact;
+    int32_t eid;
+};
+
+constexpr float kOrientFilter = 4096.f;
+
+__device__ __forceinline__ GSeg make_gseg(const GridRec &g, int x0, int y0) {
+    GSeg r;
+    const int ax = px(g.s.x) - x0, ay = py(g.s.x) - y0, bx = px(g.s.y) - x0, by = py(g.s.y) - y0;
+    const int ux = bx - ax, uy = by - ay;
+    r.ax = (float)ax; r.ay = (float)ay; r.bx = (float)bx; r.by = (float)by;
+    r.ux = (float)ux; r.uy = (float)uy;
+    r.nk = -(float)((long long)ux * ay - (long long)uy * ax);
+    r.th = g.x.y;
+    r.ida = g.s.z; r.idb = g.s.w;
+    r.eid = (int32_t)g.x.x;
+    const int m = max(max(abs(ax), abs(ay)), max(abs(bx), abs(by)));
+    r.exact = (abs(ux) <= 1024 && abs(uy) <= 1024 && m <= 4096) ? 1 : 0;
+    return r;
+}
+
+// Exact int64 classification of a pair whose FP32 orientations were not
+// conclusive, on the absolute coordinates (cell origin x0, y0 added back).
+__device__ __forceinline__ int classify_exact(const GSeg &r, const GSeg &c, int x0, int y0) {
+    const SegRec a = make_uint4(uint32_t((int)r.ax + x0) | (uint32_t((int)r.ay + y0) << 16),
+                                uint32_t((int)r.bx + x0) | (uint32_t((int)r.by + y0) << 16), r.ida, r.idb);
+    const SegRec b = make_uint4(uint32_t((int)c.ax + x0) | (uint32_t((int)c.ay + y0) << 16),
+                                uint32_t((int)c.bx + x0) | (uint32_t((int)c.by + y0) << 16), c.ida, c.idb);
+    return classify_kind(make_row(a, r.th), make_col(b, c.th));
+}
+
+// Owner of a collinear overlap: the cell holding the lexicographically
+// smallest point of the overlap, an endpoint of one of the segments.
+__device__ __forceinline__ bool owns_collinear(const GSeg &r, const GSeg &c, int w) {
+    // compare (x, y) lexicographically on the relative integer coordinates
+    int ex0 = (int)r.ax, ey0 = (int)r.ay, ex1 = (int)r.bx, ey1 = (int)r.by;
+    if (ex1 < ex0 || (ex1 == ex0 && ey1 < ey0)) { int t = ex0; ex0 = ex1; ex1 = t; t = ey0; ey0 = ey1; ey1 = t; }
+    int fx0 = (int)c.ax, fy0 = (int)c.ay, fx1 = (int)c.bx, fy1 = (int)c.by;
+    if (fx1 < fx0 || (fx1 == fx0 && fy1 < fy0)) { int t = fx0; fx0 = fx1; fx1 = t; t = fy0; fy0 = fy1; fy1 = t; }
+    int lx = ex0, ly = ey0;
+    if (fx0 > lx || (fx0 == lx && fy0 > ly)) { lx = fx0; ly = fy0; }
+    return 0 <= lx && lx < w && 0 <= ly && ly < w;
 }
 
 // a6 -- one warp per work item (cell, row tile ti, column tile tj), items in a
 // warp-strided static order.  Off-diagonal items test all rows x columns;
 // diagonal items use a rotation schedule (round q pairs lane i with
-// (i + q) mod m) so that every lane has work in every round.
+// (i + q) mod m) so that every lane has work in every round.  Orientations
+// are evaluated in FP32 in the cell's coordinates: exact for pairs of short
+// segments near the cell, filtered for the rest, and re-decided in int64
+// when inconclusive.  A pair in E_c counts only if this cell owns its
+// intersection point; a collinear overlap only if this cell owns the
+// lexicographically smallest point of the overlap.
 template <bool PER_EDGE>
 __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
-    const SegRec *__restrict__ rec, const int32_t *__restrict__ rec_eid, const uint32_t *__restrict__ rec_theta,
-    const uint32_t *__restrict__ cell_off, const uint32_t *__restrict__ item_off, int C, int k,
-    DevAcc *acc, uint32_t ideal, PerEdge pe) {
-    __shared__ ColSeg cs[GP_WARPS][TILE];
-    __shared__ int32_t ceid[GP_WARPS][PER_EDGE ? TILE : 1];
+    const GridRec *__restrict__ rec, const uint32_t *__restrict__ cell_off, const uint32_t *__restrict__ item_off,
+    const uint32_t *__restrict__ item_cell, uint32_t n_items, int k, DevAcc *acc, uint32_t ideal, PerEdge pe) {
+    __shared__ GSeg cs[GP_WARPS][TILE];
     __shared__ uint64_t shu[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int G = 65536 >> k, w = 1 << k;
-    const uint32_t n_items = item_off[C];
     PairCounts pc;
     for (uint32_t it = blockIdx.x * GP_WARPS + wid; it < n_items; it += gridDim.x * GP_WARPS) {
-        // cell of this item: largest c with item_off[c] <= it (binary search)
-        int lo = 0, hi = C - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (item_off[mid] <= it) lo = mid; else hi = mid - 1;
-        }
-        const int cell = lo;
+        const int cell = (int)item_cell[it];
         const uint32_t q = it - item_off[cell];
         int r = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
         while (r * (r + 1) / 2 > (int)q) --r;
@@ -232,21 +304,13 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
         const int tj = r, ti = (int)q - r * (r + 1) / 2;
         const uint32_t base = cell_off[cell];
         const int n = (int)(cell_off[cell + 1] - base);
-        const int cx = cell % G, cy = cell / G;
-        const int x0 = cx << k, y0 = cy << k;
+        const int x0 = (cell % G) << k, y0 = (cell / G) << k;
         const int mr = min(TILE, n - ti * TILE), mc = min(TILE, n - tj * TILE);
 
         __syncwarp();
-        if (lane < mc) {
-            cs[wid][lane] = make_col(rec[base + tj * TILE + lane], rec_theta[base + tj * TILE + lane]);
-            if (PER_EDGE) ceid[wid][lane] = rec_eid[base + tj * TILE + lane];
-        }
-        RowSeg rs;
-        int32_t reid = 0;
-        if (lane < mr) {
-            rs = make_row(rec[base + ti * TILE + lane], rec_theta[base + ti * TILE + lane]);
-            if (PER_EDGE) reid = rec_eid[base + ti * TILE + lane];
-        }
+        if (lane < mc) cs[wid][lane] = make_gseg(rec[base + tj * TILE + lane], x0, y0);
+        GSeg rs;
+        if (lane < mr) rs = make_gseg(rec[base + ti * TILE + lane], x0, y0);
         __syncwarp();
         if (lane >= mr) continue;
 
@@ -262,28 +326,61 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
             } else {
                 jj = s;
             }
-            const ColSeg c = cs[wid][jj];
-            const int kind = classify_kind(rs, c);
+            const GSeg &c = cs[wid][jj];
+            const float o1 = fmaf(rs.ux, c.ay, fmaf(-rs.uy, c.ax, rs.nk));
+            const float o2 = fmaf(rs.ux, c.by, fmaf(-rs.uy, c.bx, rs.nk));
+            const float o3 = fmaf(c.ux, rs.ay, fmaf(-c.uy, rs.ax, c.nk));
+            const float o4 = fmaf(c.ux, rs.by, fmaf(-c.uy, rs.bx, c.nk));
+            const bool exact = (rs.exact & c.exact) != 0;
+            const float mn = fminf(fminf(fabsf(o1), fabsf(o2)), fminf(fabsf(o3), fabsf(o4)));
+            int kind;
+            if (exact || mn > kOrientFilter) {
+                const bool shared = (rs.ida == c.ida) | (rs.ida == c.idb) | (rs.idb == c.ida) | (rs.idb == c.idb);
+                const float p12 = o1 * o2, p34 = o3 * o4;
+                if (shared || p12 > 0.f || p34 > 0.f) continue;
+                if (o1 == 0.f && o2 == 0.f) {
+                    // collinear: the extents meet iff the larger lexicographic minimum
+                    // is <= the smaller maximum (coordinates exact in FP32)
+                    const bool ar = rs.ax < rs.bx || (rs.ax == rs.bx && rs.ay <= rs.by);
+                    const bool ac = c.ax < c.bx || (c.ax == c.bx && c.ay <= c.by);
+                    const float elx = ar ? rs.ax : rs.bx, ely = ar ? rs.ay : rs.by;
+                    const float ehx = ar ? rs.bx : rs.ax, ehy = ar ? rs.by : rs.ay;
+                    const float flx = ac ? c.ax : c.bx, fly = ac ? c.ay : c.by;
+                    const float fhx = ac ? c.bx : c.ax, fhy = ac ? c.by : c.ay;
+                    const bool lo_e = elx > flx || (elx == flx && ely >= fly);  // lo = e's min
+                    const float lx = lo_e ? elx : flx, ly = lo_e ? ely : fly;
+                    const bool hi_e = ehx < fhx || (ehx == fhx && ehy <= fhy);
+                    const float hx = hi_e ? ehx : fhx, hy = hi_e ? ehy : fhy;
+                    kind = (lx < hx || (lx == hx && ly <= hy)) ? PAIR_COLLINEAR : PAIR_NONE;
+                } else {
+                    kind = (p12 < 0.f && p34 < 0.f) ? PAIR_PROPER : PAIR_TOUCHING;
+                }
+            } else {
+                kind = classify_exact(rs, c, x0, y0);
+            }
             if (kind == PAIR_NONE) continue;
             if (kind == PAIR_COLLINEAR) {
-                if (!owns_collinear(rs, c, cx, cy, k)) continue;
+                if (!owns_collinear(rs, c, w)) continue;
                 ++pc.collinear;
                 if (PER_EDGE) {
-                    atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)reid + 2], 1ull);
-                    atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)ceid[wid][jj] + 2], 1ull);
+                    atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)rs.eid + 2], 1ull);
+                    atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)c.eid + 2], 1ull);
                 }
                 continue;
             }
-            if (!owns_crossing(rs, c, x0, y0, w)) continue;
+            const int iax = (int)rs.ax, iay = (int)rs.ay, icx = (int)c.ax, icy = (int)c.ay;
+            if (!owns_crossing(iax, iay, (int)rs.bx - iax, (int)rs.by - iay, icx, icy, (int)c.bx - icx,
+                               (int)c.by - icy, w))
+                continue;
             const uint32_t qd = dev_term(rs.th, c.th, ideal);
             pc.dev += qd;
             if (kind == PAIR_PROPER) ++pc.proper; else ++pc.touching;
             if (PER_EDGE) {
                 const int slot = kind == PAIR_PROPER ? 0 : 1;
-                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)reid + slot], 1ull);
-                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)ceid[wid][jj] + slot], 1ull);
-                atomicAdd((unsigned long long *)&pe.dev[reid], (unsigned long long)qd);
-                atomicAdd((unsigned long long *)&pe.dev[ceid[wid][jj]], (unsigned long long)qd);
+                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)rs.eid + slot], 1ull);
+                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)c.eid + slot], 1ull);
+                atomicAdd((unsigned long long *)&pe.dev[rs.eid], (unsigned long long)qd);
+                atomicAdd((unsigned long long *)&pe.dev[c.eid], (unsigned long long)qd);
             }
         }
     }
@@ -312,25 +409,24 @@ void launch_grid_count(const Buffers &b, int64_t E, const GridBuffers &g, int k,
 void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int k, cudaStream_t s) {
     const int C = (65536 >> k) * (65536 >> k);
     cudaMemsetAsync(g.cell_fill, 0, sizeof(uint32_t) * C, s);
+    count_launches(1 + (E > 0 ? 1 : 0));
+    k_item_cells<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.item_off, C, g.item_cell);
     if (E <= 0) return;
-    count_launches(1);
     k_grid_fill<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, b.acc, k, g.cell_off,
-                                                           g.cell_fill, g.rec_cap, g.rec, g.rec_eid, g.rec_theta,
-                                                           &b.acc->eval_status);
+                                                           g.cell_fill, g.rec_cap, g.rec, &b.acc->eval_status);
 }
 
 void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items, uint32_t ideal,
                        PerEdge pe, cudaStream_t s) {
-    const int C = (65536 >> k) * (65536 >> k);
     if (n_items == 0) return;
     const int blocks = grid_for((int64_t)n_items, GP_WARPS, 152 * 8);
     count_launches(1);
     if (pe.counts)
-        k_grid_pairs<true><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.rec_eid, g.rec_theta, g.cell_off, g.item_off,
-                                                           C, k, b.acc, ideal, pe);
+        k_grid_pairs<true><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.cell_off, g.item_off, g.item_cell,
+                                                           (uint32_t)n_items, k, b.acc, ideal, pe);
     else
-        k_grid_pairs<false><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.rec_eid, g.rec_theta, g.cell_off,
-                                                            g.item_off, C, k, b.acc, ideal, pe);
+        k_grid_pairs<false><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.cell_off, g.item_off, g.item_cell,
+                                                            (uint32_t)n_items, k, b.acc, ideal, pe);
 }
 
 }  // namespace gr
