@@ -64,6 +64,8 @@ gr_status dalloc(T **p, size_t n) {
 struct gr_layout {
     int64_t V = 0, E = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;      // occlusion, min angle, ELV run here, beside the crossings
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     gr_options opt{};
     Buffers b;
     GridBuffers g;
@@ -84,7 +86,7 @@ namespace {
 std::atomic<int64_t> g_launches{0};
 
 void free_grid(GridBuffers &g) {
-    void *ptrs[] = {g.cell_off, g.item_off, g.cell_fill, g.rec, g.item_cell, g.ocell_off, g.ocell_fill, g.opts};
+    void *ptrs[] = {g.cell_off, g.item_off, g.cell_fill, g.rec, g.item_desc, g.ocell_off, g.ocell_fill, g.opts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g = GridBuffers{};
@@ -94,12 +96,15 @@ void free_layout(gr_layout *L) {
     if (!L) return;
     Buffers &b = L->b;
     void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.ma_part,
-                    b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.result};
+                    b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_grid(L->g);
     for (auto &e : L->ev)
         if (e) cudaEventDestroy(e);
+    if (L->ev_fork) cudaEventDestroy(L->ev_fork);
+    if (L->ev_join) cudaEventDestroy(L->ev_join);
+    if (L->side) cudaStreamDestroy(L->side);
     if (L->h_result) cudaFreeHost(L->h_result);
     if (L->h_acc) cudaFreeHost(L->h_acc);
     delete L;
@@ -125,8 +130,12 @@ gr_status alloc_layout(gr_layout *L) {
     GR_TRY(dalloc(&b.deg_fill, (size_t)V));
     GR_TRY(dalloc(&b.dirs, 2 * (size_t)E));
     GR_TRY(dalloc(&b.scan_tmp, (size_t)kScanMaxBlocks));
+    GR_TRY(dalloc(&b.scan_tmp_side, (size_t)kScanMaxBlocks));
     GR_TRY(dalloc(&b.result, 1));
 #undef GR_TRY
+    GR_CU(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
+    GR_CU(cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming));
+    GR_CU(cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming));
     GR_CU(cudaMallocHost((void **)&L->h_result, sizeof(gr_result)));
     GR_CU(cudaMallocHost((void **)&L->h_acc, sizeof(DevAcc)));
     GR_CU(cudaMemsetAsync(b.acc, 0, sizeof(DevAcc), L->stream));
@@ -161,12 +170,12 @@ gr_status ensure_records(gr_layout *L, uint64_t R, uint64_t items) {
         if ((st = dalloc(&g.rec, (size_t)cap)) != GR_OK) return st;
         g.rec_cap = cap;
     }
-    if (g.items_cap < items || !g.item_cell) {
-        if (g.item_cell) cudaFree(g.item_cell);
-        g.item_cell = nullptr;
+    if (g.items_cap < items || !g.item_desc) {
+        if (g.item_desc) cudaFree(g.item_desc);
+        g.item_desc = nullptr;
         g.items_cap = 0;
         const uint64_t cap = items + items / 4 + 1024;
-        if ((st = dalloc(&g.item_cell, (size_t)cap)) != GR_OK) return st;
+        if ((st = dalloc(&g.item_desc, (size_t)cap)) != GR_OK) return st;
         g.items_cap = cap;
     }
     return GR_OK;
@@ -188,15 +197,17 @@ gr_status ensure_ocells(gr_layout *L, int C) {
 }
 
 // ------------------------------------------------------------ phase timing
-void phase_begin(gr_layout *L, int ph) {
-    if (L->profiling) cudaEventRecord(L->ev[2 * ph], L->stream);
+void phase_begin(gr_layout *L, int ph, cudaStream_t s) {
+    if (L->profiling) cudaEventRecord(L->ev[2 * ph], s);
 }
-void phase_end(gr_layout *L, int ph) {
+void phase_end(gr_layout *L, int ph, cudaStream_t s) {
     if (L->profiling) {
-        cudaEventRecord(L->ev[2 * ph + 1], L->stream);
+        cudaEventRecord(L->ev[2 * ph + 1], s);
         L->pending[ph] = true;
     }
 }
+void phase_begin(gr_layout *L, int ph) { phase_begin(L, ph, L->stream); }
+void phase_end(gr_layout *L, int ph) { phase_end(L, ph, L->stream); }
 // After a stream synchronisation: folds the recorded phases into the totals.
 void phase_collect(gr_layout *L) {
     if (!L->profiling) return;
@@ -394,18 +405,49 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
                           sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
 
+    // Occlusion, minimum angle and edge length variation depend only on the
+    // inputs: they run on the side stream, beside the crossing pipeline.
+    cudaStream_t t = L->side;
+    GR_CU(cudaEventRecord(L->ev_fork, s));
+    GR_CU(cudaStreamWaitEvent(t, L->ev_fork, 0));
     if (metrics & GR_METRIC_EDGE_LENGTH) {
-        phase_begin(L, GR_PHASE_EDGE_LENGTH);
-        launch_elv(b, E, s);
-        phase_end(L, GR_PHASE_EDGE_LENGTH);
+        phase_begin(L, GR_PHASE_EDGE_LENGTH, t);
+        launch_elv(b, E, t);
+        phase_end(L, GR_PHASE_EDGE_LENGTH, t);
     }
     if (metrics & GR_METRIC_MIN_ANGLE) {
-        phase_begin(L, GR_PHASE_MIN_ANGLE);
-        launch_min_angle(b, V, E, s);
-        phase_end(L, GR_PHASE_MIN_ANGLE);
+        phase_begin(L, GR_PHASE_MIN_ANGLE, t);
+        launch_min_angle(b, V, E, t);
+        phase_end(L, GR_PHASE_MIN_ANGLE, t);
     }
+    int32_t occl_path = 0;
+    if (metrics & GR_METRIC_OCCLUSION) {
+        // grid of side >= d for many vertices; all-pairs tiles for few, or when
+        // d is so large that the grid has at most 4 x 4 cells
+        const int ko = occl_cell_log2(d);
+        bool grid;
+        if (L->opt.occlusion_path == GR_PATH_GRID) grid = ko <= 16;
+        else if (L->opt.occlusion_path == GR_PATH_ALLPAIRS) grid = false;
+        else grid = V > 4096 && ko <= 14;
+        if (grid && V >= 2 && d > 0) {
+            const int C = (65536 >> ko) * (65536 >> ko);
+            if ((st = ensure_ocells(L, C)) != GR_OK) return st;
+            phase_begin(L, GR_PHASE_OCCL_BIN, t);
+            launch_occlusion_grid_count(b, V, L->g, ko, t);
+            phase_end(L, GR_PHASE_OCCL_BIN, t);
+            phase_begin(L, GR_PHASE_OCCL_PAIRS, t);
+            launch_occlusion_grid_pairs(b, V, L->g, ko, d, t);
+            phase_end(L, GR_PHASE_OCCL_PAIRS, t);
+        } else {
+            phase_begin(L, GR_PHASE_OCCL_PAIRS, t);
+            launch_occlusion_allpairs(b, V, d, t);
+            phase_end(L, GR_PHASE_OCCL_PAIRS, t);
+        }
+        occl_path = grid ? GR_PATH_GRID : GR_PATH_ALLPAIRS;
+    }
+    GR_CU(cudaEventRecord(L->ev_join, t));
 
-    // binning passes whose sizes the host needs
+    // crossing binning; the host needs its sizes
     CrossPlan cp;
     bool need_sync = false;
     if ((metrics & GR_METRIC_CROSSINGS) && n_seg >= 2) {
@@ -419,30 +461,18 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
             need_sync = true;
         }
     }
-    bool occl_grid = false;
-    const int ko = occl_cell_log2(d);
-    if ((metrics & GR_METRIC_OCCLUSION) && V >= 2 && d > 0) {
-        if (L->opt.occlusion_path == GR_PATH_GRID) occl_grid = ko <= 16;
-        else if (L->opt.occlusion_path == GR_PATH_ALLPAIRS) occl_grid = false;
-        else occl_grid = V > 4096 && ko <= 14;
-        if (occl_grid) {
-            const int C = (65536 >> ko) * (65536 >> ko);
-            if ((st = ensure_ocells(L, C)) != GR_OK) return st;
-            phase_begin(L, GR_PHASE_OCCL_BIN);
-            launch_occlusion_grid_count(b, V, L->g, ko, s);
-            phase_end(L, GR_PHASE_OCCL_BIN);
-            need_sync = true;
-        }
-    }
     if (need_sync) {
         GR_CU(cudaGetLastError());
         GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
         L->io_d2h += (int64_t)sizeof(DevAcc);
         GR_CU(cudaStreamSynchronize(s));
-        if ((st = status_to_error(L->h_acc->eval_status)) != GR_OK) return st;
+        if ((st = status_to_error(L->h_acc->eval_status)) != GR_OK) {
+            cudaStreamSynchronize(t);
+            return st;
+        }
     }
 
-    int32_t path = 0, occl_path = 0;
+    int32_t path = 0;
     int64_t pairs_tested = -1;
     if ((metrics & GR_METRIC_CROSSINGS) && n_seg >= 2) {
         bool grid = cp.grid;
@@ -471,22 +501,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     } else if (metrics & GR_METRIC_CROSSINGS) {
         path = GR_PATH_ALLPAIRS;
     }
-    if (metrics & GR_METRIC_OCCLUSION) {
-        bool grid = occl_grid;
-        if (grid && L->opt.occlusion_path == GR_PATH_AUTO) {
-            const double v = (double)V;
-            grid = 4.0 * (double)L->h_acc->occl_work < v * (v - 1) / 2;
-        }
-        phase_begin(L, GR_PHASE_OCCL_PAIRS);
-        if (grid) {
-            launch_occlusion_grid_pairs(b, V, L->g, ko, d, s);
-            occl_path = GR_PATH_GRID;
-        } else {
-            launch_occlusion_allpairs(b, V, d, s);
-            occl_path = GR_PATH_ALLPAIRS;
-        }
-        phase_end(L, GR_PHASE_OCCL_PAIRS);
-    }
+    GR_CU(cudaStreamWaitEvent(s, L->ev_join, 0));
     phase_begin(L, GR_PHASE_FINALIZE);
     launch_finalize(b, metrics, E, ideal, d, V > 0 ? min_angle_blocks(V) : 0, path,
                     path == GR_PATH_GRID ? cp.k : 0, occl_path, pairs_tested, s);

@@ -45,7 +45,6 @@ struct DevAcc {
     uint64_t records;          // grid (edge, cell) records
     uint64_t grid_items;       // pair-kernel work items
     uint64_t grid_work;        // sum over cells of n (n - 1) / 2
-    uint64_t occl_work;        // candidate vertex pairs of the occlusion grid
     uint64_t scan_sink;        // totals nobody reads
 };
 
@@ -76,7 +75,8 @@ struct Buffers {
     uint32_t *deg = nullptr;      // [V + 1] degree, then CSR offsets (scan in place)
     uint32_t *deg_fill = nullptr; // [V]
     int2 *dirs = nullptr;         // [2 E] incident directions by vertex
-    uint64_t *scan_tmp = nullptr; // [kScanMaxBlocks] block sums
+    uint64_t *scan_tmp = nullptr; // [kScanMaxBlocks] block sums (crossing stream)
+    uint64_t *scan_tmp_side = nullptr; // [kScanMaxBlocks] block sums (side stream)
     gr_result *result = nullptr;  // device copy of the result
 };
 
@@ -94,7 +94,7 @@ struct GridBuffers {
     uint32_t *cell_fill = nullptr; // [C]
     GridRec *rec = nullptr;        // [rec_cap] records sorted by cell
     uint64_t rec_cap = 0;
-    uint32_t *item_cell = nullptr; // [items_cap] cell of every work item
+    uint4 *item_desc = nullptr;    // [items_cap] {cell record offset, records, cell, ti << 16 | tj}
     uint64_t items_cap = 0;
     int cells_cap = 0;             // C the cell arrays are sized for
     // occlusion grid
@@ -145,8 +145,8 @@ void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int 
 void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items, uint32_t ideal,
                        PerEdge pe, cudaStream_t s);
 
-// a8 occlusion grid: cell side 2^k >= d.  Count + scan + stencil work
-// (-> acc->occl_work), then scatter + pair kernel.
+// a8 occlusion grid: cell side 2^k >= d.  Count + scan, then scatter + pair
+// kernel.
 void launch_occlusion_grid_count(const Buffers &b, int64_t V, const GridBuffers &g, int k,
                                  cudaStream_t s);
 void launch_occlusion_grid_pairs(const Buffers &b, int64_t V, const GridBuffers &g, int k, int64_t d,

@@ -163,11 +163,20 @@ __global__ void __launch_bounds__(256) k_cell_items(const uint32_t *__restrict__
     if (threadIdx.x == 0) atomic_add_u64(&acc->grid_work, w);
 }
 
-// The cell of every work item (replaces a search over the item offsets).
-__global__ void __launch_bounds__(256) k_item_cells(const uint32_t *__restrict__ item_off, int C,
-                                                    uint32_t *__restrict__ item_cell) {
+// Descriptor of every work item: {record offset of its cell, records in the
+// cell, cell id, row tile << 16 | column tile}, so the pair kernel reads one
+// 16-byte word per item instead of a chain of dependent loads.
+__global__ void __launch_bounds__(256) k_item_descs(const uint32_t *__restrict__ item_off,
+                                                    const uint32_t *__restrict__ cell_off, int C,
+                                                    uint4 *__restrict__ desc) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-        for (uint32_t q = item_off[c], e = item_off[c + 1]; q < e; ++q) item_cell[q] = (uint32_t)c;
+        uint32_t q = item_off[c];
+        const uint32_t e = item_off[c + 1];
+        if (q == e) continue;
+        const uint32_t base = cell_off[c], n = cell_off[c + 1] - base;
+        const uint32_t T = (n + TILE - 1) / TILE;
+        for (uint32_t tj = 0; tj < T && q < e; ++tj)
+            for (uint32_t ti = 0; ti <= tj && q < e; ++ti) desc[q++] = make_uint4(base, n, (uint32_t)c, (ti << 16) | tj);
     }
 }
 
@@ -277,33 +286,57 @@ __device__ __forceinline__ bool owns_collinear(const GSeg &r, const GSeg &c, int
     return 0 <= lx && lx < w && 0 <= ly && ly < w;
 }
 
+// Owner test with an FP32 fast path.  For two "exact" segments (see GSeg)
+// num = (c - a) x v and den = u x v are exact integers in FP32 (|den| <= 2^21,
+// |num| <= 2^24), t = num / den carries a relative error below 2^-21 and
+// P_x = a_x + u_x t an absolute error below 2^-11 (|u_x t| <= 2^10, |P_x| <
+// 2^13).  P is decided inside or outside the half-open cell [0, w)^2 when it
+// is further than 2^-9 from the cell's border; otherwise, or for segments
+// that are not both exact, the exact int64 test decides.
+__device__ __forceinline__ bool owns_crossing_fast(const GSeg &r, const GSeg &c, int w) {
+    if (r.exact & c.exact) {
+        const float den = r.ux * c.uy - r.uy * c.ux;
+        const float num = (c.ax - r.ax) * c.uy - (c.ay - r.ay) * c.ux;
+        const float t = __fdividef(num, den);
+        const float X = fmaf(r.ux, t, r.ax), Y = fmaf(r.uy, t, r.ay);
+        const float e = 1.0f / 512.0f, fw = (float)w;
+        const bool in = X >= e && X < fw - e && Y >= e && Y < fw - e;
+        const bool out = X < -e || X >= fw + e || Y < -e || Y >= fw + e;
+        if (in) return true;
+        if (out) return false;
+    }
+    const int iax = (int)r.ax, iay = (int)r.ay, icx = (int)c.ax, icy = (int)c.ay;
+    return owns_crossing(iax, iay, (int)r.bx - iax, (int)r.by - iay, icx, icy, (int)c.bx - icx, (int)c.by - icy, w);
+}
+
 // a6 -- one warp per work item (cell, row tile ti, column tile tj), items in a
 // warp-strided static order.  Off-diagonal items test all rows x columns;
 // diagonal items use a rotation schedule (round q pairs lane i with
 // (i + q) mod m) so that every lane has work in every round.  Orientations
 // are evaluated in FP32 in the cell's coordinates: exact for pairs of short
-// segments near the cell, filtered for the rest, and re-decided in int64
-// when inconclusive.  A pair in E_c counts only if this cell owns its
-// intersection point; a collinear overlap only if this cell owns the
-// lexicographically smallest point of the overlap.
+// segments near the cell, filtered for the rest.  The rounds only record, per
+// lane, bitmasks of the columns that are E_c candidates, collinear candidates
+// or inconclusive; each lane then settles its own bits (exact int64 for the
+// inconclusive ones) and applies the owner rules: a pair in E_c counts only
+// if this cell owns its intersection point, a collinear overlap only if this
+// cell owns the lexicographically smallest point of the overlap.
 template <bool PER_EDGE>
-__global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
-    const GridRec *__restrict__ rec, const uint32_t *__restrict__ cell_off, const uint32_t *__restrict__ item_off,
-    const uint32_t *__restrict__ item_cell, uint32_t n_items, int k, DevAcc *acc, uint32_t ideal, PerEdge pe) {
+__global__ void __launch_bounds__(GP_WARPS * 32, 4) k_grid_pairs(const GridRec *__restrict__ rec,
+                                                                 const uint4 *__restrict__ descs, uint32_t n_items,
+                                                                 int k, DevAcc *acc, uint32_t ideal, PerEdge pe) {
     __shared__ GSeg cs[GP_WARPS][TILE];
     __shared__ uint64_t shu[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int G = 65536 >> k, w = 1 << k;
+    const uint32_t stride = gridDim.x * GP_WARPS;
     PairCounts pc;
-    for (uint32_t it = blockIdx.x * GP_WARPS + wid; it < n_items; it += gridDim.x * GP_WARPS) {
-        const int cell = (int)item_cell[it];
-        const uint32_t q = it - item_off[cell];
-        int r = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-        while (r * (r + 1) / 2 > (int)q) --r;
-        while ((r + 1) * (r + 2) / 2 <= (int)q) ++r;
-        const int tj = r, ti = (int)q - r * (r + 1) / 2;
-        const uint32_t base = cell_off[cell];
-        const int n = (int)(cell_off[cell + 1] - base);
+    uint32_t it = blockIdx.x * GP_WARPS + wid;
+    uint4 next = it < n_items ? descs[it] : make_uint4(0, 0, 0, 0);
+    for (; it < n_items; it += stride) {
+        const uint4 d = next;
+        if (it + stride < n_items) next = descs[it + stride];  // prefetch the next item
+        const uint32_t base = d.x;
+        const int n = (int)d.y, cell = (int)d.z, ti = (int)(d.w >> 16), tj = (int)(d.w & 0xffffu);
         const int x0 = (cell % G) << k, y0 = (cell / G) << k;
         const int mr = min(TILE, n - ti * TILE), mc = min(TILE, n - tj * TILE);
 
@@ -314,6 +347,7 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
         __syncwarp();
         if (lane >= mr) continue;
 
+        uint32_t m_ec = 0, m_prop = 0, m_coll = 0, m_unsure = 0;
         const bool diag = ti == tj;
         const int rounds = diag ? mr / 2 : mc;
         for (int s = 0; s < rounds; ++s) {
@@ -326,57 +360,70 @@ __global__ void __launch_bounds__(GP_WARPS * 32) k_grid_pairs(
             } else {
                 jj = s;
             }
-            const GSeg &c = cs[wid][jj];
+            const GSeg c = cs[wid][jj];
             const float o1 = fmaf(rs.ux, c.ay, fmaf(-rs.uy, c.ax, rs.nk));
             const float o2 = fmaf(rs.ux, c.by, fmaf(-rs.uy, c.bx, rs.nk));
             const float o3 = fmaf(c.ux, rs.ay, fmaf(-c.uy, rs.ax, c.nk));
             const float o4 = fmaf(c.ux, rs.by, fmaf(-c.uy, rs.bx, c.nk));
-            const bool exact = (rs.exact & c.exact) != 0;
             const float mn = fminf(fminf(fabsf(o1), fabsf(o2)), fminf(fabsf(o3), fabsf(o4)));
-            int kind;
-            if (exact || mn > kOrientFilter) {
-                const bool shared = (rs.ida == c.ida) | (rs.ida == c.idb) | (rs.idb == c.ida) | (rs.idb == c.idb);
-                const float p12 = o1 * o2, p34 = o3 * o4;
-                if (shared || p12 > 0.f || p34 > 0.f) continue;
-                if (o1 == 0.f && o2 == 0.f) {
-                    // collinear: the extents meet iff the larger lexicographic minimum
-                    // is <= the smaller maximum (coordinates exact in FP32)
-                    const bool ar = rs.ax < rs.bx || (rs.ax == rs.bx && rs.ay <= rs.by);
-                    const bool ac = c.ax < c.bx || (c.ax == c.bx && c.ay <= c.by);
-                    const float elx = ar ? rs.ax : rs.bx, ely = ar ? rs.ay : rs.by;
-                    const float ehx = ar ? rs.bx : rs.ax, ehy = ar ? rs.by : rs.ay;
-                    const float flx = ac ? c.ax : c.bx, fly = ac ? c.ay : c.by;
-                    const float fhx = ac ? c.bx : c.ax, fhy = ac ? c.by : c.ay;
-                    const bool lo_e = elx > flx || (elx == flx && ely >= fly);  // lo = e's min
-                    const float lx = lo_e ? elx : flx, ly = lo_e ? ely : fly;
-                    const bool hi_e = ehx < fhx || (ehx == fhx && ehy <= fhy);
-                    const float hx = hi_e ? ehx : fhx, hy = hi_e ? ehy : fhy;
-                    kind = (lx < hx || (lx == hx && ly <= hy)) ? PAIR_COLLINEAR : PAIR_NONE;
-                } else {
-                    kind = (p12 < 0.f && p34 < 0.f) ? PAIR_PROPER : PAIR_TOUCHING;
-                }
-            } else {
-                kind = classify_exact(rs, c, x0, y0);
-            }
-            if (kind == PAIR_NONE) continue;
-            if (kind == PAIR_COLLINEAR) {
-                if (!owns_collinear(rs, c, w)) continue;
-                ++pc.collinear;
-                if (PER_EDGE) {
-                    atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)rs.eid + 2], 1ull);
-                    atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)c.eid + 2], 1ull);
-                }
-                continue;
-            }
-            const int iax = (int)rs.ax, iay = (int)rs.ay, icx = (int)c.ax, icy = (int)c.ay;
-            if (!owns_crossing(iax, iay, (int)rs.bx - iax, (int)rs.by - iay, icx, icy, (int)c.bx - icx,
-                               (int)c.by - icy, w))
-                continue;
-            const uint32_t qd = dev_term(rs.th, c.th, ideal);
-            pc.dev += qd;
-            if (kind == PAIR_PROPER) ++pc.proper; else ++pc.touching;
+            const uint32_t bit = 1u << jj;
+            const bool sure = (rs.exact & c.exact) || mn > kOrientFilter;
+            const bool shared = (rs.ida == c.ida) | (rs.ida == c.idb) | (rs.idb == c.ida) | (rs.idb == c.idb);
+            const float p12 = o1 * o2, p34 = o3 * o4;
+            const bool cand = !shared && p12 <= 0.f && p34 <= 0.f;
+            const bool coll = o1 == 0.f && o2 == 0.f;
+            m_unsure |= sure ? 0u : bit;
+            m_ec |= (sure && cand && !coll) ? bit : 0u;
+            m_prop |= (sure && p12 < 0.f && p34 < 0.f) ? bit : 0u;
+            m_coll |= (sure && cand && coll) ? bit : 0u;
+        }
+        // inconclusive pairs: exact int64
+        while (m_unsure) {
+            const int jj = __ffs(m_unsure) - 1;
+            m_unsure &= m_unsure - 1;
+            const int kind = classify_exact(rs, cs[wid][jj], x0, y0);
+            const uint32_t bit = 1u << jj;
+            if (kind == PAIR_PROPER) { m_ec |= bit; m_prop |= bit; }
+            else if (kind == PAIR_TOUCHING) m_ec |= bit;
+            else if (kind == PAIR_COLLINEAR) m_coll |= bit;
+        }
+        // collinear candidates: the extents must meet, and this cell must own
+        // the smallest point of the overlap (coordinates exact in FP32)
+        while (m_coll) {
+            const int jj = __ffs(m_coll) - 1;
+            m_coll &= m_coll - 1;
+            const GSeg c = cs[wid][jj];
+            const bool ar = rs.ax < rs.bx || (rs.ax == rs.bx && rs.ay <= rs.by);
+            const bool ac = c.ax < c.bx || (c.ax == c.bx && c.ay <= c.by);
+            const float elx = ar ? rs.ax : rs.bx, ely = ar ? rs.ay : rs.by;
+            const float ehx = ar ? rs.bx : rs.ax, ehy = ar ? rs.by : rs.ay;
+            const float flx = ac ? c.ax : c.bx, fly = ac ? c.ay : c.by;
+            const float fhx = ac ? c.bx : c.ax, fhy = ac ? c.by : c.ay;
+            const bool lo_e = elx > flx || (elx == flx && ely >= fly);
+            const float lx = lo_e ? elx : flx, ly = lo_e ? ely : fly;
+            const bool hi_e = ehx < fhx || (ehx == fhx && ehy <= fhy);
+            const float hx = hi_e ? ehx : fhx, hy = hi_e ? ehy : fhy;
+            if (!(lx < hx || (lx == hx && ly <= hy))) continue;
+            if (!owns_collinear(rs, c, w)) continue;
+            ++pc.collinear;
             if (PER_EDGE) {
-                const int slot = kind == PAIR_PROPER ? 0 : 1;
+                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)rs.eid + 2], 1ull);
+                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)c.eid + 2], 1ull);
+            }
+        }
+        // E_c candidates: owner of the intersection point
+        while (m_ec) {
+            const int jj = __ffs(m_ec) - 1;
+            const uint32_t bit = 1u << jj;
+            m_ec &= m_ec - 1;
+            const GSeg c = cs[wid][jj];
+            if (!owns_crossing_fast(rs, c, w)) continue;
+            const uint32_t qd = dev_term(rs.th, c.th, ideal);
+            const bool prop = (m_prop & bit) != 0;
+            pc.dev += qd;
+            if (prop) ++pc.proper; else ++pc.touching;
+            if (PER_EDGE) {
+                const int slot = prop ? 0 : 1;
                 atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)rs.eid + slot], 1ull);
                 atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)c.eid + slot], 1ull);
                 atomicAdd((unsigned long long *)&pe.dev[rs.eid], (unsigned long long)qd);
@@ -410,7 +457,7 @@ void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int 
     const int C = (65536 >> k) * (65536 >> k);
     cudaMemsetAsync(g.cell_fill, 0, sizeof(uint32_t) * C, s);
     count_launches(1 + (E > 0 ? 1 : 0));
-    k_item_cells<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.item_off, C, g.item_cell);
+    k_item_descs<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.item_off, g.cell_off, C, g.item_desc);
     if (E <= 0) return;
     k_grid_fill<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, b.acc, k, g.cell_off,
                                                            g.cell_fill, g.rec_cap, g.rec, &b.acc->eval_status);
@@ -422,11 +469,11 @@ void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n
     const int blocks = grid_for((int64_t)n_items, GP_WARPS, 152 * 8);
     count_launches(1);
     if (pe.counts)
-        k_grid_pairs<true><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.cell_off, g.item_off, g.item_cell,
-                                                           (uint32_t)n_items, k, b.acc, ideal, pe);
+        k_grid_pairs<true><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.item_desc, (uint32_t)n_items, k, b.acc, ideal,
+                                                           pe);
     else
-        k_grid_pairs<false><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.cell_off, g.item_off, g.item_cell,
-                                                            (uint32_t)n_items, k, b.acc, ideal, pe);
+        k_grid_pairs<false><<<blocks, GP_WARPS * 32, 0, s>>>(g.rec, g.item_desc, (uint32_t)n_items, k, b.acc,
+                                                            ideal, pe);
 }
 
 }  // namespace gr

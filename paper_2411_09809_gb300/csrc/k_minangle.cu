@@ -179,7 +179,7 @@ void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
     const int gb = grid_for(E, 256, 152 * 8);
     count_launches(E > 0 ? 3 : 1);
     if (E > 0) k_degree<<<gb, 256, 0, s>>>(b.seg, b.acc, b.deg);
-    launch_scan_u32(b.deg, b.deg, V, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
+    launch_scan_u32(b.deg, b.deg, V, b.scan_tmp_side, &b.acc->scan_sink, &b.acc->eval_status, s);
     if (E > 0) k_fill_dirs<<<gb, 256, 0, s>>>(b.seg, b.acc, b.deg, b.deg_fill, b.dirs);
     k_min_angle<<<min_angle_blocks(V), MA_THREADS, 0, s>>>(b.deg, b.dirs, V, b.ma_part, b.ma_cnt);
 }

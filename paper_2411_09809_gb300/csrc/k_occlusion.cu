@@ -62,29 +62,6 @@ __global__ void __launch_bounds__(256) k_occl_count(const int2 *__restrict__ xy,
     }
 }
 
-// Candidate pairs of the stencil (for the grid vs all-pairs decision).
-__global__ void __launch_bounds__(256) k_occl_work(const uint32_t *__restrict__ off, int G, DevAcc *acc) {
-    __shared__ uint64_t sh[32];
-    uint64_t w = 0;
-    const int C = G * G;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-        const uint64_t n = off[c + 1] - off[c];
-        if (n == 0) continue;
-        const int cx = c % G, cy = c / G;
-        uint64_t nb = 0;
-        if (cx + 1 < G) nb += off[c + 2] - off[c + 1];
-        if (cy + 1 < G) {
-            const int up = c + G;
-            nb += off[up + 1] - off[up];
-            if (cx + 1 < G) nb += off[up + 2] - off[up + 1];
-            if (cx > 0) nb += off[up] - off[up - 1];
-        }
-        w += n * (n - 1) / 2 + n * nb;
-    }
-    w = block_sum<uint64_t>(w, sh);
-    if (threadIdx.x == 0) atomic_add_u64(&acc->occl_work, w);
-}
-
 __global__ void __launch_bounds__(256) k_occl_fill(const int2 *__restrict__ xy, int64_t V, int k,
                                                    const uint32_t *__restrict__ off,
                                                    uint32_t *__restrict__ fill, uint32_t *__restrict__ pts) {
@@ -148,10 +125,9 @@ int grid_for(int64_t n, int threads, int max_blocks) {
 void launch_occlusion_grid_count(const Buffers &b, int64_t V, const GridBuffers &g, int k, cudaStream_t s) {
     const int G = 65536 >> k, C = G * G;
     cudaMemsetAsync(g.ocell_off, 0, sizeof(uint32_t) * (C + 1), s);
-    count_launches(V > 0 ? 2 : 1);
+    count_launches(V > 0 ? 1 : 0);
     if (V > 0) k_occl_count<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.xy, V, k, g.ocell_off);
-    launch_scan_u32(g.ocell_off, g.ocell_off, C, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
-    k_occl_work<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.ocell_off, G, b.acc);
+    launch_scan_u32(g.ocell_off, g.ocell_off, C, b.scan_tmp_side, &b.acc->scan_sink, &b.acc->eval_status, s);
 }
 
 void launch_occlusion_grid_pairs(const Buffers &b, int64_t V, const GridBuffers &g, int k, int64_t d,
