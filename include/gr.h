@@ -178,6 +178,35 @@ gr_status gr_crossing_angle(gr_layout *layout, double ideal_rad, gr_crossing_ang
 gr_status gr_crossings_per_edge(gr_layout *layout, double ideal_rad, int64_t *d_counts,
                                 double *d_dev);
 
+/* ------------------------------------------------------------- batches
+ * Many independent layouts evaluated together (the batched form of the five
+ * metrics): layouts are packed one after another.  `v_off` and `e_off` are
+ * int64 [n_layouts + 1] prefix offsets (host or device memory): layout l owns
+ * vertices [v_off[l], v_off[l+1]) of `xy` ([V][2] int32, V = v_off[n]) and
+ * edges [e_off[l], e_off[l+1]) of `edges` ([E][2] int32), whose vertex ids
+ * are local to the layout (0 <= id < v_off[l+1] - v_off[l]).  Results are
+ * per layout, exactly those of gr_evaluate on each layout alone, except that
+ * crossings always take the grid path (pairs_tested counts grid candidates).
+ *
+ * gr_batch_create validates (GR_EINVAL / GR_ERANGE as gr_layout_create),
+ * plans one crossing grid per layout (cell size from a cost model on the
+ * layout's segment count and length, shifted by an offset an autotuner picks
+ * by timing; opt->cell_log2 < 0 fixes that offset instead, and the tuned
+ * offset is cached in the file named by the environment variable
+ * GR_TUNE_CACHE when it is set) and synchronises.  gr_batch_evaluate runs
+ * the evaluation as one CUDA graph on the batch's stream (captured on the
+ * first call and again when the metrics, ideal angle or d change), writes
+ * gr_result [n_layouts] to `out` (host or device memory) and synchronises.
+ * gr_batch_update replaces coordinates (and edges if not NULL), same sizes. */
+typedef struct gr_batch gr_batch;
+
+gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_off, const int64_t *e_off,
+                          const void *xy, gr_coord_type coord_type, const int32_t *edges,
+                          const gr_options *opt, gr_stream_t stream);
+gr_status gr_batch_update(gr_batch *batch, const void *xy, const int32_t *edges);
+gr_status gr_batch_evaluate(gr_batch *batch, uint32_t metrics, const gr_params *params, gr_result *out);
+gr_status gr_batch_destroy(gr_batch *batch);
+
 /* ------------------------------------------------------------- tracing
  * Phase timing: when enabled on a layout, every gr_layout_update and
  * gr_evaluate records CUDA events around its phases on the layout's stream;

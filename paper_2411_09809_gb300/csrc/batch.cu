@@ -1,0 +1,933 @@
+// batch.cu -- gr_batch_*: many independent layouts evaluated together.
+//
+// Layouts are packed one after another (vertex and edge offsets per layout,
+// edges with layout-local vertex ids).  Every step of the single-layout path
+// runs once over the whole pack:
+//   gather      global vertex ids, segments, directions, the layout of each
+//               segment;
+//   crossings   one uniform grid per layout (cell side 2^k_l, cells numbered
+//               from cbase[l]), so the DDA count, scan, scatter and per-cell
+//               pair kernel cover all layouts in single launches; the pair
+//               kernel is persistent (one block per SM slot, each warp a
+//               contiguous run of work items) and writes one partial per work
+//               item, reduced per layout in a fixed order;
+//   occlusion   one grid per layout with cells of side >= d;
+//   min angle, edge length variation: one block per layout.
+// The cell size k_l of every layout comes from a cost model on the layout's
+// segment count and total L1 length (records n + L1 / w against candidate
+// pairs >= R^2 / (2C)), shifted by a global offset that an autotuner picks
+// by timing the crossing pipeline at creation (cached in the file named by
+// GR_TUNE_CACHE, when set).  The whole evaluation is captured once into a
+// CUDA graph and replayed; every kernel reads the sizes it needs from device
+// memory and checks them against the buffers, so a replay after coordinates
+// changed either fits or raises an overflow bit, on which the host re-plans.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "grid_common.cuh"
+
+using namespace gr;
+
+namespace {
+
+constexpr int BP_WARPS = 8;
+
+struct ItemPart {
+    uint32_t proper, touching, collinear, pad;
+    uint64_t dev;
+};
+
+int grid_for(int64_t n, int threads, int max_blocks) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Gather + validation for packed layouts: edge e of layout l (found from
+// e_off) has layout-local vertex ids; they become global ids v_off[l] + id.
+__global__ void __launch_bounds__(256) k_batch_gather(const int2 *__restrict__ xy, const int64_t *__restrict__ v_off,
+                                                      const int2 *__restrict__ edges, const int64_t *__restrict__ e_off,
+                                                      int64_t L, int64_t E, SegRec *__restrict__ seg,
+                                                      int32_t *__restrict__ seg_eid, uint32_t *__restrict__ seg_theta,
+                                                      uint32_t *__restrict__ seg_layout, int64_t *__restrict__ len2,
+                                                      DevAcc *acc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        bool keep = false;
+        SegRec r = make_uint4(0, 0, 0, 0);
+        uint32_t l = 0;
+        if (e < E) {
+            l = (uint32_t)find_segment(e_off, L, e);
+            const int64_t v0 = v_off[l], Vl = v_off[l + 1] - v0;
+            const int2 ed = edges[e];
+            int64_t l2 = 0;
+            if (ed.x < 0 || ed.y < 0 || ed.x >= Vl || ed.y >= Vl || ed.x == ed.y) {
+                atomicOr(&acc->status, ST_BAD_ID);
+            } else {
+                const int64_t ga = v0 + ed.x, gb = v0 + ed.y;
+                const int2 a = xy[ga], b = xy[gb];
+                if ((unsigned)a.x >= 65536u || (unsigned)a.y >= 65536u || (unsigned)b.x >= 65536u ||
+                    (unsigned)b.y >= 65536u) {
+                    atomicOr(&acc->status, ST_BAD_COORD);
+                } else {
+                    const int64_t dx = b.x - a.x, dy = b.y - a.y;
+                    l2 = dx * dx + dy * dy;
+                    if (l2 != 0) {
+                        keep = true;
+                        r = make_uint4(uint32_t(a.x) | (uint32_t(a.y) << 16), uint32_t(b.x) | (uint32_t(b.y) << 16),
+                                       (uint32_t)ga, (uint32_t)gb);
+                    }
+                }
+            }
+            len2[e] = l2;
+        }
+        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+        uint32_t slot = 0;
+        if (lane == 0 && mk) slot = atomicAdd(&acc->n_seg, (uint32_t)__popc(mk));
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (keep) {
+            const uint32_t pos = slot + __popc(mk & lanemask_lt());
+            seg[pos] = r;
+            seg_eid[pos] = (int32_t)e;
+            seg_theta[pos] = line_direction(px(r.y) - px(r.x), py(r.y) - py(r.x));
+            seg_layout[pos] = l;
+        }
+    }
+}
+
+// Per-layout segment counts and total L1 length, for the plan.
+__global__ void __launch_bounds__(256) k_batch_stats(const SegRec *__restrict__ seg,
+                                                     const uint32_t *__restrict__ seg_layout,
+                                                     const DevAcc *__restrict__ acc, unsigned long long *nseg,
+                                                     unsigned long long *l1) {
+    const int64_t n = acc->n_seg;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const SegRec r = seg[i];
+        const uint32_t l = seg_layout[i];
+        atomicAdd(&nseg[l], 1ull);
+        atomicAdd(&l1[l], (unsigned long long)(abs(px(r.y) - px(r.x)) + abs(py(r.y) - py(r.x))));
+    }
+}
+
+// a2 over all layouts: segment s walks layout l's grid (k_l, cells from cbase[l]).
+__global__ void __launch_bounds__(256) k_batch_grid_count(const SegRec *__restrict__ seg,
+                                                          const uint32_t *__restrict__ seg_layout,
+                                                          const DevAcc *__restrict__ acc, const int32_t *__restrict__ kl,
+                                                          const uint32_t *__restrict__ cbase,
+                                                          uint32_t *__restrict__ cell_cnt) {
+    const int64_t n = acc->n_seg;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool ok = i < n;
+        const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
+        const uint32_t l = ok ? seg_layout[i] : 0u;
+        const int k = ok ? kl[l] : 16;
+        const uint32_t cb = ok ? cbase[l] : 0u;
+        warp_for_each_cell(r, 0, 0u, ok, k, cb, [&](const int (&ids)[2], int nc, SegRec, int32_t, uint32_t) {
+            atomicAdd(&cell_cnt[ids[0]], 1u);
+            if (nc > 1) atomicAdd(&cell_cnt[ids[1]], 1u);
+        });
+    }
+}
+
+// Work items per cell (tile pairs), and the candidate pairs of each layout.
+__global__ void __launch_bounds__(256) k_batch_cell_items(const uint32_t *__restrict__ cell_off, uint32_t C,
+                                                          const uint32_t *__restrict__ cbase, int64_t L,
+                                                          uint32_t *__restrict__ item_cnt,
+                                                          unsigned long long *work, DevAcc *acc) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        const uint32_t n = cell_off[c + 1] - cell_off[c];
+        const uint64_t T = (n + TILE - 1) / TILE;
+        const uint64_t items = n < 2 ? 0 : T * (T + 1) / 2;
+        if (items > 0x7fffffffull) atomicOr(&acc->grid_flags, GF_ITEMS_OVERFLOW);
+        item_cnt[c] = (uint32_t)min(items, (uint64_t)0x7fffffffull);
+        if (n >= 2) {
+            const int64_t l = find_segment_u32(cbase, L, c);
+            atomicAdd(&work[l], (unsigned long long)n * (n - 1) / 2);
+        }
+    }
+}
+
+// Descriptor of every work item: {record offset, records of the cell,
+// layout, ti << 16 | tj} and {local cell, k, 0, 0}.
+__global__ void __launch_bounds__(256) k_batch_item_descs(const uint32_t *__restrict__ item_off,
+                                                          const uint32_t *__restrict__ cell_off, uint32_t C,
+                                                          const uint32_t *__restrict__ cbase, int64_t L,
+                                                          const int32_t *__restrict__ kl, uint64_t cap,
+                                                          uint4 *__restrict__ desc, DevAcc *acc) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        uint32_t q = item_off[c];
+        const uint32_t e = item_off[c + 1];
+        if (q == e) continue;
+        if (e > cap) {
+            atomicOr(&acc->eval_status, ST_OVERFLOW);
+            continue;
+        }
+        const int64_t l = find_segment_u32(cbase, L, c);
+        const uint32_t base = cell_off[c], n = cell_off[c + 1] - base;
+        const uint32_t T = (n + TILE - 1) / TILE;
+        const uint4 hi = make_uint4(c - cbase[l], (uint32_t)kl[l], 0u, 0u);
+        for (uint32_t tj = 0; tj < T && q < e; ++tj)
+            for (uint32_t ti = 0; ti <= tj && q < e; ++ti, ++q) {
+                desc[2 * (uint64_t)q] = make_uint4(base, n, (uint32_t)l, (ti << 16) | tj);
+                desc[2 * (uint64_t)q + 1] = hi;
+            }
+    }
+}
+
+// a4 over all layouts.
+__global__ void __launch_bounds__(256) k_batch_grid_fill(const SegRec *__restrict__ seg,
+                                                         const int32_t *__restrict__ seg_eid,
+                                                         const uint32_t *__restrict__ seg_theta,
+                                                         const uint32_t *__restrict__ seg_layout,
+                                                         const DevAcc *__restrict__ acc, const int32_t *__restrict__ kl,
+                                                         const uint32_t *__restrict__ cbase,
+                                                         const uint32_t *__restrict__ cell_off,
+                                                         uint32_t *__restrict__ cell_fill, uint64_t cap,
+                                                         GridRec *__restrict__ rec, uint32_t *status) {
+    const int64_t n = acc->n_seg;
+    if (acc->records > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_OVERFLOW);
+        return;
+    }
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool ok = i < n;
+        const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
+        const int32_t eid = ok ? seg_eid[i] : 0;
+        const uint32_t th = ok ? seg_theta[i] : 0u;
+        const uint32_t l = ok ? seg_layout[i] : 0u;
+        const int k = ok ? kl[l] : 16;
+        const uint32_t cb = ok ? cbase[l] : 0u;
+        warp_for_each_cell(r, eid, th, ok, k, cb, [&](const int (&ids)[2], int nc, SegRec q, int32_t qe, uint32_t qt) {
+            const uint32_t s0 = atomicAdd(&cell_fill[ids[0]], 1u);
+            const uint32_t s1 = nc > 1 ? atomicAdd(&cell_fill[ids[1]], 1u) : 0u;
+            const uint32_t o0 = cell_off[ids[0]];
+            const uint32_t o1 = nc > 1 ? cell_off[ids[1]] : 0u;
+            GridRec g;
+            g.s = q;
+            g.x = make_uint4((uint32_t)qe, qt, 0u, 0u);
+            rec[o0 + s0] = g;
+            if (nc > 1) rec[o1 + s1] = g;
+        });
+    }
+}
+
+// a6 over all layouts: persistent; warp w takes the contiguous run of items
+// [w * chunk, (w + 1) * chunk) and writes one partial per item.  Does
+// nothing when the records or work items of this evaluation outgrew their
+// buffers (the scatter and the descriptors were not written; the host
+// re-plans on the overflow bit).
+__global__ void __launch_bounds__(BP_WARPS * 32, 4) k_batch_grid_pairs(const GridRec *__restrict__ rec,
+                                                                       const uint4 *__restrict__ desc,
+                                                                       const uint32_t *__restrict__ n_items_p,
+                                                                       const DevAcc *__restrict__ acc, uint64_t rec_cap,
+                                                                       uint64_t cap, uint32_t ideal,
+                                                                       ItemPart *__restrict__ part) {
+    __shared__ GSeg cs[BP_WARPS][TILE];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (acc->records > rec_cap || (uint64_t)*n_items_p > cap) return;
+    const uint64_t n_items = *n_items_p;
+    const uint64_t warps = (uint64_t)gridDim.x * BP_WARPS;
+    const uint64_t chunk = (n_items + warps - 1) / warps;
+    const uint64_t w = (uint64_t)blockIdx.x * BP_WARPS + wid;
+    const uint64_t i0 = w * chunk, i1 = min(n_items, i0 + chunk);
+    for (uint64_t it = i0; it < i1; ++it) {
+        const uint4 d0 = desc[2 * it], d1 = desc[2 * it + 1];
+        const int k = (int)d1.y, G = 65536 >> k;
+        const int cell = (int)d1.x;
+        PairCounts pc;
+        grid_item<false>(rec + d0.x, (int)d0.y, (int)(d0.w >> 16), (int)(d0.w & 0xffffu), (cell % G) << k,
+                         (cell / G) << k, k, cs[wid], ideal, pc, PerEdge{});
+        const uint32_t p = warp_sum<uint32_t>(pc.proper), t = warp_sum<uint32_t>(pc.touching);
+        const uint32_t c = warp_sum<uint32_t>(pc.collinear);
+        const uint64_t dv = warp_sum<uint64_t>(pc.dev);
+        if (lane == 0) {
+            ItemPart ip;
+            ip.proper = p; ip.touching = t; ip.collinear = c; ip.pad = 0; ip.dev = dv;
+            part[it] = ip;
+        }
+    }
+}
+
+// Per layout: the crossing partials of its items in a fixed order, plus the
+// occlusion count, into the result; metrics not evaluated get their defaults.
+__global__ void __launch_bounds__(256) k_batch_finalize(const ItemPart *__restrict__ part,
+                                                        const uint32_t *__restrict__ item_off,
+                                                        const uint32_t *__restrict__ cell_off,
+                                                        const uint32_t *__restrict__ cbase, const int32_t *__restrict__ kl,
+                                                        const unsigned long long *__restrict__ work,
+                                                        const uint64_t *__restrict__ occl, int64_t L, uint32_t metrics,
+                                                        double ideal, int64_t d, uint64_t cap,
+                                                        gr_result *__restrict__ res) {
+    __shared__ uint64_t sh[32];
+    for (int64_t l = blockIdx.x; l < L; l += gridDim.x) {
+        uint64_t p = 0, t = 0, c = 0, dv = 0;
+        if (metrics & GR_METRIC_CROSSINGS) {
+            const uint64_t a = min((uint64_t)item_off[cbase[l]], cap), b = min((uint64_t)item_off[cbase[l + 1]], cap);
+            for (uint64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+                const ItemPart q = part[i];
+                p += q.proper; t += q.touching; c += q.collinear; dv += q.dev;
+            }
+        }
+        p = block_sum<uint64_t>(p, sh);
+        t = block_sum<uint64_t>(t, sh);
+        c = block_sum<uint64_t>(c, sh);
+        dv = block_sum<uint64_t>(dv, sh);
+        if (threadIdx.x != 0) continue;
+        gr_result &r = res[l];
+        r.metrics = metrics;
+        if (metrics & GR_METRIC_CROSSINGS) {
+            r.crossing_path = GR_PATH_GRID;
+            r.cell_log2 = kl[l];
+            const uint64_t ec = p + t;
+            r.crossing.c.crossings = (int64_t)ec;
+            r.crossing.c.proper = (int64_t)p;
+            r.crossing.c.touching = (int64_t)t;
+            r.crossing.c.collinear_overlaps = (int64_t)c;
+            r.crossing.c.pairs_tested = (int64_t)work[l];
+            const double dev = (double)dv * kAngleUnit;
+            r.crossing.angle_dev_sum = dev;
+            r.crossing.ideal_rad = ideal;
+            r.crossing.E_ca = ec > 0 ? 1.0 - dev / (ideal * (double)ec) : 1.0;
+            r.grid_records = (int64_t)(cell_off[cbase[l + 1]] - cell_off[cbase[l]]);
+        } else {
+            const int64_t z = r.crossing.c.zero_length_edges;
+            memset(&r.crossing, 0, sizeof(r.crossing));
+            r.crossing.c.zero_length_edges = z;
+            r.crossing.E_ca = 1.0;
+            r.crossing_path = 0;
+            r.cell_log2 = 0;
+            r.grid_records = 0;
+        }
+        if (metrics & GR_METRIC_OCCLUSION) {
+            r.occlusion_pairs = (int64_t)occl[l];
+            r.occlusion_path = GR_PATH_GRID;
+        } else {
+            r.occlusion_pairs = 0;
+            r.occlusion_path = 0;
+        }
+        r.occlusion_d = d;
+        if (!(metrics & GR_METRIC_MIN_ANGLE)) {
+            r.min_angle.M_a = 1.0;
+            r.min_angle.sum_d = 0.0;
+            r.min_angle.n_vertices_counted = 0;
+        }
+        if (!(metrics & GR_METRIC_EDGE_LENGTH)) r.M_l = 0.0;
+    }
+}
+
+thread_local std::string g_batch_err;
+
+}  // namespace
+
+struct gr_batch {
+    int64_t L = 0, V = 0, E = 0;
+    cudaStream_t stream = nullptr;  // the caller's stream (may be the legacy default stream)
+    cudaStream_t cap = nullptr;     // the batch's own stream: evaluations are captured and replayed here
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr;
+    int64_t graph_kernels = 0;      // kernels per replay (for the launch counter)
+    gr_options opt{};
+    Buffers b;
+    uint32_t *seg_layout = nullptr;
+    int64_t *d_voff = nullptr, *d_eoff = nullptr;
+    std::vector<int64_t> v_off, e_off;
+    gr_result *d_res = nullptr, *h_res = nullptr;
+    DevAcc *h_acc = nullptr;
+    // crossing plan
+    std::vector<uint64_t> nseg_l, l1_l;
+    std::vector<int32_t> k_l;
+    int32_t *d_k = nullptr;
+    uint32_t *d_cbase = nullptr;
+    uint32_t C = 0, C_cap = 0;
+    int delta = 0;
+    unsigned long long *d_nseg = nullptr, *d_l1 = nullptr, *d_work = nullptr;
+    uint32_t *cell_off = nullptr, *item_off = nullptr, *cell_fill = nullptr;
+    GridRec *rec = nullptr;
+    uint64_t rec_cap = 0;
+    uint4 *desc = nullptr;
+    ItemPart *parts = nullptr;
+    uint64_t items_cap = 0;
+    // occlusion plan (per d)
+    int64_t plan_d = -1;
+    int32_t *d_ko = nullptr;
+    uint32_t *d_obase = nullptr;
+    uint32_t OC = 0, OC_cap = 0;
+    uint32_t *ocell_off = nullptr, *ocell_fill = nullptr, *opts = nullptr, *olay = nullptr;
+    uint64_t *occl = nullptr;
+    // captured evaluation
+    cudaGraphExec_t exec = nullptr;
+    uint32_t g_metrics = 0, g_ideal = 0;
+    int64_t g_d = -1;
+};
+
+namespace {
+
+gr_status bfail(gr_status st, const std::string &msg) {
+    set_last_error(msg.c_str());
+    return st;
+}
+
+gr_status bcuda(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return bfail(e == cudaErrorMemoryAllocation ? GR_ENOMEM : GR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define B_CU(call)                                        \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return bcuda(e_, #call);   \
+    } while (0)
+
+template <typename T>
+gr_status balloc(T **p, size_t n) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return bcuda(e, "cudaMalloc");
+    }
+    return GR_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+BatchView view(const gr_batch *B) {
+    BatchView v;
+    v.L = B->L;
+    v.v_off = B->d_voff;
+    v.e_off = B->d_eoff;
+    v.res = B->d_res;
+    return v;
+}
+
+void drop_graph(gr_batch *B) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+}
+
+void free_batch(gr_batch *B) {
+    if (!B) return;
+    drop_graph(B);
+    Buffers &b = B->b;
+    void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.deg, b.deg_fill, b.dirs,
+                    b.scan_tmp, b.scan_tmp_side, B->seg_layout, B->d_voff, B->d_eoff, B->d_res, B->d_k, B->d_cbase,
+                    B->d_nseg, B->d_l1, B->d_work, B->cell_off, B->item_off, B->cell_fill, B->rec, B->desc,
+                    B->parts, B->d_ko, B->d_obase, B->ocell_off, B->ocell_fill, B->opts, B->olay, B->occl};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (B->h_res) cudaFreeHost(B->h_res);
+    if (B->h_acc) cudaFreeHost(B->h_acc);
+    if (B->ev_in) cudaEventDestroy(B->ev_in);
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+    if (B->ev_join) cudaEventDestroy(B->ev_join);
+    if (B->side) cudaStreamDestroy(B->side);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    delete B;
+}
+
+// Cell size of each layout: the k minimising 24 R + 3 R^2 / (2 C) + 2 C with
+// R = n + L1 / 2^k records and C = (2^16 / 2^k)^2 cells (the same model as a
+// single layout; ties go to the coarser grid), shifted by the autotuned
+// offset `delta`.
+void plan_cells(gr_batch *B) {
+    B->k_l.assign(B->L, 16);
+    uint64_t C = 0;
+    for (int64_t l = 0; l < B->L; ++l) {
+        const double n = (double)B->nseg_l[l], l1 = (double)B->l1_l[l];
+        int best = 16;
+        double bestc = 1e300;
+        for (int k = 16; k >= 6; --k) {
+            const double R = n + l1 / double(1 << k);
+            const double Cl = double(65536 >> k) * double(65536 >> k);
+            const double cost = 24.0 * R + 3.0 * R * R / (2.0 * Cl) + 2.0 * Cl;
+            if (cost < bestc) { bestc = cost; best = k; }
+        }
+        B->k_l[l] = std::min(16, std::max(6, best + B->delta));
+        C += (uint64_t)(65536 >> B->k_l[l]) * (uint64_t)(65536 >> B->k_l[l]);
+    }
+    // keep the scan within its 2^26-entry limit: coarsen the finest grids
+    while (C > (uint64_t(1) << 26)) {
+        int64_t arg = 0;
+        for (int64_t l = 1; l < B->L; ++l)
+            if (B->k_l[l] < B->k_l[arg]) arg = l;
+        const uint64_t before = (uint64_t)(65536 >> B->k_l[arg]) * (uint64_t)(65536 >> B->k_l[arg]);
+        B->k_l[arg] += 1;
+        C -= before - (uint64_t)(65536 >> B->k_l[arg]) * (uint64_t)(65536 >> B->k_l[arg]);
+    }
+    B->C = (uint32_t)C;
+}
+
+gr_status upload_cells(gr_batch *B) {
+    std::vector<uint32_t> cb(B->L + 1, 0);
+    for (int64_t l = 0; l < B->L; ++l) cb[l + 1] = cb[l] + (uint32_t)((65536 >> B->k_l[l]) * (65536 >> B->k_l[l]));
+    B_CU(cudaMemcpy(B->d_k, B->k_l.data(), sizeof(int32_t) * B->L, cudaMemcpyHostToDevice));
+    B_CU(cudaMemcpy(B->d_cbase, cb.data(), sizeof(uint32_t) * (B->L + 1), cudaMemcpyHostToDevice));
+    gr_status st;
+    if (B->C_cap < B->C) {
+        if ((st = balloc(&B->cell_off, (size_t)B->C + 1)) != GR_OK) return st;
+        if ((st = balloc(&B->item_off, (size_t)B->C + 1)) != GR_OK) return st;
+        if ((st = balloc(&B->cell_fill, (size_t)B->C)) != GR_OK) return st;
+        B->C_cap = B->C;
+    }
+    drop_graph(B);
+    return GR_OK;
+}
+
+// The crossing binning (a2, a3) of all layouts.
+void enqueue_cross_count(gr_batch *B, cudaStream_t s) {
+    Buffers &b = B->b;
+    cudaMemsetAsync(B->cell_off, 0, sizeof(uint32_t) * ((size_t)B->C + 1), s);
+    cudaMemsetAsync(B->d_work, 0, sizeof(unsigned long long) * B->L, s);
+    count_launches(3);
+    k_batch_grid_count<<<grid_for(B->E, 256, 152 * 16), 256, 0, s>>>(b.seg, B->seg_layout, b.acc, B->d_k,
+                                                                     B->d_cbase, B->cell_off);
+    launch_scan_u32(B->cell_off, B->cell_off, B->C, b.scan_tmp, &b.acc->records, &b.acc->eval_status, s);
+    k_batch_cell_items<<<grid_for(B->C, 256, 152 * 8), 256, 0, s>>>(B->cell_off, B->C, B->d_cbase, B->L, B->item_off,
+                                                                    B->d_work, b.acc);
+    launch_scan_u32(B->item_off, B->item_off, B->C, b.scan_tmp, &b.acc->grid_items, &b.acc->eval_status, s);
+    k_batch_item_descs<<<grid_for(B->C, 256, 152 * 8), 256, 0, s>>>(B->item_off, B->cell_off, B->C, B->d_cbase, B->L,
+                                                                    B->d_k, B->items_cap, B->desc, b.acc);
+}
+
+// Scatter (a4) and the per-cell pair kernel (a6) of all layouts.
+void enqueue_cross_pairs(gr_batch *B, uint32_t ideal_u, cudaStream_t s) {
+    Buffers &b = B->b;
+    cudaMemsetAsync(B->cell_fill, 0, sizeof(uint32_t) * B->C, s);
+    count_launches(2);
+    k_batch_grid_fill<<<grid_for(B->E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, B->seg_layout,
+                                                                    b.acc, B->d_k, B->d_cbase, B->cell_off,
+                                                                    B->cell_fill, B->rec_cap, B->rec,
+                                                                    &b.acc->eval_status);
+    k_batch_grid_pairs<<<152 * 4, BP_WARPS * 32, 0, s>>>(B->rec, B->desc, B->item_off + B->C, b.acc, B->rec_cap,
+                                                         B->items_cap, ideal_u, B->parts);
+}
+
+// Grows the record and work-item buffers to the current sizes (read back).
+gr_status size_cross_buffers(gr_batch *B, cudaStream_t s) {
+    B->items_cap = 0;  // descriptors are not written while sizing
+    enqueue_cross_count(B, s);
+    B_CU(cudaGetLastError());
+    B_CU(cudaMemcpyAsync(B->h_acc, B->b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+    B_CU(cudaStreamSynchronize(s));
+    const uint64_t R = B->h_acc->records, items = B->h_acc->grid_items;
+    if (B->h_acc->grid_flags & GF_ITEMS_OVERFLOW)
+        return bfail(GR_ENOTSUP, "a layout has a grid cell with more than 2^31 tile pairs");
+    gr_status st;
+    if (B->rec_cap < R || !B->rec) {
+        const uint64_t cap = R + R / 4 + 4096;
+        if ((st = balloc(&B->rec, (size_t)cap)) != GR_OK) return st;
+        B->rec_cap = cap;
+    }
+    const uint64_t icap = items + items / 4 + 4096;
+    if ((st = balloc(&B->desc, 2 * (size_t)icap)) != GR_OK) return st;
+    if ((st = balloc(&B->parts, (size_t)icap)) != GR_OK) return st;
+    B->items_cap = icap;
+    B_CU(cudaMemsetAsync((char *)B->b.acc + offsetof(DevAcc, eval_status), 0,
+                         sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
+    drop_graph(B);
+    return GR_OK;
+}
+
+// Occlusion grids for diameter d: cell side 2^ko_l >= d and about V_l / 2 cells.
+gr_status plan_occlusion(gr_batch *B, int64_t d) {
+    if (B->plan_d == d) return GR_OK;
+    std::vector<int32_t> ko(B->L);
+    std::vector<uint32_t> ob(B->L + 1, 0);
+    int kd = 6;
+    while (kd < 16 && (int64_t(1) << kd) < d) ++kd;
+    uint64_t OC = 0;
+    for (int64_t l = 0; l < B->L; ++l) {
+        const double Vl = (double)(B->v_off[l + 1] - B->v_off[l]);
+        int kv = 16;
+        if (Vl >= 2) kv = (int)std::lround(std::log2(65536.0 / std::sqrt(Vl / 2.0)));
+        ko[l] = std::min(16, std::max(kd, std::max(6, kv)));
+        OC += (uint64_t)(65536 >> ko[l]) * (uint64_t)(65536 >> ko[l]);
+        ob[l + 1] = (uint32_t)OC;
+    }
+    if (OC > (uint64_t(1) << 26)) return bfail(GR_ENOTSUP, "occlusion grids exceed 2^26 cells");
+    gr_status st;
+    B_CU(cudaMemcpy(B->d_ko, ko.data(), sizeof(int32_t) * B->L, cudaMemcpyHostToDevice));
+    B_CU(cudaMemcpy(B->d_obase, ob.data(), sizeof(uint32_t) * (B->L + 1), cudaMemcpyHostToDevice));
+    if (B->OC_cap < OC) {
+        if ((st = balloc(&B->ocell_off, (size_t)OC + 1)) != GR_OK) return st;
+        if ((st = balloc(&B->ocell_fill, (size_t)OC)) != GR_OK) return st;
+        B->OC_cap = (uint32_t)OC;
+    }
+    B->OC = (uint32_t)OC;
+    B->plan_d = d;
+    drop_graph(B);
+    return GR_OK;
+}
+
+// One evaluation, stream-ordered (also what the CUDA graph captures).
+void enqueue_evaluate(gr_batch *B, uint32_t metrics, double ideal, uint32_t ideal_u, int64_t d) {
+    cudaStream_t s = B->cap, t = B->side;
+    Buffers &b = B->b;
+    const BatchView bv = view(B);
+    cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0, sizeof(DevAcc) - offsetof(DevAcc, eval_status), s);
+    cudaEventRecord(B->ev_fork, s);
+    cudaStreamWaitEvent(t, B->ev_fork, 0);
+    if (metrics & GR_METRIC_EDGE_LENGTH) launch_batch_elv(b, bv, t);
+    if (metrics & GR_METRIC_MIN_ANGLE) launch_batch_min_angle(b, bv, B->V, B->E, t);
+    if (metrics & GR_METRIC_OCCLUSION)
+        launch_batch_occlusion(b, bv, B->V, B->d_ko, B->d_obase, B->OC, B->ocell_off, B->ocell_fill, B->opts, B->olay, d,
+                               B->occl, t);
+    cudaEventRecord(B->ev_join, t);
+    if (metrics & GR_METRIC_CROSSINGS) {
+        enqueue_cross_count(B, s);
+        enqueue_cross_pairs(B, ideal_u, s);
+    }
+    cudaStreamWaitEvent(s, B->ev_join, 0);
+    count_launches(1);
+    k_batch_finalize<<<grid_for(B->L, 1, 152 * 16), 256, 0, s>>>(B->parts, B->item_off, B->cell_off, B->d_cbase, B->d_k,
+                                                                 B->d_work, B->occl, B->L, metrics, ideal, d,
+                                                                 B->items_cap, B->d_res);
+}
+
+gr_status enqueue_inputs(gr_batch *B, const void *xy, const int32_t *edges) {
+    cudaStream_t s = B->stream;
+    Buffers &b = B->b;
+    B_CU(cudaMemsetAsync(b.acc, 0, offsetof(DevAcc, eval_status), s));
+    if (B->V > 0) {
+        const cudaMemcpyKind k = is_device_ptr(xy) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        B_CU(cudaMemcpyAsync(b.xy, xy, sizeof(int32_t) * 2 * B->V, k, s));
+    }
+    if (B->E > 0 && edges) {
+        const cudaMemcpyKind k = is_device_ptr(edges) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        B_CU(cudaMemcpyAsync(b.edges, edges, sizeof(int32_t) * 2 * B->E, k, s));
+    }
+    launch_check_vertices(b.xy, B->V, b, s);
+    if (B->E > 0) {
+        count_launches(1);
+        k_batch_gather<<<grid_for(B->E, 256, 152 * 16), 256, 0, s>>>((const int2 *)b.xy, B->d_voff,
+                                                                     (const int2 *)b.edges, B->d_eoff, B->L, B->E, b.seg,
+                                                                     b.seg_eid, b.seg_theta, B->seg_layout, b.len2,
+                                                                     b.acc);
+    }
+    B_CU(cudaGetLastError());
+    return GR_OK;
+}
+
+gr_status status_error(uint32_t st) {
+    if (st & ST_BAD_ID) return bfail(GR_EINVAL, "vertex id outside its layout or self-loop in the edge list");
+    if (st & ST_BAD_COORD) return bfail(GR_ERANGE, "vertex coordinate outside [0, 65536)");
+    if (st & ST_SCAN_OVERFLOW) return bfail(GR_ENOTSUP, "an offset table exceeded 2^32 entries");
+    return GR_OK;
+}
+
+// Times the crossing pipeline (binning, scatter, pairs) with the current plan.
+gr_status time_crossings(gr_batch *B, float *ms) {
+    cudaEvent_t a, z;
+    B_CU(cudaEventCreate(&a));
+    B_CU(cudaEventCreate(&z));
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(a, B->stream);
+        enqueue_cross_count(B, B->stream);
+        enqueue_cross_pairs(B, 1u << 30, B->stream);
+        cudaEventRecord(z, B->stream);
+        cudaError_t e = cudaEventSynchronize(z);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(z);
+            return bcuda(e, "autotune");
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, z);
+        best = std::min(best, t);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    *ms = best;
+    return GR_OK;
+}
+
+// The autotuner's key: layouts, vertices and edges, each rounded to a power
+// of two, and the device's SM count.
+std::string tune_key(const gr_batch *B) {
+    auto lg = [](int64_t x) { int r = 0; while ((int64_t(1) << r) < x) ++r; return r; };
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    char buf[128];
+    snprintf(buf, sizeof buf, "batch_L%d_V%d_E%d_sm%d", lg(B->L), lg(B->V), lg(B->E), sms);
+    return buf;
+}
+
+bool tune_cache_lookup(const std::string &key, int *delta) {
+    const char *path = getenv("GR_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char k[128];
+    int v;
+    bool found = false;
+    while (fscanf(f, "%127s %d", k, &v) == 2)
+        if (key == k) { *delta = v; found = true; }
+    fclose(f);
+    return found;
+}
+
+void tune_cache_store(const std::string &key, int delta) {
+    const char *path = getenv("GR_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d\n", key.c_str(), delta);
+    fclose(f);
+}
+
+// Picks the global cell-size offset with the fastest crossing pipeline
+// among -1, 0, +1 (or takes it from the tune cache).
+gr_status autotune(gr_batch *B) {
+    const std::string key = tune_key(B);
+    int cached = 0;
+    if (tune_cache_lookup(key, &cached)) {
+        B->delta = cached;
+        plan_cells(B);
+        gr_status st = upload_cells(B);
+        return st != GR_OK ? st : size_cross_buffers(B, B->stream);
+    }
+    int best_delta = 0;
+    float best = 1e30f;
+    for (int delta : {0, -1, 1}) {
+        B->delta = delta;
+        plan_cells(B);
+        gr_status st = upload_cells(B);
+        if (st == GR_OK) st = size_cross_buffers(B, B->stream);
+        if (st != GR_OK) return st;
+        float ms = 0.f;
+        if ((st = time_crossings(B, &ms)) != GR_OK) return st;
+        if (ms < best) { best = ms; best_delta = delta; }
+    }
+    B->delta = best_delta;
+    plan_cells(B);
+    gr_status st = upload_cells(B);
+    if (st == GR_OK) st = size_cross_buffers(B, B->stream);
+    if (st == GR_OK) tune_cache_store(key, best_delta);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_off, const int64_t *e_off,
+                          const void *xy, gr_coord_type coord_type, const int32_t *edges, const gr_options *opt,
+                          gr_stream_t stream) {
+    set_last_error("");
+    if (!out || !v_off || !e_off) return bfail(GR_EINVAL, "NULL argument");
+    if (coord_type != GR_COORD_I32) return bfail(GR_ENOTSUP, "only GR_COORD_I32 batches are supported");
+    if (n_layouts < 1 || n_layouts >= (int64_t(1) << 24)) return bfail(GR_EINVAL, "n_layouts must be in [1, 2^24)");
+    std::vector<int64_t> vo(n_layouts + 1), eo(n_layouts + 1);
+    {
+        const cudaMemcpyKind kv = is_device_ptr(v_off) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        const cudaMemcpyKind ke = is_device_ptr(e_off) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        B_CU(cudaMemcpy(vo.data(), v_off, sizeof(int64_t) * (n_layouts + 1), kv));
+        B_CU(cudaMemcpy(eo.data(), e_off, sizeof(int64_t) * (n_layouts + 1), ke));
+    }
+    if (vo[0] != 0 || eo[0] != 0) return bfail(GR_EINVAL, "offsets must start at 0");
+    for (int64_t l = 0; l < n_layouts; ++l)
+        if (vo[l + 1] < vo[l] || eo[l + 1] < eo[l]) return bfail(GR_EINVAL, "offsets must be non-decreasing");
+    const int64_t V = vo[n_layouts], E = eo[n_layouts];
+    if (V >= (int64_t(1) << 31) || E >= (int64_t(1) << 31)) return bfail(GR_EINVAL, "total V and E must be < 2^31");
+    if ((V > 0 && !xy) || (E > 0 && !edges)) return bfail(GR_EINVAL, "NULL input pointer");
+    for (int64_t l = 0; l < n_layouts; ++l)
+        if (eo[l + 1] > eo[l] && vo[l + 1] - vo[l] < 2) return bfail(GR_EINVAL, "a layout with edges needs two vertices");
+
+    gr_batch *B = new gr_batch;
+    B->L = n_layouts;
+    B->V = V;
+    B->E = E;
+    B->v_off = vo;
+    B->e_off = eo;
+    B->stream = (cudaStream_t)stream;
+    if (opt) B->opt = *opt;
+    gr_status st = GR_OK;
+    Buffers &b = B->b;
+#define B_TRY(x)                                 \
+    do {                                         \
+        if ((st = (x)) != GR_OK) {               \
+            free_batch(B);                       \
+            return st;                           \
+        }                                        \
+    } while (0)
+    B_TRY(balloc(&b.xy, 2 * (size_t)V));
+    B_TRY(balloc(&b.edges, 2 * (size_t)E));
+    B_TRY(balloc(&b.seg, (size_t)E));
+    B_TRY(balloc(&b.seg_eid, (size_t)E));
+    B_TRY(balloc(&b.seg_theta, (size_t)E));
+    B_TRY(balloc(&b.len2, (size_t)E));
+    B_TRY(balloc(&b.acc, 1));
+    B_TRY(balloc(&b.deg, (size_t)V + 1));
+    B_TRY(balloc(&b.deg_fill, (size_t)V));
+    B_TRY(balloc(&b.dirs, 2 * (size_t)E));
+    B_TRY(balloc(&b.scan_tmp, (size_t)kScanMaxBlocks));
+    B_TRY(balloc(&b.scan_tmp_side, (size_t)kScanMaxBlocks));
+    B_TRY(balloc(&B->seg_layout, (size_t)E));
+    B_TRY(balloc(&B->d_voff, (size_t)n_layouts + 1));
+    B_TRY(balloc(&B->d_eoff, (size_t)n_layouts + 1));
+    B_TRY(balloc(&B->d_res, (size_t)n_layouts));
+    B_TRY(balloc(&B->d_k, (size_t)n_layouts));
+    B_TRY(balloc(&B->d_cbase, (size_t)n_layouts + 1));
+    B_TRY(balloc(&B->d_nseg, (size_t)n_layouts));
+    B_TRY(balloc(&B->d_l1, (size_t)n_layouts));
+    B_TRY(balloc(&B->d_work, (size_t)n_layouts));
+    B_TRY(balloc(&B->d_ko, (size_t)n_layouts));
+    B_TRY(balloc(&B->d_obase, (size_t)n_layouts + 1));
+    B_TRY(balloc(&B->opts, (size_t)V));
+    B_TRY(balloc(&B->olay, (size_t)V));
+    B_TRY(balloc(&B->occl, (size_t)n_layouts));
+#define B_CU2(call)                                   \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            st = bcuda(e_, #call);                    \
+            free_batch(B);                            \
+            return st;                                \
+        }                                             \
+    } while (0)
+    B_CU2(cudaMallocHost((void **)&B->h_res, sizeof(gr_result) * n_layouts));
+    B_CU2(cudaMallocHost((void **)&B->h_acc, sizeof(DevAcc)));
+    B_CU2(cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking));
+    B_CU2(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+    B_CU2(cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming));
+    B_CU2(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
+    B_CU2(cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming));
+    B_CU2(cudaMemcpy(B->d_voff, vo.data(), sizeof(int64_t) * (n_layouts + 1), cudaMemcpyHostToDevice));
+    B_CU2(cudaMemcpy(B->d_eoff, eo.data(), sizeof(int64_t) * (n_layouts + 1), cudaMemcpyHostToDevice));
+    B_CU2(cudaMemset(B->d_res, 0, sizeof(gr_result) * n_layouts));
+    B_CU2(cudaMemset(b.acc, 0, sizeof(DevAcc)));
+    B_TRY(enqueue_inputs(B, xy, edges));
+    // validation and the per-layout statistics of the plan
+    B_CU2(cudaMemsetAsync(B->d_nseg, 0, sizeof(unsigned long long) * n_layouts, B->stream));
+    B_CU2(cudaMemsetAsync(B->d_l1, 0, sizeof(unsigned long long) * n_layouts, B->stream));
+    if (E > 0) {
+        count_launches(1);
+        k_batch_stats<<<grid_for(E, 256, 152 * 16), 256, 0, B->stream>>>(b.seg, B->seg_layout, b.acc, B->d_nseg,
+                                                                         B->d_l1);
+    }
+    B->nseg_l.assign(n_layouts, 0);
+    B->l1_l.assign(n_layouts, 0);
+    B_CU2(cudaMemcpyAsync(B->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, B->stream));
+    B_CU2(cudaMemcpyAsync(B->nseg_l.data(), B->d_nseg, sizeof(uint64_t) * n_layouts, cudaMemcpyDeviceToHost, B->stream));
+    B_CU2(cudaMemcpyAsync(B->l1_l.data(), B->d_l1, sizeof(uint64_t) * n_layouts, cudaMemcpyDeviceToHost, B->stream));
+    B_CU2(cudaStreamSynchronize(B->stream));
+    B_TRY(status_error(B->h_acc->status));
+    if (B->opt.cell_log2 != 0) {
+        B->delta = B->opt.cell_log2 < 0 ? B->opt.cell_log2 : 0;  // negative values: a fixed offset
+        plan_cells(B);
+        B_TRY(upload_cells(B));
+        B_TRY(size_cross_buffers(B, B->stream));
+    } else {
+        B_TRY(autotune(B));
+    }
+#undef B_TRY
+#undef B_CU2
+    *out = B;
+    return GR_OK;
+}
+
+gr_status gr_batch_update(gr_batch *B, const void *xy, const int32_t *edges) {
+    set_last_error("");
+    if (!B) return bfail(GR_EINVAL, "batch is NULL");
+    if (B->V > 0 && !xy) return bfail(GR_EINVAL, "xy is NULL");
+    return enqueue_inputs(B, xy, edges);
+}
+
+gr_status gr_batch_evaluate(gr_batch *B, uint32_t metrics, const gr_params *params, gr_result *out) {
+    set_last_error("");
+    if (!B || !out) return bfail(GR_EINVAL, "NULL argument");
+    if (metrics & ~GR_METRIC_ALL) return bfail(GR_EINVAL, "unknown metric bits");
+    double ideal = 7.0 * M_PI / 18.0;
+    int64_t d = 0;
+    if (params) {
+        if (params->ideal_rad > 0.0) ideal = params->ideal_rad;
+        d = params->occlusion_d;
+    }
+    if (!(ideal <= M_PI / 2 + 1e-15)) return bfail(GR_EINVAL, "ideal angle must be in (0, pi/2]");
+    if (d < 0) return bfail(GR_EINVAL, "occlusion diameter d must be >= 0");
+    const uint32_t ideal_u = (uint32_t)llrint(ideal / M_PI * 4294967296.0);
+    gr_status st;
+    if ((st = plan_occlusion(B, d)) != GR_OK) return st;
+    cudaStream_t c = B->cap;
+    B_CU(cudaEventRecord(B->ev_in, B->stream));  // inputs enqueued on the caller's stream come first
+    B_CU(cudaStreamWaitEvent(c, B->ev_in, 0));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (!B->exec || B->g_metrics != metrics || B->g_ideal != ideal_u || B->g_d != d) {
+            drop_graph(B);
+            cudaGraph_t graph;
+            const int64_t k0 = gr_kernel_launches();
+            B_CU(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
+            enqueue_evaluate(B, metrics, ideal, ideal_u, d);
+            const cudaError_t ce = cudaStreamEndCapture(c, &graph);
+            B->graph_kernels = gr_kernel_launches() - k0;
+            count_launches(-(int)B->graph_kernels);  // counted when replayed, not when captured
+            if (ce != cudaSuccess) return bcuda(ce, "capturing the batch evaluation");
+            const cudaError_t ie = cudaGraphInstantiate(&B->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                B->exec = nullptr;
+                return bcuda(ie, "instantiating the batch graph");
+            }
+            B->g_metrics = metrics;
+            B->g_ideal = ideal_u;
+            B->g_d = d;
+        }
+        B_CU(cudaGraphLaunch(B->exec, c));
+        count_launches((int)B->graph_kernels);
+        B_CU(cudaMemcpyAsync(B->h_acc, B->b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, c));
+        B_CU(cudaStreamSynchronize(c));
+        if ((st = status_error(B->h_acc->status | B->h_acc->eval_status)) != GR_OK) return st;
+        if ((B->h_acc->eval_status & ST_OVERFLOW) || (B->h_acc->grid_flags & GF_ITEMS_OVERFLOW)) {
+            // the coordinates changed enough that the buffers no longer fit: re-plan
+            if (attempt == 1 || (B->h_acc->grid_flags & GF_ITEMS_OVERFLOW))
+                return bfail(GR_ENOMEM, "batch grid buffers overflowed after re-planning");
+            if ((st = size_cross_buffers(B, c)) != GR_OK) return st;
+            continue;
+        }
+        break;
+    }
+    const cudaMemcpyKind k = is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    B_CU(cudaMemcpyAsync(out, B->d_res, sizeof(gr_result) * B->L, k, c));
+    B_CU(cudaStreamSynchronize(c));
+    return GR_OK;
+}
+
+gr_status gr_batch_destroy(gr_batch *B) {
+    set_last_error("");
+    if (!B) return GR_OK;
+    cudaStreamSynchronize(B->stream);
+    cudaStreamSynchronize(B->cap);
+    free_batch(B);
+    return GR_OK;
+}
+
+}  // extern "C"

@@ -295,6 +295,7 @@ gr_status refresh_stats(gr_layout *L) {
 // owner tests).  Measured on GB300 with the workloads of the benchmark.
 constexpr double kRecordCost = 24.0;
 constexpr double kCellPairCost = 3.0;
+constexpr double kCellCost = 2.0;  // per cell: count, scan, work-item passes
 
 struct CrossPlan {
     bool grid = false;
@@ -304,18 +305,19 @@ struct CrossPlan {
 double est_records(double n, double l1, int k) { return n + l1 / double(1 << k); }
 
 // Chooses the cell size from segment count and total L1 length: records
-// n + L1 / w, and a lower bound R^2 / (2 C) on the candidate pairs (equality
-// for evenly spread records).  Picks all-pairs when even that bound loses.
+// n + L1 / w, a lower bound R^2 / (2 C) on the candidate pairs (equality for
+// evenly spread records) and a per-cell cost; ties go to the coarser grid.
+// Picks all-pairs when even that bound loses.
 CrossPlan plan_crossings(const gr_layout *L, uint64_t n_seg, uint64_t l1) {
     CrossPlan p;
     const double n = (double)n_seg, l = (double)l1;
     const double allpairs = n * (n - 1) / 2;
     int best_k = 8;
     double best = 1e300;
-    for (int k = 6; k <= 14; ++k) {
+    for (int k = 14; k >= 6; --k) {
         const double R = est_records(n, l, k);
         const double C = double(65536 >> k) * double(65536 >> k);
-        const double cost = kRecordCost * R + kCellPairCost * R * R / (2 * C);
+        const double cost = kRecordCost * R + kCellPairCost * R * R / (2 * C) + kCellCost * C;
         if (cost < best) { best = cost; best_k = k; }
     }
     p.k = L->opt.cell_log2 >= 6 && L->opt.cell_log2 <= 16 ? L->opt.cell_log2 : best_k;

@@ -175,8 +175,49 @@ void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal
 // Per-edge output conversion: integer dev sums to radians (double), in place.
 void launch_per_edge_export(uint64_t *dev_fixed, int64_t E, cudaStream_t s);
 
+// ------------------------------------------------------------------ batches
+// Device view of a batch of layouts packed one after another: layout l owns
+// vertices [v_off[l], v_off[l+1]) and edges [e_off[l], e_off[l+1]).
+struct BatchView {
+    int64_t L = 0;
+    const int64_t *v_off = nullptr;  // [L + 1]
+    const int64_t *e_off = nullptr;  // [L + 1]
+    gr_result *res = nullptr;        // [L] per-layout results
+};
+
+// a9 per layout: CSR over all vertices (global ids), then one block per
+// layout; writes res[l].min_angle.
+void launch_batch_min_angle(Buffers &b, const BatchView &bv, int64_t V, int64_t E, cudaStream_t s);
+// a10 per layout: one block per layout, deterministic; writes res[l].M_l and
+// res[l].crossing.c.zero_length_edges.
+void launch_batch_elv(const Buffers &b, const BatchView &bv, cudaStream_t s);
+// a8 per layout: a grid per layout (cell side 2^ko[l] >= d, cell ids from
+// obase[l]); per-layout pair counts into occl[l].
+void launch_batch_occlusion(const Buffers &b, const BatchView &bv, int64_t V, const int32_t *ko,
+                            const uint32_t *obase, uint32_t OC, uint32_t *ocell_off, uint32_t *ocell_fill,
+                            uint32_t *opts, uint32_t *olay, int64_t d, uint64_t *occl, cudaStream_t s);
+
 // ------------------------------------------------------------- device helpers
 #ifdef __CUDACC__
+// Largest i in [0, n) with off[i] <= x (off ascending, off[0] <= x): the
+// segment of a packed array that holds element x; empty segments are skipped.
+__device__ __forceinline__ int64_t find_segment(const int64_t *__restrict__ off, int64_t n, int64_t x) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int64_t find_segment_u32(const uint32_t *__restrict__ off, int64_t n, uint32_t x) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "gr_internal.cuh"
+#include "pair_math.cuh"
 
 namespace gr {
 
@@ -21,15 +22,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // checks them, stores the exact squared length of every edge and appends the
 // non-zero-length ones to the compacted segment array (warp-aggregated slot
 // reservation; the order of the compacted array does not affect any result).
-// Direction of the line through a segment with vector (dx, dy), as an angle
-// in [0, pi) in units of pi / 2^32 (FP64 atan2, rounded to the nearest unit).
-__device__ __forceinline__ uint32_t line_direction(int dx, int dy) {
-    double t = atan2((double)dy, (double)dx);  // (-pi, pi]
-    if (t < 0.0) t += 3.14159265358979323846;
-    const double u = rint(t * (4294967296.0 / 3.14159265358979323846));  // [0, 2^32]
-    return (uint32_t)(unsigned long long)u;  // 2^32 (angle pi) wraps to 0
-}
-
 __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int64_t V,
                                                 const int2 *__restrict__ edges, int64_t E,
                                                 SegRec *__restrict__ seg,
@@ -307,6 +299,38 @@ __global__ void k_per_edge_export(uint64_t *dev_fixed, int64_t E) {
     }
 }
 
+// a10 per layout: one block per layout (grid-strided), two passes over the
+// layout's edges in a fixed order; also counts its zero-length edges.
+__global__ void __launch_bounds__(256) k_batch_elv(const int64_t *__restrict__ len2,
+                                                   const int64_t *__restrict__ e_off, int64_t L,
+                                                   gr_result *__restrict__ res) {
+    __shared__ double shd[32];
+    __shared__ uint64_t shu[32];
+    for (int64_t l = blockIdx.x; l < L; l += gridDim.x) {
+        const int64_t e0 = e_off[l], e1 = e_off[l + 1], E = e1 - e0;
+        double sl = 0.0;
+        uint64_t z = 0;
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int64_t q = len2[e];
+            sl += sqrt((double)q);
+            z += q == 0;
+        }
+        sl = block_sum<double>(sl, shd);
+        z = block_sum<uint64_t>(z, shu);
+        const double mu = E > 0 ? sl / (double)E : 0.0;
+        double sv = 0.0;
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const double t = sqrt((double)len2[e]) - mu;
+            sv += t * t;
+        }
+        sv = block_sum<double>(sv, shd);
+        if (threadIdx.x == 0) {
+            res[l].M_l = (E > 1 && mu > 0.0) ? sqrt(sv / ((double)E * mu * mu)) / sqrt((double)E - 1.0) : 0.0;
+            res[l].crossing.c.zero_length_edges = (int64_t)z;
+        }
+    }
+}
+
 int grid_for(int64_t n, int threads, int max_blocks) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -348,6 +372,13 @@ void launch_elv(const Buffers &b, int64_t E, cudaStream_t s) {
     count_launches(2);
     k_elv_sum<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part);
     k_elv_var<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part);
+}
+
+void launch_batch_elv(const Buffers &b, const BatchView &bv, cudaStream_t s) {
+    if (bv.L <= 0) return;
+    count_launches(1);
+    const int blocks = (int)(bv.L < 152 * 16 ? bv.L : 152 * 16);
+    k_batch_elv<<<blocks, 256, 0, s>>>(b.len2, bv.e_off, bv.L, bv.res);
 }
 
 void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal, int64_t d,

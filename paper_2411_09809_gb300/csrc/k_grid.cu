@@ -16,117 +16,13 @@
 // point, which lies on both segments, holds both of them.
 #include <math.h>
 
-#include "gr_internal.cuh"
-#include "pair_math.cuh"
+#include "grid_common.cuh"
 
 namespace gr {
 
 namespace {
 
 constexpr int GP_WARPS = 8;  // warps per block of the pair kernel
-constexpr int TILE = 32;     // segments per tile (one per lane)
-
-// floor(num / den) for 0 <= num < 2^36, 1 <= den < 2^16: an FP32 estimate,
-// then exact integer correction (the estimate is off by at most a few units).
-__device__ __forceinline__ int floordiv_pos(long long num, int den) {
-    int q = (int)__fdividef((float)num, (float)den);
-    long long r = num - (long long)q * den;
-    while (r < 0) { --q; r += den; }
-    while (r >= den) { ++q; r -= den; }
-    return q;
-}
-
-// A segment walked along its major axis: coordinates swapped when |dy| > |dx|
-// (tr), then ordered so that x0 <= x1; afterwards |y1 - y0| <= x1 - x0 and
-// x1 > x0 (zero-length segments never reach the grid).
-struct DdaSeg {
-    int x0, y0, x1, y1;
-    bool tr;
-};
-
-__device__ __forceinline__ DdaSeg dda_norm(SegRec r) {
-    int ax = px(r.x), ay = py(r.x), bx = px(r.y), by = py(r.y);
-    const bool tr = abs(by - ay) > abs(bx - ax);
-    if (tr) {
-        int t = ax; ax = ay; ay = t;
-        t = bx; bx = by; by = t;
-    }
-    if (ax > bx) {
-        int t = ax; ax = bx; bx = t;
-        t = ay; ay = by; by = t;
-    }
-    return DdaSeg{ax, ay, bx, by, tr};
-}
-
-// Minor-axis cell index of the segment at major coordinate X, x0 <= X <= x1:
-// floor(y(X) / 2^k) with y(X) = y0 + (X - x0) (y1 - y0) / (x1 - x0), exact.
-__device__ __forceinline__ int minor_at(const DdaSeg &s, int X, int k) {
-    if (X == s.x0) return s.y0 >> k;
-    if (X == s.x1) return s.y1 >> k;
-    const int dx = s.x1 - s.x0, dy = s.y1 - s.y0;
-    return floordiv_pos((long long)s.y0 * dx + (long long)(X - s.x0) * dy, dx) >> k;
-}
-
-// The cells of major line c: minor indices between those at the line's two
-// ends, closed at both (a superset of the half-open cells the segment meets).
-// Along one line the major coordinate advances by at most w and the slope is
-// at most 1, so the minor index changes by at most one: at most two cells.
-// Writes their ids (cy * G + cx) and returns how many.
-__device__ __forceinline__ int line_cells(const DdaSeg &s, int c, int k, int G, int (&out)[2]) {
-    const int ra = minor_at(s, max(s.x0, c << k), k);
-    const int rb = minor_at(s, min(s.x1, (c + 1) << k), k);
-    const int lo = min(ra, rb);
-    const int n = min(max(ra, rb) - lo + 1, 2);
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int q = lo + i;
-        out[i] = s.tr ? (c * G + q) : (q * G + c);
-    }
-    return n;
-}
-
-constexpr int SHORT_LINES = 2;  // segments spanning more major lines are walked by a warp
-
-// Calls f(ids, n, record, edge id, direction) for the cells of side 2^k that
-// the segment held by this lane (valid if `ok`) meets, a batch of at most two
-// cells at a time (so a callback can issue its atomics before its stores).
-// Segments spanning at most SHORT_LINES major lines are walked by their own
-// lane; longer ones by the whole warp, one line per lane, so that a few long
-// edges do not serialise their warp.  Every lane of the warp must call it.
-// Both DDA passes use it, so they enumerate the same cells.
-template <class F>
-__device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, uint32_t th, bool ok, int k, F &&f) {
-    const int lane = threadIdx.x & 31;
-    const int G = 65536 >> k;
-    const DdaSeg s = dda_norm(r);
-    const int nl = ok ? (s.x1 >> k) - (s.x0 >> k) + 1 : 0;
-    const bool is_long = nl > SHORT_LINES;
-    if (ok && !is_long) {
-        for (int c = s.x0 >> k, e = s.x1 >> k; c <= e; ++c) {
-            int ids[2];
-            const int n = line_cells(s, c, k, G, ids);
-            f(ids, n, r, eid, th);
-        }
-    }
-    unsigned m = __ballot_sync(0xffffffffu, is_long);
-    while (m) {
-        const int src = __ffs(m) - 1;
-        m &= m - 1;
-        SegRec q;
-        q.x = __shfl_sync(0xffffffffu, r.x, src);
-        q.y = __shfl_sync(0xffffffffu, r.y, src);
-        q.z = __shfl_sync(0xffffffffu, r.z, src);
-        q.w = __shfl_sync(0xffffffffu, r.w, src);
-        const int32_t qe = __shfl_sync(0xffffffffu, eid, src);
-        const uint32_t qt = __shfl_sync(0xffffffffu, th, src);
-        const DdaSeg t = dda_norm(q);
-        for (int c = (t.x0 >> k) + lane, e = t.x1 >> k; c <= e; c += 32) {
-            int ids[2];
-            const int n = line_cells(t, c, k, G, ids);
-            f(ids, n, q, qe, qt);
-        }
-    }
-}
 
 // a2 -- per-cell record counts.
 __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ seg,
@@ -137,7 +33,7 @@ __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ s
         const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
         const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
-        warp_for_each_cell(r, 0, 0u, ok, k, [&](const int (&ids)[2], int nc, SegRec, int32_t, uint32_t) {
+        warp_for_each_cell(r, 0, 0u, ok, k, 0u, [&](const int (&ids)[2], int nc, SegRec, int32_t, uint32_t) {
             atomicAdd(&cell_cnt[ids[0]], 1u);
             if (nc > 1) atomicAdd(&cell_cnt[ids[1]], 1u);
         });
@@ -201,7 +97,7 @@ __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ se
         const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
         const int32_t eid = ok ? seg_eid[i] : 0;
         const uint32_t th = ok ? seg_theta[i] : 0u;
-        warp_for_each_cell(r, eid, th, ok, k, [&](const int (&ids)[2], int nc, SegRec q, int32_t qe, uint32_t qt) {
+        warp_for_each_cell(r, eid, th, ok, k, 0u, [&](const int (&ids)[2], int nc, SegRec q, int32_t qe, uint32_t qt) {
             const uint32_t s0 = atomicAdd(&cell_fill[ids[0]], 1u);
             const uint32_t s1 = nc > 1 ? atomicAdd(&cell_fill[ids[1]], 1u) : 0u;
             const uint32_t o0 = cell_off[ids[0]];
@@ -215,119 +111,16 @@ __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ se
     }
 }
 
-// Owner test of an E_c pair in cell-relative integer coordinates (the cell
-// spans [0, w)^2): the intersection point P = a + u t with
-// t = ((c - a) x v) / (u x v) lies in the half-open cell.  Exact in int64
-// (|P_x * den| < 2^51).
-__device__ __forceinline__ bool owns_crossing(int ax, int ay, int ux, int uy, int cx, int cy, int vx, int vy,
-                                              int w) {
-    long long den = (long long)ux * vy - (long long)uy * vx;
-    long long num = (long long)(cx - ax) * vy - (long long)(cy - ay) * vx;
-    if (den < 0) { den = -den; num = -num; }
-    const long long X = (long long)ax * den + (long long)ux * num;
-    const long long Y = (long long)ay * den + (long long)uy * num;
-    const long long W = (long long)w * den;
-    return 0 <= X && X < W && 0 <= Y && Y < W;
-}
-
-// A segment in the coordinates of the cell being processed (origin at the
-// cell's lower-left corner), in the FP32 form the pair test uses.  When
-// |u_x|, |u_y| <= 2^10 and every coordinate is within 2^12 of the origin,
-// u x p - k and all its partial sums are integers of magnitude <= 2^24, so
-// the FP32 evaluation is exact ("exact" below); otherwise (relative
-// coordinates still below 2^16 in magnitude) its error is below 1,792, under
-// the filter bound kOrientFilter.
-struct __align__(16) GSeg {
-    float ax, ay, bx, by;
-    float ux, uy, nk;  // nk = -(u x a), rounded
-    uint32_t th;
-    uint32_t ida, idb;
-    int exact;
-    int32_t eid;
-};
-
-constexpr float kOrientFilter = 4096.f;
-
-__device__ __forceinline__ GSeg make_gseg(const GridRec &g, int x0, int y0) {
-    GSeg r;
-    const int ax = px(g.s.x) - x0, ay = py(g.s.x) - y0, bx = px(g.s.y) - x0, by = py(g.s.y) - y0;
-    const int ux = bx - ax, uy = by - ay;
-    r.ax = (float)ax; r.ay = (float)ay; r.bx = (float)bx; r.by = (float)by;
-    r.ux = (float)ux; r.uy = (float)uy;
-    r.nk = -(float)((long long)ux * ay - (long long)uy * ax);
-    r.th = g.x.y;
-    r.ida = g.s.z; r.idb = g.s.w;
-    r.eid = (int32_t)g.x.x;
-    const int m = max(max(abs(ax), abs(ay)), max(abs(bx), abs(by)));
-    r.exact = (abs(ux) <= 1024 && abs(uy) <= 1024 && m <= 4096) ? 1 : 0;
-    return r;
-}
-
-// Exact int64 classification of a pair whose FP32 orientations were not
-// conclusive, on the absolute coordinates (cell origin x0, y0 added back).
-__device__ __forceinline__ int classify_exact(const GSeg &r, const GSeg &c, int x0, int y0) {
-    const SegRec a = make_uint4(uint32_t((int)r.ax + x0) | (uint32_t((int)r.ay + y0) << 16),
-                                uint32_t((int)r.bx + x0) | (uint32_t((int)r.by + y0) << 16), r.ida, r.idb);
-    const SegRec b = make_uint4(uint32_t((int)c.ax + x0) | (uint32_t((int)c.ay + y0) << 16),
-                                uint32_t((int)c.bx + x0) | (uint32_t((int)c.by + y0) << 16), c.ida, c.idb);
-    return classify_kind(make_row(a, r.th), make_col(b, c.th));
-}
-
-// Owner of a collinear overlap: the cell holding the lexicographically
-// smallest point of the overlap, an endpoint of one of the segments.
-__device__ __forceinline__ bool owns_collinear(const GSeg &r, const GSeg &c, int w) {
-    // compare (x, y) lexicographically on the relative integer coordinates
-    int ex0 = (int)r.ax, ey0 = (int)r.ay, ex1 = (int)r.bx, ey1 = (int)r.by;
-    if (ex1 < ex0 || (ex1 == ex0 && ey1 < ey0)) { int t = ex0; ex0 = ex1; ex1 = t; t = ey0; ey0 = ey1; ey1 = t; }
-    int fx0 = (int)c.ax, fy0 = (int)c.ay, fx1 = (int)c.bx, fy1 = (int)c.by;
-    if (fx1 < fx0 || (fx1 == fx0 && fy1 < fy0)) { int t = fx0; fx0 = fx1; fx1 = t; t = fy0; fy0 = fy1; fy1 = t; }
-    int lx = ex0, ly = ey0;
-    if (fx0 > lx || (fx0 == lx && fy0 > ly)) { lx = fx0; ly = fy0; }
-    return 0 <= lx && lx < w && 0 <= ly && ly < w;
-}
-
-// Owner test with an FP32 fast path.  For two "exact" segments (see GSeg)
-// num = (c - a) x v and den = u x v are exact integers in FP32 (|den| <= 2^21,
-// |num| <= 2^24), t = num / den carries a relative error below 2^-21 and
-// P_x = a_x + u_x t an absolute error below 2^-11 (|u_x t| <= 2^10, |P_x| <
-// 2^13).  P is decided inside or outside the half-open cell [0, w)^2 when it
-// is further than 2^-9 from the cell's border; otherwise, or for segments
-// that are not both exact, the exact int64 test decides.
-__device__ __forceinline__ bool owns_crossing_fast(const GSeg &r, const GSeg &c, int w) {
-    if (r.exact & c.exact) {
-        const float den = r.ux * c.uy - r.uy * c.ux;
-        const float num = (c.ax - r.ax) * c.uy - (c.ay - r.ay) * c.ux;
-        const float t = __fdividef(num, den);
-        const float X = fmaf(r.ux, t, r.ax), Y = fmaf(r.uy, t, r.ay);
-        const float e = 1.0f / 512.0f, fw = (float)w;
-        const bool in = X >= e && X < fw - e && Y >= e && Y < fw - e;
-        const bool out = X < -e || X >= fw + e || Y < -e || Y >= fw + e;
-        if (in) return true;
-        if (out) return false;
-    }
-    const int iax = (int)r.ax, iay = (int)r.ay, icx = (int)c.ax, icy = (int)c.ay;
-    return owns_crossing(iax, iay, (int)r.bx - iax, (int)r.by - iay, icx, icy, (int)c.bx - icx, (int)c.by - icy, w);
-}
-
-// a6 -- one warp per work item (cell, row tile ti, column tile tj), items in a
-// warp-strided static order.  Off-diagonal items test all rows x columns;
-// diagonal items use a rotation schedule (round q pairs lane i with
-// (i + q) mod m) so that every lane has work in every round.  Orientations
-// are evaluated in FP32 in the cell's coordinates: exact for pairs of short
-// segments near the cell, filtered for the rest.  The rounds only record, per
-// lane, bitmasks of the columns that are E_c candidates, collinear candidates
-// or inconclusive; each lane then settles its own bits (exact int64 for the
-// inconclusive ones) and applies the owner rules: a pair in E_c counts only
-// if this cell owns its intersection point, a collinear overlap only if this
-// cell owns the lexicographically smallest point of the overlap.
+// a6 -- one warp per work item (cell, row tile, column tile); items in a
+// warp-strided static order, the next item's descriptor prefetched.
 template <bool PER_EDGE>
 __global__ void __launch_bounds__(GP_WARPS * 32, 4) k_grid_pairs(const GridRec *__restrict__ rec,
                                                                  const uint4 *__restrict__ descs, uint32_t n_items,
                                                                  int k, DevAcc *acc, uint32_t ideal, PerEdge pe) {
     __shared__ GSeg cs[GP_WARPS][TILE];
     __shared__ uint64_t shu[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int G = 65536 >> k, w = 1 << k;
+    const int wid = threadIdx.x >> 5;
+    const int G = 65536 >> k;
     const uint32_t stride = gridDim.x * GP_WARPS;
     PairCounts pc;
     uint32_t it = blockIdx.x * GP_WARPS + wid;
@@ -335,101 +128,9 @@ __global__ void __launch_bounds__(GP_WARPS * 32, 4) k_grid_pairs(const GridRec *
     for (; it < n_items; it += stride) {
         const uint4 d = next;
         if (it + stride < n_items) next = descs[it + stride];  // prefetch the next item
-        const uint32_t base = d.x;
-        const int n = (int)d.y, cell = (int)d.z, ti = (int)(d.w >> 16), tj = (int)(d.w & 0xffffu);
-        const int x0 = (cell % G) << k, y0 = (cell / G) << k;
-        const int mr = min(TILE, n - ti * TILE), mc = min(TILE, n - tj * TILE);
-
-        __syncwarp();
-        if (lane < mc) cs[wid][lane] = make_gseg(rec[base + tj * TILE + lane], x0, y0);
-        GSeg rs;
-        if (lane < mr) rs = make_gseg(rec[base + ti * TILE + lane], x0, y0);
-        __syncwarp();
-        if (lane >= mr) continue;
-
-        uint32_t m_ec = 0, m_prop = 0, m_coll = 0, m_unsure = 0;
-        const bool diag = ti == tj;
-        const int rounds = diag ? mr / 2 : mc;
-        for (int s = 0; s < rounds; ++s) {
-            int jj;
-            if (diag) {
-                const int qq = s + 1;
-                if (2 * qq == mr && lane >= mr / 2) continue;
-                jj = lane + qq;
-                if (jj >= mr) jj -= mr;
-            } else {
-                jj = s;
-            }
-            const GSeg c = cs[wid][jj];
-            const float o1 = fmaf(rs.ux, c.ay, fmaf(-rs.uy, c.ax, rs.nk));
-            const float o2 = fmaf(rs.ux, c.by, fmaf(-rs.uy, c.bx, rs.nk));
-            const float o3 = fmaf(c.ux, rs.ay, fmaf(-c.uy, rs.ax, c.nk));
-            const float o4 = fmaf(c.ux, rs.by, fmaf(-c.uy, rs.bx, c.nk));
-            const float mn = fminf(fminf(fabsf(o1), fabsf(o2)), fminf(fabsf(o3), fabsf(o4)));
-            const uint32_t bit = 1u << jj;
-            const bool sure = (rs.exact & c.exact) || mn > kOrientFilter;
-            const bool shared = (rs.ida == c.ida) | (rs.ida == c.idb) | (rs.idb == c.ida) | (rs.idb == c.idb);
-            const float p12 = o1 * o2, p34 = o3 * o4;
-            const bool cand = !shared && p12 <= 0.f && p34 <= 0.f;
-            const bool coll = o1 == 0.f && o2 == 0.f;
-            m_unsure |= sure ? 0u : bit;
-            m_ec |= (sure && cand && !coll) ? bit : 0u;
-            m_prop |= (sure && p12 < 0.f && p34 < 0.f) ? bit : 0u;
-            m_coll |= (sure && cand && coll) ? bit : 0u;
-        }
-        // inconclusive pairs: exact int64
-        while (m_unsure) {
-            const int jj = __ffs(m_unsure) - 1;
-            m_unsure &= m_unsure - 1;
-            const int kind = classify_exact(rs, cs[wid][jj], x0, y0);
-            const uint32_t bit = 1u << jj;
-            if (kind == PAIR_PROPER) { m_ec |= bit; m_prop |= bit; }
-            else if (kind == PAIR_TOUCHING) m_ec |= bit;
-            else if (kind == PAIR_COLLINEAR) m_coll |= bit;
-        }
-        // collinear candidates: the extents must meet, and this cell must own
-        // the smallest point of the overlap (coordinates exact in FP32)
-        while (m_coll) {
-            const int jj = __ffs(m_coll) - 1;
-            m_coll &= m_coll - 1;
-            const GSeg c = cs[wid][jj];
-            const bool ar = rs.ax < rs.bx || (rs.ax == rs.bx && rs.ay <= rs.by);
-            const bool ac = c.ax < c.bx || (c.ax == c.bx && c.ay <= c.by);
-            const float elx = ar ? rs.ax : rs.bx, ely = ar ? rs.ay : rs.by;
-            const float ehx = ar ? rs.bx : rs.ax, ehy = ar ? rs.by : rs.ay;
-            const float flx = ac ? c.ax : c.bx, fly = ac ? c.ay : c.by;
-            const float fhx = ac ? c.bx : c.ax, fhy = ac ? c.by : c.ay;
-            const bool lo_e = elx > flx || (elx == flx && ely >= fly);
-            const float lx = lo_e ? elx : flx, ly = lo_e ? ely : fly;
-            const bool hi_e = ehx < fhx || (ehx == fhx && ehy <= fhy);
-            const float hx = hi_e ? ehx : fhx, hy = hi_e ? ehy : fhy;
-            if (!(lx < hx || (lx == hx && ly <= hy))) continue;
-            if (!owns_collinear(rs, c, w)) continue;
-            ++pc.collinear;
-            if (PER_EDGE) {
-                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)rs.eid + 2], 1ull);
-                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)c.eid + 2], 1ull);
-            }
-        }
-        // E_c candidates: owner of the intersection point
-        while (m_ec) {
-            const int jj = __ffs(m_ec) - 1;
-            const uint32_t bit = 1u << jj;
-            m_ec &= m_ec - 1;
-            const GSeg c = cs[wid][jj];
-            if (!owns_crossing_fast(rs, c, w)) continue;
-            const uint32_t qd = dev_term(rs.th, c.th, ideal);
-            const bool prop = (m_prop & bit) != 0;
-            pc.dev += qd;
-            if (prop) ++pc.proper; else ++pc.touching;
-            if (PER_EDGE) {
-                const int slot = prop ? 0 : 1;
-                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)rs.eid + slot], 1ull);
-                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)c.eid + slot], 1ull);
-                atomicAdd((unsigned long long *)&pe.dev[rs.eid], (unsigned long long)qd);
-                atomicAdd((unsigned long long *)&pe.dev[c.eid], (unsigned long long)qd);
-            }
-        }
+        const int cell = (int)d.z;
+        grid_item<PER_EDGE>(rec + d.x, (int)d.y, (int)(d.w >> 16), (int)(d.w & 0xffffu), (cell % G) << k,
+                            (cell / G) << k, k, cs[wid], ideal, pc, pe);
     }
     flush_counts(pc, acc, shu);
 }

@@ -73,6 +73,22 @@ __device__ __forceinline__ int2 ccw_successor(const int2 *__restrict__ d, int k,
     return db;
 }
 
+// Exact order of directions by their angle from the positive x axis, in
+// [0, 2 pi): half plane first, then the sign of the cross product.
+__device__ __forceinline__ bool angle_before(int2 a, int2 b) {
+    const int ha = (a.y < 0 || (a.y == 0 && a.x < 0)) ? 1 : 0;
+    const int hb = (b.y < 0 || (b.y == 0 && b.x < 0)) ? 1 : 0;
+    if (ha != hb) return ha < hb;
+    return cross2(a, b) > 0;
+}
+
+// Candidate (gap g from direction di to bs) replaces the current one when its
+// FP32 gap is smaller, or equal with di earlier in exact angular order: the
+// choice does not depend on the order the directions are stored in.
+__device__ __forceinline__ bool better_gap(float g, int2 di, float gmin, int2 bi) {
+    return g < gmin || (g == gmin && angle_before(di, bi));
+}
+
 __device__ __forceinline__ float ccw_gap_f(int2 a, int2 b) {
     float g = atan2f((float)cross2(a, b), (float)dot2(a, b));
     return g < 0.f ? g + 6.28318530717958647692f : g;
@@ -83,26 +99,22 @@ __device__ __forceinline__ double ccw_gap_d(int2 a, int2 b) {
     return g < 0.0 ? g + 2.0 * M_PI : g;
 }
 
-// One thread per vertex (fixed vertex -> block mapping, so the per-block FP64
-// partial sums are deterministic); vertices of degree > 32 are taken by the
-// whole warp after the per-thread pass.  Gaps are compared in FP32 and the
-// smallest is recomputed in FP64.  d_v = (2 pi / deg - min) / (2 pi / deg)
-// for every vertex with deg >= 2 (deg = 1 has a single 2 pi gap, d_v = 0).
-__global__ void __launch_bounds__(MA_THREADS) k_min_angle(const uint32_t *__restrict__ off,
-                                                          const int2 *__restrict__ dirs, int64_t V,
-                                                          double *__restrict__ part,
-                                                          uint32_t *__restrict__ cnt) {
-    __shared__ double shd[32];
-    __shared__ uint64_t shu[32];
+// The vertices [v0, v1) taken by this block: one thread per vertex, and
+// vertices of degree > 32 by the whole warp after the per-thread pass.  Gaps
+// are compared in FP32 and the smallest is recomputed in FP64.
+// d_v = (2 pi / deg - min) / (2 pi / deg) for every vertex with deg >= 2
+// (deg = 1 has a single 2 pi gap, d_v = 0).  Accumulates sum d_v and the
+// count of such vertices into (dsum, nv), per thread.  `step` is the stride
+// between this block's rounds of MA_THREADS vertices.
+__device__ __forceinline__ void min_angle_range(const uint32_t *__restrict__ off, const int2 *__restrict__ dirs,
+                                                int64_t v0, int64_t v1, int64_t step, double &dsum,
+                                                uint32_t &nv) {
     const int lane = threadIdx.x & 31;
-    const int64_t step = (int64_t)gridDim.x * MA_THREADS;
-    double dsum = 0.0;
-    uint32_t nv = 0;
-    for (int64_t base = (int64_t)blockIdx.x * MA_THREADS; base < V; base += step) {
+    for (int64_t base = v0; base < v1; base += step) {
         const int64_t v = base + threadIdx.x;
         int k = 0;
         uint32_t start = 0;
-        if (v < V) {
+        if (v < v1) {
             start = off[v];
             k = (int)(off[v + 1] - start);
         }
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(MA_THREADS) k_min_angle(const uint32_t *__rest
                 const int2 di = d[i];
                 const int2 db = ccw_successor(d, k, i, di);
                 const float g = ccw_gap_f(di, db);
-                if (g < gmin) { gmin = g; bi = di; bs = db; }
+                if (better_gap(g, di, gmin, bi)) { gmin = g; bi = di; bs = db; }
             }
             const double ideal = 2.0 * M_PI / (double)k;
             dsum += (ideal - ccw_gap_d(bi, bs)) / ideal;
@@ -135,24 +147,62 @@ __global__ void __launch_bounds__(MA_THREADS) k_min_angle(const uint32_t *__rest
                 const int2 di = d[i];
                 const int2 db = ccw_successor(d, hk, i, di);
                 const float g = ccw_gap_f(di, db);
-                if (g < gmin) { gmin = g; bi = di; bs = db; }
+                if (better_gap(g, di, gmin, bi)) { gmin = g; bi = di; bs = db; }
             }
-            float m = gmin;
+            // warp argmin under the same order (lanes without a candidate hold 1e30)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            const unsigned win = __ballot_sync(0xffffffffu, gmin == m);
-            if (lane == __ffs(win) - 1) {
+            for (int o = 16; o > 0; o >>= 1) {
+                const float og = __shfl_xor_sync(0xffffffffu, gmin, o);
+                const int2 obi = make_int2(__shfl_xor_sync(0xffffffffu, bi.x, o), __shfl_xor_sync(0xffffffffu, bi.y, o));
+                const int2 obs = make_int2(__shfl_xor_sync(0xffffffffu, bs.x, o), __shfl_xor_sync(0xffffffffu, bs.y, o));
+                if (better_gap(og, obi, gmin, bi)) { gmin = og; bi = obi; bs = obs; }
+            }
+            if (lane == 0) {
                 const double ideal = 2.0 * M_PI / (double)hk;
                 dsum += (ideal - ccw_gap_d(bi, bs)) / ideal;
                 nv += 1;
             }
         }
     }
+}
+
+// Single layout: fixed vertex -> block mapping, so the per-block FP64
+// partial sums are deterministic.
+__global__ void __launch_bounds__(MA_THREADS) k_min_angle(const uint32_t *__restrict__ off,
+                                                          const int2 *__restrict__ dirs, int64_t V,
+                                                          double *__restrict__ part,
+                                                          uint32_t *__restrict__ cnt) {
+    __shared__ double shd[32];
+    __shared__ uint64_t shu[32];
+    double dsum = 0.0;
+    uint32_t nv = 0;
+    min_angle_range(off, dirs, (int64_t)blockIdx.x * MA_THREADS, V, (int64_t)gridDim.x * MA_THREADS, dsum, nv);
     const double s = block_sum<double>(dsum, shd);
     const uint64_t c = block_sum<uint64_t>(nv, shu);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = s;
         cnt[blockIdx.x] = (uint32_t)c;
+    }
+}
+
+// Batch: one block per layout (grid-strided), M_a written per layout.
+__global__ void __launch_bounds__(MA_THREADS) k_batch_min_angle(const uint32_t *__restrict__ off,
+                                                                const int2 *__restrict__ dirs,
+                                                                const int64_t *__restrict__ v_off, int64_t L,
+                                                                gr_result *__restrict__ res) {
+    __shared__ double shd[32];
+    __shared__ uint64_t shu[32];
+    for (int64_t l = blockIdx.x; l < L; l += gridDim.x) {
+        double dsum = 0.0;
+        uint32_t nv = 0;
+        min_angle_range(off, dirs, v_off[l], v_off[l + 1], MA_THREADS, dsum, nv);
+        const double s = block_sum<double>(dsum, shd);
+        const uint64_t c = block_sum<uint64_t>(nv, shu);
+        if (threadIdx.x == 0) {
+            res[l].min_angle.sum_d = s;
+            res[l].min_angle.n_vertices_counted = (int64_t)c;
+            res[l].min_angle.M_a = c > 0 ? 1.0 - s / (double)c : 1.0;
+        }
     }
 }
 
@@ -172,16 +222,32 @@ int min_angle_blocks(int64_t V) {
     return (int)b;
 }
 
-void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
-    if (V <= 0) return;
+namespace {
+// CSR of the non-zero-length incident directions of every vertex (global ids).
+void build_direction_csr(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
     cudaMemsetAsync(b.deg, 0, sizeof(uint32_t) * (V + 1), s);
     cudaMemsetAsync(b.deg_fill, 0, sizeof(uint32_t) * V, s);
     const int gb = grid_for(E, 256, 152 * 8);
-    count_launches(E > 0 ? 3 : 1);
+    count_launches(E > 0 ? 2 : 0);
     if (E > 0) k_degree<<<gb, 256, 0, s>>>(b.seg, b.acc, b.deg);
     launch_scan_u32(b.deg, b.deg, V, b.scan_tmp_side, &b.acc->scan_sink, &b.acc->eval_status, s);
     if (E > 0) k_fill_dirs<<<gb, 256, 0, s>>>(b.seg, b.acc, b.deg, b.deg_fill, b.dirs);
+}
+}  // namespace
+
+void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
+    if (V <= 0) return;
+    build_direction_csr(b, V, E, s);
+    count_launches(1);
     k_min_angle<<<min_angle_blocks(V), MA_THREADS, 0, s>>>(b.deg, b.dirs, V, b.ma_part, b.ma_cnt);
+}
+
+void launch_batch_min_angle(Buffers &b, const BatchView &bv, int64_t V, int64_t E, cudaStream_t s) {
+    if (V <= 0 || bv.L <= 0) return;
+    build_direction_csr(b, V, E, s);
+    count_launches(1);
+    const int blocks = (int)(bv.L < 152 * 16 ? bv.L : 152 * 16);
+    k_batch_min_angle<<<blocks, MA_THREADS, 0, s>>>(b.deg, b.dirs, bv.v_off, bv.L, bv.res);
 }
 
 }  // namespace gr

@@ -113,6 +113,62 @@ __global__ void __launch_bounds__(256) k_occl_pairs(const uint32_t *__restrict__
     if (threadIdx.x == 0) atomic_add_u64(&acc->occlusion, cnt);
 }
 
+// Batch: vertex v of layout l goes to cell obase[l] + (y >> ko[l]) G_l + (x >> ko[l]).
+__global__ void __launch_bounds__(256) k_batch_occl_count(const int2 *__restrict__ xy, int64_t V,
+                                                          const int64_t *__restrict__ v_off, int64_t L,
+                                                          const int32_t *__restrict__ ko,
+                                                          const uint32_t *__restrict__ obase,
+                                                          uint32_t *__restrict__ cnt) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = find_segment(v_off, L, v);
+        const int k = ko[l], G = 65536 >> k;
+        const int2 p = xy[v];
+        atomicAdd(&cnt[obase[l] + (uint32_t)((p.y >> k) * G + (p.x >> k))], 1u);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_occl_fill(const int2 *__restrict__ xy, int64_t V,
+                                                         const int64_t *__restrict__ v_off, int64_t L,
+                                                         const int32_t *__restrict__ ko,
+                                                         const uint32_t *__restrict__ obase,
+                                                         const uint32_t *__restrict__ off, uint32_t *__restrict__ fill,
+                                                         uint32_t *__restrict__ pts, uint32_t *__restrict__ lay) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = find_segment(v_off, L, v);
+        const int k = ko[l], G = 65536 >> k;
+        const int2 p = xy[v];
+        const uint32_t c = obase[l] + (uint32_t)((p.y >> k) * G + (p.x >> k));
+        const uint32_t pos = off[c] + atomicAdd(&fill[c], 1u);
+        pts[pos] = uint32_t(p.x) | (uint32_t(p.y) << 16);
+        lay[pos] = (uint32_t)l;
+    }
+}
+
+// One thread per vertex in cell order, within its own layout's grid.
+__global__ void __launch_bounds__(256) k_batch_occl_pairs(const uint32_t *__restrict__ pts,
+                                                          const uint32_t *__restrict__ lay,
+                                                          const uint32_t *__restrict__ off, int64_t V,
+                                                          const int32_t *__restrict__ ko,
+                                                          const uint32_t *__restrict__ obase, long long d2,
+                                                          uint64_t *__restrict__ occl) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = pts[i];
+        const uint32_t l = lay[i];
+        const int k = ko[l], G = 65536 >> k;
+        const int cx = px(p) >> k, cy = py(p) >> k;
+        const uint32_t c = obase[l] + (uint32_t)(cy * G + cx);
+        uint32_t cnt = count_close(p, pts, (uint32_t)i + 1, off[c + 1], d2);
+        if (cx + 1 < G) cnt += count_close(p, pts, off[c + 1], off[c + 2], d2);
+        if (cy + 1 < G) {
+            const uint32_t up = c + (uint32_t)G;
+            if (cx > 0) cnt += count_close(p, pts, off[up - 1], off[up], d2);
+            cnt += count_close(p, pts, off[up], off[up + 1], d2);
+            if (cx + 1 < G) cnt += count_close(p, pts, off[up + 1], off[up + 2], d2);
+        }
+        if (cnt) atomicAdd((unsigned long long *)&occl[l], (unsigned long long)cnt);
+    }
+}
+
 int grid_for(int64_t n, int threads, int max_blocks) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -139,6 +195,23 @@ void launch_occlusion_grid_pairs(const Buffers &b, int64_t V, const GridBuffers 
     k_occl_fill<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.xy, V, k, g.ocell_off, g.ocell_fill,
                                                          g.opts);
     k_occl_pairs<<<grid_for(V, 256, 152 * 16), 256, 0, s>>>(g.opts, g.ocell_off, V, k, (long long)d * d, b.acc);
+}
+
+void launch_batch_occlusion(const Buffers &b, const BatchView &bv, int64_t V, const int32_t *ko,
+                            const uint32_t *obase, uint32_t OC, uint32_t *ocell_off, uint32_t *ocell_fill,
+                            uint32_t *opts, uint32_t *olay, int64_t d, uint64_t *occl, cudaStream_t s) {
+    cudaMemsetAsync(occl, 0, sizeof(uint64_t) * bv.L, s);
+    if (V < 2 || d <= 0 || OC == 0) return;
+    cudaMemsetAsync(ocell_off, 0, sizeof(uint32_t) * ((size_t)OC + 1), s);
+    cudaMemsetAsync(ocell_fill, 0, sizeof(uint32_t) * OC, s);
+    const int g = grid_for(V, 256, 152 * 8);
+    count_launches(3);
+    k_batch_occl_count<<<g, 256, 0, s>>>((const int2 *)b.xy, V, bv.v_off, bv.L, ko, obase, ocell_off);
+    launch_scan_u32(ocell_off, ocell_off, OC, b.scan_tmp_side, &b.acc->scan_sink, &b.acc->eval_status, s);
+    k_batch_occl_fill<<<g, 256, 0, s>>>((const int2 *)b.xy, V, bv.v_off, bv.L, ko, obase, ocell_off, ocell_fill, opts,
+                                        olay);
+    k_batch_occl_pairs<<<grid_for(V, 256, 152 * 16), 256, 0, s>>>(opts, olay, ocell_off, V, ko, obase,
+                                                                  (long long)d * d, occl);
 }
 
 void launch_occlusion_allpairs(const Buffers &b, int64_t V, int64_t d, cudaStream_t s) {

@@ -86,6 +86,15 @@ __device__ __forceinline__ int classify_kind(const RowSeg &r, const ColSeg &c) {
     return (o1 != 0 && o2 != 0 && o3 != 0 && o4 != 0) ? PAIR_PROPER : PAIR_TOUCHING;
 }
 
+// Direction of the line through a segment with vector (dx, dy), as an angle
+// in [0, pi) in units of pi / 2^32 (FP64 atan2, rounded to the nearest unit).
+__device__ __forceinline__ uint32_t line_direction(int dx, int dy) {
+    double t = atan2((double)dy, (double)dx);  // (-pi, pi]
+    if (t < 0.0) t += 3.14159265358979323846;
+    const double u = rint(t * (4294967296.0 / 3.14159265358979323846));  // [0, 2^32]
+    return (uint32_t)(unsigned long long)u;  // 2^32 (angle pi) wraps to 0
+}
+
 // |ideal - a_c| in units of pi / 2^32 for lines of directions ta and tb.
 // Symmetric in (ta, tb), so every path that meets a pair derives the same
 // term.  At most 2^31.

@@ -107,6 +107,11 @@ def load() -> ctypes.CDLL:
         "gr_io_bytes": ([P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)], c_int32),
         "gr_crossing_angle_noalloc": ([P, c_int64, P, c_int64, c_double,
                                        ctypes.POINTER(gr_crossing_angle_result), P], c_int32),
+        "gr_batch_create": ([ctypes.POINTER(c_void_p), c_int64, P, P, P, c_int32, P,
+                             ctypes.POINTER(gr_options), P], c_int32),
+        "gr_batch_update": ([P, P, P], c_int32),
+        "gr_batch_evaluate": ([P, c_uint32, ctypes.POINTER(gr_params), P], c_int32),
+        "gr_batch_destroy": ([P], c_int32),
         "gr_last_error": ([], ctypes.c_char_p),
         "gr_version": ([], ctypes.c_char_p),
     }
@@ -273,6 +278,75 @@ def gr_last_error() -> str:
 
 def gr_version() -> str:
     return load().gr_version().decode()
+
+
+def gr_batch_create(n_layouts: int, v_off, e_off, xy, edges, opt: gr_options | None = None,
+                    stream=None) -> c_void_p:
+    vp, vk = _buffer(v_off, "int64")
+    ep_, ek_ = _buffer(e_off, "int64")
+    xp, xk = _buffer(xy, "int32")
+    ep, ek = _buffer(edges, "int32")
+    if stream is None:
+        stream = _stream_of(xy, edges)
+    h = c_void_p()
+    _check(load().gr_batch_create(ctypes.byref(h), int(n_layouts), vp, ep_, xp, GR_COORD_I32, ep,
+                                  ctypes.byref(opt) if opt is not None else None, stream))
+    return h
+
+
+def gr_batch_update(batch, xy, edges=None) -> None:
+    xp, xk = _buffer(xy, "int32")
+    ep, ek = _buffer(edges, "int32")
+    _check(load().gr_batch_update(batch, xp, ep))
+
+
+def gr_batch_evaluate(batch, n_layouts: int, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+                      occlusion_d: int = 0, out=None):
+    """Returns a ctypes array of n_layouts gr_result (or fills `out`, a CUDA
+    buffer of n_layouts * sizeof(gr_result) bytes)."""
+    p = gr_params(float(ideal_rad), int(occlusion_d))
+    if out is None:
+        res = (gr_result * int(n_layouts))()
+        _check(load().gr_batch_evaluate(batch, metrics, ctypes.byref(p), ctypes.cast(res, c_void_p)))
+        return res
+    op, ok = _buffer(out, "int64") if not hasattr(out, "data_ptr") else (out.data_ptr(), out)
+    _check(load().gr_batch_evaluate(batch, metrics, ctypes.byref(p), op))
+    return out
+
+
+def gr_batch_destroy(batch) -> None:
+    _check(load().gr_batch_destroy(batch))
+
+
+class Batch:
+    """Owns a gr_batch handle over packed layouts (see include/gr.h)."""
+
+    def __init__(self, v_off, e_off, xy, edges, opt: gr_options | None = None, stream=None):
+        self.n = int(len(v_off) - 1)
+        self.handle = gr_batch_create(self.n, v_off, e_off, xy, edges, opt, stream)
+
+    def update(self, xy, edges=None) -> None:
+        gr_batch_update(self.handle, xy, edges)
+
+    def evaluate(self, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0, occlusion_d: int = 0):
+        return gr_batch_evaluate(self.handle, self.n, metrics, ideal_rad, occlusion_d)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            gr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- convenience

@@ -62,47 +62,50 @@ def _knn_table(points: np.ndarray, k: int) -> np.ndarray:
 
 
 def knn_edges(points: np.ndarray, ranks: int, count: int) -> np.ndarray:
-    """Rank-ordered, de-duplicated nearest-neighbour edges, cut at `count`."""
+    """Rank-ordered, de-duplicated nearest-neighbour edges, cut at `count`: the
+    candidates (v, rank-r neighbour of v) in rank-major, vertex-id order, each
+    unordered pair kept at its first occurrence."""
     V = points.shape[0]
+    if V < 2 or count <= 0:
+        return np.zeros((0, 2), np.int32)
     table = _knn_table(points, ranks)
-    out = []
-    seen = set()
-    n = 0
-    for r in range(table.shape[1]):
-        col = table[:, r]
-        for v in range(V):
-            u = int(col[v])
-            key = (v, u) if v < u else (u, v)
-            if u == v or key in seen:
-                continue
-            seen.add(key)
-            out.append((v, u))
-            n += 1
-            if n == count:
-                return np.asarray(out, dtype=np.int32).reshape(-1, 2)
-    return np.asarray(out, dtype=np.int32).reshape(-1, 2)
+    R = table.shape[1]
+    a = np.tile(np.arange(V, dtype=np.int64), R)          # rank-major order
+    b = table.T.reshape(-1).astype(np.int64)
+    ok = a != b
+    a, b = a[ok], b[ok]
+    key = np.minimum(a, b) * V + np.maximum(a, b)
+    _, first = np.unique(key, return_index=True)
+    first.sort()
+    first = first[:count]
+    return np.stack([a[first], b[first]], axis=1).astype(np.int32)
 
 
 def add_random_edges(rng: np.random.Generator, V: int, edges: np.ndarray, count: int) -> np.ndarray:
-    """Appends `count` uniform random edges that are not self-loops and not present."""
-    seen = {(int(a), int(b)) if a < b else (int(b), int(a)) for a, b in edges}
-    extra = []
-    while len(extra) < count:
-        need = count - len(extra)
-        cand = rng.integers(0, V, size=(2 * need + 16, 2))
-        for a, b in cand:
-            a = int(a); b = int(b)
-            if a == b:
-                continue
-            key = (a, b) if a < b else (b, a)
-            if key in seen:
-                continue
-            seen.add(key)
-            extra.append((a, b))
-            if len(extra) == count:
-                break
-    ex = np.asarray(extra, dtype=np.int32).reshape(-1, 2)
-    return np.concatenate([edges.astype(np.int32).reshape(-1, 2), ex], axis=0)
+    """Appends `count` uniform random edges that are not self-loops and not present
+    (in either orientation)."""
+    edges = edges.astype(np.int32).reshape(-1, 2)
+    if count <= 0:
+        return edges
+    seen = np.minimum(edges[:, 0], edges[:, 1]).astype(np.int64) * V + np.maximum(edges[:, 0], edges[:, 1])
+    seen = np.unique(seen)
+    out = []
+    have = 0
+    while have < count:
+        need = count - have
+        cand = rng.integers(0, V, size=(2 * need + 16, 2), dtype=np.int64)
+        cand = cand[cand[:, 0] != cand[:, 1]]
+        key = np.minimum(cand[:, 0], cand[:, 1]) * V + np.maximum(cand[:, 0], cand[:, 1])
+        _, first = np.unique(key, return_index=True)
+        first.sort()
+        cand, key = cand[first], key[first]
+        fresh = ~np.isin(key, seen)
+        cand, key = cand[fresh][:need], key[fresh][:need]
+        out.append(cand)
+        seen = np.union1d(seen, key)
+        have += len(cand)
+    ex = np.concatenate(out).astype(np.int32)
+    return np.concatenate([edges, ex], axis=0)
 
 
 def uniform_points(rng: np.random.Generator, V: int) -> np.ndarray:
@@ -165,6 +168,19 @@ def batched_layouts(n_layouts: int = 4096, v_min: int = 50, v_max: int = 20_000,
         e = add_random_edges(rng, V, e, E - e.shape[0])
         out.append(Layout(xy, e, f"batch{i}", {"d": 256, "ideal_deg": 70.0}))
     return out
+
+
+def pack_layouts(layouts: list[Layout]):
+    """(v_off, e_off, xy, edges) of a list of layouts packed one after another;
+    edges keep their layout-local vertex ids."""
+    v_off = np.zeros(len(layouts) + 1, np.int64)
+    e_off = np.zeros(len(layouts) + 1, np.int64)
+    for i, L in enumerate(layouts):
+        v_off[i + 1] = v_off[i] + L.V
+        e_off[i + 1] = e_off[i] + L.E
+    xy = np.concatenate([L.xy for L in layouts]).astype(np.int32) if layouts else np.zeros((0, 2), np.int32)
+    edges = np.concatenate([L.edges for L in layouts]).astype(np.int32) if layouts else np.zeros((0, 2), np.int32)
+    return v_off, e_off, np.ascontiguousarray(xy), np.ascontiguousarray(edges)
 
 
 def differentiable_layout(V: int = 50_000, knn_count: int = 142_500, random_count: int = 7_500,
