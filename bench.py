@@ -44,6 +44,7 @@ WORKLOADS = {
     "large_sparse": ("large_sparse_layout", 64),
     "dense_long_edge": ("dense_long_edge_layout", 256),
     "plain": ("plain_layout", 256),
+    "batched": ("batched_layouts", 256),
 }
 
 
@@ -240,9 +241,155 @@ def cpu_oracle_step(L, d, budget_s: float, rng_seed: int = 0) -> dict:
             "measured_s": t_lin + t_small + t_cross + t_occ}
 
 
+def batched_workload():
+    """The 4,096-layout batch, packed; cached in the temp directory (generation
+    takes about a minute)."""
+    import tempfile
+
+    import numpy as np
+
+    from paper_2411_09809_gb300 import synth
+    path = os.path.join(tempfile.gettempdir(), f"gr_batched_{synth.BASE_SEED + 3}_v2.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return z["v_off"], z["e_off"], z["xy"], z["edges"]
+    v_off, e_off, xy, edges = synth.pack_layouts(synth.batched_layouts())
+    tmp = path + f".{os.getpid()}.npz"
+    np.savez(tmp, v_off=v_off, e_off=e_off, xy=xy, edges=edges)
+    os.replace(tmp, path)
+    return v_off, e_off, xy, edges
+
+
+def run_batched(args, rank, world, local_rank):
+    """Batched workload: one step = gr_batch_update + gr_batch_evaluate (all five
+    metrics of every layout, one CUDA-graph replay).  Reported beside the same
+    layouts evaluated one by one through the single-layout entry points."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_09809_gb300 import build as gr_build, gr
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        if rank == 0:
+            gr_build.build()
+        dist.barrier()
+    else:
+        gr_build.build()
+    gr.load()
+    v_off, e_off, xy, edges = batched_workload()
+    n = len(v_off) - 1
+    d = WORKLOADS["batched"][1]
+    dev = torch.device("cuda", local_rank)
+    dxy = torch.from_numpy(xy).to(dev)
+    ded = torch.from_numpy(edges).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    B = gr.Batch(v_off, e_off, dxy, ded, stream=stream.cuda_stream)
+    create_s = time.perf_counter() - t0
+
+    def step():
+        B.update(dxy)
+        return B.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
+
+    for _ in range(args.warmup):
+        res = step()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = gr.gr_kernel_launches()
+    for i in range(args.steps):
+        flush.fill_(i)
+        starts[i].record(stream)
+        res = step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    launches = gr.gr_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # the same layouts one by one (a fixed sample, scaled to the batch)
+    sample = list(range(0, n, max(1, n // 256)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in sample:
+        with gr.Layout(dxy[v_off[i]:v_off[i + 1]], ded[e_off[i]:e_off[i + 1]]) as one:
+            one.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
+    single_s = (time.perf_counter() - t0) * n / len(sample)
+    B.close()
+    if rank != 0:
+        return
+    pairs = float(sum((e_off[i + 1] - e_off[i]) * (e_off[i + 1] - e_off[i] - 1) / 2 for i in range(n)))
+    value = world * n / (ms / 1e3)
+    line = {
+        "metric": "layouts/s", "value": value, "unit": "layouts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"batched_{n}_layouts", "layouts": n, "V": int(v_off[-1]), "E": int(e_off[-1]),
+                   "occlusion_d": d, "ideal_deg": 70.0,
+                   "metrics": "all five per layout", "inputs": "seeded synthetic (paper_2411_09809_gb300.synth)",
+                   "l2": "256 MiB write between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "resolved_pairs_per_s": world * pairs / (ms / 1e3),
+        "single_layout_loop": {"layouts_per_s": n / single_s, "sample_layouts": len(sample),
+                               "speedup_of_batch": (n / (ms / 1e3)) / (n / single_s)},
+        "create_s": create_s,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_batched(args):
+    """Reference arm of the batched workload: the oracle evaluates all five
+    metrics of a size-stratified sample of the layouts, scaled to the batch."""
+    import oracle
+    v_off, e_off, xy, edges = batched_workload()
+    n = len(v_off) - 1
+    d = WORKLOADS["batched"][1]
+    order = sorted(range(n), key=lambda i: v_off[i + 1] - v_off[i])
+    sample = order[:: max(1, n // 64)]
+    secs = []
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for i in sample:
+            lxy = xy[v_off[i]:v_off[i + 1]]
+            led = edges[e_off[i]:e_off[i + 1]]
+            oracle.crossings(lxy, led)
+            oracle.node_occlusion(lxy, d)
+            oracle.min_angle(lxy, led)
+            oracle.edge_length_variation(lxy, led)
+        secs.append((time.perf_counter() - t0) * n / len(sample))
+    step_s = statistics.mean(secs[args.warmup:])
+    value = n / step_s
+    line = {
+        "impl": "reference", "metric": "layouts/s", "value": value, "unit": "layouts/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"batched_{n}_layouts", "layouts": n, "occlusion_d": d},
+        "cpu_baseline": {"value": value, "unit": "layouts/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{len(sample)} layouts stratified by size, all five metrics, scaled to {n}"},
+        "e2e": {"value": value, "unit": "layouts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle (plain C brute force) on the host cores."""
     if rank != 0:
+        return
+    if args.workload == "batched":
+        run_reference_batched(args)
         return
     L, d = make_workload(args.workload)
     E = L.E
@@ -407,7 +554,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "batched":
+            run_batched(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

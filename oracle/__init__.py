@@ -12,6 +12,11 @@ Each function follows a definition of arXiv 2411.09809:
   crossings_of_edges      -- the same, restricted to sampled edges
   min_angle               -- Sec. 2.1, Algorithm 2
   edge_length_variation   -- Sec. 2.1, Algorithm 3
+and, for FP32 coordinates (the differentiable form; ``xy`` float32 [V, 2]):
+  orient_f32, crossings_f32, min_angle_f32, edge_length_variation_f32 -- the
+      same definitions with exact orientation predicates on FP32 inputs;
+  diff_terms_and_grads    -- E_ca, M_l, M_a and their FP64 gradients with the
+      crossing set and every vertex's smallest gap held fixed.
 """
 from __future__ import annotations
 
@@ -68,6 +73,19 @@ def _load():
         lib.oracle_edge_length_variation.restype = ctypes.c_double
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
+        f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+        fl = ctypes.c_float
+        lib.oracle_orient_f32.argtypes = [fl, fl, fl, fl, fl, fl]
+        lib.oracle_orient_f32.restype = ctypes.c_int
+        lib.oracle_crossings_f32.argtypes = [f32p, i64, i32p, i64, ctypes.c_double, i64p, f64p,
+                                             ctypes.c_void_p, i64]
+        lib.oracle_crossings_f32.restype = ctypes.c_int
+        lib.oracle_min_angle_f32.argtypes = [f32p, i64, i32p, i64, f64p, ctypes.c_void_p]
+        lib.oracle_min_angle_f32.restype = ctypes.c_int
+        lib.oracle_edge_length_variation_f32.argtypes = [f32p, i64, i32p, i64]
+        lib.oracle_edge_length_variation_f32.restype = ctypes.c_double
+        lib.oracle_diff_terms_and_grads.argtypes = [f32p, i64, i32p, i64, ctypes.c_double, f64p, f64p, f64p, f64p]
+        lib.oracle_diff_terms_and_grads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -151,3 +169,58 @@ def min_angle(xy, edges) -> MinAngle:
 def edge_length_variation(xy, edges) -> float:
     xy, edges = _xy(xy), _edges(edges)
     return float(_load().oracle_edge_length_variation(xy, len(xy), edges, len(edges)))
+
+
+# ---------------------------------------------------------------- FP32 form
+
+def _xyf(xy) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(xy, dtype=np.float32).reshape(-1, 2))
+
+
+def orient_f32(a, b, c) -> int:
+    """Exact sign of (b - a) x (c - a) for FP32 points (expansion arithmetic)."""
+    return int(_load().oracle_orient_f32(*(float(np.float32(v)) for v in (*a, *b, *c))))
+
+
+def crossings_f32(xy, edges, ideal: float = DEFAULT_IDEAL, return_pairs: bool = False):
+    """Crossings and crossing angle on FP32 coordinates (exact predicates)."""
+    xy, edges = _xyf(xy), _edges(edges)
+    counts = np.zeros(5, np.int64)
+    fv = np.zeros(2, np.float64)
+    lib = _load()
+    if lib.oracle_crossings_f32(xy, len(xy), edges, len(edges), float(ideal), counts, fv, None, 0) != 0:
+        raise ValueError("ideal angle must be in (0, pi/2]")
+    res = Crossings(int(counts[0]), int(counts[1]), int(counts[2]), int(counts[3]), int(counts[4]),
+                    float(fv[0]), float(fv[1]))
+    if not return_pairs:
+        return res
+    pairs = np.zeros((max(res.crossings, 1), 2), np.int32)
+    lib.oracle_crossings_f32(xy, len(xy), edges, len(edges), float(ideal), counts, fv,
+                             pairs.ctypes.data, res.crossings)
+    return res, pairs[: res.crossings]
+
+
+def min_angle_f32(xy, edges, return_args: bool = False):
+    xy, edges = _xyf(xy), _edges(edges)
+    out = np.zeros(3, np.float64)
+    args = np.zeros((max(len(xy), 1), 2), np.int32)
+    _load().oracle_min_angle_f32(xy, len(xy), edges, len(edges), out, args.ctypes.data)
+    r = MinAngle(float(out[0]), float(out[1]), int(out[2]))
+    return (r, args[: len(xy)]) if return_args else r
+
+
+def edge_length_variation_f32(xy, edges) -> float:
+    xy, edges = _xyf(xy), _edges(edges)
+    return float(_load().oracle_edge_length_variation_f32(xy, len(xy), edges, len(edges)))
+
+
+def diff_terms_and_grads(xy, edges, ideal: float = DEFAULT_IDEAL):
+    """(E_ca, M_l, M_a) and their FP64 gradients [V, 2] each, with the crossing set
+    and the smallest gaps held fixed."""
+    xy, edges = _xyf(xy), _edges(edges)
+    V = len(xy)
+    terms = np.zeros(3, np.float64)
+    g = [np.zeros((max(V, 1), 2), np.float64) for _ in range(3)]
+    if _load().oracle_diff_terms_and_grads(xy, V, edges, len(edges), float(ideal), terms, *g) != 0:
+        raise ValueError("ideal angle must be in (0, pi/2]")
+    return terms, g[0][:V], g[1][:V], g[2][:V]

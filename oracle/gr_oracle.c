@@ -408,3 +408,362 @@ double oracle_edge_length_variation(const int32_t *xy, int64_t V, const int32_t 
 
 /* Threads OpenMP will use (reported beside CPU timings). */
 int oracle_num_threads(void) { return num_threads(); }
+
+/* ======================================================================
+ * FP32 coordinates: the differentiable form (any finite coordinates).
+ *
+ * Orientation signs on FP32 inputs are decided exactly with floating-point
+ * expansion arithmetic (Shewchuk, "Adaptive Precision Floating-Point
+ * Arithmetic and Fast Robust Geometric Predicates", 1997): the inputs are
+ * exact in FP64, every difference is carried as a two-term expansion
+ * (two_diff), every product of terms as a two-term expansion (two_prod with
+ * a fused multiply-add), and the terms are summed into a non-overlapping
+ * expansion (grow_expansion) whose largest component carries the sign.
+ * Parity: pinned by the CPU tests against exact rational arithmetic
+ * (Python fractions) on random FP32 inputs spanning many exponents and on
+ * exactly collinear constructions, and the FP32 metrics against the
+ * integer oracle on coordinates k / 65536 (the same geometry scaled by a
+ * power of two).  The gradients are pinned against central differences of
+ * this FP64 forward.
+ * ====================================================================== */
+
+static void two_sum(double a, double b, double *x, double *y)
+{
+    const double s = a + b;
+    const double bv = s - a;
+    const double av = s - bv;
+    *x = s;
+    *y = (a - av) + (b - bv);
+}
+
+static void two_prod(double a, double b, double *x, double *y)
+{
+    const double p = a * b;
+    *x = p;
+    *y = fma(a, b, -p);
+}
+
+/* h = e + b for a non-overlapping expansion e of n components sorted by
+ * increasing magnitude; zero components are dropped.  Returns |h|. */
+static int grow_expansion(int n, const double *e, double b, double *h)
+{
+    double q = b;
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        double s, t;
+        two_sum(q, e[i], &s, &t);
+        q = s;
+        if (t != 0.0) h[m++] = t;
+    }
+    if (q != 0.0 || m == 0) h[m++] = q;
+    return m;
+}
+
+/* Exact sign of (b - a) x (c - a) for FP32 points. */
+int oracle_orient_f32(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    double u[2][2], w[2][2];  /* u = b - a, w = c - a as two-term expansions (hi, lo) */
+    two_sum((double)bx, -(double)ax, &u[0][0], &u[0][1]);
+    two_sum((double)by, -(double)ay, &u[1][0], &u[1][1]);
+    two_sum((double)cx, -(double)ax, &w[0][0], &w[0][1]);
+    two_sum((double)cy, -(double)ay, &w[1][0], &w[1][1]);
+    /* det = u_x w_y - u_y w_x: 16 two-term products */
+    double e[40], h[40];
+    int n = 0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double p, q;
+            two_prod(u[0][i], w[1][j], &p, &q);
+            n = grow_expansion(n, e, p, h); memcpy(e, h, sizeof(double) * n);
+            n = grow_expansion(n, e, q, h); memcpy(e, h, sizeof(double) * n);
+            two_prod(-u[1][i], w[0][j], &p, &q);
+            n = grow_expansion(n, e, p, h); memcpy(e, h, sizeof(double) * n);
+            n = grow_expansion(n, e, q, h); memcpy(e, h, sizeof(double) * n);
+        }
+    const double top = e[n - 1];
+    return (top > 0) - (top < 0);
+}
+
+static int lex_cmp_f(float ax, float ay, float bx, float by)
+{
+    if (ax != bx) return ax < bx ? -1 : 1;
+    if (ay != by) return ay < by ? -1 : 1;
+    return 0;
+}
+
+/* Classification of an edge pair with FP32 coordinates: the rules of
+ * classify_pair with exact orientations; the angle from FP64 cross and dot
+ * products of the FP64 direction vectors. */
+static int classify_pair_f32(const float *xy, const int32_t *e, const int32_t *f, double *angle)
+{
+    const int32_t ia = e[0], ib = e[1], ic = f[0], id = f[1];
+    if (ia == ic || ia == id || ib == ic || ib == id) return PAIR_NONE;
+    const float ax = xy[2 * ia], ay = xy[2 * ia + 1], bx = xy[2 * ib], by = xy[2 * ib + 1];
+    const float cx = xy[2 * ic], cy = xy[2 * ic + 1], dx = xy[2 * id], dy = xy[2 * id + 1];
+    if ((ax == bx && ay == by) || (cx == dx && cy == dy)) return PAIR_NONE;
+    const int o1 = oracle_orient_f32(ax, ay, bx, by, cx, cy);
+    const int o2 = oracle_orient_f32(ax, ay, bx, by, dx, dy);
+    const int o3 = oracle_orient_f32(cx, cy, dx, dy, ax, ay);
+    const int o4 = oracle_orient_f32(cx, cy, dx, dy, bx, by);
+    if (o1 == 0 && o2 == 0 && o3 == 0 && o4 == 0) {
+        float elx = ax, ely = ay, ehx = bx, ehy = by;
+        if (lex_cmp_f(bx, by, ax, ay) < 0) { elx = bx; ely = by; ehx = ax; ehy = ay; }
+        float flx = cx, fly = cy, fhx = dx, fhy = dy;
+        if (lex_cmp_f(dx, dy, cx, cy) < 0) { flx = dx; fly = dy; fhx = cx; fhy = cy; }
+        float lx = elx, ly = ely;
+        if (lex_cmp_f(flx, fly, lx, ly) > 0) { lx = flx; ly = fly; }
+        float hx = ehx, hy = ehy;
+        if (lex_cmp_f(fhx, fhy, hx, hy) < 0) { hx = fhx; hy = fhy; }
+        return lex_cmp_f(lx, ly, hx, hy) <= 0 ? PAIR_COLLINEAR : PAIR_NONE;
+    }
+    int kind;
+    if (o1 * o2 < 0 && o3 * o4 < 0) kind = PAIR_PROPER;
+    else if (o1 * o2 <= 0 && o3 * o4 <= 0) kind = PAIR_TOUCHING;
+    else return PAIR_NONE;
+    const double ux = (double)bx - ax, uy = (double)by - ay, vx = (double)dx - cx, vy = (double)dy - cy;
+    *angle = atan2(fabs(ux * vy - uy * vx), fabs(ux * vx + uy * vy));
+    return kind;
+}
+
+/* Edge crossings and crossing angle on FP32 coordinates; counts/fvals as
+ * oracle_crossings.  When `pairs` is not NULL, the E_c pairs (edge indices,
+ * e < f) are written to it, at most max_pairs of them. */
+int oracle_crossings_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E, double ideal,
+                         int64_t *counts, double *fvals, int32_t *pairs, int64_t max_pairs)
+{
+    (void)V;
+    if (!(ideal > 0.0 && ideal <= M_PI / 2 + 1e-15)) return -1;
+    int64_t proper = 0, touching = 0, collinear = 0, np = 0, zero = 0;
+    nsum s = {0.0, 0.0};
+    for (int64_t i = 0; i < E; ++i) {
+        for (int64_t j = i + 1; j < E; ++j) {
+            double ac = 0.0;
+            const int k = classify_pair_f32(xy, edges + 2 * i, edges + 2 * j, &ac);
+            if (k == PAIR_COLLINEAR) { ++collinear; continue; }
+            if (k == PAIR_NONE) continue;
+            if (k == PAIR_PROPER) ++proper; else ++touching;
+            nsum_add(&s, fabs(ideal - ac));
+            if (pairs && np < max_pairs) { pairs[2 * np] = (int32_t)i; pairs[2 * np + 1] = (int32_t)j; }
+            ++np;
+        }
+    }
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        if (xy[2 * a] == xy[2 * b] && xy[2 * a + 1] == xy[2 * b + 1]) ++zero;
+    }
+    const int64_t ec = proper + touching;
+    counts[0] = proper; counts[1] = touching; counts[2] = collinear; counts[3] = zero; counts[4] = ec;
+    fvals[0] = nsum_value(&s);
+    fvals[1] = ec > 0 ? 1.0 - fvals[0] / (ideal * (double)ec) : 1.0;
+    return 0;
+}
+
+/* Direction angle of (dx, dy) in [0, 2 pi). */
+static double dir_angle(double dx, double dy)
+{
+    double t = atan2(dy, dx);
+    if (t < 0) t += 2.0 * M_PI;
+    return t;
+}
+
+typedef struct { double ang; int32_t other; int64_t edge; } fdir_t;
+
+static int fdir_cmp(const void *pa, const void *pb)
+{
+    const fdir_t *a = pa, *b = pb;
+    if (a->ang != b->ang) return a->ang < b->ang ? -1 : 1;
+    return (a->edge > b->edge) - (a->edge < b->edge);
+}
+
+/* Minimum angle on FP32 coordinates (Algorithm 2 with FP64 direction angles
+ * sorted, the smallest gap including the wrap-around one).  out as
+ * oracle_min_angle.  When `arg` is not NULL, arg[v] = (i, j): the vertices
+ * at the far ends of the two edges whose directions bound v's smallest gap
+ * (the gap runs counter-clockwise from the edge to i to the edge to j), or
+ * (-1, -1) for vertices with fewer than two edges. */
+int oracle_min_angle_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E, double *out, int32_t *arg)
+{
+    int64_t *deg = calloc((size_t)V + 1, sizeof(int64_t));
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        if (xy[2 * a] == xy[2 * b] && xy[2 * a + 1] == xy[2 * b + 1]) continue;
+        deg[a]++; deg[b]++;
+    }
+    int64_t *off = malloc(sizeof(int64_t) * ((size_t)V + 1));
+    off[0] = 0;
+    for (int64_t v = 0; v < V; ++v) off[v + 1] = off[v] + deg[v];
+    fdir_t *d = malloc(sizeof(fdir_t) * ((size_t)off[V] + 1));
+    int64_t *fill = calloc((size_t)V + 1, sizeof(int64_t));
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        const double dx = (double)xy[2 * b] - xy[2 * a], dy = (double)xy[2 * b + 1] - xy[2 * a + 1];
+        if (dx == 0 && dy == 0) continue;
+        d[off[a] + fill[a]++] = (fdir_t){dir_angle(dx, dy), b, e};
+        d[off[b] + fill[b]++] = (fdir_t){dir_angle(-dx, -dy), a, e};
+    }
+    nsum S = {0.0, 0.0};
+    int64_t n = 0;
+    for (int64_t v = 0; v < V; ++v) {
+        const int64_t k = deg[v];
+        if (arg) { arg[2 * v] = -1; arg[2 * v + 1] = -1; }
+        if (k < 2) continue;
+        fdir_t *q = d + off[v];
+        qsort(q, (size_t)k, sizeof(fdir_t), fdir_cmp);
+        double mn = 2.0 * M_PI - q[k - 1].ang + q[0].ang;
+        int32_t bi = q[k - 1].other, bj = q[0].other;
+        for (int64_t i = 1; i < k; ++i) {
+            const double g = q[i].ang - q[i - 1].ang;
+            if (g < mn) { mn = g; bi = q[i - 1].other; bj = q[i].other; }
+        }
+        const double ideal = 2.0 * M_PI / (double)k;
+        nsum_add(&S, (ideal - mn) / ideal);
+        ++n;
+        if (arg) { arg[2 * v] = bi; arg[2 * v + 1] = bj; }
+    }
+    free(deg); free(off); free(d); free(fill);
+    const double s = nsum_value(&S);
+    out[0] = n > 0 ? 1.0 - s / (double)n : 1.0;
+    out[1] = s;
+    out[2] = (double)n;
+    return 0;
+}
+
+double oracle_edge_length_variation_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E)
+{
+    (void)V;
+    if (E <= 1) return 0.0;
+    nsum sl = {0.0, 0.0};
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        const double dx = (double)xy[2 * b] - xy[2 * a], dy = (double)xy[2 * b + 1] - xy[2 * a + 1];
+        nsum_add(&sl, sqrt(dx * dx + dy * dy));
+    }
+    const double mu = nsum_value(&sl) / (double)E;
+    if (mu == 0.0) return 0.0;
+    nsum ss = {0.0, 0.0};
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+        const double dx = (double)xy[2 * b] - xy[2 * a], dy = (double)xy[2 * b + 1] - xy[2 * a + 1];
+        const double t = sqrt(dx * dx + dy * dy) - mu;
+        nsum_add(&ss, t * t);
+    }
+    return sqrt(nsum_value(&ss) / ((double)E * mu * mu)) / sqrt((double)E - 1.0);
+}
+
+/* Gradient of (theta(q - p)) with respect to q, for the direction angle of
+ * the vector q - p: (-dy, dx) / |q - p|^2; with respect to p it is the
+ * negative. */
+static void dtheta(double dx, double dy, double *gx, double *gy)
+{
+    const double r2 = dx * dx + dy * dy;
+    *gx = -dy / r2;
+    *gy = dx / r2;
+}
+
+/* The three terms of the differentiable loss and their gradients with
+ * respect to every coordinate (FP64), with the crossing set and every
+ * vertex's smallest gap held fixed:
+ *   terms[0] = E_ca, terms[1] = M_l, terms[2] = M_a;
+ *   g_eca, g_ml, g_ma: [V][2] gradients of E_ca, M_l and M_a.
+ * E_ca: a_c is the acute angle between the lines, a function of the two
+ * direction angles; d|ideal - a_c| / d a_c = sign(a_c - ideal) (0 at 0).
+ * M_l: with S = sum (l_e - mu)^2, dM_l / dl_e = M_l ((l_e - mu) / S - 1 / (N mu)).
+ * M_a: d(M_a) / d(min_v) = deg_v / (2 pi n) for each counted vertex; the
+ * gap runs counter-clockwise between two fixed incident edges. */
+int oracle_diff_terms_and_grads(const float *xy, int64_t V, const int32_t *edges, int64_t E, double ideal,
+                                double *terms, double *g_eca, double *g_ml, double *g_ma)
+{
+    memset(g_eca, 0, sizeof(double) * 2 * (size_t)V);
+    memset(g_ml, 0, sizeof(double) * 2 * (size_t)V);
+    memset(g_ma, 0, sizeof(double) * 2 * (size_t)V);
+    /* E_ca and its gradient */
+    int64_t counts[5];
+    double fv[2];
+    if (oracle_crossings_f32(xy, V, edges, E, ideal, counts, fv, NULL, 0) != 0) return -1;
+    const int64_t ec = counts[4];
+    int32_t *pairs = malloc(sizeof(int32_t) * 2 * (size_t)(ec > 0 ? ec : 1));
+    oracle_crossings_f32(xy, V, edges, E, ideal, counts, fv, pairs, ec);
+    terms[0] = fv[1];
+    for (int64_t p = 0; p < ec; ++p) {
+        const int32_t *e = edges + 2 * pairs[2 * p], *f = edges + 2 * pairs[2 * p + 1];
+        const int32_t a = e[0], b = e[1], c = f[0], d = f[1];
+        const double ux = (double)xy[2 * b] - xy[2 * a], uy = (double)xy[2 * b + 1] - xy[2 * a + 1];
+        const double vx = (double)xy[2 * d] - xy[2 * c], vy = (double)xy[2 * d + 1] - xy[2 * c + 1];
+        /* a_c = acute angle between the lines; delta = theta_u - theta_v mod pi */
+        double delta = fmod(dir_angle(ux, uy) - dir_angle(vx, vy), M_PI);
+        if (delta < 0) delta += M_PI;
+        const double ac = delta <= M_PI / 2 ? delta : M_PI - delta;
+        const double s_ac = delta <= M_PI / 2 ? 1.0 : -1.0; /* d a_c / d theta_u */
+        const double dev_sign = ac > ideal ? 1.0 : (ac < ideal ? -1.0 : 0.0);
+        /* E_ca = 1 - sum |ideal - a_c| / (ideal E_c) */
+        const double coef = -dev_sign * s_ac / (ideal * (double)ec);
+        double gux, guy, gvx, gvy;
+        dtheta(ux, uy, &gux, &guy);
+        dtheta(vx, vy, &gvx, &gvy);
+        g_eca[2 * b] += coef * gux; g_eca[2 * b + 1] += coef * guy;
+        g_eca[2 * a] -= coef * gux; g_eca[2 * a + 1] -= coef * guy;
+        g_eca[2 * d] -= coef * gvx; g_eca[2 * d + 1] -= coef * gvy;
+        g_eca[2 * c] += coef * gvx; g_eca[2 * c + 1] += coef * gvy;
+    }
+    free(pairs);
+    /* M_l and its gradient */
+    terms[1] = oracle_edge_length_variation_f32(xy, V, edges, E);
+    if (E > 1) {
+        nsum sl = {0.0, 0.0};
+        for (int64_t e = 0; e < E; ++e) {
+            const double dx = (double)xy[2 * edges[2 * e + 1]] - xy[2 * edges[2 * e]];
+            const double dy = (double)xy[2 * edges[2 * e + 1] + 1] - xy[2 * edges[2 * e] + 1];
+            nsum_add(&sl, sqrt(dx * dx + dy * dy));
+        }
+        const double mu = nsum_value(&sl) / (double)E;
+        nsum ss = {0.0, 0.0};
+        for (int64_t e = 0; e < E; ++e) {
+            const double dx = (double)xy[2 * edges[2 * e + 1]] - xy[2 * edges[2 * e]];
+            const double dy = (double)xy[2 * edges[2 * e + 1] + 1] - xy[2 * edges[2 * e] + 1];
+            const double t = sqrt(dx * dx + dy * dy) - mu;
+            nsum_add(&ss, t * t);
+        }
+        const double S = nsum_value(&ss), Ml = terms[1];
+        if (S > 0 && mu > 0) {
+            for (int64_t e = 0; e < E; ++e) {
+                const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+                const double dx = (double)xy[2 * b] - xy[2 * a], dy = (double)xy[2 * b + 1] - xy[2 * a + 1];
+                const double l = sqrt(dx * dx + dy * dy);
+                if (l == 0.0) continue;
+                const double dl = Ml * ((l - mu) / S - 1.0 / ((double)E * mu));
+                g_ml[2 * b] += dl * dx / l; g_ml[2 * b + 1] += dl * dy / l;
+                g_ml[2 * a] -= dl * dx / l; g_ml[2 * a + 1] -= dl * dy / l;
+            }
+        }
+    }
+    /* M_a and its gradient */
+    double ma[3];
+    int32_t *arg = malloc(sizeof(int32_t) * 2 * (size_t)(V > 0 ? V : 1));
+    oracle_min_angle_f32(xy, V, edges, E, ma, arg);
+    terms[2] = ma[0];
+    const int64_t n = (int64_t)ma[2];
+    if (n > 0) {
+        int64_t *deg = calloc((size_t)V + 1, sizeof(int64_t));
+        for (int64_t e = 0; e < E; ++e) {
+            const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+            if (xy[2 * a] == xy[2 * b] && xy[2 * a + 1] == xy[2 * b + 1]) continue;
+            deg[a]++; deg[b]++;
+        }
+        for (int64_t v = 0; v < V; ++v) {
+            if (arg[2 * v] < 0) continue;
+            const int32_t i = arg[2 * v], j = arg[2 * v + 1];
+            /* min_v = theta(p_j - p_v) - theta(p_i - p_v) (mod 2 pi) */
+            const double c = (double)deg[v] / (2.0 * M_PI * (double)n);
+            double gix, giy, gjx, gjy;
+            dtheta((double)xy[2 * i] - xy[2 * v], (double)xy[2 * i + 1] - xy[2 * v + 1], &gix, &giy);
+            dtheta((double)xy[2 * j] - xy[2 * v], (double)xy[2 * j + 1] - xy[2 * v + 1], &gjx, &gjy);
+            g_ma[2 * j] += c * gjx; g_ma[2 * j + 1] += c * gjy;
+            g_ma[2 * v] -= c * gjx; g_ma[2 * v + 1] -= c * gjy;
+            g_ma[2 * i] -= c * gix; g_ma[2 * i + 1] -= c * giy;
+            g_ma[2 * v] += c * gix; g_ma[2 * v + 1] += c * giy;
+        }
+        free(deg);
+    }
+    free(arg);
+    return 0;
+}
