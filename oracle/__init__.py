@@ -77,6 +77,8 @@ def _load():
         fl = ctypes.c_float
         lib.oracle_orient_f32.argtypes = [fl, fl, fl, fl, fl, fl]
         lib.oracle_orient_f32.restype = ctypes.c_int
+        lib.oracle_orient_f32_exact.argtypes = [fl, fl, fl, fl, fl, fl]
+        lib.oracle_orient_f32_exact.restype = ctypes.c_int
         lib.oracle_crossings_f32.argtypes = [f32p, i64, i32p, i64, ctypes.c_double, i64p, f64p,
                                              ctypes.c_void_p, i64]
         lib.oracle_crossings_f32.restype = ctypes.c_int
@@ -84,7 +86,8 @@ def _load():
         lib.oracle_min_angle_f32.restype = ctypes.c_int
         lib.oracle_edge_length_variation_f32.argtypes = [f32p, i64, i32p, i64]
         lib.oracle_edge_length_variation_f32.restype = ctypes.c_double
-        lib.oracle_diff_terms_and_grads.argtypes = [f32p, i64, i32p, i64, ctypes.c_double, f64p, f64p, f64p, f64p]
+        lib.oracle_diff_terms_and_grads.argtypes = [f32p, i64, i32p, i64, ctypes.c_double, f64p, f64p, f64p, f64p,
+                                                    i64p]
         lib.oracle_diff_terms_and_grads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -178,8 +181,14 @@ def _xyf(xy) -> np.ndarray:
 
 
 def orient_f32(a, b, c) -> int:
-    """Exact sign of (b - a) x (c - a) for FP32 points (expansion arithmetic)."""
+    """Exact sign of (b - a) x (c - a) for FP32 points (FP64 error-bound filter,
+    then expansion arithmetic)."""
     return int(_load().oracle_orient_f32(*(float(np.float32(v)) for v in (*a, *b, *c))))
+
+
+def orient_f32_exact(a, b, c) -> int:
+    """The same sign, always by expansion arithmetic."""
+    return int(_load().oracle_orient_f32_exact(*(float(np.float32(v)) for v in (*a, *b, *c))))
 
 
 def crossings_f32(xy, edges, ideal: float = DEFAULT_IDEAL, return_pairs: bool = False):
@@ -214,13 +223,16 @@ def edge_length_variation_f32(xy, edges) -> float:
     return float(_load().oracle_edge_length_variation_f32(xy, len(xy), edges, len(edges)))
 
 
-def diff_terms_and_grads(xy, edges, ideal: float = DEFAULT_IDEAL):
+def diff_terms_and_grads(xy, edges, ideal: float = DEFAULT_IDEAL, return_counts: bool = False):
     """(E_ca, M_l, M_a) and their FP64 gradients [V, 2] each, with the crossing set
-    and the smallest gaps held fixed."""
+    and the smallest gaps held fixed; with return_counts, also the crossing counts
+    (proper, touching, collinear, zero-length edges, E_c) of the same pass."""
     xy, edges = _xyf(xy), _edges(edges)
     V = len(xy)
     terms = np.zeros(3, np.float64)
+    counts = np.zeros(5, np.int64)
     g = [np.zeros((max(V, 1), 2), np.float64) for _ in range(3)]
-    if _load().oracle_diff_terms_and_grads(xy, V, edges, len(edges), float(ideal), terms, *g) != 0:
+    if _load().oracle_diff_terms_and_grads(xy, V, edges, len(edges), float(ideal), terms, *g, counts) != 0:
         raise ValueError("ideal angle must be in (0, pi/2]")
-    return terms, g[0][:V], g[1][:V], g[2][:V]
+    out = (terms, g[0][:V], g[1][:V], g[2][:V])
+    return out + (counts,) if return_counts else out

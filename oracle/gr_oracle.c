@@ -459,8 +459,8 @@ static int grow_expansion(int n, const double *e, double b, double *h)
     return m;
 }
 
-/* Exact sign of (b - a) x (c - a) for FP32 points. */
-int oracle_orient_f32(float ax, float ay, float bx, float by, float cx, float cy)
+/* Exact sign of (b - a) x (c - a) for FP32 points, always by expansions. */
+int oracle_orient_f32_exact(float ax, float ay, float bx, float by, float cx, float cy)
 {
     double u[2][2], w[2][2];  /* u = b - a, w = c - a as two-term expansions (hi, lo) */
     two_sum((double)bx, -(double)ax, &u[0][0], &u[0][1]);
@@ -482,6 +482,24 @@ int oracle_orient_f32(float ax, float ay, float bx, float by, float cx, float cy
         }
     const double top = e[n - 1];
     return (top > 0) - (top < 0);
+}
+
+/* Exact sign of (b - a) x (c - a) for FP32 points: Shewchuk's adaptive
+ * scheme, first stage.  The determinant t1 - t2 evaluated in FP64 (unit
+ * roundoff e = 2^-53) carries the true sign whenever its magnitude exceeds
+ * (3 + 16 e) e (|t1| + |t2|) (Shewchuk 1997, the orient2d error bound; FP32
+ * inputs can neither underflow nor overflow FP64 here).  Otherwise the
+ * expansion evaluation above decides. */
+int oracle_orient_f32(float ax, float ay, float bx, float by, float cx, float cy)
+{
+    const double e = 1.1102230246251565e-16;  /* 2^-53 */
+    const double t1 = ((double)bx - (double)ax) * ((double)cy - (double)ay);
+    const double t2 = ((double)by - (double)ay) * ((double)cx - (double)ax);
+    const double det = t1 - t2;
+    const double bound = (3.0 + 16.0 * e) * e * (fabs(t1) + fabs(t2));
+    if (det > bound) return 1;
+    if (-det > bound) return -1;
+    return oracle_orient_f32_exact(ax, ay, bx, by, cx, cy);
 }
 
 static int lex_cmp_f(float ax, float ay, float bx, float by)
@@ -525,27 +543,76 @@ static int classify_pair_f32(const float *xy, const int32_t *e, const int32_t *f
     return kind;
 }
 
+/* Row i of the pair triangle (pairs (i, j), j > i) on FP32 coordinates:
+ * class counts into c[0..2] (proper, touching, collinear), |ideal - a_c|
+ * into s, and, when `out` is not NULL, the first `limit` E_c pairs of the
+ * row (in increasing j) into out. */
+static void crossings_row_f32(const float *xy, const int32_t *edges, int64_t E, int64_t i, double ideal,
+                              int64_t *c, nsum *s, int32_t *out, int64_t limit)
+{
+    int64_t n = 0;
+    for (int64_t j = i + 1; j < E; ++j) {
+        double ac = 0.0;
+        const int k = classify_pair_f32(xy, edges + 2 * i, edges + 2 * j, &ac);
+        if (k == PAIR_COLLINEAR) { ++c[2]; continue; }
+        if (k == PAIR_NONE) continue;
+        ++c[k == PAIR_PROPER ? 0 : 1];
+        nsum_add(s, fabs(ideal - ac));
+        if (out && n < limit) { out[2 * n] = (int32_t)i; out[2 * n + 1] = (int32_t)j; }
+        ++n;
+    }
+}
+
 /* Edge crossings and crossing angle on FP32 coordinates; counts/fvals as
  * oracle_crossings.  When `pairs` is not NULL, the E_c pairs (edge indices,
- * e < f) are written to it, at most max_pairs of them. */
-int oracle_crossings_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E, double ideal,
-                         int64_t *counts, double *fvals, int32_t *pairs, int64_t max_pairs)
+ * e < f, in increasing (e, f) order) are written to it, at most max_pairs of
+ * them: a second pass over the rows, each starting at its offset. */
+static int crossings_f32_impl(const float *xy, const int32_t *edges, int64_t E, double ideal, int64_t *counts,
+                              double *fvals, int32_t *pairs, int64_t max_pairs, int32_t **alloc_pairs)
 {
-    (void)V;
     if (!(ideal > 0.0 && ideal <= M_PI / 2 + 1e-15)) return -1;
-    int64_t proper = 0, touching = 0, collinear = 0, np = 0, zero = 0;
-    nsum s = {0.0, 0.0};
-    for (int64_t i = 0; i < E; ++i) {
-        for (int64_t j = i + 1; j < E; ++j) {
-            double ac = 0.0;
-            const int k = classify_pair_f32(xy, edges + 2 * i, edges + 2 * j, &ac);
-            if (k == PAIR_COLLINEAR) { ++collinear; continue; }
-            if (k == PAIR_NONE) continue;
-            if (k == PAIR_PROPER) ++proper; else ++touching;
-            nsum_add(&s, fabs(ideal - ac));
-            if (pairs && np < max_pairs) { pairs[2 * np] = (int32_t)i; pairs[2 * np + 1] = (int32_t)j; }
-            ++np;
+    const int nt = num_threads();
+    int64_t *acc = calloc((size_t)nt * 3, sizeof(int64_t));
+    nsum *sums = calloc((size_t)nt, sizeof(nsum));
+    int64_t *row = (pairs || alloc_pairs) ? calloc((size_t)E + 1, sizeof(int64_t)) : NULL;
+#pragma omp parallel
+    {
+        const int t = thread_id();
+        int64_t c[3] = {0, 0, 0};
+        nsum s = {0.0, 0.0};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < E; ++i) {
+            const int64_t before = c[0] + c[1];
+            crossings_row_f32(xy, edges, E, i, ideal, c, &s, NULL, 0);
+            if (row) row[i] = c[0] + c[1] - before;
         }
+        acc[3 * t] = c[0]; acc[3 * t + 1] = c[1]; acc[3 * t + 2] = c[2];
+        sums[t] = s;
+    }
+    int64_t proper = 0, touching = 0, collinear = 0, zero = 0;
+    nsum total = {0.0, 0.0};
+    for (int t = 0; t < nt; ++t) {
+        proper += acc[3 * t]; touching += acc[3 * t + 1]; collinear += acc[3 * t + 2];
+        nsum_add(&total, sums[t].s);
+        nsum_add(&total, sums[t].c);
+    }
+    free(acc); free(sums);
+    if (alloc_pairs) {  /* a buffer of exactly E_c pairs, owned by the caller */
+        max_pairs = proper + touching;
+        pairs = malloc(sizeof(int32_t) * 2 * (size_t)(max_pairs > 0 ? max_pairs : 1));
+        *alloc_pairs = pairs;
+    }
+    if (row) {
+        int64_t off = 0;  /* exclusive offsets of the rows */
+        for (int64_t i = 0; i < E; ++i) { const int64_t n = row[i]; row[i] = off; off += n; }
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < E; ++i) {
+            if (row[i] >= max_pairs) continue;
+            int64_t c[3] = {0, 0, 0};
+            nsum s = {0.0, 0.0};
+            crossings_row_f32(xy, edges, E, i, ideal, c, &s, pairs + 2 * row[i], max_pairs - row[i]);
+        }
+        free(row);
     }
     for (int64_t e = 0; e < E; ++e) {
         const int32_t a = edges[2 * e], b = edges[2 * e + 1];
@@ -553,9 +620,16 @@ int oracle_crossings_f32(const float *xy, int64_t V, const int32_t *edges, int64
     }
     const int64_t ec = proper + touching;
     counts[0] = proper; counts[1] = touching; counts[2] = collinear; counts[3] = zero; counts[4] = ec;
-    fvals[0] = nsum_value(&s);
+    fvals[0] = nsum_value(&total);
     fvals[1] = ec > 0 ? 1.0 - fvals[0] / (ideal * (double)ec) : 1.0;
     return 0;
+}
+
+int oracle_crossings_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E, double ideal,
+                         int64_t *counts, double *fvals, int32_t *pairs, int64_t max_pairs)
+{
+    (void)V;
+    return crossings_f32_impl(xy, edges, E, ideal, counts, fvals, pairs, max_pairs, NULL);
 }
 
 /* Direction angle of (dx, dy) in [0, 2 pi). */
@@ -671,7 +745,7 @@ static void dtheta(double dx, double dy, double *gx, double *gy)
  * M_a: d(M_a) / d(min_v) = deg_v / (2 pi n) for each counted vertex; the
  * gap runs counter-clockwise between two fixed incident edges. */
 int oracle_diff_terms_and_grads(const float *xy, int64_t V, const int32_t *edges, int64_t E, double ideal,
-                                double *terms, double *g_eca, double *g_ml, double *g_ma)
+                                double *terms, double *g_eca, double *g_ml, double *g_ma, int64_t *counts_out)
 {
     memset(g_eca, 0, sizeof(double) * 2 * (size_t)V);
     memset(g_ml, 0, sizeof(double) * 2 * (size_t)V);
@@ -679,10 +753,10 @@ int oracle_diff_terms_and_grads(const float *xy, int64_t V, const int32_t *edges
     /* E_ca and its gradient */
     int64_t counts[5];
     double fv[2];
-    if (oracle_crossings_f32(xy, V, edges, E, ideal, counts, fv, NULL, 0) != 0) return -1;
+    int32_t *pairs = NULL;
+    if (crossings_f32_impl(xy, edges, E, ideal, counts, fv, NULL, 0, &pairs) != 0) return -1;
     const int64_t ec = counts[4];
-    int32_t *pairs = malloc(sizeof(int32_t) * 2 * (size_t)(ec > 0 ? ec : 1));
-    oracle_crossings_f32(xy, V, edges, E, ideal, counts, fv, pairs, ec);
+    if (counts_out) memcpy(counts_out, counts, sizeof(counts));
     terms[0] = fv[1];
     for (int64_t p = 0; p < ec; ++p) {
         const int32_t *e = edges + 2 * pairs[2 * p], *f = edges + 2 * pairs[2 * p + 1];

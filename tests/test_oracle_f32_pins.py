@@ -17,13 +17,16 @@ def exact_orient(a, b, c):
     return (d > 0) - (d < 0)
 
 
-def test_orientation_is_exact_on_fp32_inputs():
+@pytest.mark.parametrize("lo,hi", [(-40, 1), (-120, 120)])
+def test_orientation_is_exact_on_fp32_inputs(lo, hi):
     rng = np.random.default_rng(1)
     for _ in range(3000):
-        e = rng.integers(-40, 1, size=6)
-        v = (rng.random(6) * 2.0 ** e).astype(np.float32)
+        e = rng.integers(lo, hi, size=6)
+        v = (rng.choice([-1.0, 1.0], size=6) * rng.random(6) * 2.0 ** e).astype(np.float32)
         a, b, c = v[0:2], v[2:4], v[4:6]
-        assert oracle.orient_f32(a, b, c) == exact_orient(a, b, c)
+        want = exact_orient(a, b, c)
+        assert oracle.orient_f32(a, b, c) == want
+        assert oracle.orient_f32_exact(a, b, c) == want
 
 
 def test_orientation_on_exactly_collinear_and_one_ulp_off():
@@ -39,10 +42,13 @@ def test_orientation_on_exactly_collinear_and_one_ulp_off():
         pts = [np.float32(x) for x in (*a, *b, *c)]
         o = oracle.orient_f32(pts[0:2], pts[2:4], pts[4:6])
         assert o == exact_orient(pts[0:2], pts[2:4], pts[4:6])
+        assert oracle.orient_f32_exact(pts[0:2], pts[2:4], pts[4:6]) == o
         zero += o == 0
         # one ulp away
         c2 = np.nextafter(np.float32(c[0]), np.float32(1.0))
-        assert oracle.orient_f32(pts[0:2], pts[2:4], [c2, pts[5]]) == exact_orient(pts[0:2], pts[2:4], [c2, pts[5]])
+        want = exact_orient(pts[0:2], pts[2:4], [c2, pts[5]])
+        assert oracle.orient_f32(pts[0:2], pts[2:4], [c2, pts[5]]) == want
+        assert oracle.orient_f32_exact(pts[0:2], pts[2:4], [c2, pts[5]]) == want
     assert zero > 1500
 
 
