@@ -45,6 +45,7 @@ WORKLOADS = {
     "dense_long_edge": ("dense_long_edge_layout", 256),
     "plain": ("plain_layout", 256),
     "batched": ("batched_layouts", 256),
+    "differentiable": ("differentiable_layout", 0),
 }
 
 
@@ -164,6 +165,12 @@ def kernel_source_hash(files: list[str]) -> str:
 OPS_PER_PAIR = 25
 OPS_PER_CROSSING_GRID = 60
 OPS_PER_CROSSING_ALLPAIRS = 45
+#   FP32 all-pairs kernel of the differentiable form: per pair 4 id compares,
+#     four filtered FP32 orientations (differences, two products, the
+#     difference, the error bound and its tests: 11 each) and the sign tests;
+#     per E_c pair 20 more (the angle term and the pair record).
+OPS_PER_PAIR_F32 = 52
+OPS_PER_CROSSING_F32 = 20
 SM_COUNT = 152
 LANES_PER_SM_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes, one warp instruction per clock each
 
@@ -198,6 +205,27 @@ def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload:
 
 
 # ------------------------------------------------------------- CPU baseline
+
+def cpu_oracle_diff_step(L, budget_s: float) -> dict:
+    """Times the oracle's FP32 forward + FP64 gradients on the first E_s edges of
+    the layout (all vertices), E_s sized to about budget_s seconds, and scales the
+    time by the number of edge pairs to the full edge list."""
+    import oracle
+    E = L.E
+    Es = max(256, E // 32)
+    t0 = time.perf_counter()
+    oracle.diff_terms_and_grads(L.xy, L.edges[:Es])
+    t = time.perf_counter() - t0
+    Es2 = int(min(E, Es * math.sqrt(max(1.0, budget_s / max(t, 1e-3)))))
+    t0 = time.perf_counter()
+    oracle.diff_terms_and_grads(L.xy, L.edges[:Es2])
+    t2 = time.perf_counter() - t0
+    step_s = t2 * (E * (E - 1)) / max(1, Es2 * (Es2 - 1))
+    return {"step_s": step_s, "cores": oracle.num_threads(),
+            "sample": f"terms and FP64 gradients of the first {Es2} of {E} edges (all {L.V} vertices, "
+                      f"{Es2 * (Es2 - 1) / 2:.3g} edge pairs, {t2:.1f} s), scaled by edge pairs to one full "
+                      f"step ({step_s:.1f} s)"}
+
 
 def cpu_oracle_step(L, d, budget_s: float, rng_seed: int = 0) -> dict:
     """Times the oracle on a bounded sample of one step and scales it to the full
@@ -384,12 +412,169 @@ def run_reference_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_differentiable(args):
+    """Reference arm of the differentiable workload: the oracle's FP32 forward and
+    FP64 gradients on a bounded edge sample per step, scaled to the full layout."""
+    L, _ = make_workload("differentiable")
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_diff_step(L, budget / 4)
+    steps = [cpu_oracle_diff_step(L, budget) for _ in range(args.steps)]
+    step_s = statistics.mean(s["step_s"] for s in steps)
+    value = 1.0 / step_s
+    line = {
+        "impl": "reference", "metric": "fwd+bwd steps/s", "value": value, "unit": "steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": diff_config(L),
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": steps[0]["cores"], "kind": "oracle",
+                         "sample": steps[0]["sample"]},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def diff_config(L):
+    return {"workload": L.name, "V": L.V, "E": L.E, "ideal_deg": 70.0,
+            "step": "gr_layout_update + gr_diff_forward (E_ca, M_l, M_a) + gr_diff_backward (d/dxy)",
+            "inputs": "seeded synthetic (paper_2411_09809_gb300.synth), FP32 coordinates in [0, 1)^2",
+            "l2": "256 MiB write between timed steps (inputs are smaller than L2)"}
+
+
+def run_differentiable(args, rank, world, local_rank):
+    """Differentiable workload: one step = gr_layout_update + gr_diff_forward +
+    gr_diff_backward (the gradient of (1 - E_ca) + M_l + (1 - M_a)).  The plain
+    forward (update + gr_diff_forward) is timed beside it."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_09809_gb300 import build as gr_build, gr
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        if rank == 0:
+            gr_build.build()
+        dist.barrier()
+    else:
+        gr_build.build()
+    gr.load()
+    L, _ = make_workload("differentiable")
+    dev = torch.device("cuda", local_rank)
+    xy = torch.from_numpy(L.xy).to(dev)
+    edges = torch.from_numpy(L.edges).to(dev)
+    out3 = torch.empty(3, dtype=torch.float32, device=dev)
+    gout = torch.tensor([-1.0, 1.0, -1.0], dtype=torch.float32, device=dev)
+    grad = torch.empty_like(xy)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lay = gr.Layout(xy, edges, gr.gr_options(0, 0, 0, 1), stream=stream.cuda_stream, coord_type=gr.GR_COORD_F32)
+
+    def fwd():
+        lay.update(xy)
+        gr.gr_diff_forward(lay.handle, IDEAL, out3)
+
+    def fwd_bwd():
+        fwd()
+        gr.gr_diff_backward(lay.handle, gout, grad)
+
+    def timed(fn, n):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for i in range(n):
+            flush.fill_(i)
+            starts[i].record(stream)
+            fn()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+    for _ in range(args.warmup):
+        fwd_bwd()
+    lay.profile(reset=True)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = gr.gr_kernel_launches()
+    ms = timed(fwd_bwd, args.steps)
+    launches = gr.gr_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = lay.profile()
+    fwd_ms = timed(fwd, args.steps)
+    if world > 1:
+        t = torch.tensor([ms, fwd_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, fwd_ms = (float(x) for x in t.tolist())
+    res = lay.evaluate(gr.GR_METRIC_CROSSINGS, IDEAL)
+
+    # end to end through the C ABI with host buffers (pinned): coordinates in,
+    # the three terms out, the upstream gradient in; the gradient stays on the device
+    hxy = torch.from_numpy(L.xy).pin_memory()
+    hout = torch.empty(3, dtype=torch.float32).pin_memory()
+    hg = torch.tensor([-1.0, 1.0, -1.0], dtype=torch.float32).pin_memory()
+    io0 = gr.gr_io_bytes(lay.handle)
+    e2e_s = []
+    for i in range(0 if args.no_e2e else args.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gr.gr_layout_update(lay.handle, hxy, None, gr.GR_COORD_F32)
+        gr.gr_diff_forward(lay.handle, IDEAL, hout)
+        gr.gr_diff_backward(lay.handle, hg, grad)
+        e2e_s.append(time.perf_counter() - t0)
+    io1 = gr.gr_io_bytes(lay.handle)
+    e2e_ms = statistics.mean(e2e_s) * 1e3 if e2e_s else float("nan")
+    lay.close()
+    if rank != 0:
+        return
+    E = L.E
+    pairs_ms, pairs_calls = prof["cross_pairs"]
+    t = pairs_ms / max(1, pairs_calls) / 1e3
+    ec = res.crossing.c.crossings
+    n_seg = E - res.crossing.c.zero_length_edges
+    ops = n_seg * (n_seg - 1) / 2 * OPS_PER_PAIR_F32 + ec * OPS_PER_CROSSING_F32
+    peaks, peak_kind = load_peaks()
+    peak = SM_COUNT * LANES_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    rf = {"kernel": "k_cross_f32", "bound": "alu", "achieved": ops / t / 1e12 if t > 0 else None, "peak": peak,
+          "unit": "Tops/s (int32-equivalent lane ops)", "frac": ops / t / 1e12 / peak if t > 0 else None,
+          "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
+                         f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
+          "traffic": load_traffic("k_cross_f32", "differentiable", kernel_source_hash(["k_diff.cu"])),
+          "launch_ms": t * 1e3}
+    line = {
+        "metric": "fwd+bwd steps/s", "value": world * 1e3 / ms, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(diff_config(L), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "fwd_ms": fwd_ms, "fwd_bwd_ms": ms, "fwd_bwd_over_fwd": ms / fwd_ms,
+        "results": {"E_ca": float(out3[0]), "M_l": float(out3[1]), "M_a": float(out3[2]), "E_c": ec},
+        "phase_ms": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]},
+        "roofline": rf,
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "steps/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": (io1[0] - io0[0]) // max(1, len(e2e_s)),
+                "d2h_bytes_per_step": (io1[1] - io0[1]) // max(1, len(e2e_s))},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_diff_step(L, args.cpu_budget)
+        line["cpu_baseline"] = {"value": 1.0 / cb["step_s"], "unit": "steps/s", "cores": cb["cores"],
+                                "kind": "oracle", "sample": cb["sample"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle (plain C brute force) on the host cores."""
     if rank != 0:
         return
     if args.workload == "batched":
         run_reference_batched(args)
+        return
+    if args.workload == "differentiable":
+        run_reference_differentiable(args)
         return
     L, d = make_workload(args.workload)
     E = L.E
@@ -556,6 +741,8 @@ def main():
     try:
         if args.workload == "batched":
             run_batched(args, rank, world, local_rank)
+        elif args.workload == "differentiable":
+            run_differentiable(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -127,7 +127,7 @@ typedef struct {
 
 /* Creates a layout from V vertex coordinates and E edges (Sec. 2.1 inputs;
  * Algorithms 1-5 take the vertex table D_pos and the edge table D_e).
- * `xy` is [V][2] of `coord_type` (only GR_COORD_I32 here), `edges` is [E][2]
+ * `xy` is [V][2] of `coord_type` (int32, or FP32: see below), `edges` is [E][2]
  * int32, device or host memory.  Validates the input on the device and
  * synchronises the stream: GR_EINVAL for a vertex id outside [0, V) or a
  * self-loop, GR_ERANGE for a coordinate outside [0, 65536).  `opt` may be
@@ -178,6 +178,29 @@ gr_status gr_crossing_angle(gr_layout *layout, double ideal_rad, gr_crossing_ang
 gr_status gr_crossings_per_edge(gr_layout *layout, double ideal_rad, int64_t *d_counts,
                                 double *d_dev);
 
+/* ------------------------------------------------- differentiable form
+ * Layouts created with GR_COORD_F32 take FP32 coordinates [V][2] (any finite
+ * values; GR_ERANGE otherwise).  Their crossing set is decided exactly on the
+ * FP32 inputs (orientation signs through an FP32 error-bound filter, an FP64
+ * one and exact expansion arithmetic, after Shewchuk 1997); gr_evaluate
+ * supports the crossing, edge length and minimum angle metrics on them
+ * (occlusion: GR_ENOTSUP).
+ *
+ * gr_diff_forward evaluates E_ca (ideal `ideal_rad`, <= 0 for 70 deg), M_l
+ * and M_a (Sec. 2.1, Algorithms 2, 3, 5) into out3 = {E_ca, M_l, M_a} (host or
+ * device memory), keeps the crossing pairs and every vertex's smallest gap,
+ * and synchronises.  gr_diff_backward then writes to d_grad_xy ([V][2] FP32,
+ * DEVICE memory, overwritten) the gradient of
+ *   gout3[0] * E_ca + gout3[1] * M_l + gout3[2] * M_a
+ * with respect to the coordinates, with that crossing set and those gaps held
+ * fixed (the metrics are piecewise smooth; the gradient is the one of the
+ * current piece).  `gout3` may be device or host memory; with device memory
+ * the call is stream-ordered and does not synchronise.  The paper defines the
+ * metrics only; the gradient is this library's addition (layout optimisation
+ * is the application the paper names). */
+gr_status gr_diff_forward(gr_layout *layout, double ideal_rad, float *out3);
+gr_status gr_diff_backward(gr_layout *layout, const float *gout3, float *d_grad_xy);
+
 /* ------------------------------------------------------------- batches
  * Many independent layouts evaluated together (the batched form of the five
  * metrics): layouts are packed one after another.  `v_off` and `e_off` are
@@ -208,8 +231,9 @@ gr_status gr_batch_evaluate(gr_batch *batch, uint32_t metrics, const gr_params *
 gr_status gr_batch_destroy(gr_batch *batch);
 
 /* ------------------------------------------------------------- tracing
- * Phase timing: when enabled on a layout, every gr_layout_update and
- * gr_evaluate records CUDA events around its phases on the layout's stream;
+ * Phase timing: when enabled on a layout, every gr_layout_update,
+ * gr_evaluate, gr_diff_forward and gr_diff_backward records CUDA events
+ * around its phases on the layout's stream;
  * gr_profile_read returns the accumulated device time and call count of each
  * phase (optionally resetting them).  Events cost a few microseconds per
  * phase, so leave profiling off when not reading it. */
@@ -223,6 +247,7 @@ typedef enum {
     GR_PHASE_CROSS_SCATTER,  /* a4: records sorted by cell */
     GR_PHASE_CROSS_PAIRS,    /* a6 per-cell pair kernel, or a7 all-pairs tiles */
     GR_PHASE_FINALIZE,       /* a11 and the result copy */
+    GR_PHASE_DIFF_BACKWARD,  /* gr_diff_backward: the three adjoint kernels */
     GR_NUM_PHASES
 } gr_phase;
 

@@ -71,6 +71,15 @@ struct gr_layout {
     GridBuffers g;
     gr_result *h_result = nullptr;  // pinned
     DevAcc *h_acc = nullptr;        // pinned
+    gr_coord_type coord = GR_COORD_I32;
+    // differentiable form (FP32 layouts)
+    uint2 *pairs = nullptr;         // E_c pairs of the last forward
+    uint64_t pairs_cap = 0, n_pairs = 0;
+    int2 *arg = nullptr;            // [V] smallest gap of every vertex
+    DiffState *st = nullptr;
+    float *out3 = nullptr, *gout3 = nullptr;
+    uint32_t diff_ideal_u = 0;
+    bool diff_ready = false;
     bool stats_stale = true;        // h_acc's layout part predates the last update
     int64_t io_h2d = 0, io_d2h = 0; // bytes copied between host and device
     // phase timing
@@ -96,7 +105,8 @@ void free_layout(gr_layout *L) {
     if (!L) return;
     Buffers &b = L->b;
     void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.ma_part,
-                    b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result};
+                    b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result,
+                    b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->arg, L->st, L->out3, L->gout3};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_grid(L->g);
@@ -132,6 +142,15 @@ gr_status alloc_layout(gr_layout *L) {
     GR_TRY(dalloc(&b.scan_tmp, (size_t)kScanMaxBlocks));
     GR_TRY(dalloc(&b.scan_tmp_side, (size_t)kScanMaxBlocks));
     GR_TRY(dalloc(&b.result, 1));
+    if (L->coord == GR_COORD_F32) {
+        GR_TRY(dalloc(&b.seg_ids, (size_t)E));
+        GR_TRY(dalloc(&b.dir_ang, 2 * (size_t)E));
+        GR_TRY(dalloc(&b.dir_other, 2 * (size_t)E));
+        GR_TRY(dalloc(&L->arg, (size_t)V));
+        GR_TRY(dalloc(&L->st, 1));
+        GR_TRY(dalloc(&L->out3, 3));
+        GR_TRY(dalloc(&L->gout3, 3));
+    }
 #undef GR_TRY
     GR_CU(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
     GR_CU(cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming));
@@ -249,8 +268,13 @@ gr_status enqueue_inputs(gr_layout *L, const void *xy, const int32_t *edges) {
         GR_CU(cudaMemcpyAsync(L->b.edges, edges, sizeof(int32_t) * 2 * E, k, s));
         if (k == cudaMemcpyHostToDevice) L->io_h2d += (int64_t)sizeof(int32_t) * 2 * E;
     }
-    launch_check_vertices(L->b.xy, V, L->b, s);
-    launch_gather(L->b.xy, V, L->b.edges, E, L->b, s);
+    if (L->coord == GR_COORD_F32) {
+        launch_gather_f32((const float *)L->b.xy, V, L->b.edges, E, L->b, s);
+    } else {
+        launch_check_vertices(L->b.xy, V, L->b, s);
+        launch_gather(L->b.xy, V, L->b.edges, E, L->b, s);
+    }
+    L->diff_ready = false;
     phase_end(L, GR_PHASE_GATHER);
     GR_CU(cudaGetLastError());
     L->stats_stale = true;
@@ -259,7 +283,7 @@ gr_status enqueue_inputs(gr_layout *L, const void *xy, const int32_t *edges) {
 
 gr_status status_to_error(uint32_t st) {
     if (st & ST_BAD_ID) return fail(GR_EINVAL, "vertex id outside [0, V) or self-loop in the edge list");
-    if (st & ST_BAD_COORD) return fail(GR_ERANGE, "vertex coordinate outside [0, 65536)");
+    if (st & ST_BAD_COORD) return fail(GR_ERANGE, "vertex coordinate outside [0, 65536) (not finite for FP32 layouts)");
     if (st & ST_SCAN_OVERFLOW) return fail(GR_ENOTSUP, "an offset table exceeded 2^32 entries");
     if (st & ST_OVERFLOW) return fail(GR_ENOMEM, "grid record buffer overflow");
     return GR_OK;
@@ -333,6 +357,69 @@ int occl_cell_log2(int64_t d) {
     return k;
 }
 
+// The FP32 forward: E_ca and the crossing counts (E_c pairs saved when
+// `pairs` is set), M_l, M_a (smallest gaps saved), folded into L->st/out3.
+gr_status forward_f32(gr_layout *L, uint32_t metrics, double ideal, bool save_pairs) {
+    cudaStream_t s = L->stream;
+    Buffers &b = L->b;
+    const int64_t V = L->V, E = L->E;
+    const uint32_t ideal_u = ideal_units(ideal);
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
+                              sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
+        phase_begin(L, GR_PHASE_EDGE_LENGTH);
+        if (metrics & GR_METRIC_EDGE_LENGTH) launch_elv(b, E, s, true);
+        phase_end(L, GR_PHASE_EDGE_LENGTH);
+        phase_begin(L, GR_PHASE_MIN_ANGLE);
+        if (metrics & GR_METRIC_MIN_ANGLE) launch_min_angle_f32(b, V, E, L->arg, s);
+        phase_end(L, GR_PHASE_MIN_ANGLE);
+        phase_begin(L, GR_PHASE_CROSS_PAIRS);
+        if (metrics & GR_METRIC_CROSSINGS)
+            launch_crossings_f32(b, E, ideal_u, save_pairs ? L->pairs : nullptr, save_pairs ? L->pairs_cap : 0, s);
+        phase_end(L, GR_PHASE_CROSS_PAIRS);
+        phase_begin(L, GR_PHASE_FINALIZE);
+        if (save_pairs) launch_diff_state(b, V, E, ideal, L->st, L->out3, s);
+        GR_CU(cudaGetLastError());
+        GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+        L->io_d2h += (int64_t)sizeof(DevAcc);
+        phase_end(L, GR_PHASE_FINALIZE);
+        GR_CU(cudaStreamSynchronize(s));
+        phase_collect(L);
+        gr_status st = status_to_error(L->h_acc->status | L->h_acc->eval_status);
+        if (st != GR_OK) return st;
+        const uint64_t np = L->h_acc->records;
+        if (!save_pairs || np <= L->pairs_cap) {
+            L->n_pairs = save_pairs ? np : 0;
+            L->diff_ideal_u = ideal_u;
+            return GR_OK;
+        }
+        // more E_c pairs than the buffer holds: grow it and run again
+        if (L->pairs) cudaFree(L->pairs);
+        L->pairs = nullptr;
+        L->pairs_cap = 0;
+        if ((st = dalloc(&L->pairs, (size_t)(np + np / 4 + 1024))) != GR_OK) return st;
+        L->pairs_cap = np + np / 4 + 1024;
+    }
+    return fail(GR_ENOMEM, "crossing pair buffer could not be sized");
+}
+
+gr_status evaluate_f32(gr_layout *L, uint32_t metrics, double ideal, gr_result *out) {
+    if (metrics & GR_METRIC_OCCLUSION) return fail(GR_ENOTSUP, "occlusion needs GR_COORD_I32 coordinates");
+    gr_status st = forward_f32(L, metrics, ideal, false);
+    if (st != GR_OK) return st;
+    cudaStream_t s = L->stream;
+    Buffers &b = L->b;
+    launch_finalize(b, metrics, L->E, ideal, 0, L->V > 0 ? min_angle_blocks(L->V) : 0,
+                    (metrics & GR_METRIC_CROSSINGS) ? GR_PATH_ALLPAIRS : 0, 0, 0, -1, s);
+    GR_CU(cudaGetLastError());
+    GR_CU(cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s));
+    L->io_d2h += (int64_t)sizeof(gr_result);
+    GR_CU(cudaStreamSynchronize(s));
+    *out = *L->h_result;
+    out->grid_records = 0;
+    return GR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -346,7 +433,7 @@ gr_status gr_layout_create(gr_layout **out, const void *xy, gr_coord_type coord_
                            gr_stream_t stream) {
     g_err.clear();
     if (!out) return fail(GR_EINVAL, "out is NULL");
-    if (coord_type != GR_COORD_I32) return fail(GR_ENOTSUP, "only GR_COORD_I32 layouts are supported");
+    if (coord_type != GR_COORD_I32 && coord_type != GR_COORD_F32) return fail(GR_ENOTSUP, "unknown coordinate type");
     if (V < 0 || E < 0 || V >= (int64_t(1) << 31) || E >= (int64_t(1) << 31))
         return fail(GR_EINVAL, "V and E must be in [0, 2^31)");
     if ((V > 0 && !xy) || (E > 0 && !edges)) return fail(GR_EINVAL, "NULL input pointer");
@@ -355,6 +442,7 @@ gr_status gr_layout_create(gr_layout **out, const void *xy, gr_coord_type coord_
     L->V = V;
     L->E = E;
     L->stream = (cudaStream_t)stream;
+    L->coord = coord_type;
     if (opt) L->opt = *opt;
     gr_status st = alloc_layout(L);
     if (st == GR_OK && L->opt.profile) st = set_profiling(L, true);
@@ -403,6 +491,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     const int64_t V = L->V, E = L->E;
     if ((st = refresh_stats(L)) != GR_OK) return st;
     if ((st = status_to_error(L->h_acc->status)) != GR_OK) return st;
+    if (L->coord == GR_COORD_F32) return evaluate_f32(L, metrics, ideal, out);
     const uint64_t n_seg = L->h_acc->n_seg;
     GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
                           sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
@@ -565,6 +654,7 @@ gr_status gr_crossing_angle(gr_layout *L, double ideal_rad, gr_crossing_angle_re
 gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_counts, double *d_dev) {
     g_err.clear();
     if (!L || (L->E > 0 && (!d_counts || !d_dev))) return fail(GR_EINVAL, "NULL argument");
+    if (L->coord != GR_COORD_I32) return fail(GR_ENOTSUP, "per-edge crossings need GR_COORD_I32 coordinates");
     gr_params p{ideal_rad, 0};
     double ideal;
     int64_t d;
@@ -610,6 +700,49 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     return status_to_error(L->h_acc->status | L->h_acc->eval_status);
 }
 
+gr_status gr_diff_forward(gr_layout *L, double ideal_rad, float *out3) {
+    g_err.clear();
+    if (!L || !out3) return fail(GR_EINVAL, "NULL argument");
+    if (L->coord != GR_COORD_F32) return fail(GR_ENOTSUP, "gr_diff_forward needs a GR_COORD_F32 layout");
+    gr_params p{ideal_rad, 0};
+    double ideal;
+    int64_t d;
+    gr_status st = read_params(&p, &ideal, &d);
+    if (st != GR_OK) return st;
+    if ((st = refresh_stats(L)) != GR_OK) return st;
+    if ((st = status_to_error(L->h_acc->status)) != GR_OK) return st;
+    if ((st = forward_f32(L, GR_METRIC_CROSSINGS | GR_METRIC_EDGE_LENGTH | GR_METRIC_MIN_ANGLE, ideal, true)) != GR_OK)
+        return st;
+    const cudaMemcpyKind k = is_device_pointer(out3) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    GR_CU(cudaMemcpyAsync(out3, L->out3, sizeof(float) * 3, k, L->stream));
+    if (k == cudaMemcpyDeviceToHost) L->io_d2h += (int64_t)sizeof(float) * 3;
+    GR_CU(cudaStreamSynchronize(L->stream));
+    L->diff_ready = true;
+    return GR_OK;
+}
+
+gr_status gr_diff_backward(gr_layout *L, const float *gout3, float *d_grad_xy) {
+    g_err.clear();
+    if (!L || !gout3 || (L->V > 0 && !d_grad_xy)) return fail(GR_EINVAL, "NULL argument");
+    if (L->coord != GR_COORD_F32) return fail(GR_ENOTSUP, "gr_diff_backward needs a GR_COORD_F32 layout");
+    if (!L->diff_ready) return fail(GR_EINVAL, "gr_diff_backward needs a gr_diff_forward after the last update");
+    if (L->V > 0 && !is_device_pointer(d_grad_xy)) return fail(GR_EINVAL, "the gradient must be device memory");
+    const float *g = gout3;
+    if (!is_device_pointer(gout3)) {
+        GR_CU(cudaMemcpyAsync(L->gout3, gout3, sizeof(float) * 3, cudaMemcpyHostToDevice, L->stream));
+        L->io_h2d += (int64_t)sizeof(float) * 3;
+        g = L->gout3;
+    }
+    phase_begin(L, GR_PHASE_DIFF_BACKWARD);
+    if (L->V > 0)
+        launch_diff_backward(L->b, L->V, L->E, L->pairs, L->arg, L->st, g, L->diff_ideal_u, L->n_pairs, d_grad_xy,
+                             L->stream);
+    phase_end(L, GR_PHASE_DIFF_BACKWARD);
+    GR_CU(cudaGetLastError());
+    if (!is_device_pointer(gout3)) GR_CU(cudaStreamSynchronize(L->stream));  // the host buffer may go away
+    return GR_OK;
+}
+
 gr_status gr_profile_enable(gr_layout *L, int enable) {
     g_err.clear();
     if (!L) return fail(GR_EINVAL, "layout is NULL");
@@ -620,6 +753,13 @@ gr_status gr_profile_read(gr_layout *L, gr_profile *out, int reset) {
     g_err.clear();
     if (!L || !out) return fail(GR_EINVAL, "NULL argument");
     memset(out, 0, sizeof(*out));
+    bool pending = false;  // phases of calls that did not synchronise (gr_diff_backward)
+    for (int ph = 0; ph < GR_NUM_PHASES; ++ph)
+        if (L->pending[ph]) {
+            cudaEventSynchronize(L->ev[2 * ph + 1]);
+            pending = true;
+        }
+    if (pending) phase_collect(L);
     for (int ph = 0; ph < GR_NUM_PHASES; ++ph) {
         out->ms[ph] = L->prof_ms[ph];
         out->calls[ph] = L->prof_calls[ph];

@@ -75,6 +75,9 @@ struct Buffers {
     uint32_t *deg = nullptr;      // [V + 1] degree, then CSR offsets (scan in place)
     uint32_t *deg_fill = nullptr; // [V]
     int2 *dirs = nullptr;         // [2 E] incident directions by vertex
+    uint2 *seg_ids = nullptr;     // [E] FP32 layouts: vertex ids of seg[i] (seg holds the FP32 endpoints)
+    double *dir_ang = nullptr;    // [2 E] FP32 layouts: incident direction angles by vertex
+    int32_t *dir_other = nullptr; // [2 E] FP32 layouts: far vertex of each incident direction
     uint64_t *scan_tmp = nullptr; // [kScanMaxBlocks] block sums (crossing stream)
     uint64_t *scan_tmp_side = nullptr; // [kScanMaxBlocks] block sums (side stream)
     gr_result *result = nullptr;  // device copy of the result
@@ -160,7 +163,8 @@ void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s);
 int min_angle_blocks(int64_t V);
 
 // a10: edge length variation, two passes of deterministic FP64 partials.
-void launch_elv(const Buffers &b, int64_t E, cudaStream_t s);
+// `f32`: len2 holds FP64 squared lengths (as bits) instead of int64.
+void launch_elv(const Buffers &b, int64_t E, cudaStream_t s, bool f32 = false);
 
 // Exclusive scan of n uint32 values in place into out[0..n] (out[n] = total).
 // `in` and `out` may alias.  The total also goes to *total (device).
@@ -174,6 +178,34 @@ void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal
 
 // Per-edge output conversion: integer dev sums to radians (double), in place.
 void launch_per_edge_export(uint64_t *dev_fixed, int64_t E, cudaStream_t s);
+
+// ------------------------------------------------------ differentiable form
+// What the backward needs from the forward, on the device.
+struct DiffState {
+    int64_t ec;        // E_c
+    uint64_t pairs;    // E_c pairs emitted
+    double ideal;      // radians
+    double E_ca;
+    double mu, S, M_l; // mean length, sum (l - mu)^2, M_l
+    int64_t n_ma;      // vertices counted by M_a
+    double M_a;
+};
+
+// a1 for FP32 coordinates (finite values; ids checked).
+void launch_gather_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E, Buffers &b, cudaStream_t s);
+// a7 on FP32 coordinates with exact predicates; E_c pairs (compacted segment
+// indices) to `pairs` (at most `cap`; the total goes to acc->records).
+void launch_crossings_f32(const Buffers &b, int64_t n_bound, uint32_t ideal, uint2 *pairs, uint64_t cap,
+                          cudaStream_t s);
+// a9 on FP32 coordinates; each vertex's smallest gap (far vertices) to `arg`.
+void launch_min_angle_f32(Buffers &b, int64_t V, int64_t E, int2 *arg, cudaStream_t s);
+// Folds the forward into `st` and the three values (E_ca, M_l, M_a) into out3.
+void launch_diff_state(const Buffers &b, int64_t V, int64_t E, double ideal, DiffState *st, float *out3,
+                       cudaStream_t s);
+// grad[V][2] = gout[0] dE_ca + gout[1] dM_l + gout[2] dM_a (overwritten).
+void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *pairs, const int2 *arg,
+                          const DiffState *st, const float *gout, uint32_t ideal_u, uint64_t n_pairs, float *grad,
+                          cudaStream_t s);
 
 // ------------------------------------------------------------------ batches
 // Device view of a batch of layouts packed one after another: layout l owns

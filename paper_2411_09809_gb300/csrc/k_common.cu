@@ -197,13 +197,18 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t *in, uint32_
 // ------------------------------------------------------------------ ELV a10
 // Pass 1: per-block FP64 sum of edge lengths l_e = sqrt(len2_e) over a fixed
 // strided subset of edges (fixed order => deterministic).
+__device__ __forceinline__ double edge_length(const int64_t *__restrict__ len2, int64_t e, bool f32) {
+    const int64_t q = len2[e];
+    return sqrt(f32 ? __longlong_as_double(q) : (double)q);
+}
+
 __global__ void __launch_bounds__(256) k_elv_sum(const int64_t *__restrict__ len2, int64_t E,
-                                                 double *__restrict__ part) {
+                                                 double *__restrict__ part, bool f32) {
     __shared__ double sh[32];
     double s = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
          e += (int64_t)kElvBlocks * blockDim.x)
-        s += sqrt((double)len2[e]);
+        s += edge_length(len2, e, f32);
     s = block_sum<double>(s, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(256) k_elv_sum(const int64_t *__restrict__ len
 // Pass 2: every block recomputes the mean from the pass-1 partials in the
 // same fixed order, then sums (l_e - mean)^2 over its subset.
 __global__ void __launch_bounds__(256) k_elv_var(const int64_t *__restrict__ len2, int64_t E,
-                                                 double *__restrict__ part) {
+                                                 double *__restrict__ part, bool f32) {
     __shared__ double sh[32];
     double m = 0.0;
     for (int i = threadIdx.x; i < kElvBlocks; i += blockDim.x) m += part[i];
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(256) k_elv_var(const int64_t *__restrict__ len
     double s = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
          e += (int64_t)kElvBlocks * blockDim.x) {
-        const double t = sqrt((double)len2[e]) - m;
+        const double t = edge_length(len2, e, f32) - m;
         s += t * t;
     }
     s = block_sum<double>(s, sh);
@@ -368,10 +373,10 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *blo
     if (nb > 0) k_scan_apply<<<nb, 1024, 0, s>>>(in, out, n, block_tmp);
 }
 
-void launch_elv(const Buffers &b, int64_t E, cudaStream_t s) {
+void launch_elv(const Buffers &b, int64_t E, cudaStream_t s, bool f32) {
     count_launches(2);
-    k_elv_sum<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part);
-    k_elv_var<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part);
+    k_elv_sum<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part, f32);
+    k_elv_var<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part, f32);
 }
 
 void launch_batch_elv(const Buffers &b, const BatchView &bv, cudaStream_t s) {

@@ -63,7 +63,7 @@ class gr_result(ctypes.Structure):
 
 
 GR_PHASE_NAMES = ["gather", "edge_length", "min_angle", "occl_bin", "occl_pairs", "cross_bin",
-                  "cross_scatter", "cross_pairs", "finalize"]
+                  "cross_scatter", "cross_pairs", "finalize", "diff_backward"]
 
 
 class gr_profile(ctypes.Structure):
@@ -112,6 +112,8 @@ def load() -> ctypes.CDLL:
         "gr_batch_update": ([P, P, P], c_int32),
         "gr_batch_evaluate": ([P, c_uint32, ctypes.POINTER(gr_params), P], c_int32),
         "gr_batch_destroy": ([P], c_int32),
+        "gr_diff_forward": ([P, c_double, P], c_int32),
+        "gr_diff_backward": ([P, P, P], c_int32),
         "gr_last_error": ([], ctypes.c_char_p),
         "gr_version": ([], ctypes.c_char_p),
     }
@@ -180,11 +182,34 @@ def gr_layout_create(xy, edges, coord_type: int = GR_COORD_I32, opt: gr_options 
     return h
 
 
-def gr_layout_update(layout, xy, edges=None) -> None:
+def gr_layout_update(layout, xy, edges=None, coord_type: int = GR_COORD_I32) -> None:
     lib = load()
-    xp, xk = _buffer(xy, "int32")
+    xp, xk = _buffer(xy, "int32" if coord_type == GR_COORD_I32 else "float32")
     ep, ek = _buffer(edges, "int32")
     _check(lib.gr_layout_update(layout, xp, ep))
+
+
+def gr_diff_forward(layout, ideal_rad: float = 0.0, out3=None):
+    """{E_ca, M_l, M_a} of an FP32 layout into `out3` (a float32 [3] tensor or array;
+    a new numpy array when None), keeping what gr_diff_backward needs."""
+    import numpy as np
+    if out3 is None:
+        out3 = np.zeros(3, np.float32)
+    op, ok = _buffer(out3, "float32")
+    _check(load().gr_diff_forward(layout, float(ideal_rad), op))
+    if ok is not out3:  # a converted copy: hand back the values
+        return ok
+    return out3
+
+
+def gr_diff_backward(layout, gout3, d_grad_xy) -> None:
+    """Gradient of gout3 . (E_ca, M_l, M_a) w.r.t. the coordinates into d_grad_xy
+    (float32 [V, 2] device tensor, overwritten)."""
+    gp, gk = _buffer(gout3, "float32")
+    dp, dk = _buffer(d_grad_xy, "float32")
+    if dk is not d_grad_xy:
+        raise TypeError("d_grad_xy must be a contiguous float32 device tensor")
+    _check(load().gr_diff_backward(layout, gp, dp))
 
 
 def gr_layout_destroy(layout) -> None:
@@ -358,10 +383,11 @@ class Layout:
                  coord_type: int = GR_COORD_I32):
         self.E = _count(edges)
         self.V = _count(xy)
+        self.coord_type = coord_type
         self.handle = gr_layout_create(xy, edges, coord_type, opt, stream)
 
     def update(self, xy, edges=None) -> None:
-        gr_layout_update(self.handle, xy, edges)
+        gr_layout_update(self.handle, xy, edges, self.coord_type)
 
     def evaluate(self, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0, occlusion_d: int = 0) -> gr_result:
         return gr_evaluate(self.handle, metrics, ideal_rad, occlusion_d)

@@ -1,0 +1,185 @@
+"""GPU: the differentiable (FP32) form through the C ABI against the oracle's FP32
+form -- exact crossing counts, terms within 1e-5, gradients within 1e-5 in norm
+of the oracle's FP64 gradients -- and the torch.autograd wrapper."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_09809_gb300 import build, gr, synth
+
+pytestmark = pytest.mark.gpu
+IDEAL = 7 * math.pi / 18
+REL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    gr.load()
+
+
+def cuda(a):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def random_float_layout(seed, V, knn, extra, scale=1.0, offset=0.0):
+    rng = np.random.default_rng(seed)
+    xy = (offset + scale * rng.random((V, 2))).astype(np.float32)
+    e = synth.knn_edges(xy, 5, knn)
+    return xy, synth.add_random_edges(rng, V, e, extra)
+
+
+def check_forward(xy, edges, res, label, ideal=IDEAL):
+    ref = oracle.crossings_f32(xy, edges, ideal)
+    c = res.crossing.c
+    assert (c.proper, c.touching, c.collinear_overlaps, c.zero_length_edges) == \
+        (ref.proper, ref.touching, ref.collinear, ref.zero_length_edges), label
+    assert abs(res.crossing.angle_dev_sum - ref.angle_dev_sum) <= REL * max(1.0, ref.angle_dev_sum), label
+    assert res.crossing.E_ca == pytest.approx(ref.E_ca, rel=REL, abs=REL), label
+    ma = oracle.min_angle_f32(xy, edges)
+    assert res.min_angle.n_vertices_counted == ma.n_vertices, label
+    assert res.min_angle.M_a == pytest.approx(ma.M_a, rel=REL, abs=REL), label
+    assert res.M_l == pytest.approx(oracle.edge_length_variation_f32(xy, edges), rel=REL, abs=1e-12), label
+
+
+FWD = gr.GR_METRIC_CROSSINGS | gr.GR_METRIC_MIN_ANGLE | gr.GR_METRIC_EDGE_LENGTH
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_fp32_evaluate_matches_oracle(seed):
+    xy, e = random_float_layout(seed, 3000, 6500, 1500, scale=float(10.0 ** (seed - 1)), offset=seed * 100.0)
+    with gr.Layout(cuda(xy), cuda(e), coord_type=gr.GR_COORD_F32) as L:
+        check_forward(xy, e, L.evaluate(FWD, IDEAL), f"seed {seed}")
+        check_forward(xy, e, L.evaluate(FWD, math.radians(45)), f"seed {seed} 45", math.radians(45))
+
+
+def test_fp32_degenerate_layouts_exact():
+    # coordinates k / 64 on a tiny span: collinear overlaps, touching, zero-length,
+    # duplicate edges; host buffers this time
+    rng = np.random.default_rng(11)
+    for t in range(12):
+        L0 = synth.tiny_degenerate_layout(rng, int(rng.integers(3, 50)), int(rng.integers(1, 300)),
+                                          span=int(rng.integers(2, 12)))
+        xy = (L0.xy.astype(np.float64) / 64.0 - 0.5).astype(np.float32)
+        with gr.Layout(xy, L0.edges, coord_type=gr.GR_COORD_F32) as L:
+            check_forward(xy, L0.edges, L.evaluate(FWD, IDEAL), f"trial {t}")
+
+
+def test_fp32_layout_rejects_non_finite_and_occlusion():
+    xy = np.array([[0.0, 0.0], [1.0, np.inf], [0.5, 0.5]], np.float32)
+    e = np.array([[0, 1], [1, 2]], np.int32)
+    with pytest.raises(gr.GrError) as ei:
+        gr.Layout(xy, e, coord_type=gr.GR_COORD_F32)
+    assert ei.value.status == gr.GR_ERANGE
+    xy[1, 1] = 2.0
+    with gr.Layout(xy, e, coord_type=gr.GR_COORD_F32) as L:
+        with pytest.raises(gr.GrError) as ei:
+            L.evaluate(gr.GR_METRIC_OCCLUSION, IDEAL, 10)
+        assert ei.value.status == gr.GR_ENOTSUP
+        with pytest.raises(gr.GrError) as ei:
+            gr.gr_diff_backward(L.handle, np.ones(3, np.float32), cuda(np.zeros((3, 2), np.float32)))
+        assert ei.value.status == gr.GR_EINVAL  # no forward yet
+    with gr.Layout(xy.astype(np.int32), e) as L:
+        with pytest.raises(gr.GrError) as ei:
+            gr.gr_diff_forward(L.handle, IDEAL)
+        assert ei.value.status == gr.GR_ENOTSUP
+
+
+def grad_close(g, ref, label):
+    err = np.linalg.norm(g.astype(np.float64) - ref)
+    assert err <= REL * max(np.linalg.norm(ref), 1e-30), (label, err, np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_diff_forward_and_gradients_match_oracle(seed):
+    xy, e = random_float_layout(100 + seed, 4000, 9000, 2000)
+    terms, g_eca, g_ml, g_ma = oracle.diff_terms_and_grads(xy, e, IDEAL)
+    with gr.Layout(cuda(xy), cuda(e), coord_type=gr.GR_COORD_F32) as L:
+        out = gr.gr_diff_forward(L.handle, IDEAL)
+        assert out == pytest.approx(terms, rel=REL, abs=REL)
+        grads = []
+        for k in range(3):
+            gout = np.zeros(3, np.float32)
+            gout[k] = 1.0
+            d = cuda(np.full((len(xy), 2), np.nan, np.float32))
+            gr.gr_diff_backward(L.handle, gout, d)  # host gout: synchronous
+            grads.append(d.cpu().numpy())
+        for k, (g, ref) in enumerate(zip(grads, (g_eca, g_ml, g_ma))):
+            grad_close(g, ref, f"term {k}")
+        # a combination equals the combination of the parts (device gout, stream-ordered)
+        w = np.array([-1.0, 2.0, 0.5], np.float32)
+        d = cuda(np.zeros((len(xy), 2), np.float32))
+        gr.gr_diff_backward(L.handle, cuda(w), d)
+        grad_close(d.cpu().numpy(), w[0] * g_eca + w[1] * g_ml + w[2] * g_ma, "combination")
+
+
+def test_diff_pair_buffer_grows_and_update_invalidates():
+    # many crossings (long random edges) so the first forward outgrows its pair buffer
+    rng = np.random.default_rng(7)
+    V = 1500
+    xy = rng.random((V, 2)).astype(np.float32)
+    e = synth.add_random_edges(rng, V, np.zeros((0, 2), np.int32), 4000)
+    with gr.Layout(cuda(xy), cuda(e), coord_type=gr.GR_COORD_F32) as L:
+        for it in range(2):
+            terms, g_eca, _, _ = oracle.diff_terms_and_grads(xy, e, IDEAL)
+            out = gr.gr_diff_forward(L.handle, IDEAL)
+            assert out == pytest.approx(terms, rel=REL, abs=REL)
+            d = cuda(np.zeros((V, 2), np.float32))
+            gr.gr_diff_backward(L.handle, np.array([1, 0, 0], np.float32), d)
+            grad_close(d.cpu().numpy(), g_eca, f"iteration {it}")
+            xy = (xy * np.float32(0.5) + np.float32(0.25)).astype(np.float32)
+            L.update(cuda(xy))
+            with pytest.raises(gr.GrError):
+                gr.gr_diff_backward(L.handle, np.array([1, 0, 0], np.float32), d)
+
+
+def test_autograd_loss_gradient_and_descent():
+    import torch
+    from paper_2411_09809_gb300.autograd import ReadabilityTerms, readability_loss
+    xy_np, e = random_float_layout(5, 2000, 4500, 800)
+    terms_ref, g_eca, g_ml, g_ma = oracle.diff_terms_and_grads(xy_np, e, IDEAL)
+    mod = ReadabilityTerms(cuda(e), IDEAL)
+    xy = cuda(xy_np).requires_grad_(True)
+    terms = mod(xy)
+    loss = readability_loss(terms)
+    loss.backward()
+    assert terms.detach().cpu().numpy() == pytest.approx(terms_ref, rel=REL, abs=REL)
+    grad_close(xy.grad.cpu().numpy(), -g_eca + g_ml - g_ma, "loss gradient")
+    # a few small gradient steps lower the loss
+    opt = torch.optim.SGD([xy], lr=1e-5)
+    first = float(loss)
+    for _ in range(5):
+        opt.zero_grad()
+        loss = readability_loss(mod(xy))
+        loss.backward()
+        opt.step()
+    assert float(readability_loss(mod(xy.detach()))) < first
+    # a second forward before the first backward is an error, not a wrong gradient
+    t1 = mod(xy)
+    mod(xy)
+    with pytest.raises(RuntimeError):
+        readability_loss(t1).backward()
+    mod.close()
+
+
+def test_differentiable_workload_full_size():
+    L0 = synth.differentiable_layout()
+    xy, e = L0.xy, L0.edges
+    # one oracle pass (about a minute of host work): counts, terms and gradients
+    terms, g_eca, g_ml, g_ma, counts = oracle.diff_terms_and_grads(xy, e, IDEAL, return_counts=True)
+    with gr.Layout(cuda(xy), cuda(e), coord_type=gr.GR_COORD_F32) as L:
+        r = L.evaluate(FWD, IDEAL)
+        c = r.crossing.c
+        assert [c.proper, c.touching, c.collinear_overlaps, c.zero_length_edges, c.crossings] == list(counts)
+        assert r.crossing.E_ca == pytest.approx(terms[0], rel=REL)
+        assert r.M_l == pytest.approx(terms[1], rel=REL)
+        assert r.min_angle.M_a == pytest.approx(terms[2], rel=REL)
+        out = gr.gr_diff_forward(L.handle, IDEAL)
+        assert out == pytest.approx(terms, rel=REL, abs=REL)
+        d = cuda(np.zeros((len(xy), 2), np.float32))
+        gr.gr_diff_backward(L.handle, np.array([-1, 1, -1], np.float32), d)
+        grad_close(d.cpu().numpy(), -g_eca + g_ml - g_ma, "full size")
