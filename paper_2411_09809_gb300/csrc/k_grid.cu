@@ -25,6 +25,15 @@ namespace {
 constexpr int GP_WARPS = 8;  // warps per block of the pair kernel
 
 // a2 -- per-cell record counts.
+// Segment visited by thread slot i of n: i * (2^31 - 1) mod n, a bijection
+// for n < 2^31 - 1 (2^31 - 1 is prime; larger n keep their order) that spreads runs of long edges (random
+// edges appended after the short ones, say) over all warps instead of
+// leaving them to the last few, which walk them one by one.
+__device__ __forceinline__ int64_t spread_index(int64_t i, int64_t n) {
+    if (n >= 0x7fffffffll) return i;
+    return (int64_t)(((uint64_t)i * (0x7fffffffull % (uint64_t)n)) % (uint64_t)n);
+}
+
 __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ seg,
                                                     const DevAcc *__restrict__ acc, int k,
                                                     uint32_t *__restrict__ cell_cnt) {
@@ -32,7 +41,7 @@ __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ s
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
-        const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
+        const SegRec r = ok ? seg[spread_index(i, n)] : make_uint4(0, 0, 0, 0);
         warp_for_each_cell(r, 0, 0u, ok, k, 0u, [&](const int (&ids)[2], int nc, SegRec, int32_t, uint32_t) {
             atomicAdd(&cell_cnt[ids[0]], 1u);
             if (nc > 1) atomicAdd(&cell_cnt[ids[1]], 1u);
@@ -94,9 +103,10 @@ __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ se
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
-        const SegRec r = ok ? seg[i] : make_uint4(0, 0, 0, 0);
-        const int32_t eid = ok ? seg_eid[i] : 0;
-        const uint32_t th = ok ? seg_theta[i] : 0u;
+        const int64_t j = ok ? spread_index(i, n) : 0;
+        const SegRec r = ok ? seg[j] : make_uint4(0, 0, 0, 0);
+        const int32_t eid = ok ? seg_eid[j] : 0;
+        const uint32_t th = ok ? seg_theta[j] : 0u;
         warp_for_each_cell(r, eid, th, ok, k, 0u, [&](const int (&ids)[2], int nc, SegRec q, int32_t qe, uint32_t qt) {
             const uint32_t s0 = atomicAdd(&cell_fill[ids[0]], 1u);
             const uint32_t s1 = nc > 1 ? atomicAdd(&cell_fill[ids[1]], 1u) : 0u;

@@ -87,11 +87,19 @@ __device__ __forceinline__ int classify_kind(const RowSeg &r, const ColSeg &c) {
 }
 
 // Direction of the line through a segment with vector (dx, dy), as an angle
-// in [0, pi) in units of pi / 2^32 (FP64 atan2, rounded to the nearest unit).
+// in [0, pi) in units of pi / 2^32.  The vector is first turned into the
+// upper half-plane (exact: the line is the same), then FP32 atan2 of the
+// exactly representable integers (a few units in the last place of an angle
+// below pi, i.e. below 1e-6 rad) is rounded to the nearest unit.  Each
+// segment's direction is computed once and shared by every path, so all
+// paths derive the same crossing-angle terms.
 __device__ __forceinline__ uint32_t line_direction(int dx, int dy) {
-    double t = atan2((double)dy, (double)dx);  // (-pi, pi]
-    if (t < 0.0) t += 3.14159265358979323846;
-    const double u = rint(t * (4294967296.0 / 3.14159265358979323846));  // [0, 2^32]
+    if (dy < 0 || (dy == 0 && dx < 0)) {
+        dx = -dx;
+        dy = -dy;
+    }
+    const float t = atan2f((float)dy, (float)dx);  // [0, pi]
+    const double u = rint((double)t * (4294967296.0 / 3.14159265358979323846));  // [0, 2^32]
     return (uint32_t)(unsigned long long)u;  // 2^32 (angle pi) wraps to 0
 }
 
