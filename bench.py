@@ -40,6 +40,8 @@ L2_FLUSH_BYTES = 256 << 20
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
+LONG_PAIRS = {"auto": 0, "allpairs": 1, "grid": 2}
+
 WORKLOADS = {
     "large_sparse": ("large_sparse_layout", 64),
     "dense_long_edge": ("dense_long_edge_layout", 256),
@@ -314,7 +316,8 @@ def run_batched(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
-    B = gr.Batch(v_off, e_off, dxy, ded, stream=stream.cuda_stream)
+    B = gr.Batch(v_off, e_off, dxy, ded, gr.gr_options(0, 0, 0, 0, LONG_PAIRS[args.long_pairs]),
+                 stream=stream.cuda_stream)
     create_s = time.perf_counter() - t0
 
     def step():
@@ -347,13 +350,13 @@ def run_batched(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     # the same layouts one by one (a fixed sample, scaled to the batch)
-    sample = list(range(0, n, max(1, n // 256)))
+    sample = [] if args.no_single_loop else list(range(0, n, max(1, n // 256)))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in sample:
         with gr.Layout(dxy[v_off[i]:v_off[i + 1]], ded[e_off[i]:e_off[i + 1]]) as one:
             one.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
-    single_s = (time.perf_counter() - t0) * n / len(sample)
+    single_s = (time.perf_counter() - t0) * n / max(1, len(sample))
     B.close()
     if rank != 0:
         return
@@ -370,7 +373,7 @@ def run_batched(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "resolved_pairs_per_s": world * pairs / (ms / 1e3),
         "single_layout_loop": {"layouts_per_s": n / single_s, "sample_layouts": len(sample),
-                               "speedup_of_batch": (n / (ms / 1e3)) / (n / single_s)},
+                               "speedup_of_batch": (n / (ms / 1e3)) / (n / single_s)} if sample else None,
         "create_s": create_s,
         "gpu_launches": launches,
         "clocks": clk,
@@ -627,7 +630,8 @@ def run_ours(args, rank, world, local_rank):
     edges = torch.from_numpy(L.edges).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    lay = gr.Layout(xy, edges, gr.gr_options(0, args.cell_log2, 0, 1), stream=stream.cuda_stream)
+    lay = gr.Layout(xy, edges, gr.gr_options(0, args.cell_log2, 0, 1, LONG_PAIRS[args.long_pairs]),
+                    stream=stream.cuda_stream)
 
     def step():
         lay.update(xy)
@@ -725,9 +729,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large_sparse")
     ap.add_argument("--cell-log2", type=int, default=0)
+    ap.add_argument("--long-pairs", choices=sorted(LONG_PAIRS), default="auto",
+                    help="where pairs of two long segments are tested (default: the cost model decides)")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (for profiler runs)")
+    ap.add_argument("--no-single-loop", action="store_true",
+                    help="batched workload: skip the one-layout-at-a-time comparison (for profiler runs)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
     if args.impl == "reference":

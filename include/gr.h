@@ -78,11 +78,22 @@ typedef enum {
     GR_PATH_ALLPAIRS = 2  /* tiled brute force over all edge pairs */
 } gr_path;
 
+/* Where the grid path tests pairs of two long segments (segments spanning
+ * more than two cell lines): a grid cannot prune those, so by default the
+ * cost model may send them to all-pairs tiles over the list of long
+ * segments instead.  Either choice gives the same exact counts. */
+typedef enum {
+    GR_LONG_AUTO = 0,      /* cost model picks */
+    GR_LONG_ALLPAIRS = 1,  /* all-pairs tiles over the long segments */
+    GR_LONG_GRID = 2       /* in the grid cells with every other pair */
+} gr_long_pairs;
+
 typedef struct {
     int32_t crossing_path;  /* gr_path; 0 = auto */
     int32_t cell_log2;      /* crossing grid cell side 2^k, k in [6, 16]; 0 = auto */
     int32_t occlusion_path; /* gr_path for occlusion; 0 = auto */
     int32_t profile;        /* non-zero: enable phase timing at creation */
+    int32_t long_pairs;     /* gr_long_pairs; 0 = auto */
 } gr_options;
 
 typedef struct {

@@ -10,12 +10,17 @@
 //               pair kernel cover all layouts in single launches; the pair
 //               kernel is persistent (one block per SM slot, each warp a
 //               contiguous run of work items) and writes one partial per work
-//               item, reduced per layout in a fixed order;
+//               item, reduced per layout in a fixed order.  Pairs of two
+//               long segments (spanning more than two major lines of their
+//               layout's grid) skip the grid: every layout's long segments
+//               are listed contiguously and one persistent kernel runs the
+//               all-pairs tiles of all those lists;
 //   occlusion   one grid per layout with cells of side >= d;
 //   min angle, edge length variation: one block per layout.
-// The cell size k_l of every layout comes from a cost model on the layout's
-// segment count and total L1 length (records n + L1 / w against candidate
-// pairs >= R^2 / (2C)), shifted by a global offset that an autotuner picks
+// The cell size k_l of every layout comes from the cost model of the single
+// layout (grid_cost: records, short-involved candidate pairs, cells and
+// long-long pairs, from the layout's segment length histogram), shifted by a
+// global offset that an autotuner picks
 // by timing the crossing pipeline at creation (cached in the file named by
 // GR_TUNE_CACHE, when set).  The whole evaluation is captured once into a
 // CUDA graph and replayed; every kernel reads the sizes it needs from device
@@ -31,6 +36,7 @@
 #include <string>
 #include <vector>
 
+#include "allpairs_common.cuh"
 #include "grid_common.cuh"
 
 using namespace gr;
@@ -111,27 +117,37 @@ __global__ void __launch_bounds__(256) k_batch_gather(const int2 *__restrict__ x
     }
 }
 
-// Per-layout segment counts and total L1 length, for the plan.
+// Per-layout segment counts and total L1 length, and both by major-axis
+// length class [2^b, 2^(b+1)) (hn, hl1: 16 per layout), for the plan.
 __global__ void __launch_bounds__(256) k_batch_stats(const SegRec *__restrict__ seg,
                                                      const uint32_t *__restrict__ seg_layout,
                                                      const DevAcc *__restrict__ acc, unsigned long long *nseg,
-                                                     unsigned long long *l1) {
+                                                     unsigned long long *l1, uint32_t *hn, unsigned long long *hl1) {
     const int64_t n = acc->n_seg;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const SegRec r = seg[i];
         const uint32_t l = seg_layout[i];
+        const int dx = abs(px(r.y) - px(r.x)), dy = abs(py(r.y) - py(r.x));
+        const int b = 31 - __clz(max(dx, dy));
         atomicAdd(&nseg[l], 1ull);
-        atomicAdd(&l1[l], (unsigned long long)(abs(px(r.y) - px(r.x)) + abs(py(r.y) - py(r.x))));
+        atomicAdd(&l1[l], (unsigned long long)(dx + dy));
+        atomicAdd(&hn[16 * (uint64_t)l + b], 1u);
+        atomicAdd(&hl1[16 * (uint64_t)l + b], (unsigned long long)(dx + dy));
     }
 }
 
-// a2 over all layouts: segment s walks layout l's grid (k_l, cells from cbase[l]).
+// a2 over all layouts: segment s walks layout l's grid (k_l, cells from
+// cbase[l]); counts per cell (all records, long ones) and long segments per
+// layout (warp-aggregated over lanes of the same layout).
 __global__ void __launch_bounds__(256) k_batch_grid_count(const SegRec *__restrict__ seg,
                                                           const uint32_t *__restrict__ seg_layout,
                                                           const DevAcc *__restrict__ acc, const int32_t *__restrict__ kl,
+                                                          const int32_t *__restrict__ split_l,
                                                           const uint32_t *__restrict__ cbase,
-                                                          uint32_t *__restrict__ cell_cnt) {
+                                                          uint32_t *__restrict__ cell_cnt, uint32_t *__restrict__ cell_nl,
+                                                          uint32_t *__restrict__ nlong) {
     const int64_t n = acc->n_seg;
+    const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
@@ -139,35 +155,63 @@ __global__ void __launch_bounds__(256) k_batch_grid_count(const SegRec *__restri
         const uint32_t l = ok ? seg_layout[i] : 0u;
         const int k = ok ? kl[l] : 16;
         const uint32_t cb = ok ? cbase[l] : 0u;
-        warp_for_each_cell(r, 0, 0u, ok, k, cb, [&](const int (&ids)[2], int nc, SegRec, int32_t, uint32_t) {
-            atomicAdd(&cell_cnt[ids[0]], 1u);
-            if (nc > 1) atomicAdd(&cell_cnt[ids[1]], 1u);
-        });
+        const bool split = ok && split_l[l] != 0;
+        const bool lng = split && is_long_seg(r, k);
+        const unsigned ml = __ballot_sync(0xffffffffu, lng);
+        if (lng) {
+            const unsigned same = __match_any_sync(ml, l);
+            if (lane == __ffs(same) - 1) atomicAdd(&nlong[l], (uint32_t)__popc(same));
+        }
+        warp_for_each_cell(r, 0, 0u, ok, k, cb, split,
+                           [&](const int (&ids)[2], int nc, SegRec, int32_t, uint32_t, bool lng_cell) {
+                               atomicAdd(&cell_cnt[ids[0]], 1u);
+                               if (nc > 1) atomicAdd(&cell_cnt[ids[1]], 1u);
+                               if (lng_cell) {
+                                   atomicAdd(&cell_nl[ids[0]], 1u);
+                                   if (nc > 1) atomicAdd(&cell_nl[ids[1]], 1u);
+                               }
+                           });
+    }
+}
+
+// All-pairs tiles of every layout's long-segment list (from the scanned
+// list offsets long_off): T_l (T_l + 1) / 2 with T_l = ceil(n_l / AS_ROWS)
+// (the small tiles: most lists are short).
+__global__ void __launch_bounds__(256) k_batch_long_tiles(const uint32_t *__restrict__ long_off, int64_t L,
+                                                          uint32_t *__restrict__ tile_cnt) {
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t nl = long_off[l + 1] - long_off[l];
+        const uint64_t T = (nl + AS_ROWS - 1) / AS_ROWS;
+        tile_cnt[l] = nl < 2 ? 0u : (uint32_t)(T * (T + 1) / 2);
     }
 }
 
 // Work items per cell (tile pairs), and the candidate pairs of each layout.
-__global__ void __launch_bounds__(256) k_batch_cell_items(const uint32_t *__restrict__ cell_off, uint32_t C,
+// (Tile pairs with a short row tile, as in the single-layout grid.)
+__global__ void __launch_bounds__(256) k_batch_cell_items(const uint32_t *__restrict__ cell_off,
+                                                          const uint32_t *__restrict__ cell_nl, uint32_t C,
                                                           const uint32_t *__restrict__ cbase, int64_t L,
                                                           uint32_t *__restrict__ item_cnt,
                                                           unsigned long long *work, DevAcc *acc) {
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-        const uint32_t n = cell_off[c + 1] - cell_off[c];
-        const uint64_t T = (n + TILE - 1) / TILE;
-        const uint64_t items = n < 2 ? 0 : T * (T + 1) / 2;
-        if (items > 0x7fffffffull) atomicOr(&acc->grid_flags, GF_ITEMS_OVERFLOW);
+        const uint64_t n = cell_off[c + 1] - cell_off[c];
+        const uint64_t ns = n - cell_nl[c];
+        bool tiles_over;
+        const uint64_t items = cell_item_count(n, ns, &tiles_over);
+        if (items > 0x7fffffffull || tiles_over) atomicOr(&acc->grid_flags, GF_ITEMS_OVERFLOW);
         item_cnt[c] = (uint32_t)min(items, (uint64_t)0x7fffffffull);
-        if (n >= 2) {
+        if (items > 0) {
             const int64_t l = find_segment_u32(cbase, L, c);
-            atomicAdd(&work[l], (unsigned long long)n * (n - 1) / 2);
+            atomicAdd(&work[l], (unsigned long long)(ns * (ns - 1) / 2 + ns * (n - ns)));
         }
     }
 }
 
 // Descriptor of every work item: {record offset, records of the cell,
-// layout, ti << 16 | tj} and {local cell, k, 0, 0}.
+// layout, ti << 16 | tj} and {local cell, k, short records, 0}.
 __global__ void __launch_bounds__(256) k_batch_item_descs(const uint32_t *__restrict__ item_off,
-                                                          const uint32_t *__restrict__ cell_off, uint32_t C,
+                                                          const uint32_t *__restrict__ cell_off,
+                                                          const uint32_t *__restrict__ cell_nl, uint32_t C,
                                                           const uint32_t *__restrict__ cbase, int64_t L,
                                                           const int32_t *__restrict__ kl, uint64_t cap,
                                                           uint4 *__restrict__ desc, DevAcc *acc) {
@@ -180,27 +224,32 @@ __global__ void __launch_bounds__(256) k_batch_item_descs(const uint32_t *__rest
             continue;
         }
         const int64_t l = find_segment_u32(cbase, L, c);
-        const uint32_t base = cell_off[c], n = cell_off[c + 1] - base;
-        const uint32_t T = (n + TILE - 1) / TILE;
-        const uint4 hi = make_uint4(c - cbase[l], (uint32_t)kl[l], 0u, 0u);
-        for (uint32_t tj = 0; tj < T && q < e; ++tj)
-            for (uint32_t ti = 0; ti <= tj && q < e; ++ti, ++q) {
-                desc[2 * (uint64_t)q] = make_uint4(base, n, (uint32_t)l, (ti << 16) | tj);
-                desc[2 * (uint64_t)q + 1] = hi;
-            }
+        const uint32_t base = cell_off[c], n = cell_off[c + 1] - base, ns = n - cell_nl[c];
+        const uint4 hi = make_uint4(c - cbase[l], (uint32_t)kl[l], ns, 0u);
+        cell_item_words(n, ns, q, e, [&](uint32_t i, uint32_t word) {
+            desc[2 * (uint64_t)i] = make_uint4(base, n, (uint32_t)l, word);
+            desc[2 * (uint64_t)i + 1] = hi;
+        });
     }
 }
 
-// a4 over all layouts.
+// a4 over all layouts: short records from each cell's start, long ones from
+// its end (one 64-bit counter per cell); every long segment is also copied
+// to its layout's long list.
 __global__ void __launch_bounds__(256) k_batch_grid_fill(const SegRec *__restrict__ seg,
                                                          const int32_t *__restrict__ seg_eid,
                                                          const uint32_t *__restrict__ seg_theta,
                                                          const uint32_t *__restrict__ seg_layout,
                                                          const DevAcc *__restrict__ acc, const int32_t *__restrict__ kl,
+                                                         const int32_t *__restrict__ split_l,
                                                          const uint32_t *__restrict__ cbase,
                                                          const uint32_t *__restrict__ cell_off,
-                                                         uint32_t *__restrict__ cell_fill, uint64_t cap,
-                                                         GridRec *__restrict__ rec, uint32_t *status) {
+                                                         unsigned long long *__restrict__ cell_fill, uint64_t cap,
+                                                         GridRec *__restrict__ rec,
+                                                         const uint32_t *__restrict__ long_off,
+                                                         uint32_t *__restrict__ long_fill,
+                                                         SegRec *__restrict__ seg_long,
+                                                         uint32_t *__restrict__ theta_long, uint32_t *status) {
     const int64_t n = acc->n_seg;
     if (acc->records > cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_OVERFLOW);
@@ -215,17 +264,31 @@ __global__ void __launch_bounds__(256) k_batch_grid_fill(const SegRec *__restric
         const uint32_t l = ok ? seg_layout[i] : 0u;
         const int k = ok ? kl[l] : 16;
         const uint32_t cb = ok ? cbase[l] : 0u;
-        warp_for_each_cell(r, eid, th, ok, k, cb, [&](const int (&ids)[2], int nc, SegRec q, int32_t qe, uint32_t qt) {
-            const uint32_t s0 = atomicAdd(&cell_fill[ids[0]], 1u);
-            const uint32_t s1 = nc > 1 ? atomicAdd(&cell_fill[ids[1]], 1u) : 0u;
-            const uint32_t o0 = cell_off[ids[0]];
-            const uint32_t o1 = nc > 1 ? cell_off[ids[1]] : 0u;
-            GridRec g;
-            g.s = q;
-            g.x = make_uint4((uint32_t)qe, qt, 0u, 0u);
-            rec[o0 + s0] = g;
-            if (nc > 1) rec[o1 + s1] = g;
-        });
+        const bool split = ok && split_l[l] != 0;
+        if (split && is_long_seg(r, k)) {
+            const uint32_t pos = long_off[l] + atomicAdd(&long_fill[l], 1u);
+            seg_long[pos] = r;
+            theta_long[pos] = th;
+        }
+        warp_for_each_cell(r, eid, th, ok, k, cb, split,
+                           [&](const int (&ids)[2], int nc, SegRec q, int32_t qe, uint32_t qt, bool lng) {
+                               const unsigned long long inc = lng ? (1ull << 32) : 1ull;
+                               const unsigned long long s0 = atomicAdd(&cell_fill[ids[0]], inc);
+                               const unsigned long long s1 = nc > 1 ? atomicAdd(&cell_fill[ids[1]], inc) : 0ull;
+                               uint32_t p0, p1 = 0;
+                               if (lng) {
+                                   p0 = cell_off[ids[0] + 1] - 1u - (uint32_t)(s0 >> 32);
+                                   if (nc > 1) p1 = cell_off[ids[1] + 1] - 1u - (uint32_t)(s1 >> 32);
+                               } else {
+                                   p0 = cell_off[ids[0]] + (uint32_t)s0;
+                                   if (nc > 1) p1 = cell_off[ids[1]] + (uint32_t)s1;
+                               }
+                               GridRec g;
+                               g.s = q;
+                               g.x = make_uint4((uint32_t)qe, qt, 0u, 0u);
+                               rec[p0] = g;
+                               if (nc > 1) rec[p1] = g;
+                           });
     }
 }
 
@@ -253,8 +316,8 @@ __global__ void __launch_bounds__(BP_WARPS * 32, 4) k_batch_grid_pairs(const Gri
         const int k = (int)d1.y, G = 65536 >> k;
         const int cell = (int)d1.x;
         PairCounts pc;
-        grid_item<false>(rec + d0.x, (int)d0.y, (int)(d0.w >> 16), (int)(d0.w & 0xffffu), (cell % G) << k,
-                         (cell / G) << k, k, cs[wid], ideal, pc, PerEdge{});
+        grid_item<false>(rec + d0.x, item_tiles(d0.y, d1.z, d0.w), (cell % G) << k, (cell / G) << k, k, cs[wid],
+                         ideal, pc, PerEdge{});
         const uint32_t p = warp_sum<uint32_t>(pc.proper), t = warp_sum<uint32_t>(pc.touching);
         const uint32_t c = warp_sum<uint32_t>(pc.collinear);
         const uint64_t dv = warp_sum<uint64_t>(pc.dev);
@@ -266,13 +329,52 @@ __global__ void __launch_bounds__(BP_WARPS * 32, 4) k_batch_grid_pairs(const Gri
     }
 }
 
-// Per layout: the crossing partials of its items in a fixed order, plus the
-// occlusion count, into the result; metrics not evaluated get their defaults.
+// The all-pairs tiles of every layout's long list (persistent, one tile per
+// block at a time): tile t belongs to the layout l with tile_off[l] <= t <
+// tile_off[l + 1]; its tallies are added to ll[4 l ..] (proper, touching,
+// collinear, deviation sum; integers, so the order does not matter).  Does
+// nothing when the records outgrew their buffer (the lists were not written).
+__global__ void __launch_bounds__(AS_THREADS) k_batch_long_pairs(const SegRec *__restrict__ seg_long,
+                                                                 const uint32_t *__restrict__ theta_long,
+                                                                 const uint32_t *__restrict__ long_off,
+                                                                 const uint32_t *__restrict__ tile_off, int64_t L,
+                                                                 const DevAcc *__restrict__ acc, uint64_t rec_cap,
+                                                                 uint32_t ideal, unsigned long long *__restrict__ ll) {
+    __shared__ AllPairsSmem<AS_ROWS> sm;
+    __shared__ uint64_t sh[32];
+    if (acc->records > rec_cap) return;
+    const uint32_t tiles = tile_off[L];
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t l = find_segment_u32(tile_off, L, t);
+        const uint32_t o = long_off[l];
+        int bi, bj;
+        decode_tile((int64_t)(t - tile_off[l]), bi, bj);
+        PairCounts pc;
+        allpairs_tile<AS_THREADS, AS_RPT>(seg_long + o, theta_long + o, (int)(long_off[l + 1] - o), bi, bj, ideal,
+                                          sm, pc);
+        const uint64_t p = block_sum<uint64_t>(pc.proper, sh);
+        const uint64_t q = block_sum<uint64_t>(pc.touching, sh);
+        const uint64_t c = block_sum<uint64_t>(pc.collinear, sh);
+        const uint64_t d = block_sum<uint64_t>(pc.dev, sh);
+        if (threadIdx.x == 0) {
+            if (p) atomicAdd(&ll[4 * l + 0], (unsigned long long)p);
+            if (q) atomicAdd(&ll[4 * l + 1], (unsigned long long)q);
+            if (c) atomicAdd(&ll[4 * l + 2], (unsigned long long)c);
+            if (d) atomicAdd(&ll[4 * l + 3], (unsigned long long)d);
+        }
+    }
+}
+
+// Per layout: the crossing partials of its items in a fixed order and its
+// long-long tallies, plus the occlusion count, into the result; metrics not
+// evaluated get their defaults.
 __global__ void __launch_bounds__(256) k_batch_finalize(const ItemPart *__restrict__ part,
                                                         const uint32_t *__restrict__ item_off,
                                                         const uint32_t *__restrict__ cell_off,
                                                         const uint32_t *__restrict__ cbase, const int32_t *__restrict__ kl,
                                                         const unsigned long long *__restrict__ work,
+                                                        const unsigned long long *__restrict__ ll,
+                                                        const uint32_t *__restrict__ long_off,
                                                         const uint64_t *__restrict__ occl, int64_t L, uint32_t metrics,
                                                         double ideal, int64_t d, uint64_t cap,
                                                         gr_result *__restrict__ res) {
@@ -294,6 +396,11 @@ __global__ void __launch_bounds__(256) k_batch_finalize(const ItemPart *__restri
         gr_result &r = res[l];
         r.metrics = metrics;
         if (metrics & GR_METRIC_CROSSINGS) {
+            p += ll[4 * l + 0];
+            t += ll[4 * l + 1];
+            c += ll[4 * l + 2];
+            dv += ll[4 * l + 3];
+            const uint64_t nl = long_off[l + 1] - long_off[l];
             r.crossing_path = GR_PATH_GRID;
             r.cell_log2 = kl[l];
             const uint64_t ec = p + t;
@@ -301,7 +408,7 @@ __global__ void __launch_bounds__(256) k_batch_finalize(const ItemPart *__restri
             r.crossing.c.proper = (int64_t)p;
             r.crossing.c.touching = (int64_t)t;
             r.crossing.c.collinear_overlaps = (int64_t)c;
-            r.crossing.c.pairs_tested = (int64_t)work[l];
+            r.crossing.c.pairs_tested = (int64_t)(work[l] + nl * (nl - (nl > 0)) / 2);
             const double dev = (double)dv * kAngleUnit;
             r.crossing.angle_dev_sum = dev;
             r.crossing.ideal_rad = ideal;
@@ -353,13 +460,26 @@ struct gr_batch {
     DevAcc *h_acc = nullptr;
     // crossing plan
     std::vector<uint64_t> nseg_l, l1_l;
-    std::vector<int32_t> k_l;
+    std::vector<int32_t> k_l, split_l;
     int32_t *d_k = nullptr;
+    int32_t *d_split = nullptr;  // [L] long-long pairs on the all-pairs tiles
     uint32_t *d_cbase = nullptr;
     uint32_t C = 0, C_cap = 0;
     int delta = 0;
     unsigned long long *d_nseg = nullptr, *d_l1 = nullptr, *d_work = nullptr;
-    uint32_t *cell_off = nullptr, *item_off = nullptr, *cell_fill = nullptr;
+    uint32_t *d_hn = nullptr;            // [16 L] segments by major-length class
+    unsigned long long *d_hl1 = nullptr; // [16 L] their L1 length
+    std::vector<uint32_t> hn_l;
+    std::vector<uint64_t> hl1_l;
+    uint32_t *cell_off = nullptr, *cell_nl = nullptr, *item_off = nullptr;
+    unsigned long long *cell_fill = nullptr;
+    // long segments: per-layout lists and their all-pairs tiles
+    uint32_t *long_off = nullptr;   // [L + 1] counts, then offsets
+    uint32_t *long_fill = nullptr;  // [L]
+    uint32_t *tile_off = nullptr;   // [L + 1] tiles, then offsets
+    SegRec *seg_long = nullptr;     // [E]
+    uint32_t *theta_long = nullptr; // [E]
+    unsigned long long *d_ll = nullptr;  // [4 L] long-long tallies
     GridRec *rec = nullptr;
     uint64_t rec_cap = 0;
     uint4 *desc = nullptr;
@@ -437,9 +557,11 @@ void free_batch(gr_batch *B) {
     drop_graph(B);
     Buffers &b = B->b;
     void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.deg, b.deg_fill, b.dirs,
-                    b.scan_tmp, b.scan_tmp_side, B->seg_layout, B->d_voff, B->d_eoff, B->d_res, B->d_k, B->d_cbase,
-                    B->d_nseg, B->d_l1, B->d_work, B->cell_off, B->item_off, B->cell_fill, B->rec, B->desc,
-                    B->parts, B->d_ko, B->d_obase, B->ocell_off, B->ocell_fill, B->opts, B->olay, B->occl};
+                    b.scan_tmp, b.scan_tmp_side, B->seg_layout, B->d_voff, B->d_eoff, B->d_res, B->d_k, B->d_split, B->d_cbase,
+                    B->d_nseg, B->d_l1, B->d_work, B->d_hn, B->d_hl1, B->cell_off, B->cell_nl, B->item_off,
+                    B->cell_fill, B->long_off, B->long_fill, B->tile_off, B->seg_long, B->theta_long, B->d_ll,
+                    B->rec, B->desc, B->parts, B->d_ko, B->d_obase, B->ocell_off, B->ocell_fill, B->opts, B->olay,
+                    B->occl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (B->h_res) cudaFreeHost(B->h_res);
@@ -452,24 +574,31 @@ void free_batch(gr_batch *B) {
     delete B;
 }
 
-// Cell size of each layout: the k minimising 24 R + 3 R^2 / (2 C) + 2 C with
-// R = n + L1 / 2^k records and C = (2^16 / 2^k)^2 cells (the same model as a
-// single layout; ties go to the coarser grid), shifted by the autotuned
-// offset `delta`.
+// Cell size of each layout: the k minimising grid_cost (the single-layout
+// model; ties go to the coarser grid), shifted by the autotuned offset
+// `delta`; and whether its long-long pairs go to the all-pairs tiles (the
+// better form at that cell size; one launch serves every layout, so no fixed
+// cost per layout).
 void plan_cells(gr_batch *B) {
     B->k_l.assign(B->L, 16);
+    B->split_l.assign(B->L, 0);
     uint64_t C = 0;
     for (int64_t l = 0; l < B->L; ++l) {
         const double n = (double)B->nseg_l[l], l1 = (double)B->l1_l[l];
+        const uint32_t *hn = &B->hn_l[16 * l];
+        const uint64_t *hl = &B->hl1_l[16 * l];
         int best = 16;
         double bestc = 1e300;
-        for (int k = 16; k >= 6; --k) {
-            const double R = n + l1 / double(1 << k);
-            const double Cl = double(65536 >> k) * double(65536 >> k);
-            const double cost = 24.0 * R + 3.0 * R * R / (2.0 * Cl) + 2.0 * Cl;
-            if (cost < bestc) { bestc = cost; best = k; }
-        }
+        for (int k = 16; k >= 6; --k)
+            for (bool split : {false, true}) {
+                const double cost = grid_cost(n, l1, hn, hl, k, split) - (split ? kSplitCost : 0.0);
+                if (cost < bestc) { bestc = cost; best = k; }
+            }
         B->k_l[l] = std::min(16, std::max(6, best + B->delta));
+        const int k = B->k_l[l];
+        B->split_l[l] = grid_cost(n, l1, hn, hl, k, true) - kSplitCost < grid_cost(n, l1, hn, hl, k, false) ? 1 : 0;
+        if (B->opt.long_pairs == GR_LONG_ALLPAIRS) B->split_l[l] = 1;
+        else if (B->opt.long_pairs == GR_LONG_GRID) B->split_l[l] = 0;
         C += (uint64_t)(65536 >> B->k_l[l]) * (uint64_t)(65536 >> B->k_l[l]);
     }
     // keep the scan within its 2^26-entry limit: coarsen the finest grids
@@ -478,7 +607,7 @@ void plan_cells(gr_batch *B) {
         for (int64_t l = 1; l < B->L; ++l)
             if (B->k_l[l] < B->k_l[arg]) arg = l;
         const uint64_t before = (uint64_t)(65536 >> B->k_l[arg]) * (uint64_t)(65536 >> B->k_l[arg]);
-        B->k_l[arg] += 1;
+        B->k_l[arg] += 1;  // (split stays a valid choice: it only moves pairs between kernels)
         C -= before - (uint64_t)(65536 >> B->k_l[arg]) * (uint64_t)(65536 >> B->k_l[arg]);
     }
     B->C = (uint32_t)C;
@@ -488,10 +617,12 @@ gr_status upload_cells(gr_batch *B) {
     std::vector<uint32_t> cb(B->L + 1, 0);
     for (int64_t l = 0; l < B->L; ++l) cb[l + 1] = cb[l] + (uint32_t)((65536 >> B->k_l[l]) * (65536 >> B->k_l[l]));
     B_CU(cudaMemcpy(B->d_k, B->k_l.data(), sizeof(int32_t) * B->L, cudaMemcpyHostToDevice));
+    B_CU(cudaMemcpy(B->d_split, B->split_l.data(), sizeof(int32_t) * B->L, cudaMemcpyHostToDevice));
     B_CU(cudaMemcpy(B->d_cbase, cb.data(), sizeof(uint32_t) * (B->L + 1), cudaMemcpyHostToDevice));
     gr_status st;
     if (B->C_cap < B->C) {
         if ((st = balloc(&B->cell_off, (size_t)B->C + 1)) != GR_OK) return st;
+        if ((st = balloc(&B->cell_nl, (size_t)B->C)) != GR_OK) return st;
         if ((st = balloc(&B->item_off, (size_t)B->C + 1)) != GR_OK) return st;
         if ((st = balloc(&B->cell_fill, (size_t)B->C)) != GR_OK) return st;
         B->C_cap = B->C;
@@ -504,29 +635,42 @@ gr_status upload_cells(gr_batch *B) {
 void enqueue_cross_count(gr_batch *B, cudaStream_t s) {
     Buffers &b = B->b;
     cudaMemsetAsync(B->cell_off, 0, sizeof(uint32_t) * ((size_t)B->C + 1), s);
+    cudaMemsetAsync(B->cell_nl, 0, sizeof(uint32_t) * (size_t)B->C, s);
+    cudaMemsetAsync(B->long_off, 0, sizeof(uint32_t) * ((size_t)B->L + 1), s);
     cudaMemsetAsync(B->d_work, 0, sizeof(unsigned long long) * B->L, s);
-    count_launches(3);
+    count_launches(4);
     k_batch_grid_count<<<grid_for(B->E, 256, 152 * 16), 256, 0, s>>>(b.seg, B->seg_layout, b.acc, B->d_k,
-                                                                     B->d_cbase, B->cell_off);
+                                                                     B->d_split, B->d_cbase, B->cell_off,
+                                                                     B->cell_nl, B->long_off);
     launch_scan_u32(B->cell_off, B->cell_off, B->C, b.scan_tmp, &b.acc->records, &b.acc->eval_status, s);
-    k_batch_cell_items<<<grid_for(B->C, 256, 152 * 8), 256, 0, s>>>(B->cell_off, B->C, B->d_cbase, B->L, B->item_off,
-                                                                    B->d_work, b.acc);
+    k_batch_cell_items<<<grid_for(B->C, 256, 152 * 8), 256, 0, s>>>(B->cell_off, B->cell_nl, B->C, B->d_cbase, B->L,
+                                                                    B->item_off, B->d_work, b.acc);
     launch_scan_u32(B->item_off, B->item_off, B->C, b.scan_tmp, &b.acc->grid_items, &b.acc->eval_status, s);
-    k_batch_item_descs<<<grid_for(B->C, 256, 152 * 8), 256, 0, s>>>(B->item_off, B->cell_off, B->C, B->d_cbase, B->L,
-                                                                    B->d_k, B->items_cap, B->desc, b.acc);
+    k_batch_item_descs<<<grid_for(B->C, 256, 152 * 8), 256, 0, s>>>(B->item_off, B->cell_off, B->cell_nl, B->C,
+                                                                    B->d_cbase, B->L, B->d_k, B->items_cap, B->desc,
+                                                                    b.acc);
+    launch_scan_u32(B->long_off, B->long_off, B->L, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
+    k_batch_long_tiles<<<grid_for(B->L, 256, 152 * 8), 256, 0, s>>>(B->long_off, B->L, B->tile_off);
+    launch_scan_u32(B->tile_off, B->tile_off, B->L, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
 }
 
 // Scatter (a4) and the per-cell pair kernel (a6) of all layouts.
 void enqueue_cross_pairs(gr_batch *B, uint32_t ideal_u, cudaStream_t s) {
     Buffers &b = B->b;
-    cudaMemsetAsync(B->cell_fill, 0, sizeof(uint32_t) * B->C, s);
-    count_launches(2);
+    cudaMemsetAsync(B->cell_fill, 0, sizeof(unsigned long long) * B->C, s);
+    cudaMemsetAsync(B->long_fill, 0, sizeof(uint32_t) * B->L, s);
+    cudaMemsetAsync(B->d_ll, 0, sizeof(unsigned long long) * 4 * B->L, s);
+    count_launches(3);
     k_batch_grid_fill<<<grid_for(B->E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, B->seg_layout,
-                                                                    b.acc, B->d_k, B->d_cbase, B->cell_off,
-                                                                    B->cell_fill, B->rec_cap, B->rec,
+                                                                    b.acc, B->d_k, B->d_split, B->d_cbase,
+                                                                    B->cell_off, B->cell_fill, B->rec_cap, B->rec,
+                                                                    B->long_off,
+                                                                    B->long_fill, B->seg_long, B->theta_long,
                                                                     &b.acc->eval_status);
     k_batch_grid_pairs<<<152 * 4, BP_WARPS * 32, 0, s>>>(B->rec, B->desc, B->item_off + B->C, b.acc, B->rec_cap,
                                                          B->items_cap, ideal_u, B->parts);
+    k_batch_long_pairs<<<152 * 8, AS_THREADS, 0, s>>>(B->seg_long, B->theta_long, B->long_off, B->tile_off, B->L,
+                                                      b.acc, B->rec_cap, ideal_u, B->d_ll);
 }
 
 // Grows the record and work-item buffers to the current sizes (read back).
@@ -607,8 +751,8 @@ void enqueue_evaluate(gr_batch *B, uint32_t metrics, double ideal, uint32_t idea
     cudaStreamWaitEvent(s, B->ev_join, 0);
     count_launches(1);
     k_batch_finalize<<<grid_for(B->L, 1, 152 * 16), 256, 0, s>>>(B->parts, B->item_off, B->cell_off, B->d_cbase, B->d_k,
-                                                                 B->d_work, B->occl, B->L, metrics, ideal, d,
-                                                                 B->items_cap, B->d_res);
+                                                                 B->d_work, B->d_ll, B->long_off, B->occl, B->L,
+                                                                 metrics, ideal, d, B->items_cap, B->d_res);
 }
 
 gr_status enqueue_inputs(gr_batch *B, const void *xy, const int32_t *edges) {
@@ -796,10 +940,19 @@ gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_of
     B_TRY(balloc(&B->d_eoff, (size_t)n_layouts + 1));
     B_TRY(balloc(&B->d_res, (size_t)n_layouts));
     B_TRY(balloc(&B->d_k, (size_t)n_layouts));
+    B_TRY(balloc(&B->d_split, (size_t)n_layouts));
     B_TRY(balloc(&B->d_cbase, (size_t)n_layouts + 1));
     B_TRY(balloc(&B->d_nseg, (size_t)n_layouts));
     B_TRY(balloc(&B->d_l1, (size_t)n_layouts));
     B_TRY(balloc(&B->d_work, (size_t)n_layouts));
+    B_TRY(balloc(&B->d_hn, 16 * (size_t)n_layouts));
+    B_TRY(balloc(&B->d_hl1, 16 * (size_t)n_layouts));
+    B_TRY(balloc(&B->long_off, (size_t)n_layouts + 1));
+    B_TRY(balloc(&B->long_fill, (size_t)n_layouts));
+    B_TRY(balloc(&B->tile_off, (size_t)n_layouts + 1));
+    B_TRY(balloc(&B->d_ll, 4 * (size_t)n_layouts));
+    B_TRY(balloc(&B->seg_long, (size_t)E));
+    B_TRY(balloc(&B->theta_long, (size_t)E));
     B_TRY(balloc(&B->d_ko, (size_t)n_layouts));
     B_TRY(balloc(&B->d_obase, (size_t)n_layouts + 1));
     B_TRY(balloc(&B->opts, (size_t)V));
@@ -829,13 +982,21 @@ gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_of
     // validation and the per-layout statistics of the plan
     B_CU2(cudaMemsetAsync(B->d_nseg, 0, sizeof(unsigned long long) * n_layouts, B->stream));
     B_CU2(cudaMemsetAsync(B->d_l1, 0, sizeof(unsigned long long) * n_layouts, B->stream));
+    B_CU2(cudaMemsetAsync(B->d_hn, 0, sizeof(uint32_t) * 16 * n_layouts, B->stream));
+    B_CU2(cudaMemsetAsync(B->d_hl1, 0, sizeof(unsigned long long) * 16 * n_layouts, B->stream));
     if (E > 0) {
         count_launches(1);
         k_batch_stats<<<grid_for(E, 256, 152 * 16), 256, 0, B->stream>>>(b.seg, B->seg_layout, b.acc, B->d_nseg,
-                                                                         B->d_l1);
+                                                                         B->d_l1, B->d_hn, B->d_hl1);
     }
     B->nseg_l.assign(n_layouts, 0);
     B->l1_l.assign(n_layouts, 0);
+    B->hn_l.assign(16 * n_layouts, 0);
+    B->hl1_l.assign(16 * n_layouts, 0);
+    B_CU2(cudaMemcpyAsync(B->hn_l.data(), B->d_hn, sizeof(uint32_t) * 16 * n_layouts, cudaMemcpyDeviceToHost,
+                          B->stream));
+    B_CU2(cudaMemcpyAsync(B->hl1_l.data(), B->d_hl1, sizeof(uint64_t) * 16 * n_layouts, cudaMemcpyDeviceToHost,
+                          B->stream));
     B_CU2(cudaMemcpyAsync(B->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, B->stream));
     B_CU2(cudaMemcpyAsync(B->nseg_l.data(), B->d_nseg, sizeof(uint64_t) * n_layouts, cudaMemcpyDeviceToHost, B->stream));
     B_CU2(cudaMemcpyAsync(B->l1_l.data(), B->d_l1, sizeof(uint64_t) * n_layouts, cudaMemcpyDeviceToHost, B->stream));

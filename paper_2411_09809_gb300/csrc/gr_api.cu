@@ -81,6 +81,14 @@ struct gr_layout {
     uint32_t diff_ideal_u = 0;
     bool diff_ready = false;
     bool stats_stale = true;        // h_acc's layout part predates the last update
+    // Once a synchronised evaluation has sized the grid buffers for cell size
+    // fast_k (and split), later ones with the same plan run without the
+    // mid-evaluation read-backs: the plan comes from the statistics read at
+    // the previous evaluation's end, the kernels read the sizes on the
+    // device, and an overflow re-runs the evaluation synchronised.
+    bool fast_ok = false;
+    int fast_k = -1;
+    bool fast_split = false;
     int64_t io_h2d = 0, io_d2h = 0; // bytes copied between host and device
     // phase timing
     bool profiling = false;
@@ -95,7 +103,8 @@ namespace {
 std::atomic<int64_t> g_launches{0};
 
 void free_grid(GridBuffers &g) {
-    void *ptrs[] = {g.cell_off, g.item_off, g.cell_fill, g.rec, g.item_desc, g.ocell_off, g.ocell_fill, g.opts};
+    void *ptrs[] = {g.cell_off, g.cell_nl, g.item_off, g.cell_fill, g.rec, g.item_desc, g.ocell_off, g.ocell_fill,
+                    g.opts, g.seg_long, g.theta_long, g.eid_long};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     g = GridBuffers{};
@@ -164,14 +173,22 @@ gr_status alloc_layout(gr_layout *L) {
 // Grows the crossing-grid cell arrays to C cells.
 gr_status ensure_cells(gr_layout *L, int C) {
     GridBuffers &g = L->g;
+    gr_status st;
+    if (!g.seg_long) {  // the long-segment list (at most every edge)
+        if ((st = dalloc(&g.seg_long, (size_t)L->E)) != GR_OK) return st;
+        if ((st = dalloc(&g.theta_long, (size_t)L->E)) != GR_OK) return st;
+        if ((st = dalloc(&g.eid_long, (size_t)L->E)) != GR_OK) return st;
+    }
     if (g.cells_cap >= C) return GR_OK;
     if (g.cell_off) cudaFree(g.cell_off);
+    if (g.cell_nl) cudaFree(g.cell_nl);
     if (g.item_off) cudaFree(g.item_off);
     if (g.cell_fill) cudaFree(g.cell_fill);
-    g.cell_off = g.item_off = g.cell_fill = nullptr;
+    g.cell_off = g.cell_nl = g.item_off = nullptr;
+    g.cell_fill = nullptr;
     g.cells_cap = 0;
-    gr_status st;
     if ((st = dalloc(&g.cell_off, (size_t)C + 1)) != GR_OK) return st;
+    if ((st = dalloc(&g.cell_nl, (size_t)C)) != GR_OK) return st;
     if ((st = dalloc(&g.item_off, (size_t)C + 1)) != GR_OK) return st;
     if ((st = dalloc(&g.cell_fill, (size_t)C)) != GR_OK) return st;
     g.cells_cap = C;
@@ -194,7 +211,7 @@ gr_status ensure_records(gr_layout *L, uint64_t R, uint64_t items) {
         g.item_desc = nullptr;
         g.items_cap = 0;
         const uint64_t cap = items + items / 4 + 1024;
-        if ((st = dalloc(&g.item_desc, (size_t)cap)) != GR_OK) return st;
+        if ((st = dalloc(&g.item_desc, 2 * (size_t)cap)) != GR_OK) return st;
         g.items_cap = cap;
     }
     return GR_OK;
@@ -312,42 +329,43 @@ gr_status refresh_stats(gr_layout *L) {
     return GR_OK;
 }
 
-// ---------------------------------------------------------- density model
-// Cost units are "one all-pairs pair test".  A grid record costs about as
-// much as kRecordCost pair tests (two DDA walks, atomics, scattered stores)
-// and a candidate pair in a cell about kCellPairCost (lane efficiency,
-// owner tests).  Measured on GB300 with the workloads of the benchmark.
-constexpr double kRecordCost = 24.0;
-constexpr double kCellPairCost = 3.0;
-constexpr double kCellCost = 2.0;  // per cell: count, scan, work-item passes
+constexpr double kGridMargin = 0.75;
 
 struct CrossPlan {
     bool grid = false;
+    bool split = false;  // long-long pairs on the all-pairs tiles
     int k = 0;
 };
 
-double est_records(double n, double l1, int k) { return n + l1 / double(1 << k); }
-
-// Chooses the cell size from segment count and total L1 length: records
-// n + L1 / w, a lower bound R^2 / (2 C) on the candidate pairs (equality for
-// evenly spread records) and a per-cell cost; ties go to the coarser grid.
-// Picks all-pairs when even that bound loses.
-CrossPlan plan_crossings(const gr_layout *L, uint64_t n_seg, uint64_t l1) {
+// Chooses the cell size with grid_cost (records, short-involved candidate
+// pairs at even spread, cells, long-long pairs on the all-pairs tiles); ties
+// go to the coarser grid.  Picks all-pairs unless the best grid is estimated
+// at under kGridMargin of its cost (the estimate is rough where few segments
+// are short and the grid is coarse).
+CrossPlan plan_crossings(const gr_layout *L, const DevAcc &a) {
     CrossPlan p;
-    const double n = (double)n_seg, l = (double)l1;
+    const double n = (double)a.n_seg, l = (double)a.len_l1;
     const double allpairs = n * (n - 1) / 2;
     int best_k = 8;
+    bool best_split = false;
     double best = 1e300;
-    for (int k = 14; k >= 6; --k) {
-        const double R = est_records(n, l, k);
-        const double C = double(65536 >> k) * double(65536 >> k);
-        const double cost = kRecordCost * R + kCellPairCost * R * R / (2 * C) + kCellCost * C;
-        if (cost < best) { best = cost; best_k = k; }
+    for (int k = 14; k >= 6; --k)
+        for (bool split : {false, true}) {
+            const double cost = grid_cost(n, l, a.len_hist, a.l1_hist, k, split);
+            if (cost < best) { best = cost; best_k = k; best_split = split; }
+        }
+    p.k = best_k;
+    p.split = best_split;
+    if (L->opt.cell_log2 >= 6 && L->opt.cell_log2 <= 16) {  // a fixed cell size: the better form for it
+        p.k = L->opt.cell_log2;
+        p.split = grid_cost(n, l, a.len_hist, a.l1_hist, p.k, true) <
+                  grid_cost(n, l, a.len_hist, a.l1_hist, p.k, false);
     }
-    p.k = L->opt.cell_log2 >= 6 && L->opt.cell_log2 <= 16 ? L->opt.cell_log2 : best_k;
+    if (L->opt.long_pairs == GR_LONG_ALLPAIRS) p.split = true;
+    else if (L->opt.long_pairs == GR_LONG_GRID) p.split = false;
     if (L->opt.crossing_path == GR_PATH_GRID) p.grid = true;
     else if (L->opt.crossing_path == GR_PATH_ALLPAIRS) p.grid = false;
-    else p.grid = n_seg >= 2 && best < allpairs;
+    else p.grid = a.n_seg >= 2 && best < kGridMargin * allpairs;
     return p;
 }
 
@@ -489,10 +507,15 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     cudaStream_t s = L->stream;
     Buffers &b = L->b;
     const int64_t V = L->V, E = L->E;
-    if ((st = refresh_stats(L)) != GR_OK) return st;
-    if ((st = status_to_error(L->h_acc->status)) != GR_OK) return st;
+    // fast: plan from the statistics of the previous evaluation (the inputs'
+    // validity is then checked at the end; every kernel skips invalid data)
+    const bool fast = L->fast_ok && L->coord == GR_COORD_I32;
+    if (!fast) {
+        if ((st = refresh_stats(L)) != GR_OK) return st;
+        if ((st = status_to_error(L->h_acc->status)) != GR_OK) return st;
+    }
     if (L->coord == GR_COORD_F32) return evaluate_f32(L, metrics, ideal, out);
-    const uint64_t n_seg = L->h_acc->n_seg;
+    const uint64_t n_seg = fast ? (uint64_t)E : L->h_acc->n_seg;  // (an upper bound when fast)
     GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
                           sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
 
@@ -538,18 +561,19 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     }
     GR_CU(cudaEventRecord(L->ev_join, t));
 
-    // crossing binning; the host needs its sizes
+    // crossing binning; without the fast path the host needs its sizes
     CrossPlan cp;
-    bool need_sync = false;
+    bool need_sync = false, fast_grid = false;
     if ((metrics & GR_METRIC_CROSSINGS) && n_seg >= 2) {
-        cp = plan_crossings(L, n_seg, L->h_acc->len_l1);
+        cp = plan_crossings(L, *L->h_acc);
         if (cp.grid) {
             const int C = (65536 >> cp.k) * (65536 >> cp.k);
             if ((st = ensure_cells(L, C)) != GR_OK) return st;
             phase_begin(L, GR_PHASE_CROSS_BIN);
-            launch_grid_count(b, E, L->g, cp.k, s);
+            launch_grid_count(b, E, L->g, cp.k, cp.split, s);
             phase_end(L, GR_PHASE_CROSS_BIN);
-            need_sync = true;
+            fast_grid = fast && cp.k == L->fast_k && cp.split == L->fast_split;
+            need_sync = !fast_grid;
         }
     }
     if (need_sync) {
@@ -565,24 +589,40 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
 
     int32_t path = 0;
     int64_t pairs_tested = -1;
-    if ((metrics & GR_METRIC_CROSSINGS) && n_seg >= 2) {
+    if (fast_grid) {
+        phase_begin(L, GR_PHASE_CROSS_SCATTER);
+        launch_grid_scatter(b, E, L->g, cp.k, cp.split, s);
+        phase_end(L, GR_PHASE_CROSS_SCATTER);
+        phase_begin(L, GR_PHASE_CROSS_PAIRS);
+        launch_grid_pairs(b, L->g, cp.k, L->g.items_cap, ideal_units(ideal), PerEdge{}, s);
+        if (cp.split) launch_grid_long_pairs(b, L->g, -1, ideal_units(ideal), PerEdge{}, s);
+        phase_end(L, GR_PHASE_CROSS_PAIRS);
+        path = GR_PATH_GRID;
+        pairs_tested = -2;  // computed on the device
+    } else if ((metrics & GR_METRIC_CROSSINGS) && n_seg >= 2) {
         bool grid = cp.grid;
         const DevAcc &a = *L->h_acc;
         if (grid && (a.grid_flags & GF_ITEMS_OVERFLOW)) grid = false;
+        const double nl = (double)a.n_long;
         if (grid && L->opt.crossing_path == GR_PATH_AUTO) {
             const double n = (double)n_seg;
-            grid = kRecordCost * (double)a.records + kCellPairCost * (double)a.grid_work < n * (n - 1) / 2;
+            grid = kRecordCost * (double)a.records + kCellPairCost * (double)a.grid_work + nl * (nl - 1) / 2 <
+                   kGridMargin * n * (n - 1) / 2;
         }
         if (grid) {
             if ((st = ensure_records(L, a.records, a.grid_items)) != GR_OK) return st;
             phase_begin(L, GR_PHASE_CROSS_SCATTER);
-            launch_grid_scatter(b, E, L->g, cp.k, s);
+            launch_grid_scatter(b, E, L->g, cp.k, cp.split, s);
             phase_end(L, GR_PHASE_CROSS_SCATTER);
             phase_begin(L, GR_PHASE_CROSS_PAIRS);
             launch_grid_pairs(b, L->g, cp.k, a.grid_items, ideal_units(ideal), PerEdge{}, s);
+            if (cp.split) launch_grid_long_pairs(b, L->g, a.n_long, ideal_units(ideal), PerEdge{}, s);
             phase_end(L, GR_PHASE_CROSS_PAIRS);
             path = GR_PATH_GRID;
-            pairs_tested = (int64_t)a.grid_work;
+            pairs_tested = (int64_t)a.grid_work + (int64_t)a.n_long * ((int64_t)a.n_long - 1) / 2;
+            L->fast_ok = true;  // buffers sized (with headroom) for this plan
+            L->fast_k = cp.k;
+            L->fast_split = cp.split;
         } else {
             phase_begin(L, GR_PHASE_CROSS_PAIRS);
             launch_crossings_allpairs(b, E, ideal_units(ideal), PerEdge{}, s);
@@ -603,6 +643,12 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     phase_end(L, GR_PHASE_FINALIZE);
     GR_CU(cudaStreamSynchronize(s));
     phase_collect(L);
+    L->stats_stale = false;  // the read-back holds the statistics of these inputs
+    if (fast_grid && ((L->h_acc->eval_status & ST_OVERFLOW) || (L->h_acc->grid_flags & GF_ITEMS_OVERFLOW)) &&
+        !(L->h_acc->status & (ST_BAD_ID | ST_BAD_COORD))) {
+        L->fast_ok = false;  // the buffers did not fit these inputs: again, synchronised
+        return gr_evaluate(L, metrics, params, out);
+    }
     st = status_to_error(L->h_acc->status | L->h_acc->eval_status);
     if (st != GR_OK) return st;
     *out = *L->h_result;
@@ -676,11 +722,11 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     gr_status st2 = refresh_stats(L);
     if (st2 != GR_OK) return st2;
     if ((st2 = status_to_error(L->h_acc->status)) != GR_OK) return st2;
-    CrossPlan cp = plan_crossings(L, L->h_acc->n_seg, L->h_acc->len_l1);
+    CrossPlan cp = plan_crossings(L, *L->h_acc);
     if (cp.grid && L->h_acc->n_seg >= 2) {
         const int C = (65536 >> cp.k) * (65536 >> cp.k);
         if ((st2 = ensure_cells(L, C)) != GR_OK) return st2;
-        launch_grid_count(b, E, L->g, cp.k, s);
+        launch_grid_count(b, E, L->g, cp.k, cp.split, s);
         GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
         GR_CU(cudaStreamSynchronize(s));
         if ((st2 = status_to_error(L->h_acc->eval_status)) != GR_OK) return st2;
@@ -688,8 +734,9 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     }
     if (cp.grid && L->h_acc->n_seg >= 2) {
         if ((st2 = ensure_records(L, L->h_acc->records, L->h_acc->grid_items)) != GR_OK) return st2;
-        launch_grid_scatter(b, E, L->g, cp.k, s);
+        launch_grid_scatter(b, E, L->g, cp.k, cp.split, s);
         launch_grid_pairs(b, L->g, cp.k, L->h_acc->grid_items, ideal_units(ideal), pe, s);
+        if (cp.split) launch_grid_long_pairs(b, L->g, L->h_acc->n_long, ideal_units(ideal), pe, s);
     } else {
         launch_crossings_allpairs(b, E, ideal_units(ideal), pe, s);
     }

@@ -34,6 +34,8 @@ struct DevAcc {
     uint32_t n_seg;            // non-zero-length segments after compaction
     uint64_t zero_len;         // zero-length edges
     uint64_t len_l1;           // sum over segments of |dx| + |dy|
+    uint32_t len_hist[16];     // segments by major-axis length in [2^b, 2^(b+1))
+    uint64_t l1_hist[16];      // their |dx| + |dy|
     // ---- per evaluation
     uint32_t eval_status;      // ST_* bits raised during an evaluation
     uint32_t grid_flags;       // GF_* bits: the grid path cannot be used
@@ -44,8 +46,10 @@ struct DevAcc {
     uint64_t occlusion;
     uint64_t records;          // grid (edge, cell) records
     uint64_t grid_items;       // pair-kernel work items
-    uint64_t grid_work;        // sum over cells of n (n - 1) / 2
+    uint64_t grid_work;        // candidate pairs of the grid: short-short and short-long per cell
     uint64_t scan_sink;        // totals nobody reads
+    uint32_t n_long;           // long segments (their pairs go to the all-pairs tiles)
+    uint32_t pad_;
 };
 
 enum : uint32_t {
@@ -93,19 +97,55 @@ struct __align__(32) GridRec {
 // Buffers of the uniform grids (crossings and occlusion), grown on demand.
 struct GridBuffers {
     uint32_t *cell_off = nullptr;  // [C + 1] counts, then offsets (scan in place)
+    uint32_t *cell_nl = nullptr;   // [C] long records per cell
     uint32_t *item_off = nullptr;  // [C + 1] work items per cell, then offsets
-    uint32_t *cell_fill = nullptr; // [C]
-    GridRec *rec = nullptr;        // [rec_cap] records sorted by cell
+    unsigned long long *cell_fill = nullptr; // [C] short (low 32 bits) and long (high) records placed
+    GridRec *rec = nullptr;        // [rec_cap] records sorted by cell: short ones first, then long ones
     uint64_t rec_cap = 0;
-    uint4 *item_desc = nullptr;    // [items_cap] {cell record offset, records, cell, ti << 16 | tj}
+    uint4 *item_desc = nullptr;    // [2 items_cap] {record offset, records, short records, ti << 16 | tj}, {cell}
     uint64_t items_cap = 0;
     int cells_cap = 0;             // C the cell arrays are sized for
+    SegRec *seg_long = nullptr;    // [E] the long segments, their directions and edge ids
+    uint32_t *theta_long = nullptr;
+    int32_t *eid_long = nullptr;
     // occlusion grid
     uint32_t *ocell_off = nullptr; // [OC + 1]
     uint32_t *ocell_fill = nullptr;// [OC]
     uint32_t *opts = nullptr;      // [V] packed points sorted by cell
     int ocells_cap = 0;
 };
+
+// Cost model of the crossing grid, in units of one pair test of the all-pairs
+// tiles.  A record (two DDA walks, atomics, a scattered store) costs about
+// kRecordCost, a candidate pair in a cell about kCellPairCost (lane
+// efficiency, owner tests), a cell kCellCost (count, scan and work-item
+// passes); measured on GB300 with the workloads of the benchmark.
+constexpr double kRecordCost = 24.0;
+constexpr double kCellPairCost = 3.0;
+constexpr double kCellCost = 2.0;
+constexpr double kSplitCost = 4e6;  // the long list and its all-pairs launch (a few microseconds)
+
+// Estimated cost of the grid path with cells of side 2^k for n segments of
+// total L1 length l1, hist_n / hist_l1 their counts and L1 lengths by
+// major-axis length class [2^b, 2^(b+1)): records n + L1 / w and candidate
+// pairs estimated as for evenly spread records.  With `split`, segments of
+// major length >= 2w are long (length in [w, 2w): half of them) and the
+// pairs of two long ones go to the all-pairs tiles (n_long^2 / 2); without,
+// every pair sharing a cell is a candidate.
+inline double grid_cost(double n, double l1, const uint32_t *hist_n, const uint64_t *hist_l1, int k, bool split) {
+    double nl = 0.0, ll = 0.0;
+    for (int b = 0; b < 16 && split; ++b) {
+        const double f = b > k ? 1.0 : (b == k ? 0.5 : 0.0);
+        nl += f * (double)hist_n[b];
+        ll += f * (double)hist_l1[b];
+    }
+    const double w = double(1 << k);
+    const double R_long = nl + ll / w, R_short = (n - nl) + (l1 - ll) / w;
+    const double C = double(65536 >> k) * double(65536 >> k);
+    const double pairs = (R_short * R_short / 2.0 + R_short * R_long) / C;
+    return kRecordCost * (R_long + R_short) + kCellPairCost * pairs + kCellCost * C + nl * nl / 2.0 +
+           (split ? kSplitCost : 0.0);
+}
 
 constexpr int kElvBlocks = 512;
 constexpr int kScanItems = 4096;      // elements per scan block
@@ -136,16 +176,31 @@ struct PerEdge {
 // a7: tiled all-pairs crossing kernel over the compacted segments.
 // `n_seg` is the compacted segment count (read back from the device).
 // `ideal` is the ideal crossing angle in units of pi / 2^32 (<= 2^31).
+// The same over an arbitrary list of n segments (n read from *n_p on the
+// device, at most n_bound; n_bound < 0: unknown on the host, a persistent
+// launch sized on the device, aggregate tallies only), tallies into acc.
+void launch_crossings_allpairs_of(const SegRec *seg, const int32_t *eid, const uint32_t *theta, const uint32_t *n_p,
+                                  DevAcc *acc, int64_t n_bound, uint32_t ideal, PerEdge pe, cudaStream_t s);
 void launch_crossings_allpairs(const Buffers &b, int64_t n_seg, uint32_t ideal, PerEdge pe,
                                cudaStream_t s);
 
 // a2-a4: DDA count, cell offsets, work items (records -> acc->records,
-// items -> acc->grid_items, candidate pairs -> acc->grid_work).
-void launch_grid_count(const Buffers &b, int64_t E, const GridBuffers &g, int k, cudaStream_t s);
+// items -> acc->grid_items, candidate pairs -> acc->grid_work); the long
+// segments (spanning more than two major lines of the grid) are, with
+// `split`, also copied to g.seg_long / theta_long / eid_long (count ->
+// acc->n_long) and their pairs with each other left out of the grid.
+void launch_grid_count(const Buffers &b, int64_t E, const GridBuffers &g, int k, bool split, cudaStream_t s);
+// Long-long pairs: all-pairs tiles over the long segments (at most n_bound;
+// < 0: count known on the device only).
+void launch_grid_long_pairs(const Buffers &b, const GridBuffers &g, int64_t n_bound, uint32_t ideal, PerEdge pe,
+                            cudaStream_t s);
 // a4: scatter of the records into their cells (needs rec_cap >= records).
-void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int k, cudaStream_t s);
-// a6: per-cell pair kernel with the owner-cell test.
-void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items, uint32_t ideal,
+void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int k, bool split, cudaStream_t s);
+// a6: per-cell pair kernel with the owner-cell test.  The item count is read
+// on the device (item_off[C]); the kernel does nothing when the records or
+// items outgrew their buffers (ST_OVERFLOW is raised by the scatter or the
+// descriptor pass).  n_items_hint sizes the launch (0: unknown).
+void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items_hint, uint32_t ideal,
                        PerEdge pe, cudaStream_t s);
 
 // a8 occlusion grid: cell side 2^k >= d.  Count + scan, then scatter + pair

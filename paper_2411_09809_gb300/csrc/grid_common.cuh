@@ -70,19 +70,30 @@ __device__ __forceinline__ int line_cells(const DdaSeg &s, int c, int k, int G, 
     return n;
 }
 
-constexpr int SHORT_LINES = 2;  // segments spanning more major lines are walked by a warp
+constexpr int SHORT_LINES = 2;  // segments spanning more major lines are "long": walked by a warp
 
-// Calls f(ids, n, record, edge id, direction) for the cells of side 2^k that
-// the segment held by this lane (valid if `ok`) meets, a batch of at most two
-// cells at a time (so a callback can issue its atomics before its stores).
-// Segments spanning at most SHORT_LINES major lines are walked by their own
-// lane; longer ones by the whole warp, one line per lane, so that a few long
-// edges do not serialise their warp.  Every lane of the warp must call it.
-// Both DDA passes use it, so they enumerate the same cells.
-// `k` and the cell-id `base` may differ between lanes (several grids).
+// Whether a segment is long in a grid of side 2^k.  Pairs of two long
+// segments are left to the all-pairs tiles: a grid prunes nothing there (two
+// long segments share about as many cells as they have pairs) and would only
+// add records and owner tests.
+__device__ __forceinline__ bool is_long_seg(SegRec r, int k) {
+    const DdaSeg s = dda_norm(r);
+    return (s.x1 >> k) - (s.x0 >> k) + 1 > SHORT_LINES;
+}
+
+// Calls f(ids, n, record, edge id, direction, split_long) for the cells of
+// side 2^k that the segment held by this lane (valid if `ok`) meets, a batch
+// of at most two cells at a time (so a callback can issue its atomics before
+// its stores).  Segments spanning at most SHORT_LINES major lines are walked
+// by their own lane; longer ones by the whole warp, one line per lane, so
+// that a few long edges do not serialise their warp.  Every lane of the warp
+// must call it.  Both DDA passes use it, so they enumerate the same cells.
+// `k`, the cell-id `base` and `split` may differ between lanes (several
+// grids); split_long is true for the cells of a long segment whose lane
+// passed `split`.
 template <class F>
 __device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, uint32_t th, bool ok, int k, uint32_t base,
-                                                   F &&f) {
+                                                   bool split, F &&f) {
     const int lane = threadIdx.x & 31;
     const int G = 65536 >> k;
     const DdaSeg s = dda_norm(r);
@@ -92,7 +103,7 @@ __device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, uint32
         for (int c = s.x0 >> k, e = s.x1 >> k; c <= e; ++c) {
             int ids[2];
             const int n = line_cells(s, c, k, G, base, ids);
-            f(ids, n, r, eid, th);
+            f(ids, n, r, eid, th, false);
         }
     }
     unsigned m = __ballot_sync(0xffffffffu, is_long);
@@ -108,12 +119,13 @@ __device__ __forceinline__ void warp_for_each_cell(SegRec r, int32_t eid, uint32
         const uint32_t qt = __shfl_sync(0xffffffffu, th, src);
         const int qk = __shfl_sync(0xffffffffu, k, src);
         const uint32_t qb = __shfl_sync(0xffffffffu, base, src);
+        const bool qs = __shfl_sync(0xffffffffu, split ? 1 : 0, src) != 0;
         const int qG = 65536 >> qk;
         const DdaSeg t = dda_norm(q);
         for (int c = (t.x0 >> qk) + lane, e = t.x1 >> qk; c <= e; c += 32) {
             int ids[2];
             const int n = line_cells(t, c, qk, qG, qb, ids);
-            f(ids, n, q, qe, qt);
+            f(ids, n, q, qe, qt, qs);
         }
     }
 }
@@ -212,10 +224,67 @@ __device__ __forceinline__ bool owns_crossing_fast(const GSeg &r, const GSeg &c,
     return owns_crossing(iax, iay, (int)r.bx - iax, (int)r.by - iay, icx, icy, (int)c.bx - icx, (int)c.by - icy, w);
 }
 
-// The pair tests of one work item: rows ti and columns tj (tiles of 32) of
-// the `n` records at `cell_rec` (the records of one cell whose lower-left
-// corner is (x0, y0), side 2^k), against `cs`, this warp's 32-slot staging
-// area.  Off-diagonal items test all rows x columns; diagonal items use a
+// Work items of the per-cell pair kernel.  A cell's records are its `ns`
+// short segments followed by its long ones; an item is a tile of up to 32
+// row records against a tile of up to 32 column records:
+//   short x short  row tile ti <= column tile tj of the short records
+//                  (ti == tj: a diagonal tile, each pair once);
+//   long x short   row tile tl of the long records against column tile ts of
+//                  the short ones (long x long pairs are not items: they go
+//                  to the all-pairs tiles, or, without the split, every
+//                  record counts as short).
+// Packed as {flag long-x-short << 31 | a << 16 | b}; tiles < 2^15 per cell.
+struct ItemTiles {
+    int row0, mr, col0, mc;
+    bool diag;
+};
+
+__device__ __forceinline__ ItemTiles item_tiles(uint32_t n, uint32_t ns, uint32_t w) {
+    const int a = (int)((w >> 16) & 0x7fffu), b = (int)(w & 0xffffu);
+    ItemTiles t;
+    if (w >> 31) {
+        t.row0 = (int)ns + a * TILE;
+        t.mr = min(TILE, (int)n - t.row0);
+        t.col0 = b * TILE;
+        t.mc = min(TILE, (int)ns - t.col0);
+        t.diag = false;
+    } else {
+        t.row0 = a * TILE;
+        t.mr = min(TILE, (int)ns - t.row0);
+        t.col0 = b * TILE;
+        t.mc = min(TILE, (int)ns - t.col0);
+        t.diag = a == b;
+    }
+    return t;
+}
+
+constexpr uint32_t kMaxCellTiles = 1u << 15;
+
+// Work items of a cell with n records, ns of them short (see ItemTiles).
+__device__ __forceinline__ uint64_t cell_item_count(uint64_t n, uint64_t ns, bool *overflow) {
+    const uint64_t nl = n - ns, Ts = (ns + TILE - 1) / TILE, Tl = (nl + TILE - 1) / TILE;
+    *overflow = Ts >= kMaxCellTiles || Tl >= kMaxCellTiles;
+    return (ns >= 2 ? Ts * (Ts + 1) / 2 : 0) + (ns >= 1 ? Tl * Ts : 0);
+}
+
+// Writes the descriptors' tile words of a cell's items, in the order
+// counted by cell_item_count, via emit(q, word) for q in [q0, q_end).
+template <class F>
+__device__ __forceinline__ void cell_item_words(uint32_t n, uint32_t ns, uint32_t q, uint32_t q_end, F &&emit) {
+    const uint32_t nl = n - ns, Ts = (ns + TILE - 1) / TILE, Tl = (nl + TILE - 1) / TILE;
+    if (ns >= 2)
+        for (uint32_t ti = 0; ti < Ts && q < q_end; ++ti)
+            for (uint32_t tj = ti; tj < Ts && q < q_end; ++tj, ++q) emit(q, (ti << 16) | tj);
+    if (ns >= 1)
+        for (uint32_t tl = 0; tl < Tl && q < q_end; ++tl)
+            for (uint32_t ts = 0; ts < Ts && q < q_end; ++ts, ++q) emit(q, (1u << 31) | (tl << 16) | ts);
+}
+
+// The pair tests of one work item: records [row0, row0 + mr) of the cell
+// against records [col0, col0 + mc) (diag: the same records, each pair once),
+// where `cell_rec` holds the records of one cell whose lower-left corner is
+// (x0, y0), side 2^k, and `cs` is this warp's 32-slot staging area.
+// Off-diagonal items test all rows x columns; diagonal items use a
 // rotation schedule (round q pairs lane i with (i + q) mod m) so that every
 // lane has work in every round.  Orientations are evaluated in FP32 in the
 // cell's coordinates: exact for pairs of short segments near the cell,
@@ -227,21 +296,21 @@ __device__ __forceinline__ bool owns_crossing_fast(const GSeg &r, const GSeg &c,
 // lexicographically smallest point of the overlap.  Every lane of the warp
 // must call it.
 template <bool PER_EDGE>
-__device__ __forceinline__ void grid_item(const GridRec *__restrict__ cell_rec, int n, int ti, int tj, int x0,
-                                          int y0, int k, GSeg *cs, uint32_t ideal, PairCounts &pc, PerEdge pe) {
+__device__ __forceinline__ void grid_item(const GridRec *__restrict__ cell_rec, const ItemTiles t, int x0, int y0,
+                                          int k, GSeg *cs, uint32_t ideal, PairCounts &pc, PerEdge pe) {
     const int lane = threadIdx.x & 31;
     const int w = 1 << k;
-    const int mr = min(TILE, n - ti * TILE), mc = min(TILE, n - tj * TILE);
+    const int mr = t.mr, mc = t.mc;
 
     __syncwarp();
-    if (lane < mc) cs[lane] = make_gseg(cell_rec[tj * TILE + lane], x0, y0);
+    if (lane < mc) cs[lane] = make_gseg(cell_rec[t.col0 + lane], x0, y0);
     GSeg rs;
-    if (lane < mr) rs = make_gseg(cell_rec[ti * TILE + lane], x0, y0);
+    if (lane < mr) rs = make_gseg(cell_rec[t.row0 + lane], x0, y0);
     __syncwarp();
     if (lane >= mr) return;
 
     uint32_t m_ec = 0, m_prop = 0, m_coll = 0, m_unsure = 0;
-    const bool diag = ti == tj;
+    const bool diag = t.diag;
     const int rounds = diag ? mr / 2 : mc;
     for (int s = 0; s < rounds; ++s) {
         int jj;

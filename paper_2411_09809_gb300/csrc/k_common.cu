@@ -28,6 +28,13 @@ __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int
                                                 int32_t *__restrict__ seg_eid,
                                                 uint32_t *__restrict__ seg_theta,
                                                 int64_t *__restrict__ len2, DevAcc *acc) {
+    __shared__ uint32_t h_n[16];
+    __shared__ unsigned long long h_l1[16];
+    if (threadIdx.x < 16) {
+        h_n[threadIdx.x] = 0;
+        h_l1[threadIdx.x] = 0;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride) {
@@ -73,8 +80,24 @@ __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int
             const uint32_t pos = slot + __popc(mk & lanemask_lt());
             seg[pos] = r;
             seg_eid[pos] = (int32_t)e;
-            seg_theta[pos] = line_direction(px(r.y) - px(r.x), py(r.y) - py(r.x));
+            const int dx = px(r.y) - px(r.x), dy = py(r.y) - py(r.x);
+            seg_theta[pos] = line_direction(dx, dy);
         }
+        // length classes, aggregated over the lanes of a warp in the same class
+        const int b = keep ? 31 - __clz(max(abs(px(r.y) - px(r.x)), abs(py(r.y) - py(r.x)))) : -1;
+        if (keep) {
+            const unsigned same = __match_any_sync(mk, b);
+            const uint32_t l1s = __reduce_add_sync(same, l1);
+            if (lane == __ffs(same) - 1) {
+                atomicAdd(&h_n[b], (uint32_t)__popc(same));
+                atomicAdd(&h_l1[b], (unsigned long long)l1s);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 16 && h_n[threadIdx.x]) {
+        atomicAdd(&acc->len_hist[threadIdx.x], h_n[threadIdx.x]);
+        atomicAdd((unsigned long long *)&acc->l1_hist[threadIdx.x], h_l1[threadIdx.x]);
     }
 }
 
@@ -276,7 +299,12 @@ __global__ void __launch_bounds__(256) k_finalize(const DevAcc *__restrict__ acc
     r.crossing.c.collinear_overlaps = (int64_t)acc->collinear;
     r.crossing.c.zero_length_edges = (int64_t)acc->zero_len;
     const uint64_t ns = acc->n_seg;
-    r.crossing.c.pairs_tested = pairs_tested >= 0 ? pairs_tested : (int64_t)(ns * (ns - (ns > 0)) / 2);
+    if (pairs_tested == -2) {  // grid: candidate pairs of the cells plus the long-long pairs
+        const uint64_t nl = acc->n_long;
+        r.crossing.c.pairs_tested = (int64_t)(acc->grid_work + nl * (nl - (nl > 0)) / 2);
+    } else {
+        r.crossing.c.pairs_tested = pairs_tested >= 0 ? pairs_tested : (int64_t)(ns * (ns - (ns > 0)) / 2);
+    }
     const double dev = ((double)acc->dev_hi * 18446744073709551616.0 + (double)acc->dev_lo) * kAngleUnit;
     r.crossing.angle_dev_sum = dev;
     r.crossing.ideal_rad = ideal;

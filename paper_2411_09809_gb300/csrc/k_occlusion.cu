@@ -50,7 +50,11 @@ __global__ void __launch_bounds__(OC_ROWS) k_occl_allpairs(const int2 *__restric
 // in 8-adjacent cells (the 2r x 2r grid of Sec. 3.2.1).  Each vertex is put
 // in exactly one cell and each unordered pair of cells is visited once
 // through the half stencil {E, NE, N, NW}, so no pair is seen twice and the
-// paper's `distinct` step is not needed.
+// paper's `distinct` step is not needed.  Vertices with a coordinate outside
+// [0, 65536) (the evaluation then reports GR_ERANGE) are left out of the
+// grids, so no kernel indexes a cell from them.
+
+__device__ __forceinline__ bool in_range(int2 p) { return (unsigned)p.x < 65536u && (unsigned)p.y < 65536u; }
 
 __global__ void __launch_bounds__(256) k_occl_count(const int2 *__restrict__ xy, int64_t V, int k,
                                                     uint32_t *__restrict__ cnt) {
@@ -58,6 +62,7 @@ __global__ void __launch_bounds__(256) k_occl_count(const int2 *__restrict__ xy,
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int2 p = xy[v];
+        if (!in_range(p)) continue;
         atomicAdd(&cnt[(p.y >> k) * G + (p.x >> k)], 1u);
     }
 }
@@ -69,6 +74,7 @@ __global__ void __launch_bounds__(256) k_occl_fill(const int2 *__restrict__ xy, 
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int2 p = xy[v];
+        if (!in_range(p)) continue;
         const int c = (p.y >> k) * G + (p.x >> k);
         const uint32_t slot = atomicAdd(&fill[c], 1u);
         pts[off[c] + slot] = uint32_t(p.x) | (uint32_t(p.y) << 16);
@@ -87,13 +93,14 @@ __device__ __forceinline__ uint32_t count_close(uint32_t p, const uint32_t *__re
     return n;
 }
 
-// One thread per vertex in cell order: later vertices of its own cell, then
-// every vertex of the E, NE, N and NW cells.
+// One thread per placed vertex (off[C] of them) in cell order: later
+// vertices of its own cell, then every vertex of the E, NE, N and NW cells.
 __global__ void __launch_bounds__(256) k_occl_pairs(const uint32_t *__restrict__ pts,
-                                                    const uint32_t *__restrict__ off, int64_t V, int k,
+                                                    const uint32_t *__restrict__ off, int C, int k,
                                                     long long d2, DevAcc *acc) {
     __shared__ uint64_t sh[32];
     const int G = 65536 >> k;
+    const int64_t V = off[C];
     uint64_t cnt = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -123,6 +130,7 @@ __global__ void __launch_bounds__(256) k_batch_occl_count(const int2 *__restrict
         const int64_t l = find_segment(v_off, L, v);
         const int k = ko[l], G = 65536 >> k;
         const int2 p = xy[v];
+        if (!in_range(p)) continue;
         atomicAdd(&cnt[obase[l] + (uint32_t)((p.y >> k) * G + (p.x >> k))], 1u);
     }
 }
@@ -137,6 +145,7 @@ __global__ void __launch_bounds__(256) k_batch_occl_fill(const int2 *__restrict_
         const int64_t l = find_segment(v_off, L, v);
         const int k = ko[l], G = 65536 >> k;
         const int2 p = xy[v];
+        if (!in_range(p)) continue;
         const uint32_t c = obase[l] + (uint32_t)((p.y >> k) * G + (p.x >> k));
         const uint32_t pos = off[c] + atomicAdd(&fill[c], 1u);
         pts[pos] = uint32_t(p.x) | (uint32_t(p.y) << 16);
@@ -144,13 +153,15 @@ __global__ void __launch_bounds__(256) k_batch_occl_fill(const int2 *__restrict_
     }
 }
 
-// One thread per vertex in cell order, within its own layout's grid.
+// One thread per placed vertex (off[OC] of them) in cell order, within its
+// own layout's grid.
 __global__ void __launch_bounds__(256) k_batch_occl_pairs(const uint32_t *__restrict__ pts,
                                                           const uint32_t *__restrict__ lay,
-                                                          const uint32_t *__restrict__ off, int64_t V,
+                                                          const uint32_t *__restrict__ off, uint32_t OC,
                                                           const int32_t *__restrict__ ko,
                                                           const uint32_t *__restrict__ obase, long long d2,
                                                           uint64_t *__restrict__ occl) {
+    const int64_t V = off[OC];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t p = pts[i];
         const uint32_t l = lay[i];
@@ -194,7 +205,7 @@ void launch_occlusion_grid_pairs(const Buffers &b, int64_t V, const GridBuffers 
     count_launches(2);
     k_occl_fill<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.xy, V, k, g.ocell_off, g.ocell_fill,
                                                          g.opts);
-    k_occl_pairs<<<grid_for(V, 256, 152 * 16), 256, 0, s>>>(g.opts, g.ocell_off, V, k, (long long)d * d, b.acc);
+    k_occl_pairs<<<grid_for(V, 256, 152 * 16), 256, 0, s>>>(g.opts, g.ocell_off, C, k, (long long)d * d, b.acc);
 }
 
 void launch_batch_occlusion(const Buffers &b, const BatchView &bv, int64_t V, const int32_t *ko,
@@ -210,7 +221,7 @@ void launch_batch_occlusion(const Buffers &b, const BatchView &bv, int64_t V, co
     launch_scan_u32(ocell_off, ocell_off, OC, b.scan_tmp_side, &b.acc->scan_sink, &b.acc->eval_status, s);
     k_batch_occl_fill<<<g, 256, 0, s>>>((const int2 *)b.xy, V, bv.v_off, bv.L, ko, obase, ocell_off, ocell_fill, opts,
                                         olay);
-    k_batch_occl_pairs<<<grid_for(V, 256, 152 * 16), 256, 0, s>>>(opts, olay, ocell_off, V, ko, obase,
+    k_batch_occl_pairs<<<grid_for(V, 256, 152 * 16), 256, 0, s>>>(opts, olay, ocell_off, OC, ko, obase,
                                                                   (long long)d * d, occl);
 }
 

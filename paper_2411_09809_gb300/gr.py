@@ -16,6 +16,7 @@ from . import build as _build
 
 GR_OK, GR_EINVAL, GR_ERANGE, GR_ENOMEM, GR_ECUDA, GR_ETIMEOUT, GR_ENOTSUP = range(7)
 GR_COORD_I32, GR_COORD_F32 = 0, 1
+GR_LONG_AUTO, GR_LONG_ALLPAIRS, GR_LONG_GRID = 0, 1, 2
 GR_METRIC_OCCLUSION, GR_METRIC_MIN_ANGLE, GR_METRIC_EDGE_LENGTH, GR_METRIC_CROSSINGS = 1, 2, 4, 8
 GR_METRIC_ALL = 15
 GR_PATH_AUTO, GR_PATH_GRID, GR_PATH_ALLPAIRS = 0, 1, 2
@@ -33,7 +34,7 @@ class GrError(RuntimeError):
 
 class gr_options(ctypes.Structure):
     _fields_ = [("crossing_path", c_int32), ("cell_log2", c_int32),
-                ("occlusion_path", c_int32), ("profile", c_int32)]
+                ("occlusion_path", c_int32), ("profile", c_int32), ("long_pairs", c_int32)]
 
 
 class gr_params(ctypes.Structure):

@@ -95,6 +95,16 @@ def test_batch_equals_single_layout_entry_points():
         assert a.M_l == pytest.approx(b.M_l, rel=1e-12, abs=1e-15), i
 
 
+@pytest.mark.parametrize("long_pairs", [1, 2])
+def test_batch_long_pair_forms_match_oracle(long_pairs):
+    layouts = mixed_layouts(seed=9, n=48)
+    v_off, e_off, xy, edges = synth.pack_layouts(layouts)
+    with gr.Batch(v_off, e_off, xy, edges, gr.gr_options(0, 0, 0, 0, long_pairs)) as B:
+        res = B.evaluate(gr.GR_METRIC_ALL, IDEAL, 128)
+    for i, L in enumerate(layouts):
+        check_layout(res[i], L, 128, f"layout {i}")
+
+
 def test_batch_update_subsets_and_fixed_offsets():
     layouts = mixed_layouts(seed=5, n=24)
     v_off, e_off, xy, edges = synth.pack_layouts(layouts)
