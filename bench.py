@@ -537,16 +537,18 @@ def run_differentiable(args, rank, world, local_rank):
     pairs_ms, pairs_calls = prof["cross_pairs"]
     t = pairs_ms / max(1, pairs_calls) / 1e3
     ec = res.crossing.c.crossings
-    n_seg = E - res.crossing.c.zero_length_edges
-    ops = n_seg * (n_seg - 1) / 2 * OPS_PER_PAIR_F32 + ec * OPS_PER_CROSSING_F32
+    grid = res.crossing_path == 1
+    # pair tests actually made: the grid's candidate pairs plus the long-long tiles
+    ops = res.crossing.c.pairs_tested * OPS_PER_PAIR_F32 + ec * OPS_PER_CROSSING_F32
     peaks, peak_kind = load_peaks()
     peak = SM_COUNT * LANES_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    rf = {"kernel": "k_cross_f32", "bound": "alu", "achieved": ops / t / 1e12 if t > 0 else None, "peak": peak,
+    kernel = "crossing phase: k_f32_grid_ss + k_f32_grid_ls + k_cross_f32 (long x long)" if grid else "k_cross_f32"
+    rf = {"kernel": kernel, "bound": "alu", "achieved": ops / t / 1e12 if t > 0 else None, "peak": peak,
           "unit": "Tops/s (int32-equivalent lane ops)", "frac": ops / t / 1e12 / peak if t > 0 else None,
           "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
                          f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
           "traffic": load_traffic("k_cross_f32", "differentiable", kernel_source_hash(["k_diff.cu"])),
-          "launch_ms": t * 1e3}
+          "launch_ms": t * 1e3, "pairs_tested": res.crossing.c.pairs_tested}
     line = {
         "metric": "fwd+bwd steps/s", "value": world * 1e3 / ms, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -554,6 +556,7 @@ def run_differentiable(args, rank, world, local_rank):
         "config": dict(diff_config(L), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "fwd_ms": fwd_ms, "fwd_bwd_ms": ms, "fwd_bwd_over_fwd": ms / fwd_ms,
         "results": {"E_ca": float(out3[0]), "M_l": float(out3[1]), "M_a": float(out3[2]), "E_c": ec},
+        "crossing_path": {1: "grid", 2: "all-pairs"}.get(res.crossing_path, "none"),
         "phase_ms": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]},
         "roofline": rf,
         "e2e": {"value": world * 1e3 / e2e_ms, "unit": "steps/s", "ms_per_step": e2e_ms,

@@ -3,6 +3,8 @@
 // enqueued.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <atomic>
 #include <cmath>
 #include <cstddef>
@@ -80,6 +82,10 @@ struct gr_layout {
     float *out3 = nullptr, *gout3 = nullptr;
     uint32_t diff_ideal_u = 0;
     bool diff_ready = false;
+    void *f32_work = nullptr;       // FP32 crossing grid workspace
+    double *theta_adj = nullptr;    // [E] adjoint of each segment's direction
+    int f32_G = 0;                  // its grid side (0: all-pairs tiles)
+    bool f32_planned = false;
     bool stats_stale = true;        // h_acc's layout part predates the last update
     // Once a synchronised evaluation has sized the grid buffers for cell size
     // fast_k (and split), later ones with the same plan run without the
@@ -115,7 +121,8 @@ void free_layout(gr_layout *L) {
     Buffers &b = L->b;
     void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.ma_part,
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result,
-                    b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->arg, L->st, L->out3, L->gout3};
+                    b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->arg, L->st, L->out3, L->gout3,
+                    L->f32_work, L->theta_adj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_grid(L->g);
@@ -128,6 +135,8 @@ void free_layout(gr_layout *L) {
     if (L->h_acc) cudaFreeHost(L->h_acc);
     delete L;
 }
+
+constexpr int64_t kF32GridMinEdges = 2048;  // FP32 layouts: all-pairs tiles below this many edges
 
 gr_status alloc_layout(gr_layout *L) {
     const int64_t V = L->V, E = L->E;
@@ -159,6 +168,7 @@ gr_status alloc_layout(gr_layout *L) {
         GR_TRY(dalloc(&L->st, 1));
         GR_TRY(dalloc(&L->out3, 3));
         GR_TRY(dalloc(&L->gout3, 3));
+        GR_TRY(dalloc(&L->theta_adj, (size_t)E));
     }
 #undef GR_TRY
     GR_CU(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
@@ -375,6 +385,51 @@ int occl_cell_log2(int64_t d) {
     return k;
 }
 
+float host_unord(uint32_t u) {
+    const uint32_t v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    memcpy(&f, &v, sizeof f);
+    return f;
+}
+
+// FP32 crossing grid, planned once from the statistics of the first
+// evaluation.  For each side G (a power of two in [16, 1024]) the cost of the
+// pair tests is estimated from the segments' major-axis length classes:
+// segments at least a cell long count as long; short ones give about 1.5
+// records each; short x short pairs R^2 / 2C at even spread; each long
+// segment walks about 2 L / w + 2 cells holding R / C records each; long x
+// long pairs n_long^2 / 2; plus a few units per cell and per record.
+gr_status plan_f32_grid(gr_layout *L) {
+    if (L->f32_planned) return GR_OK;
+    L->f32_planned = true;
+    const DevAcc &a = *L->h_acc;
+    const uint64_t n = a.n_seg;
+    if ((int64_t)n < kF32GridMinEdges || a.f32_bounds[0] > a.f32_bounds[2]) return GR_OK;
+    const double span = std::max((double)host_unord(a.f32_bounds[2]) - host_unord(a.f32_bounds[0]),
+                                 (double)host_unord(a.f32_bounds[3]) - host_unord(a.f32_bounds[1]));
+    if (!(span > 0.0)) return GR_OK;
+    int best_G = 0;
+    double best = 0.5 * (double)n * (double)n;  // all-pairs tiles
+    for (int G = 16; G <= 1024; G *= 2) {
+        const double w = span / G, C = (double)G * G;
+        double n_long = 0.0, len_long = 0.0;
+        for (int b = 0; b < 64; ++b) {
+            const double lo = std::ldexp(1.0, b - 48);
+            if (lo >= w) {
+                n_long += a.f32_hist[b];
+                len_long += 1.5 * lo * a.f32_hist[b];
+            }
+        }
+        const double R = 1.5 * ((double)n - n_long), dens = R / C;
+        const double cost = R * R / (2.0 * C) + (2.0 * len_long / w + 2.0 * n_long) * dens + 0.5 * n_long * n_long +
+                            4.0 * C + 8.0 * R;
+        if (cost < best) { best = cost; best_G = G; }
+    }
+    if (best_G == 0) return GR_OK;
+    L->f32_G = best_G;
+    return dalloc((char **)&L->f32_work, f32_grid_bytes(best_G, L->E));
+}
+
 // The FP32 forward: E_ca and the crossing counts (E_c pairs saved when
 // `pairs` is set), M_l, M_a (smallest gaps saved), folded into L->st/out3.
 gr_status forward_f32(gr_layout *L, uint32_t metrics, double ideal, bool save_pairs) {
@@ -382,6 +437,13 @@ gr_status forward_f32(gr_layout *L, uint32_t metrics, double ideal, bool save_pa
     Buffers &b = L->b;
     const int64_t V = L->V, E = L->E;
     const uint32_t ideal_u = ideal_units(ideal);
+    gr_status pst = plan_f32_grid(L);
+    if (pst != GR_OK) return pst;
+    if (save_pairs && !L->pairs) {  // the kernels count the E_c pairs only into a buffer
+        const uint64_t cap0 = 4 * (uint64_t)E + 1024;
+        if ((pst = dalloc(&L->pairs, (size_t)cap0)) != GR_OK) return pst;
+        L->pairs_cap = cap0;
+    }
     for (int attempt = 0; attempt < 3; ++attempt) {
         GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
                               sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
@@ -392,7 +454,10 @@ gr_status forward_f32(gr_layout *L, uint32_t metrics, double ideal, bool save_pa
         if (metrics & GR_METRIC_MIN_ANGLE) launch_min_angle_f32(b, V, E, L->arg, s);
         phase_end(L, GR_PHASE_MIN_ANGLE);
         phase_begin(L, GR_PHASE_CROSS_PAIRS);
-        if (metrics & GR_METRIC_CROSSINGS)
+        if ((metrics & GR_METRIC_CROSSINGS) && L->f32_G > 0 && L->opt.crossing_path != GR_PATH_ALLPAIRS)
+            launch_crossings_f32_grid(b, E, L->f32_G, L->f32_work, ideal_u, save_pairs ? L->pairs : nullptr,
+                                      save_pairs ? L->pairs_cap : 0, s);
+        else if (metrics & GR_METRIC_CROSSINGS)
             launch_crossings_f32(b, E, ideal_u, save_pairs ? L->pairs : nullptr, save_pairs ? L->pairs_cap : 0, s);
         phase_end(L, GR_PHASE_CROSS_PAIRS);
         phase_begin(L, GR_PHASE_FINALIZE);
@@ -427,8 +492,10 @@ gr_status evaluate_f32(gr_layout *L, uint32_t metrics, double ideal, gr_result *
     if (st != GR_OK) return st;
     cudaStream_t s = L->stream;
     Buffers &b = L->b;
+    const bool fgrid = (metrics & GR_METRIC_CROSSINGS) && L->f32_G > 0 && L->opt.crossing_path != GR_PATH_ALLPAIRS;
     launch_finalize(b, metrics, L->E, ideal, 0, L->V > 0 ? min_angle_blocks(L->V) : 0,
-                    (metrics & GR_METRIC_CROSSINGS) ? GR_PATH_ALLPAIRS : 0, 0, 0, -1, s);
+                    (metrics & GR_METRIC_CROSSINGS) ? (fgrid ? GR_PATH_GRID : GR_PATH_ALLPAIRS) : 0, 0, 0,
+                    fgrid ? -2 : -1, s);
     GR_CU(cudaGetLastError());
     GR_CU(cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s));
     L->io_d2h += (int64_t)sizeof(gr_result);
@@ -782,8 +849,8 @@ gr_status gr_diff_backward(gr_layout *L, const float *gout3, float *d_grad_xy) {
     }
     phase_begin(L, GR_PHASE_DIFF_BACKWARD);
     if (L->V > 0)
-        launch_diff_backward(L->b, L->V, L->E, L->pairs, L->arg, L->st, g, L->diff_ideal_u, L->n_pairs, d_grad_xy,
-                             L->stream);
+        launch_diff_backward(L->b, L->V, L->E, L->pairs, L->arg, L->st, g, L->diff_ideal_u, L->n_pairs, L->theta_adj,
+                             d_grad_xy, L->stream);
     phase_end(L, GR_PHASE_DIFF_BACKWARD);
     GR_CU(cudaGetLastError());
     if (!is_device_pointer(gout3)) GR_CU(cudaStreamSynchronize(L->stream));  // the host buffer may go away

@@ -36,6 +36,8 @@ struct DevAcc {
     uint64_t len_l1;           // sum over segments of |dx| + |dy|
     uint32_t len_hist[16];     // segments by major-axis length in [2^b, 2^(b+1))
     uint64_t l1_hist[16];      // their |dx| + |dy|
+    uint32_t f32_hist[64];     // FP32 layouts: segments by major-axis length class ilogb + 48
+    uint32_t f32_bounds[4];    // FP32 layouts: bounding box (order-preserving keys: min x, min y, max x, max y)
     // ---- per evaluation
     uint32_t eval_status;      // ST_* bits raised during an evaluation
     uint32_t grid_flags;       // GF_* bits: the grid path cannot be used
@@ -250,6 +252,12 @@ struct DiffState {
 void launch_gather_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E, Buffers &b, cudaStream_t s);
 // a7 on FP32 coordinates with exact predicates; E_c pairs (compacted segment
 // indices) to `pairs` (at most `cap`; the total goes to acc->records).
+// The same through a G x G grid over the segments' bounding box (short x
+// short pairs in cells, long x short along the long segments' walks, long x
+// long on all-pairs tiles); `work` holds f32_grid_bytes(G, E) bytes.
+size_t f32_grid_bytes(int G, int64_t E);
+void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, uint32_t ideal, uint2 *pairs,
+                               uint64_t cap, cudaStream_t s);
 void launch_crossings_f32(const Buffers &b, int64_t n_bound, uint32_t ideal, uint2 *pairs, uint64_t cap,
                           cudaStream_t s);
 // a9 on FP32 coordinates; each vertex's smallest gap (far vertices) to `arg`.
@@ -259,8 +267,8 @@ void launch_diff_state(const Buffers &b, int64_t V, int64_t E, double ideal, Dif
                        cudaStream_t s);
 // grad[V][2] = gout[0] dE_ca + gout[1] dM_l + gout[2] dM_a (overwritten).
 void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *pairs, const int2 *arg,
-                          const DiffState *st, const float *gout, uint32_t ideal_u, uint64_t n_pairs, float *grad,
-                          cudaStream_t s);
+                          const DiffState *st, const float *gout, uint32_t ideal_u, uint64_t n_pairs, double *adj,
+                          float *grad, cudaStream_t s);
 
 // ------------------------------------------------------------------ batches
 // Device view of a batch of layouts packed one after another: layout l owns

@@ -9,10 +9,13 @@
 // that crossing set and those gaps held fixed, the gradient of
 // g0 * E_ca + g1 * M_l + g2 * M_a with respect to every coordinate, scattered
 // with atomics into an FP32 [V][2] array.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "gr_internal.cuh"
 #include "pair_math.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gr {
 
@@ -22,6 +25,14 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+__device__ __forceinline__ uint32_t ord_f(float f) {  // order-preserving float -> uint
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord_f(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
 int grid_for(int64_t n, int threads, int max_blocks) {
@@ -146,6 +157,9 @@ __global__ void __launch_bounds__(256) k_gather_f32(const float2 *__restrict__ x
                                                     float4 *__restrict__ seg, uint2 *__restrict__ seg_ids,
                                                     int32_t *__restrict__ seg_eid, uint32_t *__restrict__ seg_theta,
                                                     int64_t *__restrict__ len2, DevAcc *acc) {
+    __shared__ uint32_t h[64];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) h[i] = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = base + threadIdx.x;
@@ -184,8 +198,29 @@ __global__ void __launch_bounds__(256) k_gather_f32(const float2 *__restrict__ x
             seg_ids[pos] = make_uint2((uint32_t)ed.x, (uint32_t)ed.y);
             seg_eid[pos] = (int32_t)e;
             seg_theta[pos] = line_direction_d((double)r.z - (double)r.x, (double)r.w - (double)r.y);
+            // statistics for the crossing grid: major-axis length class and the bounding box
+            const float m = fmaxf(fabsf(r.z - r.x), fabsf(r.w - r.y));
+            const int cls = min(max(ilogbf(m) + 48, 0), 63);
+            atomicAdd(&h[cls], 1u);
+        }
+        uint32_t mnx = keep ? min(ord_f(r.x), ord_f(r.z)) : 0xffffffffu, mny = keep ? min(ord_f(r.y), ord_f(r.w)) : 0xffffffffu;
+        uint32_t mxx = keep ? max(ord_f(r.x), ord_f(r.z)) : 0u, mxy = keep ? max(ord_f(r.y), ord_f(r.w)) : 0u;
+        for (int o = 16; o > 0; o >>= 1) {
+            mnx = min(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+            mny = min(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+            mxx = max(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+            mxy = max(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+        }
+        if (lane == 0 && mk) {
+            atomicMin(&acc->f32_bounds[0], mnx);
+            atomicMin(&acc->f32_bounds[1], mny);
+            atomicMax(&acc->f32_bounds[2], mxx);
+            atomicMax(&acc->f32_bounds[3], mxy);
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64; i += blockDim.x)
+        if (h[i]) atomicAdd(&acc->f32_hist[i], h[i]);
 }
 
 __global__ void __launch_bounds__(256) k_check_vertices_f32(const float2 *__restrict__ xy, int64_t V, DevAcc *acc) {
@@ -209,18 +244,65 @@ __device__ __forceinline__ void decode_tile(int64_t t, int &bi, int &bj) {
     bi = (int)(t - r * (r + 1) / 2);
 }
 
-// All-pairs tiles over the compacted FP32 segments; E_c pairs (compacted
-// indices) appended to `pairs` (warp-aggregated), at most `cap` of them; the
-// total goes to acc->records.
+// Exclusive prefix of v over the warp; *total = the warp's sum.  Every lane
+// must call it.
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t *total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    *total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+// Exclusive prefix of v over the block; *total = the block's sum.  Every
+// thread must call it; sh holds 33 words.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, uint32_t *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t wt;
+    const uint32_t in_warp = warp_excl_scan(v, &wt);
+    __syncthreads();
+    if (lane == 0) sh[wid] = wt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const uint32_t t = sh[w];
+            sh[w] = run;
+            run += t;
+        }
+        sh[32] = run;
+    }
+    __syncthreads();
+    *total = sh[32];
+    return sh[wid] + in_warp;
+}
+
+// All-pairs tiles over n FP32 segments (n = *n_p on the device): the
+// compacted segments themselves, or those listed in idx.  E_c pairs
+// (compacted segment indices) are appended to `pairs` (warp-aggregated), at
+// most `cap` of them; the total goes to acc->records.  tiles < 0: sized on
+// the device (a persistent launch).
 __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
-                                                       const uint32_t *__restrict__ theta, DevAcc *acc, uint32_t ideal,
-                                                       int64_t tiles, uint2 *__restrict__ pairs, uint64_t cap) {
+                                                       const uint32_t *__restrict__ theta,
+                                                       const uint32_t *__restrict__ idx, const uint32_t *__restrict__ n_p,
+                                                       DevAcc *acc, uint32_t ideal, int64_t tiles,
+                                                       uint2 *__restrict__ pairs, uint64_t cap) {
     __shared__ float4 cs[DF_COLS];
     __shared__ uint2 cid[DF_COLS];
     __shared__ uint32_t cth[DF_COLS];
+    __shared__ uint32_t cix[DF_COLS];
     __shared__ uint64_t shu[32];
-    const int lane = threadIdx.x & 31;
-    const int n_seg = (int)acc->n_seg;
+    __shared__ uint32_t scan_sh[33];
+    __shared__ unsigned long long tile_base;
+    const int n_seg = (int)*n_p;
+    if (tiles < 0) {
+        const int64_t nb = (n_seg + DF_ROWS - 1) / DF_ROWS;
+        tiles = nb * (nb + 1) / 2;
+    }
     PairCounts pc;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         int bi, bj;
@@ -230,22 +312,29 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
         const int nc = min(DF_COLS, n_seg - j0);
         __syncthreads();
         if (threadIdx.x < nc) {
-            cs[threadIdx.x] = seg[j0 + threadIdx.x];
-            cid[threadIdx.x] = ids[j0 + threadIdx.x];
-            cth[threadIdx.x] = theta[j0 + threadIdx.x];
+            const uint32_t q = idx ? idx[j0 + threadIdx.x] : (uint32_t)(j0 + threadIdx.x);
+            cs[threadIdx.x] = seg[q];
+            cid[threadIdx.x] = ids[q];
+            cth[threadIdx.x] = theta[q];
+            cix[threadIdx.x] = q;
         }
         const int i = bi * DF_ROWS + threadIdx.x;
         const bool row_ok = i < n_seg;
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
         uint2 ri = make_uint2(0xffffffffu, 0xfffffffeu);
-        uint32_t rth = 0;
+        uint32_t rth = 0, rix = 0;
         if (row_ok) {
-            r = seg[i];
-            ri = ids[i];
-            rth = theta[i];
+            rix = idx ? idx[i] : (uint32_t)i;
+            r = seg[rix];
+            ri = ids[rix];
+            rth = theta[rix];
         }
         __syncthreads();
         const bool diag = bi == bj;
+        // pass 1: classify and tally; pass 2 (when pairs are kept): classify
+        // again and write the E_c pairs at offsets reserved with one atomic
+        // per tile (per-pair atomics on one counter serialise)
+        uint32_t mine = 0;
         for (int jj = 0; jj < nc; ++jj) {
             const bool valid = row_ok && (!diag || jj > (int)threadIdx.x);
             const int kind = valid ? classify_f32(r, ri, cs[jj], cid[jj]) : PAIR_NONE;
@@ -253,20 +342,432 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
             if (kind == PAIR_PROPER) ++pc.proper;
             else if (kind == PAIR_TOUCHING) ++pc.touching;
             else if (kind == PAIR_COLLINEAR) ++pc.collinear;
-            if (ec) pc.dev += dev_term(rth, cth[jj], ideal);
-            const unsigned m = __ballot_sync(0xffffffffu, ec);
-            if (m) {
-                unsigned long long slot = 0;
-                if (lane == 0) slot = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)__popc(m));
-                slot = __shfl_sync(0xffffffffu, slot, 0);
-                if (ec) {
-                    const uint64_t pos = slot + __popc(m & lanemask_lt());
-                    if (pos < cap) pairs[pos] = make_uint2((uint32_t)i, (uint32_t)(j0 + jj));
+            if (ec) {
+                pc.dev += dev_term(rth, cth[jj], ideal);
+                ++mine;
+            }
+        }
+        if (pairs) {
+            uint32_t total;
+            const uint32_t off = block_excl_scan(mine, scan_sh, &total);
+            if (threadIdx.x == 0) tile_base = total ? atomicAdd((unsigned long long *)&acc->records, (unsigned long long)total) : 0ull;
+            __syncthreads();
+            uint64_t pos = tile_base + off;
+            for (int jj = 0; jj < nc && mine; ++jj) {
+                const bool valid = row_ok && (!diag || jj > (int)threadIdx.x);
+                const int kind = valid ? classify_f32(r, ri, cs[jj], cid[jj]) : PAIR_NONE;
+                if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) {
+                    if (pos < cap) pairs[pos] = make_uint2(rix, cix[jj]);
+                    ++pos;
+                    --mine;
                 }
             }
         }
     }
     flush_counts(pc, acc, shu);
+}
+
+// ------------------------------------------------- crossing grid (FP32)
+// The crossing set on FP32 coordinates is decided exactly (classify_f32); the
+// grid only chooses which pairs are tested and where each is counted.  Cells:
+// a G x G grid over the segments' bounding box, cell of a coordinate
+// cx(x) = clamp(floor((x - x0) * inv_w)) in FP32 with explicit rounding: a
+// non-decreasing function, so the cell range of a segment's bounding box
+// [cx(min x), cx(max x)] x [cy(min y), cy(max y)] holds the cell of every
+// point of the segment rounded to FP32.
+//   short  bounding box within 2 x 2 cells: registered in each of its (1, 2
+//          or 4) cells.  Two short segments meet only in cells of both
+//          boxes, a rectangle; their pair is counted in its smallest cell
+//          (max of the box minima), so once.
+//   long   the rest.  Its walk: for each column (or row, along its major
+//          axis) the cells the segment can reach there, computed in FP64 with
+//          a margin (a superset of the cells of its points).  A long x short
+//          pair is tested in every walked cell holding the short one and
+//          counted in the first cell of the short's box (in row-major order)
+//          that the walk covers; the cell of the intersection point is one of
+//          them, so the pair is counted once.
+//   long x long pairs go to all-pairs tiles over the list of long segments.
+struct FGrid {
+    float x0, y0, inv_w;
+    int G;
+    double w, mx, my;  // cell side; walk margins (x, y)
+};
+
+
+__device__ __forceinline__ int fcell(float v, float o, float inv_w, int G) {
+    const float t = __fmul_rn(__fsub_rn(v, o), inv_w);
+    const int c = t < 1.0e9f ? (t > -1.0e9f ? (int)floorf(t) : 0) : G - 1;
+    return min(max(c, 0), G - 1);
+}
+
+struct CellBox {
+    int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ CellBox cell_box(float4 r, const FGrid &g) {
+    CellBox b;
+    b.x0 = fcell(fminf(r.x, r.z), g.x0, g.inv_w, g.G);
+    b.x1 = fcell(fmaxf(r.x, r.z), g.x0, g.inv_w, g.G);
+    b.y0 = fcell(fminf(r.y, r.w), g.y0, g.inv_w, g.G);
+    b.y1 = fcell(fmaxf(r.y, r.w), g.y0, g.inv_w, g.G);
+    return b;
+}
+
+__device__ __forceinline__ bool is_short_box(const CellBox &b) { return b.x1 - b.x0 <= 1 && b.y1 - b.y0 <= 1; }
+
+// The walk of a long segment: along its major axis (x when |dx| >= |dy|),
+// line i of [lo, hi] covers minor cells [a, b].
+struct Walk {
+    bool xmajor;
+    int lo, hi;
+    double ax, ay, bx, by;  // endpoints, in (major, minor) order
+    double slope;           // d minor / d major
+    double lo_m, hi_m;      // the segment's extent along the major axis
+    double o_maj, o_min;    // grid origin (major, minor)
+    float o_min_f, inv_w;
+    int G;
+    double w, m_maj, m_min;
+};
+
+__device__ __forceinline__ Walk make_walk(float4 r, const FGrid &g) {
+    Walk k;
+    const double dx = (double)r.z - r.x, dy = (double)r.w - r.y;
+    k.xmajor = fabs(dx) >= fabs(dy);
+    const float a_maj = k.xmajor ? r.x : r.y, b_maj = k.xmajor ? r.z : r.w;
+    k.ax = k.xmajor ? r.x : r.y; k.ay = k.xmajor ? r.y : r.x;
+    k.bx = k.xmajor ? r.z : r.w; k.by = k.xmajor ? r.w : r.z;
+    k.lo_m = fmin(k.ax, k.bx); k.hi_m = fmax(k.ax, k.bx);
+    k.slope = k.bx != k.ax ? (k.by - k.ay) / (k.bx - k.ax) : 0.0;
+    const float o_maj = k.xmajor ? g.x0 : g.y0;
+    k.o_min_f = k.xmajor ? g.y0 : g.x0;
+    k.o_maj = o_maj; k.o_min = k.o_min_f;
+    k.inv_w = g.inv_w; k.G = g.G; k.w = g.w;
+    k.m_maj = k.xmajor ? g.mx : g.my;
+    k.m_min = k.xmajor ? g.my : g.mx;
+    k.lo = fcell(fminf(a_maj, b_maj), o_maj, g.inv_w, g.G);
+    k.hi = fcell(fmaxf(a_maj, b_maj), o_maj, g.inv_w, g.G);
+    return k;
+}
+
+// Minor cells [a, b] of major line i of the walk (i in [lo, hi]).
+__device__ __forceinline__ void walk_line(const Walk &k, int i, int &a, int &b) {
+    const double u0 = fmax(k.lo_m, k.o_maj + (double)i * k.w - k.m_maj);
+    const double u1 = fmin(k.hi_m, k.o_maj + (double)(i + 1) * k.w + k.m_maj);
+    double v0, v1;
+    if (k.bx == k.ax) {
+        v0 = fmin(k.ay, k.by);
+        v1 = fmax(k.ay, k.by);
+    } else {
+        const double p = k.ay + (u0 - k.ax) * k.slope, q = k.ay + (u1 - k.ax) * k.slope;
+        v0 = fmin(p, q);
+        v1 = fmax(p, q);
+    }
+    a = fcell((float)(v0 - k.m_min), k.o_min_f, k.inv_w, k.G);
+    b = fcell((float)(v1 + k.m_min), k.o_min_f, k.inv_w, k.G);
+}
+
+// Whether the walk covers cell (cx, cy).
+__device__ __forceinline__ bool walk_covers(const Walk &k, int cx, int cy) {
+    const int i = k.xmajor ? cx : cy, j = k.xmajor ? cy : cx;
+    if (i < k.lo || i > k.hi) return false;
+    int a, b;
+    walk_line(k, i, a, b);
+    return a <= j && j <= b;
+}
+
+__device__ __forceinline__ double ulp32(double v) {  // a unit in the last place of FP32 at |v|
+    const float f = fabsf((float)v);
+    return (double)(nextafterf(f, INFINITY) - f);
+}
+
+__global__ void k_f32_grid_setup(const uint32_t *__restrict__ bounds, int G, FGrid *__restrict__ g) {
+    FGrid q;
+    q.G = G;
+    const bool any = bounds[0] <= bounds[2];
+    const float x0 = any ? unord_f(bounds[0]) : 0.f, y0 = any ? unord_f(bounds[1]) : 0.f;
+    const float x1 = any ? unord_f(bounds[2]) : 0.f, y1 = any ? unord_f(bounds[3]) : 0.f;
+    const double span = fmax((double)x1 - x0, (double)y1 - y0);
+    q.x0 = x0;
+    q.y0 = y0;
+    q.w = span > 0.0 ? span / G : 1.0;
+    q.inv_w = span > 0.0 ? (float)(G / span) : 0.f;
+    // margins: well above the FP32 rounding of the cell function (a few units
+    // in the last place of the coordinates) and the FP64 evaluation of the walk
+    const double ux = fmax(ulp32(x0), ulp32(x1)), uy = fmax(ulp32(y0), ulp32(y1));
+    q.mx = 1e-3 * q.w + 8.0 * ux;
+    q.my = 1e-3 * q.w + 8.0 * uy;
+    *g = q;
+}
+
+// Short segments count their box cells; long ones go to the long list with
+// the number of lines of their walk.
+__global__ void __launch_bounds__(256) k_f32_grid_count(const float4 *__restrict__ seg, DevAcc *acc,
+                                                        const FGrid *__restrict__ gp, uint32_t *__restrict__ cnt,
+                                                        uint32_t *__restrict__ long_idx,
+                                                        uint32_t *__restrict__ long_lines,
+                                                        int2 *__restrict__ walk_meta) {
+    const FGrid g = *gp;
+    const int64_t n = acc->n_seg;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 r = seg[i];
+        const CellBox b = cell_box(r, g);
+        if (is_short_box(b)) {
+            for (int y = b.y0; y <= b.y1; ++y)
+                for (int x = b.x0; x <= b.x1; ++x) atomicAdd(&cnt[y * g.G + x], 1u);
+        } else {
+            auto grp = cg::coalesced_threads();
+            uint32_t base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(&acc->n_long, (uint32_t)grp.size());
+            base = grp.shfl(base, 0);
+            long_idx[base + grp.thread_rank()] = (uint32_t)i;
+            const Walk k = make_walk(r, g);
+            long_lines[base + grp.thread_rank()] = (uint32_t)(k.hi - k.lo + 1);
+            walk_meta[base + grp.thread_rank()] = make_int2(k.lo, k.xmajor ? 1 : 0);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_f32_grid_fill(const float4 *__restrict__ seg, const DevAcc *__restrict__ acc,
+                                                       const FGrid *__restrict__ gp, const uint32_t *__restrict__ off,
+                                                       uint32_t *__restrict__ fill, uint32_t *__restrict__ rec) {
+    const FGrid g = *gp;
+    const int64_t n = acc->n_seg;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const CellBox b = cell_box(seg[i], g);
+        if (!is_short_box(b)) continue;
+        for (int y = b.y0; y <= b.y1; ++y)
+            for (int x = b.x0; x <= b.x1; ++x) {
+                const int c = y * g.G + x;
+                rec[off[c] + atomicAdd(&fill[c], 1u)] = (uint32_t)i;
+            }
+    }
+}
+
+__device__ __forceinline__ void tally(int kind, uint32_t ta, uint32_t tb, uint32_t ideal, PairCounts &pc) {
+    if (kind == PAIR_COLLINEAR) ++pc.collinear;
+    else if (kind == PAIR_PROPER) ++pc.proper;
+    else if (kind == PAIR_TOUCHING) ++pc.touching;
+    if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) pc.dev += dev_term(ta, tb, ideal);
+}
+
+// Short x short: one warp per cell (grid-strided), rows and columns in tiles
+// of 32; a pair counts only in the smallest cell of both boxes.  `visit`
+// runs the cell's tests and calls hit(kind, i, j, theta_i, theta_j) for each
+// counted pair; the kernel runs it once to tally (and count each lane's E_c
+// pairs) and, when pairs are kept, once more to write them at offsets
+// reserved with one atomic per cell.
+__global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
+                                                     const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
+                                                     const uint32_t *__restrict__ off, const uint32_t *__restrict__ rec,
+                                                     DevAcc *acc, uint32_t ideal, uint2 *__restrict__ pairs,
+                                                     uint64_t cap) {
+    __shared__ float4 cs[8][32];
+    __shared__ uint2 cid[8][32];
+    __shared__ uint32_t cth[8][32], cix[8][32];
+    __shared__ uint64_t shu[32];
+    const FGrid g = *gp;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int C = g.G * g.G;
+    PairCounts pc;
+    uint64_t tested = 0;
+    for (int c = blockIdx.x * 8 + wid; c < C; c += gridDim.x * 8) {
+        const uint32_t b0 = off[c], n = off[c + 1] - b0;
+        if (n < 2) continue;
+        const int cxc = c % g.G, cyc = c / g.G;
+        auto visit = [&](auto &&hit, bool count_tests) {
+            for (uint32_t ti = 0; ti * 32 < n; ++ti) {
+                const uint32_t ri_ = ti * 32 + lane;
+                const bool rok = ri_ < n;
+                uint32_t rix = 0;
+                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+                uint2 rid = make_uint2(0, 0);
+                uint32_t rth = 0;
+                CellBox rb{0, 0, 0, 0};
+                if (rok) {
+                    rix = rec[b0 + ri_];
+                    r = seg[rix];
+                    rid = ids[rix];
+                    rth = theta[rix];
+                    rb = cell_box(r, g);
+                }
+                for (uint32_t tj = ti; tj * 32 < n; ++tj) {
+                    const uint32_t cj = tj * 32 + lane;
+                    __syncwarp();
+                    if (cj < n) {
+                        const uint32_t q = rec[b0 + cj];
+                        cs[wid][lane] = seg[q];
+                        cid[wid][lane] = ids[q];
+                        cth[wid][lane] = theta[q];
+                        cix[wid][lane] = q;
+                    }
+                    __syncwarp();
+                    const int mc = (int)min(32u, n - tj * 32);
+                    if (!rok) continue;
+                    if (count_tests) tested += (uint64_t)max(0, mc - ((ti == tj) ? lane + 1 : 0));
+                    for (int jj = (ti == tj) ? lane + 1 : 0; jj < mc; ++jj) {
+                        const float4 q = cs[wid][jj];
+                        const int kind = classify_f32(r, rid, q, cid[wid][jj]);
+                        if (kind == PAIR_NONE) continue;
+                        const CellBox qb = cell_box(q, g);
+                        if (max(rb.x0, qb.x0) != cxc || max(rb.y0, qb.y0) != cyc) continue;  // not the owner cell
+                        hit(kind, rix, cix[wid][jj], rth, cth[wid][jj]);
+                    }
+                }
+            }
+        };
+        uint32_t mine = 0;
+        visit([&](int kind, uint32_t, uint32_t, uint32_t ta, uint32_t tb) {
+            tally(kind, ta, tb, ideal, pc);
+            mine += (kind == PAIR_PROPER || kind == PAIR_TOUCHING) ? 1u : 0u;
+        }, true);
+        if (pairs) {
+            uint32_t total;
+            const uint32_t lo = warp_excl_scan(mine, &total);
+            unsigned long long base = 0;
+            if (lane == 0 && total) base = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)total);
+            uint64_t pos = __shfl_sync(0xffffffffu, base, 0) + lo;
+            if (__any_sync(0xffffffffu, mine != 0))
+                visit([&](int kind, uint32_t ia, uint32_t ib, uint32_t, uint32_t) {
+                    if (kind != PAIR_PROPER && kind != PAIR_TOUCHING) return;
+                    if (pos < cap) pairs[pos] = make_uint2(ia, ib);
+                    ++pos;
+                }, false);
+        }
+    }
+    flush_counts(pc, acc, shu);
+    tested = block_sum<uint64_t>(tested, shu);
+    if (threadIdx.x == 0 && tested) atomic_add_u64(&acc->grid_work, tested);
+}
+
+// The minor-cell range [a, b] of every line of every walk (line u of all
+// walks belongs to the long segment t with line_off[t] <= u < line_off[t + 1]),
+// in FP64 once per line; lines past `cap` are left to the pair kernel.
+__global__ void __launch_bounds__(256) k_f32_walk_lines(const float4 *__restrict__ seg, const FGrid *__restrict__ gp,
+                                                        const uint32_t *__restrict__ long_idx,
+                                                        const uint32_t *__restrict__ line_off, uint32_t line_total_at,
+                                                        const DevAcc *__restrict__ acc, uint64_t cap,
+                                                        int2 *__restrict__ wl) {
+    const FGrid g = *gp;
+    const uint32_t n_long = acc->n_long;
+    const uint32_t total = n_long ? line_off[line_total_at] : 0u;
+    const uint32_t end = (uint32_t)min((uint64_t)total, cap);
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < end; u += gridDim.x * blockDim.x) {
+        const uint32_t t = (uint32_t)find_segment_u32(line_off, n_long, u);
+        const Walk k = make_walk(seg[long_idx[t]], g);
+        int a, b;
+        walk_line(k, k.lo + (int)(u - line_off[t]), a, b);
+        wl[u] = make_int2(a, b);
+    }
+}
+
+// The range of line i of walk t (lo = its first line), from the table or,
+// past its end, recomputed.
+__device__ __forceinline__ int2 line_range(const int2 *__restrict__ wl, uint64_t cap, uint32_t off_t, int lo, int i,
+                                           const float4 &L, const FGrid &g) {
+    const uint64_t u = (uint64_t)off_t + (uint64_t)(i - lo);
+    if (u < cap) return wl[u];
+    const Walk k = make_walk(L, g);
+    int a, b;
+    walk_line(k, i, a, b);
+    return make_int2(a, b);
+}
+
+// Long x short: one thread per line of a long segment's walk, testing the
+// short records of the line's cells.  A pair counts only in the first cell of
+// the short's box (in row-major order) that the walk covers.  Two passes as
+// in k_f32_grid_ss, one reservation per warp.
+__global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
+                                                     const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
+                                                     const uint32_t *__restrict__ off, const uint32_t *__restrict__ rec,
+                                                     const uint32_t *__restrict__ long_idx,
+                                                     const uint32_t *__restrict__ line_off, uint32_t line_total_at,
+                                                     const int2 *__restrict__ walk_meta, const int2 *__restrict__ wl,
+                                                     uint64_t wl_cap, DevAcc *acc, uint32_t ideal,
+                                                     uint2 *__restrict__ pairs, uint64_t cap) {
+    __shared__ uint64_t shu[32];
+    const FGrid g = *gp;
+    const int lane = threadIdx.x & 31;
+    const uint32_t n_long = acc->n_long;
+    const uint32_t total = n_long ? line_off[line_total_at] : 0u;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    PairCounts pc;
+    uint64_t tested = 0;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+        const uint32_t u = base + lane;
+        const bool ok = u < total;
+        uint32_t li = 0, off_t = 0;
+        int lo = 0, hi = 0, i = 0;
+        bool xmajor = true;
+        float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
+        int2 ab = make_int2(0, -1);
+        if (ok) {
+            const uint32_t t = (uint32_t)find_segment_u32(line_off, n_long, u);
+            off_t = line_off[t];
+            hi = (int)(line_off[t + 1] - off_t) - 1;  // relative for now
+            li = long_idx[t];
+            L = seg[li];
+            const int2 m = walk_meta[t];
+            lo = m.x;
+            hi += lo;
+            xmajor = m.y != 0;
+            i = lo + (int)(u - off_t);
+            ab = line_range(wl, wl_cap, off_t, lo, i, L, g);
+        }
+        const uint2 lid = ok ? ids[li] : make_uint2(0, 0);
+        const uint32_t lth = ok ? theta[li] : 0u;
+        auto visit = [&](auto &&hit, bool count_tests) {
+            for (int j = ab.x; j <= ab.y; ++j) {
+                const int cx = xmajor ? i : j, cy = xmajor ? j : i;
+                const int c = cy * g.G + cx;
+                const uint32_t p0 = off[c], p1 = off[c + 1];
+                if (count_tests) tested += p1 - p0;
+                for (uint32_t p = p0; p < p1; ++p) {
+                    const uint32_t q = rec[p];
+                    const float4 S = seg[q];
+                    const int kind = classify_f32(L, lid, S, ids[q]);
+                    if (kind == PAIR_NONE) continue;
+                    // owner: the first cell of the short's box (row-major) on the
+                    // walk; this cell is on it, so only the cells before it matter
+                    const CellBox sb = cell_box(S, g);
+                    bool earlier = false;
+                    for (int y = sb.y0; y <= cy && !earlier; ++y)
+                        for (int x = sb.x0; x <= sb.x1; ++x) {
+                            if (y == cy && x == cx) break;
+                            const int li2 = xmajor ? x : y, lj2 = xmajor ? y : x;
+                            if (li2 < lo || li2 > hi) continue;
+                            const int2 r2 = line_range(wl, wl_cap, off_t, lo, li2, L, g);
+                            if (r2.x <= lj2 && lj2 <= r2.y) {
+                                earlier = true;
+                                break;
+                            }
+                        }
+                    if (earlier) continue;
+                    hit(kind, li, q, lth, theta[q]);
+                }
+            }
+        };
+        uint32_t mine = 0;
+        visit([&](int kind, uint32_t, uint32_t, uint32_t ta, uint32_t tb) {
+            tally(kind, ta, tb, ideal, pc);
+            mine += (kind == PAIR_PROPER || kind == PAIR_TOUCHING) ? 1u : 0u;
+        }, true);
+        if (pairs) {
+            uint32_t wt;
+            const uint32_t lo_off = warp_excl_scan(mine, &wt);
+            unsigned long long wb = 0;
+            if (lane == 0 && wt) wb = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)wt);
+            uint64_t pos = __shfl_sync(0xffffffffu, wb, 0) + lo_off;
+            if (mine)
+                visit([&](int kind, uint32_t ia, uint32_t ib, uint32_t, uint32_t) {
+                    if (kind != PAIR_PROPER && kind != PAIR_TOUCHING) return;
+                    if (pos < cap) pairs[pos] = make_uint2(ia, ib);
+                    ++pos;
+                }, false);
+        }
+    }
+    flush_counts(pc, acc, shu);
+    tested = block_sum<uint64_t>(tested, shu);
+    if (threadIdx.x == 0 && tested) atomic_add_u64(&acc->grid_work, tested);
 }
 
 // ------------------------------------------------------ min angle (FP32)
@@ -404,32 +905,46 @@ __device__ __forceinline__ void atomic_add2(float *g, int64_t v, float x, float 
 // d E_ca: a_c is the acute angle between the lines of directions theta_u,
 // theta_v; the fold (d = theta_u - theta_v mod pi, a_c = d or pi - d) and the
 // sign of a_c - ideal are read from the same integer directions the forward
-// used.  d theta / d q = (-dy, dx) / |q - p|^2 for the vector q - p.
-__global__ void __launch_bounds__(256) k_grad_cross(const uint2 *__restrict__ pairs, const float4 *__restrict__ seg,
-                                                    const uint2 *__restrict__ ids, const uint32_t *__restrict__ theta,
+// used.  First the adjoint of every segment's direction is summed over its
+// E_c pairs (FP64, two atomics per pair); then each segment turns it into its
+// endpoints' gradients: d theta / d q = (-dy, dx) / |q - p|^2 for the vector
+// q - p.
+__global__ void __launch_bounds__(256) k_grad_theta(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ theta,
                                                     const DiffState *__restrict__ st, const float *__restrict__ gout,
-                                                    uint32_t ideal_u, float *__restrict__ grad) {
+                                                    uint32_t ideal_u, double *__restrict__ adj) {
     const DiffState d = *st;
     const uint64_t n = min((uint64_t)d.pairs, (uint64_t)d.ec);
     if (d.ec == 0) return;
     const double scale = -(double)gout[0] / (d.ideal * (double)d.ec);
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint2 pr = pairs[p];
-        const float4 r = seg[pr.x], c = seg[pr.y];
-        const uint2 ri = ids[pr.x], ci = ids[pr.y];
         const uint32_t dd = theta[pr.x] - theta[pr.y];
         const bool folded = dd > 0x80000000u;           // a_c = pi - d
         const uint32_t a = folded ? 0u - dd : dd;
         const double sgn = a > ideal_u ? 1.0 : (a < ideal_u ? -1.0 : 0.0);
-        const double coef = scale * sgn * (folded ? -1.0 : 1.0);  // d E_ca / d theta_u
-        const double ux = (double)r.z - r.x, uy = (double)r.w - r.y, vx = (double)c.z - c.x, vy = (double)c.w - c.y;
-        const double ru = ux * ux + uy * uy, rv = vx * vx + vy * vy;
-        const float gux = (float)(coef * -uy / ru), guy = (float)(coef * ux / ru);
-        const float gvx = (float)(coef * -vy / rv), gvy = (float)(coef * vx / rv);
-        atomic_add2(grad, ri.y, gux, guy);
-        atomic_add2(grad, ri.x, -gux, -guy);
-        atomic_add2(grad, ci.y, -gvx, -gvy);
-        atomic_add2(grad, ci.x, gvx, gvy);
+        const double coef = scale * sgn * (folded ? -1.0 : 1.0);  // d E_ca / d theta_u = -d E_ca / d theta_v
+        if (coef != 0.0) {
+            atomicAdd(&adj[pr.x], coef);
+            atomicAdd(&adj[pr.y], -coef);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_grad_theta_scatter(const float4 *__restrict__ seg,
+                                                            const uint2 *__restrict__ ids,
+                                                            const DevAcc *__restrict__ acc,
+                                                            const double *__restrict__ adj, float *__restrict__ grad) {
+    const int64_t n = acc->n_seg;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double c = adj[i];
+        if (c == 0.0) continue;
+        const float4 r = seg[i];
+        const uint2 v = ids[i];
+        const double ux = (double)r.z - r.x, uy = (double)r.w - r.y;
+        const double ru = ux * ux + uy * uy;
+        const float gx = (float)(c * -uy / ru), gy = (float)(c * ux / ru);
+        atomic_add2(grad, v.y, gx, gy);
+        atomic_add2(grad, v.x, -gx, -gy);
     }
 }
 
@@ -481,6 +996,7 @@ __global__ void __launch_bounds__(256) k_grad_min_angle(const int2 *__restrict__
 
 // ------------------------------------------------------------- launchers
 void launch_gather_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E, Buffers &b, cudaStream_t s) {
+    cudaMemsetAsync(&b.acc->f32_bounds[0], 0xff, 2 * sizeof(uint32_t), s);  // minima (the maxima start at 0)
     count_launches(V > 0 ? 1 : 0);
     if (V > 0) k_check_vertices_f32<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const float2 *)xy, V, b.acc);
     if (E <= 0) return;
@@ -497,8 +1013,59 @@ void launch_crossings_f32(const Buffers &b, int64_t n_bound, uint32_t ideal, uin
     const int64_t tiles = nb * (nb + 1) / 2;
     const unsigned grid = (unsigned)(tiles < (int64_t(1) << 30) ? tiles : (int64_t(1) << 30));
     count_launches(1);
-    k_cross_f32<<<grid, DF_ROWS, 0, s>>>((const float4 *)b.seg, b.seg_ids, b.seg_theta, b.acc, ideal, tiles, pairs,
-                                         cap);
+    k_cross_f32<<<grid, DF_ROWS, 0, s>>>((const float4 *)b.seg, b.seg_ids, b.seg_theta, nullptr, &b.acc->n_seg,
+                                         b.acc, ideal, tiles, pairs, cap);
+}
+
+// Lines of the walk table: up to 16 per edge (more are recomputed when needed).
+uint64_t f32_walk_lines_cap(int64_t E) { return 16 * (uint64_t)E + 1024; }
+
+size_t f32_grid_bytes(int G, int64_t E) {
+    const size_t C = (size_t)G * G;
+    return sizeof(FGrid) + sizeof(uint32_t) * ((C + 1) + C + 4 * (size_t)E + 2 * (size_t)E + 1) +
+           sizeof(int2) * ((size_t)E + f32_walk_lines_cap(E)) + 256 * 10;
+}
+
+void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, uint32_t ideal, uint2 *pairs,
+                               uint64_t cap, cudaStream_t s) {
+    if (E < 2) return;
+    const size_t C = (size_t)G * G;
+    char *p = (char *)work;
+    auto take = [&](size_t bytes) {
+        char *q = p;
+        p += (bytes + 255) & ~(size_t)255;
+        return q;
+    };
+    FGrid *g = (FGrid *)take(sizeof(FGrid));
+
+    uint32_t *cnt = (uint32_t *)take(sizeof(uint32_t) * (C + 1));
+    uint32_t *fill = (uint32_t *)take(sizeof(uint32_t) * C);
+    uint32_t *rec = (uint32_t *)take(sizeof(uint32_t) * 4 * (size_t)E);
+    uint32_t *long_idx = (uint32_t *)take(sizeof(uint32_t) * (size_t)E);
+    uint32_t *long_lines = (uint32_t *)take(sizeof(uint32_t) * ((size_t)E + 1));
+    int2 *walk_meta = (int2 *)take(sizeof(int2) * (size_t)E);
+    const uint64_t wl_cap = f32_walk_lines_cap(E);
+    int2 *wl = (int2 *)take(sizeof(int2) * wl_cap);
+    cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (C + 1), s);
+    cudaMemsetAsync(fill, 0, sizeof(uint32_t) * C, s);
+    const float4 *seg = (const float4 *)b.seg;
+    const int gb = grid_for(E, 256, 152 * 8);
+    count_launches(3);
+    k_f32_grid_setup<<<1, 1, 0, s>>>(b.acc->f32_bounds, G, g);
+    cudaMemsetAsync(long_lines, 0, sizeof(uint32_t) * ((size_t)E + 1), s);
+    k_f32_grid_count<<<gb, 256, 0, s>>>(seg, b.acc, g, cnt, long_idx, long_lines, walk_meta);
+    launch_scan_u32(long_lines, long_lines, E, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
+    count_launches(1);
+    k_f32_walk_lines<<<152 * 8, 256, 0, s>>>(seg, g, long_idx, long_lines, (uint32_t)E, b.acc, wl_cap, wl);
+    launch_scan_u32(cnt, cnt, (int64_t)C, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
+    k_f32_grid_fill<<<gb, 256, 0, s>>>(seg, b.acc, g, cnt, fill, rec);
+    count_launches(3);
+    k_f32_grid_ss<<<grid_for((int64_t)C, 8, 152 * 16), 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, b.acc,
+                                                                    ideal, pairs, cap);
+    k_f32_grid_ls<<<152 * 8, 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, long_idx, long_lines,
+                                          (uint32_t)E, walk_meta, wl, wl_cap, b.acc, ideal, pairs, cap);
+    k_cross_f32<<<152 * 8, DF_ROWS, 0, s>>>(seg, b.seg_ids, b.seg_theta, long_idx, &b.acc->n_long, b.acc, ideal, -1,
+                                            pairs, cap);
 }
 
 void launch_min_angle_f32(Buffers &b, int64_t V, int64_t E, int2 *arg, cudaStream_t s) {
@@ -523,12 +1090,13 @@ void launch_diff_state(const Buffers &b, int64_t V, int64_t E, double ideal, Dif
 }
 
 void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *pairs, const int2 *arg,
-                          const DiffState *st, const float *gout, uint32_t ideal_u, uint64_t n_pairs, float *grad,
-                          cudaStream_t s) {
+                          const DiffState *st, const float *gout, uint32_t ideal_u, uint64_t n_pairs, double *adj,
+                          float *grad, cudaStream_t s) {
     cudaMemsetAsync(grad, 0, sizeof(float) * 2 * V, s);
-    count_launches(3);
-    k_grad_cross<<<grid_for((int64_t)n_pairs, 256, 152 * 16), 256, 0, s>>>(pairs, (const float4 *)b.seg, b.seg_ids,
-                                                                          b.seg_theta, st, gout, ideal_u, grad);
+    cudaMemsetAsync(adj, 0, sizeof(double) * (E > 0 ? E : 1), s);
+    count_launches(4);
+    k_grad_theta<<<grid_for((int64_t)n_pairs, 256, 152 * 16), 256, 0, s>>>(pairs, b.seg_theta, st, gout, ideal_u, adj);
+    k_grad_theta_scatter<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const float4 *)b.seg, b.seg_ids, b.acc, adj, grad);
     k_grad_elv<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.edges, (const float2 *)b.xy, E, st, gout,
                                                          grad);
     k_grad_min_angle<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>(arg, b.deg, (const float2 *)b.xy, V, st, gout, grad);

@@ -183,3 +183,57 @@ def test_differentiable_workload_full_size():
         d = cuda(np.zeros((len(xy), 2), np.float32))
         gr.gr_diff_backward(L.handle, np.array([-1, 1, -1], np.float32), d)
         grad_close(d.cpu().numpy(), -g_eca + g_ml - g_ma, "full size")
+
+
+def f32_forward(xy, e, path=0):
+    with gr.Layout(cuda(xy), cuda(e), gr.gr_options(path, 0, 0, 0), coord_type=gr.GR_COORD_F32) as L:
+        return L.evaluate(FWD, IDEAL)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fp32_grid_on_degenerate_layouts(seed):
+    # enough edges for the grid; coordinates k / 64 in a small box: collinear
+    # overlaps, touching, coincident endpoints, duplicate edges, lines along cell edges
+    rng = np.random.default_rng(300 + seed)
+    L0 = synth.tiny_degenerate_layout(rng, 400, 3000, span=int(rng.integers(3, 60)))
+    xy = (L0.xy.astype(np.float64) / 64.0 + [0.0, 3.0, -7.5, 1e3, 0.25, -1e4][seed]).astype(np.float32)
+    r = f32_forward(xy, L0.edges)
+    check_forward(xy, L0.edges, r, f"seed {seed}")
+    a = f32_forward(xy, L0.edges, gr.GR_PATH_ALLPAIRS)
+    assert r.crossing.angle_dev_sum == pytest.approx(a.crossing.angle_dev_sum, rel=1e-12, abs=1e-9)
+
+
+@pytest.mark.parametrize("case", ["lattice", "offset", "wide", "clustered"])
+def test_fp32_grid_matches_allpairs_and_oracle(case):
+    rng = np.random.default_rng({"lattice": 1, "offset": 2, "wide": 3, "clustered": 4}[case])
+    V = 2500
+    if case == "lattice":  # vertices on the grid's own lines (the bounding box is [0, 1])
+        xy = (rng.integers(0, 65, size=(V, 2)) / 64.0).astype(np.float32)
+        xy[0], xy[1] = (0.0, 0.0), (1.0, 1.0)
+    elif case == "offset":  # coordinates far from the origin: cells a few FP32 ulps wide
+        xy = (1.0e5 + rng.random((V, 2)) * 0.25).astype(np.float32)
+    elif case == "wide":  # exponents over many binades
+        xy = (np.sign(rng.random((V, 2)) - 0.5) * 2.0 ** rng.uniform(-30, 30, size=(V, 2))).astype(np.float32)
+    else:
+        xy = (rng.normal(0.5, 0.01, size=(V, 2))).astype(np.float32)
+        xy[: V // 10] = rng.random((V // 10, 2)).astype(np.float32)
+    e = synth.add_random_edges(rng, V, synth.knn_edges(xy.astype(np.float64), 3, 5000), 600)
+    r = f32_forward(xy, e)
+    check_forward(xy, e, r, case)
+    a = f32_forward(xy, e, gr.GR_PATH_ALLPAIRS)
+    assert (r.crossing.c.proper, r.crossing.c.touching, r.crossing.c.collinear_overlaps) == \
+        (a.crossing.c.proper, a.crossing.c.touching, a.crossing.c.collinear_overlaps)
+
+
+def test_fp32_grid_gradients_equal_allpairs_gradients():
+    xy, e = random_float_layout(77, 6000, 14000, 900)
+    grads = []
+    for path in (0, gr.GR_PATH_ALLPAIRS):
+        with gr.Layout(cuda(xy), cuda(e), gr.gr_options(path, 0, 0, 0), coord_type=gr.GR_COORD_F32) as L:
+            out = gr.gr_diff_forward(L.handle, IDEAL)
+            d = cuda(np.zeros((len(xy), 2), np.float32))
+            gr.gr_diff_backward(L.handle, np.array([-1, 1, -1], np.float32), d)
+            grads.append((out.copy(), d.cpu().numpy().astype(np.float64)))
+    assert np.array_equal(grads[0][0], grads[1][0])
+    g0, g1 = grads[0][1], grads[1][1]
+    assert np.linalg.norm(g0 - g1) <= 1e-6 * np.linalg.norm(g1)
