@@ -187,8 +187,9 @@ def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload:
         pairs = res.crossing.c.pairs_tested
         ops = pairs * OPS_PER_PAIR + ec * (OPS_PER_CROSSING_GRID if grid else OPS_PER_CROSSING_ALLPAIRS)
         peak = SM_COUNT * LANES_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        kernel = "k_grid_pairs" if grid else "k_cross_allpairs"
-        src = ["k_grid.cu", "pair_math.cuh"] if grid else ["k_crossings.cu", "pair_math.cuh"]
+        kernel = "k_grid_pairs" if grid else "k_cross_allpairs_agg"
+        src = (["k_grid.cu", "grid_common.cuh", "pair_math.cuh"] if grid
+               else ["k_crossings.cu", "allpairs_common.cuh", "pair_math.cuh"])
         achieved = ops / t / 1e12
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Tops/s (int32-equivalent lane ops)", "frac": achieved / peak,
@@ -202,7 +203,7 @@ def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload:
     achieved = nbytes / t / 1e9
     return {"kernel": "k_grid_fill", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_kind})",
-            "traffic": load_traffic("k_grid_fill", workload, kernel_source_hash(["k_grid.cu"])),
+            "traffic": load_traffic("k_grid_fill", workload, kernel_source_hash(["k_grid.cu", "grid_common.cuh"])),
             "launch_ms": t * 1e3}
 
 
