@@ -201,24 +201,49 @@ __device__ __forceinline__ bool owns_collinear(const GSeg &r, const GSeg &c, int
     return 0 <= lx && lx < w && 0 <= ly && ly < w;
 }
 
-// Owner test with an FP32 fast path.  For two "exact" segments (see GSeg)
+// Owner test with FP32 fast paths.  For two "exact" segments (see GSeg)
 // num = (c - a) x v and den = u x v are exact integers in FP32 (|den| <= 2^21,
 // |num| <= 2^24), t = num / den carries a relative error below 2^-21 and
 // P_x = a_x + u_x t an absolute error below 2^-11 (|u_x t| <= 2^10, |P_x| <
 // 2^13).  P is decided inside or outside the half-open cell [0, w)^2 when it
-// is further than 2^-9 from the cell's border; otherwise, or for segments
-// that are not both exact, the exact int64 test decides.
+// is further than 2^-9 from the cell's border.  For other segments (cell-
+// relative integer coordinates below 2^17, so every input and difference is
+// exact in FP32) each product carries a relative error of at most 2^-24, so
+// |den~ - den| <= bd = 2^-22 (|u_x v_y| + |u_y v_x|) and likewise bn for num
+// (a factor 4 to spare); when |den~| > 4 bd, t~ = num~ / den~ is within
+// et = (bn + |t~| bd) / (|den~| - 2 bd) + 2^-22 |t~| of t, and P~ within
+// |u| et + 2^-22 (|P~| + 1) of P, a margin doubled again for the decision.
+// Otherwise, and near a border, the exact int64 test decides.
 __device__ __forceinline__ bool owns_crossing_fast(const GSeg &r, const GSeg &c, int w) {
+    const float fw = (float)w;
     if (r.exact & c.exact) {
         const float den = r.ux * c.uy - r.uy * c.ux;
         const float num = (c.ax - r.ax) * c.uy - (c.ay - r.ay) * c.ux;
         const float t = __fdividef(num, den);
         const float X = fmaf(r.ux, t, r.ax), Y = fmaf(r.uy, t, r.ay);
-        const float e = 1.0f / 512.0f, fw = (float)w;
+        const float e = 1.0f / 512.0f;
         const bool in = X >= e && X < fw - e && Y >= e && Y < fw - e;
         const bool out = X < -e || X >= fw + e || Y < -e || Y >= fw + e;
         if (in) return true;
         if (out) return false;
+    } else {
+        const float p1 = r.ux * c.uy, p2 = r.uy * c.ux;
+        const float dx = c.ax - r.ax, dy = c.ay - r.ay;
+        const float q1 = dx * c.uy, q2 = dy * c.ux;
+        const float den = p1 - p2, num = q1 - q2;
+        const float bd = 0x1p-22f * (fabsf(p1) + fabsf(p2)), bn = 0x1p-22f * (fabsf(q1) + fabsf(q2));
+        if (fabsf(den) > 4.0f * bd) {
+            const float t = num / den;
+            const float at = fabsf(t);
+            const float et = (bn + at * bd) / (fabsf(den) - 2.0f * bd) + 0x1p-22f * at;
+            const float X = fmaf(r.ux, t, r.ax), Y = fmaf(r.uy, t, r.ay);
+            const float ex = 2.0f * (fabsf(r.ux) * et + 0x1p-22f * (fabsf(X) + 1.0f));
+            const float ey = 2.0f * (fabsf(r.uy) * et + 0x1p-22f * (fabsf(Y) + 1.0f));
+            const bool in = X >= ex && X < fw - ex && Y >= ey && Y < fw - ey;
+            const bool out = X < -ex || X >= fw + ex || Y < -ey || Y >= fw + ey;
+            if (in) return true;
+            if (out) return false;
+        }
     }
     const int iax = (int)r.ax, iay = (int)r.ay, icx = (int)c.ax, icy = (int)c.ay;
     return owns_crossing(iax, iay, (int)r.bx - iax, (int)r.by - iay, icx, icy, (int)c.bx - icx, (int)c.by - icy, w);
