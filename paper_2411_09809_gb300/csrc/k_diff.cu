@@ -95,6 +95,8 @@ __device__ __noinline__ int orient_exact(double px, double py, double qx, double
     return (top > 0.0) - (top < 0.0);
 }
 
+__device__ __noinline__ int orient_f64(float px, float py, float qx, float qy, float rx, float ry);
+
 __device__ __forceinline__ int orient_f32(float px, float py, float qx, float qy, float rx, float ry) {
     const float e32 = 5.9604645e-08f;  // 2^-24
     const float t1 = (qx - px) * (ry - py), t2 = (qy - py) * (rx - px), d = t1 - t2;
@@ -105,6 +107,12 @@ __device__ __forceinline__ int orient_f32(float px, float py, float qx, float qy
         if (d > b32) return 1;
         if (-d > b32) return -1;
     }
+    return orient_f64(px, py, qx, qy, rx, ry);
+}
+
+// The FP64 stage and the exact fallback (out of line: rare, and their FP64
+// code must not be if-converted into the FP32 callers).
+__device__ __noinline__ int orient_f64(float px, float py, float qx, float qy, float rx, float ry) {
     const double e64 = 1.1102230246251565e-16;  // 2^-53
     const double T1 = ((double)qx - (double)px) * ((double)ry - (double)py);
     const double T2 = ((double)qy - (double)py) * ((double)rx - (double)px);
@@ -660,22 +668,31 @@ __global__ void __launch_bounds__(256) k_f32_walk_lines(const float4 *__restrict
     }
 }
 
-// The range of line i of walk t (lo = its first line), from the table or,
-// past its end, recomputed.
-__device__ __forceinline__ int2 line_range(const int2 *__restrict__ wl, uint64_t cap, uint32_t off_t, int lo, int i,
-                                           const float4 &L, const FGrid &g) {
-    const uint64_t u = (uint64_t)off_t + (uint64_t)(i - lo);
-    if (u < cap) return wl[u];
+// Line i of a walk recomputed (kept out of line: a rare path whose FP64
+// code must not be if-converted into its callers).
+__device__ __noinline__ int2 line_range_slow(float4 L, FGrid g, int i) {
     const Walk k = make_walk(L, g);
     int a, b;
     walk_line(k, i, a, b);
     return make_int2(a, b);
 }
 
-// Long x short: one thread per line of a long segment's walk, testing the
-// short records of the line's cells.  A pair counts only in the first cell of
-// the short's box (in row-major order) that the walk covers.  Two passes as
-// in k_f32_grid_ss, one reservation per warp.
+// The range of line i of walk t (lo = its first line), from the table or,
+// past its end, recomputed.
+__device__ __forceinline__ int2 line_range(const int2 *__restrict__ wl, uint64_t cap, uint32_t off_t, int lo, int i,
+                                           const float4 &L, const FGrid &g) {
+    const uint64_t u = (uint64_t)off_t + (uint64_t)(i - lo);
+    if (u < cap) return wl[u];
+    return line_range_slow(L, g, i);
+}
+
+// Long x short: a warp takes 32 consecutive lines of the walks (line u
+// belongs to the long segment t with line_off[t] <= u < line_off[t + 1]) and
+// spreads the (line, short record) pairs of their cells over its lanes, so
+// that every lane tests a pair in every round.  A pair counts only in the
+// first cell of the short's box (in row-major order) that the walk covers.
+// Two passes as in k_f32_grid_ss: tally and count, then (when pairs are
+// kept) write at offsets reserved once per warp and chunk.
 __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
                                                      const uint32_t *__restrict__ off, const uint32_t *__restrict__ rec,
@@ -693,76 +710,106 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
     PairCounts pc;
     uint64_t tested = 0;
     for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+        // this lane's line: its long segment, the line's minor-cell range and its record count
         const uint32_t u = base + lane;
         const bool ok = u < total;
         uint32_t li = 0, off_t = 0;
         int lo = 0, hi = 0, i = 0;
-        bool xmajor = true;
+        int xmaj = 1;
         float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
         int2 ab = make_int2(0, -1);
+        uint32_t cnt = 0;
         if (ok) {
             const uint32_t t = (uint32_t)find_segment_u32(line_off, n_long, u);
             off_t = line_off[t];
-            hi = (int)(line_off[t + 1] - off_t) - 1;  // relative for now
             li = long_idx[t];
             L = seg[li];
             const int2 m = walk_meta[t];
             lo = m.x;
-            hi += lo;
-            xmajor = m.y != 0;
+            hi = lo + (int)(line_off[t + 1] - off_t) - 1;
+            xmaj = m.y;
             i = lo + (int)(u - off_t);
             ab = line_range(wl, wl_cap, off_t, lo, i, L, g);
-        }
-        const uint2 lid = ok ? ids[li] : make_uint2(0, 0);
-        const uint32_t lth = ok ? theta[li] : 0u;
-        auto visit = [&](auto &&hit, bool count_tests) {
             for (int j = ab.x; j <= ab.y; ++j) {
-                const int cx = xmajor ? i : j, cy = xmajor ? j : i;
-                const int c = cy * g.G + cx;
-                const uint32_t p0 = off[c], p1 = off[c + 1];
-                if (count_tests) tested += p1 - p0;
-                for (uint32_t p = p0; p < p1; ++p) {
-                    const uint32_t q = rec[p];
-                    const float4 S = seg[q];
-                    const int kind = classify_f32(L, lid, S, ids[q]);
-                    if (kind == PAIR_NONE) continue;
-                    // owner: the first cell of the short's box (row-major) on the
-                    // walk; this cell is on it, so only the cells before it matter
-                    const CellBox sb = cell_box(S, g);
-                    bool earlier = false;
-                    for (int y = sb.y0; y <= cy && !earlier; ++y)
-                        for (int x = sb.x0; x <= sb.x1; ++x) {
-                            if (y == cy && x == cx) break;
-                            const int li2 = xmajor ? x : y, lj2 = xmajor ? y : x;
-                            if (li2 < lo || li2 > hi) continue;
-                            const int2 r2 = line_range(wl, wl_cap, off_t, lo, li2, L, g);
-                            if (r2.x <= lj2 && lj2 <= r2.y) {
-                                earlier = true;
-                                break;
-                            }
-                        }
-                    if (earlier) continue;
-                    hit(kind, li, q, lth, theta[q]);
+                const int c = xmaj ? j * g.G + i : i * g.G + j;
+                cnt += off[c + 1] - off[c];
+            }
+        }
+        tested += cnt;
+        uint32_t chunk_total;
+        const uint32_t pre = warp_excl_scan(cnt, &chunk_total);
+        auto visit = [&](auto &&hit) {
+            for (uint32_t b0 = 0; b0 < chunk_total; b0 += 32) {
+                const uint32_t q = b0 + lane;
+                int o = 0;  // the lane whose line holds pair q
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const uint32_t pp = __shfl_sync(0xffffffffu, pre, o + step);
+                    if (pp <= q) o += step;
                 }
+                const uint32_t pre_o = __shfl_sync(0xffffffffu, pre, o);
+                const uint32_t li_o = __shfl_sync(0xffffffffu, li, o);
+                const uint32_t off_o = __shfl_sync(0xffffffffu, off_t, o);
+                const int lo_o = __shfl_sync(0xffffffffu, lo, o), hi_o = __shfl_sync(0xffffffffu, hi, o);
+                const int i_o = __shfl_sync(0xffffffffu, i, o), xm_o = __shfl_sync(0xffffffffu, xmaj, o);
+                const int a_o = __shfl_sync(0xffffffffu, ab.x, o);
+                float4 Lo;
+                Lo.x = __shfl_sync(0xffffffffu, L.x, o);
+                Lo.y = __shfl_sync(0xffffffffu, L.y, o);
+                Lo.z = __shfl_sync(0xffffffffu, L.z, o);
+                Lo.w = __shfl_sync(0xffffffffu, L.w, o);
+                if (q >= chunk_total) continue;
+                // the cell and record of pair q within the line
+                uint32_t k = q - pre_o;
+                int j = a_o, c = 0;
+                uint32_t p;
+                for (;; ++j) {
+                    c = xm_o ? j * g.G + i_o : i_o * g.G + j;
+                    const uint32_t n_c = off[c + 1] - off[c];
+                    if (k < n_c) break;
+                    k -= n_c;
+                }
+                p = off[c] + k;
+                const int cx = xm_o ? i_o : j, cy = xm_o ? j : i_o;
+                const uint32_t qs = rec[p];
+                const float4 S = seg[qs];
+                const int kind = classify_f32(Lo, ids[li_o], S, ids[qs]);
+                if (kind == PAIR_NONE) continue;
+                // owner: the first cell of the short's box (row-major) on the
+                // walk; this cell is on it, so only the cells before it matter
+                const CellBox sb = cell_box(S, g);
+                bool earlier = false;
+                for (int y = sb.y0; y <= cy && !earlier; ++y)
+                    for (int x = sb.x0; x <= sb.x1; ++x) {
+                        if (y == cy && x == cx) break;
+                        const int l2 = xm_o ? x : y, m2 = xm_o ? y : x;
+                        if (l2 < lo_o || l2 > hi_o) continue;
+                        const int2 r2 = line_range(wl, wl_cap, off_o, lo_o, l2, Lo, g);
+                        if (r2.x <= m2 && m2 <= r2.y) {
+                            earlier = true;
+                            break;
+                        }
+                    }
+                if (earlier) continue;
+                hit(kind, li_o, qs, theta[li_o], theta[qs]);
             }
         };
         uint32_t mine = 0;
         visit([&](int kind, uint32_t, uint32_t, uint32_t ta, uint32_t tb) {
             tally(kind, ta, tb, ideal, pc);
             mine += (kind == PAIR_PROPER || kind == PAIR_TOUCHING) ? 1u : 0u;
-        }, true);
-        if (pairs) {
+        });
+        if (pairs && __any_sync(0xffffffffu, mine != 0)) {
             uint32_t wt;
             const uint32_t lo_off = warp_excl_scan(mine, &wt);
             unsigned long long wb = 0;
             if (lane == 0 && wt) wb = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)wt);
             uint64_t pos = __shfl_sync(0xffffffffu, wb, 0) + lo_off;
-            if (mine)
-                visit([&](int kind, uint32_t ia, uint32_t ib, uint32_t, uint32_t) {
-                    if (kind != PAIR_PROPER && kind != PAIR_TOUCHING) return;
-                    if (pos < cap) pairs[pos] = make_uint2(ia, ib);
-                    ++pos;
-                }, false);
+            visit([&](int kind, uint32_t ia, uint32_t ib, uint32_t, uint32_t) {
+                if (kind != PAIR_PROPER && kind != PAIR_TOUCHING) return;
+                if (pos < cap) pairs[pos] = make_uint2(ia, ib);
+                ++pos;
+            });
         }
     }
     flush_counts(pc, acc, shu);
