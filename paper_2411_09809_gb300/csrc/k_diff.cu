@@ -537,7 +537,8 @@ __global__ void __launch_bounds__(256) k_f32_grid_count(const float4 *__restrict
 
 __global__ void __launch_bounds__(256) k_f32_grid_fill(const float4 *__restrict__ seg, const DevAcc *__restrict__ acc,
                                                        const FGrid *__restrict__ gp, const uint32_t *__restrict__ off,
-                                                       uint32_t *__restrict__ fill, uint32_t *__restrict__ rec) {
+                                                       uint32_t *__restrict__ fill, uint32_t *__restrict__ rec,
+                                                       uint32_t *__restrict__ rec_cell) {
     const FGrid g = *gp;
     const int64_t n = acc->n_seg;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -546,7 +547,9 @@ __global__ void __launch_bounds__(256) k_f32_grid_fill(const float4 *__restrict_
         for (int y = b.y0; y <= b.y1; ++y)
             for (int x = b.x0; x <= b.x1; ++x) {
                 const int c = y * g.G + x;
-                rec[off[c] + atomicAdd(&fill[c], 1u)] = (uint32_t)i;
+                const uint32_t pos = off[c] + atomicAdd(&fill[c], 1u);
+                rec[pos] = (uint32_t)i;
+                rec_cell[pos] = (uint32_t)c;
             }
     }
 }
@@ -558,88 +561,70 @@ __device__ __forceinline__ void tally(int kind, uint32_t ta, uint32_t tb, uint32
     if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) pc.dev += dev_term(ta, tb, ideal);
 }
 
-// Short x short: one warp per cell (grid-strided), rows and columns in tiles
-// of 32; a pair counts only in the smallest cell of both boxes.  `visit`
-// runs the cell's tests and calls hit(kind, i, j, theta_i, theta_j) for each
-// counted pair; the kernel runs it once to tally (and count each lane's E_c
-// pairs) and, when pairs are kept, once more to write them at offsets
-// reserved with one atomic per cell.
+// Short x short: one thread per record (row), against the later records of
+// its cell; a pair counts only in the smallest cell of both boxes.  Consecutive
+// records belong to the same or neighbouring cells, so a warp's rows are
+// short loops of similar length.  Two passes: tally and count, then (when
+// pairs are kept) write at offsets reserved once per warp and chunk.
 __global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
                                                      const uint32_t *__restrict__ off, const uint32_t *__restrict__ rec,
-                                                     DevAcc *acc, uint32_t ideal, uint2 *__restrict__ pairs,
-                                                     uint64_t cap) {
-    __shared__ float4 cs[8][32];
-    __shared__ uint2 cid[8][32];
-    __shared__ uint32_t cth[8][32], cix[8][32];
+                                                     const uint32_t *__restrict__ rec_cell, DevAcc *acc,
+                                                     uint32_t ideal, uint2 *__restrict__ pairs, uint64_t cap) {
     __shared__ uint64_t shu[32];
     const FGrid g = *gp;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int C = g.G * g.G;
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = off[g.G * g.G];
+    const uint32_t stride = gridDim.x * blockDim.x;
     PairCounts pc;
     uint64_t tested = 0;
-    for (int c = blockIdx.x * 8 + wid; c < C; c += gridDim.x * 8) {
-        const uint32_t b0 = off[c], n = off[c + 1] - b0;
-        if (n < 2) continue;
-        const int cxc = c % g.G, cyc = c / g.G;
-        auto visit = [&](auto &&hit, bool count_tests) {
-            for (uint32_t ti = 0; ti * 32 < n; ++ti) {
-                const uint32_t ri_ = ti * 32 + lane;
-                const bool rok = ri_ < n;
-                uint32_t rix = 0;
-                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                uint2 rid = make_uint2(0, 0);
-                uint32_t rth = 0;
-                CellBox rb{0, 0, 0, 0};
-                if (rok) {
-                    rix = rec[b0 + ri_];
-                    r = seg[rix];
-                    rid = ids[rix];
-                    rth = theta[rix];
-                    rb = cell_box(r, g);
-                }
-                for (uint32_t tj = ti; tj * 32 < n; ++tj) {
-                    const uint32_t cj = tj * 32 + lane;
-                    __syncwarp();
-                    if (cj < n) {
-                        const uint32_t q = rec[b0 + cj];
-                        cs[wid][lane] = seg[q];
-                        cid[wid][lane] = ids[q];
-                        cth[wid][lane] = theta[q];
-                        cix[wid][lane] = q;
-                    }
-                    __syncwarp();
-                    const int mc = (int)min(32u, n - tj * 32);
-                    if (!rok) continue;
-                    if (count_tests) tested += (uint64_t)max(0, mc - ((ti == tj) ? lane + 1 : 0));
-                    for (int jj = (ti == tj) ? lane + 1 : 0; jj < mc; ++jj) {
-                        const float4 q = cs[wid][jj];
-                        const int kind = classify_f32(r, rid, q, cid[wid][jj]);
-                        if (kind == PAIR_NONE) continue;
-                        const CellBox qb = cell_box(q, g);
-                        if (max(rb.x0, qb.x0) != cxc || max(rb.y0, qb.y0) != cyc) continue;  // not the owner cell
-                        hit(kind, rix, cix[wid][jj], rth, cth[wid][jj]);
-                    }
-                }
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+        const uint32_t p = base + lane;
+        const bool ok = p < total;
+        uint32_t ri = 0, c = 0, end = 0;
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint2 rid = make_uint2(0, 0);
+        uint32_t rth = 0;
+        CellBox rb{0, 0, 0, 0};
+        if (ok) {
+            ri = rec[p];
+            c = rec_cell[p];
+            end = off[c + 1];
+            r = seg[ri];
+            rid = ids[ri];
+            rth = theta[ri];
+            rb = cell_box(r, g);
+            tested += end - p - 1;
+        }
+        const int cxc = (int)(c % (uint32_t)g.G), cyc = (int)(c / (uint32_t)g.G);
+        auto visit = [&](auto &&hit) {
+            if (!ok) return;
+            for (uint32_t q = p + 1; q < end; ++q) {
+                const uint32_t qi = rec[q];
+                const float4 Q = seg[qi];
+                const int kind = classify_f32(r, rid, Q, ids[qi]);
+                if (kind == PAIR_NONE) continue;
+                const CellBox qb = cell_box(Q, g);
+                if (max(rb.x0, qb.x0) != cxc || max(rb.y0, qb.y0) != cyc) continue;  // not the owner cell
+                hit(kind, ri, qi, rth, theta[qi]);
             }
         };
         uint32_t mine = 0;
         visit([&](int kind, uint32_t, uint32_t, uint32_t ta, uint32_t tb) {
             tally(kind, ta, tb, ideal, pc);
             mine += (kind == PAIR_PROPER || kind == PAIR_TOUCHING) ? 1u : 0u;
-        }, true);
-        if (pairs) {
-            uint32_t total;
-            const uint32_t lo = warp_excl_scan(mine, &total);
-            unsigned long long base = 0;
-            if (lane == 0 && total) base = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)total);
-            uint64_t pos = __shfl_sync(0xffffffffu, base, 0) + lo;
-            if (__any_sync(0xffffffffu, mine != 0))
-                visit([&](int kind, uint32_t ia, uint32_t ib, uint32_t, uint32_t) {
-                    if (kind != PAIR_PROPER && kind != PAIR_TOUCHING) return;
-                    if (pos < cap) pairs[pos] = make_uint2(ia, ib);
-                    ++pos;
-                }, false);
+        });
+        if (pairs && __any_sync(0xffffffffu, mine != 0)) {
+            uint32_t wt;
+            const uint32_t lo = warp_excl_scan(mine, &wt);
+            unsigned long long wb = 0;
+            if (lane == 0 && wt) wb = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)wt);
+            uint64_t pos = __shfl_sync(0xffffffffu, wb, 0) + lo;
+            visit([&](int kind, uint32_t ia, uint32_t ib, uint32_t, uint32_t) {
+                if (kind != PAIR_PROPER && kind != PAIR_TOUCHING) return;
+                if (pos < cap) pairs[pos] = make_uint2(ia, ib);
+                ++pos;
+            });
         }
     }
     flush_counts(pc, acc, shu);
@@ -1069,7 +1054,7 @@ uint64_t f32_walk_lines_cap(int64_t E) { return 16 * (uint64_t)E + 1024; }
 
 size_t f32_grid_bytes(int G, int64_t E) {
     const size_t C = (size_t)G * G;
-    return sizeof(FGrid) + sizeof(uint32_t) * ((C + 1) + C + 4 * (size_t)E + 2 * (size_t)E + 1) +
+    return sizeof(FGrid) + sizeof(uint32_t) * ((C + 1) + C + 8 * (size_t)E + 2 * (size_t)E + 1) +
            sizeof(int2) * ((size_t)E + f32_walk_lines_cap(E)) + 256 * 10;
 }
 
@@ -1088,6 +1073,7 @@ void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, u
     uint32_t *cnt = (uint32_t *)take(sizeof(uint32_t) * (C + 1));
     uint32_t *fill = (uint32_t *)take(sizeof(uint32_t) * C);
     uint32_t *rec = (uint32_t *)take(sizeof(uint32_t) * 4 * (size_t)E);
+    uint32_t *rec_cell = (uint32_t *)take(sizeof(uint32_t) * 4 * (size_t)E);
     uint32_t *long_idx = (uint32_t *)take(sizeof(uint32_t) * (size_t)E);
     uint32_t *long_lines = (uint32_t *)take(sizeof(uint32_t) * ((size_t)E + 1));
     int2 *walk_meta = (int2 *)take(sizeof(int2) * (size_t)E);
@@ -1105,10 +1091,10 @@ void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, u
     count_launches(1);
     k_f32_walk_lines<<<152 * 8, 256, 0, s>>>(seg, g, long_idx, long_lines, (uint32_t)E, b.acc, wl_cap, wl);
     launch_scan_u32(cnt, cnt, (int64_t)C, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
-    k_f32_grid_fill<<<gb, 256, 0, s>>>(seg, b.acc, g, cnt, fill, rec);
+    k_f32_grid_fill<<<gb, 256, 0, s>>>(seg, b.acc, g, cnt, fill, rec, rec_cell);
     count_launches(3);
-    k_f32_grid_ss<<<grid_for((int64_t)C, 8, 152 * 16), 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, b.acc,
-                                                                    ideal, pairs, cap);
+    k_f32_grid_ss<<<152 * 8, 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, rec_cell, b.acc, ideal, pairs,
+                                          cap);
     k_f32_grid_ls<<<152 * 8, 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, long_idx, long_lines,
                                           (uint32_t)E, walk_meta, wl, wl_cap, b.acc, ideal, pairs, cap);
     k_cross_f32<<<152 * 8, DF_ROWS, 0, s>>>(seg, b.seg_ids, b.seg_theta, long_idx, &b.acc->n_long, b.acc, ideal, -1,
