@@ -210,8 +210,9 @@ __device__ __forceinline__ bool owns_collinear(const GSeg &r, const GSeg &c, int
 // relative integer coordinates below 2^17, so every input and difference is
 // exact in FP32) each product carries a relative error of at most 2^-24, so
 // |den~ - den| <= bd = 2^-22 (|u_x v_y| + |u_y v_x|) and likewise bn for num
-// (a factor 4 to spare); when |den~| > 4 bd, t~ = num~ / den~ is within
-// et = (bn + |t~| bd) / (|den~| - 2 bd) + 2^-22 |t~| of t, and P~ within
+// (a factor 4 to spare); when |den~| > 4 bd, t~ = num~ / den~ (the fast
+// division, within 2 units in the last place) is within
+// et = (bn + |t~| bd) / (|den~| - 2 bd) + 2^-20 |t~| of t, and P~ within
 // |u| et + 2^-22 (|P~| + 1) of P, a margin doubled again for the decision.
 // Otherwise, and near a border, the exact int64 test decides.
 __device__ __forceinline__ bool owns_crossing_fast(const GSeg &r, const GSeg &c, int w) {
@@ -233,9 +234,9 @@ __device__ __forceinline__ bool owns_crossing_fast(const GSeg &r, const GSeg &c,
         const float den = p1 - p2, num = q1 - q2;
         const float bd = 0x1p-22f * (fabsf(p1) + fabsf(p2)), bn = 0x1p-22f * (fabsf(q1) + fabsf(q2));
         if (fabsf(den) > 4.0f * bd) {
-            const float t = num / den;
+            const float t = __fdividef(num, den);
             const float at = fabsf(t);
-            const float et = (bn + at * bd) / (fabsf(den) - 2.0f * bd) + 0x1p-22f * at;
+            const float et = __fdividef(bn + at * bd, fabsf(den) - 2.0f * bd) * 1.001f + 0x1p-20f * at;
             const float X = fmaf(r.ux, t, r.ax), Y = fmaf(r.uy, t, r.ay);
             const float ex = 2.0f * (fabsf(r.ux) * et + 0x1p-22f * (fabsf(X) + 1.0f));
             const float ey = 2.0f * (fabsf(r.uy) * et + 0x1p-22f * (fabsf(Y) + 1.0f));

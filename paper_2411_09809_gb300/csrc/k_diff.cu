@@ -423,6 +423,15 @@ __device__ __forceinline__ CellBox cell_box(float4 r, const FGrid &g) {
 
 __device__ __forceinline__ bool is_short_box(const CellBox &b) { return b.x1 - b.x0 <= 1 && b.y1 - b.y0 <= 1; }
 
+// A short segment's record in a cell: its endpoints, vertex ids, direction
+// and compacted index, so the pair passes read one 32-byte record instead of
+// chasing an index into three arrays.
+struct __align__(16) FRec {
+    float4 s;
+    uint2 ids;
+    uint32_t th, i;
+};
+
 // The walk of a long segment: along its major axis (x when |dx| >= |dy|),
 // line i of [lo, hi] covers minor cells [a, b].
 struct Walk {
@@ -537,18 +546,25 @@ __global__ void __launch_bounds__(256) k_f32_grid_count(const float4 *__restrict
 
 __global__ void __launch_bounds__(256) k_f32_grid_fill(const float4 *__restrict__ seg, const DevAcc *__restrict__ acc,
                                                        const FGrid *__restrict__ gp, const uint32_t *__restrict__ off,
-                                                       uint32_t *__restrict__ fill, uint32_t *__restrict__ rec,
+                                                       uint32_t *__restrict__ fill, const uint2 *__restrict__ ids,
+                                                       const uint32_t *__restrict__ theta, FRec *__restrict__ rec,
                                                        uint32_t *__restrict__ rec_cell) {
     const FGrid g = *gp;
     const int64_t n = acc->n_seg;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const CellBox b = cell_box(seg[i], g);
+        const float4 r = seg[i];
+        const CellBox b = cell_box(r, g);
         if (!is_short_box(b)) continue;
+        FRec q;
+        q.s = r;
+        q.ids = ids[i];
+        q.th = theta[i];
+        q.i = (uint32_t)i;
         for (int y = b.y0; y <= b.y1; ++y)
             for (int x = b.x0; x <= b.x1; ++x) {
                 const int c = y * g.G + x;
                 const uint32_t pos = off[c] + atomicAdd(&fill[c], 1u);
-                rec[pos] = (uint32_t)i;
+                rec[pos] = q;
                 rec_cell[pos] = (uint32_t)c;
             }
     }
@@ -568,7 +584,7 @@ __device__ __forceinline__ void tally(int kind, uint32_t ta, uint32_t tb, uint32
 // pairs are kept) write at offsets reserved once per warp and chunk.
 __global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
-                                                     const uint32_t *__restrict__ off, const uint32_t *__restrict__ rec,
+                                                     const uint32_t *__restrict__ off, const FRec *__restrict__ rec,
                                                      const uint32_t *__restrict__ rec_cell, DevAcc *acc,
                                                      uint32_t ideal, uint2 *__restrict__ pairs, uint64_t cap) {
     __shared__ uint64_t shu[32];
@@ -587,12 +603,13 @@ __global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ 
         uint32_t rth = 0;
         CellBox rb{0, 0, 0, 0};
         if (ok) {
-            ri = rec[p];
+            const FRec fr = rec[p];
+            ri = fr.i;
             c = rec_cell[p];
             end = off[c + 1];
-            r = seg[ri];
-            rid = ids[ri];
-            rth = theta[ri];
+            r = fr.s;
+            rid = fr.ids;
+            rth = fr.th;
             rb = cell_box(r, g);
             tested += end - p - 1;
         }
@@ -600,13 +617,12 @@ __global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ 
         auto visit = [&](auto &&hit) {
             if (!ok) return;
             for (uint32_t q = p + 1; q < end; ++q) {
-                const uint32_t qi = rec[q];
-                const float4 Q = seg[qi];
-                const int kind = classify_f32(r, rid, Q, ids[qi]);
+                const FRec fq = rec[q];
+                const int kind = classify_f32(r, rid, fq.s, fq.ids);
                 if (kind == PAIR_NONE) continue;
-                const CellBox qb = cell_box(Q, g);
+                const CellBox qb = cell_box(fq.s, g);
                 if (max(rb.x0, qb.x0) != cxc || max(rb.y0, qb.y0) != cyc) continue;  // not the owner cell
-                hit(kind, ri, qi, rth, theta[qi]);
+                hit(kind, ri, fq.i, rth, fq.th);
             }
         };
         uint32_t mine = 0;
@@ -680,7 +696,7 @@ __device__ __forceinline__ int2 line_range(const int2 *__restrict__ wl, uint64_t
 // kept) write at offsets reserved once per warp and chunk.
 __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
-                                                     const uint32_t *__restrict__ off, const uint32_t *__restrict__ rec,
+                                                     const uint32_t *__restrict__ off, const FRec *__restrict__ rec,
                                                      const uint32_t *__restrict__ long_idx,
                                                      const uint32_t *__restrict__ line_off, uint32_t line_total_at,
                                                      const int2 *__restrict__ walk_meta, const int2 *__restrict__ wl,
@@ -702,6 +718,8 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
         int lo = 0, hi = 0, i = 0;
         int xmaj = 1;
         float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint2 lid = make_uint2(0, 0);
+        uint32_t lth = 0;
         int2 ab = make_int2(0, -1);
         uint32_t cnt = 0;
         if (ok) {
@@ -709,6 +727,8 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
             off_t = line_off[t];
             li = long_idx[t];
             L = seg[li];
+            lid = ids[li];
+            lth = theta[li];
             const int2 m = walk_meta[t];
             lo = m.x;
             hi = lo + (int)(line_off[t + 1] - off_t) - 1;
@@ -743,6 +763,10 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                 Lo.y = __shfl_sync(0xffffffffu, L.y, o);
                 Lo.z = __shfl_sync(0xffffffffu, L.z, o);
                 Lo.w = __shfl_sync(0xffffffffu, L.w, o);
+                uint2 lid_o;
+                lid_o.x = __shfl_sync(0xffffffffu, lid.x, o);
+                lid_o.y = __shfl_sync(0xffffffffu, lid.y, o);
+                const uint32_t lth_o = __shfl_sync(0xffffffffu, lth, o);
                 if (q >= chunk_total) continue;
                 // the cell and record of pair q within the line
                 uint32_t k = q - pre_o;
@@ -756,9 +780,9 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                 }
                 p = off[c] + k;
                 const int cx = xm_o ? i_o : j, cy = xm_o ? j : i_o;
-                const uint32_t qs = rec[p];
-                const float4 S = seg[qs];
-                const int kind = classify_f32(Lo, ids[li_o], S, ids[qs]);
+                const FRec fs = rec[p];
+                const float4 S = fs.s;
+                const int kind = classify_f32(Lo, lid_o, S, fs.ids);
                 if (kind == PAIR_NONE) continue;
                 // owner: the first cell of the short's box (row-major) on the
                 // walk; this cell is on it, so only the cells before it matter
@@ -776,7 +800,7 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                         }
                     }
                 if (earlier) continue;
-                hit(kind, li_o, qs, theta[li_o], theta[qs]);
+                hit(kind, li_o, fs.i, lth_o, fs.th);
             }
         };
         uint32_t mine = 0;
@@ -1054,7 +1078,7 @@ uint64_t f32_walk_lines_cap(int64_t E) { return 16 * (uint64_t)E + 1024; }
 
 size_t f32_grid_bytes(int G, int64_t E) {
     const size_t C = (size_t)G * G;
-    return sizeof(FGrid) + sizeof(uint32_t) * ((C + 1) + C + 8 * (size_t)E + 2 * (size_t)E + 1) +
+    return sizeof(FGrid) + sizeof(FRec) * 4 * (size_t)E + sizeof(uint32_t) * ((C + 1) + C + 4 * (size_t)E + 2 * (size_t)E + 1) +
            sizeof(int2) * ((size_t)E + f32_walk_lines_cap(E)) + 256 * 10;
 }
 
@@ -1072,7 +1096,7 @@ void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, u
 
     uint32_t *cnt = (uint32_t *)take(sizeof(uint32_t) * (C + 1));
     uint32_t *fill = (uint32_t *)take(sizeof(uint32_t) * C);
-    uint32_t *rec = (uint32_t *)take(sizeof(uint32_t) * 4 * (size_t)E);
+    FRec *rec = (FRec *)take(sizeof(FRec) * 4 * (size_t)E);
     uint32_t *rec_cell = (uint32_t *)take(sizeof(uint32_t) * 4 * (size_t)E);
     uint32_t *long_idx = (uint32_t *)take(sizeof(uint32_t) * (size_t)E);
     uint32_t *long_lines = (uint32_t *)take(sizeof(uint32_t) * ((size_t)E + 1));
@@ -1091,7 +1115,7 @@ void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, u
     count_launches(1);
     k_f32_walk_lines<<<152 * 8, 256, 0, s>>>(seg, g, long_idx, long_lines, (uint32_t)E, b.acc, wl_cap, wl);
     launch_scan_u32(cnt, cnt, (int64_t)C, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
-    k_f32_grid_fill<<<gb, 256, 0, s>>>(seg, b.acc, g, cnt, fill, rec, rec_cell);
+    k_f32_grid_fill<<<gb, 256, 0, s>>>(seg, b.acc, g, cnt, fill, b.seg_ids, b.seg_theta, rec, rec_cell);
     count_launches(3);
     k_f32_grid_ss<<<152 * 8, 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, rec_cell, b.acc, ideal, pairs,
                                           cap);
