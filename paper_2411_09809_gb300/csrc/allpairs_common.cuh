@@ -112,35 +112,47 @@ __device__ __forceinline__ void allpairs_tile(const SegRec *__restrict__ seg, co
         rs[k] = make_frow(rr[k], rok[k] ? theta[i] : 0u);
     }
     __syncthreads();
-    const bool diag = bi == bj;
-#pragma unroll 2
-    for (int jj = 0; jj < nc; ++jj) {
-        const FCol c = sm.fc[jj];
-        bool unsure[RPT];
-        bool any_unsure = false;
+    // a pair counts when its column index exceeds lim (diagonal tiles: the row's own index)
+    int lim[RPT];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            const FRow &r = rs[k];
-            const float o1 = fmaf(r.ux, c.cy, fmaf(-r.uy, c.cx, r.nk));
-            const float o2 = fmaf(r.ux, c.dy, fmaf(-r.uy, c.dx, r.nk));
-            const float o3 = fmaf(c.vx, r.ay, fmaf(-c.vy, r.ax, c.nk));
-            const float o4 = fmaf(c.vx, r.by, fmaf(-c.vy, r.bx, c.nk));
-            const float mn = fminf(fminf(fabsf(o1), fabsf(o2)), fminf(fabsf(o3), fabsf(o4)));
-            const bool valid = rok[k] && (!diag || jj > (int)threadIdx.x + k * THREADS);
-            const bool sure = mn > kAllPairsFilter;
-            const int sx = (__float_as_int(o1) ^ __float_as_int(o2)) & (__float_as_int(o3) ^ __float_as_int(o4));
-            const bool hit = valid && sure && sx < 0;
-            pc.proper += hit ? 1u : 0u;
-            pc.dev += hit ? dev_term(r.th, c.th, ideal) : 0u;
-            unsure[k] = valid && !sure;
-            any_unsure |= unsure[k];
-        }
-        if (__any_sync(0xffffffffu, any_unsure)) {
+    for (int k = 0; k < RPT; ++k)
+        lim[k] = !rok[k] ? 0x7fffffff : (bi == bj ? (int)threadIdx.x + k * THREADS : -1);
+    // columns in chunks of 32: the sure crossings and the inconclusive pairs
+    // are marked in per-row bitmasks; the angle terms of the crossings and the
+    // exact re-decisions run per set bit after each chunk
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int ce = min(32, nc - c0);
+        uint32_t hm[RPT], um[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) hm[k] = um[k] = 0u;
+#pragma unroll 2
+        for (int q = 0; q < ce; ++q) {
+            const int jj = c0 + q;
+            const FCol c = sm.fc[jj];
+            const uint32_t bit = 1u << q;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
-                if (!unsure[k]) continue;
+                const FRow &r = rs[k];
+                const float o1 = fmaf(r.ux, c.cy, fmaf(-r.uy, c.cx, r.nk));
+                const float o2 = fmaf(r.ux, c.dy, fmaf(-r.uy, c.dx, r.nk));
+                const float o3 = fmaf(c.vx, r.ay, fmaf(-c.vy, r.ax, c.nk));
+                const float o4 = fmaf(c.vx, r.by, fmaf(-c.vy, r.bx, c.nk));
+                const float mn = fminf(fminf(fabsf(o1), fabsf(o2)), fminf(fabsf(o3), fabsf(o4)));
+                const bool valid = jj > lim[k];
+                const bool sure = mn > kAllPairsFilter;
+                const int sx = (__float_as_int(o1) ^ __float_as_int(o2)) & (__float_as_int(o3) ^ __float_as_int(o4));
+                if (valid && sure && sx < 0) hm[k] |= bit;
+                if (valid && !sure) um[k] |= bit;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            pc.proper += (uint32_t)__popc(hm[k]);
+            for (uint32_t m = hm[k]; m; m &= m - 1) pc.dev += dev_term(rs[k].th, sm.fc[c0 + __ffs(m) - 1].th, ideal);
+            for (uint32_t m = um[k]; m; m &= m - 1) {
+                const int jj = c0 + __ffs(m) - 1;
                 const RowSeg er = make_row(rr[k], rs[k].th);
-                const ColSeg ec = make_col(sm.raw[jj], c.th);
+                const ColSeg ec = make_col(sm.raw[jj], sm.fc[jj].th);
                 const int kind = classify_kind(er, ec);
                 if (kind == PAIR_COLLINEAR) {
                     ++pc.collinear;
