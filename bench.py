@@ -548,7 +548,8 @@ def run_differentiable(args, rank, world, local_rank):
           "unit": "Tops/s (int32-equivalent lane ops)", "frac": ops / t / 1e12 / peak if t > 0 else None,
           "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
                          f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
-          "traffic": load_traffic("k_cross_f32", "differentiable", kernel_source_hash(["k_diff.cu"])),
+          "traffic": load_traffic("crossing_phase_f32" if grid else "k_cross_f32", "differentiable",
+                                  kernel_source_hash(["k_diff.cu"])),
           "launch_ms": t * 1e3, "pairs_tested": res.crossing.c.pairs_tested}
     line = {
         "metric": "fwd+bwd steps/s", "value": world * 1e3 / ms, "unit": "steps/s", "n_gpus": world,
