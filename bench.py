@@ -48,7 +48,9 @@ WORKLOADS = {
     "plain": ("plain_layout", 256),
     "batched": ("batched_layouts", 256),
     "differentiable": ("differentiable_layout", 0),
+    "moves": ("large_sparse_layout", 64),
 }
+MOVES_PER_STEP = 16
 
 
 def dist_env():
@@ -574,6 +576,88 @@ def run_differentiable(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_moves(args, rank, world, local_rank):
+    """Incremental workload: on the large sparse layout, one step = gr_move_vertices
+    of 16 random vertices to random positions (all five metrics of the moved
+    layout, the crossing and occlusion counts updated from the previous
+    evaluation).  A full evaluation of the same layout is timed beside it."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_09809_gb300 import build as gr_build, gr
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        if rank == 0:
+            gr_build.build()
+        dist.barrier()
+    else:
+        gr_build.build()
+    gr.load()
+    L, d = make_workload("moves")
+    dev = torch.device("cuda", local_rank)
+    xy = torch.from_numpy(L.xy).to(dev)
+    edges = torch.from_numpy(L.edges).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lay = gr.Layout(xy, edges, stream=stream.cuda_stream)
+    rng = np.random.default_rng(20241115 + 5)
+    n_steps = args.warmup + 2 * args.steps
+    ids = [torch.from_numpy(rng.choice(L.V, size=MOVES_PER_STEP, replace=False).astype(np.int32)).to(dev)
+           for _ in range(n_steps)]
+    new = [torch.from_numpy(rng.integers(0, 65536, size=(MOVES_PER_STEP, 2)).astype(np.int32)).to(dev)
+           for _ in range(n_steps)]
+    res = lay.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
+
+    def timed(fn, k, off):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        out = None
+        for i in range(k):
+            flush.fill_(i)
+            starts[i].record(stream)
+            out = fn(off + i)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)), out
+
+    move = lambda i: lay.move(ids[i], new[i], gr.GR_METRIC_ALL, IDEAL, d)
+    timed(move, args.warmup, 0)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = gr.gr_kernel_launches()
+    ms, res = timed(move, args.steps, args.warmup)
+    launches = gr.gr_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    full_ms, _ = timed(lambda i: lay.evaluate(gr.GR_METRIC_ALL, IDEAL, d), args.steps, 0)
+    if world > 1:
+        t = torch.tensor([ms, full_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, full_ms = (float(x) for x in t.tolist())
+    lay.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "incremental evaluations/s", "value": world * 1e3 / ms, "unit": "evaluations/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": dict(workload_config(L, d, "moves"), workload=f"moves_{MOVES_PER_STEP}_of_{L.name}",
+                       step=f"gr_move_vertices of {MOVES_PER_STEP} random vertices, all five metrics",
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "full_evaluation_ms": full_ms, "speedup_over_full": full_ms / ms,
+        "pairs_tested_per_step": res.crossing.c.pairs_tested,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle (plain C brute force) on the host cores."""
     if rank != 0:
@@ -756,6 +840,8 @@ def main():
             run_batched(args, rank, world, local_rank)
         elif args.workload == "differentiable":
             run_differentiable(args, rank, world, local_rank)
+        elif args.workload == "moves":
+            run_moves(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -75,7 +75,8 @@ enum {
 typedef enum {
     GR_PATH_AUTO = 0,     /* density heuristic picks */
     GR_PATH_GRID = 1,     /* uniform grid + per-cell pair kernel */
-    GR_PATH_ALLPAIRS = 2  /* tiled brute force over all edge pairs */
+    GR_PATH_ALLPAIRS = 2, /* tiled brute force over all edge pairs */
+    GR_PATH_DELTA = 3     /* (results only) updated from the previous evaluation by gr_move_vertices */
 } gr_path;
 
 /* Where the grid path tests pairs of two long segments (segments spanning
@@ -188,6 +189,28 @@ gr_status gr_crossing_angle(gr_layout *layout, double ideal_rad, gr_crossing_ang
  * overwritten.  Edges are indexed as passed to gr_layout_create. */
 gr_status gr_crossings_per_edge(gr_layout *layout, double ideal_rad, int64_t *d_counts,
                                 double *d_dev);
+
+/* ------------------------------------------------- incremental moves
+ * gr_move_vertices moves the n vertices ids[i] (distinct, in [0, V)) to
+ * xy_new[i] (int32 [n][2] in [0, 65536); ids and xy_new in host or device
+ * memory) and evaluates the metrics of the moved layout, as gr_evaluate
+ * would.  When the previous evaluation of this layout (gr_evaluate or
+ * gr_move_vertices, with no gr_layout_update since) covered the crossings
+ * and occlusion requested here with the same ideal angle and d, those counts
+ * and the crossing-angle sum are updated instead of recomputed: only the
+ * pairs of an edge with a moved endpoint (crossings, Algorithms 4 and 5) and
+ * of a moved vertex (occlusion, Algorithm 1) are classified, before and after
+ * the move, so the work is proportional to (affected edges) x E + n x V; the
+ * result equals a full evaluation exactly (the same predicates and integer
+ * angle terms).  Minimum angle and edge length variation are recomputed.
+ * The result's crossing_path and occlusion_path are then GR_PATH_DELTA and
+ * pairs_tested counts the pairs this call tested.  Otherwise the moves are
+ * applied and a full evaluation runs.  GR_EINVAL for an id outside [0, V) or
+ * given twice, GR_ERANGE for a coordinate outside [0, 65536); the layout is
+ * unchanged then.  GR_COORD_I32 layouts only (GR_ENOTSUP otherwise).
+ * Synchronises. */
+gr_status gr_move_vertices(gr_layout *layout, int64_t n, const int32_t *ids, const int32_t *xy_new,
+                           uint32_t metric_mask, const gr_params *params, gr_result *out);
 
 /* ------------------------------------------------- differentiable form
  * Layouts created with GR_COORD_F32 take FP32 coordinates [V][2] (any finite

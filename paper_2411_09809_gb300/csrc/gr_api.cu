@@ -95,6 +95,25 @@ struct gr_layout {
     bool fast_ok = false;
     int fast_k = -1;
     bool fast_split = false;
+    // the last evaluation's crossing and occlusion totals, for gr_move_vertices
+    struct Last {
+        bool valid = false;
+        uint32_t metrics = 0, ideal_u = 0;
+        int64_t d = 0;
+        uint64_t proper = 0, touching = 0, collinear = 0, dev_lo = 0, dev_hi = 0, occlusion = 0;
+    } last;
+    // incremental-move workspace
+    uint32_t *moved = nullptr;      // [V] flags, zero between calls
+    uint32_t *affected = nullptr;   // [E] edges with a moved endpoint
+    DeltaAcc *dacc = nullptr, *h_dacc = nullptr;
+    int32_t *mv_ids = nullptr, *mv_xy = nullptr;
+    int64_t mv_cap = 0;
+    // The crossing grid left by the last full evaluation indexes the edges
+    // for the incremental passes while dgrid_k >= 0 (its cell side is
+    // 2^dgrid_k); edges moved since then are in the dirty set.
+    int dgrid_k = -1;
+    DirtySet dirty;
+    bool dirty_any = false;         // the dirty set may be non-empty
     int64_t io_h2d = 0, io_d2h = 0; // bytes copied between host and device
     // phase timing
     bool profiling = false;
@@ -122,7 +141,9 @@ void free_layout(gr_layout *L) {
     void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.ma_part,
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result,
                     b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->arg, L->st, L->out3, L->gout3,
-                    L->f32_work, L->theta_adj};
+                    L->f32_work, L->theta_adj, L->moved, L->affected, L->dacc, L->mv_ids, L->mv_xy,
+                    L->dirty.flag, L->dirty.list, L->dirty.n, b.adj_off, b.adj, b.ma_nz, b.ma_dv, b.ma_touch,
+                    b.ma_flag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_grid(L->g);
@@ -133,6 +154,7 @@ void free_layout(gr_layout *L) {
     if (L->side) cudaStreamDestroy(L->side);
     if (L->h_result) cudaFreeHost(L->h_result);
     if (L->h_acc) cudaFreeHost(L->h_acc);
+    if (L->h_dacc) cudaFreeHost(L->h_dacc);
     delete L;
 }
 
@@ -160,6 +182,16 @@ gr_status alloc_layout(gr_layout *L) {
     GR_TRY(dalloc(&b.scan_tmp, (size_t)kScanMaxBlocks));
     GR_TRY(dalloc(&b.scan_tmp_side, (size_t)kScanMaxBlocks));
     GR_TRY(dalloc(&b.result, 1));
+    if (L->coord == GR_COORD_I32) {
+        GR_TRY(dalloc(&b.adj_off, (size_t)V + 1));
+        GR_TRY(dalloc(&b.adj, 2 * (size_t)E));
+        GR_TRY(dalloc(&b.ma_nz, (size_t)V));
+        GR_TRY(dalloc(&b.ma_dv, (size_t)V));
+        GR_TRY(dalloc(&b.ma_touch, (size_t)V));
+        GR_TRY(dalloc(&b.ma_flag, 1024));
+        GR_CU(cudaMemsetAsync(b.ma_touch, 0, sizeof(uint32_t) * (V > 0 ? V : 1), L->stream));
+        GR_CU(cudaMemsetAsync(b.ma_flag, 0, sizeof(uint32_t) * 1024, L->stream));
+    }
     if (L->coord == GR_COORD_F32) {
         GR_TRY(dalloc(&b.seg_ids, (size_t)E));
         GR_TRY(dalloc(&b.dir_ang, 2 * (size_t)E));
@@ -300,8 +332,10 @@ gr_status enqueue_inputs(gr_layout *L, const void *xy, const int32_t *edges) {
     } else {
         launch_check_vertices(L->b.xy, V, L->b, s);
         launch_gather(L->b.xy, V, L->b.edges, E, L->b, s);
+        if (edges) launch_adjacency(L->b, V, E, s);
     }
     L->diff_ready = false;
+    L->dgrid_k = -1;
     phase_end(L, GR_PHASE_GATHER);
     GR_CU(cudaGetLastError());
     L->stats_stale = true;
@@ -383,6 +417,21 @@ int occl_cell_log2(int64_t d) {
     int k = 6;
     while ((int64_t(1) << k) < d) ++k;
     return k;
+}
+
+// Keeps the crossing and occlusion totals of the evaluation just read back.
+void remember_totals(gr_layout *L, uint32_t metrics, uint32_t ideal_u, int64_t d) {
+    const DevAcc &a = *L->h_acc;
+    L->last.valid = true;
+    L->last.metrics = metrics;
+    L->last.ideal_u = ideal_u;
+    L->last.d = d;
+    L->last.proper = a.proper;
+    L->last.touching = a.touching;
+    L->last.collinear = a.collinear;
+    L->last.dev_lo = a.dev_lo;
+    L->last.dev_hi = a.dev_hi;
+    L->last.occlusion = a.occlusion;
 }
 
 float host_unord(uint32_t u) {
@@ -551,6 +600,7 @@ gr_status gr_layout_create(gr_layout **out, const void *xy, gr_coord_type coord_
 gr_status gr_layout_update(gr_layout *L, const void *xy, const int32_t *edges) {
     g_err.clear();
     if (!L) return fail(GR_EINVAL, "layout is NULL");
+    L->last.valid = false;
     if (L->V > 0 && !xy) return fail(GR_EINVAL, "xy is NULL");
     return enqueue_inputs(L, xy, edges);
 }
@@ -585,6 +635,12 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     const uint64_t n_seg = fast ? (uint64_t)E : L->h_acc->n_seg;  // (an upper bound when fast)
     GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
                           sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
+    L->dgrid_k = -1;  // set again below when this evaluation leaves a complete crossing grid
+    if (L->dirty_any) {
+        GR_CU(cudaMemsetAsync(L->dirty.flag, 0, (size_t)(E > 0 ? E : 1), s));
+        GR_CU(cudaMemsetAsync(L->dirty.n, 0, sizeof(uint32_t), s));
+        L->dirty_any = false;
+    }
 
     // Occlusion, minimum angle and edge length variation depend only on the
     // inputs: they run on the side stream, beside the crossing pipeline.
@@ -719,6 +775,8 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     st = status_to_error(L->h_acc->status | L->h_acc->eval_status);
     if (st != GR_OK) return st;
     *out = *L->h_result;
+    remember_totals(L, metrics, ideal_units(ideal), d);
+    if (path == GR_PATH_GRID) L->dgrid_k = cp.k;
     return GR_OK;
 }
 
@@ -779,6 +837,7 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
         return fail(GR_EINVAL, "per-edge outputs must be device memory");
     cudaStream_t s = L->stream;
     Buffers &b = L->b;
+    L->dgrid_k = -1;  // the grid buffers are rebuilt below
     GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
                           sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
     GR_CU(cudaMemsetAsync(d_counts, 0, sizeof(int64_t) * 3 * E, s));
@@ -812,6 +871,149 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
     GR_CU(cudaStreamSynchronize(s));
     return status_to_error(L->h_acc->status | L->h_acc->eval_status);
+}
+
+gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const int32_t *xy_new, uint32_t metrics,
+                           const gr_params *params, gr_result *out) {
+    g_err.clear();
+    if (!L || !out) return fail(GR_EINVAL, "NULL argument");
+    if (n < 0 || n > L->V) return fail(GR_EINVAL, "n must be in [0, V]");
+    if (n > 0 && (!ids || !xy_new)) return fail(GR_EINVAL, "NULL ids or coordinates");
+    if (metrics & ~GR_METRIC_ALL) return fail(GR_EINVAL, "unknown metric bits");
+    if (L->coord != GR_COORD_I32) return fail(GR_ENOTSUP, "gr_move_vertices needs a GR_COORD_I32 layout");
+    double ideal;
+    int64_t d;
+    gr_status st = read_params(params, &ideal, &d);
+    if (st != GR_OK) return st;
+    cudaStream_t s = L->stream;
+    Buffers &b = L->b;
+    const int64_t V = L->V, E = L->E;
+    // workspace
+    if (!L->dacc) {
+        if ((st = dalloc(&L->moved, (size_t)V)) != GR_OK) return st;
+        if ((st = dalloc(&L->affected, (size_t)E)) != GR_OK) return st;
+        if ((st = dalloc(&L->dacc, 1)) != GR_OK) return st;
+        GR_CU(cudaMallocHost((void **)&L->h_dacc, sizeof(DeltaAcc)));
+        GR_CU(cudaMemsetAsync(L->moved, 0, sizeof(uint32_t) * (V > 0 ? V : 1), s));
+    }
+    if (L->mv_cap < n) {
+        if (L->mv_ids) cudaFree(L->mv_ids);
+        if (L->mv_xy) cudaFree(L->mv_xy);
+        L->mv_ids = L->mv_xy = nullptr;
+        L->mv_cap = 0;
+        if ((st = dalloc(&L->mv_ids, (size_t)n)) != GR_OK) return st;
+        if ((st = dalloc(&L->mv_xy, 2 * (size_t)n)) != GR_OK) return st;
+        L->mv_cap = n;
+    }
+    if (n > 0) {
+        const cudaMemcpyKind ki = is_device_pointer(ids) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kx = is_device_pointer(xy_new) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        GR_CU(cudaMemcpyAsync(L->mv_ids, ids, sizeof(int32_t) * n, ki, s));
+        GR_CU(cudaMemcpyAsync(L->mv_xy, xy_new, sizeof(int32_t) * 2 * n, kx, s));
+        if (ki == cudaMemcpyHostToDevice) L->io_h2d += (int64_t)sizeof(int32_t) * n;
+        if (kx == cudaMemcpyHostToDevice) L->io_h2d += (int64_t)sizeof(int32_t) * 2 * n;
+    }
+    // Validation, the before and after passes, the regather and the new
+    // totals are queued without a host round trip; every kernel after the
+    // validation does nothing on an invalid move, which leaves the layout as
+    // it was and is reported after the one synchronisation.
+    GR_CU(cudaMemsetAsync(L->dacc, 0, sizeof(DeltaAcc), s));
+    if (n > 0) launch_delta_validate(L->mv_ids, L->mv_xy, n, V, L->moved, L->dacc, s);
+    const uint32_t ideal_u = ideal_units(ideal);
+    const uint32_t need = metrics & (GR_METRIC_CROSSINGS | GR_METRIC_OCCLUSION);
+    const bool incremental = L->last.valid && !L->stats_stale && (L->last.metrics & need) == need &&
+                             L->last.ideal_u == ideal_u && L->last.d == d;
+    const bool crossings = (need & GR_METRIC_CROSSINGS) != 0, occl = (need & GR_METRIC_OCCLUSION) != 0 && d > 0;
+    const long long d2 = d >= 100000 ? (long long)1e11 : (long long)d * d;
+    // the affected edges against the others: through the last full
+    // evaluation's crossing grid when it left one, else against every segment
+    const bool use_grid = incremental && crossings && L->dgrid_k >= 0;
+    if (use_grid && !L->dirty.flag) {
+        L->dirty.cap = (uint32_t)std::min<int64_t>(E, std::max<int64_t>(4096, E / 32));
+        if ((st = dalloc(&L->dirty.flag, (size_t)E)) != GR_OK) return st;
+        if ((st = dalloc(&L->dirty.list, (size_t)L->dirty.cap)) != GR_OK) return st;
+        if ((st = dalloc(&L->dirty.n, 1)) != GR_OK) return st;
+        GR_CU(cudaMemsetAsync(L->dirty.flag, 0, (size_t)E, s));
+        GR_CU(cudaMemsetAsync(L->dirty.n, 0, sizeof(uint32_t), s));
+    }
+    if (incremental && n > 0) {
+        if (crossings) launch_delta_affected(b, E, L->moved, L->affected, L->dacc, use_grid ? L->dirty : DirtySet{}, s);
+        if (use_grid) {
+            L->dirty_any = true;
+            launch_delta_grid_pass(b, L->g, L->dgrid_k, L->moved, L->affected, L->dirty, ideal_u, L->dacc, 0, s);
+        }
+        launch_delta_pass(b, V, E, L->mv_ids, n, L->moved, L->affected, crossings && !use_grid, ideal_u, occl, d2,
+                          L->dacc, 0, s);
+    }
+    if (n > 0) launch_delta_apply(L->mv_ids, L->mv_xy, n, L->dacc, b, s);
+    if (!incremental) {
+        if (n > 0) launch_delta_unmark(L->mv_ids, n, V, L->moved, s);
+        GR_CU(cudaMemcpyAsync(L->h_dacc, L->dacc, sizeof(DeltaAcc), cudaMemcpyDeviceToHost, s));
+        GR_CU(cudaStreamSynchronize(s));
+        if (L->h_dacc->status) return status_to_error(L->h_dacc->status);
+        L->last.valid = false;
+        GR_CU(cudaMemsetAsync(b.acc, 0, offsetof(DevAcc, eval_status), s));
+        launch_check_vertices(b.xy, V, b, s);
+        launch_gather(b.xy, V, b.edges, E, b, s);
+        GR_CU(cudaGetLastError());
+        L->stats_stale = true;
+        return gr_evaluate(L, metrics, params, out);
+    }
+    // the moved layout's segments and statistics, then the after pass on
+    // them; edge length variation and minimum angle run on the side stream
+    // meanwhile
+    GR_CU(cudaMemsetAsync(b.acc, 0, offsetof(DevAcc, eval_status), s));
+    launch_check_vertices(b.xy, V, b, s);
+    launch_gather(b.xy, V, b.edges, E, b, s);
+    const bool side_work = (metrics & (GR_METRIC_EDGE_LENGTH | GR_METRIC_MIN_ANGLE)) != 0;
+    if (side_work) {
+        cudaStream_t t = L->side;
+        GR_CU(cudaEventRecord(L->ev_fork, s));
+        GR_CU(cudaStreamWaitEvent(t, L->ev_fork, 0));
+        if (metrics & GR_METRIC_EDGE_LENGTH) launch_elv(b, E, t);
+        if (metrics & GR_METRIC_MIN_ANGLE) {
+            if (L->last.metrics & GR_METRIC_MIN_ANGLE) launch_min_angle_moved(b, V, L->mv_ids, n, t);
+            else launch_min_angle(b, V, E, t);
+        }
+        GR_CU(cudaEventRecord(L->ev_join, t));
+    }
+    if (n > 0) {
+        if (use_grid)
+            launch_delta_grid_pass(b, L->g, L->dgrid_k, L->moved, L->affected, L->dirty, ideal_u, L->dacc, 1, s);
+        launch_delta_pass(b, V, E, L->mv_ids, n, L->moved, L->affected, crossings && !use_grid, ideal_u, occl, d2,
+                          L->dacc, 1, s);
+        launch_delta_unmark(L->mv_ids, n, V, L->moved, s);
+    }
+    DeltaCounts last;  // only the totals asked for (the others stay zero, as in a full evaluation)
+    memset(&last, 0, sizeof last);
+    if (crossings) {
+        last.proper = L->last.proper;
+        last.touching = L->last.touching;
+        last.collinear = L->last.collinear;
+        last.dev_lo = L->last.dev_lo;
+        last.dev_hi = L->last.dev_hi;
+    }
+    if (occl) last.occlusion = L->last.occlusion;
+    launch_delta_combine(last, L->dacc, b, s);
+    if (side_work) GR_CU(cudaStreamWaitEvent(s, L->ev_join, 0));
+    launch_finalize(b, metrics, E, ideal, d, V > 0 ? min_angle_blocks(V) : 0, crossings ? GR_PATH_DELTA : 0, 0,
+                    (need & GR_METRIC_OCCLUSION) ? GR_PATH_DELTA : 0, -2, s);
+    GR_CU(cudaGetLastError());
+    GR_CU(cudaMemcpyAsync(L->h_dacc, L->dacc, sizeof(DeltaAcc), cudaMemcpyDeviceToHost, s));
+    GR_CU(cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s));
+    GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+    L->io_d2h += (int64_t)(sizeof(DeltaAcc) + sizeof(gr_result) + sizeof(DevAcc));
+    GR_CU(cudaStreamSynchronize(s));
+    if (L->h_dacc->status) return status_to_error(L->h_dacc->status);  // nothing moved
+    L->stats_stale = false;
+    if (L->h_dacc->fallback) {  // too many edges moved since the grid was built: a full evaluation rebuilds it
+        L->last.valid = false;
+        return gr_evaluate(L, metrics, params, out);
+    }
+    if ((st = status_to_error(L->h_acc->status | L->h_acc->eval_status)) != GR_OK) return st;
+    *out = *L->h_result;
+    remember_totals(L, metrics, ideal_u, d);
+    return GR_OK;
 }
 
 gr_status gr_diff_forward(gr_layout *L, double ideal_rad, float *out3) {

@@ -81,6 +81,12 @@ struct Buffers {
     uint32_t *deg = nullptr;      // [V + 1] degree, then CSR offsets (scan in place)
     uint32_t *deg_fill = nullptr; // [V]
     int2 *dirs = nullptr;         // [2 E] incident directions by vertex
+    uint32_t *adj_off = nullptr;  // [V + 1] single I32 layouts: adjacency offsets (per edge list)
+    int32_t *adj = nullptr;       // [2 E] the other endpoint of each incident edge
+    uint32_t *ma_nz = nullptr;    // [V] non-zero incident directions of each vertex (at the start of its slots)
+    double *ma_dv = nullptr;      // [V] d_v of each vertex (-1: degree < 2, not counted)
+    uint32_t *ma_touch = nullptr; // [V] zero between calls (incremental min angle)
+    uint32_t *ma_flag = nullptr;  // [1024] min-angle blocks to recompute, zero between calls
     uint2 *seg_ids = nullptr;     // [E] FP32 layouts: vertex ids of seg[i] (seg holds the FP32 endpoints)
     double *dir_ang = nullptr;    // [2 E] FP32 layouts: incident direction angles by vertex
     int32_t *dir_other = nullptr; // [2 E] FP32 layouts: far vertex of each incident direction
@@ -216,7 +222,15 @@ void launch_occlusion_grid_pairs(const Buffers &b, int64_t V, const GridBuffers 
 void launch_occlusion_allpairs(const Buffers &b, int64_t V, int64_t d, cudaStream_t s);
 
 // a9: minimum angle.
+// Adjacency CSR of the edge list (b.adj_off, b.adj), once per edge list.
+void launch_adjacency(Buffers &b, int64_t V, int64_t E, cudaStream_t s);
+// Minimum angle of a single I32 layout (needs the adjacency): per-block
+// partials into b.ma_part / b.ma_cnt.
 void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s);
+// The same after vertices ids[0, n) moved (b.xy updated), when b.ma_part
+// holds the partials of the layout before the move: only the blocks holding
+// a moved vertex or a neighbour of one are recomputed.
+void launch_min_angle_moved(Buffers &b, int64_t V, const int32_t *ids, int64_t n, cudaStream_t s);
 int min_angle_blocks(int64_t V);
 
 // a10: edge length variation, two passes of deterministic FP64 partials.
@@ -235,6 +249,62 @@ void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal
 
 // Per-edge output conversion: integer dev sums to radians (double), in place.
 void launch_per_edge_export(uint64_t *dev_fixed, int64_t E, cudaStream_t s);
+
+// ------------------------------------------------------ incremental moves
+// Tallies of the pairs that involve moved vertices, before (k[0]) and after
+// (k[1]) the move.
+struct DeltaCounts {
+    uint64_t proper, touching, collinear, dev_lo, dev_hi, occlusion;
+};
+struct DeltaAcc {
+    uint32_t status;      // ST_* bits from the validation of the moves
+    uint32_t n_affected;  // edges with a moved endpoint
+    uint64_t tested;      // crossing pairs classified in both passes
+    uint32_t fallback;    // the dirty list overflowed: the counts are incomplete (a full evaluation follows)
+    uint32_t pad_;
+    DeltaCounts k[2];
+};
+
+// Edges moved since the crossing grid was built ("dirty"): their grid
+// records are stale, so the incremental passes take them from a list of
+// their own.  dirty[e] flags membership, list[0, *n) holds them (n may pass
+// cap, which raises DeltaAcc::fallback).
+struct DirtySet {
+    uint8_t *flag = nullptr;  // [E]
+    uint32_t *list = nullptr; // [cap]
+    uint32_t *n = nullptr;    // device count
+    uint32_t cap = 0;
+};
+
+// Marks the moved vertices in `moved` (zero on entry), checking ids and new
+// coordinates (device arrays, n entries) into d->status.
+void launch_delta_validate(const int32_t *ids, const int32_t *xy_new, int64_t n, int64_t V, uint32_t *moved,
+                           DeltaAcc *d, cudaStream_t s);
+void launch_delta_unmark(const int32_t *ids, int64_t n, int64_t V, uint32_t *moved, cudaStream_t s);
+// Lists the edges with a moved endpoint (count -> d->n_affected); with a
+// dirty set (flag != nullptr), also adds the ones not yet in it.
+void launch_delta_affected(const Buffers &b, int64_t E, const uint32_t *moved, uint32_t *affected, DeltaAcc *d,
+                           const DirtySet &ds, cudaStream_t s);
+// The crossing part of a pass through the grid of the last full evaluation
+// (cell side 2^k, GridBuffers cell_off and rec as it left them): the affected
+// edges against every clean edge via the cells, and against the dirty list.
+void launch_delta_grid_pass(const Buffers &b, const GridBuffers &g, int k, const uint32_t *moved,
+                            const uint32_t *affected, const DirtySet &ds, uint32_t ideal, DeltaAcc *d, int which,
+                            cudaStream_t s);
+// Tallies into d->k[which] the crossing pairs of the affected edges and the
+// occlusion pairs of the moved vertices, on the coordinates in b.xy; the
+// gathered segments (b.seg, b.seg_eid, b.seg_theta, b.acc->n_seg) must be
+// those of the same coordinates.  Does nothing once d->status is set.
+void launch_delta_pass(const Buffers &b, int64_t V, int64_t E, const int32_t *ids, int64_t n, const uint32_t *moved,
+                       const uint32_t *affected, bool crossings, uint32_t ideal, bool occlusion, long long d2,
+                       DeltaAcc *d, int which, cudaStream_t s);
+// Writes the new coordinates of the moved vertices into b.xy (unless
+// d->status reports an invalid move).
+void launch_delta_apply(const int32_t *ids, const int32_t *xy_new, int64_t n, const DeltaAcc *d, Buffers &b,
+                        cudaStream_t s);
+// The evaluation part of b.acc = last - k[0] + k[1] (unless d->status
+// reports an invalid move).
+void launch_delta_combine(const DeltaCounts &last, const DeltaAcc *d, Buffers &b, cudaStream_t s);
 
 // ------------------------------------------------------ differentiable form
 // What the backward needs from the forward, on the device.

@@ -1,14 +1,22 @@
 // k_minangle.cu -- minimum angle M_a (a9, Algorithm 2).
 //
 // The aggregateMessages step of Algorithm 2 (collect, per vertex, the angles
-// of its incident edges) becomes a CSR build: degree count, exclusive scan,
-// scatter of the incident direction vectors.  GetMinAngle (sort the angles,
-// take the smallest gap between neighbours, wrap-around included) becomes an
-// exact successor search: for every incident direction d_i, the next
-// direction counter-clockwise is found with exact integer comparisons (half
-// plane relative to d_i, then the sign of a cross product), and the gap to it
-// is the ccw angle between the two vectors.  The set of gaps is the set of
-// neighbour gaps of the sorted order, so its minimum is GetMinAngle's result.
+// of its incident edges) becomes a CSR: for a single layout, the adjacency of
+// the edge list (degree count, exclusive scan, scatter of the other
+// endpoints) is built once per edge list, and every evaluation writes each
+// vertex's non-zero incident direction vectors into its slot range; the
+// batched evaluator builds the CSR of direction vectors directly.
+// GetMinAngle (sort the angles, take the smallest gap between neighbours,
+// wrap-around included) becomes an exact successor search: for every
+// incident direction d_i, the next direction counter-clockwise is found with
+// exact integer comparisons (half plane relative to d_i, then the sign of a
+// cross product), and the gap to it is the ccw angle between the two
+// vectors.  The set of gaps is the set of neighbour gaps of the sorted order,
+// so its minimum is GetMinAngle's result.  A vertex's d_v does not depend on
+// the order its directions are stored in, and each block's partial sum covers
+// a fixed set of vertices, so after a few vertices move only the blocks
+// holding them or their neighbours are recomputed, with the same result as a
+// full pass.
 #include <math.h>
 
 #include "gr_internal.cuh"
@@ -99,16 +107,34 @@ __device__ __forceinline__ double ccw_gap_d(int2 a, int2 b) {
     return g < 0.0 ? g + 2.0 * M_PI : g;
 }
 
+// d_v of a vertex from its k incident directions d[0, k) by one thread:
+// (2 pi / k - min) / (2 pi / k), or -1 when k < 2 (not counted; deg = 1 has a
+// single 2 pi gap).  Gaps are compared in FP32 and the smallest is recomputed
+// in FP64; the choice does not depend on the storage order.
+__device__ __forceinline__ double vertex_dv(const int2 *__restrict__ d, int k) {
+    if (k < 2) return -1.0;
+    float gmin = 1e30f;
+    int2 bi = make_int2(1, 0), bs = make_int2(1, 0);
+    for (int i = 0; i < k; ++i) {
+        const int2 di = d[i];
+        const int2 db = ccw_successor(d, k, i, di);
+        const float g = ccw_gap_f(di, db);
+        if (better_gap(g, di, gmin, bi)) { gmin = g; bi = di; bs = db; }
+    }
+    const double ideal = 2.0 * M_PI / (double)k;
+    return (ideal - ccw_gap_d(bi, bs)) / ideal;
+}
+
 // The vertices [v0, v1) taken by this block: one thread per vertex, and
-// vertices of degree > 32 by the whole warp after the per-thread pass.  Gaps
-// are compared in FP32 and the smallest is recomputed in FP64.
-// d_v = (2 pi / deg - min) / (2 pi / deg) for every vertex with deg >= 2
-// (deg = 1 has a single 2 pi gap, d_v = 0).  Accumulates sum d_v and the
-// count of such vertices into (dsum, nv), per thread.  `step` is the stride
-// between this block's rounds of MA_THREADS vertices.
-__device__ __forceinline__ void min_angle_range(const uint32_t *__restrict__ off, const int2 *__restrict__ dirs,
-                                                int64_t v0, int64_t v1, int64_t step, double &dsum,
-                                                uint32_t &nv) {
+// vertices of degree > 32 by the whole warp after the per-thread pass.
+// Accumulates d_v and the count of vertices with deg >= 2 into (dsum, nv) of
+// the thread that owns the vertex (also for the warp-shared ones), so each
+// thread adds its own vertices' d_v in round order; with `dv`, d_v (or -1)
+// is stored per vertex as well.  `step` is the stride between this block's
+// rounds of MA_THREADS vertices.
+__device__ __forceinline__ void min_angle_range(const uint32_t *__restrict__ off, const uint32_t *__restrict__ nz,
+                                                const int2 *__restrict__ dirs, int64_t v0, int64_t v1, int64_t step,
+                                                double *__restrict__ dv, double &dsum, uint32_t &nv) {
     const int lane = threadIdx.x & 31;
     for (int64_t base = v0; base < v1; base += step) {
         const int64_t v = base + threadIdx.x;
@@ -116,22 +142,16 @@ __device__ __forceinline__ void min_angle_range(const uint32_t *__restrict__ off
         uint32_t start = 0;
         if (v < v1) {
             start = off[v];
-            k = (int)(off[v + 1] - start);
+            k = (int)(nz ? nz[v] : off[v + 1] - start);
         }
         const bool heavy = k > MA_HEAVY;
-        if (k >= 2 && !heavy) {
-            const int2 *d = dirs + start;
-            float gmin = 1e30f;
-            int2 bi = make_int2(1, 0), bs = make_int2(1, 0);
-            for (int i = 0; i < k; ++i) {
-                const int2 di = d[i];
-                const int2 db = ccw_successor(d, k, i, di);
-                const float g = ccw_gap_f(di, db);
-                if (better_gap(g, di, gmin, bi)) { gmin = g; bi = di; bs = db; }
+        if (v < v1 && !heavy) {
+            const double x = vertex_dv(dirs + start, k);
+            if (dv) dv[v] = x;
+            if (x >= 0.0) {
+                dsum += x;
+                nv += 1;
             }
-            const double ideal = 2.0 * M_PI / (double)k;
-            dsum += (ideal - ccw_gap_d(bi, bs)) / ideal;
-            nv += 1;
         }
         // heavy vertices: the whole warp splits the directions of one vertex
         unsigned hm = __ballot_sync(0xffffffffu, heavy);
@@ -157,31 +177,184 @@ __device__ __forceinline__ void min_angle_range(const uint32_t *__restrict__ off
                 const int2 obs = make_int2(__shfl_xor_sync(0xffffffffu, bs.x, o), __shfl_xor_sync(0xffffffffu, bs.y, o));
                 if (better_gap(og, obi, gmin, bi)) { gmin = og; bi = obi; bs = obs; }
             }
-            if (lane == 0) {
+            if (lane == src) {
                 const double ideal = 2.0 * M_PI / (double)hk;
-                dsum += (ideal - ccw_gap_d(bi, bs)) / ideal;
+                const double x = (ideal - ccw_gap_d(bi, bs)) / ideal;
+                if (dv) dv[v] = x;
+                dsum += x;
                 nv += 1;
             }
         }
     }
 }
 
-// Single layout: fixed vertex -> block mapping, so the per-block FP64
-// partial sums are deterministic.
+// Single layout: fixed vertex -> block mapping (vertex v in block
+// (v / MA_THREADS) mod gridDim.x), so the per-block FP64 partial sums are
+// deterministic.  Stores every vertex's d_v (-1: not counted) in dv.
 __global__ void __launch_bounds__(MA_THREADS) k_min_angle(const uint32_t *__restrict__ off,
+                                                          const uint32_t *__restrict__ nz,
                                                           const int2 *__restrict__ dirs, int64_t V,
-                                                          double *__restrict__ part,
+                                                          double *__restrict__ dv, double *__restrict__ part,
                                                           uint32_t *__restrict__ cnt) {
     __shared__ double shd[32];
     __shared__ uint64_t shu[32];
     double dsum = 0.0;
     uint32_t nv = 0;
-    min_angle_range(off, dirs, (int64_t)blockIdx.x * MA_THREADS, V, (int64_t)gridDim.x * MA_THREADS, dsum, nv);
+    min_angle_range(off, nz, dirs, (int64_t)blockIdx.x * MA_THREADS, V, (int64_t)gridDim.x * MA_THREADS, dv, dsum,
+                    nv);
     const double s = block_sum<double>(dsum, shd);
     const uint64_t c = block_sum<uint64_t>(nv, shu);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = s;
         cnt[blockIdx.x] = (uint32_t)c;
+    }
+}
+
+// The partial sums of the flagged blocks again from the stored d_v, in the
+// order k_min_angle adds them (each thread its own vertices by round, then
+// the same block reduction), so they equal a full pass bit for bit; clears
+// the flags.
+__global__ void __launch_bounds__(MA_THREADS) k_min_angle_resum(const double *__restrict__ dv, int64_t V,
+                                                                double *__restrict__ part,
+                                                                uint32_t *__restrict__ cnt, uint32_t *flag) {
+    __shared__ double shd[32];
+    __shared__ uint64_t shu[32];
+    if (!flag[blockIdx.x]) return;
+    double dsum = 0.0;
+    uint32_t nv = 0;
+    for (int64_t v = (int64_t)blockIdx.x * MA_THREADS + threadIdx.x; v < V; v += (int64_t)gridDim.x * MA_THREADS) {
+        const double x = dv[v];
+        if (x >= 0.0) {
+            dsum += x;
+            nv += 1;
+        }
+    }
+    const double s = block_sum<double>(dsum, shd);
+    const uint64_t c = block_sum<uint64_t>(nv, shu);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s;
+        cnt[blockIdx.x] = (uint32_t)c;
+        flag[blockIdx.x] = 0u;
+    }
+}
+
+__device__ __forceinline__ bool valid_edge(int2 ed, int64_t V) {
+    return ed.x >= 0 && ed.y >= 0 && ed.x < V && ed.y < V && ed.x != ed.y;
+}
+
+// Adjacency of the edge list: degrees, then (after the scan) the other
+// endpoint of every incident edge.  Invalid edges are left out (the gather
+// reports them).
+__global__ void k_adj_degree(const int2 *__restrict__ edges, int64_t E, int64_t V, uint32_t *__restrict__ deg) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ed = edges[e];
+        if (!valid_edge(ed, V)) continue;
+        atomicAdd(&deg[ed.x], 1u);
+        atomicAdd(&deg[ed.y], 1u);
+    }
+}
+
+__global__ void k_adj_fill(const int2 *__restrict__ edges, int64_t E, int64_t V, const uint32_t *__restrict__ off,
+                           uint32_t *__restrict__ fill, int32_t *__restrict__ adj) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ed = edges[e];
+        if (!valid_edge(ed, V)) continue;
+        adj[off[ed.x] + atomicAdd(&fill[ed.x], 1u)] = ed.y;
+        adj[off[ed.y] + atomicAdd(&fill[ed.y], 1u)] = ed.x;
+    }
+}
+
+// The non-zero direction vectors from v to its neighbours, written to the
+// start of v's slot range by one thread; returns how many.
+__device__ __forceinline__ uint32_t vertex_dirs(const int2 *__restrict__ xy, int64_t v, uint32_t o0, uint32_t o1,
+                                                const int32_t *__restrict__ adj, int2 *__restrict__ dirs) {
+    const int2 p = xy[v];
+    uint32_t j = o0;
+    for (uint32_t q = o0; q < o1; ++q) {
+        const int2 u = xy[adj[q]];
+        const int dx = u.x - p.x, dy = u.y - p.y;
+        if (dx | dy) dirs[j++] = make_int2(dx, dy);
+    }
+    return j - o0;
+}
+
+// Every vertex's non-zero directions (nz[v] of them) at the start of its
+// slot range: one thread per vertex, a warp per vertex of degree > MA_HEAVY
+// (ballot compaction).
+__global__ void __launch_bounds__(256) k_ma_dirs(const int2 *__restrict__ xy, int64_t V,
+                                                 const uint32_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                                 uint32_t *__restrict__ nz, int2 *__restrict__ dirs) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + threadIdx.x;
+        uint32_t o0 = 0, o1 = 0;
+        if (v < V) {
+            o0 = off[v];
+            o1 = off[v + 1];
+        }
+        const bool heavy = o1 - o0 > (uint32_t)MA_HEAVY;
+        if (v < V && !heavy) nz[v] = vertex_dirs(xy, v, o0, o1, adj, dirs);
+        unsigned hm = __ballot_sync(0xffffffffu, heavy);
+        while (hm) {
+            const int src = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const int64_t hv = __shfl_sync(0xffffffffu, v, src);
+            const uint32_t h0 = __shfl_sync(0xffffffffu, o0, src), h1 = __shfl_sync(0xffffffffu, o1, src);
+            const int2 p = xy[hv];
+            uint32_t j = h0;
+            for (uint32_t q0 = h0; q0 < h1; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                int2 dd = make_int2(0, 0);
+                if (q < h1) {
+                    const int2 u = xy[adj[q]];
+                    dd = make_int2(u.x - p.x, u.y - p.y);
+                }
+                const bool keep = q < h1 && (dd.x | dd.y);
+                const unsigned km = __ballot_sync(0xffffffffu, keep);
+                unsigned lt;
+                asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+                if (keep) dirs[j + __popc(km & lt)] = dd;
+                j += __popc(km);
+            }
+            if (lane == 0) nz[hv] = j - h0;
+        }
+    }
+}
+
+// After a move: a warp per moved vertex v rewrites the directions and d_v
+// of v and of each neighbour (once each: `touch` flags; one thread per
+// vertex) and flags the min-angle blocks holding them (nb blocks).
+__global__ void k_ma_touch(const int2 *__restrict__ xy, int64_t V, const int32_t *__restrict__ ids, int64_t n,
+                           const uint32_t *__restrict__ off, const int32_t *__restrict__ adj,
+                           uint32_t *__restrict__ touch, uint32_t *__restrict__ nz, int2 *__restrict__ dirs,
+                           double *__restrict__ dv, uint32_t *__restrict__ flag, int nb) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const int32_t v = ids[i];
+        if (v < 0 || v >= V) continue;  // an invalid move (reported by its validation)
+        const uint32_t o0 = off[v], o1 = off[v + 1];
+        for (int64_t q = (int64_t)o0 - 1 + lane; q < (int64_t)o1; q += 32) {
+            const int32_t u = q < (int64_t)o0 ? v : adj[q];  // slot o0 - 1 stands for v itself
+            if (atomicExch(&touch[u], 1u) != 0u) continue;
+            const uint32_t k = vertex_dirs(xy, u, off[u], off[u + 1], adj, dirs);
+            nz[u] = k;
+            dv[u] = vertex_dv(dirs + off[u], (int)k);
+            flag[(u / MA_THREADS) % nb] = 1u;
+        }
+    }
+}
+
+__global__ void k_ma_untouch(int64_t V, const int32_t *__restrict__ ids, int64_t n,
+                             const uint32_t *__restrict__ off, const int32_t *__restrict__ adj,
+                             uint32_t *__restrict__ touch) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const int32_t v = ids[i];
+        if (v < 0 || v >= V) continue;
+        const uint32_t o0 = off[v], o1 = off[v + 1];
+        for (int64_t q = (int64_t)o0 - 1 + lane; q < (int64_t)o1; q += 32) touch[q < (int64_t)o0 ? v : adj[q]] = 0u;
     }
 }
 
@@ -195,7 +368,7 @@ __global__ void __launch_bounds__(MA_THREADS) k_batch_min_angle(const uint32_t *
     for (int64_t l = blockIdx.x; l < L; l += gridDim.x) {
         double dsum = 0.0;
         uint32_t nv = 0;
-        min_angle_range(off, dirs, v_off[l], v_off[l + 1], MA_THREADS, dsum, nv);
+        min_angle_range(off, nullptr, dirs, v_off[l], v_off[l + 1], MA_THREADS, nullptr, dsum, nv);
         const double s = block_sum<double>(dsum, shd);
         const uint64_t c = block_sum<uint64_t>(nv, shu);
         if (threadIdx.x == 0) {
@@ -235,11 +408,34 @@ void build_direction_csr(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
 }
 }  // namespace
 
+void launch_adjacency(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
+    if (V <= 0) return;
+    cudaMemsetAsync(b.adj_off, 0, sizeof(uint32_t) * (V + 1), s);
+    cudaMemsetAsync(b.deg_fill, 0, sizeof(uint32_t) * V, s);
+    const int gb = grid_for(E, 256, 152 * 8);
+    count_launches(E > 0 ? 2 : 0);
+    if (E > 0) k_adj_degree<<<gb, 256, 0, s>>>((const int2 *)b.edges, E, V, b.adj_off);
+    launch_scan_u32(b.adj_off, b.adj_off, V, b.scan_tmp, &b.acc->scan_sink, &b.acc->status, s);
+    if (E > 0) k_adj_fill<<<gb, 256, 0, s>>>((const int2 *)b.edges, E, V, b.adj_off, b.deg_fill, b.adj);
+}
+
 void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
     if (V <= 0) return;
-    build_direction_csr(b, V, E, s);
-    count_launches(1);
-    k_min_angle<<<min_angle_blocks(V), MA_THREADS, 0, s>>>(b.deg, b.dirs, V, b.ma_part, b.ma_cnt);
+    count_launches(2);
+    k_ma_dirs<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.xy, V, b.adj_off, b.adj, b.ma_nz, b.dirs);
+    k_min_angle<<<min_angle_blocks(V), MA_THREADS, 0, s>>>(b.adj_off, b.ma_nz, b.dirs, V, b.ma_dv, b.ma_part,
+                                                           b.ma_cnt);
+}
+
+void launch_min_angle_moved(Buffers &b, int64_t V, const int32_t *ids, int64_t n, cudaStream_t s) {
+    if (V <= 0 || n <= 0) return;
+    const int nb = min_angle_blocks(V);
+    const int gw = grid_for(n * 32, 256, 152 * 4);
+    count_launches(3);
+    k_ma_touch<<<gw, 256, 0, s>>>((const int2 *)b.xy, V, ids, n, b.adj_off, b.adj, b.ma_touch, b.ma_nz, b.dirs,
+                                  b.ma_dv, b.ma_flag, nb);
+    k_min_angle_resum<<<nb, MA_THREADS, 0, s>>>(b.ma_dv, V, b.ma_part, b.ma_cnt, b.ma_flag);
+    k_ma_untouch<<<gw, 256, 0, s>>>(V, ids, n, b.adj_off, b.adj, b.ma_touch);
 }
 
 void launch_batch_min_angle(Buffers &b, const BatchView &bv, int64_t V, int64_t E, cudaStream_t s) {

@@ -19,7 +19,7 @@ GR_COORD_I32, GR_COORD_F32 = 0, 1
 GR_LONG_AUTO, GR_LONG_ALLPAIRS, GR_LONG_GRID = 0, 1, 2
 GR_METRIC_OCCLUSION, GR_METRIC_MIN_ANGLE, GR_METRIC_EDGE_LENGTH, GR_METRIC_CROSSINGS = 1, 2, 4, 8
 GR_METRIC_ALL = 15
-GR_PATH_AUTO, GR_PATH_GRID, GR_PATH_ALLPAIRS = 0, 1, 2
+GR_PATH_AUTO, GR_PATH_GRID, GR_PATH_ALLPAIRS, GR_PATH_DELTA = 0, 1, 2, 3
 DEFAULT_IDEAL = 7.0 * math.pi / 18.0
 
 _STATUS_NAMES = ["GR_OK", "GR_EINVAL", "GR_ERANGE", "GR_ENOMEM", "GR_ECUDA", "GR_ETIMEOUT", "GR_ENOTSUP"]
@@ -113,6 +113,8 @@ def load() -> ctypes.CDLL:
         "gr_batch_update": ([P, P, P], c_int32),
         "gr_batch_evaluate": ([P, c_uint32, ctypes.POINTER(gr_params), P], c_int32),
         "gr_batch_destroy": ([P], c_int32),
+        "gr_move_vertices": ([P, c_int64, P, P, c_uint32, ctypes.POINTER(gr_params), ctypes.POINTER(gr_result)],
+                             c_int32),
         "gr_diff_forward": ([P, c_double, P], c_int32),
         "gr_diff_backward": ([P, P, P], c_int32),
         "gr_last_error": ([], ctypes.c_char_p),
@@ -188,6 +190,21 @@ def gr_layout_update(layout, xy, edges=None, coord_type: int = GR_COORD_I32) -> 
     xp, xk = _buffer(xy, "int32" if coord_type == GR_COORD_I32 else "float32")
     ep, ek = _buffer(edges, "int32")
     _check(lib.gr_layout_update(layout, xp, ep))
+
+
+def gr_move_vertices(layout, ids, xy_new, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+                     occlusion_d: int = 0) -> gr_result:
+    """Moves vertices ids[i] to xy_new[i] and evaluates the moved layout
+    (incrementally when the previous evaluation allows it)."""
+    ip, ik = _buffer(ids, "int32")
+    xp, xk = _buffer(xy_new, "int32")
+    n = _count(ik)
+    if tuple(xk.shape) != (n, 2):
+        raise ValueError(f"xy_new must have shape ({n}, 2), got {tuple(xk.shape)}")
+    r = gr_result()
+    p = gr_params(float(ideal_rad), int(occlusion_d))
+    _check(load().gr_move_vertices(layout, n, ip, xp, metrics, ctypes.byref(p), ctypes.byref(r)))
+    return r
 
 
 def gr_diff_forward(layout, ideal_rad: float = 0.0, out3=None):
@@ -392,6 +409,10 @@ class Layout:
 
     def evaluate(self, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0, occlusion_d: int = 0) -> gr_result:
         return gr_evaluate(self.handle, metrics, ideal_rad, occlusion_d)
+
+    def move(self, ids, xy_new, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+             occlusion_d: int = 0) -> gr_result:
+        return gr_move_vertices(self.handle, ids, xy_new, metrics, ideal_rad, occlusion_d)
 
     def profile(self, reset: bool = False) -> dict:
         return gr_profile_read(self.handle, reset).as_dict()
