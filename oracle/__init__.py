@@ -12,6 +12,10 @@ Each function follows a definition of arXiv 2411.09809:
   crossings_of_edges      -- the same, restricted to sampled edges
   min_angle               -- Sec. 2.1, Algorithm 2
   edge_length_variation   -- Sec. 2.1, Algorithm 3
+the paper's approximate strip algorithms (``strip_oracle.c``):
+  strip_crossings         -- Sec. 3.2.2 (E_c estimate) and Sec. 3.2.3 with
+      Eq. 1 (crossing-angle estimate), vertical or horizontal strips;
+  strip_eq1, strip_category -- Eq. 1 and its 8 angle categories;
 and, for FP32 coordinates (the differentiable form; ``xy`` float32 [V, 2]):
   orient_f32, crossings_f32, min_angle_f32, edge_length_variation_f32 -- the
       same definitions with exact orientation predicates on FP32 inputs;
@@ -30,6 +34,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gr_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "strip_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "_build", "libgr_oracle.so")
 _lib = None
 
@@ -39,11 +44,12 @@ DEFAULT_IDEAL = 7.0 * math.pi / 18.0  # 70 degrees (Sec. 2.1)
 def build(force: bool = False) -> str:
     """Compiles the oracle shared library with gcc (plain C, OpenMP)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.run(
             ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
-             _SRC, "-o", tmp, "-lm"],
+             *_SRCS, "-o", tmp, "-lm"],
             check=True,
         )
         os.replace(tmp, _LIB_PATH)
@@ -71,6 +77,13 @@ def _load():
         lib.oracle_min_angle.restype = ctypes.c_int
         lib.oracle_edge_length_variation.argtypes = [i32p, i64, i32p, i64]
         lib.oracle_edge_length_variation.restype = ctypes.c_double
+        lib.oracle_strip_crossings.argtypes = [i32p, i64, i32p, i64, i64, ctypes.c_int, ctypes.c_double, i64p,
+                                               f64p, i64p]
+        lib.oracle_strip_crossings.restype = ctypes.c_int
+        lib.oracle_strip_eq1.argtypes = [ctypes.c_double, ctypes.c_double, i64p, f64p]
+        lib.oracle_strip_eq1.restype = ctypes.c_double
+        lib.oracle_strip_category.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.oracle_strip_category.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
@@ -236,3 +249,44 @@ def diff_terms_and_grads(xy, edges, ideal: float = DEFAULT_IDEAL, return_counts:
         raise ValueError("ideal angle must be in (0, pi/2]")
     out = (terms, g[0][:V], g[1][:V], g[2][:V])
     return out + (counts,) if return_counts else out
+
+
+# ------------------------------------------------ approximate strip algorithm
+
+@dataclass
+class StripEstimate:
+    crossings: int       # pairs whose key order reverses inside a strip both span (Sec. 3.2.2)
+    term_sum: float      # sum over those pairs of |ideal - angle| / ideal (Sec. 3.2.3, Eq. 1)
+    records: int         # (segment, strip) pairs
+    E_ca: float          # 1 - term_sum / crossings (1 when there is none)
+    orientation: int     # 0 vertical strips, 1 horizontal
+
+
+def strip_crossings(xy, edges, l: int, orientation: int = 0, ideal: float = DEFAULT_IDEAL) -> StripEstimate:
+    """The strip estimates of E_c and E_ca (Sec. 3.2.2-3.2.3) for strips of width l.
+    orientation 0: vertical strips, 1: horizontal, 2: both (the larger count)."""
+    if orientation == 2:
+        a = strip_crossings(xy, edges, l, 0, ideal)
+        b = strip_crossings(xy, edges, l, 1, ideal)
+        return b if b.crossings > a.crossings else a
+    xy, edges = _xy(xy), _edges(edges)
+    c = np.zeros(1, np.int64)
+    t = np.zeros(1, np.float64)
+    r = np.zeros(1, np.int64)
+    if _load().oracle_strip_crossings(xy, xy.shape[0], edges, edges.shape[0], int(l), int(orientation),
+                                      float(ideal), c, t, r) != 0:
+        raise ValueError("bad strip width, orientation or edge ids")
+    n = int(c[0])
+    return StripEstimate(n, float(t[0]), int(r[0]), 1.0 - float(t[0]) / n if n > 0 else 1.0, int(orientation))
+
+
+def strip_eq1(theta_i: float, ideal: float, counts, sums) -> float:
+    """Eq. 1: category counts and angle sums (LIL, LIG, LOG, LOL, RIL, RIG, ROG, ROL)
+    -> sum of |ideal - angle| over the crossing segments."""
+    return float(_load().oracle_strip_eq1(float(theta_i), float(ideal), np.ascontiguousarray(counts, np.int64),
+                                          np.ascontiguousarray(sums, np.float64)))
+
+
+def strip_category(theta_i: float, theta_j: float, ideal: float) -> int:
+    """Angle category (0..7 = LIL, LIG, LOG, LOL, RIL, RIG, ROG, ROL) of theta_j relative to theta_i."""
+    return int(_load().oracle_strip_category(float(theta_i), float(theta_j), float(ideal)))
