@@ -49,8 +49,12 @@ WORKLOADS = {
     "batched": ("batched_layouts", 256),
     "differentiable": ("differentiable_layout", 0),
     "moves": ("large_sparse_layout", 64),
+    "strips": ("dense_long_edge_layout", 0),
 }
 MOVES_PER_STEP = 16
+STRIP_WIDTH = 64          # vertical strips of the approximate algorithm (Sec. 3.2.2)
+OPS_PER_STRIP_PAIR = 10   # per counted pair: direction load, wrapped difference, acute fold, |ideal - a|, add
+OPS_PER_MERGE_STEP = 6    # per binary-search step of a merge level: load, 64-bit compare, select
 
 
 def dist_env():
@@ -658,6 +662,170 @@ def run_moves(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def strip_oracle_sample(L, l, budget_s: float, seed: int = 0) -> dict:
+    """The strip oracle on the first E' edges, E' grown until one run takes about
+    budget_s / 4; the rate in resolved pairs/s (the oracle's work and the metric
+    both scale as E'^2)."""
+    import oracle
+    E = min(L.E, 2000)
+    while True:
+        t0 = time.perf_counter()
+        oracle.strip_crossings(L.xy, L.edges[:E], l, 0)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or E >= L.E:
+            break
+        E = min(L.E, int(E * max(1.3, min(4.0, math.sqrt(budget_s / 4 / max(dt, 1e-3))))))
+    return {"rate": E * (E - 1) / 2 / dt, "step_s": dt, "edges": E, "cores": oracle.num_threads(),
+            "sample": f"the strip oracle (vertical strips of width {l}) on the first {E} of {L.E} edges, "
+                      f"rate = E'(E'-1)/2 / time (its work grows as E'^2)"}
+
+
+def run_strips(args, rank, world, local_rank):
+    """Approximate-strip workload (Sec. 3.2.2-3.2.3): on the dense long-edge
+    layout (random segments, the paper's setting for Table 3), one step =
+    gr_strip_crossings with vertical strips of width STRIP_WIDTH (the E_c
+    estimate and the crossing-angle estimate).  The exact count is taken once,
+    untimed, for the errors."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_09809_gb300 import build as gr_build, gr
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        if rank == 0:
+            gr_build.build()
+        dist.barrier()
+    else:
+        gr_build.build()
+    gr.load()
+    L, _ = make_workload("strips")
+    l = args.strip_width
+    dev = torch.device("cuda", local_rank)
+    xy = torch.from_numpy(L.xy).to(dev)
+    edges = torch.from_numpy(L.edges).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lay = gr.Layout(xy, edges, gr.gr_options(0, 0, 0, 1, 0), stream=stream.cuda_stream)
+    exact = lay.evaluate(gr.GR_METRIC_CROSSINGS, IDEAL, 0).crossing
+
+    def step():
+        lay.update(xy)
+        return lay.strips(l, gr.GR_STRIP_VERTICAL, IDEAL)
+
+    for _ in range(args.warmup):
+        res = step()
+    lay.profile(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = gr.gr_kernel_launches()
+    for i in range(args.steps):
+        flush.fill_(i)
+        starts[i].record(stream)
+        res = step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    launches = gr.gr_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    prof = lay.profile()
+    # end to end through the C ABI from pinned host coordinates
+    hxy = torch.from_numpy(L.xy).pin_memory()
+    io0 = gr.gr_io_bytes(lay.handle)
+    e2e_s = []
+    for i in range(0 if args.no_e2e else args.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gr.gr_layout_update(lay.handle, hxy, None)
+        gr.gr_strip_crossings(lay.handle, l, gr.GR_STRIP_VERTICAL, IDEAL)
+        e2e_s.append(time.perf_counter() - t0)
+    io1 = gr.gr_io_bytes(lay.handle)
+    e2e_ms = statistics.mean(e2e_s) * 1e3 if e2e_s else float("nan")
+    lay.close()
+    if rank != 0:
+        return
+    E = L.E
+    pairs = E * (E - 1) / 2
+    # roofline of the counting phase (merge by r with the inverted pairs)
+    peaks, peak_kind = load_peaks()
+    R = res.records
+    levels = max(1, math.ceil(math.log2(max(2, R / max(1, res.strips)))))
+    merge_ops = R * sum(OPS_PER_MERGE_STEP * (k + 2) for k in range(levels))
+    count_ops = merge_ops + res.crossings * OPS_PER_STRIP_PAIR
+    cnt_ms = prof["strip_count"][0] / max(1, prof["strip_count"][1])
+    peak = SM_COUNT * LANES_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = count_ops / (cnt_ms / 1e3) / 1e12
+    line = {
+        "metric": "edge-pair tests/s", "value": world * pairs / (ms / 1e3), "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"strips_{l}_of_{L.name}", "V": L.V, "E": E, "strip_width": l,
+                   "orientation": "vertical", "ideal_deg": 70.0,
+                   "step": "gr_layout_update + gr_strip_crossings (E_c and E_ca estimates, Sec. 3.2.2-3.2.3)",
+                   "inputs": "seeded synthetic (paper_2411_09809_gb300.synth)",
+                   "l2": "256 MiB write between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "results": {"E_c_estimate": res.crossings, "E_c_exact": exact.c.crossings,
+                    "E_c_error": 1.0 - res.crossings / max(1, exact.c.crossings),
+                    "E_ca_estimate": res.E_ca, "E_ca_exact": exact.E_ca,
+                    "E_ca_error": abs(res.E_ca - exact.E_ca) / exact.E_ca,
+                    "records": R, "strips": res.strips},
+        "phase_ms": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]},
+        "roofline": {"kernel": "k_strip_tile<true> + k_strip_level<true> (the counting phase)", "bound": "alu",
+                     "achieved": achieved, "peak": peak, "unit": "Tops/s (int32-equivalent lane ops)",
+                     "frac": achieved / peak,
+                     "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
+                                    f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
+                     "work": f"{OPS_PER_MERGE_STEP} ops per binary-search step of each merge level and record, "
+                             f"{OPS_PER_STRIP_PAIR} per counted pair",
+                     "traffic": None, "launch_ms": cnt_ms},
+        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": (io1[0] - io0[0]) // max(1, len(e2e_s)),
+                "d2h_bytes_per_step": (io1[1] - io0[1]) // max(1, len(e2e_s))},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = strip_oracle_sample(L, l, args.cpu_budget)
+        line["cpu_baseline"] = {"value": cb["rate"], "unit": "pairs/s", "cores": cb["cores"], "kind": "oracle",
+                                "sample": cb["sample"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_strips(args):
+    L, _ = make_workload("strips")
+    l = args.strip_width
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        strip_oracle_sample(L, l, budget / 2)
+    runs = [strip_oracle_sample(L, l, budget) for _ in range(args.steps)]
+    rate = statistics.mean(r["rate"] for r in runs)
+    E = L.E
+    line = {
+        "impl": "reference", "metric": "edge-pair tests/s", "value": rate, "unit": "pairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": E * (E - 1) / 2 / rate * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"strips_{l}_of_{L.name}", "V": L.V, "E": E, "strip_width": l,
+                   "orientation": "vertical", "ideal_deg": 70.0},
+        "cpu_baseline": {"value": rate, "unit": "pairs/s", "cores": runs[0]["cores"], "kind": "oracle",
+                         "sample": runs[0]["sample"]},
+        "e2e": {"value": rate, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle (plain C brute force) on the host cores."""
     if rank != 0:
@@ -667,6 +835,9 @@ def run_reference(args, rank, world):
         return
     if args.workload == "differentiable":
         run_reference_differentiable(args)
+        return
+    if args.workload == "strips":
+        run_reference_strips(args)
         return
     L, d = make_workload(args.workload)
     E = L.E
@@ -820,6 +991,7 @@ def main():
     ap.add_argument("--cell-log2", type=int, default=0)
     ap.add_argument("--long-pairs", choices=sorted(LONG_PAIRS), default="auto",
                     help="where pairs of two long segments are tested (default: the cost model decides)")
+    ap.add_argument("--strip-width", type=int, default=STRIP_WIDTH, help="strips workload: strip width")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (for profiler runs)")
@@ -842,6 +1014,8 @@ def main():
             run_differentiable(args, rank, world, local_rank)
         elif args.workload == "moves":
             run_moves(args, rank, world, local_rank)
+        elif args.workload == "strips":
+            run_strips(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

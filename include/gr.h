@@ -181,6 +181,33 @@ gr_status gr_edge_crossings(gr_layout *layout, gr_crossing_counts *out);
  * `ideal_rad` in (0, pi/2]; <= 0 selects 70 deg = 7 pi / 18. */
 gr_status gr_crossing_angle(gr_layout *layout, double ideal_rad, gr_crossing_angle_result *out);
 
+/* The paper's approximate crossing count and crossing angle (Sec. 3.2.2 and
+ * Sec. 3.2.3 with Eq. 1), for comparison with the exact metrics.  The plane
+ * is cut by the lines x = s * strip_width (GR_STRIP_VERTICAL) or
+ * y = s * strip_width (GR_STRIP_HORIZONTAL); two segments that both cross
+ * both lines of a strip count as crossing when their order along the lines
+ * reverses strictly from one line to the other (y at a line compared as the
+ * exact key floor(y * 2^30)).  Pairs whose crossing lies in a strip that
+ * one of them does not span are missed, so the count never exceeds E_c.
+ * angle_dev_sum and E_ca are Algorithm 5's sum and metric over the counted
+ * pairs.  GR_STRIP_BOTH runs both orientations and reports the one with the
+ * larger count.  strip_width in [1, 65535], ideal_rad in (0, pi/2] (<= 0:
+ * 70 deg).  GR_COORD_I32 layouts only (GR_ENOTSUP otherwise); synchronises;
+ * result on the host. */
+enum { GR_STRIP_VERTICAL = 0, GR_STRIP_HORIZONTAL = 1, GR_STRIP_BOTH = 2 };
+typedef struct {
+    int64_t crossings;     /* pairs counted (the E_c estimate) */
+    int64_t records;       /* (segment, strip) records of the reported orientation */
+    int64_t strips;        /* strips of width strip_width covering [0, 65536) */
+    double angle_dev_sum;  /* sum of |ideal - a_c| over the counted pairs, radians */
+    double ideal_rad;
+    double E_ca;           /* 1 - angle_dev_sum / (ideal_rad * crossings); 1 when crossings = 0 */
+    int32_t orientation;   /* the orientation reported */
+    int32_t strip_width;
+} gr_strip_result;
+gr_status gr_strip_crossings(gr_layout *layout, int32_t strip_width, int32_t orientation, double ideal_rad,
+                             gr_strip_result *out);
+
 /* Per-edge crossing data (the per-segment quantity of Sec. 3.2.3 / Eq. 1,
  * computed exactly): for every edge e, the number of proper crossings,
  * touching pairs and collinear overlaps it takes part in, and the sum of
@@ -282,6 +309,8 @@ typedef enum {
     GR_PHASE_CROSS_PAIRS,    /* a6 per-cell pair kernel, or a7 all-pairs tiles */
     GR_PHASE_FINALIZE,       /* a11 and the result copy */
     GR_PHASE_DIFF_BACKWARD,  /* gr_diff_backward: the three adjoint kernels */
+    GR_PHASE_STRIP_SORT,     /* gr_strip_crossings: records emitted and sorted by (l, r) in each strip */
+    GR_PHASE_STRIP_COUNT,    /* gr_strip_crossings: merge by r, inverted pairs and their angle terms */
     GR_NUM_PHASES
 } gr_phase;
 

@@ -113,6 +113,7 @@ struct gr_layout {
     // 2^dgrid_k); edges moved since then are in the dirty set.
     int dgrid_k = -1;
     DirtySet dirty;
+    StripBuffers strip;             // the approximate strip algorithm's workspace
     bool dirty_any = false;         // the dirty set may be non-empty
     int64_t io_h2d = 0, io_d2h = 0; // bytes copied between host and device
     // phase timing
@@ -147,6 +148,13 @@ void free_layout(gr_layout *L) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_grid(L->g);
+    {
+        StripBuffers &sb = L->strip;
+        void *sp[] = {sb.mark_start, sb.mark_end, sb.strip_off, sb.tile_off, sb.fill, sb.k1[0], sb.k1[1],
+                      sb.rk[0], sb.rk[1], sb.th[0], sb.th[1], sb.acc};
+        for (void *p : sp)
+            if (p) cudaFree(p);
+    }
     for (auto &e : L->ev)
         if (e) cudaEventDestroy(e);
     if (L->ev_fork) cudaEventDestroy(L->ev_fork);
@@ -820,6 +828,105 @@ gr_status gr_crossing_angle(gr_layout *L, double ideal_rad, gr_crossing_angle_re
     gr_status st = gr_evaluate(L, GR_METRIC_CROSSINGS, &p, &r);
     if (st == GR_OK) *out = r.crossing;
     return st;
+}
+
+namespace {
+
+// One orientation of the strip estimate into out (synchronises twice: the
+// record count sizes the buffers).
+gr_status strip_one(gr_layout *L, int l, int orient, double ideal, gr_strip_result *out) {
+    cudaStream_t s = L->stream;
+    StripBuffers &sb = L->strip;
+    const int ns = strip_count(l);
+    gr_status st;
+    if (sb.ns_cap < ns + 1) {
+        uint32_t **arr[] = {&sb.mark_start, &sb.mark_end, &sb.strip_off, &sb.tile_off, &sb.fill};
+        for (uint32_t **a : arr) {
+            if (*a) cudaFree(*a);
+            *a = nullptr;
+        }
+        sb.ns_cap = 0;
+        for (uint32_t **a : arr)
+            if ((st = dalloc(a, (size_t)ns + 1)) != GR_OK) return st;
+        sb.ns_cap = ns + 1;
+    }
+    if (!sb.acc && (st = dalloc(&sb.acc, 1)) != GR_OK) return st;
+    const size_t nb = sizeof(uint32_t) * ((size_t)ns + 1);
+    GR_CU(cudaMemsetAsync(sb.mark_start, 0, nb, s));
+    GR_CU(cudaMemsetAsync(sb.mark_end, 0, nb, s));
+    GR_CU(cudaMemsetAsync(sb.fill, 0, nb, s));
+    GR_CU(cudaMemsetAsync(sb.acc, 0, sizeof(StripAcc), s));
+    launch_strip_span(L->b, L->E, l, orient, sb, s);
+    GR_CU(cudaGetLastError());
+    StripAcc h;
+    GR_CU(cudaMemcpyAsync(&h, sb.acc, sizeof h, cudaMemcpyDeviceToHost, s));
+    GR_CU(cudaStreamSynchronize(s));
+    if (h.status) return status_to_error(h.status);
+    if (h.records > sb.cap) {
+        for (int i = 0; i < 2; ++i) {
+            if (sb.k1[i]) cudaFree(sb.k1[i]);
+            if (sb.rk[i]) cudaFree(sb.rk[i]);
+            if (sb.th[i]) cudaFree(sb.th[i]);
+            sb.k1[i] = sb.rk[i] = nullptr;
+            sb.th[i] = nullptr;
+        }
+        sb.cap = 0;
+        const size_t want = (size_t)h.records;
+        for (int i = 0; i < 2; ++i) {
+            if ((st = dalloc(&sb.k1[i], want)) != GR_OK) return st;
+            if ((st = dalloc(&sb.rk[i], want)) != GR_OK) return st;
+            if ((st = dalloc(&sb.th[i], want)) != GR_OK) return st;
+        }
+        sb.cap = h.records;
+    }
+    sb.records = h.records;
+    sb.tiles = h.tiles;
+    phase_begin(L, GR_PHASE_STRIP_SORT);
+    launch_strip_sort(L->b, L->E, l, orient, sb, h.max_n, s);
+    phase_end(L, GR_PHASE_STRIP_SORT);
+    phase_begin(L, GR_PHASE_STRIP_COUNT);
+    launch_strip_inversions(l, sb, h.max_n, ideal_units(ideal), s);
+    phase_end(L, GR_PHASE_STRIP_COUNT);
+    GR_CU(cudaGetLastError());
+    GR_CU(cudaMemcpyAsync(&h, sb.acc, sizeof h, cudaMemcpyDeviceToHost, s));
+    GR_CU(cudaStreamSynchronize(s));
+    phase_collect(L);
+    L->io_d2h += (int64_t)(2 * sizeof h);
+    if (h.status) return status_to_error(h.status);
+    const double dev = ((double)h.dev_hi * 18446744073709551616.0 + (double)h.dev_lo) * kAngleUnit;
+    out->crossings = (int64_t)h.count;
+    out->records = (int64_t)h.records;
+    out->strips = ns;
+    out->angle_dev_sum = dev;
+    out->ideal_rad = ideal;
+    out->E_ca = h.count > 0 ? 1.0 - dev / (ideal * (double)h.count) : 1.0;
+    out->orientation = orient;
+    out->strip_width = l;
+    return GR_OK;
+}
+
+}  // namespace
+
+gr_status gr_strip_crossings(gr_layout *L, int32_t strip_width, int32_t orientation, double ideal_rad,
+                             gr_strip_result *out) {
+    g_err.clear();
+    if (!L || !out) return fail(GR_EINVAL, "NULL argument");
+    if (L->coord != GR_COORD_I32) return fail(GR_ENOTSUP, "the strip estimate needs GR_COORD_I32 coordinates");
+    if (strip_width < 1 || strip_width > 65535) return fail(GR_EINVAL, "strip width must be in [1, 65535]");
+    if (orientation < GR_STRIP_VERTICAL || orientation > GR_STRIP_BOTH) return fail(GR_EINVAL, "bad orientation");
+    gr_params p{ideal_rad, 0};
+    double ideal;
+    int64_t d;
+    gr_status st = read_params(&p, &ideal, &d);
+    if (st != GR_OK) return st;
+    if ((st = refresh_stats(L)) != GR_OK) return st;
+    if ((st = status_to_error(L->h_acc->status)) != GR_OK) return st;
+    gr_strip_result r[2];
+    const int o0 = orientation == GR_STRIP_HORIZONTAL ? 1 : 0, o1 = orientation == GR_STRIP_VERTICAL ? 0 : 1;
+    for (int o = o0; o <= o1; ++o)
+        if ((st = strip_one(L, strip_width, o, ideal, &r[o])) != GR_OK) return st;
+    *out = (o0 != o1 && r[1].crossings > r[0].crossings) ? r[1] : r[o0];
+    return GR_OK;
 }
 
 gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_counts, double *d_dev) {

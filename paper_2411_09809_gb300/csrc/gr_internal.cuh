@@ -250,6 +250,42 @@ void launch_finalize(const Buffers &b, uint32_t metrics, int64_t E, double ideal
 // Per-edge output conversion: integer dev sums to radians (double), in place.
 void launch_per_edge_export(uint64_t *dev_fixed, int64_t E, cudaStream_t s);
 
+// ---------------------------------------------- approximate strip algorithm
+struct StripAcc {
+    uint64_t records;       // (segment, strip) records
+    uint64_t count;         // inverted pairs (the E_c estimate)
+    uint64_t dev_lo, dev_hi;// 128-bit sum of their angle terms, units of pi / 2^32
+    uint32_t tiles;         // shared-memory tiles over all strips
+    uint32_t max_n;         // records of the largest strip
+    uint32_t status;        // ST_* bits
+    uint32_t pad_;
+};
+struct StripBuffers {
+    uint32_t *mark_start = nullptr, *mark_end = nullptr;  // [ns + 1] segments starting / past their last strip
+    uint32_t *strip_off = nullptr, *tile_off = nullptr;   // [ns + 1]
+    uint32_t *fill = nullptr;                             // [ns + 1]
+    int ns_cap = 0;
+    uint64_t *k1[2] = {nullptr, nullptr};  // strip << 46 | key at the left line
+    uint64_t *rk[2] = {nullptr, nullptr};  // key at the right line
+    uint32_t *th[2] = {nullptr, nullptr};  // line direction
+    uint64_t cap = 0;
+    StripAcc *acc = nullptr;
+    uint64_t records = 0;  // host copies for the launches
+    uint32_t tiles = 0;
+    int cur = 0;           // which of the two record arrays holds the current order
+};
+int strip_count(int l);  // strips of width l covering [0, 65536): the span marks need strip_count + 1
+// Marks the strips each segment spans and lays out the strips (offsets,
+// tiles, records, largest strip into sb.acc).
+void launch_strip_span(const Buffers &b, int64_t E, int l, int orient, const StripBuffers &sb, cudaStream_t s);
+// Emits the records (sb.records of them, sb.cap >= that) and sorts each strip
+// by (l, r) (max_n: records of the largest strip); sb.cur names the result.
+void launch_strip_sort(const Buffers &b, int64_t E, int l, int orient, StripBuffers &sb, uint32_t max_n,
+                       cudaStream_t s);
+// Merge sort by r within each strip, counting the inverted pairs and their
+// angle terms into sb.acc.
+void launch_strip_inversions(int l, StripBuffers &sb, uint32_t max_n, uint32_t ideal, cudaStream_t s);
+
 // ------------------------------------------------------ incremental moves
 // Tallies of the pairs that involve moved vertices, before (k[0]) and after
 // (k[1]) the move.

@@ -63,8 +63,17 @@ class gr_result(ctypes.Structure):
                 ("min_angle", gr_min_angle_result), ("M_l", c_double), ("grid_records", c_int64)]
 
 
+GR_STRIP_VERTICAL, GR_STRIP_HORIZONTAL, GR_STRIP_BOTH = 0, 1, 2
+
+
+class gr_strip_result(ctypes.Structure):
+    _fields_ = [("crossings", c_int64), ("records", c_int64), ("strips", c_int64),
+                ("angle_dev_sum", c_double), ("ideal_rad", c_double), ("E_ca", c_double),
+                ("orientation", c_int32), ("strip_width", c_int32)]
+
+
 GR_PHASE_NAMES = ["gather", "edge_length", "min_angle", "occl_bin", "occl_pairs", "cross_bin",
-                  "cross_scatter", "cross_pairs", "finalize", "diff_backward"]
+                  "cross_scatter", "cross_pairs", "finalize", "diff_backward", "strip_sort", "strip_count"]
 
 
 class gr_profile(ctypes.Structure):
@@ -115,6 +124,7 @@ def load() -> ctypes.CDLL:
         "gr_batch_destroy": ([P], c_int32),
         "gr_move_vertices": ([P, c_int64, P, P, c_uint32, ctypes.POINTER(gr_params), ctypes.POINTER(gr_result)],
                              c_int32),
+        "gr_strip_crossings": ([P, c_int32, c_int32, c_double, ctypes.POINTER(gr_strip_result)], c_int32),
         "gr_diff_forward": ([P, c_double, P], c_int32),
         "gr_diff_backward": ([P, P, P], c_int32),
         "gr_last_error": ([], ctypes.c_char_p),
@@ -272,6 +282,15 @@ def gr_crossing_angle(layout, ideal_rad: float = 0.0) -> gr_crossing_angle_resul
     return out
 
 
+def gr_strip_crossings(layout, strip_width: int, orientation: int = GR_STRIP_VERTICAL,
+                       ideal_rad: float = 0.0) -> gr_strip_result:
+    """The paper's approximate strip estimates of E_c and E_ca (Sec. 3.2.2-3.2.3)."""
+    out = gr_strip_result()
+    _check(load().gr_strip_crossings(layout, int(strip_width), int(orientation), float(ideal_rad),
+                                     ctypes.byref(out)))
+    return out
+
+
 def gr_crossings_per_edge(layout, ideal_rad: float, d_counts, d_dev) -> None:
     """d_counts: CUDA int64 tensor [E, 3]; d_dev: CUDA float64 tensor [E] (overwritten)."""
     cp, ck = _buffer(d_counts, "int64")
@@ -413,6 +432,10 @@ class Layout:
     def move(self, ids, xy_new, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
              occlusion_d: int = 0) -> gr_result:
         return gr_move_vertices(self.handle, ids, xy_new, metrics, ideal_rad, occlusion_d)
+
+    def strips(self, strip_width: int, orientation: int = GR_STRIP_VERTICAL,
+               ideal_rad: float = 0.0) -> gr_strip_result:
+        return gr_strip_crossings(self.handle, strip_width, orientation, ideal_rad)
 
     def profile(self, reset: bool = False) -> dict:
         return gr_profile_read(self.handle, reset).as_dict()
