@@ -31,7 +31,8 @@ namespace gr {
 namespace {
 
 constexpr int ST_THREADS = 256;
-constexpr int ST_TILE = 2048;  // records per shared-memory tile
+constexpr int ST_TILE = 2048;          // records per shared-memory tile
+constexpr int ST_TILE_THREADS = 512;   // threads of the tile kernel (two blocks per SM)
 constexpr int ST_KEY_SHIFT = 30;
 constexpr int ST_STRIP_SHIFT = 46;  // k1 = strip << 46 | l key (keys < 2^46)
 
@@ -54,12 +55,30 @@ __device__ __forceinline__ StripSeg strip_seg(SegRec r, int orient) {
     return StripSeg{ax, ay, bx, by};
 }
 
-// floor(y(X) * 2^30), x0 < x1, x0 <= X <= x1: y(X) dx = y0 dx + (X - x0) dy is
-// an integer in [0, 2^32), so the key is exact.
-__device__ __forceinline__ uint64_t strip_key(const StripSeg &s, int X) {
-    const long long dx = s.x1 - s.x0, dy = s.y1 - s.y0;
-    const long long num = (long long)s.y0 * dx + (long long)(X - s.x0) * dy;
-    return ((uint64_t)num << ST_KEY_SHIFT) / (uint64_t)dx;
+// floor(y(X) * 2^30), x0 < x1, x0 <= X <= x1: num = y(X) dx = y0 dx + (X - x0)
+// dy is an integer in [0, 2^32), so the key floor(num 2^30 / dx) is exact.
+// Without a 64-bit division per record: with inv = floor(2^47 / dx) (one
+// division per segment), num = q dx + r and r < dx < 2^16,
+// floor(r 2^30 / dx) is floor(r 2^30 inv / 2^47) or one more (the estimate
+// is low by less than r / 2^17 < 1), settled by one exact comparison.
+struct KeyDiv {
+    uint32_t dx;
+    uint64_t inv;
+};
+
+__device__ __forceinline__ KeyDiv key_div(const StripSeg &s) {
+    const uint32_t dx = (uint32_t)(s.x1 - s.x0);
+    return KeyDiv{dx, (1ull << 47) / dx};
+}
+
+__device__ __forceinline__ uint64_t strip_key_fast(const StripSeg &s, const KeyDiv &kd, int X) {
+    const long long dy = s.y1 - s.y0;
+    const uint32_t num = (uint32_t)((long long)s.y0 * kd.dx + (long long)(X - s.x0) * dy);
+    const uint32_t q = num / kd.dx, r = num - q * kd.dx;
+    const uint64_t rs = (uint64_t)r << ST_KEY_SHIFT;
+    uint64_t t = __umul64hi(rs, kd.inv << 17);
+    if ((t + 1) * kd.dx <= rs) ++t;
+    return ((uint64_t)q << ST_KEY_SHIFT) + t;
 }
 
 // Strips [s0, s1] whose two lines lie within the segment's x range (none when
@@ -172,6 +191,11 @@ __global__ void __launch_bounds__(1024) k_strip_layout(const uint32_t *__restric
     if ((threadIdx.x & 31) == 0) atomicMax(&sacc->max_n, mx);
 }
 
+// The records of the segments: a warp walks the union of its 32 segments'
+// strip ranges in order, so that for each strip one atomic reserves the
+// slots of all its lanes that span it and their records are stored side by
+// side; the key at a line is computed once and serves as the right key of one
+// strip and the left key of the next.
 __global__ void __launch_bounds__(ST_THREADS) k_strip_emit(const SegRec *__restrict__ seg,
                                                            const uint32_t *__restrict__ seg_theta,
                                                            const DevAcc *__restrict__ acc, int l, int orient,
@@ -180,20 +204,42 @@ __global__ void __launch_bounds__(ST_THREADS) k_strip_emit(const SegRec *__restr
                                                            uint64_t *__restrict__ k1, uint64_t *__restrict__ rk,
                                                            uint32_t *__restrict__ th, StripAcc *sacc) {
     const int64_t n = acc->n_seg;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const StripSeg s = strip_seg(seg[i], orient);
-        int s0, s1;
-        strip_range(s, l, s0, s1);
-        const uint32_t t = seg_theta[i];
-        for (int q = s0; q <= s1; ++q) {
-            const uint64_t pos = (uint64_t)strip_off[q] + atomicAdd(&fill[q], 1u);
-            if (pos >= cap) {  // sized from the same count; never expected
+    const int lane = threadIdx.x & 31;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        StripSeg s{0, 0, 0, 0};
+        int s0 = 1, s1 = 0;
+        uint32_t t = 0;
+        if (i < n) {
+            s = strip_seg(seg[i], orient);
+            strip_range(s, l, s0, s1);
+            t = seg_theta[i];
+        }
+        const bool any = s1 >= s0;
+        const KeyDiv kd = any ? key_div(s) : KeyDiv{1u, 0ull};
+        const int lo = __reduce_min_sync(0xffffffffu, any ? s0 : 0x7fffffff);
+        const int hi = __reduce_max_sync(0xffffffffu, any ? s1 : -1);
+        uint64_t kl = any ? strip_key_fast(s, kd, s0 * l) : 0ull;
+        for (int q = lo; q <= hi; ++q) {
+            const bool act = s0 <= q && q <= s1;
+            const unsigned m = __ballot_sync(0xffffffffu, act);
+            if (!m) continue;
+            uint32_t slot = 0;
+            if (lane == __ffs(m) - 1) slot = atomicAdd(&fill[q], (uint32_t)__popc(m));
+            slot = __shfl_sync(0xffffffffu, slot, __ffs(m) - 1);
+            if (!act) continue;
+            const uint64_t kr = strip_key_fast(s, kd, (q + 1) * l);
+            const uint64_t pos = (uint64_t)strip_off[q] + slot + __popc(m & lt);
+            if (pos < cap) {
+                k1[pos] = ((uint64_t)q << ST_STRIP_SHIFT) | kl;
+                rk[pos] = kr;
+                th[pos] = t;
+            } else {  // sized from the same count; never expected
                 atomicOr(&sacc->status, ST_OVERFLOW);
-                continue;
             }
-            k1[pos] = ((uint64_t)q << ST_STRIP_SHIFT) | strip_key(s, q * l);
-            rk[pos] = strip_key(s, (q + 1) * l);
-            th[pos] = t;
+            kl = kr;
         }
     }
 }
@@ -223,6 +269,19 @@ __device__ __forceinline__ uint32_t sibling_rank(uint64_t xk1, uint64_t xrk, boo
     return lo;
 }
 
+// Sum of |ideal - angle| of direction xt against directions y[0, n) (shared
+// memory), four at a time with two accumulators.
+__device__ __forceinline__ uint64_t dev_sum(uint32_t xt, const uint32_t *y, uint32_t n, uint32_t ideal) {
+    uint64_t a0 = 0, a1 = 0;
+    uint32_t m = 0;
+    for (; m + 4 <= n; m += 4) {
+        a0 += (uint64_t)dev_term(xt, y[m], ideal) + dev_term(xt, y[m + 1], ideal);
+        a1 += (uint64_t)dev_term(xt, y[m + 2], ideal) + dev_term(xt, y[m + 3], ideal);
+    }
+    for (; m < n; ++m) a0 += dev_term(xt, y[m], ideal);
+    return a0 + a1;
+}
+
 struct StripTotals {
     uint64_t count = 0, dev = 0;
 };
@@ -240,7 +299,7 @@ __device__ __forceinline__ void flush_strip_totals(const StripTotals &t, StripAc
 // memory from runs of 1 (INV: by r, counting and summing the inverted pairs;
 // else by (l, r)).
 template <bool INV>
-__global__ void __launch_bounds__(ST_THREADS) k_strip_tile(const uint64_t *__restrict__ k1_in,
+__global__ void __launch_bounds__(ST_TILE_THREADS) k_strip_tile(const uint64_t *__restrict__ k1_in,
                                                            const uint64_t *__restrict__ rk_in,
                                                            const uint32_t *__restrict__ th_in,
                                                            uint64_t *__restrict__ k1_out,
@@ -268,7 +327,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_strip_tile(const uint64_t *__res
         const uint32_t start = strip_off[lo] + (t - tile_off[lo]) * ST_TILE;
         const uint32_t n = min((uint32_t)ST_TILE, strip_off[lo + 1] - start);
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < n; i += ST_THREADS) {
+        for (uint32_t i = threadIdx.x; i < n; i += ST_TILE_THREADS) {
             ak1[i] = k1_in[start + i];
             ark[i] = rk_in[start + i];
             ath[i] = th_in[start + i];
@@ -277,7 +336,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_strip_tile(const uint64_t *__res
         uint64_t *sk1 = ak1, *srk = ark, *dk1 = bk1, *drk = brk;
         uint32_t *sth = ath, *dth = bth;
         for (uint32_t w = 1; w < n; w <<= 1) {
-            for (uint32_t i = threadIdx.x; i < n; i += ST_THREADS) {
+            for (uint32_t i = threadIdx.x; i < n; i += ST_TILE_THREADS) {
                 const uint32_t run = i / w, rb = run * w, sib = run ^ 1u, sb = sib * w;
                 const uint32_t sn = sb < n ? min(w, n - sb) : 0u;
                 const bool left = (run & 1u) == 0u;
@@ -292,8 +351,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_strip_tile(const uint64_t *__res
                 dth[pos] = sth[i];
                 if (INV && !left) {  // left-run elements with a greater r: inverted pairs
                     tot.count += sn - rank;
-                    const uint32_t xt = sth[i];
-                    for (uint32_t m = rank; m < sn; ++m) tot.dev += dev_term(xt, sth[sb + m], ideal);
+                    tot.dev += dev_sum(sth[i], sth + sb + rank, sn - rank, ideal);
                 }
             }
             __syncthreads();
@@ -301,7 +359,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_strip_tile(const uint64_t *__res
             t1 = srk; srk = drk; drk = t1;
             uint32_t *t2 = sth; sth = dth; dth = t2;
         }
-        for (uint32_t i = threadIdx.x; i < n; i += ST_THREADS) {
+        for (uint32_t i = threadIdx.x; i < n; i += ST_TILE_THREADS) {
             k1_out[start + i] = sk1[i];
             rk_out[start + i] = srk[i];
             th_out[start + i] = sth[i];
@@ -310,41 +368,122 @@ __global__ void __launch_bounds__(ST_THREADS) k_strip_tile(const uint64_t *__res
     if (INV) flush_strip_totals(tot, sacc, shu);
 }
 
-// One global merge level: runs of w records (w >= ST_TILE) within each strip
-// merged pairwise, one thread per record (binary search in the sibling run).
+// One global merge level: within each strip, runs of w records (w >= ST_TILE,
+// a multiple of it) merged pairwise.  The output of a strip is cut into
+// chunks of ST_TILE records (the tiles of the strip; a pair of runs covers
+// whole chunks); each block takes a chunk, finds by one binary search along
+// its diagonals how many of its outputs come from the left run (merge path),
+// loads both input slices into shared memory (coalesced), places every
+// element by a binary search in the other slice and stores the chunk
+// (coalesced).  INV: a right-run element x is preceded by the left-run
+// elements with a greater r: those of the chunk's left slice past x's place,
+// and every left-run element after the slice (all of them follow the whole
+// chunk, so their r is greater than any of its right-run elements) -- the
+// latter are streamed through shared memory in batches against all of the
+// chunk's right-run elements.
 template <bool INV>
-__global__ void __launch_bounds__(ST_THREADS) k_strip_level(const uint64_t *__restrict__ k1_in,
-                                                            const uint64_t *__restrict__ rk_in,
-                                                            const uint32_t *__restrict__ th_in,
-                                                            uint64_t *__restrict__ k1_out,
-                                                            uint64_t *__restrict__ rk_out,
-                                                            uint32_t *__restrict__ th_out,
-                                                            const uint32_t *__restrict__ strip_off, uint64_t R,
-                                                            uint32_t w, uint32_t ideal, StripAcc *sacc) {
+__global__ void __launch_bounds__(ST_TILE_THREADS) k_strip_merge(const uint64_t *__restrict__ k1_in,
+                                                                 const uint64_t *__restrict__ rk_in,
+                                                                 const uint32_t *__restrict__ th_in,
+                                                                 uint64_t *__restrict__ k1_out,
+                                                                 uint64_t *__restrict__ rk_out,
+                                                                 uint32_t *__restrict__ th_out,
+                                                                 const uint32_t *__restrict__ strip_off,
+                                                                 const uint32_t *__restrict__ tile_off, int ns,
+                                                                 uint32_t w, uint32_t ideal, StripAcc *sacc) {
+    extern __shared__ __align__(16) unsigned char st_smem[];
+    uint64_t *ck1 = (uint64_t *)st_smem;   // chunk inputs: left slice, then right slice
+    uint64_t *crk = ck1 + ST_TILE;
+    uint64_t *ok1 = crk + ST_TILE;         // chunk outputs
+    uint64_t *ork = ok1 + ST_TILE;
+    uint32_t *cth = (uint32_t *)(ork + ST_TILE);
+    uint32_t *oth = cth + ST_TILE;
+    __shared__ uint32_t split[2];
     __shared__ uint64_t shu[32];
     StripTotals tot;
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < R; p += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t xk1 = k1_in[p], xrk = rk_in[p];
-        const uint32_t xt = th_in[p];
-        const uint32_t s = (uint32_t)(xk1 >> ST_STRIP_SHIFT);
-        const uint32_t s0 = strip_off[s], n = strip_off[s + 1] - s0;
-        const uint32_t i = (uint32_t)(p - s0);
-        const uint32_t run = i / w, rb = run * w, sib = run ^ 1u, sb = sib * w;
-        const uint32_t sn = sb < n ? min(w, n - sb) : 0u;
-        const bool left = (run & 1u) == 0u;
-        const uint64_t *sk1 = k1_in + s0 + sb, *srk = rk_in + s0 + sb;
-        const uint32_t rank = sibling_rank<INV>(xk1, xrk, left, sn, [&](uint32_t m, uint64_t &k1, uint64_t &rk) {
-            k1 = INV ? 0ull : sk1[m];
-            rk = srk[m];
-        });
-        const uint64_t pos = (uint64_t)s0 + (run & ~1u) * w + (i - rb) + rank;
-        k1_out[pos] = xk1;
-        rk_out[pos] = xrk;
-        th_out[pos] = xt;
-        if (INV && !left) {
-            tot.count += sn - rank;
-            const uint32_t *sth = th_in + s0 + sb;
-            for (uint32_t m = rank; m < sn; ++m) tot.dev += dev_term(xt, sth[m], ideal);
+    const uint32_t tiles = sacc->tiles;
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        int lo_s = 0, hi_s = ns;
+        while (hi_s - lo_s > 1) {
+            const int mid = (lo_s + hi_s) >> 1;
+            if (tile_off[mid] <= t) lo_s = mid; else hi_s = mid;
+        }
+        const uint32_t S0 = strip_off[lo_s], n = strip_off[lo_s + 1] - S0;
+        const uint32_t o0 = (t - tile_off[lo_s]) * ST_TILE, o1 = min(o0 + ST_TILE, n);
+        const uint32_t p0 = o0 / (2 * w) * (2 * w);
+        const uint32_t la = min(w, n - p0), lb = n > p0 + w ? min(w, n - p0 - w) : 0u;
+        const uint64_t *ak1 = k1_in + S0 + p0, *ark = rk_in + S0 + p0;
+        const uint64_t *bk1 = ak1 + w, *brk = ark + w;
+        const uint32_t *ath = th_in + S0 + p0, *bth = ath + w;
+        if (lb == 0) {  // no right run: the chunk keeps its place
+            for (uint32_t i = o0 + threadIdx.x; i < o1; i += ST_TILE_THREADS) {
+                k1_out[S0 + i] = k1_in[S0 + i];
+                rk_out[S0 + i] = rk_in[S0 + i];
+                th_out[S0 + i] = th_in[S0 + i];
+            }
+            continue;
+        }
+        __syncthreads();  // the previous chunk is done with the shared arrays
+        if (threadIdx.x < 2) {  // merge path: left-run elements among the first k outputs of the pair
+            const uint32_t k = (threadIdx.x == 0 ? o0 : o1) - p0;
+            uint32_t lo = k > lb ? k - lb : 0u, hi = min(k, la);
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                const uint32_t j = k - mid - 1;
+                // left[mid] goes first unless right[j] is smaller
+                if (!key_less<INV>(bk1[j], brk[j], ak1[mid], ark[mid])) lo = mid + 1; else hi = mid;
+            }
+            split[threadIdx.x] = lo;
+        }
+        __syncthreads();
+        const uint32_t i0 = split[0], i1 = split[1];
+        const uint32_t j0 = (o0 - p0) - i0, j1 = (o1 - p0) - i1;
+        const uint32_t na = i1 - i0, nb = j1 - j0;
+        for (uint32_t e = threadIdx.x; e < na + nb; e += ST_TILE_THREADS) {
+            if (e < na) {
+                ck1[e] = INV ? 0ull : ak1[i0 + e];
+                crk[e] = ark[i0 + e];
+                cth[e] = ath[i0 + e];
+            } else {
+                ck1[e] = INV ? 0ull : bk1[j0 + e - na];
+                crk[e] = brk[j0 + e - na];
+                cth[e] = bth[j0 + e - na];
+            }
+        }
+        __syncthreads();
+        for (uint32_t e = threadIdx.x; e < na + nb; e += ST_TILE_THREADS) {
+            const bool left = e < na;
+            const uint64_t xk1 = ck1[e], xrk = crk[e];
+            const uint32_t sb = left ? na : 0u, sn = left ? nb : na;
+            const uint32_t rank = sibling_rank<INV>(xk1, xrk, left, sn, [&](uint32_t m, uint64_t &k1, uint64_t &rk) {
+                k1 = ck1[sb + m];
+                rk = crk[sb + m];
+            });
+            const uint32_t pos = (left ? e : e - na) + rank;
+            ok1[pos] = xk1;
+            ork[pos] = xrk;
+            oth[pos] = cth[e];
+            if (INV && !left) {
+                tot.count += la - i0 - rank;  // left elements with a greater r, in the slice and after it
+                tot.dev += dev_sum(cth[e], cth + rank, na - rank, ideal);
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < na + nb; i += ST_TILE_THREADS) {
+            if (!INV) k1_out[S0 + o0 + i] = ok1[i];  // (the r merge needs no l key)
+            rk_out[S0 + o0 + i] = ork[i];
+            th_out[S0 + o0 + i] = oth[i];
+        }
+        if (INV && i1 < la) {
+            // left-run elements after the slice, in batches (oth is free now), against the right slice
+            for (uint32_t g0 = i1; g0 < la; g0 += ST_TILE) {
+                const uint32_t gn = min((uint32_t)ST_TILE, la - g0);
+                __syncthreads();
+                for (uint32_t i = threadIdx.x; i < gn; i += ST_TILE_THREADS) oth[i] = ath[g0 + i];
+                __syncthreads();
+                for (uint32_t e = na + threadIdx.x; e < na + nb; e += ST_TILE_THREADS)
+                    tot.dev += dev_sum(cth[e], oth, gn, ideal);
+            }
         }
     }
     if (INV) flush_strip_totals(tot, sacc, shu);
@@ -357,7 +496,7 @@ int grid_for(int64_t n, int threads, int max_blocks) {
     return (int)b;
 }
 
-constexpr size_t kTileSmem = (size_t)ST_TILE * (8 + 8 + 8 + 8 + 4 + 4);
+constexpr size_t kTileSmem = (size_t)ST_TILE * (8 + 8 + 8 + 8 + 4 + 4);  // tile and merge kernels alike
 
 }  // namespace
 
@@ -378,6 +517,8 @@ void launch_strip_sort(const Buffers &b, int64_t E, int l, int orient, StripBuff
     if (!attr_set) {
         cudaFuncSetAttribute(k_strip_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
         cudaFuncSetAttribute(k_strip_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+        cudaFuncSetAttribute(k_strip_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+        cudaFuncSetAttribute(k_strip_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
         attr_set = true;
     }
     const int ns = strip_count(l);
@@ -389,18 +530,17 @@ void launch_strip_sort(const Buffers &b, int64_t E, int l, int orient, StripBuff
                                                                         sb.rk[0], sb.th[0], sb.acc);
     if (R == 0) return;
     const int tb = grid_for((int64_t)sb.tiles, 1, 152 * 2);
-    const int gb = grid_for((int64_t)R, ST_THREADS, 152 * 16);
     int cur = 0;
     count_launches(1);
-    k_strip_tile<false><<<tb, ST_THREADS, kTileSmem, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur], sb.k1[cur ^ 1],
+    k_strip_tile<false><<<tb, ST_TILE_THREADS, kTileSmem, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur], sb.k1[cur ^ 1],
                                                           sb.rk[cur ^ 1], sb.th[cur ^ 1], sb.strip_off, sb.tile_off,
                                                           ns, 0u, sb.acc);
     cur ^= 1;
     for (uint32_t w = ST_TILE; w < max_n; w <<= 1) {
         count_launches(1);
-        k_strip_level<false><<<gb, ST_THREADS, 0, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur], sb.k1[cur ^ 1],
-                                                       sb.rk[cur ^ 1], sb.th[cur ^ 1], sb.strip_off, R, w, 0u,
-                                                       sb.acc);
+        k_strip_merge<false><<<tb, ST_TILE_THREADS, kTileSmem, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur],
+                                                                    sb.k1[cur ^ 1], sb.rk[cur ^ 1], sb.th[cur ^ 1],
+                                                                    sb.strip_off, sb.tile_off, ns, w, 0u, sb.acc);
         cur ^= 1;
     }
     sb.cur = cur;
@@ -411,18 +551,17 @@ void launch_strip_inversions(int l, StripBuffers &sb, uint32_t max_n, uint32_t i
     if (R == 0) return;
     const int ns = strip_count(l);
     const int tb = grid_for((int64_t)sb.tiles, 1, 152 * 2);
-    const int gb = grid_for((int64_t)R, ST_THREADS, 152 * 16);
     int cur = sb.cur;
     count_launches(1);
-    k_strip_tile<true><<<tb, ST_THREADS, kTileSmem, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur], sb.k1[cur ^ 1],
+    k_strip_tile<true><<<tb, ST_TILE_THREADS, kTileSmem, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur], sb.k1[cur ^ 1],
                                                          sb.rk[cur ^ 1], sb.th[cur ^ 1], sb.strip_off, sb.tile_off,
                                                          ns, ideal, sb.acc);
     cur ^= 1;
     for (uint32_t w = ST_TILE; w < max_n; w <<= 1) {
         count_launches(1);
-        k_strip_level<true><<<gb, ST_THREADS, 0, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur], sb.k1[cur ^ 1],
-                                                      sb.rk[cur ^ 1], sb.th[cur ^ 1], sb.strip_off, R, w, ideal,
-                                                      sb.acc);
+        k_strip_merge<true><<<tb, ST_TILE_THREADS, kTileSmem, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur],
+                                                                   sb.k1[cur ^ 1], sb.rk[cur ^ 1], sb.th[cur ^ 1],
+                                                                   sb.strip_off, sb.tile_off, ns, w, ideal, sb.acc);
         cur ^= 1;
     }
     sb.cur = cur;
