@@ -151,7 +151,7 @@ void free_layout(gr_layout *L) {
     {
         StripBuffers &sb = L->strip;
         void *sp[] = {sb.mark_start, sb.mark_end, sb.strip_off, sb.tile_off, sb.fill, sb.k1[0], sb.k1[1],
-                      sb.rk[0], sb.rk[1], sb.th[0], sb.th[1], sb.acc};
+                      sb.rk[0], sb.rk[1], sb.th[0], sb.th[1], sb.acc, sb.split};
         for (void *p : sp)
             if (p) cudaFree(p);
     }
@@ -878,6 +878,13 @@ gr_status strip_one(gr_layout *L, int l, int orient, double ideal, gr_strip_resu
             if ((st = dalloc(&sb.th[i], want)) != GR_OK) return st;
         }
         sb.cap = h.records;
+    }
+    if (2ull * h.tiles > sb.split_cap) {
+        if (sb.split) cudaFree(sb.split);
+        sb.split = nullptr;
+        sb.split_cap = 0;
+        if ((st = dalloc(&sb.split, 2 * (size_t)h.tiles)) != GR_OK) return st;
+        sb.split_cap = 2ull * h.tiles;
     }
     sb.records = h.records;
     sb.tiles = h.tiles;

@@ -269,6 +269,8 @@ struct StripBuffers {
     uint64_t *rk[2] = {nullptr, nullptr};  // key at the right line
     uint32_t *th[2] = {nullptr, nullptr};  // line direction
     uint64_t cap = 0;
+    uint32_t *split = nullptr;             // [2 tiles] merge-path splits of a global merge level
+    uint64_t split_cap = 0;
     StripAcc *acc = nullptr;
     uint64_t records = 0;  // host copies for the launches
     uint32_t tiles = 0;

@@ -368,12 +368,50 @@ __global__ void __launch_bounds__(ST_TILE_THREADS) k_strip_tile(const uint64_t *
     if (INV) flush_strip_totals(tot, sacc, shu);
 }
 
+// Merge path of every chunk of a global merge level (see k_strip_merge):
+// for chunk t, how many of the outputs before its start (2t) and before its
+// end (2t + 1) come from the left run, one thread per entry so that the
+// binary searches' global loads overlap.
+template <bool INV>
+__global__ void __launch_bounds__(ST_THREADS) k_strip_splits(const uint64_t *__restrict__ k1_in,
+                                                             const uint64_t *__restrict__ rk_in,
+                                                             const uint32_t *__restrict__ strip_off,
+                                                             const uint32_t *__restrict__ tile_off, int ns,
+                                                             uint32_t w, const StripAcc *__restrict__ sacc,
+                                                             uint32_t *__restrict__ split) {
+    const uint32_t tiles = sacc->tiles;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * tiles; q += gridDim.x * blockDim.x) {
+        const uint32_t t = q >> 1;
+        int lo_s = 0, hi_s = ns;
+        while (hi_s - lo_s > 1) {
+            const int mid = (lo_s + hi_s) >> 1;
+            if (tile_off[mid] <= t) lo_s = mid; else hi_s = mid;
+        }
+        const uint32_t S0 = strip_off[lo_s], n = strip_off[lo_s + 1] - S0;
+        const uint32_t o0 = (t - tile_off[lo_s]) * ST_TILE, o1 = min(o0 + ST_TILE, n);
+        const uint32_t p0 = o0 / (2 * w) * (2 * w);
+        const uint32_t la = min(w, n - p0), lb = n > p0 + w ? min(w, n - p0 - w) : 0u;
+        const uint64_t *ak1 = k1_in + S0 + p0, *ark = rk_in + S0 + p0;
+        const uint64_t *bk1 = ak1 + w, *brk = ark + w;
+        const uint32_t k = ((q & 1u) ? o1 : o0) - p0;
+        uint32_t lo = k > lb ? k - lb : 0u, hi = min(k, la);
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            const uint32_t j = k - mid - 1;
+            // left[mid] goes first unless right[j] is smaller
+            if (!key_less<INV>(INV ? 0ull : bk1[j], brk[j], INV ? 0ull : ak1[mid], ark[mid])) lo = mid + 1;
+            else hi = mid;
+        }
+        split[q] = lo;
+    }
+}
+
 // One global merge level: within each strip, runs of w records (w >= ST_TILE,
 // a multiple of it) merged pairwise.  The output of a strip is cut into
 // chunks of ST_TILE records (the tiles of the strip; a pair of runs covers
-// whole chunks); each block takes a chunk, finds by one binary search along
-// its diagonals how many of its outputs come from the left run (merge path),
-// loads both input slices into shared memory (coalesced), places every
+// whole chunks); each block takes a chunk, reads how many of its outputs come
+// from the left run (merge path, from k_strip_splits), loads both input
+// slices into shared memory (coalesced), places every
 // element by a binary search in the other slice and stores the chunk
 // (coalesced).  INV: a right-run element x is preceded by the left-run
 // elements with a greater r: those of the chunk's left slice past x's place,
@@ -390,7 +428,8 @@ __global__ void __launch_bounds__(ST_TILE_THREADS) k_strip_merge(const uint64_t 
                                                                  uint32_t *__restrict__ th_out,
                                                                  const uint32_t *__restrict__ strip_off,
                                                                  const uint32_t *__restrict__ tile_off, int ns,
-                                                                 uint32_t w, uint32_t ideal, StripAcc *sacc) {
+                                                                 uint32_t w, const uint32_t *__restrict__ split,
+                                                                 uint32_t ideal, StripAcc *sacc) {
     extern __shared__ __align__(16) unsigned char st_smem[];
     uint64_t *ck1 = (uint64_t *)st_smem;   // chunk inputs: left slice, then right slice
     uint64_t *crk = ck1 + ST_TILE;
@@ -398,7 +437,6 @@ __global__ void __launch_bounds__(ST_TILE_THREADS) k_strip_merge(const uint64_t 
     uint64_t *ork = ok1 + ST_TILE;
     uint32_t *cth = (uint32_t *)(ork + ST_TILE);
     uint32_t *oth = cth + ST_TILE;
-    __shared__ uint32_t split[2];
     __shared__ uint64_t shu[32];
     StripTotals tot;
     const uint32_t tiles = sacc->tiles;
@@ -424,19 +462,7 @@ __global__ void __launch_bounds__(ST_TILE_THREADS) k_strip_merge(const uint64_t 
             continue;
         }
         __syncthreads();  // the previous chunk is done with the shared arrays
-        if (threadIdx.x < 2) {  // merge path: left-run elements among the first k outputs of the pair
-            const uint32_t k = (threadIdx.x == 0 ? o0 : o1) - p0;
-            uint32_t lo = k > lb ? k - lb : 0u, hi = min(k, la);
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                const uint32_t j = k - mid - 1;
-                // left[mid] goes first unless right[j] is smaller
-                if (!key_less<INV>(bk1[j], brk[j], ak1[mid], ark[mid])) lo = mid + 1; else hi = mid;
-            }
-            split[threadIdx.x] = lo;
-        }
-        __syncthreads();
-        const uint32_t i0 = split[0], i1 = split[1];
+        const uint32_t i0 = split[2 * t], i1 = split[2 * t + 1];
         const uint32_t j0 = (o0 - p0) - i0, j1 = (o1 - p0) - i1;
         const uint32_t na = i1 - i0, nb = j1 - j0;
         for (uint32_t e = threadIdx.x; e < na + nb; e += ST_TILE_THREADS) {
@@ -537,10 +563,12 @@ void launch_strip_sort(const Buffers &b, int64_t E, int l, int orient, StripBuff
                                                           ns, 0u, sb.acc);
     cur ^= 1;
     for (uint32_t w = ST_TILE; w < max_n; w <<= 1) {
-        count_launches(1);
+        count_launches(2);
+        k_strip_splits<false><<<grid_for(2 * (int64_t)sb.tiles, ST_THREADS, 152 * 8), ST_THREADS, 0, s>>>(
+            sb.k1[cur], sb.rk[cur], sb.strip_off, sb.tile_off, ns, w, sb.acc, sb.split);
         k_strip_merge<false><<<tb, ST_TILE_THREADS, kTileSmem, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur],
                                                                     sb.k1[cur ^ 1], sb.rk[cur ^ 1], sb.th[cur ^ 1],
-                                                                    sb.strip_off, sb.tile_off, ns, w, 0u, sb.acc);
+                                                                    sb.strip_off, sb.tile_off, ns, w, sb.split, 0u, sb.acc);
         cur ^= 1;
     }
     sb.cur = cur;
@@ -558,10 +586,12 @@ void launch_strip_inversions(int l, StripBuffers &sb, uint32_t max_n, uint32_t i
                                                          ns, ideal, sb.acc);
     cur ^= 1;
     for (uint32_t w = ST_TILE; w < max_n; w <<= 1) {
-        count_launches(1);
+        count_launches(2);
+        k_strip_splits<true><<<grid_for(2 * (int64_t)sb.tiles, ST_THREADS, 152 * 8), ST_THREADS, 0, s>>>(
+            sb.k1[cur], sb.rk[cur], sb.strip_off, sb.tile_off, ns, w, sb.acc, sb.split);
         k_strip_merge<true><<<tb, ST_TILE_THREADS, kTileSmem, s>>>(sb.k1[cur], sb.rk[cur], sb.th[cur],
                                                                    sb.k1[cur ^ 1], sb.rk[cur ^ 1], sb.th[cur ^ 1],
-                                                                   sb.strip_off, sb.tile_off, ns, w, ideal, sb.acc);
+                                                                   sb.strip_off, sb.tile_off, ns, w, sb.split, ideal, sb.acc);
         cur ^= 1;
     }
     sb.cur = cur;
