@@ -68,6 +68,8 @@ struct gr_layout {
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;      // occlusion, min angle, ELV run here, beside the crossings
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t gstream = nullptr;   // evaluation graphs are captured and replayed here
+    cudaEvent_t ev_gin = nullptr, ev_gout = nullptr;
     gr_options opt{};
     Buffers b;
     GridBuffers g;
@@ -111,6 +113,24 @@ struct gr_layout {
     // The crossing grid left by the last full evaluation indexes the edges
     // for the incremental passes while dgrid_k >= 0 (its cell side is
     // 2^dgrid_k); edges moved since then are in the dirty set.
+    // The fast-path evaluation as one CUDA graph, captured for one
+    // configuration (metrics, parameters, plan, buffers) and replayed while it
+    // holds.
+    struct EvalGraph {
+        bool valid = false;
+        uint32_t metrics = 0;
+        double ideal = 0.0;
+        int64_t d = 0;
+        bool x_on = false, grid = false, split = false, o_on = false, ogrid = false, profiling = false;
+        int k = 0, ko = 0;
+        const void *bufs[8] = {};
+        uint64_t caps[3] = {};
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0, d2h = 0;
+        uint32_t phases = 0;  // phases whose events the graph records
+        int32_t path = 0, occl_path = 0;
+        int64_t pairs_tested = -1;
+    } eg;
     int dgrid_k = -1;
     DirtySet dirty;
     StripBuffers strip;             // the approximate strip algorithm's workspace
@@ -118,6 +138,7 @@ struct gr_layout {
     int64_t io_h2d = 0, io_d2h = 0; // bytes copied between host and device
     // phase timing
     bool profiling = false;
+    bool capturing = false;         // an evaluation is being captured into a graph
     cudaEvent_t ev[2 * GR_NUM_PHASES] = {};
     bool pending[GR_NUM_PHASES] = {};
     double prof_ms[GR_NUM_PHASES] = {};
@@ -148,6 +169,7 @@ void free_layout(gr_layout *L) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_grid(L->g);
+    if (L->eg.exec) cudaGraphExecDestroy(L->eg.exec);
     {
         StripBuffers &sb = L->strip;
         void *sp[] = {sb.mark_start, sb.mark_end, sb.strip_off, sb.tile_off, sb.fill, sb.k1[0], sb.k1[1],
@@ -160,6 +182,9 @@ void free_layout(gr_layout *L) {
     if (L->ev_fork) cudaEventDestroy(L->ev_fork);
     if (L->ev_join) cudaEventDestroy(L->ev_join);
     if (L->side) cudaStreamDestroy(L->side);
+    if (L->gstream) cudaStreamDestroy(L->gstream);
+    if (L->ev_gin) cudaEventDestroy(L->ev_gin);
+    if (L->ev_gout) cudaEventDestroy(L->ev_gout);
     if (L->h_result) cudaFreeHost(L->h_result);
     if (L->h_acc) cudaFreeHost(L->h_acc);
     if (L->h_dacc) cudaFreeHost(L->h_dacc);
@@ -212,6 +237,9 @@ gr_status alloc_layout(gr_layout *L) {
     }
 #undef GR_TRY
     GR_CU(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
+    GR_CU(cudaStreamCreateWithFlags(&L->gstream, cudaStreamNonBlocking));
+    GR_CU(cudaEventCreateWithFlags(&L->ev_gin, cudaEventDisableTiming));
+    GR_CU(cudaEventCreateWithFlags(&L->ev_gout, cudaEventDisableTiming));
     GR_CU(cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming));
     GR_CU(cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming));
     GR_CU(cudaMallocHost((void **)&L->h_result, sizeof(gr_result)));
@@ -283,12 +311,16 @@ gr_status ensure_ocells(gr_layout *L, int C) {
 }
 
 // ------------------------------------------------------------ phase timing
+// Phase events; while an evaluation is being captured into a graph they are
+// captured as event-record nodes, so that every replay records them.
 void phase_begin(gr_layout *L, int ph, cudaStream_t s) {
-    if (L->profiling) cudaEventRecord(L->ev[2 * ph], s);
+    if (L->profiling)
+        cudaEventRecordWithFlags(L->ev[2 * ph], s, L->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 void phase_end(gr_layout *L, int ph, cudaStream_t s) {
     if (L->profiling) {
-        cudaEventRecord(L->ev[2 * ph + 1], s);
+        cudaEventRecordWithFlags(L->ev[2 * ph + 1], s,
+                                 L->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
         L->pending[ph] = true;
     }
 }
@@ -621,6 +653,211 @@ gr_status gr_layout_destroy(gr_layout *L) {
     return GR_OK;
 }
 
+namespace {
+
+// The end of an evaluation: one synchronisation, then the checks.  A fast
+// grid evaluation whose buffers the inputs outgrew runs again, synchronised.
+gr_status finish_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, double ideal, int64_t d,
+                          bool fast_grid, int32_t path, int k, gr_result *out) {
+    GR_CU(cudaStreamSynchronize(L->stream));
+    phase_collect(L);
+    L->stats_stale = false;  // the read-back holds the statistics of these inputs
+    if (fast_grid && ((L->h_acc->eval_status & ST_OVERFLOW) || (L->h_acc->grid_flags & GF_ITEMS_OVERFLOW)) &&
+        !(L->h_acc->status & (ST_BAD_ID | ST_BAD_COORD))) {
+        L->fast_ok = false;  // the buffers did not fit these inputs: again, synchronised
+        return gr_evaluate(L, metrics, params, out);
+    }
+    gr_status st = status_to_error(L->h_acc->status | L->h_acc->eval_status);
+    if (st != GR_OK) return st;
+    *out = *L->h_result;
+    remember_totals(L, metrics, ideal_units(ideal), d);
+    if (path == GR_PATH_GRID) L->dgrid_k = k;
+    return GR_OK;
+}
+
+struct FastPlan {
+    bool x_on = false, o_on = false, ogrid = false, graphable = false;
+    int ko = 0;
+    CrossPlan cp;
+};
+
+// The occlusion choice: a grid of side >= d for many vertices; all-pairs
+// tiles for few, or when d is so large that the grid has at most 4 x 4 cells.
+bool occlusion_grid(const gr_layout *L, int ko) {
+    if (L->opt.occlusion_path == GR_PATH_GRID) return ko <= 16;
+    if (L->opt.occlusion_path == GR_PATH_ALLPAIRS) return false;
+    return L->V > 4096 && ko <= 14;
+}
+
+// Plan of a fast-path evaluation and its buffers.  It can run as one graph
+// when no step needs a read-back: crossings absent, on all-pairs tiles, or on
+// the grid plan the buffers were sized for.
+gr_status plan_fast(gr_layout *L, uint32_t metrics, int64_t d, uint64_t n_seg, FastPlan *fp) {
+    gr_status st;
+    fp->x_on = (metrics & GR_METRIC_CROSSINGS) && n_seg >= 2;
+    fp->o_on = (metrics & GR_METRIC_OCCLUSION) != 0;
+    fp->ko = occl_cell_log2(d);
+    fp->ogrid = fp->o_on && occlusion_grid(L, fp->ko);
+    if (fp->ogrid && L->V >= 2 && d > 0) {
+        const int C = (65536 >> fp->ko) * (65536 >> fp->ko);
+        if ((st = ensure_ocells(L, C)) != GR_OK) return st;
+    }
+    if (fp->x_on) {
+        fp->cp = plan_crossings(L, *L->h_acc);
+        if (fp->cp.grid) {
+            const int C = (65536 >> fp->cp.k) * (65536 >> fp->cp.k);
+            if ((st = ensure_cells(L, C)) != GR_OK) return st;
+        }
+    }
+    fp->graphable = !fp->x_on || !fp->cp.grid || (fp->cp.k == L->fast_k && fp->cp.split == L->fast_split);
+    return GR_OK;
+}
+
+// Enqueues a fast-path evaluation (no read-back before the end): the same
+// steps as the synchronised path of gr_evaluate.
+void enqueue_fast(gr_layout *L, cudaStream_t s, uint32_t metrics, double ideal, int64_t d, const FastPlan &fp,
+                  int32_t *path, int32_t *occl_path, int64_t *pairs_tested) {
+    cudaStream_t t = L->side;
+    Buffers &b = L->b;
+    const int64_t V = L->V, E = L->E;
+    cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0, sizeof(DevAcc) - offsetof(DevAcc, eval_status),
+                    s);
+    cudaEventRecord(L->ev_fork, s);
+    cudaStreamWaitEvent(t, L->ev_fork, 0);
+    if (metrics & GR_METRIC_EDGE_LENGTH) {
+        phase_begin(L, GR_PHASE_EDGE_LENGTH, t);
+        launch_elv(b, E, t);
+        phase_end(L, GR_PHASE_EDGE_LENGTH, t);
+    }
+    if (metrics & GR_METRIC_MIN_ANGLE) {
+        phase_begin(L, GR_PHASE_MIN_ANGLE, t);
+        launch_min_angle(b, V, E, t);
+        phase_end(L, GR_PHASE_MIN_ANGLE, t);
+    }
+    *occl_path = 0;
+    if (fp.o_on) {
+        if (fp.ogrid && V >= 2 && d > 0) {
+            phase_begin(L, GR_PHASE_OCCL_BIN, t);
+            launch_occlusion_grid_count(b, V, L->g, fp.ko, t);
+            phase_end(L, GR_PHASE_OCCL_BIN, t);
+            phase_begin(L, GR_PHASE_OCCL_PAIRS, t);
+            launch_occlusion_grid_pairs(b, V, L->g, fp.ko, d, t);
+            phase_end(L, GR_PHASE_OCCL_PAIRS, t);
+        } else {
+            phase_begin(L, GR_PHASE_OCCL_PAIRS, t);
+            launch_occlusion_allpairs(b, V, d, t);
+            phase_end(L, GR_PHASE_OCCL_PAIRS, t);
+        }
+        *occl_path = fp.ogrid ? GR_PATH_GRID : GR_PATH_ALLPAIRS;
+    }
+    cudaEventRecord(L->ev_join, t);
+    *path = 0;
+    *pairs_tested = -1;
+    if (fp.x_on && fp.cp.grid) {
+        phase_begin(L, GR_PHASE_CROSS_BIN, s);
+        launch_grid_count(b, E, L->g, fp.cp.k, fp.cp.split, s);
+        phase_end(L, GR_PHASE_CROSS_BIN, s);
+        phase_begin(L, GR_PHASE_CROSS_SCATTER, s);
+        launch_grid_scatter(b, E, L->g, fp.cp.k, fp.cp.split, s);
+        phase_end(L, GR_PHASE_CROSS_SCATTER, s);
+        phase_begin(L, GR_PHASE_CROSS_PAIRS, s);
+        launch_grid_pairs(b, L->g, fp.cp.k, L->g.items_cap, ideal_units(ideal), PerEdge{}, s);
+        if (fp.cp.split) launch_grid_long_pairs(b, L->g, -1, ideal_units(ideal), PerEdge{}, s);
+        phase_end(L, GR_PHASE_CROSS_PAIRS, s);
+        *path = GR_PATH_GRID;
+        *pairs_tested = -2;  // computed on the device
+    } else if (fp.x_on) {
+        phase_begin(L, GR_PHASE_CROSS_PAIRS, s);
+        launch_crossings_allpairs(b, E, ideal_units(ideal), PerEdge{}, s);
+        phase_end(L, GR_PHASE_CROSS_PAIRS, s);
+        *path = GR_PATH_ALLPAIRS;
+    } else if (metrics & GR_METRIC_CROSSINGS) {
+        *path = GR_PATH_ALLPAIRS;
+    }
+    cudaStreamWaitEvent(s, L->ev_join, 0);
+    phase_begin(L, GR_PHASE_FINALIZE, s);
+    launch_finalize(b, metrics, E, ideal, d, V > 0 ? min_angle_blocks(V) : 0, *path,
+                    *path == GR_PATH_GRID ? fp.cp.k : 0, *occl_path, *pairs_tested, s);
+    cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s);
+    L->io_d2h += (int64_t)(sizeof(gr_result) + sizeof(DevAcc));
+    phase_end(L, GR_PHASE_FINALIZE, s);
+}
+
+// Replays the graph of this configuration, capturing it first when the
+// configuration or a buffer changed since the last capture.
+gr_status run_eval_graph(gr_layout *L, uint32_t metrics, double ideal, int64_t d, const FastPlan &fp) {
+    auto &g = L->eg;
+    const GridBuffers &gb = L->g;
+    const void *bufs[8] = {gb.cell_off, gb.cell_nl, gb.item_off, gb.cell_fill, gb.rec, gb.item_desc, gb.ocell_off,
+                           gb.opts};
+    const uint64_t caps[3] = {gb.rec_cap, gb.items_cap, (uint64_t)gb.cells_cap};
+    const bool same = g.valid && g.metrics == metrics && g.ideal == ideal && g.d == d && g.x_on == fp.x_on &&
+                      g.grid == fp.cp.grid && g.split == fp.cp.split && g.k == fp.cp.k && g.o_on == fp.o_on &&
+                      g.ogrid == fp.ogrid && g.ko == fp.ko && g.profiling == L->profiling &&
+                      memcmp(g.bufs, bufs, sizeof bufs) == 0 && memcmp(g.caps, caps, sizeof caps) == 0;
+    cudaStream_t s = L->gstream;  // (the caller's stream may be the legacy one, which cannot be captured)
+    if (!same) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.valid = false;
+        bool pend0[GR_NUM_PHASES];
+        memcpy(pend0, L->pending, sizeof pend0);
+        const int64_t l0 = gr_kernel_launches(), io0 = L->io_d2h;
+        GR_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        L->capturing = true;
+        enqueue_fast(L, s, metrics, ideal, d, fp, &g.path, &g.occl_path, &g.pairs_tested);
+        L->capturing = false;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        g.launches = gr_kernel_launches() - l0;
+        count_launches((int)-g.launches);  // nothing ran yet
+        g.d2h = L->io_d2h - io0;
+        L->io_d2h = io0;
+        g.phases = 0;
+        for (int ph = 0; ph < GR_NUM_PHASES; ++ph)
+            if (L->pending[ph] && !pend0[ph]) g.phases |= 1u << ph;
+        memcpy(L->pending, pend0, sizeof pend0);
+        if (ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(ec, "capturing the evaluation");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_fail(ei, "instantiating the evaluation graph");
+        }
+        g.valid = true;
+        g.metrics = metrics;
+        g.ideal = ideal;
+        g.d = d;
+        g.x_on = fp.x_on;
+        g.grid = fp.cp.grid;
+        g.split = fp.cp.split;
+        g.k = fp.cp.k;
+        g.o_on = fp.o_on;
+        g.ogrid = fp.ogrid;
+        g.ko = fp.ko;
+        g.profiling = L->profiling;
+        memcpy(g.bufs, bufs, sizeof bufs);
+        memcpy(g.caps, caps, sizeof caps);
+    }
+    // after the work queued on the layout's stream, and before what follows it there
+    GR_CU(cudaEventRecord(L->ev_gin, L->stream));
+    GR_CU(cudaStreamWaitEvent(s, L->ev_gin, 0));
+    GR_CU(cudaGraphLaunch(g.exec, s));
+    GR_CU(cudaEventRecord(L->ev_gout, s));
+    GR_CU(cudaStreamWaitEvent(L->stream, L->ev_gout, 0));
+    count_launches((int)g.launches);
+    L->io_d2h += g.d2h;
+    for (int ph = 0; ph < GR_NUM_PHASES; ++ph)
+        if (g.phases & (1u << ph)) L->pending[ph] = true;
+    return GR_OK;
+}
+
+}  // namespace
+
 gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, gr_result *out) {
     g_err.clear();
     if (!L || !out) return fail(GR_EINVAL, "NULL argument");
@@ -641,14 +878,23 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     }
     if (L->coord == GR_COORD_F32) return evaluate_f32(L, metrics, ideal, out);
     const uint64_t n_seg = fast ? (uint64_t)E : L->h_acc->n_seg;  // (an upper bound when fast)
-    GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
-                          sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
     L->dgrid_k = -1;  // set again below when this evaluation leaves a complete crossing grid
     if (L->dirty_any) {
         GR_CU(cudaMemsetAsync(L->dirty.flag, 0, (size_t)(E > 0 ? E : 1), s));
         GR_CU(cudaMemsetAsync(L->dirty.n, 0, sizeof(uint32_t), s));
         L->dirty_any = false;
     }
+    if (fast) {
+        // the plan of the fast path, and every buffer it needs, before anything is enqueued
+        FastPlan fp;
+        if ((st = plan_fast(L, metrics, d, n_seg, &fp)) != GR_OK) return st;
+        if (fp.graphable) {
+            if ((st = run_eval_graph(L, metrics, ideal, d, fp)) != GR_OK) return st;
+            return finish_evaluate(L, metrics, params, ideal, d, fp.x_on && fp.cp.grid, L->eg.path, fp.cp.k, out);
+        }
+    }
+    GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
+                          sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
 
     // Occlusion, minimum angle and edge length variation depend only on the
     // inputs: they run on the side stream, beside the crossing pipeline.
@@ -772,20 +1018,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
     L->io_d2h += (int64_t)(sizeof(gr_result) + sizeof(DevAcc));
     phase_end(L, GR_PHASE_FINALIZE);
-    GR_CU(cudaStreamSynchronize(s));
-    phase_collect(L);
-    L->stats_stale = false;  // the read-back holds the statistics of these inputs
-    if (fast_grid && ((L->h_acc->eval_status & ST_OVERFLOW) || (L->h_acc->grid_flags & GF_ITEMS_OVERFLOW)) &&
-        !(L->h_acc->status & (ST_BAD_ID | ST_BAD_COORD))) {
-        L->fast_ok = false;  // the buffers did not fit these inputs: again, synchronised
-        return gr_evaluate(L, metrics, params, out);
-    }
-    st = status_to_error(L->h_acc->status | L->h_acc->eval_status);
-    if (st != GR_OK) return st;
-    *out = *L->h_result;
-    remember_totals(L, metrics, ideal_units(ideal), d);
-    if (path == GR_PATH_GRID) L->dgrid_k = cp.k;
-    return GR_OK;
+    return finish_evaluate(L, metrics, params, ideal, d, fast_grid, path, cp.k, out);
 }
 
 gr_status gr_node_occlusion(gr_layout *L, int64_t d, int64_t *out_pairs) {

@@ -270,16 +270,11 @@ __device__ __forceinline__ uint32_t sibling_rank(uint64_t xk1, uint64_t xrk, boo
 }
 
 // Sum of |ideal - angle| of direction xt against directions y[0, n) (shared
-// memory), four at a time with two accumulators.
+// memory).
 __device__ __forceinline__ uint64_t dev_sum(uint32_t xt, const uint32_t *y, uint32_t n, uint32_t ideal) {
-    uint64_t a0 = 0, a1 = 0;
-    uint32_t m = 0;
-    for (; m + 4 <= n; m += 4) {
-        a0 += (uint64_t)dev_term(xt, y[m], ideal) + dev_term(xt, y[m + 1], ideal);
-        a1 += (uint64_t)dev_term(xt, y[m + 2], ideal) + dev_term(xt, y[m + 3], ideal);
-    }
-    for (; m < n; ++m) a0 += dev_term(xt, y[m], ideal);
-    return a0 + a1;
+    uint64_t a = 0;
+    for (uint32_t m = 0; m < n; ++m) a += dev_term(xt, y[m], ideal);
+    return a;
 }
 
 struct StripTotals {
