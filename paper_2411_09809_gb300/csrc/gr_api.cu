@@ -110,6 +110,20 @@ struct gr_layout {
     DeltaAcc *dacc = nullptr, *h_dacc = nullptr;
     int32_t *mv_ids = nullptr, *mv_xy = nullptr;
     int64_t mv_cap = 0;
+    MoveParams *mp_dev = nullptr;            // count and previous totals on the device
+    void *mp_host = nullptr;                 // their pinned staging copy
+    struct MoveGraph {
+        bool valid = false;
+        uint32_t metrics = 0;
+        double ideal = 0.0;
+        int64_t d = 0;
+        bool use_grid = false, ma_incremental = false;
+        int k = -1;
+        int64_t cap = 0;
+        const void *bufs[8] = {};
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0, d2h = 0;
+    } mg;
     // The crossing grid left by the last full evaluation indexes the edges
     // for the incremental passes while dgrid_k >= 0 (its cell side is
     // 2^dgrid_k); edges moved since then are in the dirty set.
@@ -164,7 +178,7 @@ void free_layout(gr_layout *L) {
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result,
                     b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->arg, L->st, L->out3, L->gout3,
                     L->f32_work, L->theta_adj, L->moved, L->affected, L->dacc, L->mv_ids, L->mv_xy,
-                    L->dirty.flag, L->dirty.list, L->dirty.n, b.adj_off, b.adj, b.ma_nz, b.ma_dv, b.ma_touch,
+                    L->dirty.flag, L->dirty.list, L->dirty.n, L->mp_dev, b.adj_off, b.adj, b.ma_nz, b.ma_dv, b.ma_touch,
                     b.ma_flag};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -188,6 +202,8 @@ void free_layout(gr_layout *L) {
     if (L->h_result) cudaFreeHost(L->h_result);
     if (L->h_acc) cudaFreeHost(L->h_acc);
     if (L->h_dacc) cudaFreeHost(L->h_dacc);
+    if (L->mp_host) cudaFreeHost(L->mp_host);
+    if (L->mg.exec) cudaGraphExecDestroy(L->mg.exec);
     delete L;
 }
 
@@ -1220,6 +1236,122 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     return status_to_error(L->h_acc->status | L->h_acc->eval_status);
 }
 
+namespace {
+
+struct MovePlan {
+    uint32_t metrics;
+    double ideal;
+    int64_t d;
+    uint32_t ideal_u;
+    bool crossings, occl, use_grid, ma_incremental;
+    long long d2;
+};
+
+// Enqueues an incremental move on stream s (side work on the side stream):
+// validation, the before pass, the new coordinates, the regather, the after
+// pass, the new totals, the other metrics and the read-back.  Every kernel
+// after the validation does nothing on an invalid move.
+void enqueue_move(gr_layout *L, cudaStream_t s, const MovePlan &mp) {
+    Buffers &b = L->b;
+    const int64_t V = L->V, E = L->E, cap = L->mv_cap;
+    const int64_t *np = &L->mp_dev->n;
+    cudaMemsetAsync(L->dacc, 0, sizeof(DeltaAcc), s);
+    launch_delta_validate(L->mv_ids, L->mv_xy, np, cap, V, L->moved, L->dacc, s);
+    if (mp.crossings)
+        launch_delta_affected(b, E, L->moved, L->affected, L->dacc, mp.use_grid ? L->dirty : DirtySet{}, s);
+    if (mp.use_grid)
+        launch_delta_grid_pass(b, L->g, L->dgrid_k, L->moved, L->affected, L->dirty, mp.ideal_u, L->dacc, 0, s);
+    launch_delta_pass(b, V, E, L->mv_ids, np, L->moved, L->affected, mp.crossings && !mp.use_grid, mp.ideal_u,
+                      mp.occl, mp.d2, L->dacc, 0, s);
+    launch_delta_apply(L->mv_ids, L->mv_xy, np, cap, L->dacc, b, s);
+    // the moved layout's segments and statistics, then the after pass on
+    // them; edge length variation and minimum angle on the side stream
+    cudaMemsetAsync(b.acc, 0, offsetof(DevAcc, eval_status), s);
+    launch_check_vertices(b.xy, V, b, s);
+    launch_gather(b.xy, V, b.edges, E, b, s);
+    const bool side_work = (mp.metrics & (GR_METRIC_EDGE_LENGTH | GR_METRIC_MIN_ANGLE)) != 0;
+    if (side_work) {
+        cudaStream_t t = L->side;
+        cudaEventRecord(L->ev_fork, s);
+        cudaStreamWaitEvent(t, L->ev_fork, 0);
+        if (mp.metrics & GR_METRIC_EDGE_LENGTH) launch_elv(b, E, t);
+        if (mp.metrics & GR_METRIC_MIN_ANGLE) {
+            if (mp.ma_incremental) launch_min_angle_moved(b, V, L->mv_ids, np, cap, t);
+            else launch_min_angle(b, V, E, t);
+        }
+        cudaEventRecord(L->ev_join, t);
+    }
+    if (mp.use_grid)
+        launch_delta_grid_pass(b, L->g, L->dgrid_k, L->moved, L->affected, L->dirty, mp.ideal_u, L->dacc, 1, s);
+    launch_delta_pass(b, V, E, L->mv_ids, np, L->moved, L->affected, mp.crossings && !mp.use_grid, mp.ideal_u,
+                      mp.occl, mp.d2, L->dacc, 1, s);
+    launch_delta_unmark(L->mv_ids, np, cap, V, L->moved, s);
+    launch_delta_combine(&L->mp_dev->last, L->dacc, b, s);
+    if (side_work) cudaStreamWaitEvent(s, L->ev_join, 0);
+    const uint32_t need = mp.metrics & (GR_METRIC_CROSSINGS | GR_METRIC_OCCLUSION);
+    launch_finalize(b, mp.metrics, E, mp.ideal, mp.d, V > 0 ? min_angle_blocks(V) : 0,
+                    mp.crossings ? GR_PATH_DELTA : 0, 0, (need & GR_METRIC_OCCLUSION) ? GR_PATH_DELTA : 0, -2, s);
+    cudaMemcpyAsync(L->h_dacc, L->dacc, sizeof(DeltaAcc), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s);
+    L->io_d2h += (int64_t)(sizeof(DeltaAcc) + sizeof(gr_result) + sizeof(DevAcc));
+}
+
+// Replays the captured move of this configuration (capturing it first when
+// the configuration or a buffer changed), ordered after the layout's stream.
+gr_status run_move_graph(gr_layout *L, const MovePlan &mp) {
+    auto &g = L->mg;
+    const void *bufs[8] = {L->mv_ids, L->mv_xy, L->dirty.flag, L->dirty.list, L->g.cell_off, L->g.rec, L->mp_dev,
+                           L->dacc};
+    const bool same = g.valid && g.metrics == mp.metrics && g.ideal == mp.ideal && g.d == mp.d &&
+                      g.use_grid == mp.use_grid && g.ma_incremental == mp.ma_incremental && g.k == L->dgrid_k &&
+                      g.cap == L->mv_cap && memcmp(g.bufs, bufs, sizeof bufs) == 0;
+    cudaStream_t s = L->gstream;
+    if (!same) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.valid = false;
+        const int64_t l0 = gr_kernel_launches(), io0 = L->io_d2h;
+        GR_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        enqueue_move(L, s, mp);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        g.launches = gr_kernel_launches() - l0;
+        count_launches((int)-g.launches);
+        g.d2h = L->io_d2h - io0;
+        L->io_d2h = io0;
+        if (ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(ec, "capturing the move");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_fail(ei, "instantiating the move graph");
+        }
+        g.valid = true;
+        g.metrics = mp.metrics;
+        g.ideal = mp.ideal;
+        g.d = mp.d;
+        g.use_grid = mp.use_grid;
+        g.ma_incremental = mp.ma_incremental;
+        g.k = L->dgrid_k;
+        g.cap = L->mv_cap;
+        memcpy(g.bufs, bufs, sizeof bufs);
+    }
+    GR_CU(cudaEventRecord(L->ev_gin, L->stream));
+    GR_CU(cudaStreamWaitEvent(s, L->ev_gin, 0));
+    GR_CU(cudaGraphLaunch(g.exec, s));
+    GR_CU(cudaEventRecord(L->ev_gout, s));
+    GR_CU(cudaStreamWaitEvent(L->stream, L->ev_gout, 0));
+    count_launches((int)g.launches);
+    L->io_d2h += g.d2h;
+    return GR_OK;
+}
+
+}  // namespace
+
 gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const int32_t *xy_new, uint32_t metrics,
                            const gr_params *params, gr_result *out) {
     g_err.clear();
@@ -1240,17 +1372,20 @@ gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const in
         if ((st = dalloc(&L->moved, (size_t)V)) != GR_OK) return st;
         if ((st = dalloc(&L->affected, (size_t)E)) != GR_OK) return st;
         if ((st = dalloc(&L->dacc, 1)) != GR_OK) return st;
+        if ((st = dalloc(&L->mp_dev, 1)) != GR_OK) return st;
         GR_CU(cudaMallocHost((void **)&L->h_dacc, sizeof(DeltaAcc)));
+        GR_CU(cudaMallocHost((void **)&L->mp_host, sizeof(MoveParams)));
         GR_CU(cudaMemsetAsync(L->moved, 0, sizeof(uint32_t) * (V > 0 ? V : 1), s));
     }
-    if (L->mv_cap < n) {
+    if (L->mv_cap < n || !L->mv_ids) {
         if (L->mv_ids) cudaFree(L->mv_ids);
         if (L->mv_xy) cudaFree(L->mv_xy);
         L->mv_ids = L->mv_xy = nullptr;
         L->mv_cap = 0;
-        if ((st = dalloc(&L->mv_ids, (size_t)n)) != GR_OK) return st;
-        if ((st = dalloc(&L->mv_xy, 2 * (size_t)n)) != GR_OK) return st;
-        L->mv_cap = n;
+        const int64_t cap = std::max<int64_t>(n, 64);
+        if ((st = dalloc(&L->mv_ids, (size_t)cap)) != GR_OK) return st;
+        if ((st = dalloc(&L->mv_xy, 2 * (size_t)cap)) != GR_OK) return st;
+        L->mv_cap = cap;
     }
     if (n > 0) {
         const cudaMemcpyKind ki = is_device_pointer(ids) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1260,41 +1395,42 @@ gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const in
         if (ki == cudaMemcpyHostToDevice) L->io_h2d += (int64_t)sizeof(int32_t) * n;
         if (kx == cudaMemcpyHostToDevice) L->io_h2d += (int64_t)sizeof(int32_t) * 2 * n;
     }
-    // Validation, the before and after passes, the regather and the new
-    // totals are queued without a host round trip; every kernel after the
-    // validation does nothing on an invalid move, which leaves the layout as
-    // it was and is reported after the one synchronisation.
-    GR_CU(cudaMemsetAsync(L->dacc, 0, sizeof(DeltaAcc), s));
-    if (n > 0) launch_delta_validate(L->mv_ids, L->mv_xy, n, V, L->moved, L->dacc, s);
-    const uint32_t ideal_u = ideal_units(ideal);
+    MovePlan mp;
+    mp.metrics = metrics;
+    mp.ideal = ideal;
+    mp.d = d;
+    mp.ideal_u = ideal_units(ideal);
     const uint32_t need = metrics & (GR_METRIC_CROSSINGS | GR_METRIC_OCCLUSION);
     const bool incremental = L->last.valid && !L->stats_stale && (L->last.metrics & need) == need &&
-                             L->last.ideal_u == ideal_u && L->last.d == d;
-    const bool crossings = (need & GR_METRIC_CROSSINGS) != 0, occl = (need & GR_METRIC_OCCLUSION) != 0 && d > 0;
-    const long long d2 = d >= 100000 ? (long long)1e11 : (long long)d * d;
+                             L->last.ideal_u == mp.ideal_u && L->last.d == d;
+    mp.crossings = (need & GR_METRIC_CROSSINGS) != 0;
+    mp.occl = (need & GR_METRIC_OCCLUSION) != 0 && d > 0;
+    mp.d2 = d >= 100000 ? (long long)1e11 : (long long)d * d;
     // the affected edges against the others: through the last full
     // evaluation's crossing grid when it left one, else against every segment
-    const bool use_grid = incremental && crossings && L->dgrid_k >= 0;
-    if (use_grid && !L->dirty.flag) {
-        L->dirty.cap = (uint32_t)std::min<int64_t>(E, std::max<int64_t>(4096, E / 32));
-        if ((st = dalloc(&L->dirty.flag, (size_t)E)) != GR_OK) return st;
-        if ((st = dalloc(&L->dirty.list, (size_t)L->dirty.cap)) != GR_OK) return st;
-        if ((st = dalloc(&L->dirty.n, 1)) != GR_OK) return st;
-        GR_CU(cudaMemsetAsync(L->dirty.flag, 0, (size_t)E, s));
-        GR_CU(cudaMemsetAsync(L->dirty.n, 0, sizeof(uint32_t), s));
+    mp.use_grid = incremental && mp.crossings && L->dgrid_k >= 0;
+    mp.ma_incremental = (L->last.metrics & GR_METRIC_MIN_ANGLE) != 0;
+    // the count and the totals the move updates (only those asked for; the
+    // others stay zero, as in a full evaluation)
+    MoveParams *h = (MoveParams *)L->mp_host;
+    memset(h, 0, sizeof *h);
+    h->n = n;
+    if (mp.crossings) {
+        h->last.proper = L->last.proper;
+        h->last.touching = L->last.touching;
+        h->last.collinear = L->last.collinear;
+        h->last.dev_lo = L->last.dev_lo;
+        h->last.dev_hi = L->last.dev_hi;
     }
-    if (incremental && n > 0) {
-        if (crossings) launch_delta_affected(b, E, L->moved, L->affected, L->dacc, use_grid ? L->dirty : DirtySet{}, s);
-        if (use_grid) {
-            L->dirty_any = true;
-            launch_delta_grid_pass(b, L->g, L->dgrid_k, L->moved, L->affected, L->dirty, ideal_u, L->dacc, 0, s);
-        }
-        launch_delta_pass(b, V, E, L->mv_ids, n, L->moved, L->affected, crossings && !use_grid, ideal_u, occl, d2,
-                          L->dacc, 0, s);
-    }
-    if (n > 0) launch_delta_apply(L->mv_ids, L->mv_xy, n, L->dacc, b, s);
+    if (mp.occl) h->last.occlusion = L->last.occlusion;
+    GR_CU(cudaMemcpyAsync(L->mp_dev, h, sizeof *h, cudaMemcpyHostToDevice, s));
     if (!incremental) {
-        if (n > 0) launch_delta_unmark(L->mv_ids, n, V, L->moved, s);
+        // validate, move, then a full evaluation
+        const int64_t *np = &L->mp_dev->n;
+        GR_CU(cudaMemsetAsync(L->dacc, 0, sizeof(DeltaAcc), s));
+        launch_delta_validate(L->mv_ids, L->mv_xy, np, L->mv_cap, V, L->moved, L->dacc, s);
+        launch_delta_apply(L->mv_ids, L->mv_xy, np, L->mv_cap, L->dacc, b, s);
+        launch_delta_unmark(L->mv_ids, np, L->mv_cap, V, L->moved, s);
         GR_CU(cudaMemcpyAsync(L->h_dacc, L->dacc, sizeof(DeltaAcc), cudaMemcpyDeviceToHost, s));
         GR_CU(cudaStreamSynchronize(s));
         if (L->h_dacc->status) return status_to_error(L->h_dacc->status);
@@ -1306,50 +1442,17 @@ gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const in
         L->stats_stale = true;
         return gr_evaluate(L, metrics, params, out);
     }
-    // the moved layout's segments and statistics, then the after pass on
-    // them; edge length variation and minimum angle run on the side stream
-    // meanwhile
-    GR_CU(cudaMemsetAsync(b.acc, 0, offsetof(DevAcc, eval_status), s));
-    launch_check_vertices(b.xy, V, b, s);
-    launch_gather(b.xy, V, b.edges, E, b, s);
-    const bool side_work = (metrics & (GR_METRIC_EDGE_LENGTH | GR_METRIC_MIN_ANGLE)) != 0;
-    if (side_work) {
-        cudaStream_t t = L->side;
-        GR_CU(cudaEventRecord(L->ev_fork, s));
-        GR_CU(cudaStreamWaitEvent(t, L->ev_fork, 0));
-        if (metrics & GR_METRIC_EDGE_LENGTH) launch_elv(b, E, t);
-        if (metrics & GR_METRIC_MIN_ANGLE) {
-            if (L->last.metrics & GR_METRIC_MIN_ANGLE) launch_min_angle_moved(b, V, L->mv_ids, n, t);
-            else launch_min_angle(b, V, E, t);
-        }
-        GR_CU(cudaEventRecord(L->ev_join, t));
+    if (mp.use_grid && !L->dirty.flag) {
+        L->dirty.cap = (uint32_t)std::min<int64_t>(E, std::max<int64_t>(4096, E / 32));
+        if ((st = dalloc(&L->dirty.flag, (size_t)E)) != GR_OK) return st;
+        if ((st = dalloc(&L->dirty.list, (size_t)L->dirty.cap)) != GR_OK) return st;
+        if ((st = dalloc(&L->dirty.n, 1)) != GR_OK) return st;
+        GR_CU(cudaMemsetAsync(L->dirty.flag, 0, (size_t)E, s));
+        GR_CU(cudaMemsetAsync(L->dirty.n, 0, sizeof(uint32_t), s));
     }
-    if (n > 0) {
-        if (use_grid)
-            launch_delta_grid_pass(b, L->g, L->dgrid_k, L->moved, L->affected, L->dirty, ideal_u, L->dacc, 1, s);
-        launch_delta_pass(b, V, E, L->mv_ids, n, L->moved, L->affected, crossings && !use_grid, ideal_u, occl, d2,
-                          L->dacc, 1, s);
-        launch_delta_unmark(L->mv_ids, n, V, L->moved, s);
-    }
-    DeltaCounts last;  // only the totals asked for (the others stay zero, as in a full evaluation)
-    memset(&last, 0, sizeof last);
-    if (crossings) {
-        last.proper = L->last.proper;
-        last.touching = L->last.touching;
-        last.collinear = L->last.collinear;
-        last.dev_lo = L->last.dev_lo;
-        last.dev_hi = L->last.dev_hi;
-    }
-    if (occl) last.occlusion = L->last.occlusion;
-    launch_delta_combine(last, L->dacc, b, s);
-    if (side_work) GR_CU(cudaStreamWaitEvent(s, L->ev_join, 0));
-    launch_finalize(b, metrics, E, ideal, d, V > 0 ? min_angle_blocks(V) : 0, crossings ? GR_PATH_DELTA : 0, 0,
-                    (need & GR_METRIC_OCCLUSION) ? GR_PATH_DELTA : 0, -2, s);
-    GR_CU(cudaGetLastError());
-    GR_CU(cudaMemcpyAsync(L->h_dacc, L->dacc, sizeof(DeltaAcc), cudaMemcpyDeviceToHost, s));
-    GR_CU(cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s));
-    GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
-    L->io_d2h += (int64_t)(sizeof(DeltaAcc) + sizeof(gr_result) + sizeof(DevAcc));
+    if (mp.use_grid) L->dirty_any = true;
+    // one graph replay (one host synchronisation)
+    if ((st = run_move_graph(L, mp)) != GR_OK) return st;
     GR_CU(cudaStreamSynchronize(s));
     if (L->h_dacc->status) return status_to_error(L->h_dacc->status);  // nothing moved
     L->stats_stale = false;
@@ -1359,7 +1462,7 @@ gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const in
     }
     if ((st = status_to_error(L->h_acc->status | L->h_acc->eval_status)) != GR_OK) return st;
     *out = *L->h_result;
-    remember_totals(L, metrics, ideal_u, d);
+    remember_totals(L, metrics, mp.ideal_u, d);
     return GR_OK;
 }
 

@@ -230,7 +230,8 @@ void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s);
 // The same after vertices ids[0, n) moved (b.xy updated), when b.ma_part
 // holds the partials of the layout before the move: only the blocks holding
 // a moved vertex or a neighbour of one are recomputed.
-void launch_min_angle_moved(Buffers &b, int64_t V, const int32_t *ids, int64_t n, cudaStream_t s);
+void launch_min_angle_moved(Buffers &b, int64_t V, const int32_t *ids, const int64_t *np, int64_t cap,
+                            cudaStream_t s);
 int min_angle_blocks(int64_t V);
 
 // a10: edge length variation, two passes of deterministic FP64 partials.
@@ -294,6 +295,12 @@ void launch_strip_inversions(int l, StripBuffers &sb, uint32_t max_n, uint32_t i
 struct DeltaCounts {
     uint64_t proper, touching, collinear, dev_lo, dev_hi, occlusion;
 };
+// Device-resident inputs of a move, so that a captured move replays for any
+// count: the number of moved vertices and the totals it updates.
+struct MoveParams {
+    int64_t n;
+    DeltaCounts last;
+};
 struct DeltaAcc {
     uint32_t status;      // ST_* bits from the validation of the moves
     uint32_t n_affected;  // edges with a moved endpoint
@@ -315,10 +322,12 @@ struct DirtySet {
 };
 
 // Marks the moved vertices in `moved` (zero on entry), checking ids and new
-// coordinates (device arrays, n entries) into d->status.
-void launch_delta_validate(const int32_t *ids, const int32_t *xy_new, int64_t n, int64_t V, uint32_t *moved,
-                           DeltaAcc *d, cudaStream_t s);
-void launch_delta_unmark(const int32_t *ids, int64_t n, int64_t V, uint32_t *moved, cudaStream_t s);
+// coordinates (device arrays, *np entries; grids sized for cap) into
+// d->status.
+void launch_delta_validate(const int32_t *ids, const int32_t *xy_new, const int64_t *np, int64_t cap, int64_t V,
+                           uint32_t *moved, DeltaAcc *d, cudaStream_t s);
+void launch_delta_unmark(const int32_t *ids, const int64_t *np, int64_t cap, int64_t V, uint32_t *moved,
+                         cudaStream_t s);
 // Lists the edges with a moved endpoint (count -> d->n_affected); with a
 // dirty set (flag != nullptr), also adds the ones not yet in it.
 void launch_delta_affected(const Buffers &b, int64_t E, const uint32_t *moved, uint32_t *affected, DeltaAcc *d,
@@ -333,16 +342,16 @@ void launch_delta_grid_pass(const Buffers &b, const GridBuffers &g, int k, const
 // occlusion pairs of the moved vertices, on the coordinates in b.xy; the
 // gathered segments (b.seg, b.seg_eid, b.seg_theta, b.acc->n_seg) must be
 // those of the same coordinates.  Does nothing once d->status is set.
-void launch_delta_pass(const Buffers &b, int64_t V, int64_t E, const int32_t *ids, int64_t n, const uint32_t *moved,
-                       const uint32_t *affected, bool crossings, uint32_t ideal, bool occlusion, long long d2,
-                       DeltaAcc *d, int which, cudaStream_t s);
+void launch_delta_pass(const Buffers &b, int64_t V, int64_t E, const int32_t *ids, const int64_t *np,
+                       const uint32_t *moved, const uint32_t *affected, bool crossings, uint32_t ideal, bool occlusion,
+                       long long d2, DeltaAcc *d, int which, cudaStream_t s);
 // Writes the new coordinates of the moved vertices into b.xy (unless
 // d->status reports an invalid move).
-void launch_delta_apply(const int32_t *ids, const int32_t *xy_new, int64_t n, const DeltaAcc *d, Buffers &b,
-                        cudaStream_t s);
-// The evaluation part of b.acc = last - k[0] + k[1] (unless d->status
-// reports an invalid move).
-void launch_delta_combine(const DeltaCounts &last, const DeltaAcc *d, Buffers &b, cudaStream_t s);
+void launch_delta_apply(const int32_t *ids, const int32_t *xy_new, const int64_t *np, int64_t cap, const DeltaAcc *d,
+                        Buffers &b, cudaStream_t s);
+// The evaluation part of b.acc = *last - k[0] + k[1] (last: device memory;
+// nothing when d->status reports an invalid move).
+void launch_delta_combine(const DeltaCounts *last, const DeltaAcc *d, Buffers &b, cudaStream_t s);
 
 // ------------------------------------------------------ differentiable form
 // What the backward needs from the forward, on the device.

@@ -35,8 +35,9 @@ int grid_for(int64_t n, int threads, int max_blocks) {
 
 // Marks the moved vertices; raises ST_BAD_ID for an id outside [0, V) or an
 // id given twice, ST_BAD_COORD for a new coordinate outside [0, 65536).
-__global__ void k_mark_moved(const int32_t *__restrict__ ids, const int2 *__restrict__ xy_new, int64_t n, int64_t V,
-                             uint32_t *__restrict__ moved, DeltaAcc *d) {
+__global__ void k_mark_moved(const int32_t *__restrict__ ids, const int2 *__restrict__ xy_new,
+                             const int64_t *__restrict__ np, int64_t V, uint32_t *__restrict__ moved, DeltaAcc *d) {
+    const int64_t n = *np;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = ids[i];
         const int2 p = xy_new[i];
@@ -49,7 +50,9 @@ __global__ void k_mark_moved(const int32_t *__restrict__ ids, const int2 *__rest
     }
 }
 
-__global__ void k_unmark_moved(const int32_t *__restrict__ ids, int64_t n, int64_t V, uint32_t *__restrict__ moved) {
+__global__ void k_unmark_moved(const int32_t *__restrict__ ids, const int64_t *__restrict__ np, int64_t V,
+                               uint32_t *__restrict__ moved) {
+    const int64_t n = *np;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = ids[i];
         if (v >= 0 && v < V) moved[v] = 0u;
@@ -58,9 +61,10 @@ __global__ void k_unmark_moved(const int32_t *__restrict__ ids, int64_t n, int64
 
 // Writes the new coordinates, unless the validation raised an error (the
 // layout then stays as it was).
-__global__ void k_apply_moves(const int32_t *__restrict__ ids, const int2 *__restrict__ xy_new, int64_t n,
-                              const DeltaAcc *__restrict__ d, int2 *__restrict__ xy) {
+__global__ void k_apply_moves(const int32_t *__restrict__ ids, const int2 *__restrict__ xy_new,
+                              const int64_t *__restrict__ np, const DeltaAcc *__restrict__ d, int2 *__restrict__ xy) {
     if (d->status) return;
+    const int64_t n = *np;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         xy[ids[i]] = xy_new[i];
 }
@@ -68,8 +72,9 @@ __global__ void k_apply_moves(const int32_t *__restrict__ ids, const int2 *__res
 // New totals = last - before + after (the 128-bit angle sum likewise) into
 // the evaluation part of the accumulators, the classified pairs as the
 // grid's candidate count; nothing when the validation raised an error.
-__global__ void k_delta_combine(DeltaCounts last, const DeltaAcc *__restrict__ d, DevAcc *acc) {
+__global__ void k_delta_combine(const DeltaCounts *__restrict__ lastp, const DeltaAcc *__restrict__ d, DevAcc *acc) {
     if (threadIdx.x != 0 || blockIdx.x != 0 || d->status || d->fallback) return;
+    const DeltaCounts last = *lastp;
     const DeltaCounts k0 = d->k[0], k1 = d->k[1];
     const unsigned __int128 dev = (((unsigned __int128)last.dev_hi << 64) | last.dev_lo) -
                                   (((unsigned __int128)k0.dev_hi << 64) | k0.dev_lo) +
@@ -436,12 +441,14 @@ __global__ void __launch_bounds__(256) k_delta_dirty(const int2 *__restrict__ ed
 // squared distance below d2.  A pair of two moved vertices counts once.
 __global__ void __launch_bounds__(DL_COLS) k_delta_occl(const int2 *__restrict__ xy, int64_t V,
                                                         const uint32_t *__restrict__ moved,
-                                                        const int32_t *__restrict__ ids, int64_t n, long long d2,
-                                                        DeltaAcc *d, int which) {
+                                                        const int32_t *__restrict__ ids,
+                                                        const int64_t *__restrict__ np, long long d2, DeltaAcc *d,
+                                                        int which) {
     __shared__ int2 cp[DL_COLS];
     __shared__ int32_t cv[DL_COLS];
     __shared__ uint64_t shu[32];
     if (d->status | d->fallback) return;
+    const int64_t n = *np;
     uint64_t cnt = 0;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = base + threadIdx.x;
@@ -472,29 +479,30 @@ __global__ void __launch_bounds__(DL_COLS) k_delta_occl(const int2 *__restrict__
 
 }  // namespace
 
-void launch_delta_validate(const int32_t *ids, const int32_t *xy_new, int64_t n, int64_t V, uint32_t *moved,
-                           DeltaAcc *d, cudaStream_t s) {
+void launch_delta_validate(const int32_t *ids, const int32_t *xy_new, const int64_t *np, int64_t cap, int64_t V,
+                           uint32_t *moved, DeltaAcc *d, cudaStream_t s) {
     count_launches(1);
-    k_mark_moved<<<grid_for(n, 256, 152 * 4), 256, 0, s>>>(ids, (const int2 *)xy_new, n, V, moved, d);
+    k_mark_moved<<<grid_for(cap, 256, 152 * 4), 256, 0, s>>>(ids, (const int2 *)xy_new, np, V, moved, d);
 }
 
-void launch_delta_unmark(const int32_t *ids, int64_t n, int64_t V, uint32_t *moved, cudaStream_t s) {
+void launch_delta_unmark(const int32_t *ids, const int64_t *np, int64_t cap, int64_t V, uint32_t *moved,
+                         cudaStream_t s) {
     count_launches(1);
-    k_unmark_moved<<<grid_for(n, 256, 152 * 4), 256, 0, s>>>(ids, n, V, moved);
+    k_unmark_moved<<<grid_for(cap, 256, 152 * 4), 256, 0, s>>>(ids, np, V, moved);
 }
 
-void launch_delta_pass(const Buffers &b, int64_t V, int64_t E, const int32_t *ids, int64_t n, const uint32_t *moved,
-                       const uint32_t *affected, bool crossings, uint32_t ideal, bool occlusion, long long d2,
-                       DeltaAcc *d, int which, cudaStream_t s) {
+void launch_delta_pass(const Buffers &b, int64_t V, int64_t E, const int32_t *ids, const int64_t *np,
+                       const uint32_t *moved, const uint32_t *affected, bool crossings, uint32_t ideal, bool occlusion,
+                       long long d2, DeltaAcc *d, int which, cudaStream_t s) {
     if (crossings && E > 0) {
         count_launches(1);
         k_delta_cross<<<grid_for(E, DL_COLS, 152 * 8), DL_COLS, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, b.acc,
                                                                         (const int2 *)b.edges, (const int2 *)b.xy,
                                                                         moved, affected, ideal, d, which);
     }
-    if (occlusion && V > 0 && n > 0) {
+    if (occlusion && V > 0) {
         count_launches(1);
-        k_delta_occl<<<grid_for(V, DL_COLS, 152 * 8), DL_COLS, 0, s>>>((const int2 *)b.xy, V, moved, ids, n, d2, d,
+        k_delta_occl<<<grid_for(V, DL_COLS, 152 * 8), DL_COLS, 0, s>>>((const int2 *)b.xy, V, moved, ids, np, d2, d,
                                                                        which);
     }
 }
@@ -516,14 +524,13 @@ void launch_delta_grid_pass(const Buffers &b, const GridBuffers &g, int k, const
                                           which);
 }
 
-void launch_delta_apply(const int32_t *ids, const int32_t *xy_new, int64_t n, const DeltaAcc *d, Buffers &b,
-                        cudaStream_t s) {
-    if (n <= 0) return;
+void launch_delta_apply(const int32_t *ids, const int32_t *xy_new, const int64_t *np, int64_t cap, const DeltaAcc *d,
+                        Buffers &b, cudaStream_t s) {
     count_launches(1);
-    k_apply_moves<<<grid_for(n, 256, 152 * 4), 256, 0, s>>>(ids, (const int2 *)xy_new, n, d, (int2 *)b.xy);
+    k_apply_moves<<<grid_for(cap, 256, 152 * 4), 256, 0, s>>>(ids, (const int2 *)xy_new, np, d, (int2 *)b.xy);
 }
 
-void launch_delta_combine(const DeltaCounts &last, const DeltaAcc *d, Buffers &b, cudaStream_t s) {
+void launch_delta_combine(const DeltaCounts *last, const DeltaAcc *d, Buffers &b, cudaStream_t s) {
     count_launches(1);
     k_delta_combine<<<1, 32, 0, s>>>(last, d, b.acc);
 }

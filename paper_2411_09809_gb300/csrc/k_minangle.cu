@@ -324,11 +324,12 @@ __global__ void __launch_bounds__(256) k_ma_dirs(const int2 *__restrict__ xy, in
 // After a move: a warp per moved vertex v rewrites the directions and d_v
 // of v and of each neighbour (once each: `touch` flags; one thread per
 // vertex) and flags the min-angle blocks holding them (nb blocks).
-__global__ void k_ma_touch(const int2 *__restrict__ xy, int64_t V, const int32_t *__restrict__ ids, int64_t n,
-                           const uint32_t *__restrict__ off, const int32_t *__restrict__ adj,
-                           uint32_t *__restrict__ touch, uint32_t *__restrict__ nz, int2 *__restrict__ dirs,
-                           double *__restrict__ dv, uint32_t *__restrict__ flag, int nb) {
+__global__ void k_ma_touch(const int2 *__restrict__ xy, int64_t V, const int32_t *__restrict__ ids,
+                           const int64_t *__restrict__ np, const uint32_t *__restrict__ off,
+                           const int32_t *__restrict__ adj, uint32_t *__restrict__ touch, uint32_t *__restrict__ nz,
+                           int2 *__restrict__ dirs, double *__restrict__ dv, uint32_t *__restrict__ flag, int nb) {
     const int lane = threadIdx.x & 31;
+    const int64_t n = *np;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         const int32_t v = ids[i];
@@ -345,10 +346,11 @@ __global__ void k_ma_touch(const int2 *__restrict__ xy, int64_t V, const int32_t
     }
 }
 
-__global__ void k_ma_untouch(int64_t V, const int32_t *__restrict__ ids, int64_t n,
+__global__ void k_ma_untouch(int64_t V, const int32_t *__restrict__ ids, const int64_t *__restrict__ np,
                              const uint32_t *__restrict__ off, const int32_t *__restrict__ adj,
                              uint32_t *__restrict__ touch) {
     const int lane = threadIdx.x & 31;
+    const int64_t n = *np;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         const int32_t v = ids[i];
@@ -427,15 +429,16 @@ void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s) {
                                                            b.ma_cnt);
 }
 
-void launch_min_angle_moved(Buffers &b, int64_t V, const int32_t *ids, int64_t n, cudaStream_t s) {
-    if (V <= 0 || n <= 0) return;
+void launch_min_angle_moved(Buffers &b, int64_t V, const int32_t *ids, const int64_t *np, int64_t cap,
+                            cudaStream_t s) {
+    if (V <= 0) return;
     const int nb = min_angle_blocks(V);
-    const int gw = grid_for(n * 32, 256, 152 * 4);
+    const int gw = grid_for(cap * 32, 256, 152 * 4);
     count_launches(3);
-    k_ma_touch<<<gw, 256, 0, s>>>((const int2 *)b.xy, V, ids, n, b.adj_off, b.adj, b.ma_touch, b.ma_nz, b.dirs,
+    k_ma_touch<<<gw, 256, 0, s>>>((const int2 *)b.xy, V, ids, np, b.adj_off, b.adj, b.ma_touch, b.ma_nz, b.dirs,
                                   b.ma_dv, b.ma_flag, nb);
     k_min_angle_resum<<<nb, MA_THREADS, 0, s>>>(b.ma_dv, V, b.ma_part, b.ma_cnt, b.ma_flag);
-    k_ma_untouch<<<gw, 256, 0, s>>>(V, ids, n, b.adj_off, b.adj, b.ma_touch);
+    k_ma_untouch<<<gw, 256, 0, s>>>(V, ids, np, b.adj_off, b.adj, b.ma_touch);
 }
 
 void launch_batch_min_angle(Buffers &b, const BatchView &bv, int64_t V, int64_t E, cudaStream_t s) {

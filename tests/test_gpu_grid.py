@@ -219,3 +219,38 @@ def test_update_with_invalid_coordinates_reports_erange():
         with pytest.raises(gr.GrError) as ei:
             B.evaluate(gr.GR_METRIC_ALL, IDEAL, 64)
         assert ei.value.status == gr.GR_ERANGE
+
+
+def same_result(a, b, label):
+    assert counts(a) == counts(b), label
+    assert a.crossing.angle_dev_sum == b.crossing.angle_dev_sum, label
+    assert a.occlusion_pairs == b.occlusion_pairs, label
+    assert a.min_angle.M_a == b.min_angle.M_a and a.M_l == b.M_l, label
+    # (the plan may differ: repeated evaluations keep the plan of the previous statistics)
+
+
+@pytest.mark.parametrize("opt", [gr.gr_options(0, 0, 0, 0), gr.gr_options(gr.GR_PATH_GRID, 9, 0, 0),
+                                 gr.gr_options(gr.GR_PATH_ALLPAIRS, 0, gr.GR_PATH_ALLPAIRS, 0)])
+def test_replayed_evaluations_follow_every_change(opt):
+    # repeated evaluations replay a captured graph; a change of metrics,
+    # parameters, profiling or buffers must give what a fresh layout gives
+    rng = np.random.default_rng(31)
+    V = 6000
+    xy0 = synth.uniform_points(rng, V)
+    e = synth.add_random_edges(rng, V, synth.knn_edges(xy0, 3, 12000), 600)
+    far = synth.uniform_points(rng, V)
+    calls = [(xy0, gr.GR_METRIC_ALL, IDEAL, 64, False), (xy0, gr.GR_METRIC_ALL, IDEAL, 64, False),
+             (xy0, gr.GR_METRIC_ALL, IDEAL, 128, False), (xy0, gr.GR_METRIC_CROSSINGS, IDEAL, 128, False),
+             (xy0, gr.GR_METRIC_ALL, math.radians(45), 64, True), (xy0, gr.GR_METRIC_ALL, math.radians(45), 64, True),
+             (far, gr.GR_METRIC_ALL, IDEAL, 64, False),  # long edges: buffers outgrown, re-run, new capture
+             (far, gr.GR_METRIC_ALL, IDEAL, 64, False), (xy0, gr.GR_METRIC_OCCLUSION | gr.GR_METRIC_MIN_ANGLE,
+                                                        IDEAL, 300, False), (xy0, gr.GR_METRIC_ALL, IDEAL, 64, False)]
+    with gr.Layout(xy0, e, opt) as L:
+        for i, (xy, m, ideal, d, prof) in enumerate(calls):
+            gr.gr_profile_enable(L.handle, prof)
+            L.update(xy)
+            r = L.evaluate(m, ideal, d)
+            with gr.Layout(xy, e, opt) as F:
+                same_result(r, F.evaluate(m, ideal, d), f"call {i}")
+            if prof:
+                assert L.profile()["finalize"][1] > 0
