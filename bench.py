@@ -659,6 +659,10 @@ def run_moves(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = oracle_move_steps(L, 3)
+        line["cpu_baseline"] = {"value": 1.0 / cb["step_s"], "unit": "evaluations/s", "cores": cb["cores"],
+                                "kind": "oracle", "sample": cb["sample"]}
     print(json.dumps(line), flush=True)
 
 
@@ -826,6 +830,53 @@ def run_reference_strips(args):
     print(json.dumps(line), flush=True)
 
 
+def oracle_move_steps(L, n: int, warmup: int = 1) -> dict:
+    """The oracle's form of a move, timed n times: the crossings of the
+    affected edges (a moved endpoint) against all edges before and after the
+    move, plus the minimum angle and edge length variation in full
+    (occlusion left out)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(20241115 + 5)
+    xy = L.xy.copy()
+
+    def one():
+        ids = rng.choice(L.V, size=MOVES_PER_STEP, replace=False)
+        aff = np.nonzero(np.isin(L.edges[:, 0], ids) | np.isin(L.edges[:, 1], ids))[0]
+        t0 = time.perf_counter()
+        oracle.crossings_of_edges(xy, L.edges, aff)
+        xy[ids] = rng.integers(0, 65536, size=(len(ids), 2)).astype(np.int32)
+        oracle.crossings_of_edges(xy, L.edges, aff)
+        oracle.min_angle(xy, L.edges)
+        oracle.edge_length_variation(xy, L.edges)
+        return time.perf_counter() - t0, len(aff)
+
+    for _ in range(warmup):
+        one()
+    runs = [one() for _ in range(n)]
+    return {"step_s": statistics.mean(r[0] for r in runs), "cores": oracle.num_threads(),
+            "sample": f"the oracle's incremental form of a move, {n} moves: crossings of the ~{runs[0][1]} "
+                      f"affected edges against all {L.E} edges before and after, minimum angle and edge "
+                      f"length variation in full (occlusion left out)"}
+
+
+def run_reference_moves(args):
+    L, d = make_workload("moves")
+    cb = oracle_move_steps(L, args.steps, args.warmup)
+    step_s = cb["step_s"]
+    line = {
+        "impl": "reference", "metric": "incremental evaluations/s", "value": 1.0 / step_s, "unit": "evaluations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": dict(workload_config(L, d, "moves"), workload=f"moves_{MOVES_PER_STEP}_of_{L.name}"),
+        "cpu_baseline": {"value": 1.0 / step_s, "unit": "evaluations/s", "cores": cb["cores"], "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": 1.0 / step_s, "unit": "evaluations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle (plain C brute force) on the host cores."""
     if rank != 0:
@@ -838,6 +889,9 @@ def run_reference(args, rank, world):
         return
     if args.workload == "strips":
         run_reference_strips(args)
+        return
+    if args.workload == "moves":
+        run_reference_moves(args)
         return
     L, d = make_workload(args.workload)
     E = L.E
