@@ -50,6 +50,7 @@ WORKLOADS = {
     "differentiable": ("differentiable_layout", 0),
     "moves": ("large_sparse_layout", 64),
     "strips": ("dense_long_edge_layout", 0),
+    "per_edge": ("large_sparse_layout", 0),
 }
 MOVES_PER_STEP = 16
 STRIP_WIDTH = 64          # vertical strips of the approximate algorithm (Sec. 3.2.2)
@@ -236,7 +237,7 @@ def cpu_oracle_diff_step(L, budget_s: float) -> dict:
                       f"step ({step_s:.1f} s)"}
 
 
-def cpu_oracle_step(L, d, budget_s: float, rng_seed: int = 0) -> dict:
+def cpu_oracle_step(L, d, budget_s: float, rng_seed: int = 0, crossings_only: bool = False) -> dict:
     """Times the oracle on a bounded sample of one step and scales it to the full
     step: crossings of S sampled edges against all edges, occlusion on the first
     V_s vertices, minimum angle and edge length variation in full."""
@@ -246,8 +247,9 @@ def cpu_oracle_step(L, d, budget_s: float, rng_seed: int = 0) -> dict:
     E, V = L.E, L.V
     rng = np.random.default_rng(rng_seed)
     t0 = time.perf_counter()
-    oracle.edge_length_variation(L.xy, L.edges)
-    oracle.min_angle(L.xy, L.edges)
+    if not crossings_only:
+        oracle.edge_length_variation(L.xy, L.edges)
+        oracle.min_angle(L.xy, L.edges)
     t_lin = time.perf_counter() - t0
     # calibrate crossings on growing samples, then take one of ~budget/2 seconds
     S, t_small = 16, 0.0
@@ -264,12 +266,19 @@ def cpu_oracle_step(L, d, budget_s: float, rng_seed: int = 0) -> dict:
     oracle.crossings_of_edges(L.xy, L.edges, sample)
     t_cross = time.perf_counter() - t0
     cross_full = t_cross * (E * (E - 1) / 2) / (S2 * (E - 1))
-    Vs = min(V, 20000)
+    Vs = 0 if crossings_only else min(V, 20000)
     t0 = time.perf_counter()
-    oracle.node_occlusion(L.xy[:Vs], d)
+    if Vs:
+        oracle.node_occlusion(L.xy[:Vs], d)
     t_occ = time.perf_counter() - t0
-    occ_full = t_occ * (V * (V - 1) / 2) / max(1, Vs * (Vs - 1) / 2)
+    occ_full = t_occ * (V * (V - 1) / 2) / max(1, Vs * (Vs - 1) / 2) if Vs else 0.0
     step_s = cross_full + occ_full + t_lin
+    if crossings_only:
+        return {"step_s": step_s, "cores": oracle.num_threads(),
+                "sample": f"per-edge crossings (oracle.crossings_of_edges) of {S2} sampled edges against all "
+                          f"{E} edges ({S2 * (E - 1):.3g} pair tests, {t_cross:.1f} s), scaled to all edges "
+                          f"({step_s:.1f} s)",
+                "measured_s": t_small + t_cross}
     return {"step_s": step_s, "cores": oracle.num_threads(),
             "sample": f"crossings of {S2} sampled edges against all {E} edges "
                       f"({S2 * (E - 1):.3g} pair tests, {t_cross:.1f} s), occlusion of the first {Vs} "
@@ -808,6 +817,127 @@ def run_strips(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_per_edge(args, rank, world, local_rank):
+    """Per-edge workload (the per-segment quantities of Sec. 3.2.3 / Eq. 1, NEXT-2):
+    on the large sparse layout, one step = gr_layout_update + gr_crossings_per_edge
+    (every edge's proper, touching and collinear counts and its sum of
+    |ideal - a_c|, into device arrays).  The crossing-only evaluation of the same
+    layout is timed beside it."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_09809_gb300 import build as gr_build, gr
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        if rank == 0:
+            gr_build.build()
+        dist.barrier()
+    else:
+        gr_build.build()
+    gr.load()
+    L, _ = make_workload("per_edge")
+    dev = torch.device("cuda", local_rank)
+    xy = torch.from_numpy(L.xy).to(dev)
+    edges = torch.from_numpy(L.edges).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lay = gr.Layout(xy, edges, gr.gr_options(0, 0, 0, 1, 0), stream=stream.cuda_stream)
+    counts = torch.zeros((L.E, 3), dtype=torch.int64, device=dev)
+    devsum = torch.zeros(L.E, dtype=torch.float64, device=dev)
+    res = lay.evaluate(gr.GR_METRIC_CROSSINGS, IDEAL, 0)
+
+    def timed(fn, k):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        for i in range(k):
+            flush.fill_(i)
+            starts[i].record(stream)
+            fn()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+    def step():
+        lay.update(xy)
+        gr.gr_crossings_per_edge(lay.handle, IDEAL, counts, devsum)
+
+    timed(step, args.warmup)
+    lay.profile(reset=True)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = gr.gr_kernel_launches()
+    ms = timed(step, args.steps)
+    launches = gr.gr_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = lay.profile()
+
+    def plain():
+        lay.update(xy)
+        lay.evaluate(gr.GR_METRIC_CROSSINGS, IDEAL, 0)
+
+    timed(plain, 3)
+    plain_ms = timed(plain, args.steps)
+    if world > 1:
+        t = torch.tensor([ms, plain_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, plain_ms = (float(x) for x in t.tolist())
+    # end to end: coordinates from pinned host memory, the per-edge arrays read back
+    hxy = torch.from_numpy(L.xy).pin_memory()
+    hc = torch.empty((L.E, 3), dtype=torch.int64).pin_memory()
+    hd = torch.empty(L.E, dtype=torch.float64).pin_memory()
+    e2e_s = []
+    for i in range(0 if args.no_e2e else args.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gr.gr_layout_update(lay.handle, hxy, None)
+        gr.gr_crossings_per_edge(lay.handle, IDEAL, counts, devsum)
+        hc.copy_(counts, non_blocking=True)
+        hd.copy_(devsum, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_ms = statistics.mean(e2e_s) * 1e3 if e2e_s else float("nan")
+    tot = counts.sum(dim=0).tolist()
+    lay.close()
+    if rank != 0:
+        return
+    E = L.E
+    pairs = E * (E - 1) / 2
+    peaks, peak_kind = load_peaks()
+    rf = roofline(res, prof, E - res.crossing.c.zero_length_edges, peaks, peak_kind, "per_edge")
+    rf["traffic"] = None  # the per-edge form of the kernel has no committed capture
+    rf["kernel"] += " (per-edge form: + 4 atomics per E_c pair)"
+    line = {
+        "metric": "edge-pair tests/s", "value": world * pairs / (ms / 1e3), "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"per_edge_of_{L.name}", "V": L.V, "E": E, "ideal_deg": 70.0,
+                   "step": "gr_layout_update + gr_crossings_per_edge (per-edge counts and angle sums, device arrays)",
+                   "inputs": "seeded synthetic (paper_2411_09809_gb300.synth)",
+                   "l2": "256 MiB write between timed steps (inputs are smaller than L2)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "crossings_only_evaluation_ms": plain_ms, "per_edge_over_plain": ms / plain_ms,
+        "results": {"sum_proper": tot[0] // 2, "sum_touching": tot[1] // 2, "E_c": res.crossing.c.crossings},
+        "phase_ms": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]},
+        "roofline": rf,
+        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": L.V * 8, "d2h_bytes_per_step": E * 32},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_step(L, 0, args.cpu_budget, crossings_only=True)
+        line["cpu_baseline"] = {"value": pairs / cb["step_s"], "unit": "pairs/s", "cores": cb["cores"],
+                                "kind": "oracle", "sample": cb["sample"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_strips(args):
     L, _ = make_workload("strips")
     l = args.strip_width
@@ -897,9 +1027,10 @@ def run_reference(args, rank, world):
     E = L.E
     pairs = E * (E - 1) / 2
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    xo = args.workload == "per_edge"  # the per-edge crossing tallies only
     for _ in range(args.warmup):
-        cpu_oracle_step(L, d, budget / 4)
-    steps = [cpu_oracle_step(L, d, budget, rng_seed=i + 1) for i in range(args.steps)]
+        cpu_oracle_step(L, d, budget / 4, crossings_only=xo)
+    steps = [cpu_oracle_step(L, d, budget, rng_seed=i + 1, crossings_only=xo) for i in range(args.steps)]
     step_s = statistics.mean(s["step_s"] for s in steps)
     value = pairs / step_s
     line = {
@@ -1070,6 +1201,8 @@ def main():
             run_moves(args, rank, world, local_rank)
         elif args.workload == "strips":
             run_strips(args, rank, world, local_rank)
+        elif args.workload == "per_edge":
+            run_per_edge(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

@@ -1215,7 +1215,9 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     if (cp.grid && L->h_acc->n_seg >= 2) {
         const int C = (65536 >> cp.k) * (65536 >> cp.k);
         if ((st2 = ensure_cells(L, C)) != GR_OK) return st2;
+        phase_begin(L, GR_PHASE_CROSS_BIN);
         launch_grid_count(b, E, L->g, cp.k, cp.split, s);
+        phase_end(L, GR_PHASE_CROSS_BIN);
         GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
         GR_CU(cudaStreamSynchronize(s));
         if ((st2 = status_to_error(L->h_acc->eval_status)) != GR_OK) return st2;
@@ -1223,16 +1225,23 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     }
     if (cp.grid && L->h_acc->n_seg >= 2) {
         if ((st2 = ensure_records(L, L->h_acc->records, L->h_acc->grid_items)) != GR_OK) return st2;
+        phase_begin(L, GR_PHASE_CROSS_SCATTER);
         launch_grid_scatter(b, E, L->g, cp.k, cp.split, s);
+        phase_end(L, GR_PHASE_CROSS_SCATTER);
+        phase_begin(L, GR_PHASE_CROSS_PAIRS);
         launch_grid_pairs(b, L->g, cp.k, L->h_acc->grid_items, ideal_units(ideal), pe, s);
         if (cp.split) launch_grid_long_pairs(b, L->g, L->h_acc->n_long, ideal_units(ideal), pe, s);
+        phase_end(L, GR_PHASE_CROSS_PAIRS);
     } else {
+        phase_begin(L, GR_PHASE_CROSS_PAIRS);
         launch_crossings_allpairs(b, E, ideal_units(ideal), pe, s);
+        phase_end(L, GR_PHASE_CROSS_PAIRS);
     }
     launch_per_edge_export(pe.dev, E, s);
     GR_CU(cudaGetLastError());
     GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
     GR_CU(cudaStreamSynchronize(s));
+    phase_collect(L);
     return status_to_error(L->h_acc->status | L->h_acc->eval_status);
 }
 
