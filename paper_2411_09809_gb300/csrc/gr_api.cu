@@ -929,13 +929,8 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     }
     int32_t occl_path = 0;
     if (metrics & GR_METRIC_OCCLUSION) {
-        // grid of side >= d for many vertices; all-pairs tiles for few, or when
-        // d is so large that the grid has at most 4 x 4 cells
         const int ko = occl_cell_log2(d);
-        bool grid;
-        if (L->opt.occlusion_path == GR_PATH_GRID) grid = ko <= 16;
-        else if (L->opt.occlusion_path == GR_PATH_ALLPAIRS) grid = false;
-        else grid = V > 4096 && ko <= 14;
+        const bool grid = occlusion_grid(L, ko);
         if (grid && V >= 2 && d > 0) {
             const int C = (65536 >> ko) * (65536 >> ko);
             if ((st = ensure_ocells(L, C)) != GR_OK) return st;
