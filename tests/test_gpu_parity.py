@@ -224,3 +224,33 @@ def test_single_metric_entry_points():
         assert gr.gr_min_angle(lay.handle).M_a == pytest.approx(oracle.min_angle(L.xy, L.edges).M_a, rel=REL)
         assert gr.gr_edge_length_variation(lay.handle) == pytest.approx(
             oracle.edge_length_variation(L.xy, L.edges), rel=REL)
+
+
+def test_empty_and_trivial_layouts_on_every_entry_point():
+    # repeated evaluations (the replayed graph), the strip estimate and moves on
+    # layouts with no edge, one vertex, or only coincident points
+    z = np.zeros((0, 2), np.int32)
+    cases = [(z, z), (np.array([[7, 7]], np.int32), z),
+             (np.array([[5, 5], [5, 5], [9, 9]], np.int32), np.array([[0, 1], [1, 2]], np.int32)),
+             (np.array([[0, 0], [65535, 65535], [0, 65535], [65535, 0]], np.int32),
+              np.array([[0, 1], [2, 3]], np.int32))]
+    for xy, e in cases:
+        with gr.Layout(xy, e) as L:
+            for _ in range(3):
+                r = L.evaluate(gr.GR_METRIC_ALL, IDEAL, 3)
+                if len(xy):
+                    check_all(xy, e, 3, r)
+                else:
+                    assert (r.crossing.c.crossings, r.occlusion_pairs, r.M_l) == (0, 0, 0.0)
+            for w in (1, 1000, 65535):
+                st = L.strips(w, gr.GR_STRIP_BOTH, IDEAL)
+                assert st.crossings == oracle.strip_crossings(xy, e, w, 2, IDEAL).crossings
+            if len(xy):
+                ids = np.array([0], np.int32)
+                new = np.array([[65535, 0]], np.int32)
+                r = L.move(ids, new, gr.GR_METRIC_ALL, IDEAL, 3)
+                moved = xy.copy()
+                moved[0] = new[0]
+                check_all(moved, e, 3, r)
+            r = L.move(np.zeros(0, np.int32), np.zeros((0, 2), np.int32), gr.GR_METRIC_ALL, IDEAL, 3)
+            assert r.crossing.c.crossings == (oracle.crossings(moved, e).crossings if len(xy) else 0)
