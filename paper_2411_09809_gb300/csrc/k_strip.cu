@@ -534,14 +534,11 @@ void launch_strip_span(const Buffers &b, int64_t E, int l, int orient, const Str
 
 void launch_strip_sort(const Buffers &b, int64_t E, int l, int orient, StripBuffers &sb, uint32_t max_n,
                        cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_strip_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-        cudaFuncSetAttribute(k_strip_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-        cudaFuncSetAttribute(k_strip_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-        cudaFuncSetAttribute(k_strip_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-        attr_set = true;
-    }
+    // (cheap, and set on every call: the current device may change between calls)
+    cudaFuncSetAttribute(k_strip_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_strip_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_strip_merge<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    cudaFuncSetAttribute(k_strip_merge<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
     const int ns = strip_count(l);
     const uint64_t R = sb.records;
     sb.cur = 0;
