@@ -163,6 +163,21 @@ gr_status gr_layout_destroy(gr_layout *layout);
 gr_status gr_evaluate(gr_layout *layout, uint32_t metrics, const gr_params *params,
                       gr_result *out);
 
+/* gr_evaluate without any host synchronisation: the evaluation is ordered
+ * after the work already queued on `stream` (NULL: the layout's stream), and
+ * the gr_result is written to `d_result`, DEVICE memory owned by the caller,
+ * before anything queued on `stream` afterwards runs.  The call can itself be
+ * captured into the caller's CUDA graph (it replays the layout's own graph
+ * of this configuration) once a gr_evaluate of the layout with the same
+ * metrics and parameters has planned it and sized its buffers; before that,
+ * and whenever the layout's plan changes, the call synchronises once to plan.
+ * A result whose `metrics` field is 0 reports a failed evaluation (invalid
+ * input, or inputs that outgrew the planned buffers): call gr_evaluate for
+ * the error.  Incremental moves after an asynchronous evaluation start with
+ * a full evaluation.  GR_COORD_I32 layouts only. */
+gr_status gr_evaluate_async(gr_layout *layout, uint32_t metrics, const gr_params *params, gr_result *d_result,
+                            gr_stream_t stream);
+
 /* Node occlusion N_c (Sec. 2.1, Algorithm 1): unordered vertex pairs whose
  * distance is < d, d = 2r.  Strict inequality; d = 0 gives 0. */
 gr_status gr_node_occlusion(gr_layout *layout, int64_t d, int64_t *out_pairs);
@@ -290,6 +305,15 @@ gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_of
 gr_status gr_batch_update(gr_batch *batch, const void *xy, const int32_t *edges);
 gr_status gr_batch_evaluate(gr_batch *batch, uint32_t metrics, const gr_params *params, gr_result *out);
 gr_status gr_batch_destroy(gr_batch *batch);
+/* gr_batch_evaluate without any host synchronisation: ordered after the work
+ * queued on `stream` (NULL: the batch's stream), results written to
+ * `d_results` (DEVICE memory, [n_layouts] gr_result) before anything queued
+ * on `stream` afterwards runs; capturable into the caller's CUDA graph once a
+ * gr_batch_evaluate with the same metrics and parameters has run.  Results
+ * whose `metrics` field is 0 report a failed evaluation (gr_batch_evaluate
+ * gives the error). */
+gr_status gr_batch_evaluate_async(gr_batch *batch, uint32_t metrics, const gr_params *params, gr_result *d_results,
+                                  gr_stream_t stream);
 
 /* ------------------------------------------------------------- tracing
  * Phase timing: when enabled on a layout, every gr_layout_update,

@@ -377,8 +377,11 @@ __global__ void __launch_bounds__(256) k_batch_finalize(const ItemPart *__restri
                                                         const uint32_t *__restrict__ long_off,
                                                         const uint64_t *__restrict__ occl, int64_t L, uint32_t metrics,
                                                         double ideal, int64_t d, uint64_t cap,
+                                                        const DevAcc *__restrict__ acc,
                                                         gr_result *__restrict__ res) {
     __shared__ uint64_t sh[32];
+    // a failed evaluation (invalid input, outgrown buffers) is marked by metrics = 0 in every result
+    const bool failed = (acc->status | acc->eval_status) != 0 || (acc->grid_flags & GF_ITEMS_OVERFLOW) != 0;
     for (int64_t l = blockIdx.x; l < L; l += gridDim.x) {
         uint64_t p = 0, t = 0, c = 0, dv = 0;
         if (metrics & GR_METRIC_CROSSINGS) {
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(256) k_batch_finalize(const ItemPart *__restri
         dv = block_sum<uint64_t>(dv, sh);
         if (threadIdx.x != 0) continue;
         gr_result &r = res[l];
-        r.metrics = metrics;
+        r.metrics = failed ? 0u : metrics;
         if (metrics & GR_METRIC_CROSSINGS) {
             p += ll[4 * l + 0];
             t += ll[4 * l + 1];
@@ -447,7 +450,9 @@ thread_local std::string g_batch_err;
 struct gr_batch {
     int64_t L = 0, V = 0, E = 0;
     cudaStream_t stream = nullptr;  // the caller's stream (may be the legacy default stream)
-    cudaStream_t cap = nullptr;     // the batch's own stream: evaluations are captured and replayed here
+    cudaStream_t cap = nullptr;     // the batch's own stream: evaluations are replayed here
+    cudaStream_t cs = nullptr;      // and captured here (never joined to a caller's stream)
+    cudaEvent_t ev_in2 = nullptr, ev_out = nullptr;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_in = nullptr, ev_fork = nullptr, ev_join = nullptr;
     int64_t graph_kernels = 0;      // kernels per replay (for the launch counter)
@@ -571,6 +576,9 @@ void free_batch(gr_batch *B) {
     if (B->ev_join) cudaEventDestroy(B->ev_join);
     if (B->side) cudaStreamDestroy(B->side);
     if (B->cap) cudaStreamDestroy(B->cap);
+    if (B->cs) cudaStreamDestroy(B->cs);
+    if (B->ev_in2) cudaEventDestroy(B->ev_in2);
+    if (B->ev_out) cudaEventDestroy(B->ev_out);
     delete B;
 }
 
@@ -730,9 +738,9 @@ gr_status plan_occlusion(gr_batch *B, int64_t d) {
     return GR_OK;
 }
 
-// One evaluation, stream-ordered (also what the CUDA graph captures).
-void enqueue_evaluate(gr_batch *B, uint32_t metrics, double ideal, uint32_t ideal_u, int64_t d) {
-    cudaStream_t s = B->cap, t = B->side;
+// One evaluation, stream-ordered on s (what the CUDA graph captures).
+void enqueue_evaluate(gr_batch *B, cudaStream_t s, uint32_t metrics, double ideal, uint32_t ideal_u, int64_t d) {
+    cudaStream_t t = B->side;
     Buffers &b = B->b;
     const BatchView bv = view(B);
     cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0, sizeof(DevAcc) - offsetof(DevAcc, eval_status), s);
@@ -752,7 +760,7 @@ void enqueue_evaluate(gr_batch *B, uint32_t metrics, double ideal, uint32_t idea
     count_launches(1);
     k_batch_finalize<<<grid_for(B->L, 1, 152 * 16), 256, 0, s>>>(B->parts, B->item_off, B->cell_off, B->d_cbase, B->d_k,
                                                                  B->d_work, B->d_ll, B->long_off, B->occl, B->L,
-                                                                 metrics, ideal, d, B->items_cap, B->d_res);
+                                                                 metrics, ideal, d, B->items_cap, b.acc, B->d_res);
 }
 
 gr_status enqueue_inputs(gr_batch *B, const void *xy, const int32_t *edges) {
@@ -971,6 +979,9 @@ gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_of
     B_CU2(cudaMallocHost((void **)&B->h_acc, sizeof(DevAcc)));
     B_CU2(cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking));
     B_CU2(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+    B_CU2(cudaStreamCreateWithFlags(&B->cs, cudaStreamNonBlocking));
+    B_CU2(cudaEventCreateWithFlags(&B->ev_in2, cudaEventDisableTiming));
+    B_CU2(cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming));
     B_CU2(cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming));
     B_CU2(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
     B_CU2(cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming));
@@ -1023,6 +1034,86 @@ gr_status gr_batch_update(gr_batch *B, const void *xy, const int32_t *edges) {
     return enqueue_inputs(B, xy, edges);
 }
 
+namespace {
+
+// The graph of one evaluation with these metrics and parameters, captured on
+// the batch's capture stream when it is missing or was made for others.
+gr_status ensure_graph(gr_batch *B, uint32_t metrics, double ideal, uint32_t ideal_u, int64_t d) {
+    if (B->exec && B->g_metrics == metrics && B->g_ideal == ideal_u && B->g_d == d) return GR_OK;
+    drop_graph(B);
+    cudaGraph_t graph;
+    const int64_t k0 = gr_kernel_launches();
+    B_CU(cudaStreamBeginCapture(B->cs, cudaStreamCaptureModeRelaxed));
+    enqueue_evaluate(B, B->cs, metrics, ideal, ideal_u, d);
+    const cudaError_t ce = cudaStreamEndCapture(B->cs, &graph);
+    B->graph_kernels = gr_kernel_launches() - k0;
+    count_launches(-(int)B->graph_kernels);  // counted when replayed, not when captured
+    if (ce != cudaSuccess) return bcuda(ce, "capturing the batch evaluation");
+    const cudaError_t ie = cudaGraphInstantiate(&B->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        B->exec = nullptr;
+        return bcuda(ie, "instantiating the batch graph");
+    }
+    B->g_metrics = metrics;
+    B->g_ideal = ideal_u;
+    B->g_d = d;
+    return GR_OK;
+}
+
+gr_status batch_params(const gr_params *params, double *ideal, int64_t *d, uint32_t *ideal_u) {
+    *ideal = 7.0 * M_PI / 18.0;
+    *d = 0;
+    if (params) {
+        if (params->ideal_rad > 0.0) *ideal = params->ideal_rad;
+        *d = params->occlusion_d;
+    }
+    if (!(*ideal <= M_PI / 2 + 1e-15)) return bfail(GR_EINVAL, "ideal angle must be in (0, pi/2]");
+    if (*d < 0) return bfail(GR_EINVAL, "occlusion diameter d must be >= 0");
+    *ideal_u = (uint32_t)llrint(*ideal / M_PI * 4294967296.0);
+    return GR_OK;
+}
+
+}  // namespace
+
+gr_status gr_batch_evaluate_async(gr_batch *B, uint32_t metrics, const gr_params *params, gr_result *d_results,
+                                  gr_stream_t stream) {
+    set_last_error("");
+    if (!B || !d_results) return bfail(GR_EINVAL, "NULL argument");
+    if (metrics & ~GR_METRIC_ALL) return bfail(GR_EINVAL, "unknown metric bits");
+    if (!is_device_ptr(d_results)) return bfail(GR_EINVAL, "d_results must be device memory");
+    double ideal;
+    int64_t d;
+    uint32_t ideal_u;
+    gr_status st = batch_params(params, &ideal, &d, &ideal_u);
+    if (st != GR_OK) return st;
+    if ((st = plan_occlusion(B, d)) != GR_OK) return st;
+    cudaStream_t after = stream ? (cudaStream_t)stream : B->stream, c = B->cap;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (after != B->stream) B_CU(cudaStreamIsCapturing(after, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        // the caller's stream is being captured: the evaluation's steps are captured there directly
+        enqueue_evaluate(B, after, metrics, ideal, ideal_u, d);
+        B_CU(cudaMemcpyAsync(d_results, B->d_res, sizeof(gr_result) * B->L, cudaMemcpyDeviceToDevice, after));
+        return GR_OK;
+    }
+    if ((st = ensure_graph(B, metrics, ideal, ideal_u, d)) != GR_OK) return st;
+    // after the inputs (the batch's stream) and the caller's work, before what follows on the caller's stream
+    B_CU(cudaEventRecord(B->ev_in, B->stream));
+    B_CU(cudaStreamWaitEvent(c, B->ev_in, 0));
+    if (after != B->stream) {
+        B_CU(cudaEventRecord(B->ev_in2, after));
+        B_CU(cudaStreamWaitEvent(c, B->ev_in2, 0));
+    }
+    B_CU(cudaGraphLaunch(B->exec, c));
+    count_launches((int)B->graph_kernels);
+    B_CU(cudaMemcpyAsync(d_results, B->d_res, sizeof(gr_result) * B->L, cudaMemcpyDeviceToDevice, c));
+    B_CU(cudaEventRecord(B->ev_out, c));
+    B_CU(cudaStreamWaitEvent(after, B->ev_out, 0));
+    if (after != B->stream) B_CU(cudaStreamWaitEvent(B->stream, B->ev_out, 0));
+    return GR_OK;
+}
+
 gr_status gr_batch_evaluate(gr_batch *B, uint32_t metrics, const gr_params *params, gr_result *out) {
     set_last_error("");
     if (!B || !out) return bfail(GR_EINVAL, "NULL argument");
@@ -1042,26 +1133,7 @@ gr_status gr_batch_evaluate(gr_batch *B, uint32_t metrics, const gr_params *para
     B_CU(cudaEventRecord(B->ev_in, B->stream));  // inputs enqueued on the caller's stream come first
     B_CU(cudaStreamWaitEvent(c, B->ev_in, 0));
     for (int attempt = 0; attempt < 2; ++attempt) {
-        if (!B->exec || B->g_metrics != metrics || B->g_ideal != ideal_u || B->g_d != d) {
-            drop_graph(B);
-            cudaGraph_t graph;
-            const int64_t k0 = gr_kernel_launches();
-            B_CU(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
-            enqueue_evaluate(B, metrics, ideal, ideal_u, d);
-            const cudaError_t ce = cudaStreamEndCapture(c, &graph);
-            B->graph_kernels = gr_kernel_launches() - k0;
-            count_launches(-(int)B->graph_kernels);  // counted when replayed, not when captured
-            if (ce != cudaSuccess) return bcuda(ce, "capturing the batch evaluation");
-            const cudaError_t ie = cudaGraphInstantiate(&B->exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ie != cudaSuccess) {
-                B->exec = nullptr;
-                return bcuda(ie, "instantiating the batch graph");
-            }
-            B->g_metrics = metrics;
-            B->g_ideal = ideal_u;
-            B->g_d = d;
-        }
+        if ((st = ensure_graph(B, metrics, ideal, ideal_u, d)) != GR_OK) return st;
         B_CU(cudaGraphLaunch(B->exec, c));
         count_launches((int)B->graph_kernels);
         B_CU(cudaMemcpyAsync(B->h_acc, B->b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, c));

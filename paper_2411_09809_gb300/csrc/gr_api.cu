@@ -68,8 +68,9 @@ struct gr_layout {
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;      // occlusion, min angle, ELV run here, beside the crossings
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaStream_t gstream = nullptr;   // evaluation graphs are captured and replayed here
-    cudaEvent_t ev_gin = nullptr, ev_gout = nullptr;
+    cudaStream_t gstream = nullptr;   // evaluation and move graphs are replayed here
+    cudaStream_t cstream = nullptr;   // and captured here (never joined to a caller's stream)
+    cudaEvent_t ev_gin = nullptr, ev_gin2 = nullptr, ev_gout = nullptr;
     gr_options opt{};
     Buffers b;
     GridBuffers g;
@@ -136,6 +137,7 @@ struct gr_layout {
         double ideal = 0.0;
         int64_t d = 0;
         bool x_on = false, grid = false, split = false, o_on = false, ogrid = false, profiling = false;
+        bool readback = true;  // the graph ends with the read-back copies to pinned host memory
         int k = 0, ko = 0;
         const void *bufs[8] = {};
         uint64_t caps[3] = {};
@@ -197,7 +199,9 @@ void free_layout(gr_layout *L) {
     if (L->ev_join) cudaEventDestroy(L->ev_join);
     if (L->side) cudaStreamDestroy(L->side);
     if (L->gstream) cudaStreamDestroy(L->gstream);
+    if (L->cstream) cudaStreamDestroy(L->cstream);
     if (L->ev_gin) cudaEventDestroy(L->ev_gin);
+    if (L->ev_gin2) cudaEventDestroy(L->ev_gin2);
     if (L->ev_gout) cudaEventDestroy(L->ev_gout);
     if (L->h_result) cudaFreeHost(L->h_result);
     if (L->h_acc) cudaFreeHost(L->h_acc);
@@ -254,7 +258,9 @@ gr_status alloc_layout(gr_layout *L) {
 #undef GR_TRY
     GR_CU(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
     GR_CU(cudaStreamCreateWithFlags(&L->gstream, cudaStreamNonBlocking));
+    GR_CU(cudaStreamCreateWithFlags(&L->cstream, cudaStreamNonBlocking));
     GR_CU(cudaEventCreateWithFlags(&L->ev_gin, cudaEventDisableTiming));
+    GR_CU(cudaEventCreateWithFlags(&L->ev_gin2, cudaEventDisableTiming));
     GR_CU(cudaEventCreateWithFlags(&L->ev_gout, cudaEventDisableTiming));
     GR_CU(cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming));
     GR_CU(cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming));
@@ -688,6 +694,13 @@ gr_status finish_evaluate(gr_layout *L, uint32_t metrics, const gr_params *param
     *out = *L->h_result;
     remember_totals(L, metrics, ideal_units(ideal), d);
     if (path == GR_PATH_GRID) L->dgrid_k = k;
+    if (!L->fast_ok && path != GR_PATH_GRID) {
+        // no grid buffers to size: later evaluations may take the fast path (a grid plan then
+        // does not match fast_k and runs synchronised once)
+        L->fast_ok = true;
+        L->fast_k = -1;
+        L->fast_split = false;
+    }
     return GR_OK;
 }
 
@@ -732,7 +745,7 @@ gr_status plan_fast(gr_layout *L, uint32_t metrics, int64_t d, uint64_t n_seg, F
 // Enqueues a fast-path evaluation (no read-back before the end): the same
 // steps as the synchronised path of gr_evaluate.
 void enqueue_fast(gr_layout *L, cudaStream_t s, uint32_t metrics, double ideal, int64_t d, const FastPlan &fp,
-                  int32_t *path, int32_t *occl_path, int64_t *pairs_tested) {
+                  bool readback, int32_t *path, int32_t *occl_path, int64_t *pairs_tested) {
     cudaStream_t t = L->side;
     Buffers &b = L->b;
     const int64_t V = L->V, E = L->E;
@@ -794,15 +807,31 @@ void enqueue_fast(gr_layout *L, cudaStream_t s, uint32_t metrics, double ideal, 
     phase_begin(L, GR_PHASE_FINALIZE, s);
     launch_finalize(b, metrics, E, ideal, d, V > 0 ? min_angle_blocks(V) : 0, *path,
                     *path == GR_PATH_GRID ? fp.cp.k : 0, *occl_path, *pairs_tested, s);
-    cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s);
-    L->io_d2h += (int64_t)(sizeof(gr_result) + sizeof(DevAcc));
+    if (readback) {
+        cudaMemcpyAsync(L->h_result, b.result, sizeof(gr_result), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s);
+        L->io_d2h += (int64_t)(sizeof(gr_result) + sizeof(DevAcc));
+    }
     phase_end(L, GR_PHASE_FINALIZE, s);
 }
 
 // Replays the graph of this configuration, capturing it first when the
 // configuration or a buffer changed since the last capture.
-gr_status run_eval_graph(gr_layout *L, uint32_t metrics, double ideal, int64_t d, const FastPlan &fp) {
+gr_status run_eval_graph(gr_layout *L, uint32_t metrics, double ideal, int64_t d, const FastPlan &fp,
+                         cudaStream_t after, gr_result *d_result, bool readback) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (after != L->stream) GR_CU(cudaStreamIsCapturing(after, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        // `after` is being captured into the caller's graph: the evaluation's own steps are captured
+        // there directly (the caller orders the inputs before replaying)
+        int32_t path, occl_path;
+        int64_t pairs_tested;
+        L->capturing = true;
+        enqueue_fast(L, after, metrics, ideal, d, fp, false, &path, &occl_path, &pairs_tested);
+        L->capturing = false;
+        if (d_result) GR_CU(cudaMemcpyAsync(d_result, L->b.result, sizeof(gr_result), cudaMemcpyDeviceToDevice, after));
+        return GR_OK;
+    }
     auto &g = L->eg;
     const GridBuffers &gb = L->g;
     const void *bufs[8] = {gb.cell_off, gb.cell_nl, gb.item_off, gb.cell_fill, gb.rec, gb.item_desc, gb.ocell_off,
@@ -811,8 +840,11 @@ gr_status run_eval_graph(gr_layout *L, uint32_t metrics, double ideal, int64_t d
     const bool same = g.valid && g.metrics == metrics && g.ideal == ideal && g.d == d && g.x_on == fp.x_on &&
                       g.grid == fp.cp.grid && g.split == fp.cp.split && g.k == fp.cp.k && g.o_on == fp.o_on &&
                       g.ogrid == fp.ogrid && g.ko == fp.ko && g.profiling == L->profiling &&
-                      memcmp(g.bufs, bufs, sizeof bufs) == 0 && memcmp(g.caps, caps, sizeof caps) == 0;
-    cudaStream_t s = L->gstream;  // (the caller's stream may be the legacy one, which cannot be captured)
+                      g.readback == readback && memcmp(g.bufs, bufs, sizeof bufs) == 0 &&
+                      memcmp(g.caps, caps, sizeof caps) == 0;
+    // captured on a stream of its own (the caller's stream may be the legacy one, which cannot be
+    // captured, or be capturing itself), replayed on another
+    cudaStream_t s = L->cstream;
     if (!same) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
@@ -822,7 +854,7 @@ gr_status run_eval_graph(gr_layout *L, uint32_t metrics, double ideal, int64_t d
         const int64_t l0 = gr_kernel_launches(), io0 = L->io_d2h;
         GR_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
         L->capturing = true;
-        enqueue_fast(L, s, metrics, ideal, d, fp, &g.path, &g.occl_path, &g.pairs_tested);
+        enqueue_fast(L, s, metrics, ideal, d, fp, readback, &g.path, &g.occl_path, &g.pairs_tested);
         L->capturing = false;
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(s, &graph);
@@ -856,15 +888,24 @@ gr_status run_eval_graph(gr_layout *L, uint32_t metrics, double ideal, int64_t d
         g.ogrid = fp.ogrid;
         g.ko = fp.ko;
         g.profiling = L->profiling;
+        g.readback = readback;
         memcpy(g.bufs, bufs, sizeof bufs);
         memcpy(g.caps, caps, sizeof caps);
     }
-    // after the work queued on the layout's stream, and before what follows it there
+    // after the work queued on the layout's stream (its inputs) and on `after`, and before what
+    // follows on `after`
+    cudaStream_t r = L->gstream;
     GR_CU(cudaEventRecord(L->ev_gin, L->stream));
-    GR_CU(cudaStreamWaitEvent(s, L->ev_gin, 0));
-    GR_CU(cudaGraphLaunch(g.exec, s));
-    GR_CU(cudaEventRecord(L->ev_gout, s));
-    GR_CU(cudaStreamWaitEvent(L->stream, L->ev_gout, 0));
+    GR_CU(cudaStreamWaitEvent(r, L->ev_gin, 0));
+    if (after != L->stream) {
+        GR_CU(cudaEventRecord(L->ev_gin2, after));
+        GR_CU(cudaStreamWaitEvent(r, L->ev_gin2, 0));
+    }
+    GR_CU(cudaGraphLaunch(g.exec, r));
+    if (d_result) GR_CU(cudaMemcpyAsync(d_result, L->b.result, sizeof(gr_result), cudaMemcpyDeviceToDevice, r));
+    GR_CU(cudaEventRecord(L->ev_gout, r));
+    GR_CU(cudaStreamWaitEvent(after, L->ev_gout, 0));
+    if (after != L->stream) GR_CU(cudaStreamWaitEvent(L->stream, L->ev_gout, 0));
     count_launches((int)g.launches);
     L->io_d2h += g.d2h;
     for (int ph = 0; ph < GR_NUM_PHASES; ++ph)
@@ -905,7 +946,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
         FastPlan fp;
         if ((st = plan_fast(L, metrics, d, n_seg, &fp)) != GR_OK) return st;
         if (fp.graphable) {
-            if ((st = run_eval_graph(L, metrics, ideal, d, fp)) != GR_OK) return st;
+            if ((st = run_eval_graph(L, metrics, ideal, d, fp, L->stream, nullptr, true)) != GR_OK) return st;
             return finish_evaluate(L, metrics, params, ideal, d, fp.x_on && fp.cp.grid, L->eg.path, fp.cp.k, out);
         }
     }
@@ -1030,6 +1071,43 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     L->io_d2h += (int64_t)(sizeof(gr_result) + sizeof(DevAcc));
     phase_end(L, GR_PHASE_FINALIZE);
     return finish_evaluate(L, metrics, params, ideal, d, fast_grid, path, cp.k, out);
+}
+
+gr_status gr_evaluate_async(gr_layout *L, uint32_t metrics, const gr_params *params, gr_result *d_result,
+                            gr_stream_t stream) {
+    g_err.clear();
+    if (!L || !d_result) return fail(GR_EINVAL, "NULL argument");
+    if (metrics & ~GR_METRIC_ALL) return fail(GR_EINVAL, "unknown metric bits");
+    if (L->coord != GR_COORD_I32) return fail(GR_ENOTSUP, "gr_evaluate_async needs a GR_COORD_I32 layout");
+    if (!is_device_pointer(d_result)) return fail(GR_EINVAL, "d_result must be device memory");
+    double ideal;
+    int64_t d;
+    gr_status st = read_params(params, &ideal, &d);
+    if (st != GR_OK) return st;
+    cudaStream_t after = stream ? (cudaStream_t)stream : L->stream;
+    FastPlan fp;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (L->fast_ok) {
+            if ((st = plan_fast(L, metrics, d, (uint64_t)L->E, &fp)) != GR_OK) return st;
+            if (fp.graphable) break;
+        }
+        // not planned yet, or the plan changed: one synchronised evaluation plans and sizes the buffers
+        gr_result tmp;
+        if ((st = gr_evaluate(L, metrics, params, &tmp)) != GR_OK) return st;
+        fp.graphable = false;
+    }
+    if (!fp.graphable) return fail(GR_ENOTSUP, "the layout's crossing plan does not settle");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (after != L->stream) GR_CU(cudaStreamIsCapturing(after, &cap));
+    if (L->dirty_any && cap == cudaStreamCaptureStatusNone) {  // (else the next synchronous evaluation does it)
+        GR_CU(cudaMemsetAsync(L->dirty.flag, 0, (size_t)(L->E > 0 ? L->E : 1), L->stream));
+        GR_CU(cudaMemsetAsync(L->dirty.n, 0, sizeof(uint32_t), L->stream));
+        L->dirty_any = false;
+    }
+    // the host keeps no totals of an evaluation it does not read back
+    L->last.valid = false;
+    L->dgrid_k = -1;
+    return run_eval_graph(L, metrics, ideal, d, fp, after, d_result, false);
 }
 
 gr_status gr_node_occlusion(gr_layout *L, int64_t d, int64_t *out_pairs) {
@@ -1310,7 +1388,7 @@ gr_status run_move_graph(gr_layout *L, const MovePlan &mp) {
     const bool same = g.valid && g.metrics == mp.metrics && g.ideal == mp.ideal && g.d == mp.d &&
                       g.use_grid == mp.use_grid && g.ma_incremental == mp.ma_incremental && g.k == L->dgrid_k &&
                       g.cap == L->mv_cap && memcmp(g.bufs, bufs, sizeof bufs) == 0;
-    cudaStream_t s = L->gstream;
+    cudaStream_t s = L->cstream;
     if (!same) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
@@ -1344,10 +1422,11 @@ gr_status run_move_graph(gr_layout *L, const MovePlan &mp) {
         g.cap = L->mv_cap;
         memcpy(g.bufs, bufs, sizeof bufs);
     }
+    cudaStream_t r = L->gstream;
     GR_CU(cudaEventRecord(L->ev_gin, L->stream));
-    GR_CU(cudaStreamWaitEvent(s, L->ev_gin, 0));
-    GR_CU(cudaGraphLaunch(g.exec, s));
-    GR_CU(cudaEventRecord(L->ev_gout, s));
+    GR_CU(cudaStreamWaitEvent(r, L->ev_gin, 0));
+    GR_CU(cudaGraphLaunch(g.exec, r));
+    GR_CU(cudaEventRecord(L->ev_gout, r));
     GR_CU(cudaStreamWaitEvent(L->stream, L->ev_gout, 0));
     count_launches((int)g.launches);
     L->io_d2h += g.d2h;

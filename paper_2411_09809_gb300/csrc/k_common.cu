@@ -287,7 +287,11 @@ __global__ void __launch_bounds__(256) k_finalize(const DevAcc *__restrict__ acc
 
     gr_result r;
     memset(&r, 0, sizeof(r));
-    r.metrics = metrics;
+    // a failed evaluation (invalid input, outgrown buffers) is marked by metrics = 0, so that results
+    // written to device memory without a read-back can be told apart
+    const bool failed = (acc->status | acc->eval_status) != 0 ||
+                        (path == GR_PATH_GRID && (acc->grid_flags & GF_ITEMS_OVERFLOW) != 0);
+    r.metrics = failed ? 0u : metrics;
     r.crossing_path = path;
     r.cell_log2 = cell_log2;
     r.occlusion_path = occl_path;

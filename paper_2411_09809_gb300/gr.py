@@ -125,6 +125,8 @@ def load() -> ctypes.CDLL:
         "gr_move_vertices": ([P, c_int64, P, P, c_uint32, ctypes.POINTER(gr_params), ctypes.POINTER(gr_result)],
                              c_int32),
         "gr_strip_crossings": ([P, c_int32, c_int32, c_double, ctypes.POINTER(gr_strip_result)], c_int32),
+        "gr_evaluate_async": ([P, c_uint32, ctypes.POINTER(gr_params), P, P], c_int32),
+        "gr_batch_evaluate_async": ([P, c_uint32, ctypes.POINTER(gr_params), P, P], c_int32),
         "gr_diff_forward": ([P, c_double, P], c_int32),
         "gr_diff_backward": ([P, P, P], c_int32),
         "gr_last_error": ([], ctypes.c_char_p),
@@ -151,7 +153,7 @@ def _buffer(x, dtype: str):
         import torch  # noqa: F401
         if isinstance(x, torch.Tensor):
             want = {"int32": torch.int32, "float32": torch.float32, "int64": torch.int64,
-                    "float64": torch.float64}[dtype]
+                    "float64": torch.float64, "uint8": torch.uint8}[dtype]
             if x.dtype != want:
                 raise TypeError(f"expected a {dtype} tensor, got {x.dtype}")
             if not x.is_contiguous():
@@ -282,6 +284,41 @@ def gr_crossing_angle(layout, ideal_rad: float = 0.0) -> gr_crossing_angle_resul
     return out
 
 
+def result_buffer(n: int = 1, device=None):
+    """A CUDA byte tensor for n gr_result structs (the asynchronous evaluations' output)."""
+    import torch
+    return torch.empty(n * ctypes.sizeof(gr_result), dtype=torch.uint8, device=device or "cuda")
+
+
+def results_from_device(buf, n: int = 1) -> list:
+    """The gr_result structs of a result buffer (copies it to the host; synchronises)."""
+    raw = bytes(buf.detach().cpu().numpy().tobytes())
+    size = ctypes.sizeof(gr_result)
+    return [gr_result.from_buffer_copy(raw[i * size:(i + 1) * size]) for i in range(n)]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def gr_evaluate_async(layout, d_result, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+                      occlusion_d: int = 0, stream=None) -> None:
+    """Enqueues an evaluation writing its gr_result into d_result (see result_buffer)."""
+    rp, rk = _buffer(d_result, "uint8")
+    p = gr_params(float(ideal_rad), int(occlusion_d))
+    _check(load().gr_evaluate_async(layout, metrics, ctypes.byref(p), rp, _stream_ptr(stream)))
+
+
+def gr_batch_evaluate_async(batch, d_results, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+                            occlusion_d: int = 0, stream=None) -> None:
+    """Enqueues a batch evaluation writing its gr_result structs into d_results."""
+    rp, rk = _buffer(d_results, "uint8")
+    p = gr_params(float(ideal_rad), int(occlusion_d))
+    _check(load().gr_batch_evaluate_async(batch, metrics, ctypes.byref(p), rp, _stream_ptr(stream)))
+
+
 def gr_strip_crossings(layout, strip_width: int, orientation: int = GR_STRIP_VERTICAL,
                        ideal_rad: float = 0.0) -> gr_strip_result:
     """The paper's approximate strip estimates of E_c and E_ca (Sec. 3.2.2-3.2.3)."""
@@ -393,6 +430,10 @@ class Batch:
     def evaluate(self, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0, occlusion_d: int = 0):
         return gr_batch_evaluate(self.handle, self.n, metrics, ideal_rad, occlusion_d)
 
+    def evaluate_async(self, d_results, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+                       occlusion_d: int = 0, stream=None) -> None:
+        gr_batch_evaluate_async(self.handle, d_results, metrics, ideal_rad, occlusion_d, stream)
+
     def close(self) -> None:
         if getattr(self, "handle", None) is not None and self.handle.value:
             gr_batch_destroy(self.handle)
@@ -432,6 +473,10 @@ class Layout:
     def move(self, ids, xy_new, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
              occlusion_d: int = 0) -> gr_result:
         return gr_move_vertices(self.handle, ids, xy_new, metrics, ideal_rad, occlusion_d)
+
+    def evaluate_async(self, d_result, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+                       occlusion_d: int = 0, stream=None) -> None:
+        gr_evaluate_async(self.handle, d_result, metrics, ideal_rad, occlusion_d, stream)
 
     def strips(self, strip_width: int, orientation: int = GR_STRIP_VERTICAL,
                ideal_rad: float = 0.0) -> gr_strip_result:

@@ -34,7 +34,8 @@ def test_header_declares_the_boundary():
               "gr_last_error", "gr_version", "gr_profile_enable", "gr_profile_read",
               "gr_kernel_launches", "gr_io_bytes", "gr_crossing_angle_noalloc",
               "gr_batch_create", "gr_batch_update", "gr_batch_evaluate", "gr_batch_destroy",
-              "gr_diff_forward", "gr_diff_backward", "gr_move_vertices", "gr_strip_crossings"]:
+              "gr_diff_forward", "gr_diff_backward", "gr_move_vertices", "gr_strip_crossings",
+              "gr_evaluate_async", "gr_batch_evaluate_async"]:
         assert n in names
 
 
