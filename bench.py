@@ -184,6 +184,28 @@ SM_COUNT = 152
 LANES_PER_SM_PER_CLK = 128  # 4 SM sub-partitions x 32 lanes, one warp instruction per clock each
 
 
+_PIPES = None
+
+
+def measured_pipes() -> dict | None:
+    """Thread-operations per second (T/s) of the instruction classes the pair
+    kernels use, measured on this GPU by the pipe microbenchmarks
+    (paper_2411_09809_gb300/peaks/pipe_peaks.cu); cached per process."""
+    global _PIPES
+    if _PIPES is None:
+        import ctypes
+        try:
+            from paper_2411_09809_gb300 import build as gb
+            lib = ctypes.CDLL(gb.build_peaks())
+            out = (ctypes.c_double * 7)()
+            n = lib.gr_peaks_measure(out, 7)
+            names = ["iadd3", "lop3", "imnmx_plus_iadd", "imad", "ffma", "mufu_rsqrt", "dfma"]
+            _PIPES = {names[i]: round(out[i] / 1e12, 3) for i in range(n)} if n > 0 else {}
+        except (OSError, RuntimeError):
+            _PIPES = {}
+    return _PIPES or None
+
+
 def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload: str) -> dict:
     pairs_ms, pairs_calls = prof["cross_pairs"]
     scat_ms, scat_calls = prof["cross_scatter"]
@@ -803,7 +825,7 @@ def run_strips(args, rank, world, local_rank):
                                     f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
                      "work": f"{OPS_PER_MERGE_STEP} ops per binary-search step of each merge level and record, "
                              f"{OPS_PER_STRIP_PAIR} per counted pair",
-                     "traffic": None, "launch_ms": cnt_ms},
+                     "traffic": None, "launch_ms": cnt_ms, "pipe_peaks_tops": measured_pipes()},
         "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": (io1[0] - io0[0]) // max(1, len(e2e_s)),
                 "d2h_bytes_per_step": (io1[1] - io0[1]) // max(1, len(e2e_s))},
@@ -912,6 +934,7 @@ def run_per_edge(args, rank, world, local_rank):
     peaks, peak_kind = load_peaks()
     rf = roofline(res, prof, E - res.crossing.c.zero_length_edges, peaks, peak_kind, "per_edge")
     rf["traffic"] = None  # the per-edge form of the kernel has no committed capture
+    rf["pipe_peaks_tops"] = measured_pipes()
     rf["kernel"] += " (per-edge form: + 4 atomics per E_c pair)"
     line = {
         "metric": "edge-pair tests/s", "value": world * pairs / (ms / 1e3), "unit": "pairs/s", "n_gpus": world,
@@ -1133,6 +1156,7 @@ def run_ours(args, rank, world, local_rank):
     n_seg = L.E - res.crossing.c.zero_length_edges
     peaks, peak_kind = load_peaks()
     rf = roofline(res, prof, n_seg, peaks, peak_kind, args.workload)
+    rf["pipe_peaks_tops"] = measured_pipes()
     lay.close()
     if rank != 0:
         return

@@ -18,6 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgr.so")
+PEAKS_SRC = os.path.join(PKG, "peaks", "pipe_peaks.cu")
+PEAKS_LIB = os.path.join(BUILD, "libgr_peaks.so")  # the pipe microbenchmarks bench.py reports beside the roofline
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -45,8 +47,24 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
+def build_peaks(force: bool = False) -> str:
+    """Compiles the pipe microbenchmarks into libgr_peaks.so; returns its path."""
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PEAKS_SRC, "-o", tmp]
+    p = subprocess.run(cmd, capture_output=True, text=True)
+    if p.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{p.stdout}\n{p.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compiles every CUDA translation unit and links libgr.so; returns its path."""
+    """Compiles every CUDA translation unit and links libgr.so (and the pipe
+    microbenchmarks); returns libgr.so's path."""
+    build_peaks(force)
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
