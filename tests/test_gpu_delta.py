@@ -213,3 +213,46 @@ def test_dirty_list_overflow_rebuilds_the_grid():
             same(r, full(xy, L0.edges, 100), f"step {step}")
         assert gr.GR_PATH_GRID in paths[1:]  # a rebuild
         assert paths[0] == gr.GR_PATH_DELTA and paths[-1] == gr.GR_PATH_DELTA
+
+
+@pytest.mark.parametrize("opt", [None, grid_opt(9), grid_opt(11, gr.GR_LONG_ALLPAIRS)])
+def test_long_random_move_sequence_with_interleaved_evaluations(opt):
+    # 60 moves of 1-60 vertices (local steps, jumps, onto other vertices), with
+    # synchronous and asynchronous full evaluations in between: every state
+    # transition (incremental, full, dirty-list growth) against fresh layouts
+    import torch
+    rng = np.random.default_rng(71)
+    L0 = synth.plain_layout(V=3000, knn_count=6000, random_count=1200, seed=72)
+    xy = L0.xy.copy()
+    d = 150
+    buf = gr.result_buffer(1)
+    with gr.Layout(torch.from_numpy(xy).cuda(), torch.from_numpy(L0.edges).cuda(), opt=opt) as L:
+        L.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
+        for step in range(60):
+            n = int(rng.integers(1, 61))
+            ids = rng.choice(L0.V, size=n, replace=False).astype(np.int32)
+            kind = step % 3
+            if kind == 0:
+                new = np.clip(xy[ids] + rng.integers(-150, 151, size=(n, 2)), 0, 65535).astype(np.int32)
+            elif kind == 1:
+                new = rng.integers(0, 65536, size=(n, 2)).astype(np.int32)
+            else:
+                new = xy[rng.integers(0, L0.V, size=n)].astype(np.int32)
+            xy[ids] = new
+            r = L.move(torch.from_numpy(ids).cuda(), torch.from_numpy(new).cuda(), gr.GR_METRIC_ALL, IDEAL, d)
+            if step % 10 == 4:
+                L.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
+            if step % 10 == 7:
+                L.evaluate_async(buf, gr.GR_METRIC_ALL, IDEAL, d)
+                torch.cuda.synchronize()
+                got = gr.results_from_device(buf)[0]
+                if got.metrics == 0:
+                    # the moves outgrew the buffers planned at the last synchronous evaluation: the
+                    # asynchronous result says so, a synchronous evaluation re-plans, and then it works
+                    L.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
+                    L.evaluate_async(buf, gr.GR_METRIC_ALL, IDEAL, d)
+                    torch.cuda.synchronize()
+                    got = gr.results_from_device(buf)[0]
+                same(got, full(xy, L0.edges, d), f"async after step {step}")
+            if step % 5 == 0 or step == 59:
+                same(r, full(xy, L0.edges, d), f"step {step}")
