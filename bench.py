@@ -95,6 +95,11 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # wait for the sampler's first line, so that short timed regions still see a live sampler
+        # (the last sample before a region of a few milliseconds is then the one reported)
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
