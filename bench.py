@@ -22,6 +22,7 @@ path; weak scaling).  `--impl reference` times the CPU oracle instead.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -400,11 +401,31 @@ def run_batched(args, rank, world, local_rank):
         with gr.Layout(dxy[v_off[i]:v_off[i + 1]], ded[e_off[i]:e_off[i + 1]]) as one:
             one.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
     single_s = (time.perf_counter() - t0) * n / max(1, len(sample))
+    # end to end through the C ABI: coordinates and edges from pinned host memory, results to the host
+    hxy = torch.from_numpy(xy).pin_memory()
+    hed = torch.from_numpy(edges).pin_memory()
+    e2e_s = []
+    for i in range(0 if args.no_e2e else args.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gr.gr_batch_update(B.handle, hxy, hed)
+        gr.gr_batch_evaluate(B.handle, n, gr.GR_METRIC_ALL, IDEAL, d)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_ms = statistics.mean(e2e_s) * 1e3 if e2e_s else float("nan")
     B.close()
     if rank != 0:
         return
     pairs = float(sum((e_off[i + 1] - e_off[i]) * (e_off[i + 1] - e_off[i] - 1) / 2 for i in range(n)))
     value = world * n / (ms / 1e3)
+    # roofline over the whole step: the pair tests of every layout (grid candidates and long-long
+    # tile pairs) and their crossings, against the issue-rate peak
+    peaks, peak_kind = load_peaks()
+    tested = float(sum(r.crossing.c.pairs_tested for r in res))
+    crossings = float(sum(r.crossing.c.crossings for r in res))
+    ops = tested * OPS_PER_PAIR + crossings * OPS_PER_CROSSING_GRID
+    peak = SM_COUNT * LANES_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = ops / (ms / 1e3) / 1e12
     line = {
         "metric": "layouts/s", "value": value, "unit": "layouts/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -418,10 +439,44 @@ def run_batched(args, rank, world, local_rank):
         "single_layout_loop": {"layouts_per_s": n / single_s, "sample_layouts": len(sample),
                                "speedup_of_batch": (n / (ms / 1e3)) / (n / single_s)} if sample else None,
         "create_s": create_s,
+        "roofline": {"kernel": "the whole step (k_batch_long_pairs and k_batch_grid_pairs take three quarters)",
+                     "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "Tops/s (int32-equivalent lane ops)", "frac": achieved / peak,
+                     "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
+                                    f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
+                     "work": f"{OPS_PER_PAIR} ops per pair tested, {OPS_PER_CROSSING_GRID} per crossing",
+                     "traffic": None, "pipe_peaks_tops": measured_pipes()},
+        "e2e": {"value": world * n / (e2e_ms / 1e3), "unit": "layouts/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(xy.nbytes + edges.nbytes),
+                "d2h_bytes_per_step": n * ctypes.sizeof(gr.gr_result)},
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if world == 1 and not args.no_cpu_baseline:
+        cb_s, n_sample = batch_oracle_step(v_off, e_off, xy, edges, d)
+        import oracle
+        line["cpu_baseline"] = {"value": n / cb_s, "unit": "layouts/s", "cores": oracle.num_threads(),
+                                "kind": "oracle",
+                                "sample": f"{n_sample} layouts stratified by size, all five metrics, scaled to {n}"}
     print(json.dumps(line), flush=True)
+
+
+def batch_oracle_step(v_off, e_off, xy, edges, d) -> tuple[float, int]:
+    """The oracle's time for all five metrics of a size-stratified sample of the
+    layouts (every 64th by size), scaled to the whole batch; and the sample size."""
+    import oracle
+    n = len(v_off) - 1
+    order = sorted(range(n), key=lambda i: v_off[i + 1] - v_off[i])
+    sample = order[:: max(1, n // 64)]
+    t0 = time.perf_counter()
+    for i in sample:
+        lxy = xy[v_off[i]:v_off[i + 1]]
+        led = edges[e_off[i]:e_off[i + 1]]
+        oracle.crossings(lxy, led)
+        oracle.node_occlusion(lxy, d)
+        oracle.min_angle(lxy, led)
+        oracle.edge_length_variation(lxy, led)
+    return (time.perf_counter() - t0) * n / len(sample), len(sample)
 
 
 def run_reference_batched(args):
@@ -431,19 +486,11 @@ def run_reference_batched(args):
     v_off, e_off, xy, edges = batched_workload()
     n = len(v_off) - 1
     d = WORKLOADS["batched"][1]
-    order = sorted(range(n), key=lambda i: v_off[i + 1] - v_off[i])
-    sample = order[:: max(1, n // 64)]
     secs = []
     for _ in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        for i in sample:
-            lxy = xy[v_off[i]:v_off[i + 1]]
-            led = edges[e_off[i]:e_off[i + 1]]
-            oracle.crossings(lxy, led)
-            oracle.node_occlusion(lxy, d)
-            oracle.min_angle(lxy, led)
-            oracle.edge_length_variation(lxy, led)
-        secs.append((time.perf_counter() - t0) * n / len(sample))
+        t, n_sample = batch_oracle_step(v_off, e_off, xy, edges, d)
+        secs.append(t)
+    sample = range(n_sample)
     step_s = statistics.mean(secs[args.warmup:])
     value = n / step_s
     line = {
@@ -616,6 +663,20 @@ def run_differentiable(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def move_roofline(L, ms: float) -> dict:
+    """A move against HBM: its algorithmic bytes are dominated by the O(E) passes (the regather:
+    8 B of ids, 16 B of coordinates, 16 + 4 + 4 B of segment, id and direction, 8 B of squared length
+    per edge; the edge length variation: 2 x 8 B per edge; the affected-edge scan: 8 B of ids and 8 B
+    of moved flags per edge).  The step is latency-bound: the fraction is small by construction."""
+    peaks, peak_kind = load_peaks()
+    nbytes = L.E * (56 + 16 + 16)
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = nbytes / (ms / 1e3) / 1e9
+    return {"kernel": "the whole move (the O(E) regather, edge length variation and affected-edge scan)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": f"hbm_gbs ({peak_kind})", "work": "88 B per edge", "traffic": None}
+
+
 def run_moves(args, rank, world, local_rank):
     """Incremental workload: on the large sparse layout, one step = gr_move_vertices
     of 16 random vertices to random positions (all five metrics of the moved
@@ -676,6 +737,20 @@ def run_moves(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     full_ms, _ = timed(lambda i: lay.evaluate(gr.GR_METRIC_ALL, IDEAL, d), args.steps, 0)
+    # end to end through the C ABI: the moved ids and coordinates from pinned host memory, the result
+    # read back (gr_move_vertices returns it on the host)
+    h_ids = [ids[i].cpu().pin_memory() for i in range(args.warmup, args.warmup + args.steps)]
+    h_new = [new[i].cpu().pin_memory() for i in range(args.warmup, args.warmup + args.steps)]
+    io0 = gr.gr_io_bytes(lay.handle)
+    e2e_s = []
+    for i in range(args.steps):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gr.gr_move_vertices(lay.handle, h_ids[i], h_new[i], gr.GR_METRIC_ALL, IDEAL, d)
+        e2e_s.append(time.perf_counter() - t0)
+    io1 = gr.gr_io_bytes(lay.handle)
+    e2e_ms = statistics.mean(e2e_s) * 1e3
     if world > 1:
         t = torch.tensor([ms, full_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -691,6 +766,10 @@ def run_moves(args, rank, world, local_rank):
                        step=f"gr_move_vertices of {MOVES_PER_STEP} random vertices, all five metrics",
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "full_evaluation_ms": full_ms, "speedup_over_full": full_ms / ms,
+        "e2e": {"value": world * 1e3 / e2e_ms, "unit": "evaluations/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": (io1[0] - io0[0]) // args.steps,
+                "d2h_bytes_per_step": (io1[1] - io0[1]) // args.steps},
+        "roofline": move_roofline(L, ms),
         "pairs_tested_per_step": res.crossing.c.pairs_tested,
         "gpu_launches": launches,
         "clocks": clk,
