@@ -146,18 +146,24 @@ def load_peaks() -> tuple[dict, str]:
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def load_traffic(kernel: str, workload: str, src_hash: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None if
-    the kernel source changed since the capture."""
+def load_capture(kernel: str, workload: str, src_hash: str) -> dict:
+    """The committed ncu summary's figures for `kernel` (DRAM bytes per launch,
+    issue-slot utilisation), or {} if the kernel source changed since the capture."""
     try:
         with open(PROFILE_TRAFFIC) as f:
             t = json.load(f)
     except OSError:
-        return None
+        return {}
     e = t.get(f"{kernel}/{workload}")
     if not e or e.get("source_sha256") != src_hash:
-        return None
-    return e.get("dram_bytes_per_launch")
+        return {}
+    return e
+
+
+def load_traffic(kernel: str, workload: str, src_hash: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None if
+    the kernel source changed since the capture."""
+    return load_capture(kernel, workload, src_hash).get("dram_bytes_per_launch")
 
 
 def kernel_source_hash(files: list[str]) -> str:
@@ -226,11 +232,15 @@ def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload:
         src = (["k_grid.cu", "grid_common.cuh", "pair_math.cuh"] if grid
                else ["k_crossings.cu", "allpairs_common.cuh", "pair_math.cuh"])
         achieved = ops / t / 1e12
+        cap = load_capture(kernel, workload, kernel_source_hash(src))
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Tops/s (int32-equivalent lane ops)", "frac": achieved / peak,
                 "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
                                f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
-                "traffic": load_traffic(kernel, workload, kernel_source_hash(src)),
+                "traffic": cap.get("dram_bytes_per_launch"),
+                # issued instructions against the issue-rate peak (smsp__issue_active, ncu), the
+                # pair kernels' target measure; null once the kernel changed since the capture
+                "issue_slot_frac": cap.get("issue_active_frac"),
                 "launch_ms": t * 1e3}
     t = scat_ms / scat_calls / 1e3
     nbytes = res.grid_records * 20 + n_seg * 20
