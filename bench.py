@@ -52,6 +52,7 @@ WORKLOADS = {
     "moves": ("large_sparse_layout", 64),
     "strips": ("dense_long_edge_layout", 0),
     "per_edge": ("large_sparse_layout", 0),
+    "paper_sized": ("paper_sized_layout", 256),
 }
 MOVES_PER_STEP = 16
 STRIP_WIDTH = 64          # vertical strips of the approximate algorithm (Sec. 3.2.2)

@@ -152,6 +152,16 @@ def dense_long_edge_layout(V: int = 20_000, E: int = 200_000, seed: int = BASE_S
     return Layout(xy, e, "dense_long_edge_v20k_e200k", {"d": 256, "ideal_deg": 70.0, "seed": seed})
 
 
+def paper_sized_layout(V: int = 75_879, E: int = 508_837, seed: int = BASE_SEED + 6) -> Layout:
+    """The random-layout workload at the size of the paper's largest graph
+    (Table 1: 75,879 vertices, 508,837 edges): V uniform points, E uniform
+    random edges; d = 256."""
+    rng = np.random.default_rng(seed)
+    xy = uniform_points(rng, V)
+    e = add_random_edges(rng, V, np.zeros((0, 2), np.int32), E)
+    return Layout(xy, e, "paper_sized_v75879_e508837", {"d": 256, "ideal_deg": 70.0, "seed": seed})
+
+
 def batched_layouts(n_layouts: int = 4096, v_min: int = 50, v_max: int = 20_000,
                     seed: int = BASE_SEED + 3) -> list[Layout]:
     """Batched workload: V_i log-uniform in [v_min, v_max], E_i = round(2.5 V_i) of which
