@@ -60,6 +60,19 @@ OPS_PER_STRIP_PAIR = 10   # per counted pair: direction load, wrapped difference
 OPS_PER_MERGE_STEP = 6    # per binary-search step of a merge level: load, 64-bit compare, select
 
 
+def max_over_ranks(values, world: int, device) -> list[float]:
+    """The element-wise maximum of per-rank timings over all ranks (one
+    all-reduce); the values themselves on a single rank."""
+    vals = [float(v) for v in values]
+    if world <= 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -400,10 +413,7 @@ def run_batched(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    (ms,) = max_over_ranks([ms], world, dev)
     # the same layouts one by one (a fixed sample, scaled to the batch)
     sample = [] if args.no_single_loop else list(range(0, n, max(1, n // 256)))
     torch.cuda.synchronize()
@@ -608,10 +618,7 @@ def run_differentiable(args, rank, world, local_rank):
     clk = clocks.stop()
     prof = lay.profile()
     fwd_ms = timed(fwd, args.steps)
-    if world > 1:
-        t = torch.tensor([ms, fwd_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, fwd_ms = (float(x) for x in t.tolist())
+    ms, fwd_ms = max_over_ranks([ms, fwd_ms], world, dev)
     res = lay.evaluate(gr.GR_METRIC_CROSSINGS, IDEAL)
 
     # end to end through the C ABI with host buffers (pinned): coordinates in,
@@ -762,10 +769,7 @@ def run_moves(args, rank, world, local_rank):
         e2e_s.append(time.perf_counter() - t0)
     io1 = gr.gr_io_bytes(lay.handle)
     e2e_ms = statistics.mean(e2e_s) * 1e3
-    if world > 1:
-        t = torch.tensor([ms, full_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, full_ms = (float(x) for x in t.tolist())
+    ms, full_ms = max_over_ranks([ms, full_ms], world, dev)
     lay.close()
     if rank != 0:
         return
@@ -865,10 +869,7 @@ def run_strips(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    (ms,) = max_over_ranks([ms], world, dev)
     prof = lay.profile()
     # end to end through the C ABI from pinned host coordinates
     hxy = torch.from_numpy(L.xy).pin_memory()
@@ -1000,10 +1001,7 @@ def run_per_edge(args, rank, world, local_rank):
 
     timed(plain, 3)
     plain_ms = timed(plain, args.steps)
-    if world > 1:
-        t = torch.tensor([ms, plain_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, plain_ms = (float(x) for x in t.tolist())
+    ms, plain_ms = max_over_ranks([ms, plain_ms], world, dev)
     # end to end: coordinates from pinned host memory, the per-edge arrays read back
     hxy = torch.from_numpy(L.xy).pin_memory()
     hc = torch.empty((L.E, 3), dtype=torch.int64).pin_memory()
@@ -1223,10 +1221,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    (ms,) = max_over_ranks([ms], world, dev)
     prof = lay.profile()
 
     # end to end through the C ABI with host buffers (pinned), copies inside
@@ -1243,10 +1238,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_s.append(time.perf_counter() - t0)
     io1 = gr.gr_io_bytes(lay.handle)
     e2e_ms = statistics.mean(e2e_s) * 1e3 if e2e_s else float("nan")
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    (e2e_ms,) = max_over_ranks([e2e_ms], world, dev)
 
     n_seg = L.E - res.crossing.c.zero_length_edges
     peaks, peak_kind = load_peaks()
