@@ -58,9 +58,9 @@ __device__ __forceinline__ FRow make_frow(SegRec s, uint32_t th) {
     FRow r;
     const int ax = px(s.x), ay = py(s.x), bx = px(s.y), by = py(s.y);
     const int ux = bx - ax, uy = by - ay;
-    r.ax = (float)ax; r.ay = (float)ay; r.bx = (float)bx; r.by = (float)by;
-    r.ux = (float)ux; r.uy = (float)uy;
-    r.nk = -(float)((long long)ux * ay - (long long)uy * ax);
+    r.ax = i2f_exact(ax); r.ay = i2f_exact(ay); r.bx = i2f_exact(bx); r.by = i2f_exact(by);
+    r.ux = i2f_exact(ux); r.uy = i2f_exact(uy);
+    r.nk = -ll2f_rn((long long)ux * ay - (long long)uy * ax);
     r.th = th;
     return r;
 }
@@ -69,9 +69,9 @@ __device__ __forceinline__ FCol make_fcol(SegRec s, uint32_t th) {
     FCol c;
     const int cx = px(s.x), cy = py(s.x), dx = px(s.y), dy = py(s.y);
     const int vx = dx - cx, vy = dy - cy;
-    c.cx = (float)cx; c.cy = (float)cy; c.dx = (float)dx; c.dy = (float)dy;
-    c.vx = (float)vx; c.vy = (float)vy;
-    c.nk = -(float)((long long)vx * cy - (long long)vy * cx);
+    c.cx = i2f_exact(cx); c.cy = i2f_exact(cy); c.dx = i2f_exact(dx); c.dy = i2f_exact(dy);
+    c.vx = i2f_exact(vx); c.vy = i2f_exact(vy);
+    c.nk = -ll2f_rn((long long)vx * cy - (long long)vy * cx);
     c.th = th;
     return c;
 }

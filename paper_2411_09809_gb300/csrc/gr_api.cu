@@ -67,7 +67,8 @@ struct gr_layout {
     int64_t V = 0, E = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;      // occlusion, min angle, ELV run here, beside the crossings
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side2 = nullptr;     // a move's minimum-angle update, beside its ELV
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     cudaStream_t gstream = nullptr;   // evaluation and move graphs are replayed here
     cudaStream_t cstream = nullptr;   // and captured here (never joined to a caller's stream)
     cudaEvent_t ev_gin = nullptr, ev_gin2 = nullptr, ev_gout = nullptr;
@@ -197,7 +198,9 @@ void free_layout(gr_layout *L) {
         if (e) cudaEventDestroy(e);
     if (L->ev_fork) cudaEventDestroy(L->ev_fork);
     if (L->ev_join) cudaEventDestroy(L->ev_join);
+    if (L->ev_join2) cudaEventDestroy(L->ev_join2);
     if (L->side) cudaStreamDestroy(L->side);
+    if (L->side2) cudaStreamDestroy(L->side2);
     if (L->gstream) cudaStreamDestroy(L->gstream);
     if (L->cstream) cudaStreamDestroy(L->cstream);
     if (L->ev_gin) cudaEventDestroy(L->ev_gin);
@@ -257,6 +260,7 @@ gr_status alloc_layout(gr_layout *L) {
     }
 #undef GR_TRY
     GR_CU(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
+    GR_CU(cudaStreamCreateWithFlags(&L->side2, cudaStreamNonBlocking));
     GR_CU(cudaStreamCreateWithFlags(&L->gstream, cudaStreamNonBlocking));
     GR_CU(cudaStreamCreateWithFlags(&L->cstream, cudaStreamNonBlocking));
     GR_CU(cudaEventCreateWithFlags(&L->ev_gin, cudaEventDisableTiming));
@@ -264,6 +268,7 @@ gr_status alloc_layout(gr_layout *L) {
     GR_CU(cudaEventCreateWithFlags(&L->ev_gout, cudaEventDisableTiming));
     GR_CU(cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming));
     GR_CU(cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming));
+    GR_CU(cudaEventCreateWithFlags(&L->ev_join2, cudaEventDisableTiming));
     GR_CU(cudaMallocHost((void **)&L->h_result, sizeof(gr_result)));
     GR_CU(cudaMallocHost((void **)&L->h_acc, sizeof(DevAcc)));
     GR_CU(cudaMemsetAsync(b.acc, 0, sizeof(DevAcc), L->stream));
@@ -392,7 +397,6 @@ gr_status enqueue_inputs(gr_layout *L, const void *xy, const int32_t *edges) {
     if (L->coord == GR_COORD_F32) {
         launch_gather_f32((const float *)L->b.xy, V, L->b.edges, E, L->b, s);
     } else {
-        launch_check_vertices(L->b.xy, V, L->b, s);
         launch_gather(L->b.xy, V, L->b.edges, E, L->b, s);
         if (edges) launch_adjacency(L->b, V, E, s);
     }
@@ -1329,7 +1333,7 @@ struct MovePlan {
     long long d2;
 };
 
-// Enqueues an incremental move on stream s (side work on the side stream):
+// Enqueues an incremental move on stream s (side work on two side streams):
 // validation, the before pass, the new coordinates, the regather, the after
 // pass, the new totals, the other metrics and the read-back.  Every kernel
 // after the validation does nothing on an invalid move.
@@ -1347,21 +1351,22 @@ void enqueue_move(gr_layout *L, cudaStream_t s, const MovePlan &mp) {
                       mp.occl, mp.d2, L->dacc, 0, s);
     launch_delta_apply(L->mv_ids, L->mv_xy, np, cap, L->dacc, b, s);
     // the moved layout's segments and statistics, then the after pass on
-    // them; edge length variation and minimum angle on the side stream
+    // them; edge length variation and minimum angle on two side streams
     cudaMemsetAsync(b.acc, 0, offsetof(DevAcc, eval_status), s);
-    launch_check_vertices(b.xy, V, b, s);
     launch_gather(b.xy, V, b.edges, E, b, s);
-    const bool side_work = (mp.metrics & (GR_METRIC_EDGE_LENGTH | GR_METRIC_MIN_ANGLE)) != 0;
-    if (side_work) {
-        cudaStream_t t = L->side;
-        cudaEventRecord(L->ev_fork, s);
+    const bool elv = (mp.metrics & GR_METRIC_EDGE_LENGTH) != 0, ma = (mp.metrics & GR_METRIC_MIN_ANGLE) != 0;
+    if (elv || ma) cudaEventRecord(L->ev_fork, s);
+    if (elv) {
+        cudaStreamWaitEvent(L->side, L->ev_fork, 0);
+        launch_elv(b, E, L->side);
+        cudaEventRecord(L->ev_join, L->side);
+    }
+    if (ma) {
+        cudaStream_t t = L->side2;
         cudaStreamWaitEvent(t, L->ev_fork, 0);
-        if (mp.metrics & GR_METRIC_EDGE_LENGTH) launch_elv(b, E, t);
-        if (mp.metrics & GR_METRIC_MIN_ANGLE) {
-            if (mp.ma_incremental) launch_min_angle_moved(b, V, L->mv_ids, np, cap, t);
-            else launch_min_angle(b, V, E, t);
-        }
-        cudaEventRecord(L->ev_join, t);
+        if (mp.ma_incremental) launch_min_angle_moved(b, V, L->mv_ids, np, cap, t);
+        else launch_min_angle(b, V, E, t);
+        cudaEventRecord(L->ev_join2, t);
     }
     if (mp.use_grid)
         launch_delta_grid_pass(b, L->g, L->dgrid_k, L->moved, L->affected, L->dirty, mp.ideal_u, L->dacc, 1, s);
@@ -1369,7 +1374,8 @@ void enqueue_move(gr_layout *L, cudaStream_t s, const MovePlan &mp) {
                       mp.occl, mp.d2, L->dacc, 1, s);
     launch_delta_unmark(L->mv_ids, np, cap, V, L->moved, s);
     launch_delta_combine(&L->mp_dev->last, L->dacc, b, s);
-    if (side_work) cudaStreamWaitEvent(s, L->ev_join, 0);
+    if (elv) cudaStreamWaitEvent(s, L->ev_join, 0);
+    if (ma) cudaStreamWaitEvent(s, L->ev_join2, 0);
     const uint32_t need = mp.metrics & (GR_METRIC_CROSSINGS | GR_METRIC_OCCLUSION);
     launch_finalize(b, mp.metrics, E, mp.ideal, mp.d, V > 0 ? min_angle_blocks(V) : 0,
                     mp.crossings ? GR_PATH_DELTA : 0, 0, (need & GR_METRIC_OCCLUSION) ? GR_PATH_DELTA : 0, -2, s);
@@ -1519,7 +1525,6 @@ gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const in
         if (L->h_dacc->status) return status_to_error(L->h_dacc->status);
         L->last.valid = false;
         GR_CU(cudaMemsetAsync(b.acc, 0, offsetof(DevAcc, eval_status), s));
-        launch_check_vertices(b.xy, V, b, s);
         launch_gather(b.xy, V, b.edges, E, b, s);
         GR_CU(cudaGetLastError());
         L->stats_stale = true;

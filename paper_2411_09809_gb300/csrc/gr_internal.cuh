@@ -166,11 +166,12 @@ void count_launches(int n);
 // Sets the message gr_last_error() returns on this host thread.
 void set_last_error(const char *msg);
 
-// a1: gathers every edge's endpoints, validates ids and coordinates, stores
-// the squared length of every edge, compacts the non-zero-length segments.
+// a1: gathers every edge's endpoints, validates ids and every vertex's
+// coordinates (vertices in no edge included), stores the squared length of
+// every edge, compacts the non-zero-length segments.
 void launch_gather(const int32_t *xy, int64_t V, const int32_t *edges, int64_t E,
                    Buffers &b, cudaStream_t s);
-// Validates every vertex coordinate (vertices in no edge included).
+// Validates every vertex coordinate only (the batch path's gather is its own).
 void launch_check_vertices(const int32_t *xy, int64_t V, Buffers &b, cudaStream_t s);
 
 // Optional per-edge outputs of the crossing kernels (both nullable together):
@@ -428,6 +429,21 @@ __device__ __forceinline__ int64_t find_segment_u32(const uint32_t *__restrict__
         if (off[mid] <= x) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Exact int -> float for |x| < 2^22 without a conversion instruction: x is
+// added to the bit pattern of 1.5 * 2^23 (floats in [2^23, 2^24) are the
+// integers, one unit apart) and 1.5 * 2^23 subtracted again.  The 64-bit
+// integer conversions run on the FP64 pipe, of which GB300 has little.
+__device__ __forceinline__ float i2f_exact(int x) {
+    return __int_as_float(0x4B400000 + x) - 12582912.0f;
+}
+
+// Round-to-nearest int64 -> float for |v| < 2^38 (the same value as a
+// conversion instruction): the high part times 2^16 plus the low 16 bits,
+// both exact, in one fused multiply-add with a single rounding.
+__device__ __forceinline__ float ll2f_rn(long long v) {
+    return fmaf(i2f_exact((int)(v >> 16)), 65536.0f, i2f_exact((int)(v & 0xffff)));
 }
 
 template <typename T>

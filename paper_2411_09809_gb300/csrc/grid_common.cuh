@@ -13,8 +13,9 @@ constexpr int TILE = 32;  // segments per tile (one per lane)
 
 // floor(num / den) for 0 <= num < 2^36, 1 <= den < 2^16: an FP32 estimate,
 // then exact integer correction (the estimate is off by at most a few units).
+// The operands reach FP32 without a 64-bit conversion instruction.
 __device__ __forceinline__ int floordiv_pos(long long num, int den) {
-    int q = (int)__fdividef((float)num, (float)den);
+    int q = (int)__fdividef(ll2f_rn(num), i2f_exact(den));
     long long r = num - (long long)q * den;
     while (r < 0) { --q; r += den; }
     while (r >= den) { ++q; r -= den; }
@@ -167,9 +168,9 @@ __device__ __forceinline__ GSeg make_gseg(const GridRec &g, int x0, int y0) {
     GSeg r;
     const int ax = px(g.s.x) - x0, ay = py(g.s.x) - y0, bx = px(g.s.y) - x0, by = py(g.s.y) - y0;
     const int ux = bx - ax, uy = by - ay;
-    r.ax = (float)ax; r.ay = (float)ay; r.bx = (float)bx; r.by = (float)by;
-    r.ux = (float)ux; r.uy = (float)uy;
-    r.nk = -(float)((long long)ux * ay - (long long)uy * ax);
+    r.ax = i2f_exact(ax); r.ay = i2f_exact(ay); r.bx = i2f_exact(bx); r.by = i2f_exact(by);
+    r.ux = i2f_exact(ux); r.uy = i2f_exact(uy);
+    r.nk = -ll2f_rn((long long)ux * ay - (long long)uy * ax);
     r.th = g.x.y;
     r.ida = g.s.z; r.idb = g.s.w;
     r.eid = (int32_t)g.x.x;

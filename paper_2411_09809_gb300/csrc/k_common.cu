@@ -17,27 +17,44 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// a1 -- one thread per edge (grid-stride, warp-uniform trip count).  Reads the
-// edge's vertex ids and coordinates (the D_e x D_pos join of Algorithm 4),
+// a1 -- one thread per edge (grid-stride, block-uniform trip count).  Reads
+// the edge's vertex ids and coordinates (the D_e x D_pos join of Algorithm 4),
 // checks them, stores the exact squared length of every edge and appends the
-// non-zero-length ones to the compacted segment array (warp-aggregated slot
-// reservation; the order of the compacted array does not affect any result).
-__global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int64_t V,
-                                                const int2 *__restrict__ edges, int64_t E,
-                                                SegRec *__restrict__ seg,
-                                                int32_t *__restrict__ seg_eid,
-                                                uint32_t *__restrict__ seg_theta,
-                                                int64_t *__restrict__ len2, DevAcc *acc) {
+// non-zero-length ones to the compacted segment array.  Slots are reserved
+// once per block and iteration (a block-wide prefix over the warps' counts),
+// the L1-length and zero-length totals once per block: same-address atomics
+// per warp serialised at L2 and dominated the kernel.  The order of the
+// compacted array does not affect any result.  The same grid also checks
+// every vertex's coordinates (isolated vertices included).
+constexpr int kGatherThreads = 256, kGatherWarps = kGatherThreads / 32;
+
+__global__ void __launch_bounds__(kGatherThreads) k_gather(const int2 *__restrict__ xy, int64_t V,
+                                                           const int2 *__restrict__ edges, int64_t E,
+                                                           SegRec *__restrict__ seg,
+                                                           int32_t *__restrict__ seg_eid,
+                                                           uint32_t *__restrict__ seg_theta,
+                                                           int64_t *__restrict__ len2, DevAcc *acc) {
     __shared__ uint32_t h_n[16];
     __shared__ unsigned long long h_l1[16];
+    // per-warp counts, then the warps' slots; double-buffered by iteration parity
+    __shared__ uint32_t w_cnt[2][kGatherWarps];
+    __shared__ unsigned long long red[kGatherWarps][2];
     if (threadIdx.x < 16) {
         h_n[threadIdx.x] = 0;
         h_l1[threadIdx.x] = 0;
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride) {
+    bool bad_v = false;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
+        const int2 p = xy[v];
+        bad_v |= ((unsigned)p.x >= 65536u) | ((unsigned)p.y >= 65536u);
+    }
+    if (bad_v) atomicOr(&acc->status, ST_BAD_COORD);
+    __syncthreads();
+    uint64_t l1_sum = 0, zero_sum = 0;
+    int par = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < E; base += stride, par ^= 1) {
         const int64_t e = base + threadIdx.x;
         bool keep = false, zero = false;
         uint32_t l1 = 0;
@@ -68,16 +85,28 @@ __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int
             }
             len2[e] = l2;
         }
+        l1_sum += l1;
+        zero_sum += zero;
         const unsigned mk = __ballot_sync(FULL, keep);
-        const unsigned mz = __ballot_sync(FULL, zero);
-        uint32_t slot = 0;
-        if (lane == 0 && mk) slot = atomicAdd(&acc->n_seg, (uint32_t)__popc(mk));
-        if (lane == 0 && mz) atomicAdd((unsigned long long *)&acc->zero_len, (unsigned long long)__popc(mz));
-        slot = __shfl_sync(FULL, slot, 0);
-        const uint64_t l1w = warp_sum<uint64_t>(l1);
-        if (lane == 0 && l1w) atomicAdd((unsigned long long *)&acc->len_l1, (unsigned long long)l1w);
+        if (lane == 0) w_cnt[par][wid] = (uint32_t)__popc(mk);
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t c = lane < kGatherWarps ? w_cnt[par][lane] : 0u;
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < kGatherWarps; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t total = __shfl_sync(FULL, incl, kGatherWarps - 1);
+            uint32_t b0 = 0;
+            if (lane == 0 && total) b0 = atomicAdd(&acc->n_seg, total);
+            b0 = __shfl_sync(FULL, b0, 0);
+            if (lane < kGatherWarps) w_cnt[par][lane] = b0 + incl - c;
+        }
+        __syncthreads();
         if (keep) {
-            const uint32_t pos = slot + __popc(mk & lanemask_lt());
+            const uint32_t pos = w_cnt[par][wid] + __popc(mk & lanemask_lt());
             seg[pos] = r;
             seg_eid[pos] = (int32_t)e;
             const int dx = px(r.y) - px(r.x), dy = py(r.y) - py(r.x);
@@ -94,7 +123,19 @@ __global__ void __launch_bounds__(256) k_gather(const int2 *__restrict__ xy, int
             }
         }
     }
+    l1_sum = warp_sum<uint64_t>(l1_sum);
+    zero_sum = warp_sum<uint64_t>(zero_sum);
+    if (lane == 0) {
+        red[wid][0] = l1_sum;
+        red[wid][1] = zero_sum;
+    }
     __syncthreads();
+    if (threadIdx.x < 2) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kGatherWarps; ++w) t += red[w][threadIdx.x];
+        if (t) atomicAdd(threadIdx.x == 0 ? (unsigned long long *)&acc->len_l1 : (unsigned long long *)&acc->zero_len,
+                         t);
+    }
     if (threadIdx.x < 16 && h_n[threadIdx.x]) {
         atomicAdd(&acc->len_hist[threadIdx.x], h_n[threadIdx.x]);
         atomicAdd((unsigned long long *)&acc->l1_hist[threadIdx.x], h_l1[threadIdx.x]);
@@ -379,9 +420,9 @@ int grid_for(int64_t n, int threads, int max_blocks) {
 
 void launch_gather(const int32_t *xy, int64_t V, const int32_t *edges, int64_t E, Buffers &b,
                    cudaStream_t s) {
-    if (E <= 0) return;
+    if (E <= 0 && V <= 0) return;
     count_launches(1);
-    k_gather<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>((const int2 *)xy, V, (const int2 *)edges, E,
+    k_gather<<<grid_for(E > V ? E : V, kGatherThreads, 152 * 16), kGatherThreads, 0, s>>>((const int2 *)xy, V, (const int2 *)edges, E,
                                                         b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc);
 }
 

@@ -39,10 +39,34 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // for n < 2^31 - 1 (2^31 - 1 is prime; larger n keep their order).  It
 // spreads runs of long edges (random edges appended after the short ones,
 // say) over all warps instead of leaving them to the last few, which walk
-// them one by one.
-__device__ __forceinline__ int64_t spread_index(int64_t i, int64_t n) {
-    if (n >= 0x7fffffffll) return i;
-    return (int64_t)(((uint64_t)i * (0x7fffffffull % (uint64_t)n)) % (uint64_t)n);
+// them one by one.  The product (< 2^62) is reduced by Barrett's method with
+// inv = floor((2^64 - 1) / n), set up once per block: the quotient estimate
+// floor(p inv / 2^64) is at most one below floor(p / n), so one conditional
+// subtraction finishes it (integer multiplies only, no 64-bit division or
+// remainder per thread).
+struct Spread {
+    uint64_t n, m, inv;
+};
+
+__device__ __forceinline__ Spread spread_setup(int64_t n, Spread *sh) {
+    if (threadIdx.x == 0) {
+        Spread s{(uint64_t)n, 0, 0};
+        if (n > 0 && n < 0x7fffffffll) {
+            s.m = 0x7fffffffull % (uint64_t)n;
+            s.inv = ~0ull / (uint64_t)n;
+        }
+        *sh = s;
+    }
+    __syncthreads();
+    return *sh;
+}
+
+__device__ __forceinline__ int64_t spread_index(int64_t i, const Spread &s) {
+    if (s.n >= 0x7fffffffull) return i;
+    const uint64_t p = (uint64_t)i * s.m;
+    uint64_t r = p - __umul64hi(p, s.inv) * s.n;
+    if (r >= s.n) r -= s.n;
+    return (int64_t)r;
 }
 
 // a2 -- per-cell record counts (all, and long ones); the long segments are
@@ -54,12 +78,14 @@ __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ s
                                                     uint32_t *__restrict__ cell_nl,
                                                     SegRec *__restrict__ seg_long, uint32_t *__restrict__ theta_long,
                                                     int32_t *__restrict__ eid_long) {
+    __shared__ Spread sp_sh;
     const int64_t n = acc->n_seg;
+    const Spread sp = spread_setup(n, &sp_sh);
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
-        const int64_t j = ok ? spread_index(i, n) : 0;
+        const int64_t j = ok ? spread_index(i, sp) : 0;
         const SegRec r = ok ? seg[j] : make_uint4(0, 0, 0, 0);
         const bool lng = split && ok && is_long_seg(r, k);
         const unsigned ml = __ballot_sync(0xffffffffu, lng);
@@ -142,15 +168,17 @@ __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ se
                                                    const uint32_t *__restrict__ cell_off,
                                                    unsigned long long *__restrict__ cell_fill, uint64_t cap,
                                                    GridRec *__restrict__ rec, uint32_t *status) {
+    __shared__ Spread sp_sh;
     const int64_t n = acc->n_seg;
     if (acc->records > cap) {  // sized from the same counts; cannot happen unless inputs changed
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_OVERFLOW);
         return;
     }
+    const Spread sp = spread_setup(n, &sp_sh);
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool ok = i < n;
-        const int64_t j = ok ? spread_index(i, n) : 0;
+        const int64_t j = ok ? spread_index(i, sp) : 0;
         const SegRec r = ok ? seg[j] : make_uint4(0, 0, 0, 0);
         const int32_t eid = ok ? seg_eid[j] : 0;
         const uint32_t th = ok ? seg_theta[j] : 0u;

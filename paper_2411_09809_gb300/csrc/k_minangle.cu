@@ -98,7 +98,7 @@ __device__ __forceinline__ bool better_gap(float g, int2 di, float gmin, int2 bi
 }
 
 __device__ __forceinline__ float ccw_gap_f(int2 a, int2 b) {
-    float g = atan2f((float)cross2(a, b), (float)dot2(a, b));
+    float g = atan2f(ll2f_rn(cross2(a, b)), ll2f_rn(dot2(a, b)));  // |cross|, |dot| < 2^33
     return g < 0.f ? g + 6.28318530717958647692f : g;
 }
 

@@ -136,7 +136,6 @@ gr_status gr_crossing_angle_noalloc(const int32_t *d_xy, int64_t V, const int32_
     b.acc = &sc->acc;
     cudaError_t e = cudaMemsetAsync(&sc->acc, 0, sizeof(gr::DevAcc), s);
     if (e == cudaSuccess) {
-        gr::launch_check_vertices(d_xy, V, b, s);
         gr::launch_gather(d_xy, V, d_edges, E, b, s);
         const uint32_t ideal_u = (uint32_t)llrint(ideal / M_PI * 4294967296.0);
         gr::launch_crossings_allpairs(b, E, ideal_u, gr::PerEdge{}, s);

@@ -90,17 +90,27 @@ __device__ __forceinline__ int classify_kind(const RowSeg &r, const ColSeg &c) {
 // in [0, pi) in units of pi / 2^32.  The vector is first turned into the
 // upper half-plane (exact: the line is the same), then FP32 atan2 of the
 // exactly representable integers (a few units in the last place of an angle
-// below pi, i.e. below 1e-6 rad) is rounded to the nearest unit.  Each
-// segment's direction is computed once and shared by every path, so all
-// paths derive the same crossing-angle terms.
+// below pi, i.e. below 1e-6 rad) is rounded to the nearest unit.  With t =
+// m 2^(be - 150) (m the 24-bit significand, be the biased exponent),
+// t 2^32 / pi = m K 2^(be - 180) for K = round(2^62 / pi); the product
+// (< 2^85) is formed and rounded in 128-bit integer arithmetic, so no FP64
+// instruction is needed.  Each segment's direction is computed once and
+// shared by every path, so all paths derive the same crossing-angle terms.
 __device__ __forceinline__ uint32_t line_direction(int dx, int dy) {
     if (dy < 0 || (dy == 0 && dx < 0)) {
         dx = -dx;
         dy = -dy;
     }
-    const float t = atan2f((float)dy, (float)dx);  // [0, pi]
-    const double u = rint((double)t * (4294967296.0 / 3.14159265358979323846));  // [0, 2^32]
-    return (uint32_t)(unsigned long long)u;  // 2^32 (angle pi) wraps to 0
+    const float t = atan2f(i2f_exact(dy), i2f_exact(dx));  // [0, pi)
+    const uint32_t bits = __float_as_uint(t);
+    const int be = (int)(bits >> 23);  // biased exponent; t >= 0
+    if (be < 90) return 0u;            // t < 2^-37: below half a unit (and t = 0)
+    const uint64_t m = (bits & 0x7fffffu) | 0x800000u;
+    constexpr uint64_t K = 1467945251641000613ull;  // round(2^62 / pi)
+    const int sh = 180 - be;                        // t 2^32 / pi = m K 2^(be - 180); 52 ... 90
+    unsigned __int128 P = (unsigned __int128)m * K;
+    P += (unsigned __int128)1 << (sh - 1);
+    return (uint32_t)(uint64_t)(P >> sh);  // t <= pi - 1.5e-5 here: below 2^32
 }
 
 // |ideal - a_c| in units of pi / 2^32 for lines of directions ta and tb.
