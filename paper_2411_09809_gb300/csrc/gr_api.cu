@@ -177,7 +177,7 @@ void free_grid(GridBuffers &g) {
 void free_layout(gr_layout *L) {
     if (!L) return;
     Buffers &b = L->b;
-    void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.ma_part,
+    void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.elv_len, b.ma_part,
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result,
                     b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->arg, L->st, L->out3, L->gout3,
                     L->f32_work, L->theta_adj, L->moved, L->affected, L->dacc, L->mv_ids, L->mv_xy,
@@ -230,6 +230,7 @@ gr_status alloc_layout(gr_layout *L) {
     GR_TRY(dalloc(&b.len2, (size_t)E));
     GR_TRY(dalloc(&b.acc, 1));
     GR_TRY(dalloc(&b.elv_part, 2 * (size_t)kElvBlocks));
+    GR_TRY(dalloc(&b.elv_len, (size_t)E));
     GR_TRY(dalloc(&b.ma_part, 1024));
     GR_TRY(dalloc(&b.ma_cnt, 1024));
     GR_TRY(dalloc(&b.deg, (size_t)V + 1));

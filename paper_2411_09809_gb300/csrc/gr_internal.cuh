@@ -76,6 +76,7 @@ struct Buffers {
     int64_t *len2 = nullptr;      // [E] squared length of every edge
     DevAcc *acc = nullptr;        // accumulators
     double *elv_part = nullptr;   // [kElvBlocks * 2] per-block FP64 partial sums
+    double *elv_len = nullptr;    // [E] l_e, written by the first ELV pass for the second
     double *ma_part = nullptr;    // [ma blocks] per-block sums of d_v
     uint32_t *ma_cnt = nullptr;   // [ma blocks] per-block vertex counts
     uint32_t *deg = nullptr;      // [V + 1] degree, then CSR offsets (scan in place)

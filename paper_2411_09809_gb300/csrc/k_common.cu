@@ -260,27 +260,31 @@ __global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t *in, uint32_
 
 // ------------------------------------------------------------------ ELV a10
 // Pass 1: per-block FP64 sum of edge lengths l_e = sqrt(len2_e) over a fixed
-// strided subset of edges (fixed order => deterministic).
+// strided subset of edges (fixed order => deterministic); l_e is stored for
+// pass 2, so the FP64 square root (slow on GB300) runs once per edge.
 __device__ __forceinline__ double edge_length(const int64_t *__restrict__ len2, int64_t e, bool f32) {
     const int64_t q = len2[e];
     return sqrt(f32 ? __longlong_as_double(q) : (double)q);
 }
 
 __global__ void __launch_bounds__(256) k_elv_sum(const int64_t *__restrict__ len2, int64_t E,
-                                                 double *__restrict__ part, bool f32) {
+                                                 double *__restrict__ len, double *__restrict__ part, bool f32) {
     __shared__ double sh[32];
     double s = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
-         e += (int64_t)kElvBlocks * blockDim.x)
-        s += edge_length(len2, e, f32);
+         e += (int64_t)kElvBlocks * blockDim.x) {
+        const double l = edge_length(len2, e, f32);
+        len[e] = l;
+        s += l;
+    }
     s = block_sum<double>(s, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 // Pass 2: every block recomputes the mean from the pass-1 partials in the
 // same fixed order, then sums (l_e - mean)^2 over its subset.
-__global__ void __launch_bounds__(256) k_elv_var(const int64_t *__restrict__ len2, int64_t E,
-                                                 double *__restrict__ part, bool f32) {
+__global__ void __launch_bounds__(256) k_elv_var(const double *__restrict__ len, int64_t E,
+                                                 double *__restrict__ part) {
     __shared__ double sh[32];
     double m = 0.0;
     for (int i = threadIdx.x; i < kElvBlocks; i += blockDim.x) m += part[i];
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(256) k_elv_var(const int64_t *__restrict__ len
     double s = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
          e += (int64_t)kElvBlocks * blockDim.x) {
-        const double t = edge_length(len2, e, f32) - m;
+        const double t = len[e] - m;
         s += t * t;
     }
     s = block_sum<double>(s, sh);
@@ -448,8 +452,8 @@ void launch_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *blo
 
 void launch_elv(const Buffers &b, int64_t E, cudaStream_t s, bool f32) {
     count_launches(2);
-    k_elv_sum<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part, f32);
-    k_elv_var<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_part, f32);
+    k_elv_sum<<<kElvBlocks, 256, 0, s>>>(b.len2, E, b.elv_len, b.elv_part, f32);
+    k_elv_var<<<kElvBlocks, 256, 0, s>>>(b.elv_len, E, b.elv_part);
 }
 
 void launch_batch_elv(const Buffers &b, const BatchView &bv, cudaStream_t s) {

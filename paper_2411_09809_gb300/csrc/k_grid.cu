@@ -19,11 +19,14 @@
 // of two long records, and those pairs go to the all-pairs tiles over the
 // list of long segments instead (a grid cannot prune them: two long segments
 // share about as many cells as there are such pairs).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "grid_common.cuh"
 
 namespace gr {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -131,6 +134,155 @@ __global__ void __launch_bounds__(256) k_cell_items(const uint32_t *__restrict__
     }
     w = block_sum<uint64_t>(w, sh);
     if (threadIdx.x == 0) atomic_add_u64(&acc->grid_work, w);
+}
+
+// a3 + work items in one launch, for grids of at most kOffsetsMaxCells
+// cells: the exclusive scan of the per-cell record counts (in place), the
+// work items per cell and their exclusive scan, the candidate-pair total and
+// the overflow flags -- what the three-kernel scans and k_cell_items do.  One
+// thread-block cluster of kOffsetsCluster CTAs, 16 cells a thread: each CTA
+// scans its cells, publishes its two totals in shared memory, and after a
+// cluster barrier reads the totals of the CTAs before it through distributed
+// shared memory.  Each thread reads its cells' counts before it overwrites
+// them with offsets, and no other thread touches them (in place).
+constexpr int kOffsetsThreads = 512, kOffsetsPer = 16, kOffsetsCluster = 8;
+constexpr int kOffsetsMaxCells = kOffsetsCluster * kOffsetsThreads * kOffsetsPer;  // 65,536
+
+__device__ __forceinline__ void block_excl_scan2(uint64_t a, uint64_t b, uint64_t &ea, uint64_t &eb, uint64_t &ta,
+                                                 uint64_t &tb, uint64_t (*sh)[32]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t ya = __shfl_up_sync(0xffffffffu, ia, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += ya; ib += yb; }
+    }
+    if (lane == 31) { sh[0][wid] = ia; sh[1][wid] = ib; }
+    __syncthreads();
+    if (wid == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        const uint64_t wa = in ? sh[0][lane] : 0ull, wb = in ? sh[1][lane] : 0ull;
+        uint64_t xa = wa, xb = wb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
+            if (lane >= o) { xa += ya; xb += yb; }
+        }
+        sh[0][lane] = xa - wa;  // exclusive warp offsets
+        sh[1][lane] = xb - wb;
+        if (lane == 31) { sh[2][0] = xa; sh[2][1] = xb; }  // totals (zeros past the last warp)
+    }
+    __syncthreads();
+    ea = sh[0][wid] + ia - a;
+    eb = sh[1][wid] + ib - b;
+    ta = sh[2][0];
+    tb = sh[2][1];
+}
+
+__global__ void __cluster_dims__(kOffsetsCluster, 1, 1) __launch_bounds__(kOffsetsThreads)
+    k_grid_offsets(uint32_t *__restrict__ cell_off, const uint32_t *__restrict__ cell_nl, int C,
+                   uint32_t *__restrict__ item_off, DevAcc *acc) {
+    __shared__ uint64_t sh[3][32];
+    __shared__ uint64_t cta_tot[2];
+    __shared__ uint64_t base_sh[4];
+    __shared__ uint64_t shw[32];
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    const int c0 = (int)rank * kOffsetsThreads * kOffsetsPer + threadIdx.x * kOffsetsPer;
+    // whole runs of 16 cells by 16-byte accesses (C = G^2 is a multiple of 16
+    // for G >= 4); the tail of smaller grids cell by cell
+    const bool full = c0 + kOffsetsPer <= C;
+    uint32_t n[kOffsetsPer], it[kOffsetsPer];
+    uint64_t tr = 0, ti = 0, work = 0;
+    bool over = false;
+#pragma unroll
+    for (int q = 0; q < kOffsetsPer / 4; ++q) {
+        uint32_t vn[4], vl[4];
+        if (full) {
+            const uint4 v = *(const uint4 *)(cell_off + c0 + 4 * q);
+            const uint4 l = *(const uint4 *)(cell_nl + c0 + 4 * q);
+            vn[0] = v.x; vn[1] = v.y; vn[2] = v.z; vn[3] = v.w;
+            vl[0] = l.x; vl[1] = l.y; vl[2] = l.z; vl[3] = l.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = c0 + 4 * q + j;
+                vn[j] = c < C ? cell_off[c] : 0u;
+                vl[j] = c < C ? cell_nl[c] : 0u;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint64_t nn = vn[j], ns = nn - vl[j];
+            bool tiles_over;
+            const uint64_t items = cell_item_count(nn, ns, &tiles_over);
+            over |= items > 0x7fffffffull || tiles_over;
+            n[4 * q + j] = vn[j];
+            it[4 * q + j] = (uint32_t)min(items, (uint64_t)0x7fffffffull);
+            work += ns * (ns - (ns > 0)) / 2 + ns * (nn - ns);
+            tr += vn[j];
+            ti += it[4 * q + j];
+        }
+    }
+    uint64_t er, ei, sr, si;
+    block_excl_scan2(tr, ti, er, ei, sr, si, sh);
+    if (threadIdx.x == 0) {
+        cta_tot[0] = sr;
+        cta_tot[1] = si;
+    }
+    cluster.sync();
+    if (threadIdx.x == 0) {
+        uint64_t br = 0, bi = 0, ar = 0, ai = 0;
+        for (unsigned q = 0; q < (unsigned)kOffsetsCluster; ++q) {
+            const uint64_t *t = cluster.map_shared_rank(cta_tot, q);
+            const uint64_t x = t[0], y = t[1];
+            if (q < rank) { br += x; bi += y; }
+            ar += x;
+            ai += y;
+        }
+        base_sh[0] = br; base_sh[1] = bi; base_sh[2] = ar; base_sh[3] = ai;
+    }
+    __syncthreads();
+    uint64_t r = base_sh[0] + er, i = base_sh[1] + ei;
+#pragma unroll
+    for (int q = 0; q < kOffsetsPer / 4; ++q) {
+        uint32_t o[4], oi[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            o[j] = (uint32_t)r;
+            oi[j] = (uint32_t)i;
+            r += n[4 * q + j];
+            i += it[4 * q + j];
+        }
+        if (full) {
+            *(uint4 *)(cell_off + c0 + 4 * q) = make_uint4(o[0], o[1], o[2], o[3]);
+            *(uint4 *)(item_off + c0 + 4 * q) = make_uint4(oi[0], oi[1], oi[2], oi[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = c0 + 4 * q + j;
+                if (c < C) {
+                    cell_off[c] = o[j];
+                    item_off[c] = oi[j];
+                }
+            }
+        }
+    }
+    work = block_sum<uint64_t>(work, shw);
+    const int any_over = __syncthreads_or(over ? 1 : 0);
+    if (threadIdx.x == 0) {
+        if (work) atomic_add_u64(&acc->grid_work, work);
+        if (any_over) atomicOr(&acc->grid_flags, GF_ITEMS_OVERFLOW);
+        if (rank == 0) {
+            const uint64_t ar = base_sh[2], ai = base_sh[3];
+            cell_off[C] = (uint32_t)ar;
+            item_off[C] = (uint32_t)ai;
+            acc->records = ar;
+            acc->grid_items = ai;
+            if (ar > 0xffffffffull || ai > 0xffffffffull) atomicOr(&acc->eval_status, ST_SCAN_OVERFLOW);
+        }
+    }
+    cluster.sync();  // no CTA leaves while another may still read its totals
 }
 
 // Descriptor of every work item, two 16-byte words: {record offset of its
@@ -252,12 +404,18 @@ void launch_grid_count(const Buffers &b, int64_t E, const GridBuffers &g, int k,
     const int C = (65536 >> k) * (65536 >> k);
     cudaMemsetAsync(g.cell_off, 0, sizeof(uint32_t) * (C + 1), s);
     cudaMemsetAsync(g.cell_nl, 0, sizeof(uint32_t) * C, s);
-    count_launches(E > 0 ? 2 : 1);
+    count_launches(E > 0 ? 1 : 0);
     if (E > 0)
         k_grid_count<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, b.acc, k, split ? 1 : 0,
                                                                  g.cell_off, g.cell_nl, g.seg_long, g.theta_long,
                                                                  g.eid_long);
+    if (C <= kOffsetsMaxCells) {
+        count_launches(1);
+        k_grid_offsets<<<kOffsetsCluster, kOffsetsThreads, 0, s>>>(g.cell_off, g.cell_nl, C, g.item_off, b.acc);
+        return;
+    }
     launch_scan_u32(g.cell_off, g.cell_off, C, b.scan_tmp, &b.acc->records, &b.acc->eval_status, s);
+    count_launches(1);
     k_cell_items<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.cell_off, g.cell_nl, C, g.item_off, b.acc);
     launch_scan_u32(g.item_off, g.item_off, C, b.scan_tmp, &b.acc->grid_items, &b.acc->eval_status, s);
 }
