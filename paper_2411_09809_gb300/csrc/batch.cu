@@ -989,6 +989,7 @@ gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_of
     B_CU2(cudaMemcpy(B->d_eoff, eo.data(), sizeof(int64_t) * (n_layouts + 1), cudaMemcpyHostToDevice));
     B_CU2(cudaMemset(B->d_res, 0, sizeof(gr_result) * n_layouts));
     B_CU2(cudaMemset(b.acc, 0, sizeof(DevAcc)));
+    B_CU2(init_min_angle_table(B->stream));
     B_TRY(enqueue_inputs(B, xy, edges));
     // validation and the per-layout statistics of the plan
     B_CU2(cudaMemsetAsync(B->d_nseg, 0, sizeof(unsigned long long) * n_layouts, B->stream));

@@ -646,6 +646,10 @@ gr_status gr_layout_create(gr_layout **out, const void *xy, gr_coord_type coord_
     L->coord = coord_type;
     if (opt) L->opt = *opt;
     gr_status st = alloc_layout(L);
+    if (st == GR_OK) {
+        const cudaError_t e = init_min_angle_table(L->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "uploading the minimum-angle table");
+    }
     if (st == GR_OK && L->opt.profile) st = set_profiling(L, true);
     if (st == GR_OK) st = enqueue_inputs(L, xy, edges);
     if (st == GR_OK) {

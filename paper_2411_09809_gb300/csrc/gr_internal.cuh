@@ -235,6 +235,9 @@ void launch_min_angle(Buffers &b, int64_t V, int64_t E, cudaStream_t s);
 void launch_min_angle_moved(Buffers &b, int64_t V, const int32_t *ids, const int64_t *np, int64_t cap,
                             cudaStream_t s);
 int min_angle_blocks(int64_t V);
+// Uploads the FP64 sector table of the minimum-angle kernels (cosine and
+// sine of 256 evenly spaced angles) to the current device, ordered on s.
+cudaError_t init_min_angle_table(cudaStream_t s);
 
 // a10: edge length variation, two passes of deterministic FP64 partials.
 // `f32`: len2 holds FP64 squared lengths (as bits) instead of int64.

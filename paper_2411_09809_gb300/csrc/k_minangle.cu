@@ -102,9 +102,43 @@ __device__ __forceinline__ float ccw_gap_f(int2 a, int2 b) {
     return g < 0.f ? g + 6.28318530717958647692f : g;
 }
 
+// FP64 counter-clockwise angle from a to b, in [0, 2 pi), by table-driven
+// argument reduction (Tang's method): (X, Y) = (a . b, a x b) are exact; the
+// FP32 atan2 picks the sector j of width w = 2 pi / kSectors nearest to the
+// angle; (X, Y) is rotated back by j w with cosine and sine from an FP64
+// table (built on the host); the residual angle atan(t), t = Y' / X' with
+// |t| <= tan(w / 2 + 1e-6) < 0.0123, is the odd Taylor series through t^9
+// (the next term is below 2^-60 of t).  About half the FP64 work of a general
+// atan2, and as accurate: the rotation and the series each add a few units
+// in the last place.
+constexpr int kSectors = 256;
+constexpr double kTwoPi = 2.0 * 3.14159265358979323846;
+constexpr double kSectorW = kTwoPi / kSectors;
+__device__ double2 g_sector[kSectors];  // (cos, sin)(j kSectorW)
+
 __device__ __forceinline__ double ccw_gap_d(int2 a, int2 b) {
-    double g = atan2((double)cross2(a, b), (double)dot2(a, b));
-    return g < 0.0 ? g + 2.0 * M_PI : g;
+    const long long cr = cross2(a, b), dt = dot2(a, b);
+    const float g = atan2f(ll2f_rn(cr), ll2f_rn(dt));  // (-pi, pi], |cross|, |dot| < 2^34
+    const int j = __float2int_rn(g * (float)(kSectors / kTwoPi)) & (kSectors - 1);
+    const double2 cs = __ldg(&g_sector[j]);
+    const double X = (double)dt, Y = (double)cr;
+    const double x = fma(X, cs.x, Y * cs.y);     // rotation by -j w
+    const double y = fma(Y, cs.x, -(X * cs.y));
+    const double t = y / x, t2 = t * t;
+    const double p = fma(fma(fma(fma(t2, 1.0 / 9.0, -1.0 / 7.0), t2, 1.0 / 5.0), t2, -1.0 / 3.0), t2, 1.0);
+    double th = fma(t, p, (double)j * kSectorW);
+    if (th < 0.0) th += kTwoPi;
+    if (th >= kTwoPi) th -= kTwoPi;
+    return th;
+}
+
+// d_v = (2 pi / k - gap) / (2 pi / k) for the smallest of the k gaps, which
+// is at most 2 pi / k: a rounding below zero (a gap of exactly 2 pi / k, one
+// unit in the last place off) is clamped, so d_v >= 0 always and -1 stays
+// the only "not counted" mark.
+__device__ __forceinline__ double dv_of_gap(double gap, int k) {
+    const double ideal = kTwoPi / (double)k;
+    return fmax(0.0, (ideal - gap) / ideal);
 }
 
 // d_v of a vertex from its k incident directions d[0, k) by one thread:
@@ -121,8 +155,7 @@ __device__ __forceinline__ double vertex_dv(const int2 *__restrict__ d, int k) {
         const float g = ccw_gap_f(di, db);
         if (better_gap(g, di, gmin, bi)) { gmin = g; bi = di; bs = db; }
     }
-    const double ideal = 2.0 * M_PI / (double)k;
-    return (ideal - ccw_gap_d(bi, bs)) / ideal;
+    return dv_of_gap(ccw_gap_d(bi, bs), k);
 }
 
 // The vertices [v0, v1) taken by this block: one thread per vertex, and
@@ -178,8 +211,7 @@ __device__ __forceinline__ void min_angle_range(const uint32_t *__restrict__ off
                 if (better_gap(og, obi, gmin, bi)) { gmin = og; bi = obi; bs = obs; }
             }
             if (lane == src) {
-                const double ideal = 2.0 * M_PI / (double)hk;
-                const double x = (ideal - ccw_gap_d(bi, bs)) / ideal;
+                const double x = dv_of_gap(ccw_gap_d(bi, bs), hk);
                 if (dv) dv[v] = x;
                 dsum += x;
                 nv += 1;
@@ -389,6 +421,17 @@ int grid_for(int64_t n, int threads, int max_blocks) {
 }
 
 }  // namespace
+
+cudaError_t init_min_angle_table(cudaStream_t s) {
+    static const struct Table {
+        double2 v[kSectors];
+        Table() {
+            for (int j = 0; j < kSectors; ++j)
+                v[j] = make_double2(cos((double)j * kSectorW), sin((double)j * kSectorW));
+        }
+    } table;
+    return cudaMemcpyToSymbolAsync(g_sector, table.v, sizeof table.v, 0, cudaMemcpyHostToDevice, s);
+}
 
 int min_angle_blocks(int64_t V) {
     int64_t b = (V + MA_THREADS - 1) / MA_THREADS;
