@@ -108,9 +108,9 @@ __device__ __forceinline__ float ccw_gap_f(int2 a, int2 b) {
 // angle; (X, Y) is rotated back by j w with cosine and sine from an FP64
 // table (built on the host); the residual angle atan(t), t = Y' / X' with
 // |t| <= tan(w / 2 + 1e-6) < 0.0123, is the odd Taylor series through t^9
-// (the next term is below 2^-60 of t).  About half the FP64 work of a general
-// atan2, and as accurate: the rotation and the series each add a few units
-// in the last place.
+// (the next term is below 2^-60 of t).  Fewer FP64 instructions than a
+// general atan2 and as accurate: the rotation and the series each add a few
+// units in the last place.
 constexpr int kSectors = 256;
 constexpr double kTwoPi = 2.0 * 3.14159265358979323846;
 constexpr double kSectorW = kTwoPi / kSectors;
@@ -118,7 +118,7 @@ __device__ double2 g_sector[kSectors];  // (cos, sin)(j kSectorW)
 
 __device__ __forceinline__ double ccw_gap_d(int2 a, int2 b) {
     const long long cr = cross2(a, b), dt = dot2(a, b);
-    const float g = atan2f(ll2f_rn(cr), ll2f_rn(dt));  // (-pi, pi], |cross|, |dot| < 2^34
+    const float g = atan2f(ll2f_rn(cr), ll2f_rn(dt));  // (-pi, pi], |cross|, |dot| < 2^33
     const int j = __float2int_rn(g * (float)(kSectors / kTwoPi)) & (kSectors - 1);
     const double2 cs = __ldg(&g_sector[j]);
     const double X = (double)dt, Y = (double)cr;
