@@ -684,15 +684,18 @@ def run_differentiable(args, rank, world, local_rank):
 def move_roofline(L, ms: float) -> dict:
     """A move against HBM: its algorithmic bytes are dominated by the O(E) passes (the regather:
     8 B of ids, 16 B of coordinates, 16 + 4 + 4 B of segment, id and direction, 8 B of squared length
-    per edge; the edge length variation: 2 x 8 B per edge; the affected-edge scan: 8 B of ids and 8 B
-    of moved flags per edge).  The step is latency-bound: the fraction is small by construction."""
+    per edge, and 8 B of coordinates per vertex for the range check; the edge length variation: the
+    squared length read, the length written and read back, 3 x 8 B per edge; the affected-edge scan:
+    8 B of ids and 8 B of moved flags per edge).  The step is latency-bound: the fraction is small by
+    construction."""
     peaks, peak_kind = load_peaks()
-    nbytes = L.E * (56 + 16 + 16)
+    nbytes = L.E * (56 + 24 + 16) + L.V * 8
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = nbytes / (ms / 1e3) / 1e9
     return {"kernel": "the whole move (the O(E) regather, edge length variation and affected-edge scan)",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": f"hbm_gbs ({peak_kind})", "work": "88 B per edge", "traffic": None}
+            "peak_source": f"hbm_gbs ({peak_kind})", "work": "96 B per edge + 8 B per vertex",
+            "traffic": None}
 
 
 def run_moves(args, rank, world, local_rank):
