@@ -4,7 +4,8 @@ Barrett-reduced visiting order of the DDA passes (a bijection equal to
 i * (2^31 - 1) mod n), the cells each thread of the offsets cluster reads and
 writes (every cell of [0, C) exactly once, 16-byte accesses aligned), and the
 integer scaling of a line direction to units of pi / 2^32 (the FP64 product
-rounded to the nearest integer)."""
+rounded to the nearest integer); and the minimum angle's table-driven FP64
+gap against atan2 (with NumPy's FP32 atan2 standing in for the device's)."""
 import math
 import os
 import re
@@ -93,3 +94,44 @@ def test_line_direction_scaling_equals_the_fp64_product():
         sh = 180 - be
         got = (m * K + (1 << (sh - 1))) >> sh if be >= 90 else 0
         assert got == int(w)
+
+
+def sector_gap(a, b, tab, w):
+    # k_minangle.cu ccw_gap_d, FP64 steps in the same order
+    cr = a[0] * b[1] - a[1] * b[0]
+    dt = a[0] * b[0] + a[1] * b[1]
+    g = np.arctan2(np.float32(cr), np.float32(dt))
+    j = int(np.rint(np.float32(g) * np.float32(len(tab) / (2 * math.pi)))) & (len(tab) - 1)
+    c, s_ = tab[j]
+    X, Y = float(dt), float(cr)
+    x = X * c + Y * s_
+    y = Y * c - X * s_
+    t = y / x
+    t2 = t * t
+    p = (((t2 / 9.0 - 1.0 / 7.0) * t2 + 1.0 / 5.0) * t2 - 1.0 / 3.0) * t2 + 1.0
+    th = t * p + j * w
+    if th < 0.0:
+        th += 2 * math.pi
+    if th >= 2 * math.pi:
+        th -= 2 * math.pi
+    return th
+
+
+def test_min_angle_sector_gap_matches_atan2():
+    s = source("k_minangle.cu")
+    n = int(re.search(r"constexpr int kSectors = (\d+);", s).group(1))
+    w = 2.0 * math.pi / n
+    tab = [(math.cos(j * w), math.sin(j * w)) for j in range(n)]
+    rng = np.random.default_rng(7)
+    vecs = [tuple(int(v) for v in rng.integers(-65535, 65536, size=2)) for _ in range(4000)]
+    vecs += [(1, 0), (-1, 0), (0, 1), (0, -1), (65535, 1), (-65535, 1), (3, 4), (-4, 3)]
+    worst = 0.0
+    for i in range(len(vecs) - 1):
+        a, b = vecs[i], vecs[i + 1]
+        if a == (0, 0) or b == (0, 0):
+            continue
+        ref = math.atan2(a[0] * b[1] - a[1] * b[0], a[0] * b[0] + a[1] * b[1])
+        ref = ref + 2 * math.pi if ref < 0 else ref
+        d = abs(sector_gap(a, b, tab, w) - ref)
+        worst = max(worst, min(d, 2 * math.pi - d))
+    assert worst < 2e-15
