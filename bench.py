@@ -180,6 +180,16 @@ def load_traffic(kernel: str, workload: str, src_hash: str):
     return load_capture(kernel, workload, src_hash).get("dram_bytes_per_launch")
 
 
+# The sources each captured kernel is built from: its own file and every
+# header it includes, so an edit anywhere in them retires the capture.
+KERNEL_SOURCES = {
+    "k_grid_pairs": ["k_grid.cu", "grid_common.cuh", "pair_math.cuh", "gr_internal.cuh"],
+    "k_grid_fill": ["k_grid.cu", "grid_common.cuh", "pair_math.cuh", "gr_internal.cuh"],
+    "k_cross_allpairs_agg": ["k_crossings.cu", "allpairs_common.cuh", "pair_math.cuh", "gr_internal.cuh"],
+    "crossing_phase_f32": ["k_diff.cu", "gr_internal.cuh"],
+}
+
+
 def kernel_source_hash(files: list[str]) -> str:
     import hashlib
     h = hashlib.sha256()
@@ -243,10 +253,8 @@ def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload:
         ops = pairs * OPS_PER_PAIR + ec * (OPS_PER_CROSSING_GRID if grid else OPS_PER_CROSSING_ALLPAIRS)
         peak = SM_COUNT * LANES_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         kernel = "k_grid_pairs" if grid else "k_cross_allpairs_agg"
-        src = (["k_grid.cu", "grid_common.cuh", "pair_math.cuh"] if grid
-               else ["k_crossings.cu", "allpairs_common.cuh", "pair_math.cuh"])
         achieved = ops / t / 1e12
-        cap = load_capture(kernel, workload, kernel_source_hash(src))
+        cap = load_capture(kernel, workload, kernel_source_hash(KERNEL_SOURCES[kernel]))
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Tops/s (int32-equivalent lane ops)", "frac": achieved / peak,
                 "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
@@ -262,7 +270,7 @@ def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload:
     achieved = nbytes / t / 1e9
     return {"kernel": "k_grid_fill", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_kind})",
-            "traffic": load_traffic("k_grid_fill", workload, kernel_source_hash(["k_grid.cu", "grid_common.cuh"])),
+            "traffic": load_traffic("k_grid_fill", workload, kernel_source_hash(KERNEL_SOURCES["k_grid_fill"])),
             "launch_ms": t * 1e3}
 
 
@@ -479,7 +487,7 @@ def run_batched(args, rank, world, local_rank):
         line["cpu_baseline"] = {"value": n / cb_s, "unit": "layouts/s", "cores": oracle.num_threads(),
                                 "kind": "oracle",
                                 "sample": f"{n_sample} layouts stratified by size, all five metrics, scaled to {n}"}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def batch_oracle_step(v_off, e_off, xy, edges, d) -> tuple[float, int]:
@@ -656,7 +664,7 @@ def run_differentiable(args, rank, world, local_rank):
           "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM_PER_CLK} lanes x "
                          f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock)",
           "traffic": load_traffic("crossing_phase_f32" if grid else "k_cross_f32", "differentiable",
-                                  kernel_source_hash(["k_diff.cu"])),
+                                  kernel_source_hash(KERNEL_SOURCES["crossing_phase_f32"])),
           "launch_ms": t * 1e3, "pairs_tested": res.crossing.c.pairs_tested}
     line = {
         "metric": "fwd+bwd steps/s", "value": world * 1e3 / ms, "unit": "steps/s", "n_gpus": world,
@@ -678,7 +686,7 @@ def run_differentiable(args, rank, world, local_rank):
         cb = cpu_oracle_diff_step(L, args.cpu_budget)
         line["cpu_baseline"] = {"value": 1.0 / cb["step_s"], "unit": "steps/s", "cores": cb["cores"],
                                 "kind": "oracle", "sample": cb["sample"]}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def move_roofline(L, ms: float) -> dict:
@@ -1277,7 +1285,38 @@ def run_ours(args, rank, world, local_rank):
         cb = cpu_oracle_step(L, d, args.cpu_budget)
         line["cpu_baseline"] = {"value": pairs / cb["step_s"], "unit": "pairs/s", "cores": cb["cores"],
                                 "kind": "oracle", "sample": cb["sample"]}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+# The other workloads the headline metric names, measured in the default run
+# beside the large sparse layout: the dense long-edge layout (edge-pair
+# tests/s on the all-pairs tiles), the batch of 4,096 layouts (layouts/s) and
+# the differentiable form (fwd+bwd steps/s and fwd+bwd / fwd).  Each is its
+# own bounded run (its own warm-up, timed steps, clocks, roofline, e2e and
+# oracle baseline).
+SUB_WORKLOADS = ("dense_long_edge", "batched", "differentiable")
+SUB_STEPS = 10
+SUB_CPU_BUDGET = 8.0
+
+
+def run_sub_workloads(args, rank, world, local_rank) -> dict:
+    out = {}
+    for name in SUB_WORKLOADS:
+        sub = argparse.Namespace(**vars(args))
+        sub.workload = name
+        sub.steps = min(args.steps, SUB_STEPS)
+        sub.cpu_budget = min(args.cpu_budget, SUB_CPU_BUDGET)
+        sub.cell_log2 = 0
+        sub.long_pairs = "auto"
+        if name == "batched":
+            r = run_batched(sub, rank, world, local_rank)
+        elif name == "differentiable":
+            r = run_differentiable(sub, rank, world, local_rank)
+        else:
+            r = run_ours(sub, rank, world, local_rank)
+        if r is not None:
+            out[name] = r
+    return out
 
 
 def main():
@@ -1294,6 +1333,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (for profiler runs)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="default workload: skip the dense, batched and differentiable runs reported beside it")
     ap.add_argument("--no-single-loop", action="store_true",
                     help="batched workload: skip the one-layout-at-a-time comparison (for profiler runs)")
     args = ap.parse_args()
@@ -1307,10 +1348,11 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
+        line = None
         if args.workload == "batched":
-            run_batched(args, rank, world, local_rank)
+            line = run_batched(args, rank, world, local_rank)
         elif args.workload == "differentiable":
-            run_differentiable(args, rank, world, local_rank)
+            line = run_differentiable(args, rank, world, local_rank)
         elif args.workload == "moves":
             run_moves(args, rank, world, local_rank)
         elif args.workload == "strips":
@@ -1318,7 +1360,11 @@ def main():
         elif args.workload == "per_edge":
             run_per_edge(args, rank, world, local_rank)
         else:
-            run_ours(args, rank, world, local_rank)
+            line = run_ours(args, rank, world, local_rank)
+            if args.workload == "large_sparse" and world == 1 and not args.no_workloads and line is not None:
+                line["workloads"] = run_sub_workloads(args, rank, world, local_rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
     finally:
         if world > 1:
             import torch.distributed as dist

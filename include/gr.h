@@ -265,17 +265,29 @@ gr_status gr_move_vertices(gr_layout *layout, int64_t n, const int32_t *ids, con
  * gr_diff_forward evaluates E_ca (ideal `ideal_rad`, <= 0 for 70 deg), M_l
  * and M_a (Sec. 2.1, Algorithms 2, 3, 5) into out3 = {E_ca, M_l, M_a} (host or
  * device memory), keeps the crossing pairs and every vertex's smallest gap,
- * and synchronises.  gr_diff_backward then writes to d_grad_xy ([V][2] FP32,
- * DEVICE memory, overwritten) the gradient of
+ * and synchronises the host (it sizes its buffers from counts it reads back).
+ * gr_diff_backward then writes to d_grad_xy ([V][2] FP32, DEVICE memory,
+ * overwritten) the gradient of
  *   gout3[0] * E_ca + gout3[1] * M_l + gout3[2] * M_a
  * with respect to the coordinates, with that crossing set and those gaps held
  * fixed (the metrics are piecewise smooth; the gradient is the one of the
- * current piece).  `gout3` may be device or host memory; with device memory
- * the call is stream-ordered and does not synchronise.  The paper defines the
- * metrics only; the gradient is this library's addition (layout optimisation
- * is the application the paper names). */
-gr_status gr_diff_forward(gr_layout *layout, double ideal_rad, float *out3);
-gr_status gr_diff_backward(gr_layout *layout, const float *gout3, float *d_grad_xy);
+ * current piece).  The paper defines the metrics only; the gradient is this
+ * library's addition (layout optimisation is the application the paper names).
+ *
+ * Streams: both calls are ordered after the work already queued on `stream`
+ * (NULL: the layout's own stream), and later work on `stream` sees their
+ * outputs.  gr_diff_forward returns GR_ENOTSUP while `stream` is being
+ * captured into a CUDA graph.  gr_diff_backward with `gout3` in device memory
+ * does not synchronise the host (host memory: it does, after copying gout3);
+ * while `stream` is being captured it adds its kernels to the caller's graph
+ * (gout3 must then be device memory), and each replay of that graph computes
+ * the gradient of the last gr_diff_forward that completed before the replay
+ * (the crossing pairs are read through the layout at replay time).  Replays,
+ * backward calls and forwards of one layout share its scratch buffers, so
+ * they must not overlap on the GPU.  GR_ENOTSUP also when the layout's own
+ * stream is being captured while `stream` names another one. */
+gr_status gr_diff_forward(gr_layout *layout, double ideal_rad, float *out3, gr_stream_t stream);
+gr_status gr_diff_backward(gr_layout *layout, const float *gout3, float *d_grad_xy, gr_stream_t stream);
 
 /* ------------------------------------------------------------- batches
  * Many independent layouts evaluated together (the batched form of the five
@@ -367,8 +379,9 @@ int64_t gr_kernel_launches(void);
  * gr_layout_create); `out` is device or host memory.  Work runs on `stream`
  * and the call synchronises it.  Scratch is a fixed array of about 1 MiB in
  * the library's device image, held by every GPU that loads the library
- * until the process exits.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
+ * until the process exits.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) with its device current; the first call on a device
+ * is the set-up that also loads the library's module there, so make that
  * first call before any stream capture on the device.  Every call reuses the
  * same array: calls whose GPU work overlaps (other streams or host threads)
  * race and must be serialised by the caller.  GR_EINVAL for E above the

@@ -27,7 +27,7 @@ class _Terms(torch.autograd.Function):
     def forward(ctx, xy, module):
         layout = module._layout_for(xy)
         out = torch.empty(3, dtype=torch.float32, device=xy.device)
-        gr.gr_diff_forward(layout.handle, module.ideal_rad, out)
+        gr.gr_diff_forward(layout.handle, module.ideal_rad, out, torch.cuda.current_stream(xy.device).cuda_stream)
         module._generation += 1
         ctx.module = module
         ctx.generation = module._generation
@@ -41,7 +41,8 @@ class _Terms(torch.autograd.Function):
             raise RuntimeError("ReadabilityTerms: backward must follow its own forward "
                                "(the module ran another forward in between)")
         grad = torch.empty(ctx.shape, dtype=torch.float32, device=gout.device)
-        gr.gr_diff_backward(module._layout.handle, gout.detach().to(torch.float32).contiguous(), grad)
+        gr.gr_diff_backward(module._layout.handle, gout.detach().to(torch.float32).contiguous(), grad,
+                            torch.cuda.current_stream(gout.device).cuda_stream)
         return grad, None
 
 

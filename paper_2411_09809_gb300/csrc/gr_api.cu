@@ -81,6 +81,8 @@ struct gr_layout {
     // differentiable form (FP32 layouts)
     uint2 *pairs = nullptr;         // E_c pairs of the last forward
     uint64_t pairs_cap = 0, n_pairs = 0;
+    uint2 **pairs_slot = nullptr;   // device copy of `pairs`: a captured backward reads the current buffer
+    cudaEvent_t ev_din = nullptr, ev_dout = nullptr;  // orders the differentiable calls with the caller's stream
     int2 *arg = nullptr;            // [V] smallest gap of every vertex
     DiffState *st = nullptr;
     float *out3 = nullptr, *gout3 = nullptr;
@@ -167,7 +169,7 @@ namespace {
 std::atomic<int64_t> g_launches{0};
 
 void free_grid(GridBuffers &g) {
-    void *ptrs[] = {g.cell_off, g.cell_nl, g.item_off, g.cell_fill, g.rec, g.item_desc, g.ocell_off, g.ocell_fill,
+    void *ptrs[] = {g.cell_off, g.cell_nl, g.item_off, g.cell_fill, g.rec, g.rgeo, g.item_desc, g.ocell_off, g.ocell_fill,
                     g.opts, g.seg_long, g.theta_long, g.eid_long};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -179,7 +181,7 @@ void free_layout(gr_layout *L) {
     Buffers &b = L->b;
     void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.elv_len, b.ma_part,
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result,
-                    b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->arg, L->st, L->out3, L->gout3,
+                    b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->pairs_slot, L->arg, L->st, L->out3, L->gout3,
                     L->f32_work, L->theta_adj, L->moved, L->affected, L->dacc, L->mv_ids, L->mv_xy,
                     L->dirty.flag, L->dirty.list, L->dirty.n, L->mp_dev, b.adj_off, b.adj, b.ma_nz, b.ma_dv, b.ma_touch,
                     b.ma_flag};
@@ -197,6 +199,8 @@ void free_layout(gr_layout *L) {
     for (auto &e : L->ev)
         if (e) cudaEventDestroy(e);
     if (L->ev_fork) cudaEventDestroy(L->ev_fork);
+    if (L->ev_din) cudaEventDestroy(L->ev_din);
+    if (L->ev_dout) cudaEventDestroy(L->ev_dout);
     if (L->ev_join) cudaEventDestroy(L->ev_join);
     if (L->ev_join2) cudaEventDestroy(L->ev_join2);
     if (L->side) cudaStreamDestroy(L->side);
@@ -258,6 +262,7 @@ gr_status alloc_layout(gr_layout *L) {
         GR_TRY(dalloc(&L->out3, 3));
         GR_TRY(dalloc(&L->gout3, 3));
         GR_TRY(dalloc(&L->theta_adj, (size_t)E));
+        GR_TRY(dalloc(&L->pairs_slot, 1));
     }
 #undef GR_TRY
     GR_CU(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
@@ -306,10 +311,13 @@ gr_status ensure_records(gr_layout *L, uint64_t R, uint64_t items) {
     gr_status st;
     if (g.rec_cap < R || !g.rec) {
         if (g.rec) cudaFree(g.rec);
+        if (g.rgeo) cudaFree(g.rgeo);
         g.rec = nullptr;
+        g.rgeo = nullptr;
         g.rec_cap = 0;
         const uint64_t cap = R + R / 4 + 1024;
         if ((st = dalloc(&g.rec, (size_t)cap)) != GR_OK) return st;
+        if ((st = dalloc(&g.rgeo, 3 * (size_t)cap)) != GR_OK) return st;
         g.rec_cap = cap;
     }
     if (g.items_cap < items || !g.item_desc) {
@@ -559,6 +567,7 @@ gr_status forward_f32(gr_layout *L, uint32_t metrics, double ideal, bool save_pa
         const uint64_t cap0 = 4 * (uint64_t)E + 1024;
         if ((pst = dalloc(&L->pairs, (size_t)cap0)) != GR_OK) return pst;
         L->pairs_cap = cap0;
+        GR_CU(cudaMemcpyAsync(L->pairs_slot, &L->pairs, sizeof L->pairs, cudaMemcpyHostToDevice, s));
     }
     for (int attempt = 0; attempt < 3; ++attempt) {
         GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
@@ -598,6 +607,7 @@ gr_status forward_f32(gr_layout *L, uint32_t metrics, double ideal, bool save_pa
         L->pairs_cap = 0;
         if ((st = dalloc(&L->pairs, (size_t)(np + np / 4 + 1024))) != GR_OK) return st;
         L->pairs_cap = np + np / 4 + 1024;
+        GR_CU(cudaMemcpyAsync(L->pairs_slot, &L->pairs, sizeof L->pairs, cudaMemcpyHostToDevice, s));
     }
     return fail(GR_ENOMEM, "crossing pair buffer could not be sized");
 }
@@ -799,7 +809,7 @@ void enqueue_fast(gr_layout *L, cudaStream_t s, uint32_t metrics, double ideal, 
         launch_grid_scatter(b, E, L->g, fp.cp.k, fp.cp.split, s);
         phase_end(L, GR_PHASE_CROSS_SCATTER, s);
         phase_begin(L, GR_PHASE_CROSS_PAIRS, s);
-        launch_grid_pairs(b, L->g, fp.cp.k, L->g.items_cap, ideal_units(ideal), PerEdge{}, s);
+        launch_grid_pairs(b, L->g, fp.cp.k, fp.cp.split, L->g.items_cap, ideal_units(ideal), PerEdge{}, s);
         if (fp.cp.split) launch_grid_long_pairs(b, L->g, -1, ideal_units(ideal), PerEdge{}, s);
         phase_end(L, GR_PHASE_CROSS_PAIRS, s);
         *path = GR_PATH_GRID;
@@ -1032,7 +1042,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
         launch_grid_scatter(b, E, L->g, cp.k, cp.split, s);
         phase_end(L, GR_PHASE_CROSS_SCATTER);
         phase_begin(L, GR_PHASE_CROSS_PAIRS);
-        launch_grid_pairs(b, L->g, cp.k, L->g.items_cap, ideal_units(ideal), PerEdge{}, s);
+        launch_grid_pairs(b, L->g, cp.k, cp.split, L->g.items_cap, ideal_units(ideal), PerEdge{}, s);
         if (cp.split) launch_grid_long_pairs(b, L->g, -1, ideal_units(ideal), PerEdge{}, s);
         phase_end(L, GR_PHASE_CROSS_PAIRS);
         path = GR_PATH_GRID;
@@ -1053,7 +1063,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
             launch_grid_scatter(b, E, L->g, cp.k, cp.split, s);
             phase_end(L, GR_PHASE_CROSS_SCATTER);
             phase_begin(L, GR_PHASE_CROSS_PAIRS);
-            launch_grid_pairs(b, L->g, cp.k, a.grid_items, ideal_units(ideal), PerEdge{}, s);
+            launch_grid_pairs(b, L->g, cp.k, cp.split, a.grid_items, ideal_units(ideal), PerEdge{}, s);
             if (cp.split) launch_grid_long_pairs(b, L->g, a.n_long, ideal_units(ideal), PerEdge{}, s);
             phase_end(L, GR_PHASE_CROSS_PAIRS);
             path = GR_PATH_GRID;
@@ -1311,7 +1321,7 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
         launch_grid_scatter(b, E, L->g, cp.k, cp.split, s);
         phase_end(L, GR_PHASE_CROSS_SCATTER);
         phase_begin(L, GR_PHASE_CROSS_PAIRS);
-        launch_grid_pairs(b, L->g, cp.k, L->h_acc->grid_items, ideal_units(ideal), pe, s);
+        launch_grid_pairs(b, L->g, cp.k, cp.split, L->h_acc->grid_items, ideal_units(ideal), pe, s);
         if (cp.split) launch_grid_long_pairs(b, L->g, L->h_acc->n_long, ideal_units(ideal), pe, s);
         phase_end(L, GR_PHASE_CROSS_PAIRS);
     } else {
@@ -1559,15 +1569,41 @@ gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const in
     return GR_OK;
 }
 
-gr_status gr_diff_forward(gr_layout *L, double ideal_rad, float *out3) {
+// The stream a differentiable call is ordered on (NULL: the layout's own) and
+// whether it is being captured into a CUDA graph.
+gr_status diff_stream(gr_layout *L, gr_stream_t stream, cudaStream_t *cs, bool *capturing) {
+    *cs = stream ? (cudaStream_t)stream : L->stream;
+    // (the legacy default stream, NULL, is never captured)
+    cudaStreamCaptureStatus c1 = cudaStreamCaptureStatusNone, c2 = cudaStreamCaptureStatusNone;
+    if (*cs) GR_CU(cudaStreamIsCapturing(*cs, &c1));
+    if (*cs != L->stream && L->stream) GR_CU(cudaStreamIsCapturing(L->stream, &c2));
+    if (c2 != cudaStreamCaptureStatusNone)
+        return fail(GR_ENOTSUP, "the layout's own stream is being captured while another stream was named");
+    *capturing = c1 != cudaStreamCaptureStatusNone;
+    if (!L->ev_din) {
+        GR_CU(cudaEventCreateWithFlags(&L->ev_din, cudaEventDisableTiming));
+        GR_CU(cudaEventCreateWithFlags(&L->ev_dout, cudaEventDisableTiming));
+    }
+    return GR_OK;
+}
+
+gr_status gr_diff_forward(gr_layout *L, double ideal_rad, float *out3, gr_stream_t stream) {
     g_err.clear();
     if (!L || !out3) return fail(GR_EINVAL, "NULL argument");
     if (L->coord != GR_COORD_F32) return fail(GR_ENOTSUP, "gr_diff_forward needs a GR_COORD_F32 layout");
+    cudaStream_t cs;
+    bool capturing;
+    gr_status st = diff_stream(L, stream, &cs, &capturing);
+    if (st != GR_OK) return st;
+    if (capturing) return fail(GR_ENOTSUP, "gr_diff_forward synchronises and cannot be captured into a graph");
     gr_params p{ideal_rad, 0};
     double ideal;
     int64_t d;
-    gr_status st = read_params(&p, &ideal, &d);
-    if (st != GR_OK) return st;
+    if ((st = read_params(&p, &ideal, &d)) != GR_OK) return st;
+    if (cs != L->stream) {  // after the work already queued on the caller's stream
+        GR_CU(cudaEventRecord(L->ev_din, cs));
+        GR_CU(cudaStreamWaitEvent(L->stream, L->ev_din, 0));
+    }
     if ((st = refresh_stats(L)) != GR_OK) return st;
     if ((st = status_to_error(L->h_acc->status)) != GR_OK) return st;
     if ((st = forward_f32(L, GR_METRIC_CROSSINGS | GR_METRIC_EDGE_LENGTH | GR_METRIC_MIN_ANGLE, ideal, true)) != GR_OK)
@@ -1580,25 +1616,50 @@ gr_status gr_diff_forward(gr_layout *L, double ideal_rad, float *out3) {
     return GR_OK;
 }
 
-gr_status gr_diff_backward(gr_layout *L, const float *gout3, float *d_grad_xy) {
+gr_status gr_diff_backward(gr_layout *L, const float *gout3, float *d_grad_xy, gr_stream_t stream) {
     g_err.clear();
     if (!L || !gout3 || (L->V > 0 && !d_grad_xy)) return fail(GR_EINVAL, "NULL argument");
     if (L->coord != GR_COORD_F32) return fail(GR_ENOTSUP, "gr_diff_backward needs a GR_COORD_F32 layout");
     if (!L->diff_ready) return fail(GR_EINVAL, "gr_diff_backward needs a gr_diff_forward after the last update");
     if (L->V > 0 && !is_device_pointer(d_grad_xy)) return fail(GR_EINVAL, "the gradient must be device memory");
+    cudaStream_t cs;
+    bool capturing;
+    gr_status st = diff_stream(L, stream, &cs, &capturing);
+    if (st != GR_OK) return st;
+    const bool host_g = !is_device_pointer(gout3);
+    if (capturing) {
+        // the kernels become nodes of the caller's graph; a replay reads the
+        // crossing pairs of the last forward before it through pairs_slot
+        if (host_g) return fail(GR_EINVAL, "while its stream is being captured, gout3 must be device memory");
+        const int64_t l0 = gr_kernel_launches();
+        if (L->V > 0)
+            launch_diff_backward(L->b, L->V, L->E, L->pairs_slot, L->arg, L->st, gout3, L->diff_ideal_u,
+                                 L->theta_adj, d_grad_xy, cs);
+        count_launches((int)(l0 - gr_kernel_launches()));  // nothing ran yet
+        GR_CU(cudaGetLastError());
+        return GR_OK;
+    }
+    if (cs != L->stream) {
+        GR_CU(cudaEventRecord(L->ev_din, cs));
+        GR_CU(cudaStreamWaitEvent(L->stream, L->ev_din, 0));
+    }
     const float *g = gout3;
-    if (!is_device_pointer(gout3)) {
+    if (host_g) {
         GR_CU(cudaMemcpyAsync(L->gout3, gout3, sizeof(float) * 3, cudaMemcpyHostToDevice, L->stream));
         L->io_h2d += (int64_t)sizeof(float) * 3;
         g = L->gout3;
     }
     phase_begin(L, GR_PHASE_DIFF_BACKWARD);
     if (L->V > 0)
-        launch_diff_backward(L->b, L->V, L->E, L->pairs, L->arg, L->st, g, L->diff_ideal_u, L->n_pairs, L->theta_adj,
+        launch_diff_backward(L->b, L->V, L->E, L->pairs_slot, L->arg, L->st, g, L->diff_ideal_u, L->theta_adj,
                              d_grad_xy, L->stream);
     phase_end(L, GR_PHASE_DIFF_BACKWARD);
     GR_CU(cudaGetLastError());
-    if (!is_device_pointer(gout3)) GR_CU(cudaStreamSynchronize(L->stream));  // the host buffer may go away
+    if (cs != L->stream) {  // what follows on the caller's stream sees the gradient
+        GR_CU(cudaEventRecord(L->ev_dout, L->stream));
+        GR_CU(cudaStreamWaitEvent(cs, L->ev_dout, 0));
+    }
+    if (host_g) GR_CU(cudaStreamSynchronize(L->stream));  // the host buffer may go away
     return GR_OK;
 }
 

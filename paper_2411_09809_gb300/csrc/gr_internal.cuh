@@ -110,6 +110,7 @@ struct GridBuffers {
     uint32_t *item_off = nullptr;  // [C + 1] work items per cell, then offsets
     unsigned long long *cell_fill = nullptr; // [C] short (low 32 bits) and long (high) records placed
     GridRec *rec = nullptr;        // [rec_cap] records sorted by cell: short ones first, then long ones
+    float4 *rgeo = nullptr;        // [3 rec_cap] the records' FP32 cell-relative form (rotation kernel, make_rgeo)
     uint64_t rec_cap = 0;
     uint4 *item_desc = nullptr;    // [2 items_cap] {record offset, records, short records, ti << 16 | tj}, {cell}
     uint64_t items_cap = 0;
@@ -210,8 +211,11 @@ void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int 
 // on the device (item_off[C]); the kernel does nothing when the records or
 // items outgrew their buffers (ST_OVERFLOW is raised by the scatter or the
 // descriptor pass).  n_items_hint sizes the launch (0: unknown).
-void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items_hint, uint32_t ideal,
-                       PerEdge pe, cudaStream_t s);
+// Without `split`, the work items are rotation items over every pair of each
+// cell (k_cell_pairs); with it, tile items over short x short and long x
+// short pairs (k_grid_pairs).
+void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, bool split, uint64_t n_items_hint,
+                       uint32_t ideal, PerEdge pe, cudaStream_t s);
 
 // a8 occlusion grid: cell side 2^k >= d.  Count + scan, then scatter + pair
 // kernel.
@@ -388,9 +392,11 @@ void launch_min_angle_f32(Buffers &b, int64_t V, int64_t E, int2 *arg, cudaStrea
 void launch_diff_state(const Buffers &b, int64_t V, int64_t E, double ideal, DiffState *st, float *out3,
                        cudaStream_t s);
 // grad[V][2] = gout[0] dE_ca + gout[1] dM_l + gout[2] dM_a (overwritten).
-void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *pairs, const int2 *arg,
-                          const DiffState *st, const float *gout, uint32_t ideal_u, uint64_t n_pairs, double *adj,
-                          float *grad, cudaStream_t s);
+// The E_c pairs are read through *pairs_slot (their count from st), so a
+// captured launch follows the pair buffer of the last forward before it.
+void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *const *pairs_slot, const int2 *arg,
+                          const DiffState *st, const float *gout, uint32_t ideal_u, double *adj, float *grad,
+                          cudaStream_t s);
 
 // ------------------------------------------------------------------ batches
 // Device view of a batch of layouts packed one after another: layout l owns

@@ -422,3 +422,218 @@ __device__ __forceinline__ void grid_item(const GridRec *__restrict__ cell_rec, 
 }
 
 }  // namespace gr
+
+namespace gr {
+
+// ------------------------------------------------ rotation work items (a6)
+// All pairs of a cell's n records in the rotation order: row i meets rows
+// (i + q) mod n for q = 1 .. n/2, except that for even n the offset n/2 is
+// taken from rows i < n/2 only; every unordered pair of the cell appears
+// exactly once.  A work item is one warp's share: the 32 rows (one per lane;
+// the last chunk of a cell may have fewer) of a chunk and RQ consecutive
+// offsets.  The item's columns, rows 32 c + q0 + t (mod n) for t < 32 + RQ - 1,
+// form a window the warp stages in shared memory, so lane l meets window
+// slot l + (q - q0).
+constexpr int RQ = 16;                 // rotation offsets per work item
+constexpr int RWIN = 32 + RQ - 1;      // window slots of an item
+
+// Work items of a cell with n records; overflow when the item word cannot
+// hold the chunk or offset index.
+__device__ __forceinline__ uint64_t rot_item_count(uint64_t n, bool *overflow) {
+    *overflow = false;
+    if (n < 2) return 0;
+    const uint64_t Q = n >> 1, F = (n + 31) >> 5, P = (Q + RQ - 1) / RQ;
+    *overflow = F > (1u << 15) || P >= (1u << 16);
+    return F * P;
+}
+
+// The item words of a cell, in the order counted by rot_item_count, via
+// emit(i, word) for i in [q, q_end): chunk c, offsets piece p as c << 16 | p.
+template <class F>
+__device__ __forceinline__ void rot_item_words(uint32_t n, uint32_t q, uint32_t q_end, F &&emit) {
+    if (n < 2) return;
+    const uint32_t Q = n >> 1, Fc = (n + 31) >> 5, P = (Q + RQ - 1) / RQ;
+    for (uint32_t c = 0; c < Fc && q < q_end; ++c)
+        for (uint32_t p = 0; p < P && q < q_end; ++p, ++q) emit(q, (c << 16) | p);
+}
+
+// A lane's share of a rotation item: row i of the cell, the item's first
+// offset q0 and the number of offsets this lane takes from it (0: none).
+struct RotLane {
+    int i, q0, cnt;
+};
+
+__device__ __forceinline__ RotLane rot_lane(int n, uint32_t w, int lane) {
+    const int Q = n >> 1, c = (int)((w >> 16) & 0x7fffu), p = (int)(w & 0xffffu);
+    RotLane r;
+    r.i = 32 * c + lane;
+    r.q0 = 1 + p * RQ;
+    const int Qi = ((n & 1) == 0 && r.i >= (n >> 1)) ? Q - 1 : Q;
+    r.cnt = r.i < n ? max(0, min(Qi, r.q0 + RQ - 1) - r.q0 + 1) : 0;
+    if (r.i >= n) r.i = 0;
+    return r;
+}
+
+// The FP32 form of a record for the rotation kernel, written by the scatter
+// into three arrays of float4 (one row each per record): its segment in the
+// coordinates of its cell (origin at the cell's lower-left corner)
+//   a = {ax, ay, bx, by},
+//   b = {ux, uy, nk, v}, nk = -(u x a) rounded and v its margin code,
+//   c = {E0x, E0y, E1x, E1y}, the part of the segment inside the closed cell.
+// A segment is "exact" when |u_x|, |u_y| <= 2^10 and its coordinates lie
+// within 2^12 of the origin (then its line evaluated at integer points within
+// 2^12 of the origin is an exact FP32 integer: products and sums below 2^24),
+// and "whole" when it lies inside the closed cell (its clip points are its
+// own integer endpoints).  v = 0 for an exact whole segment, 64 for another
+// exact one, 8192 otherwise.  kRotFilter is the bound on the FP32 error of
+// one orientation of two records: with |u|, |coordinates| < 2^16 the rounded
+// nk (< 2^33) errs by at most 256, the inner fused multiply-add (< 2^34) by
+// 512 and the outer (< 2^35) by 1024: 1792 in all.
+constexpr float kRotFilter = 4096.f;
+constexpr float kClipExact = 64.f;    // margin of a clip test against an exact line
+constexpr float kClipFiltered = 8192.f;  // ... against any other line
+
+// The clipped part [E0, E1] is computed by Liang and Barsky's parametric
+// clipping against the box [0, w]^2: the parameters t of the box lines are
+// quotients of integers from the fast division (within 2 ulp: |t| error
+// below 2^-23 for t in [0, 1], where t is clamped), E = a + t u rounded, so
+// each coordinate of E is within |u| 2^-23 + ulp(w) / 2 < 2^-6 of the exact
+// point; a whole segment keeps its endpoints exactly.  A segment lying on a
+// line of the cell's border (its clipped part on the border itself) gets NaN
+// clip points, which make every clip test inconclusive.
+__device__ __forceinline__ void make_rgeo(SegRec s, int x0, int y0, int w, float4 &a, float4 &b, float4 &c) {
+    const int ax = px(s.x) - x0, ay = py(s.x) - y0, bx = px(s.y) - x0, by = py(s.y) - y0;
+    const int ux = bx - ax, uy = by - ay;
+    const float fax = i2f_exact(ax), fay = i2f_exact(ay), fbx = i2f_exact(bx), fby = i2f_exact(by);
+    const float fux = i2f_exact(ux), fuy = i2f_exact(uy);
+    a = make_float4(fax, fay, fbx, fby);
+    const int m = max(max(abs(ax), abs(ay)), max(abs(bx), abs(by)));
+    const bool exact = abs(ux) <= 1024 && abs(uy) <= 1024 && m <= 4096;
+    const bool whole = min(min(ax, ay), min(bx, by)) >= 0 && max(max(ax, ay), max(bx, by)) <= w;
+    b = make_float4(fux, fuy, -ll2f_rn((long long)ux * ay - (long long)uy * ax),
+                    exact ? (whole ? 0.f : kClipExact) : kClipFiltered);
+    const bool on_border = (uy == 0 && (ay == 0 || ay == w)) || (ux == 0 && (ax == 0 || ax == w));
+    if (on_border) {
+        const float nan = __int_as_float(0x7fc00000);
+        c = make_float4(nan, nan, nan, nan);
+        return;
+    }
+    if (whole) {
+        c = make_float4(fax, fay, fbx, fby);
+        return;
+    }
+    float t0 = 0.f, t1 = 1.f;
+    if (ux != 0) {
+        const float ta = __fdividef(i2f_exact(-ax), fux), tb = __fdividef(i2f_exact(w - ax), fux);
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+    }
+    if (uy != 0) {
+        const float ta = __fdividef(i2f_exact(-ay), fuy), tb = __fdividef(i2f_exact(w - ay), fuy);
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+    }
+    if (t1 < t0) t1 = t0;
+    c = make_float4(fmaf(t0, fux, fax), fmaf(t0, fuy, fay), fmaf(t1, fux, fax), fmaf(t1, fuy, fay));
+}
+
+// The clip test of a pair: the row's clipped part against the column's line
+// (s0, s1) and the column's clipped part against the row's line (s2, s3).
+// The error of s0, s1 is the column line's FP32 error at the row's clip
+// points plus |u_col| times their error: at most 1792 + 2 * 2^16 * 2^-6 =
+// 3840 for a filtered line (margin 8192), 12 + 32 for an exact one (margin
+// 64) and none for an exact line at a whole exact segment's endpoints
+// (margin 0); the margin of s0, s1 is max(v_col as a line, v_row as points),
+// where a record's "points" margin is min(v, 64).  Both clipped parts lie in
+// the closed cell, so the pair can count here only if each clipped part
+// meets the other's line: a pair is surely outside (clip_out) when either
+// part lies strictly beyond the margin on one side.  clip_in: the row's part
+// strictly straddles the column's line, so an intersection point on the row's
+// segment lies strictly inside it, hence in the open cell (the open part of
+// a segment that does not run along the border lies in the cell's interior).
+struct ClipTest {
+    bool out, in;
+};
+
+__device__ __forceinline__ ClipTest clip_test(const float4 &rb, const float4 &rc, float r_pts, const float4 &cb,
+                                              const float4 &cc) {
+    const float s0 = fmaf(cb.x, rc.y, fmaf(-cb.y, rc.x, cb.z));
+    const float s1 = fmaf(cb.x, rc.w, fmaf(-cb.y, rc.z, cb.z));
+    const float s2 = fmaf(rb.x, cc.y, fmaf(-rb.y, cc.x, rb.z));
+    const float s3 = fmaf(rb.x, cc.w, fmaf(-rb.y, cc.z, rb.z));
+    const float M01 = fmaxf(cb.w, r_pts), M23 = fmaxf(rb.w, fminf(cb.w, kClipExact));
+    const float lo01 = fminf(s0, s1), hi01 = fmaxf(s0, s1), lo23 = fminf(s2, s3), hi23 = fmaxf(s2, s3);
+    ClipTest t;
+    t.out = (lo01 > M01) | (hi01 < -M01) | (lo23 > M23) | (hi23 < -M23);
+    t.in = (lo01 < -M01) & (hi01 > M01);
+    return t;
+}
+
+// The four orientations of a pair: o1, o2 of c's endpoints against r's line,
+// o3, o4 of r's endpoints against c's line.
+struct Orient4 {
+    float o1, o2, o3, o4;
+};
+
+__device__ __forceinline__ Orient4 orient4(const float4 &ra, const float4 &rb, const float4 &ca, const float4 &cb) {
+    Orient4 o;
+    o.o1 = fmaf(rb.x, ca.y, fmaf(-rb.y, ca.x, rb.z));
+    o.o2 = fmaf(rb.x, ca.w, fmaf(-rb.y, ca.z, rb.z));
+    o.o3 = fmaf(cb.x, ra.y, fmaf(-cb.y, ra.x, cb.z));
+    o.o4 = fmaf(cb.x, ra.w, fmaf(-cb.y, ra.z, cb.z));
+    return o;
+}
+
+// Whether the pair is surely disjoint: one segment's endpoints lie strictly
+// on one side of the other's line, beyond the filter F.
+__device__ __forceinline__ bool surely_apart(const Orient4 &o, float F) {
+    const float lo12 = fminf(o.o1, o.o2), hi12 = fmaxf(o.o1, o.o2);
+    const float lo34 = fminf(o.o3, o.o4), hi34 = fmaxf(o.o3, o.o4);
+    return (lo12 > F) | (hi12 < -F) | (lo34 > F) | (hi34 < -F);
+}
+
+// Lexicographic (x, then y) order of two integer points in signed
+// coordinates: a <= b.
+__device__ __forceinline__ bool lex_le(int ax, int ay, int bx, int by) { return ax < bx || (ax == bx && ay <= by); }
+
+// Exact int64 classification (classify_kind's rules) of a pair given in the
+// integer coordinates of one cell (|values| < 2^17, products below 2^35).
+__device__ __forceinline__ int classify_rel(const float4 &ra, const float4 &ca, uint32_t ida, uint32_t idb,
+                                            uint32_t idc, uint32_t idd) {
+    if ((ida == idc) | (ida == idd) | (idb == idc) | (idb == idd)) return PAIR_NONE;
+    const int ax = (int)ra.x, ay = (int)ra.y, bx = (int)ra.z, by = (int)ra.w;
+    const int cx = (int)ca.x, cy = (int)ca.y, dx = (int)ca.z, dy = (int)ca.w;
+    const long long ux = bx - ax, uy = by - ay, vx = dx - cx, vy = dy - cy;
+    const long long o1 = ux * (cy - ay) - uy * (cx - ax);
+    const long long o2 = ux * (dy - ay) - uy * (dx - ax);
+    if ((o1 > 0 && o2 > 0) || (o1 < 0 && o2 < 0)) return PAIR_NONE;
+    const long long o3 = vx * (ay - cy) - vy * (ax - cx);
+    const long long o4 = vx * (by - cy) - vy * (bx - cx);
+    if ((o3 > 0 && o4 > 0) || (o3 < 0 && o4 < 0)) return PAIR_NONE;
+    if (o1 == 0 && o2 == 0) {
+        // collinear: the extents along the line meet (lexicographic order is
+        // a linear order of the points of one line)
+        int lx = ax, ly = ay, hx = bx, hy = by;
+        if (!lex_le(lx, ly, hx, hy)) { lx = bx; ly = by; hx = ax; hy = ay; }
+        int mx = cx, my = cy, nx = dx, ny = dy;
+        if (!lex_le(mx, my, nx, ny)) { mx = dx; my = dy; nx = cx; ny = cy; }
+        if (lex_le(lx, ly, mx, my)) { lx = mx; ly = my; }  // larger low end
+        if (lex_le(nx, ny, hx, hy)) { hx = nx; hy = ny; }  // smaller high end
+        return lex_le(lx, ly, hx, hy) ? PAIR_COLLINEAR : PAIR_NONE;
+    }
+    return (o1 != 0 && o2 != 0 && o3 != 0 && o4 != 0) ? PAIR_PROPER : PAIR_TOUCHING;
+}
+
+// Owner of a collinear overlap in its cell's coordinates: the cell holding
+// the lexicographically smallest point of the overlap (the larger of the two
+// segments' smaller endpoints).
+__device__ __forceinline__ bool owns_collinear_rel(const float4 &ra, const float4 &ca, int w) {
+    int ex = (int)ra.x, ey = (int)ra.y;
+    if (!lex_le(ex, ey, (int)ra.z, (int)ra.w)) { ex = (int)ra.z; ey = (int)ra.w; }
+    int fx = (int)ca.x, fy = (int)ca.y;
+    if (!lex_le(fx, fy, (int)ca.z, (int)ca.w)) { fx = (int)ca.z; fy = (int)ca.w; }
+    if (lex_le(ex, ey, fx, fy)) { ex = fx; ey = fy; }
+    return 0 <= ex && ex < w && 0 <= ey && ey < w;
+}
+
+}  // namespace gr

@@ -965,10 +965,12 @@ __device__ __forceinline__ void atomic_add2(float *g, int64_t v, float x, float 
 // E_c pairs (FP64, two atomics per pair); then each segment turns it into its
 // endpoints' gradients: d theta / d q = (-dy, dx) / |q - p|^2 for the vector
 // q - p.
-__global__ void __launch_bounds__(256) k_grad_theta(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ theta,
+__global__ void __launch_bounds__(256) k_grad_theta(const uint2 *const *__restrict__ pairs_slot,
+                                                    const uint32_t *__restrict__ theta,
                                                     const DiffState *__restrict__ st, const float *__restrict__ gout,
                                                     uint32_t ideal_u, double *__restrict__ adj) {
     const DiffState d = *st;
+    const uint2 *__restrict__ pairs = *pairs_slot;
     const uint64_t n = min((uint64_t)d.pairs, (uint64_t)d.ec);
     if (d.ec == 0) return;
     const double scale = -(double)gout[0] / (d.ideal * (double)d.ec);
@@ -1146,13 +1148,14 @@ void launch_diff_state(const Buffers &b, int64_t V, int64_t E, double ideal, Dif
                                    st, out3);
 }
 
-void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *pairs, const int2 *arg,
-                          const DiffState *st, const float *gout, uint32_t ideal_u, uint64_t n_pairs, double *adj,
-                          float *grad, cudaStream_t s) {
+void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *const *pairs_slot, const int2 *arg,
+                          const DiffState *st, const float *gout, uint32_t ideal_u, double *adj, float *grad,
+                          cudaStream_t s) {
     cudaMemsetAsync(grad, 0, sizeof(float) * 2 * V, s);
     cudaMemsetAsync(adj, 0, sizeof(double) * (E > 0 ? E : 1), s);
     count_launches(4);
-    k_grad_theta<<<grid_for((int64_t)n_pairs, 256, 152 * 16), 256, 0, s>>>(pairs, b.seg_theta, st, gout, ideal_u, adj);
+    // the pair count is known on the device only: a grid-stride launch of fixed size
+    k_grad_theta<<<152 * 8, 256, 0, s>>>(pairs_slot, b.seg_theta, st, gout, ideal_u, adj);
     k_grad_theta_scatter<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const float4 *)b.seg, b.seg_ids, b.acc, adj, grad);
     k_grad_elv<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.edges, (const float2 *)b.xy, E, st, gout,
                                                          grad);

@@ -116,10 +116,10 @@ __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ s
 }
 
 // Work items of the pair kernel per cell (cell_item_count: short x short tile
-// pairs and long x short tiles).  Also sums the candidate pairs,
+// pairs and long x short tiles; rot: rot_item_count).  Also sums the candidate pairs,
 // ns (ns - 1) / 2 + ns (n - ns), of all cells.
 __global__ void __launch_bounds__(256) k_cell_items(const uint32_t *__restrict__ cell_off,
-                                                    const uint32_t *__restrict__ cell_nl, int C,
+                                                    const uint32_t *__restrict__ cell_nl, int C, int rot,
                                                     uint32_t *__restrict__ item_cnt, DevAcc *acc) {
     __shared__ uint64_t sh[32];
     uint64_t w = 0;
@@ -127,13 +127,16 @@ __global__ void __launch_bounds__(256) k_cell_items(const uint32_t *__restrict__
         const uint64_t n = cell_off[c + 1] - cell_off[c];
         const uint64_t ns = n - cell_nl[c];
         bool tiles_over;
-        const uint64_t items = cell_item_count(n, ns, &tiles_over);
+        const uint64_t items = rot ? rot_item_count(n, &tiles_over) : cell_item_count(n, ns, &tiles_over);
         if (items > 0x7fffffffull || tiles_over) atomicOr(&acc->grid_flags, GF_ITEMS_OVERFLOW);
         item_cnt[c] = (uint32_t)min(items, (uint64_t)0x7fffffffull);
         w += ns * (ns - (ns > 0)) / 2 + ns * (n - ns);
     }
     w = block_sum<uint64_t>(w, sh);
     if (threadIdx.x == 0) atomic_add_u64(&acc->grid_work, w);
+    // the rotation kernel's queue words keep a flag in the top bit of a record index
+    if (rot && blockIdx.x == 0 && threadIdx.x == 0 && acc->records >= 0x80000000ull)
+        atomicOr(&acc->grid_flags, GF_ITEMS_OVERFLOW);
 }
 
 // a3 + work items in one launch, for grids of at most kOffsetsMaxCells
@@ -180,7 +183,7 @@ __device__ __forceinline__ void block_excl_scan2(uint64_t a, uint64_t b, uint64_
 }
 
 __global__ void __cluster_dims__(kOffsetsCluster, 1, 1) __launch_bounds__(kOffsetsThreads)
-    k_grid_offsets(uint32_t *__restrict__ cell_off, const uint32_t *__restrict__ cell_nl, int C,
+    k_grid_offsets(uint32_t *__restrict__ cell_off, const uint32_t *__restrict__ cell_nl, int C, int rot,
                    uint32_t *__restrict__ item_off, DevAcc *acc) {
     __shared__ uint64_t sh[3][32];
     __shared__ uint64_t cta_tot[2];
@@ -215,7 +218,7 @@ __global__ void __cluster_dims__(kOffsetsCluster, 1, 1) __launch_bounds__(kOffse
         for (int j = 0; j < 4; ++j) {
             const uint64_t nn = vn[j], ns = nn - vl[j];
             bool tiles_over;
-            const uint64_t items = cell_item_count(nn, ns, &tiles_over);
+            const uint64_t items = rot ? rot_item_count(nn, &tiles_over) : cell_item_count(nn, ns, &tiles_over);
             over |= items > 0x7fffffffull || tiles_over;
             n[4 * q + j] = vn[j];
             it[4 * q + j] = (uint32_t)min(items, (uint64_t)0x7fffffffull);
@@ -280,6 +283,8 @@ __global__ void __cluster_dims__(kOffsetsCluster, 1, 1) __launch_bounds__(kOffse
             acc->records = ar;
             acc->grid_items = ai;
             if (ar > 0xffffffffull || ai > 0xffffffffull) atomicOr(&acc->eval_status, ST_SCAN_OVERFLOW);
+            // the rotation kernel's queue words keep a flag in the top bit of a record index
+            if (rot && ar >= 0x80000000ull) atomicOr(&acc->grid_flags, GF_ITEMS_OVERFLOW);
         }
     }
     cluster.sync();  // no CTA leaves while another may still read its totals
@@ -291,8 +296,8 @@ __global__ void __cluster_dims__(kOffsetsCluster, 1, 1) __launch_bounds__(kOffse
 // dependent loads.
 __global__ void __launch_bounds__(256) k_item_descs(const uint32_t *__restrict__ item_off,
                                                     const uint32_t *__restrict__ cell_off,
-                                                    const uint32_t *__restrict__ cell_nl, int C, uint64_t cap,
-                                                    uint4 *__restrict__ desc, uint32_t *status) {
+                                                    const uint32_t *__restrict__ cell_nl, int C, int rot,
+                                                    uint64_t cap, uint4 *__restrict__ desc, uint32_t *status) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
         const uint32_t q = item_off[c];
         const uint32_t e = item_off[c + 1];
@@ -302,10 +307,12 @@ __global__ void __launch_bounds__(256) k_item_descs(const uint32_t *__restrict__
             continue;
         }
         const uint32_t base = cell_off[c], n = cell_off[c + 1] - base, ns = n - cell_nl[c];
-        cell_item_words(n, ns, q, e, [&](uint32_t i, uint32_t word) {
+        auto emit = [&](uint32_t i, uint32_t word) {
             desc[2 * (uint64_t)i] = make_uint4(base, n, ns, word);
             desc[2 * (uint64_t)i + 1] = make_uint4((uint32_t)c, 0u, 0u, 0u);
-        });
+        };
+        if (rot) rot_item_words(n, q, e, emit);
+        else cell_item_words(n, ns, q, e, emit);
     }
 }
 
@@ -349,9 +356,12 @@ __global__ void __launch_bounds__(256) k_grid_fill(const SegRec *__restrict__ se
                                }
                                GridRec g;
                                g.s = q;
-                               g.x = make_uint4((uint32_t)qe, qt, 0u, 0u);
+                               g.x = make_uint4((uint32_t)qe, qt, (uint32_t)ids[0], 0u);
                                rec[p0] = g;
-                               if (nc > 1) rec[p1] = g;
+                               if (nc > 1) {
+                                   g.x.z = (uint32_t)ids[1];
+                                   rec[p1] = g;
+                               }
                            });
     }
 }
@@ -391,6 +401,170 @@ __global__ void __launch_bounds__(GP_WARPS * 32, 4) k_grid_pairs(const GridRec *
     flush_counts(pc, acc, shu);
 }
 
+// The FP32 cell-relative form of every record (make_rgeo) for the rotation
+// kernel, in record order: coalesced reads of the records (their cell id in
+// .x.z) and coalesced writes of the three geometry arrays.
+__global__ void __launch_bounds__(256) k_rec_geo(const GridRec *__restrict__ rec, const DevAcc *__restrict__ acc,
+                                                 uint64_t cap, int k, float4 *__restrict__ geo) {
+    const uint64_t R = acc->records;
+    if (R > cap) return;  // overflow raised by the scatter
+    const int lg = 16 - k, msk = (1 << lg) - 1;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < R; p += (uint64_t)gridDim.x * blockDim.x) {
+        const SegRec q = rec[p].s;
+        const int id = (int)rec[p].x.z;
+        float4 a, b, c;
+        make_rgeo(q, (id & msk) << k, (id >> lg) << k, 1 << k, a, b, c);
+        geo[p] = a;
+        geo[cap + p] = b;
+        geo[2 * cap + p] = c;
+    }
+}
+
+// a6, rotation form -- one warp per rotation work item (rot_item_count):
+// each lane keeps one row record of the cell in registers; the item's column
+// window (RWIN records) is staged in shared memory, so lane l meets slot
+// l + t at the item's t-th offset.  Records are read as FP32 cell-relative
+// geometry (geo_a = {ax, ay, bx, by}, geo_b = {ux, uy, nk, v}, geo_c = the
+// clipped part; three arrays of rec_cap float4, see make_rgeo).  A pair is
+// queued unless the clip test shows it cannot count in this cell; the queued
+// pairs are settled 32 at a time by the whole warp (settle_pair) after each
+// item, so the rare cases never run with idle lanes.
+constexpr int CP_WARPS = 8;                    // warps per block
+constexpr int CP_QUEUE = 32 * RQ + 32;         // queued pairs per warp: up to 31 left + 32 per offset
+
+// Settles one queued pair (row | clip-in flag << 31, col) of a cell of side w:
+// shared vertex ids skip it; the FP32 orientations decide it when they are
+// exact or clear of the filter, else the exact int64 test does; a pair in E_c
+// counts if its intersection point lies in this cell (decided by the clip
+// test, else by the exact test), a collinear overlap if this cell holds the
+// smallest point of the overlap.
+template <bool PER_EDGE>
+__device__ __forceinline__ void settle_pair(const float4 *__restrict__ geo, uint64_t cap,
+                                            const GridRec *__restrict__ rec, uint2 e, int w, uint32_t ideal,
+                                            PairCounts &pc, PerEdge pe) {
+    const uint32_t row = e.x & 0x7fffffffu, col = e.y;
+    const bool clip_in = (e.x >> 31) != 0;
+    const uint2 rid = *(const uint2 *)&rec[row].s.z, cid = *(const uint2 *)&rec[col].s.z;
+    if ((rid.x == cid.x) | (rid.x == cid.y) | (rid.y == cid.x) | (rid.y == cid.y)) return;
+    const float4 ra = geo[row], rb = geo[cap + row], ca = geo[col], cb = geo[cap + col];
+    const Orient4 o = orient4(ra, rb, ca, cb);
+    const float F = fmaxf(rb.w, cb.w) > kClipExact ? kRotFilter : 0.f;  // a filtered record takes part
+    const float mn = fminf(fminf(fabsf(o.o1), fabsf(o.o2)), fminf(fabsf(o.o3), fabsf(o.o4)));
+    int kind;
+    if ((F == 0.f || mn > F) && !(o.o1 == 0.f && o.o2 == 0.f)) {
+        const float p12 = o.o1 * o.o2, p34 = o.o3 * o.o4;
+        kind = (p12 <= 0.f && p34 <= 0.f) ? ((p12 < 0.f && p34 < 0.f) ? PAIR_PROPER : PAIR_TOUCHING) : PAIR_NONE;
+    } else {
+        kind = classify_rel(ra, ca, rid.x, rid.y, cid.x, cid.y);
+    }
+    if (kind == PAIR_NONE) return;
+    if (kind == PAIR_COLLINEAR) {
+        if (!owns_collinear_rel(ra, ca, w)) return;
+        ++pc.collinear;
+        if (PER_EDGE) {
+            atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)rec[row].x.x + 2], 1ull);
+            atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)rec[col].x.x + 2], 1ull);
+        }
+        return;
+    }
+    if (!clip_in) {
+        const int iax = (int)ra.x, iay = (int)ra.y, icx = (int)ca.x, icy = (int)ca.y;
+        if (!owns_crossing(iax, iay, (int)ra.z - iax, (int)ra.w - iay, icx, icy, (int)ca.z - icx, (int)ca.w - icy,
+                           w))
+            return;
+    }
+    const uint2 rx = *(const uint2 *)&rec[row].x, cx = *(const uint2 *)&rec[col].x;  // edge id, direction
+    const uint32_t qd = dev_term(rx.y, cx.y, ideal);
+    const bool prop = kind == PAIR_PROPER;
+    pc.dev += qd;
+    if (prop) ++pc.proper; else ++pc.touching;
+    if (PER_EDGE) {
+        const int slot = prop ? 0 : 1;
+        atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)rx.x + slot], 1ull);
+        atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)cx.x + slot], 1ull);
+        atomicAdd((unsigned long long *)&pe.dev[(int32_t)rx.x], (unsigned long long)qd);
+        atomicAdd((unsigned long long *)&pe.dev[(int32_t)cx.x], (unsigned long long)qd);
+    }
+}
+
+// Settles the queue's whole batches of 32 and moves the rest to its front.
+template <bool PER_EDGE>
+__device__ __forceinline__ void settle_queue(const float4 *__restrict__ geo, uint64_t cap,
+                                             const GridRec *__restrict__ rec, uint2 *q, int &qn, int lane, int w,
+                                             uint32_t ideal, PairCounts &pc, PerEdge pe) {
+    if (qn < 32) return;
+    __syncwarp();
+    int h = 0;
+    for (; h + 32 <= qn; h += 32) settle_pair<PER_EDGE>(geo, cap, rec, q[h + lane], w, ideal, pc, pe);
+    const uint2 rest = lane < qn - h ? q[h + lane] : make_uint2(0u, 0u);
+    __syncwarp();
+    if (lane < qn - h) q[lane] = rest;
+    qn -= h;
+    __syncwarp();
+}
+
+template <bool PER_EDGE>
+__global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *__restrict__ geo,
+                                                                 const GridRec *__restrict__ rec,
+                                                                 const uint4 *__restrict__ descs,
+                                                                 const uint32_t *__restrict__ n_items_p,
+                                                                 uint64_t rec_cap, uint64_t items_cap, int k,
+                                                                 DevAcc *acc, uint32_t ideal, PerEdge pe) {
+    __shared__ float4 win_b[CP_WARPS][RWIN], win_c[CP_WARPS][RWIN];
+    __shared__ uint2 qbuf[CP_WARPS][CP_QUEUE];
+    __shared__ uint64_t shu[32];
+    const uint32_t n_items = *n_items_p;
+    if (acc->records > rec_cap || n_items > items_cap) return;  // overflow raised by the scatter or descriptors
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int w = 1 << k;
+    const unsigned lt = lanemask_lt();
+    const float4 *__restrict__ geo_b = geo + rec_cap;
+    const float4 *__restrict__ geo_c = geo + 2 * rec_cap;
+    float4 *wb = win_b[wid], *wc = win_c[wid];
+    uint2 *q = qbuf[wid];
+    int qn = 0;
+    PairCounts pc;
+    const uint32_t stride = gridDim.x * CP_WARPS;
+    uint32_t it = blockIdx.x * CP_WARPS + wid;
+    uint4 next = it < n_items ? descs[2 * (uint64_t)it] : make_uint4(0, 0, 0, 0);
+    for (; it < n_items; it += stride) {
+        const uint4 d = next;
+        if (it + stride < n_items) next = descs[2 * (uint64_t)(it + stride)];  // prefetch the next item
+        const uint32_t base = d.x, n = d.y;
+        const RotLane rl = rot_lane((int)n, d.w, lane);
+        // the item's column window: records 32 c + q0 + t (mod n) of the cell
+        const uint32_t first = 32u * ((d.w >> 16) & 0x7fffu) + (uint32_t)rl.q0;
+        __syncwarp();
+        for (int t = lane; t < RWIN; t += 32) {
+            const uint32_t r = base + (first + (uint32_t)t) % n;
+            wb[t] = geo_b[r];
+            wc[t] = geo_c[r];
+        }
+        const uint32_t row = base + (uint32_t)rl.i;
+        const float4 rb = geo_b[row], rc = geo_c[row];
+        const float r_pts = fminf(rb.w, kClipExact);
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < RQ; ++t) {
+            const ClipTest ct = clip_test(rb, rc, r_pts, wb[lane + t], wc[lane + t]);
+            const bool keep = t < rl.cnt && !ct.out;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (m) {
+                if (keep) {
+                    uint32_t j = (uint32_t)(rl.i + rl.q0 + t);
+                    if (j >= n) j -= n;
+                    q[qn + __popc(m & lt)] = make_uint2(row | (ct.in ? 0x80000000u : 0u), base + j);
+                }
+                qn += __popc(m);
+            }
+        }
+        settle_queue<PER_EDGE>(geo, rec_cap, rec, q, qn, lane, w, ideal, pc, pe);
+    }
+    __syncwarp();
+    if (lane < qn) settle_pair<PER_EDGE>(geo, rec_cap, rec, q[lane], w, ideal, pc, pe);
+    flush_counts(pc, acc, shu);
+}
+
 int grid_for(int64_t n, int threads, int max_blocks) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -409,14 +583,15 @@ void launch_grid_count(const Buffers &b, int64_t E, const GridBuffers &g, int k,
         k_grid_count<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, b.acc, k, split ? 1 : 0,
                                                                  g.cell_off, g.cell_nl, g.seg_long, g.theta_long,
                                                                  g.eid_long);
+    const int rot = split ? 0 : 1;  // without the split every pair of a cell is a rotation pair
     if (C <= kOffsetsMaxCells) {
         count_launches(1);
-        k_grid_offsets<<<kOffsetsCluster, kOffsetsThreads, 0, s>>>(g.cell_off, g.cell_nl, C, g.item_off, b.acc);
+        k_grid_offsets<<<kOffsetsCluster, kOffsetsThreads, 0, s>>>(g.cell_off, g.cell_nl, C, rot, g.item_off, b.acc);
         return;
     }
     launch_scan_u32(g.cell_off, g.cell_off, C, b.scan_tmp, &b.acc->records, &b.acc->eval_status, s);
     count_launches(1);
-    k_cell_items<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.cell_off, g.cell_nl, C, g.item_off, b.acc);
+    k_cell_items<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.cell_off, g.cell_nl, C, rot, g.item_off, b.acc);
     launch_scan_u32(g.item_off, g.item_off, C, b.scan_tmp, &b.acc->grid_items, &b.acc->eval_status, s);
 }
 
@@ -424,17 +599,32 @@ void launch_grid_scatter(const Buffers &b, int64_t E, const GridBuffers &g, int 
     const int C = (65536 >> k) * (65536 >> k);
     cudaMemsetAsync(g.cell_fill, 0, sizeof(unsigned long long) * C, s);
     count_launches(1 + (E > 0 ? 1 : 0));
-    k_item_descs<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.item_off, g.cell_off, g.cell_nl, C, g.items_cap,
-                                                           g.item_desc, &b.acc->eval_status);
+    k_item_descs<<<grid_for(C, 256, 152 * 8), 256, 0, s>>>(g.item_off, g.cell_off, g.cell_nl, C, split ? 0 : 1,
+                                                           g.items_cap, g.item_desc, &b.acc->eval_status);
     if (E <= 0) return;
     k_grid_fill<<<grid_for(E, 256, 152 * 16), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, b.acc, k, split ? 1 : 0,
                                                            g.cell_off, g.cell_fill, g.rec_cap, g.rec,
                                                            &b.acc->eval_status);
+    if (!split) {
+        count_launches(1);
+        k_rec_geo<<<152 * 8, 256, 0, s>>>(g.rec, b.acc, g.rec_cap, k, g.rgeo);
+    }
 }
 
-void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, uint64_t n_items_hint, uint32_t ideal,
-                       PerEdge pe, cudaStream_t s) {
+void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, bool split, uint64_t n_items_hint,
+                       uint32_t ideal, PerEdge pe, cudaStream_t s) {
     const int C = (65536 >> k) * (65536 >> k);
+    if (!split) {  // rotation items over every pair of each cell
+        const int blocks = n_items_hint ? grid_for((int64_t)n_items_hint, CP_WARPS, 152 * 4) : 152 * 4;
+        count_launches(1);
+        if (pe.counts)
+            k_cell_pairs<true><<<blocks, CP_WARPS * 32, 0, s>>>(g.rgeo, g.rec, g.item_desc, g.item_off + C,
+                                                               g.rec_cap, g.items_cap, k, b.acc, ideal, pe);
+        else
+            k_cell_pairs<false><<<blocks, CP_WARPS * 32, 0, s>>>(g.rgeo, g.rec, g.item_desc, g.item_off + C,
+                                                                g.rec_cap, g.items_cap, k, b.acc, ideal, pe);
+        return;
+    }
     const int blocks = n_items_hint ? grid_for((int64_t)n_items_hint, GP_WARPS, 152 * 8) : 152 * 8;
     count_launches(1);
     if (pe.counts)

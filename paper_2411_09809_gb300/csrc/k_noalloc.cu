@@ -11,10 +11,13 @@
 // Scratch: the file-scope array g_noalloc_scratch below (kNoAllocMaxEdges
 // compacted segments with their edge ids, line directions and squared
 // lengths, plus one accumulator block and one result slot, about 1 MiB).
-// Host code cannot use the array's name as a device address; the first call
-// on each device looks the address up with cudaGetSymbolAddress while that
-// device is current and caches it.  That first call on a device should
-// therefore come before any stream capture on it.
+// Host code cannot use the array's name as a device address: every call looks
+// the address up with cudaGetSymbolAddress while its device is current (a host
+// call that allocates nothing), so a device reset between calls, which reloads
+// the library's module at a possibly different address, cannot leave a stale
+// address behind.  The first call on a device is the set-up: it also makes the
+// runtime load the module there, so that first call should come before any
+// stream capture on the device.
 //
 // Every call reuses the same array and leaves its contents behind; the
 // accumulators are cleared at the start of each call.  Calls whose work
@@ -25,7 +28,6 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "gr_internal.cuh"
@@ -33,7 +35,6 @@
 namespace {
 
 constexpr int64_t kNoAllocMaxEdges = GR_NOALLOC_MAX_EDGES;
-constexpr int kMaxDevices = 64;
 
 struct NoAllocScratch {
     gr::DevAcc acc;
@@ -45,9 +46,6 @@ struct NoAllocScratch {
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
-
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
 
 gr_status noalloc_fail(gr_status st, const std::string &msg) {
     gr::set_last_error(msg.c_str());
@@ -84,24 +82,15 @@ bool is_device_memory(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device.
+// Device address of the scratch array on the current device.
 gr_status scratch_address(NoAllocScratch **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(GR_ENOTSUP, "device index above 63");
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return noalloc_fail(GR_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        }
-        g_scratch_addr[dev] = p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return noalloc_fail(GR_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     }
-    *out = (NoAllocScratch *)g_scratch_addr[dev];
+    *out = (NoAllocScratch *)p;
     return GR_OK;
 }
 

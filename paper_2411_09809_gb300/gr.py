@@ -127,8 +127,8 @@ def load() -> ctypes.CDLL:
         "gr_strip_crossings": ([P, c_int32, c_int32, c_double, ctypes.POINTER(gr_strip_result)], c_int32),
         "gr_evaluate_async": ([P, c_uint32, ctypes.POINTER(gr_params), P, P], c_int32),
         "gr_batch_evaluate_async": ([P, c_uint32, ctypes.POINTER(gr_params), P, P], c_int32),
-        "gr_diff_forward": ([P, c_double, P], c_int32),
-        "gr_diff_backward": ([P, P, P], c_int32),
+        "gr_diff_forward": ([P, c_double, P, P], c_int32),
+        "gr_diff_backward": ([P, P, P, P], c_int32),
         "gr_last_error": ([], ctypes.c_char_p),
         "gr_version": ([], ctypes.c_char_p),
     }
@@ -219,27 +219,29 @@ def gr_move_vertices(layout, ids, xy_new, metrics: int = GR_METRIC_ALL, ideal_ra
     return r
 
 
-def gr_diff_forward(layout, ideal_rad: float = 0.0, out3=None):
+def gr_diff_forward(layout, ideal_rad: float = 0.0, out3=None, stream: int = 0):
     """{E_ca, M_l, M_a} of an FP32 layout into `out3` (a float32 [3] tensor or array;
-    a new numpy array when None), keeping what gr_diff_backward needs."""
+    a new numpy array when None), keeping what gr_diff_backward needs; ordered
+    after the work on `stream` (a cudaStream_t as int; 0: the layout's own)."""
     import numpy as np
     if out3 is None:
         out3 = np.zeros(3, np.float32)
     op, ok = _buffer(out3, "float32")
-    _check(load().gr_diff_forward(layout, float(ideal_rad), op))
+    _check(load().gr_diff_forward(layout, float(ideal_rad), op, ctypes.c_void_p(int(stream) or None)))
     if ok is not out3:  # a converted copy: hand back the values
         return ok
     return out3
 
 
-def gr_diff_backward(layout, gout3, d_grad_xy) -> None:
+def gr_diff_backward(layout, gout3, d_grad_xy, stream: int = 0) -> None:
     """Gradient of gout3 . (E_ca, M_l, M_a) w.r.t. the coordinates into d_grad_xy
-    (float32 [V, 2] device tensor, overwritten)."""
+    (float32 [V, 2] device tensor, overwritten), ordered on `stream` (a
+    cudaStream_t as int; 0: the layout's own)."""
     gp, gk = _buffer(gout3, "float32")
     dp, dk = _buffer(d_grad_xy, "float32")
     if dk is not d_grad_xy:
         raise TypeError("d_grad_xy must be a contiguous float32 device tensor")
-    _check(load().gr_diff_backward(layout, gp, dp))
+    _check(load().gr_diff_backward(layout, gp, dp, ctypes.c_void_p(int(stream) or None)))
 
 
 def gr_layout_destroy(layout) -> None:

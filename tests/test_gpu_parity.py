@@ -174,6 +174,23 @@ def test_large_sparse_layout_full_size_sampled():
     _sampled_parity(L, 64, 4, 64)
 
 
+def test_dense_long_edge_layout_full_size_totals():
+    # every one of the 2.0e10 edge pairs on the oracle (tens of seconds of host work)
+    L = synth.dense_long_edge_layout()
+    res = evaluate_all(L.xy, L.edges, 256)
+    check_crossings(res, oracle.crossings(L.xy, L.edges), "dense long-edge, all pairs")
+    assert res.occlusion_pairs == oracle.node_occlusion(L.xy, 256)
+
+
+def test_large_sparse_layout_full_size_totals():
+    # occlusion over all 2.0e10 vertex pairs and crossings over all 1.25e11 edge
+    # pairs on the oracle (about two minutes of host work on the GPU machine)
+    L = synth.large_sparse_layout()
+    res = evaluate_all(L.xy, L.edges, 64)
+    assert res.occlusion_pairs == oracle.node_occlusion(L.xy, 64)
+    check_crossings(res, oracle.crossings(L.xy, L.edges), "large sparse, all pairs")
+
+
 def _expect_error(status, fn):
     with pytest.raises(gr.GrError) as ei:
         fn()

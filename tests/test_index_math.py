@@ -135,3 +135,203 @@ def test_min_angle_sector_gap_matches_atan2():
         d = abs(sector_gap(a, b, tab, w) - ref)
         worst = max(worst, min(d, 2 * math.pi - d))
     assert worst < 2e-15
+
+
+def rotation_constant():
+    m = re.search(r"constexpr int RQ = (\d+);", source("grid_common.cuh"))
+    return int(m.group(1))
+
+
+def rot_items(n, RQ):
+    # grid_common.cuh rot_item_count / rot_item_words
+    if n < 2:
+        return []
+    Q, F = n >> 1, (n + 31) >> 5
+    P = (Q + RQ - 1) // RQ
+    return [(c << 16) | p for c in range(F) for p in range(P)]
+
+
+def rot_lane(n, w, lane, RQ):
+    # grid_common.cuh rot_lane: (row, first offset, offsets taken)
+    Q, c, p = n >> 1, (w >> 16) & 0x7FFF, w & 0xFFFF
+    i, q0 = 32 * c + lane, 1 + p * RQ
+    Qi = Q - 1 if (n % 2 == 0 and i >= n // 2) else Q
+    cnt = max(0, min(Qi, q0 + RQ - 1) - q0 + 1) if i < n else 0
+    return (i if i < n else 0), q0, cnt
+
+
+@pytest.mark.parametrize("n", list(range(0, 70)) + [95, 96, 97, 127, 128, 129, 255, 256, 299, 300, 513, 1000])
+def test_rotation_items_cover_every_pair_of_a_cell_once(n):
+    # every unordered pair {i, j} of the cell's n records is met exactly once by
+    # the lanes of its rotation work items, each lane within the cell's rows and
+    # its columns within the item's window of 32 + RQ - 1 slots
+    RQ = rotation_constant()
+    seen = {}
+    for w in rot_items(n, RQ):
+        c = (w >> 16) & 0x7FFF
+        for lane in range(32):
+            i, q0, cnt = rot_lane(n, w, lane, RQ)
+            assert cnt <= RQ
+            for t in range(cnt):
+                q = q0 + t
+                slot = lane + t
+                assert slot < 32 + RQ - 1
+                j = (i + q) % n
+                assert j == (32 * c + q0 + slot) % n  # the window slot holds the column
+                key = (min(i, j), max(i, j))
+                seen[key] = seen.get(key, 0) + 1
+    assert len(seen) == n * (n - 1) // 2
+    assert all(v == 1 for v in seen.values())
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def fmaf(a, b, c):
+    # one rounding of the exact a * b + c to FP32
+    from fractions import Fraction
+    return f32(Fraction(a) * Fraction(b) + Fraction(c)) if not any(map(math.isnan, (a, b, c))) else math.nan
+
+
+def div_fast(a, b, rng=None):
+    # the device's fast division: within 2 ulp of the quotient (modelled as the
+    # correctly rounded quotient moved by up to 2 ulp either way)
+    from fractions import Fraction
+    q = f32(Fraction(a) / Fraction(b))
+    if rng is not None and q != 0.0:
+        q = float(np.float32(q) + np.float32(rng.integers(-2, 3)) * np.spacing(np.float32(abs(q))))
+    return q
+
+
+def make_clip(ax, ay, bx, by, w, rng=None):
+    # grid_common.cuh make_rgeo: the clip points and {ux, uy, nk, v}
+    ux, uy = bx - ax, by - ay
+    m = max(abs(ax), abs(ay), abs(bx), abs(by))
+    exact = abs(ux) <= 1024 and abs(uy) <= 1024 and m <= 4096
+    whole = min(ax, ay, bx, by) >= 0 and max(ax, ay, bx, by) <= w
+    line = (float(ux), float(uy), -f32(ux * ay - uy * ax), (0.0 if whole else 64.0) if exact else 8192.0)
+    if (uy == 0 and ay in (0, w)) or (ux == 0 and ax in (0, w)):
+        return (math.nan,) * 4, line
+    if whole:
+        return (float(ax), float(ay), float(bx), float(by)), line
+    t0, t1 = 0.0, 1.0
+    if ux:
+        ta, tb = div_fast(-ax, ux, rng), div_fast(w - ax, ux, rng)
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    if uy:
+        ta, tb = div_fast(-ay, uy, rng), div_fast(w - ay, uy, rng)
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    if t1 < t0:
+        t1 = t0
+    return (fmaf(t0, ux, ax), fmaf(t0, uy, ay), fmaf(t1, ux, ax), fmaf(t1, uy, ay)), line
+
+
+def fmin(a, b):
+    # IEEE minNum (fminf): a NaN operand yields the other
+    return b if math.isnan(a) else (a if math.isnan(b) else min(a, b))
+
+
+def fmax(a, b):
+    return b if math.isnan(a) else (a if math.isnan(b) else max(a, b))
+
+
+def clip_test(rb, rc, cb, cc):
+    # grid_common.cuh clip_test: (out, in)
+    def s(line, p):
+        return fmaf(line[0], p[1], fmaf(-line[1], p[0], line[2]))
+    s0, s1 = s(cb, rc[:2]), s(cb, rc[2:])
+    s2, s3 = s(rb, cc[:2]), s(rb, cc[2:])
+    M01 = fmax(cb[3], min(rb[3], 64.0))
+    M23 = fmax(rb[3], min(cb[3], 64.0))
+    lo01, hi01, lo23, hi23 = fmin(s0, s1), fmax(s0, s1), fmin(s2, s3), fmax(s2, s3)
+    out = lo01 > M01 or hi01 < -M01 or lo23 > M23 or hi23 < -M23
+    inside = lo01 < -M01 and hi01 > M01
+    return out, inside
+
+
+def exact_owner(r, c, w):
+    # the half-open cell [0, w)^2 holds the intersection point of the two lines
+    from fractions import Fraction
+    ax, ay, bx, by = r
+    cx, cy, dx, dy = c
+    ux, uy, vx, vy = bx - ax, by - ay, dx - cx, dy - cy
+    den = ux * vy - uy * vx
+    t = Fraction((cx - ax) * vy - (cy - ay) * vx, den)
+    X, Y = ax + ux * t, ay + uy * t
+    return int(0 <= X < w and 0 <= Y < w)
+
+
+def crossing(r, c):
+    from fractions import Fraction
+    def o(p, q, s):
+        return (q[0] - p[0]) * (s[1] - p[1]) - (q[1] - p[1]) * (s[0] - p[0])
+    a, b, p, q = r[:2], r[2:], c[:2], c[2:]
+    o1, o2, o3, o4 = o(a, b, p), o(a, b, q), o(p, q, a), o(p, q, b)
+    return o1 * o2 <= 0 and o3 * o4 <= 0 and not (o1 == 0 and o2 == 0)
+
+
+def meets_cell(r, w):
+    # the closed segment meets the closed cell [0, w]^2 (exact, Liang-Barsky)
+    from fractions import Fraction
+    lo, hi = Fraction(0), Fraction(1)
+    for a0, u in ((r[0], r[2] - r[0]), (r[1], r[3] - r[1])):
+        if u == 0:
+            if not 0 <= a0 <= w:
+                return False
+        else:
+            ta, tb = Fraction(-a0, u), Fraction(w - a0, u)
+            lo, hi = max(lo, min(ta, tb)), min(hi, max(ta, tb))
+    return lo <= hi
+
+
+def test_clip_test_never_drops_a_pair_this_cell_owns():
+    # pairs of crossing segments in the coordinates of one cell, among them long
+    # ones reaching far outside it, intersections near the cell's corners and
+    # borders, and segments along its border lines: the FP32 clip test (both
+    # clipped parts against the other's line) never rejects a pair whose exact
+    # intersection point lies in the half-open cell, and whenever it places the
+    # point inside, the exact owner is this cell
+    rng = np.random.default_rng(123)
+    owned = rejected = inside = 0
+    for trial in range(8000):
+        k = int(rng.choice([6, 8, 10, 12]))
+        w = 1 << k
+        x0 = int(rng.integers(1, 65536 // w - 1)) * w
+        y0 = int(rng.integers(1, 65536 // w - 1)) * w
+        P = rng.uniform(-0.25 * w, 1.25 * w, size=2)
+        if rng.random() < 0.3:
+            P = np.array([float(rng.choice([0, w])), float(rng.choice([0, w]))])
+        elif rng.random() < 0.3:
+            P[int(rng.integers(0, 2))] = float(rng.choice([0, w]))
+
+        def seg():
+            th = rng.uniform(0, math.pi)
+            if rng.random() < 0.15:
+                th = float(rng.choice([0.0, math.pi / 2]))  # axis-parallel, possibly along a cell line
+            d = np.array([math.cos(th), math.sin(th)])
+            la, lb = (rng.uniform(0, 40000, size=2) if rng.random() < 0.4 else rng.uniform(0, 1.5 * w, size=2))
+            p = np.rint(np.concatenate([P - la * d, P + lb * d]) + [x0, y0, x0, y0])
+            p = np.clip(p, 0, 65535).astype(np.int64)
+            return tuple(int(v) for v in (p[0] - x0, p[1] - y0, p[2] - x0, p[3] - y0))
+        r, c = seg(), seg()
+        if (r[0], r[1]) == (r[2], r[3]) or (c[0], c[1]) == (c[2], c[3]) or not crossing(r, c):
+            continue
+        ux, uy, vx, vy = r[2] - r[0], r[3] - r[1], c[2] - c[0], c[3] - c[1]
+        if ux * vy - uy * vx == 0:
+            continue
+        if not (meets_cell(r, w) and meets_cell(c, w)):  # the grid only emits such records
+            continue
+        rc, rb = make_clip(*r, w, rng)
+        cc, cb = make_clip(*c, w, rng)
+        out, ins = clip_test(rb, rc, cb, cc)
+        own = exact_owner(r, c, w)
+        owned += own
+        if own:
+            assert not out, (trial, r, c, w)
+        else:
+            rejected += out
+        if ins:
+            inside += 1
+            assert own, (trial, r, c, w)
+    assert owned > 500 and rejected > 500 and inside > 300

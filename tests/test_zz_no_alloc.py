@@ -53,3 +53,29 @@ def test_noalloc_rejects_layouts_above_its_limit():
     st = lib.gr_crossing_angle_noalloc(xy.data_ptr(), 100, ed.data_ptr(), E, 0.0, ctypes.byref(out), None)
     assert st == gr.GR_EINVAL
     assert "limit" in gr.gr_last_error()
+
+
+def test_noalloc_reports_bad_inputs_and_recovers():
+    # the device-side checks come back through the shared scratch accumulator:
+    # a self-loop (GR_EINVAL) and a coordinate of 65536 (GR_ERANGE); a valid
+    # call right after each must still equal gr_crossing_angle
+    build.build()
+    lib = gr.load()
+    L = synth.plain_layout(V=800, knn_count=1600, random_count=400, seed=21)
+    xy, ed = _cuda(L.xy), _cuda(L.edges)
+    with gr.Layout(xy, ed, gr.gr_options(gr.GR_PATH_ALLPAIRS, 0, 0, 0)) as lay:
+        ref = gr.gr_crossing_angle(lay.handle, 0.0)
+    bad_e = L.edges.copy()
+    bad_e[17] = [5, 5]
+    bad_xy = L.xy.copy()
+    bad_xy[3] = [65536, 10]
+    for xs, es, status in [(L.xy, bad_e, gr.GR_EINVAL), (bad_xy, L.edges, gr.GR_ERANGE)]:
+        bx, be = _cuda(xs), _cuda(es)
+        out = gr.gr_crossing_angle_result()
+        st = lib.gr_crossing_angle_noalloc(bx.data_ptr(), len(xs), be.data_ptr(), len(es), 0.0,
+                                           ctypes.byref(out), None)
+        assert st == status, gr.gr_last_error()
+        got = gr.gr_crossing_angle_noalloc(xy, ed, 0.0)
+        for f in ("crossings", "proper", "touching", "collinear_overlaps", "zero_length_edges", "pairs_tested"):
+            assert getattr(got.c, f) == getattr(ref.c, f), f
+        assert got.angle_dev_sum == pytest.approx(ref.angle_dev_sum, rel=REL)
