@@ -183,6 +183,7 @@ def load_traffic(kernel: str, workload: str, src_hash: str):
 # The sources each captured kernel is built from: its own file and every
 # header it includes, so an edit anywhere in them retires the capture.
 KERNEL_SOURCES = {
+    "k_cell_pairs": ["k_grid.cu", "grid_common.cuh", "pair_math.cuh", "gr_internal.cuh"],
     "k_grid_pairs": ["k_grid.cu", "grid_common.cuh", "pair_math.cuh", "gr_internal.cuh"],
     "k_grid_fill": ["k_grid.cu", "grid_common.cuh", "pair_math.cuh", "gr_internal.cuh"],
     "k_cross_allpairs_agg": ["k_crossings.cu", "allpairs_common.cuh", "pair_math.cuh", "gr_internal.cuh"],
@@ -252,7 +253,10 @@ def roofline(res, prof: dict, n_seg: int, peaks: dict, peak_kind: str, workload:
         pairs = res.crossing.c.pairs_tested
         ops = pairs * OPS_PER_PAIR + ec * (OPS_PER_CROSSING_GRID if grid else OPS_PER_CROSSING_ALLPAIRS)
         peak = SM_COUNT * LANES_PER_SM_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        kernel = "k_grid_pairs" if grid else "k_cross_allpairs_agg"
+        # the grid path runs the rotation kernel unless the planner sends pairs of two long
+        # segments to the all-pairs tiles (then the tile kernel k_grid_pairs); the bench
+        # workloads keep them in the grid
+        kernel = "k_cell_pairs" if grid else "k_cross_allpairs_agg"
         achieved = ops / t / 1e12
         cap = load_capture(kernel, workload, kernel_source_hash(KERNEL_SOURCES[kernel]))
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak,

@@ -429,48 +429,78 @@ namespace gr {
 // All pairs of a cell's n records in the rotation order: row i meets rows
 // (i + q) mod n for q = 1 .. n/2, except that for even n the offset n/2 is
 // taken from rows i < n/2 only; every unordered pair of the cell appears
-// exactly once.  A work item is one warp's share: the 32 rows (one per lane;
-// the last chunk of a cell may have fewer) of a chunk and RQ consecutive
-// offsets.  The item's columns, rows 32 c + q0 + t (mod n) for t < 32 + RQ - 1,
-// form a window the warp stages in shared memory, so lane l meets window
-// slot l + (q - q0).
-constexpr int RQ = 16;                 // rotation offsets per work item
-constexpr int RWIN = 32 + RQ - 1;      // window slots of an item
+// exactly once.  A work item is one warp's share of a chunk of m rows (32,
+// or n mod 32 for a cell's last chunk): s streams of the m rows (s = 1 for a
+// full chunk, up to 3 for a short last chunk, so that fewer lanes idle), each
+// stream taking RQ consecutive offsets, stream sigma the offsets
+// q0 + sigma RQ ... .  The item's columns form a window the warp stages in
+// shared memory: stream sigma's rows 32 c + r meet, at their t-th offset,
+// window slot sigma (m + RQ - 1) + r + t, which holds row
+// 32 c + q0 + sigma RQ + r + t (mod n) of the cell.
+constexpr int RQ = 16;                 // rotation offsets per stream of a work item
+constexpr int RQ_HALF = RQ / 2;        // the kernel settles its queue after each half
+constexpr int RSTREAMS = 3;            // at most this many streams of a short last chunk
+constexpr int RWIN = 75;               // window slots: max over m of s (m + RQ - 1)
+
+// Streams of a chunk of m rows in a cell with P offset pieces.
+__host__ __device__ __forceinline__ int rot_streams(int m, int P) {
+    return m >= 32 ? 1 : min(min(RSTREAMS, max(1, 32 / m)), max(1, P));
+}
 
 // Work items of a cell with n records; overflow when the item word cannot
 // hold the chunk or offset index.
 __device__ __forceinline__ uint64_t rot_item_count(uint64_t n, bool *overflow) {
     *overflow = false;
     if (n < 2) return 0;
-    const uint64_t Q = n >> 1, F = (n + 31) >> 5, P = (Q + RQ - 1) / RQ;
-    *overflow = F > (1u << 15) || P >= (1u << 16);
-    return F * P;
+    const uint64_t Q = n >> 1, Ff = n >> 5, m = n & 31, P = (Q + RQ - 1) / RQ;
+    *overflow = Ff + 1 > (1u << 15) || P >= (1u << 16);
+    uint64_t items = Ff * P;
+    if (m) {
+        const uint64_t s = (uint64_t)rot_streams((int)m, (int)min(P, (uint64_t)RSTREAMS));
+        items += (P + s - 1) / s;
+    }
+    return items;
 }
 
 // The item words of a cell, in the order counted by rot_item_count, via
-// emit(i, word) for i in [q, q_end): chunk c, offsets piece p as c << 16 | p.
+// emit(i, word) for i in [q, q_end): chunk c and piece group p (of s pieces
+// for the last chunk) as c << 16 | p.
 template <class F>
 __device__ __forceinline__ void rot_item_words(uint32_t n, uint32_t q, uint32_t q_end, F &&emit) {
     if (n < 2) return;
-    const uint32_t Q = n >> 1, Fc = (n + 31) >> 5, P = (Q + RQ - 1) / RQ;
-    for (uint32_t c = 0; c < Fc && q < q_end; ++c)
+    const uint32_t Q = n >> 1, Ff = n >> 5, m = n & 31, P = (Q + RQ - 1) / RQ;
+    for (uint32_t c = 0; c < Ff && q < q_end; ++c)
         for (uint32_t p = 0; p < P && q < q_end; ++p, ++q) emit(q, (c << 16) | p);
+    if (m) {
+        const uint32_t s = (uint32_t)rot_streams((int)m, (int)min(P, (uint32_t)RSTREAMS));
+        for (uint32_t p = 0; p < (P + s - 1) / s && q < q_end; ++p, ++q) emit(q, (Ff << 16) | p);
+    }
 }
 
-// A lane's share of a rotation item: row i of the cell, the item's first
-// offset q0 and the number of offsets this lane takes from it (0: none).
+// A lane's share of a rotation item: row i of the cell, its first offset q0,
+// the number of offsets it takes (0: none) and its first window slot; and the
+// item's stream layout (m rows, s streams, first window row of stream 0).
 struct RotLane {
-    int i, q0, cnt;
+    int i, q0, cnt, slot;
+    int m, s;
+    uint32_t first;
 };
 
 __device__ __forceinline__ RotLane rot_lane(int n, uint32_t w, int lane) {
     const int Q = n >> 1, c = (int)((w >> 16) & 0x7fffu), p = (int)(w & 0xffffu);
+    const int P = (Q + RQ - 1) / RQ;
     RotLane r;
-    r.i = 32 * c + lane;
-    r.q0 = 1 + p * RQ;
+    r.m = min(32, n - 32 * c);
+    r.s = rot_streams(r.m, min(P, RSTREAMS));
+    const int sig = lane / r.m, row = lane - sig * r.m;
+    const int piece = (r.m == 32 ? p : p * r.s) + sig;
+    r.i = 32 * c + row;
+    r.q0 = 1 + piece * RQ;
+    r.first = (uint32_t)(32 * c + 1 + (r.m == 32 ? p : p * r.s) * RQ);
+    r.slot = sig * (r.m + RQ - 1) + row;
     const int Qi = ((n & 1) == 0 && r.i >= (n >> 1)) ? Q - 1 : Q;
-    r.cnt = r.i < n ? max(0, min(Qi, r.q0 + RQ - 1) - r.q0 + 1) : 0;
-    if (r.i >= n) r.i = 0;
+    r.cnt = (sig < r.s && piece < P) ? max(0, min(Qi, r.q0 + RQ - 1) - r.q0 + 1) : 0;
+    if (r.cnt == 0) { r.i = 0; r.slot = 0; }
     return r;
 }
 

@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256) k_rec_geo(const GridRec *__restrict__ rec
 // pairs are settled 32 at a time by the whole warp (settle_pair) after each
 // item, so the rare cases never run with idle lanes.
 constexpr int CP_WARPS = 8;                    // warps per block
-constexpr int CP_QUEUE = 32 * RQ + 32;         // queued pairs per warp: up to 31 left + 32 per offset
+constexpr int CP_QUEUE = 32 * RQ_HALF + 32;    // queued pairs per warp: up to 31 left + 32 per offset
 
 // Settles one queued pair (row | clip-in flag << 31, col) of a cell of side w:
 // shared vertex ids skip it; the FP32 orientations decide it when they are
@@ -511,6 +511,7 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
                                                                  uint64_t rec_cap, uint64_t items_cap, int k,
                                                                  DevAcc *acc, uint32_t ideal, PerEdge pe) {
     __shared__ float4 win_b[CP_WARPS][RWIN], win_c[CP_WARPS][RWIN];
+    __shared__ uint32_t win_i[CP_WARPS][RWIN];
     __shared__ uint2 qbuf[CP_WARPS][CP_QUEUE];
     __shared__ uint64_t shu[32];
     const uint32_t n_items = *n_items_p;
@@ -521,6 +522,7 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
     const float4 *__restrict__ geo_b = geo + rec_cap;
     const float4 *__restrict__ geo_c = geo + 2 * rec_cap;
     float4 *wb = win_b[wid], *wc = win_c[wid];
+    uint32_t *wi = win_i[wid];
     uint2 *q = qbuf[wid];
     int qn = 0;
     PairCounts pc;
@@ -532,33 +534,36 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
         if (it + stride < n_items) next = descs[2 * (uint64_t)(it + stride)];  // prefetch the next item
         const uint32_t base = d.x, n = d.y;
         const RotLane rl = rot_lane((int)n, d.w, lane);
-        // the item's column window: records 32 c + q0 + t (mod n) of the cell
-        const uint32_t first = 32u * ((d.w >> 16) & 0x7fffu) + (uint32_t)rl.q0;
+        // the item's column window: stream sigma's slots hold rows
+        // first + sigma RQ + x (mod n) of the cell, x < m + RQ - 1
+        const int span = rl.m + RQ - 1, slots = rl.s * span;
         __syncwarp();
-        for (int t = lane; t < RWIN; t += 32) {
-            const uint32_t r = base + (first + (uint32_t)t) % n;
-            wb[t] = geo_b[r];
-            wc[t] = geo_c[r];
+        for (int u = lane; u < slots; u += 32) {
+            const int sig = u / span;
+            const uint32_t r = base + (rl.first + (uint32_t)(sig * RQ + (u - sig * span))) % n;
+            wb[u] = geo_b[r];
+            wc[u] = geo_c[r];
+            wi[u] = r;
         }
         const uint32_t row = base + (uint32_t)rl.i;
         const float4 rb = geo_b[row], rc = geo_c[row];
         const float r_pts = fminf(rb.w, kClipExact);
+        const uint32_t rowq = row;
         __syncwarp();
+        for (int h = 0; h < RQ; h += RQ_HALF) {
 #pragma unroll
-        for (int t = 0; t < RQ; ++t) {
-            const ClipTest ct = clip_test(rb, rc, r_pts, wb[lane + t], wc[lane + t]);
-            const bool keep = t < rl.cnt && !ct.out;
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (m) {
-                if (keep) {
-                    uint32_t j = (uint32_t)(rl.i + rl.q0 + t);
-                    if (j >= n) j -= n;
-                    q[qn + __popc(m & lt)] = make_uint2(row | (ct.in ? 0x80000000u : 0u), base + j);
+            for (int tt = 0; tt < RQ_HALF; ++tt) {
+                const int t = h + tt, u = rl.slot + t;
+                const ClipTest ct = clip_test(rb, rc, r_pts, wb[u], wc[u]);
+                const bool keep = t < rl.cnt && !ct.out;
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (m) {
+                    if (keep) q[qn + __popc(m & lt)] = make_uint2(rowq | (ct.in ? 0x80000000u : 0u), wi[u]);
+                    qn += __popc(m);
                 }
-                qn += __popc(m);
             }
+            settle_queue<PER_EDGE>(geo, rec_cap, rec, q, qn, lane, w, ideal, pc, pe);
         }
-        settle_queue<PER_EDGE>(geo, rec_cap, rec, q, qn, lane, w, ideal, pc, pe);
     }
     __syncwarp();
     if (lane < qn) settle_pair<PER_EDGE>(geo, rec_cap, rec, q[lane], w, ideal, pc, pe);

@@ -137,51 +137,82 @@ def test_min_angle_sector_gap_matches_atan2():
     assert worst < 2e-15
 
 
-def rotation_constant():
-    m = re.search(r"constexpr int RQ = (\d+);", source("grid_common.cuh"))
-    return int(m.group(1))
+def rotation_constants():
+    src = source("grid_common.cuh")
+    get = lambda name: int(re.search(r"constexpr int %s = (\d+);" % name, src).group(1))
+    return get("RQ"), get("RSTREAMS"), get("RWIN")
 
 
-def rot_items(n, RQ):
+def rot_streams(m, P, RS):
+    # grid_common.cuh rot_streams
+    return 1 if m >= 32 else min(RS, max(1, 32 // m), max(1, P))
+
+
+def rot_items(n, RQ, RS):
     # grid_common.cuh rot_item_count / rot_item_words
     if n < 2:
         return []
-    Q, F = n >> 1, (n + 31) >> 5
+    Q, Ff, m = n >> 1, n >> 5, n & 31
     P = (Q + RQ - 1) // RQ
-    return [(c << 16) | p for c in range(F) for p in range(P)]
+    words = [(c << 16) | p for c in range(Ff) for p in range(P)]
+    if m:
+        s = rot_streams(m, min(P, RS), RS)
+        words += [(Ff << 16) | p for p in range((P + s - 1) // s)]
+    return words
 
 
-def rot_lane(n, w, lane, RQ):
-    # grid_common.cuh rot_lane: (row, first offset, offsets taken)
+def rot_lane(n, w, lane, RQ, RS):
+    # grid_common.cuh rot_lane: (row, first offset, offsets taken, window slot, m, s, first window row)
     Q, c, p = n >> 1, (w >> 16) & 0x7FFF, w & 0xFFFF
-    i, q0 = 32 * c + lane, 1 + p * RQ
+    P = (Q + RQ - 1) // RQ
+    m = min(32, n - 32 * c)
+    s = rot_streams(m, min(P, RS), RS)
+    sig, row = lane // m, lane % m
+    pbase = p if m == 32 else p * s
+    piece = pbase + sig
+    i, q0 = 32 * c + row, 1 + piece * RQ
+    first = 32 * c + 1 + pbase * RQ
+    slot = sig * (m + RQ - 1) + row
     Qi = Q - 1 if (n % 2 == 0 and i >= n // 2) else Q
-    cnt = max(0, min(Qi, q0 + RQ - 1) - q0 + 1) if i < n else 0
-    return (i if i < n else 0), q0, cnt
+    cnt = max(0, min(Qi, q0 + RQ - 1) - q0 + 1) if (sig < s and piece < P) else 0
+    if cnt == 0:
+        i, slot = 0, 0
+    return i, q0, cnt, slot, m, s, first
 
 
 @pytest.mark.parametrize("n", list(range(0, 70)) + [95, 96, 97, 127, 128, 129, 255, 256, 299, 300, 513, 1000])
 def test_rotation_items_cover_every_pair_of_a_cell_once(n):
     # every unordered pair {i, j} of the cell's n records is met exactly once by
-    # the lanes of its rotation work items, each lane within the cell's rows and
-    # its columns within the item's window of 32 + RQ - 1 slots
-    RQ = rotation_constant()
+    # the lanes of its rotation work items, each lane within the cell's rows, and
+    # the window slot a lane reads at each offset (staged as the kernel stages
+    # it, within RWIN slots) holds that pair's column
+    RQ, RS, RWIN = rotation_constants()
     seen = {}
-    for w in rot_items(n, RQ):
-        c = (w >> 16) & 0x7FFF
-        for lane in range(32):
-            i, q0, cnt = rot_lane(n, w, lane, RQ)
+    for w in rot_items(n, RQ, RS):
+        lanes = [rot_lane(n, w, lane, RQ, RS) for lane in range(32)]
+        _, _, _, _, m, s, first = lanes[0]
+        span = m + RQ - 1
+        assert s * span <= RWIN
+        window = [(first + (u // span) * RQ + (u % span)) % n for u in range(s * span)]
+        for i, q0, cnt, slot, *_ in lanes:
             assert cnt <= RQ
             for t in range(cnt):
-                q = q0 + t
-                slot = lane + t
-                assert slot < 32 + RQ - 1
-                j = (i + q) % n
-                assert j == (32 * c + q0 + slot) % n  # the window slot holds the column
+                j = (i + q0 + t) % n
+                assert window[slot + t] == j
                 key = (min(i, j), max(i, j))
                 seen[key] = seen.get(key, 0) + 1
     assert len(seen) == n * (n - 1) // 2
     assert all(v == 1 for v in seen.values())
+
+
+def test_rotation_items_use_most_lanes():
+    # lane slots of a cell's items (32 lanes x RQ offsets) against its pairs:
+    # the streams of a short last chunk keep most lanes busy
+    RQ, RS, _ = rotation_constants()
+    sizes = range(33, 400)
+    pairs = sum(n * (n - 1) // 2 for n in sizes)
+    slots = sum(32 * RQ * len(rot_items(n, RQ, RS)) for n in sizes)
+    assert pairs >= 0.8 * slots
 
 
 def f32(x):
