@@ -366,6 +366,39 @@ gr_status gr_io_bytes(gr_layout *layout, int64_t *h2d, int64_t *d2h);
  * (all layouts, all threads). */
 int64_t gr_kernel_launches(void);
 
+/* ------------------------------------------------------- parts of a layout
+ * The pair work of one layout in n_parts disjoint shares, for evaluating one
+ * large layout on several GPUs (one part per rank) -- the spatial
+ * partitioning by which Sec. 3.2.1-3.2.2 split the plane across machines,
+ * made exact: every pair is counted in one cell (the owner of its
+ * intersection point) and every cell's pairs are enumerated by work items,
+ * so a split of the work items (the all-pairs tiles, the occlusion points)
+ * splits the tallies with nothing counted twice.  Binning, minimum angle and
+ * edge length variation are repeated by every part (they are O(|E|)).
+ *
+ * gr_evaluate_part evaluates part `part` (0 <= part < n_parts) of a
+ * GR_COORD_I32 layout with the metrics and parameters of gr_evaluate and
+ * writes its tallies to *out (host memory); it synchronises.  Summing the
+ * gr_partial of all parts field by field (an integer all-reduce: every field
+ * is an exact integer, and the values only part 0 reports are zero in the
+ * others) and passing the sum to gr_combine_parts gives the gr_result of
+ * gr_evaluate on the whole layout, bit for bit.  gr_combine_parts is host
+ * arithmetic only (no GPU needed).  Errors: GR_EINVAL for a bad part or
+ * NULL, GR_ENOTSUP for FP32 layouts, else as gr_evaluate. */
+typedef struct {
+    /* summed over the parts (each pair and each vertex pair counts in one part) */
+    int64_t proper, touching, collinear_overlaps, occlusion_pairs;
+    int64_t dev_hi32, dev_lo32; /* sum of |ideal - a_c| in units of pi / 2^32: dev_hi32 * 2^32 + dev_lo32 */
+    /* part 0's values, zero in every other part */
+    int64_t metrics, crossing_path, cell_log2, occlusion_path;
+    int64_t zero_length_edges, pairs_tested, n_vertices_counted, grid_records;
+    int64_t min_angle_sum_d_bits, M_a_bits, M_l_bits; /* IEEE-754 bit patterns of part 0's doubles */
+} gr_partial;
+
+gr_status gr_evaluate_part(gr_layout *layout, uint32_t metric_mask, const gr_params *params, int32_t part,
+                           int32_t n_parts, gr_partial *out);
+gr_status gr_combine_parts(const gr_partial *sum, const gr_params *params, gr_result *out);
+
 /* ------------------------------------------------- no device allocation
  * Edge crossings and crossing angle of one layout of at most
  * GR_NOALLOC_MAX_EDGES edges, computed without allocating anything: for

@@ -82,6 +82,13 @@ struct gr_layout {
     uint2 *pairs = nullptr;         // E_c pairs of the last forward
     uint64_t pairs_cap = 0, n_pairs = 0;
     uint2 **pairs_slot = nullptr;   // device copy of `pairs`: a captured backward reads the current buffer
+    bool part_dirty = false;        // the device accumulators hold a share (gr_evaluate_part) other than all
+    bool seg_canonical = false;     // the compacted segments are in edge order (gr_evaluate_part)
+    uint32_t *canon_flags = nullptr;  // [E + 1] and [E] x 3: workspace of the canonical order
+    SegRec *canon_seg = nullptr;
+    int32_t *canon_eid = nullptr;
+    uint32_t *canon_theta = nullptr;
+    bool in_part = false;           // inside gr_evaluate_part
     cudaEvent_t ev_din = nullptr, ev_dout = nullptr;  // orders the differentiable calls with the caller's stream
     int2 *arg = nullptr;            // [V] smallest gap of every vertex
     DiffState *st = nullptr;
@@ -181,7 +188,8 @@ void free_layout(gr_layout *L) {
     Buffers &b = L->b;
     void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.elv_len, b.ma_part,
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result,
-                    b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->pairs_slot, L->arg, L->st, L->out3, L->gout3,
+                    b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->pairs_slot, L->canon_flags, L->canon_seg,
+                    L->canon_eid, L->canon_theta, L->arg, L->st, L->out3, L->gout3,
                     L->f32_work, L->theta_adj, L->moved, L->affected, L->dacc, L->mv_ids, L->mv_xy,
                     L->dirty.flag, L->dirty.list, L->dirty.n, L->mp_dev, b.adj_off, b.adj, b.ma_nz, b.ma_dv, b.ma_touch,
                     b.ma_flag};
@@ -411,6 +419,7 @@ gr_status enqueue_inputs(gr_layout *L, const void *xy, const int32_t *edges) {
     }
     L->diff_ready = false;
     L->dgrid_k = -1;
+    L->seg_canonical = false;  // the gather's order depends on which block reserved its slots first
     phase_end(L, GR_PHASE_GATHER);
     GR_CU(cudaGetLastError());
     L->stats_stale = true;
@@ -423,6 +432,22 @@ gr_status status_to_error(uint32_t st) {
     if (st & ST_SCAN_OVERFLOW) return fail(GR_ENOTSUP, "an offset table exceeded 2^32 entries");
     if (st & ST_OVERFLOW) return fail(GR_ENOMEM, "grid record buffer overflow");
     return GR_OK;
+}
+
+// The share of the pair work the next evaluation does (DevAcc part_id /
+// n_parts, read by the pair kernels); n_parts = 0 means all of it, the state
+// every rewrite of the accumulators' first block leaves.
+gr_status set_part(gr_layout *L, uint32_t part, uint32_t n_parts) {
+    const uint32_t v[2] = {part, n_parts};
+    GR_CU(cudaMemcpyAsync(&L->b.acc->part_id, v, sizeof v, cudaMemcpyHostToDevice, L->stream));
+    L->part_dirty = n_parts > 1;
+    return GR_OK;
+}
+
+// Entry points other than gr_evaluate_part evaluate all of the work.
+gr_status reset_part(gr_layout *L) {
+    if (!L->part_dirty || L->in_part) return GR_OK;
+    return set_part(L, 0, 0);
 }
 
 gr_status read_params(const gr_params *p, double *ideal, int64_t *d) {
@@ -942,6 +967,7 @@ gr_status gr_evaluate(gr_layout *L, uint32_t metrics, const gr_params *params, g
     int64_t d;
     gr_status st = read_params(params, &ideal, &d);
     if (st != GR_OK) return st;
+    if ((st = reset_part(L)) != GR_OK) return st;
     cudaStream_t s = L->stream;
     Buffers &b = L->b;
     const int64_t V = L->V, E = L->E;
@@ -1103,6 +1129,7 @@ gr_status gr_evaluate_async(gr_layout *L, uint32_t metrics, const gr_params *par
     int64_t d;
     gr_status st = read_params(params, &ideal, &d);
     if (st != GR_OK) return st;
+    if ((st = reset_part(L)) != GR_OK) return st;
     cudaStream_t after = stream ? (cudaStream_t)stream : L->stream;
     FastPlan fp;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -1127,6 +1154,95 @@ gr_status gr_evaluate_async(gr_layout *L, uint32_t metrics, const gr_params *par
     L->last.valid = false;
     L->dgrid_k = -1;
     return run_eval_graph(L, metrics, ideal, d, fp, after, d_result, false);
+}
+
+gr_status gr_evaluate_part(gr_layout *L, uint32_t metrics, const gr_params *params, int32_t part, int32_t n_parts,
+                           gr_partial *out) {
+    g_err.clear();
+    if (!L || !out) return fail(GR_EINVAL, "NULL argument");
+    if (n_parts < 1 || part < 0 || part >= n_parts) return fail(GR_EINVAL, "part must be in [0, n_parts), n_parts >= 1");
+    if (L->coord != GR_COORD_I32) return fail(GR_ENOTSUP, "gr_evaluate_part needs a GR_COORD_I32 layout");
+    gr_status st;
+    if (!L->seg_canonical && L->E > 0) {
+        // every rank must enumerate the all-pairs tiles over the same segment order
+        if (!L->canon_flags) {
+            if ((st = dalloc(&L->canon_flags, (size_t)L->E + 1)) != GR_OK) return st;
+            if ((st = dalloc(&L->canon_seg, (size_t)L->E)) != GR_OK) return st;
+            if ((st = dalloc(&L->canon_eid, (size_t)L->E)) != GR_OK) return st;
+            if ((st = dalloc(&L->canon_theta, (size_t)L->E)) != GR_OK) return st;
+        }
+        launch_canonical_segments(L->b, L->E, L->canon_flags, L->canon_seg, L->canon_eid, L->canon_theta, L->stream);
+        GR_CU(cudaGetLastError());
+    }
+    L->seg_canonical = true;
+    if ((st = set_part(L, (uint32_t)part, (uint32_t)n_parts)) != GR_OK) return st;
+    gr_result r;
+    L->in_part = true;
+    st = gr_evaluate(L, metrics, params, &r);
+    L->in_part = false;
+    L->last.valid = false;  // a share's tallies must not seed an incremental move
+    if (st != GR_OK) return st;
+    const DevAcc &a = *L->h_acc;  // read back at the end of the evaluation
+    memset(out, 0, sizeof *out);
+    out->proper = (int64_t)a.proper;
+    out->touching = (int64_t)a.touching;
+    out->collinear_overlaps = (int64_t)a.collinear;
+    out->occlusion_pairs = (int64_t)a.occlusion;
+    // the 128-bit angle sum (dev_hi, dev_lo) as two halves that sum without overflow over many parts
+    out->dev_hi32 = (int64_t)((a.dev_hi << 32) | (a.dev_lo >> 32));
+    out->dev_lo32 = (int64_t)(a.dev_lo & 0xffffffffull);
+    if (part == 0) {
+        out->metrics = r.metrics;
+        out->crossing_path = r.crossing_path;
+        out->cell_log2 = r.cell_log2;
+        out->occlusion_path = r.occlusion_path;
+        out->zero_length_edges = r.crossing.c.zero_length_edges;
+        out->pairs_tested = r.crossing.c.pairs_tested;
+        out->n_vertices_counted = r.min_angle.n_vertices_counted;
+        out->grid_records = r.grid_records;
+        memcpy(&out->min_angle_sum_d_bits, &r.min_angle.sum_d, sizeof(double));
+        memcpy(&out->M_a_bits, &r.min_angle.M_a, sizeof(double));
+        memcpy(&out->M_l_bits, &r.M_l, sizeof(double));
+    }
+    return GR_OK;
+}
+
+gr_status gr_combine_parts(const gr_partial *sp, const gr_params *params, gr_result *out) {
+    g_err.clear();
+    if (!sp || !out) return fail(GR_EINVAL, "NULL argument");
+    double ideal;
+    int64_t d;
+    gr_status st = read_params(params, &ideal, &d);
+    if (st != GR_OK) return st;
+    gr_result r;
+    memset(&r, 0, sizeof r);
+    r.metrics = (uint32_t)sp->metrics;
+    r.crossing_path = (int32_t)sp->crossing_path;
+    r.cell_log2 = (int32_t)sp->cell_log2;
+    r.occlusion_path = (int32_t)sp->occlusion_path;
+    const uint64_t ec = (uint64_t)sp->proper + (uint64_t)sp->touching;
+    r.crossing.c.crossings = (int64_t)ec;
+    r.crossing.c.proper = sp->proper;
+    r.crossing.c.touching = sp->touching;
+    r.crossing.c.collinear_overlaps = sp->collinear_overlaps;
+    r.crossing.c.zero_length_edges = sp->zero_length_edges;
+    r.crossing.c.pairs_tested = sp->pairs_tested;
+    // the same arithmetic as the device's final reduction, on the same 128-bit sum
+    const unsigned __int128 dev = ((unsigned __int128)(uint64_t)sp->dev_hi32 << 32) + (uint64_t)sp->dev_lo32;
+    const uint64_t dev_hi = (uint64_t)(dev >> 64), dev_lo = (uint64_t)dev;
+    const double dv = ((double)dev_hi * 18446744073709551616.0 + (double)dev_lo) * kAngleUnit;
+    r.crossing.angle_dev_sum = dv;
+    r.crossing.ideal_rad = ideal;
+    r.crossing.E_ca = ec > 0 ? 1.0 - dv / (ideal * (double)ec) : 1.0;
+    r.occlusion_pairs = sp->occlusion_pairs;
+    r.occlusion_d = d;
+    memcpy(&r.min_angle.sum_d, &sp->min_angle_sum_d_bits, sizeof(double));
+    memcpy(&r.min_angle.M_a, &sp->M_a_bits, sizeof(double));
+    r.min_angle.n_vertices_counted = sp->n_vertices_counted;
+    memcpy(&r.M_l, &sp->M_l_bits, sizeof(double));
+    r.grid_records = sp->grid_records;
+    *out = r;
+    return GR_OK;
 }
 
 gr_status gr_node_occlusion(gr_layout *L, int64_t d, int64_t *out_pairs) {
@@ -1286,6 +1402,7 @@ gr_status gr_crossings_per_edge(gr_layout *L, double ideal_rad, int64_t *d_count
     int64_t d;
     gr_status st = read_params(&p, &ideal, &d);
     if (st != GR_OK) return st;
+    if ((st = reset_part(L)) != GR_OK) return st;
     const int64_t E = L->E;
     if (E == 0) return GR_OK;
     if (!is_device_pointer(d_counts) || !is_device_pointer(d_dev))
@@ -1468,6 +1585,8 @@ gr_status gr_move_vertices(gr_layout *L, int64_t n, const int32_t *ids, const in
     int64_t d;
     gr_status st = read_params(params, &ideal, &d);
     if (st != GR_OK) return st;
+    if ((st = reset_part(L)) != GR_OK) return st;
+    L->seg_canonical = false;  // a move gathers the segments again
     cudaStream_t s = L->stream;
     Buffers &b = L->b;
     const int64_t V = L->V, E = L->E;

@@ -38,6 +38,7 @@ struct DevAcc {
     uint64_t l1_hist[16];      // their |dx| + |dy|
     uint32_t f32_hist[64];     // FP32 layouts: segments by major-axis length class ilogb + 48
     uint32_t f32_bounds[4];    // FP32 layouts: bounding box (order-preserving keys: min x, min y, max x, max y)
+    uint32_t part_id, n_parts; // the share of the pair work an evaluation does (n_parts 0 or 1: all of it)
     // ---- per evaluation
     uint32_t eval_status;      // ST_* bits raised during an evaluation
     uint32_t grid_flags;       // GF_* bits: the grid path cannot be used
@@ -190,8 +191,17 @@ struct PerEdge {
 // The same over an arbitrary list of n segments (n read from *n_p on the
 // device, at most n_bound; n_bound < 0: unknown on the host, a persistent
 // launch sized on the device, aggregate tallies only), tallies into acc.
+// With `part0_only`, a partitioned evaluation leaves the whole list to part
+// 0 (for lists whose order is not the same on every rank).
 void launch_crossings_allpairs_of(const SegRec *seg, const int32_t *eid, const uint32_t *theta, const uint32_t *n_p,
-                                  DevAcc *acc, int64_t n_bound, uint32_t ideal, PerEdge pe, cudaStream_t s);
+                                  DevAcc *acc, int64_t n_bound, uint32_t ideal, PerEdge pe, cudaStream_t s,
+                                  bool part0_only = false);
+// Puts the compacted segments (seg, seg_eid, seg_theta) in edge order, the
+// order every rank derives alike (the gather's order depends on which block
+// reserved its slots first).  `flags` holds E + 1 uint32, the tmp_* arrays E
+// entries each.
+void launch_canonical_segments(Buffers &b, int64_t E, uint32_t *flags, SegRec *tmp_seg, int32_t *tmp_eid,
+                               uint32_t *tmp_theta, cudaStream_t s);
 void launch_crossings_allpairs(const Buffers &b, int64_t n_seg, uint32_t ideal, PerEdge pe,
                                cudaStream_t s);
 
@@ -455,6 +465,18 @@ __device__ __forceinline__ float i2f_exact(int x) {
 __device__ __forceinline__ float ll2f_rn(long long v) {
     return fmaf(i2f_exact((int)(v >> 16)), 65536.0f, i2f_exact((int)(v & 0xffff)));
 }
+
+// The share [lo, hi) of `units` work units that the evaluation's part takes:
+// part p of n takes floor(units p / n) up to floor(units (p + 1) / n), so the
+// parts cover every unit exactly once.  The units must be enumerated in an
+// order every rank derives alike from the inputs (all-pairs tiles of the
+// segments in edge order, the records or points of cells in cell order).
+__device__ __forceinline__ void part_range(const DevAcc *acc, uint64_t units, uint64_t &lo, uint64_t &hi) {
+    const uint64_t np = acc->n_parts > 1 ? acc->n_parts : 1, p = acc->n_parts > 1 ? acc->part_id : 0;
+    lo = (uint64_t)((unsigned __int128)units * p / np);
+    hi = (uint64_t)((unsigned __int128)units * (p + 1) / np);
+}
+__device__ __forceinline__ bool partitioned(const DevAcc *acc) { return acc->n_parts > 1; }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

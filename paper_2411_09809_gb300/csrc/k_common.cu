@@ -413,6 +413,31 @@ __global__ void __launch_bounds__(256) k_batch_elv(const int64_t *__restrict__ l
     }
 }
 
+// The canonical order of the compacted segments: edge order.  flags[e] = 1
+// for an edge that was not kept (zero length, or invalid); after an exclusive
+// scan, edge e's segment goes to e - flags[e].
+__global__ void __launch_bounds__(256) k_drop_flags(const int64_t *__restrict__ len2, int64_t E,
+                                                    uint32_t *__restrict__ flags) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+        flags[e] = len2[e] == 0 ? 1u : 0u;
+}
+
+__global__ void __launch_bounds__(256) k_canon_scatter(const SegRec *__restrict__ seg, const int32_t *__restrict__ eid,
+                                                       const uint32_t *__restrict__ theta,
+                                                       const DevAcc *__restrict__ acc,
+                                                       const uint32_t *__restrict__ dropped_before,
+                                                       SegRec *__restrict__ tseg, int32_t *__restrict__ teid,
+                                                       uint32_t *__restrict__ ttheta) {
+    const int64_t n = acc->n_seg;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = eid[i];
+        const uint32_t p = (uint32_t)e - dropped_before[e];
+        tseg[p] = seg[i];
+        teid[p] = e;
+        ttheta[p] = theta[i];
+    }
+}
+
 int grid_for(int64_t n, int threads, int max_blocks) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -428,6 +453,19 @@ void launch_gather(const int32_t *xy, int64_t V, const int32_t *edges, int64_t E
     count_launches(1);
     k_gather<<<grid_for(E > V ? E : V, kGatherThreads, 152 * 16), kGatherThreads, 0, s>>>((const int2 *)xy, V, (const int2 *)edges, E,
                                                         b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc);
+}
+
+void launch_canonical_segments(Buffers &b, int64_t E, uint32_t *flags, SegRec *tmp_seg, int32_t *tmp_eid,
+                               uint32_t *tmp_theta, cudaStream_t s) {
+    if (E <= 0) return;
+    count_launches(2);
+    k_drop_flags<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>(b.len2, E, flags);
+    launch_scan_u32(flags, flags, E, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
+    k_canon_scatter<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>(b.seg, b.seg_eid, b.seg_theta, b.acc, flags, tmp_seg,
+                                                              tmp_eid, tmp_theta);
+    cudaMemcpyAsync(b.seg, tmp_seg, sizeof(SegRec) * E, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(b.seg_eid, tmp_eid, sizeof(int32_t) * E, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(b.seg_theta, tmp_theta, sizeof(uint32_t) * E, cudaMemcpyDeviceToDevice, s);
 }
 
 void launch_check_vertices(const int32_t *xy, int64_t V, Buffers &b, cudaStream_t s) {

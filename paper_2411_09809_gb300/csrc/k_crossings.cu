@@ -17,7 +17,7 @@ template <int THREADS, int RPT>
 __global__ void __launch_bounds__(THREADS) k_cross_allpairs_agg(const SegRec *__restrict__ seg,
                                                                 const uint32_t *__restrict__ theta,
                                                                 const uint32_t *__restrict__ n_p, DevAcc *acc,
-                                                                uint32_t ideal, int64_t tiles) {
+                                                                uint32_t ideal, int64_t tiles, int part0_only) {
     __shared__ AllPairsSmem<THREADS * RPT> sm;
     __shared__ uint64_t shu[32];
     const int n = (int)*n_p;
@@ -26,7 +26,14 @@ __global__ void __launch_bounds__(THREADS) k_cross_allpairs_agg(const SegRec *__
         tiles = nb * (nb + 1) / 2;
     }
     PairCounts pc;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    uint64_t lo, hi;  // this evaluation's share of the tiles
+    if (part0_only) {
+        lo = 0;
+        hi = (partitioned(acc) && acc->part_id != 0) ? 0 : (uint64_t)tiles;
+    } else {
+        part_range(acc, (uint64_t)tiles, lo, hi);
+    }
+    for (int64_t t = (int64_t)lo + blockIdx.x; t < (int64_t)hi; t += gridDim.x) {
         int bi, bj;
         decode_tile(t, bi, bj);
         allpairs_tile<THREADS, RPT>(seg, theta, n, bi, bj, ideal, sm, pc);
@@ -113,10 +120,12 @@ void launch_crossings_allpairs(const Buffers &b, int64_t n_seg, uint32_t ideal, 
 }
 
 void launch_crossings_allpairs_of(const SegRec *seg, const int32_t *eid, const uint32_t *theta, const uint32_t *n_p,
-                                  DevAcc *acc, int64_t n_bound, uint32_t ideal, PerEdge pe, cudaStream_t s) {
+                                  DevAcc *acc, int64_t n_bound, uint32_t ideal, PerEdge pe, cudaStream_t s,
+                                  bool part0_only) {
+    const int p0 = part0_only ? 1 : 0;
     if (n_bound < 0) {  // the count is known on the device only: small tiles, persistent
         count_launches(1);
-        k_cross_allpairs_agg<AS_THREADS, AS_RPT><<<152 * 8, AS_THREADS, 0, s>>>(seg, theta, n_p, acc, ideal, -1);
+        k_cross_allpairs_agg<AS_THREADS, AS_RPT><<<152 * 8, AS_THREADS, 0, s>>>(seg, theta, n_p, acc, ideal, -1, p0);
         return;
     }
     if (n_bound < 2) return;
@@ -129,12 +138,12 @@ void launch_crossings_allpairs_of(const SegRec *seg, const int32_t *eid, const u
         const int64_t nb = (n_bound + AS_ROWS - 1) / AS_ROWS;
         const int64_t tiles = nb * (nb + 1) / 2;
         k_cross_allpairs_agg<AS_THREADS, AS_RPT><<<grid_of(tiles), AS_THREADS, 0, s>>>(seg, theta, n_p, acc, ideal,
-                                                                                      tiles);
+                                                                                      tiles, p0);
     } else {
         const int64_t nb = (n_bound + AG_ROWS - 1) / AG_ROWS;
         const int64_t tiles = nb * (nb + 1) / 2;
         k_cross_allpairs_agg<AG_THREADS, AG_RPT><<<grid_of(tiles), AG_THREADS, 0, s>>>(seg, theta, n_p, acc, ideal,
-                                                                                      tiles);
+                                                                                      tiles, p0);
     }
 }
 

@@ -72,6 +72,36 @@ __device__ __forceinline__ int64_t spread_index(int64_t i, const Spread &s) {
     return (int64_t)r;
 }
 
+// The work items of the evaluation's part: the items of the cells whose
+// first record (d.x of an item's descriptor, ascending with the item index)
+// lies in the part's share of the records, so that each cell falls to one
+// part whatever order its records were placed in; binary searches over the
+// descriptors by thread 0, shared through `sh`.  All items when the
+// evaluation is not partitioned.  Every thread of the block must call it.
+__device__ __forceinline__ void part_items(const DevAcc *acc, const uint4 *__restrict__ descs, uint32_t n_items,
+                                           uint32_t *sh, uint32_t &i0, uint32_t &i1) {
+    if (!partitioned(acc)) {
+        i0 = 0;
+        i1 = n_items;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        uint64_t r[2];
+        part_range(acc, acc->records, r[0], r[1]);
+        for (int z = 0; z < 2; ++z) {  // the first item whose cell starts at record >= r[z]
+            uint32_t lo = 0, hi = n_items;
+            while (lo < hi) {
+                const uint32_t mid = lo + (hi - lo) / 2;
+                if ((uint64_t)descs[2 * (uint64_t)mid].x < r[z]) lo = mid + 1; else hi = mid;
+            }
+            sh[z] = lo;
+        }
+    }
+    __syncthreads();
+    i0 = sh[0];
+    i1 = sh[1];
+}
+
 // a2 -- per-cell record counts (all, and long ones); the long segments are
 // appended to the long list.
 __global__ void __launch_bounds__(256) k_grid_count(const SegRec *__restrict__ seg,
@@ -382,15 +412,18 @@ __global__ void __launch_bounds__(GP_WARPS * 32, 4) k_grid_pairs(const GridRec *
     const int G = 65536 >> k;
     const uint32_t stride = gridDim.x * GP_WARPS;
     PairCounts pc;
-    uint32_t it = blockIdx.x * GP_WARPS + wid;
+    __shared__ uint32_t part_sh[2];
+    uint32_t lo, i_end;  // this evaluation's share of the items
+    part_items(acc, descs, n_items, part_sh, lo, i_end);
+    uint32_t it = lo + blockIdx.x * GP_WARPS + wid;
     uint4 next = make_uint4(0, 0, 0, 0), next_c = make_uint4(0, 0, 0, 0);
-    if (it < n_items) {
+    if (it < i_end) {
         next = descs[2 * (uint64_t)it];
         next_c = descs[2 * (uint64_t)it + 1];
     }
-    for (; it < n_items; it += stride) {
+    for (; it < i_end; it += stride) {
         const uint4 d = next, dc = next_c;
-        if (it + stride < n_items) {  // prefetch the next item
+        if (it + stride < i_end) {  // prefetch the next item
             next = descs[2 * (uint64_t)(it + stride)];
             next_c = descs[2 * (uint64_t)(it + stride) + 1];
         }
@@ -526,12 +559,15 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
     uint2 *q = qbuf[wid];
     int qn = 0;
     PairCounts pc;
+    __shared__ uint32_t part_sh[2];
+    uint32_t lo, i_end;  // this evaluation's share of the items
+    part_items(acc, descs, n_items, part_sh, lo, i_end);
     const uint32_t stride = gridDim.x * CP_WARPS;
-    uint32_t it = blockIdx.x * CP_WARPS + wid;
-    uint4 next = it < n_items ? descs[2 * (uint64_t)it] : make_uint4(0, 0, 0, 0);
-    for (; it < n_items; it += stride) {
+    uint32_t it = lo + blockIdx.x * CP_WARPS + wid;
+    uint4 next = it < i_end ? descs[2 * (uint64_t)it] : make_uint4(0, 0, 0, 0);
+    for (; it < i_end; it += stride) {
         const uint4 d = next;
-        if (it + stride < n_items) next = descs[2 * (uint64_t)(it + stride)];  // prefetch the next item
+        if (it + stride < i_end) next = descs[2 * (uint64_t)(it + stride)];  // prefetch the next item
         const uint32_t base = d.x, n = d.y;
         const RotLane rl = rot_lane((int)n, d.w, lane);
         // the item's column window: stream sigma's slots hold rows
@@ -642,7 +678,10 @@ void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, bool split
 
 void launch_grid_long_pairs(const Buffers &b, const GridBuffers &g, int64_t n_bound, uint32_t ideal, PerEdge pe,
                             cudaStream_t s) {
-    launch_crossings_allpairs_of(g.seg_long, g.eid_long, g.theta_long, &b.acc->n_long, b.acc, n_bound, ideal, pe, s);
+    // the long list is filled in the order its warps arrived: in a partitioned
+    // evaluation part 0 takes all of it
+    launch_crossings_allpairs_of(g.seg_long, g.eid_long, g.theta_long, &b.acc->n_long, b.acc, n_bound, ideal, pe, s,
+                                 true);
 }
 
 }  // namespace gr

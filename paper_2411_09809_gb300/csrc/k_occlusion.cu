@@ -18,7 +18,9 @@ __global__ void __launch_bounds__(OC_ROWS) k_occl_allpairs(const int2 *__restric
     __shared__ int2 cp[OC_COLS];
     __shared__ uint64_t shu[32];
     uint32_t cnt = 0;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    uint64_t lo, hi;  // this evaluation's share of the tiles
+    part_range(acc, (uint64_t)tiles, lo, hi);
+    for (int64_t t = (int64_t)lo + blockIdx.x; t < (int64_t)hi; t += gridDim.x) {
         int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
         while (r * (r + 1) / 2 > t) --r;
         while ((r + 1) * (r + 2) / 2 <= t) ++r;
@@ -101,12 +103,18 @@ __global__ void __launch_bounds__(256) k_occl_pairs(const uint32_t *__restrict__
     __shared__ uint64_t sh[32];
     const int G = 65536 >> k;
     const int64_t V = off[C];
+    // this evaluation's share: the vertices of the cells whose first vertex
+    // lies in the part's share of the placed vertices (a cell falls to one
+    // part whatever order its vertices were placed in)
+    uint64_t lo = 0, hi = (uint64_t)V;
+    const bool part = partitioned(acc);
+    if (part) part_range(acc, (uint64_t)V, lo, hi);
     uint64_t cnt = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t p = pts[i];
         const int cx = px(p) >> k, cy = py(p) >> k;
         const int c = cy * G + cx;
+        if (part && (off[c] < lo || off[c] >= hi)) continue;
         cnt += count_close(p, pts, (uint32_t)i + 1, off[c + 1], d2);
         if (cx + 1 < G) cnt += count_close(p, pts, off[c + 1], off[c + 2], d2);
         if (cy + 1 < G) {

@@ -37,6 +37,15 @@ class gr_options(ctypes.Structure):
                 ("occlusion_path", c_int32), ("profile", c_int32), ("long_pairs", c_int32)]
 
 
+class gr_partial(ctypes.Structure):
+    """One part's tallies (gr_evaluate_part): every field an int64, summed over
+    the parts by an integer all-reduce."""
+    _fields_ = [(name, c_int64) for name in (
+        "proper", "touching", "collinear_overlaps", "occlusion_pairs", "dev_hi32", "dev_lo32",
+        "metrics", "crossing_path", "cell_log2", "occlusion_path", "zero_length_edges", "pairs_tested",
+        "n_vertices_counted", "grid_records", "min_angle_sum_d_bits", "M_a_bits", "M_l_bits")]
+
+
 class gr_params(ctypes.Structure):
     _fields_ = [("ideal_rad", c_double), ("occlusion_d", c_int64)]
 
@@ -115,6 +124,10 @@ def load() -> ctypes.CDLL:
         "gr_profile_read": ([P, ctypes.POINTER(gr_profile), c_int32], c_int32),
         "gr_kernel_launches": ([], c_int64),
         "gr_io_bytes": ([P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)], c_int32),
+        "gr_evaluate_part": ([P, c_uint32, ctypes.POINTER(gr_params), c_int32, c_int32,
+                              ctypes.POINTER(gr_partial)], c_int32),
+        "gr_combine_parts": ([ctypes.POINTER(gr_partial), ctypes.POINTER(gr_params),
+                              ctypes.POINTER(gr_result)], c_int32),
         "gr_crossing_angle_noalloc": ([P, c_int64, P, c_int64, c_double,
                                        ctypes.POINTER(gr_crossing_angle_result), P], c_int32),
         "gr_batch_create": ([ctypes.POINTER(c_void_p), c_int64, P, P, P, c_int32, P,
@@ -254,6 +267,31 @@ def gr_evaluate(layout, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
     p = gr_params(float(ideal_rad), int(occlusion_d))
     _check(load().gr_evaluate(layout, metrics, ctypes.byref(p), ctypes.byref(r)))
     return r
+
+
+def gr_evaluate_part(layout, part: int, n_parts: int, metrics: int = GR_METRIC_ALL, ideal_rad: float = 0.0,
+                     occlusion_d: int = 0) -> gr_partial:
+    """Part `part` of `n_parts` of the pair work of an evaluation (its tallies)."""
+    out = gr_partial()
+    p = gr_params(float(ideal_rad), int(occlusion_d))
+    _check(load().gr_evaluate_part(layout, metrics, ctypes.byref(p), int(part), int(n_parts), ctypes.byref(out)))
+    return out
+
+
+def gr_combine_parts(total: gr_partial, ideal_rad: float = 0.0, occlusion_d: int = 0) -> gr_result:
+    """The gr_result of the summed tallies of all parts (host arithmetic)."""
+    r = gr_result()
+    p = gr_params(float(ideal_rad), int(occlusion_d))
+    _check(load().gr_combine_parts(ctypes.byref(total), ctypes.byref(p), ctypes.byref(r)))
+    return r
+
+
+def partial_to_list(p: gr_partial) -> list[int]:
+    return [getattr(p, name) for name, _ in gr_partial._fields_]
+
+
+def partial_from_list(values) -> gr_partial:
+    return gr_partial(*[int(v) for v in values])
 
 
 def gr_node_occlusion(layout, d: int) -> int:

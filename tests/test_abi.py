@@ -35,7 +35,7 @@ def test_header_declares_the_boundary():
               "gr_kernel_launches", "gr_io_bytes", "gr_crossing_angle_noalloc",
               "gr_batch_create", "gr_batch_update", "gr_batch_evaluate", "gr_batch_destroy",
               "gr_diff_forward", "gr_diff_backward", "gr_move_vertices", "gr_strip_crossings",
-              "gr_evaluate_async", "gr_batch_evaluate_async"]:
+              "gr_evaluate_async", "gr_batch_evaluate_async", "gr_evaluate_part", "gr_combine_parts"]:
         assert n in names
 
 
@@ -91,3 +91,18 @@ def test_argument_errors_need_no_gpu(lib):
     assert "limit" in gr.gr_last_error()
     assert gr.gr_version().startswith("gr ")
     assert gr.gr_kernel_launches() == 0  # nothing launched in a process without a GPU call
+
+
+def test_partial_struct_is_seventeen_int64(tmp_path):
+    src = tmp_path / "partial.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "gr.h"
+int main(void) { printf("%zu %zu\\n", sizeof(gr_partial), offsetof(gr_partial, M_l_bits)); return 0; }
+""")
+    exe = tmp_path / "partial"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include", str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(x) for x in out] == [17 * 8, 16 * 8] == [ctypes.sizeof(gr.gr_partial), gr.gr_partial.M_l_bits.offset]
