@@ -446,6 +446,7 @@ def run_batched(args, rank, world, local_rank):
         gr.gr_batch_evaluate(B.handle, n, gr.GR_METRIC_ALL, IDEAL, d)
         e2e_s.append(time.perf_counter() - t0)
     e2e_ms = statistics.mean(e2e_s) * 1e3 if e2e_s else float("nan")
+    tuned_offset, tuned_tile = gr.gr_batch_tuning(B.handle)
     B.close()
     if rank != 0:
         return
@@ -467,6 +468,7 @@ def run_batched(args, rank, world, local_rank):
                    "occlusion_d": d, "ideal_deg": 70.0,
                    "metrics": "all five per layout", "inputs": "seeded synthetic (paper_2411_09809_gb300.synth)",
                    "l2": "256 MiB write between timed steps",
+                   "autotuned": {"cell_offset": tuned_offset, "tile": tuned_tile},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "resolved_pairs_per_s": world * pairs / (ms / 1e3),
         "single_layout_loop": {"layouts_per_s": n / single_s, "sample_layouts": len(sample),
@@ -922,6 +924,7 @@ def run_strips(args, rank, world, local_rank):
                    "step": "gr_layout_update + gr_strip_crossings (E_c and E_ca estimates, Sec. 3.2.2-3.2.3)",
                    "inputs": "seeded synthetic (paper_2411_09809_gb300.synth)",
                    "l2": "256 MiB write between timed steps",
+                   "autotuned": {"cell_offset": tuned_offset, "tile": tuned_tile},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "results": {"E_c_estimate": res.crossings, "E_c_exact": exact.c.crossings,
                     "E_c_error": 1.0 - res.crossings / max(1, exact.c.crossings),
@@ -937,7 +940,7 @@ def run_strips(args, rank, world, local_rank):
                      "work": f"{OPS_PER_MERGE_STEP} ops per binary-search step of each merge level and record, "
                              f"{OPS_PER_STRIP_PAIR} per counted pair",
                      "traffic": None, "launch_ms": cnt_ms, "pipe_peaks_tops": measured_pipes()},
-        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": copies * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": (io1[0] - io0[0]) // max(1, len(e2e_s)),
                 "d2h_bytes_per_step": (io1[1] - io0[1]) // max(1, len(e2e_s))},
         "gpu_launches": launches,
@@ -1057,7 +1060,7 @@ def run_per_edge(args, rank, world, local_rank):
         "results": {"sum_proper": tot[0] // 2, "sum_touching": tot[1] // 2, "E_c": res.crossing.c.crossings},
         "phase_ms": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]},
         "roofline": rf,
-        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": copies * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": L.V * 8, "d2h_bytes_per_step": E * 32},
         "gpu_launches": launches,
         "clocks": clk,
@@ -1209,8 +1212,14 @@ def run_ours(args, rank, world, local_rank):
     lay = gr.Layout(xy, edges, gr.gr_options(0, args.cell_log2, 0, 1, LONG_PAIRS[args.long_pairs]),
                     stream=stream.cuda_stream)
 
+    shard = args.shard and world > 1
+    if shard:
+        from paper_2411_09809_gb300 import shard as gr_shard
+
     def step():
         lay.update(xy)
+        if shard:  # this rank's part of the one layout, then one all-reduce of the parts' tallies
+            return gr_shard.evaluate_sharded(lay, gr.GR_METRIC_ALL, IDEAL, d)
         return lay.evaluate(gr.GR_METRIC_ALL, IDEAL, d)
 
     for _ in range(args.warmup):
@@ -1249,7 +1258,10 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         gr.gr_layout_update(lay.handle, hxy, hed)
-        gr.gr_evaluate(lay.handle, gr.GR_METRIC_ALL, IDEAL, d)
+        if shard:
+            gr_shard.evaluate_sharded(lay, gr.GR_METRIC_ALL, IDEAL, d)
+        else:
+            gr.gr_evaluate(lay.handle, gr.GR_METRIC_ALL, IDEAL, d)
         e2e_s.append(time.perf_counter() - t0)
     io1 = gr.gr_io_bytes(lay.handle)
     e2e_ms = statistics.mean(e2e_s) * 1e3 if e2e_s else float("nan")
@@ -1264,22 +1276,24 @@ def run_ours(args, rank, world, local_rank):
         return
     E = L.E
     pairs = E * (E - 1) / 2
-    value = world * pairs / (ms / 1e3)
+    copies = 1 if shard else world  # sharded: the ranks share one layout
+    value = copies * pairs / (ms / 1e3)
     line = {
         "metric": "edge-pair tests/s", "value": value, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": dict(workload_config(L, d, args.workload),
-                       parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       parallelism=(f"one layout in {world} parts" if shard else f"replicas x{world}")
+                       if world > 1 else "single GPU",
                        crossing_path={1: "grid", 2: "all-pairs"}.get(res.crossing_path, "none"),
                        cell_log2=res.cell_log2, grid_records=res.grid_records,
                        occlusion_path={1: "grid", 2: "all-pairs"}.get(res.occlusion_path, "none")),
-        "issued_pairs_per_s": world * res.crossing.c.pairs_tested / (ms / 1e3),
+        "issued_pairs_per_s": copies * res.crossing.c.pairs_tested / (ms / 1e3),
         "results": {"E_c": res.crossing.c.crossings, "E_ca": res.crossing.E_ca,
                     "N_c": res.occlusion_pairs, "M_a": res.min_angle.M_a, "M_l": res.M_l},
         "phase_ms": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]},
         "roofline": rf,
-        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": copies * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": (io1[0] - io0[0]) // max(1, len(e2e_s)),
                 "d2h_bytes_per_step": (io1[1] - io0[1]) // max(1, len(e2e_s))},
         "gpu_launches": launches,
@@ -1337,6 +1351,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (for profiler runs)")
+    ap.add_argument("--shard", action="store_true",
+                    help="single layouts under torchrun: every rank evaluates its part of the one layout "
+                         "(gr_evaluate_part) and one all-reduce combines them (strong scaling)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="default workload: skip the dense, batched and differentiable runs reported beside it")
     ap.add_argument("--no-single-loop", action="store_true",

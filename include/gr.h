@@ -301,10 +301,13 @@ gr_status gr_diff_backward(gr_layout *layout, const float *gout3, float *d_grad_
  *
  * gr_batch_create validates (GR_EINVAL / GR_ERANGE as gr_layout_create),
  * plans one crossing grid per layout (cell size from a cost model on the
- * layout's segment count and length, shifted by an offset an autotuner picks
- * by timing; opt->cell_log2 < 0 fixes that offset instead, and the tuned
- * offset is cached in the file named by the environment variable
- * GR_TUNE_CACHE when it is set) and synchronises.  gr_batch_evaluate runs
+ * layout's segment count and length, shifted by an offset) and picks the
+ * tile height of the pair kernel's work items (16 or 32 segments: two items
+ * per warp or one), both by an autotuner that times the crossing pipeline of
+ * each choice (opt->cell_log2 < 0 fixes the offset instead; the environment
+ * variable GR_BATCH_TILE = 16 or 32 fixes the tile height; the tuned pair is
+ * cached in the file named by GR_TUNE_CACHE when it is set), and
+ * synchronises.  gr_batch_evaluate runs
  * the evaluation as one CUDA graph on the batch's stream (captured on the
  * first call and again when the metrics, ideal angle or d change), writes
  * gr_result [n_layouts] to `out` (host or device memory) and synchronises.
@@ -317,6 +320,10 @@ gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_of
 gr_status gr_batch_update(gr_batch *batch, const void *xy, const int32_t *edges);
 gr_status gr_batch_evaluate(gr_batch *batch, uint32_t metrics, const gr_params *params, gr_result *out);
 gr_status gr_batch_destroy(gr_batch *batch);
+/* The plan gr_batch_create settled on: the cell-size offset added to every
+ * layout's cost-model choice and the tile height (16 or 32) of the pair
+ * kernel's work items. */
+gr_status gr_batch_tuning(const gr_batch *batch, int32_t *cell_offset, int32_t *tile);
 /* gr_batch_evaluate without any host synchronisation: ordered after the work
  * queued on `stream` (NULL: the batch's stream), results written to
  * `d_results` (DEVICE memory, [n_layouts] gr_result) before anything queued

@@ -190,14 +190,15 @@ __global__ void __launch_bounds__(256) k_batch_long_tiles(const uint32_t *__rest
 // (Tile pairs with a short row tile, as in the single-layout grid.)
 __global__ void __launch_bounds__(256) k_batch_cell_items(const uint32_t *__restrict__ cell_off,
                                                           const uint32_t *__restrict__ cell_nl, uint32_t C,
-                                                          const uint32_t *__restrict__ cbase, int64_t L,
+                                                          const uint32_t *__restrict__ cbase, int64_t L, int tile,
                                                           uint32_t *__restrict__ item_cnt,
                                                           unsigned long long *work, DevAcc *acc) {
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
         const uint64_t n = cell_off[c + 1] - cell_off[c];
         const uint64_t ns = n - cell_nl[c];
         bool tiles_over;
-        const uint64_t items = cell_item_count(n, ns, &tiles_over);
+        const uint64_t items = tile == 16 ? cell_item_count<16>(n, ns, &tiles_over)
+                                          : cell_item_count<32>(n, ns, &tiles_over);
         if (items > 0x7fffffffull || tiles_over) atomicOr(&acc->grid_flags, GF_ITEMS_OVERFLOW);
         item_cnt[c] = (uint32_t)min(items, (uint64_t)0x7fffffffull);
         if (items > 0) {
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(256) k_batch_item_descs(const uint32_t *__rest
                                                           const uint32_t *__restrict__ cell_off,
                                                           const uint32_t *__restrict__ cell_nl, uint32_t C,
                                                           const uint32_t *__restrict__ cbase, int64_t L,
-                                                          const int32_t *__restrict__ kl, uint64_t cap,
+                                                          const int32_t *__restrict__ kl, int tile, uint64_t cap,
                                                           uint4 *__restrict__ desc, DevAcc *acc) {
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
         uint32_t q = item_off[c];
@@ -226,10 +227,12 @@ __global__ void __launch_bounds__(256) k_batch_item_descs(const uint32_t *__rest
         const int64_t l = find_segment_u32(cbase, L, c);
         const uint32_t base = cell_off[c], n = cell_off[c + 1] - base, ns = n - cell_nl[c];
         const uint4 hi = make_uint4(c - cbase[l], (uint32_t)kl[l], ns, 0u);
-        cell_item_words(n, ns, q, e, [&](uint32_t i, uint32_t word) {
+        auto emit = [&](uint32_t i, uint32_t word) {
             desc[2 * (uint64_t)i] = make_uint4(base, n, (uint32_t)l, word);
             desc[2 * (uint64_t)i + 1] = hi;
-        });
+        };
+        if (tile == 16) cell_item_words<16>(n, ns, q, e, emit);
+        else cell_item_words<32>(n, ns, q, e, emit);
     }
 }
 
@@ -293,35 +296,52 @@ __global__ void __launch_bounds__(256) k_batch_grid_fill(const SegRec *__restric
 }
 
 // a6 over all layouts: persistent; warp w takes the contiguous run of items
-// [w * chunk, (w + 1) * chunk) and writes one partial per item.  Does
-// nothing when the records or work items of this evaluation outgrew their
-// buffers (the scatter and the descriptors were not written; the host
-// re-plans on the overflow bit).
+// [w * chunk, (w + 1) * chunk), T = 32 one item at a time, T = 16 two at a
+// time (one per half-warp), and writes one partial per item.  Does nothing
+// when the records or work items of this evaluation outgrew their buffers
+// (the scatter and the descriptors were not written; the host re-plans on the
+// overflow bit).
+template <int T>
 __global__ void __launch_bounds__(BP_WARPS * 32, 4) k_batch_grid_pairs(const GridRec *__restrict__ rec,
                                                                        const uint4 *__restrict__ desc,
                                                                        const uint32_t *__restrict__ n_items_p,
                                                                        const DevAcc *__restrict__ acc, uint64_t rec_cap,
                                                                        uint64_t cap, uint32_t ideal,
                                                                        ItemPart *__restrict__ part) {
-    __shared__ GSeg cs[BP_WARPS][TILE];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int GROUPS = 32 / T;
+    __shared__ GSeg cs[BP_WARPS][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, grp = lane / T, loc = lane & (T - 1);
     if (acc->records > rec_cap || (uint64_t)*n_items_p > cap) return;
     const uint64_t n_items = *n_items_p;
     const uint64_t warps = (uint64_t)gridDim.x * BP_WARPS;
     const uint64_t chunk = (n_items + warps - 1) / warps;
     const uint64_t w = (uint64_t)blockIdx.x * BP_WARPS + wid;
     const uint64_t i0 = w * chunk, i1 = min(n_items, i0 + chunk);
-    for (uint64_t it = i0; it < i1; ++it) {
-        const uint4 d0 = desc[2 * it], d1 = desc[2 * it + 1];
-        const int k = (int)d1.y, G = 65536 >> k;
+    for (uint64_t it0 = i0; it0 < i1; it0 += GROUPS) {
+        const uint64_t it = it0 + grp;
+        const bool has = it < i1;
+        uint4 d0 = make_uint4(0, 0, 0, 0), d1 = make_uint4(0, 0, 0, 0);
+        if (has) {
+            d0 = desc[2 * it];
+            d1 = desc[2 * it + 1];
+        }
+        const int k = has ? (int)d1.y : 16, G = 65536 >> k;
         const int cell = (int)d1.x;
+        ItemTiles tl = has ? item_tiles<T>(d0.y, d1.z, d0.w) : ItemTiles{0, 0, 0, 0, false};
         PairCounts pc;
-        grid_item<false>(rec + d0.x, item_tiles(d0.y, d1.z, d0.w), (cell % G) << k, (cell / G) << k, k, cs[wid],
-                         ideal, pc, PerEdge{});
-        const uint32_t p = warp_sum<uint32_t>(pc.proper), t = warp_sum<uint32_t>(pc.touching);
-        const uint32_t c = warp_sum<uint32_t>(pc.collinear);
-        const uint64_t dv = warp_sum<uint64_t>(pc.dev);
-        if (lane == 0) {
+        grid_item<false, T>(rec + d0.x, tl, (cell % G) << k, (cell / G) << k, k, cs[wid] + grp * T, ideal, pc,
+                            PerEdge{});
+        // sums over this item's T lanes
+        uint32_t p = pc.proper, t = pc.touching, c = pc.collinear;
+        uint64_t dv = pc.dev;
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) {
+            p += __shfl_xor_sync(0xffffffffu, p, o);
+            t += __shfl_xor_sync(0xffffffffu, t, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            dv += __shfl_xor_sync(0xffffffffu, dv, o);
+        }
+        if (loc == 0 && has) {
             ItemPart ip;
             ip.proper = p; ip.touching = t; ip.collinear = c; ip.pad = 0; ip.dev = dv;
             part[it] = ip;
@@ -471,6 +491,7 @@ struct gr_batch {
     uint32_t *d_cbase = nullptr;
     uint32_t C = 0, C_cap = 0;
     int delta = 0;
+    int tile = 32;                  // segments per tile of the pair kernel's items (16 or 32)
     unsigned long long *d_nseg = nullptr, *d_l1 = nullptr, *d_work = nullptr;
     uint32_t *d_hn = nullptr;            // [16 L] segments by major-length class
     unsigned long long *d_hl1 = nullptr; // [16 L] their L1 length
@@ -652,11 +673,11 @@ void enqueue_cross_count(gr_batch *B, cudaStream_t s) {
                                                                      B->cell_nl, B->long_off);
     launch_scan_u32(B->cell_off, B->cell_off, B->C, b.scan_tmp, &b.acc->records, &b.acc->eval_status, s);
     k_batch_cell_items<<<grid_for(B->C, 256, 152 * 8), 256, 0, s>>>(B->cell_off, B->cell_nl, B->C, B->d_cbase, B->L,
-                                                                    B->item_off, B->d_work, b.acc);
+                                                                    B->tile, B->item_off, B->d_work, b.acc);
     launch_scan_u32(B->item_off, B->item_off, B->C, b.scan_tmp, &b.acc->grid_items, &b.acc->eval_status, s);
     k_batch_item_descs<<<grid_for(B->C, 256, 152 * 8), 256, 0, s>>>(B->item_off, B->cell_off, B->cell_nl, B->C,
-                                                                    B->d_cbase, B->L, B->d_k, B->items_cap, B->desc,
-                                                                    b.acc);
+                                                                    B->d_cbase, B->L, B->d_k, B->tile, B->items_cap,
+                                                                    B->desc, b.acc);
     launch_scan_u32(B->long_off, B->long_off, B->L, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
     k_batch_long_tiles<<<grid_for(B->L, 256, 152 * 8), 256, 0, s>>>(B->long_off, B->L, B->tile_off);
     launch_scan_u32(B->tile_off, B->tile_off, B->L, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
@@ -675,8 +696,12 @@ void enqueue_cross_pairs(gr_batch *B, uint32_t ideal_u, cudaStream_t s) {
                                                                     B->long_off,
                                                                     B->long_fill, B->seg_long, B->theta_long,
                                                                     &b.acc->eval_status);
-    k_batch_grid_pairs<<<152 * 4, BP_WARPS * 32, 0, s>>>(B->rec, B->desc, B->item_off + B->C, b.acc, B->rec_cap,
-                                                         B->items_cap, ideal_u, B->parts);
+    if (B->tile == 16)
+        k_batch_grid_pairs<16><<<152 * 4, BP_WARPS * 32, 0, s>>>(B->rec, B->desc, B->item_off + B->C, b.acc,
+                                                                 B->rec_cap, B->items_cap, ideal_u, B->parts);
+    else
+        k_batch_grid_pairs<32><<<152 * 4, BP_WARPS * 32, 0, s>>>(B->rec, B->desc, B->item_off + B->C, b.acc,
+                                                                 B->rec_cap, B->items_cap, ideal_u, B->parts);
     k_batch_long_pairs<<<152 * 8, AS_THREADS, 0, s>>>(B->seg_long, B->theta_long, B->long_off, B->tile_off, B->L,
                                                       b.acc, B->rec_cap, ideal_u, B->d_ll);
 }
@@ -829,61 +854,82 @@ std::string tune_key(const gr_batch *B) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     char buf[128];
-    snprintf(buf, sizeof buf, "batch_L%d_V%d_E%d_sm%d", lg(B->L), lg(B->V), lg(B->E), sms);
+    snprintf(buf, sizeof buf, "batch_tiled_L%d_V%d_E%d_sm%d", lg(B->L), lg(B->V), lg(B->E), sms);
     return buf;
 }
 
-bool tune_cache_lookup(const std::string &key, int *delta) {
+// Cache lines: "key offset tile" (a line without the tile means 32).
+bool tune_cache_lookup(const std::string &key, int *delta, int *tile) {
     const char *path = getenv("GR_TUNE_CACHE");
     if (!path || !*path) return false;
     FILE *f = fopen(path, "r");
     if (!f) return false;
-    char k[128];
-    int v;
+    char line[256], k[128];
     bool found = false;
-    while (fscanf(f, "%127s %d", k, &v) == 2)
-        if (key == k) { *delta = v; found = true; }
+    while (fgets(line, sizeof line, f)) {
+        int v = 0, t = 32;
+        const int got = sscanf(line, "%127s %d %d", k, &v, &t);
+        if (got >= 2 && key == k && (t == 16 || t == 32)) {
+            *delta = v;
+            *tile = t;
+            found = true;
+        }
+    }
     fclose(f);
     return found;
 }
 
-void tune_cache_store(const std::string &key, int delta) {
+void tune_cache_store(const std::string &key, int delta, int tile) {
     const char *path = getenv("GR_TUNE_CACHE");
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d\n", key.c_str(), delta);
+    fprintf(f, "%s %d %d\n", key.c_str(), delta, tile);
     fclose(f);
 }
 
-// Picks the global cell-size offset with the fastest crossing pipeline
-// among -1, 0, +1 (or takes it from the tune cache).
-gr_status autotune(gr_batch *B) {
-    const std::string key = tune_key(B);
-    int cached = 0;
-    if (tune_cache_lookup(key, &cached)) {
-        B->delta = cached;
-        plan_cells(B);
-        gr_status st = upload_cells(B);
-        return st != GR_OK ? st : size_cross_buffers(B, B->stream);
-    }
-    int best_delta = 0;
-    float best = 1e30f;
-    for (int delta : {0, -1, 1}) {
-        B->delta = delta;
-        plan_cells(B);
-        gr_status st = upload_cells(B);
-        if (st == GR_OK) st = size_cross_buffers(B, B->stream);
-        if (st != GR_OK) return st;
-        float ms = 0.f;
-        if ((st = time_crossings(B, &ms)) != GR_OK) return st;
-        if (ms < best) { best = ms; best_delta = delta; }
-    }
-    B->delta = best_delta;
+// A tile height fixed by the environment (GR_BATCH_TILE = 16 or 32), else 0.
+int fixed_tile() {
+    const char *v = getenv("GR_BATCH_TILE");
+    if (!v) return 0;
+    const int t = atoi(v);
+    return (t == 16 || t == 32) ? t : 0;
+}
+
+gr_status apply_plan(gr_batch *B, int delta, int tile) {
+    B->delta = delta;
+    B->tile = tile;
     plan_cells(B);
     gr_status st = upload_cells(B);
-    if (st == GR_OK) st = size_cross_buffers(B, B->stream);
-    if (st == GR_OK) tune_cache_store(key, best_delta);
+    return st != GR_OK ? st : size_cross_buffers(B, B->stream);
+}
+
+// Picks the global cell-size offset (-1, 0, +1) and the tile height of the
+// pair kernel's items (16 or 32 segments: two items per warp or one) with the
+// fastest crossing pipeline, or takes them from the tune cache.
+gr_status autotune(gr_batch *B) {
+    const std::string key = tune_key(B);
+    const int ft = fixed_tile();
+    int cached = 0, ctile = 32;
+    if (tune_cache_lookup(key, &cached, &ctile)) return apply_plan(B, cached, ft ? ft : ctile);
+    int best_delta = 0, best_tile = 32;
+    float best = 1e30f;
+    for (int tile : {32, 16}) {
+        if (ft && tile != ft) continue;
+        for (int delta : {0, -1, 1}) {
+            gr_status st = apply_plan(B, delta, tile);
+            if (st != GR_OK) return st;
+            float ms = 0.f;
+            if ((st = time_crossings(B, &ms)) != GR_OK) return st;
+            if (ms < best) {
+                best = ms;
+                best_delta = delta;
+                best_tile = tile;
+            }
+        }
+    }
+    gr_status st = apply_plan(B, best_delta, best_tile);
+    if (st == GR_OK && !ft) tune_cache_store(key, best_delta, best_tile);
     return st;
 }
 
@@ -1015,10 +1061,9 @@ gr_status gr_batch_create(gr_batch **out, int64_t n_layouts, const int64_t *v_of
     B_CU2(cudaStreamSynchronize(B->stream));
     B_TRY(status_error(B->h_acc->status));
     if (B->opt.cell_log2 != 0) {
-        B->delta = B->opt.cell_log2 < 0 ? B->opt.cell_log2 : 0;  // negative values: a fixed offset
-        plan_cells(B);
-        B_TRY(upload_cells(B));
-        B_TRY(size_cross_buffers(B, B->stream));
+        // negative values: a fixed offset (the tile height from GR_BATCH_TILE, else 32)
+        const int ft = fixed_tile();
+        B_TRY(apply_plan(B, B->opt.cell_log2 < 0 ? B->opt.cell_log2 : 0, ft ? ft : 32));
     } else {
         B_TRY(autotune(B));
     }
@@ -1152,6 +1197,14 @@ gr_status gr_batch_evaluate(gr_batch *B, uint32_t metrics, const gr_params *para
     const cudaMemcpyKind k = is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     B_CU(cudaMemcpyAsync(out, B->d_res, sizeof(gr_result) * B->L, k, c));
     B_CU(cudaStreamSynchronize(c));
+    return GR_OK;
+}
+
+gr_status gr_batch_tuning(const gr_batch *B, int32_t *cell_offset, int32_t *tile) {
+    set_last_error("");
+    if (!B || !cell_offset || !tile) return bfail(GR_EINVAL, "NULL argument");
+    *cell_offset = B->delta;
+    *tile = B->tile;
     return GR_OK;
 }
 

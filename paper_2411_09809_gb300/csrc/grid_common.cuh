@@ -266,20 +266,23 @@ struct ItemTiles {
     bool diag;
 };
 
+// T: segments per tile, 32 (one warp per item) or 16 (two items per warp,
+// one per half-warp; fewer idle lanes in cells of few records).
+template <int T = TILE>
 __device__ __forceinline__ ItemTiles item_tiles(uint32_t n, uint32_t ns, uint32_t w) {
     const int a = (int)((w >> 16) & 0x7fffu), b = (int)(w & 0xffffu);
     ItemTiles t;
     if (w >> 31) {
-        t.row0 = (int)ns + a * TILE;
-        t.mr = min(TILE, (int)n - t.row0);
-        t.col0 = b * TILE;
-        t.mc = min(TILE, (int)ns - t.col0);
+        t.row0 = (int)ns + a * T;
+        t.mr = min(T, (int)n - t.row0);
+        t.col0 = b * T;
+        t.mc = min(T, (int)ns - t.col0);
         t.diag = false;
     } else {
-        t.row0 = a * TILE;
-        t.mr = min(TILE, (int)ns - t.row0);
-        t.col0 = b * TILE;
-        t.mc = min(TILE, (int)ns - t.col0);
+        t.row0 = a * T;
+        t.mr = min(T, (int)ns - t.row0);
+        t.col0 = b * T;
+        t.mc = min(T, (int)ns - t.col0);
         t.diag = a == b;
     }
     return t;
@@ -288,17 +291,18 @@ __device__ __forceinline__ ItemTiles item_tiles(uint32_t n, uint32_t ns, uint32_
 constexpr uint32_t kMaxCellTiles = 1u << 15;
 
 // Work items of a cell with n records, ns of them short (see ItemTiles).
+template <int T = TILE>
 __device__ __forceinline__ uint64_t cell_item_count(uint64_t n, uint64_t ns, bool *overflow) {
-    const uint64_t nl = n - ns, Ts = (ns + TILE - 1) / TILE, Tl = (nl + TILE - 1) / TILE;
+    const uint64_t nl = n - ns, Ts = (ns + T - 1) / T, Tl = (nl + T - 1) / T;
     *overflow = Ts >= kMaxCellTiles || Tl >= kMaxCellTiles;
     return (ns >= 2 ? Ts * (Ts + 1) / 2 : 0) + (ns >= 1 ? Tl * Ts : 0);
 }
 
 // Writes the descriptors' tile words of a cell's items, in the order
 // counted by cell_item_count, via emit(q, word) for q in [q0, q_end).
-template <class F>
+template <int T = TILE, class F>
 __device__ __forceinline__ void cell_item_words(uint32_t n, uint32_t ns, uint32_t q, uint32_t q_end, F &&emit) {
-    const uint32_t nl = n - ns, Ts = (ns + TILE - 1) / TILE, Tl = (nl + TILE - 1) / TILE;
+    const uint32_t nl = n - ns, Ts = (ns + T - 1) / T, Tl = (nl + T - 1) / T;
     if (ns >= 2)
         for (uint32_t ti = 0; ti < Ts && q < q_end; ++ti)
             for (uint32_t tj = ti; tj < Ts && q < q_end; ++tj, ++q) emit(q, (ti << 16) | tj);
@@ -322,10 +326,10 @@ __device__ __forceinline__ void cell_item_words(uint32_t n, uint32_t ns, uint32_
 // intersection point, a collinear overlap only if this cell owns the
 // lexicographically smallest point of the overlap.  Every lane of the warp
 // must call it.
-template <bool PER_EDGE>
+template <bool PER_EDGE, int T = TILE>
 __device__ __forceinline__ void grid_item(const GridRec *__restrict__ cell_rec, const ItemTiles t, int x0, int y0,
                                           int k, GSeg *cs, uint32_t ideal, PairCounts &pc, PerEdge pe) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & (T - 1);  // the lane within this item's T lanes
     const int w = 1 << k;
     const int mr = t.mr, mc = t.mc;
 

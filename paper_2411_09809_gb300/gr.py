@@ -124,6 +124,7 @@ def load() -> ctypes.CDLL:
         "gr_profile_read": ([P, ctypes.POINTER(gr_profile), c_int32], c_int32),
         "gr_kernel_launches": ([], c_int64),
         "gr_io_bytes": ([P, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64)], c_int32),
+        "gr_batch_tuning": ([P, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)], c_int32),
         "gr_evaluate_part": ([P, c_uint32, ctypes.POINTER(gr_params), c_int32, c_int32,
                               ctypes.POINTER(gr_partial)], c_int32),
         "gr_combine_parts": ([ctypes.POINTER(gr_partial), ctypes.POINTER(gr_params),
@@ -276,6 +277,13 @@ def gr_evaluate_part(layout, part: int, n_parts: int, metrics: int = GR_METRIC_A
     p = gr_params(float(ideal_rad), int(occlusion_d))
     _check(load().gr_evaluate_part(layout, metrics, ctypes.byref(p), int(part), int(n_parts), ctypes.byref(out)))
     return out
+
+
+def gr_batch_tuning(batch) -> tuple[int, int]:
+    """(cell-size offset, tile height) that gr_batch_create settled on."""
+    off, tile = c_int32(), c_int32()
+    _check(load().gr_batch_tuning(batch, ctypes.byref(off), ctypes.byref(tile)))
+    return off.value, tile.value
 
 
 def gr_combine_parts(total: gr_partial, ideal_rad: float = 0.0, occlusion_d: int = 0) -> gr_result:

@@ -159,3 +159,38 @@ def test_batched_workload_full_size():
     order = np.argsort(v_off[1:] - v_off[:-1])
     for i in list(order[::256][:14]):
         check_layout(res[i], layouts[i], 256, f"layout {i}")
+
+
+@pytest.mark.parametrize("long_pairs", [1, 2])
+def test_batch_tile_heights_agree(long_pairs, monkeypatch):
+    # the pair kernel's items with 16-segment tiles (two items per warp) and
+    # with 32-segment tiles give the same tallies, layout by layout, and both
+    # match the oracle; the autotuner's cache keeps the tile height it chose
+    layouts = mixed_layouts(seed=21, n=60)
+    v_off, e_off, xy, edges = synth.pack_layouts(layouts)
+    res = {}
+    for tile in ("16", "32"):  # the same cell sizes (a fixed offset), so the same results bit for bit
+        monkeypatch.setenv("GR_BATCH_TILE", tile)
+        with gr.Batch(v_off, e_off, xy, edges, gr.gr_options(0, -1, 0, 0, long_pairs)) as B:
+            res[tile] = [bytes(memoryview(r)) for r in B.evaluate(gr.GR_METRIC_ALL, IDEAL, 160)]
+    assert res["16"] == res["32"]
+    monkeypatch.delenv("GR_BATCH_TILE")
+    with gr.Batch(v_off, e_off, xy, edges, gr.gr_options(0, 0, 0, 0, long_pairs)) as B:  # autotuned
+        got = B.evaluate(gr.GR_METRIC_ALL, IDEAL, 160)
+    for i, L in enumerate(layouts):
+        check_layout(got[i], L, 160, f"layout {i}")
+
+
+def test_autotuner_caches_offset_and_tile(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("GR_TUNE_CACHE", str(cache))
+    monkeypatch.delenv("GR_BATCH_TILE", raising=False)
+    layouts = mixed_layouts(seed=22, n=30)
+    v_off, e_off, xy, edges = synth.pack_layouts(layouts)
+    with gr.Batch(v_off, e_off, xy, edges) as B:
+        first = [bytes(memoryview(r)) for r in B.evaluate(gr.GR_METRIC_ALL, IDEAL, 200)]
+    key, delta, tile = cache.read_text().split()
+    assert key.startswith("batch_tiled_") and int(delta) in (-1, 0, 1) and int(tile) in (16, 32)
+    with gr.Batch(v_off, e_off, xy, edges) as B:  # from the cache: the same plan, the same results
+        assert [bytes(memoryview(r)) for r in B.evaluate(gr.GR_METRIC_ALL, IDEAL, 200)] == first
+    assert len(cache.read_text().splitlines()) == 1
