@@ -924,7 +924,6 @@ def run_strips(args, rank, world, local_rank):
                    "step": "gr_layout_update + gr_strip_crossings (E_c and E_ca estimates, Sec. 3.2.2-3.2.3)",
                    "inputs": "seeded synthetic (paper_2411_09809_gb300.synth)",
                    "l2": "256 MiB write between timed steps",
-                   "autotuned": {"cell_offset": tuned_offset, "tile": tuned_tile},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "results": {"E_c_estimate": res.crossings, "E_c_exact": exact.c.crossings,
                     "E_c_error": 1.0 - res.crossings / max(1, exact.c.crossings),
@@ -940,7 +939,7 @@ def run_strips(args, rank, world, local_rank):
                      "work": f"{OPS_PER_MERGE_STEP} ops per binary-search step of each merge level and record, "
                              f"{OPS_PER_STRIP_PAIR} per counted pair",
                      "traffic": None, "launch_ms": cnt_ms, "pipe_peaks_tops": measured_pipes()},
-        "e2e": {"value": copies * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": (io1[0] - io0[0]) // max(1, len(e2e_s)),
                 "d2h_bytes_per_step": (io1[1] - io0[1]) // max(1, len(e2e_s))},
         "gpu_launches": launches,
@@ -1060,7 +1059,7 @@ def run_per_edge(args, rank, world, local_rank):
         "results": {"sum_proper": tot[0] // 2, "sum_touching": tot[1] // 2, "E_c": res.crossing.c.crossings},
         "phase_ms": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]},
         "roofline": rf,
-        "e2e": {"value": copies * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": L.V * 8, "d2h_bytes_per_step": E * 32},
         "gpu_launches": launches,
         "clocks": clk,

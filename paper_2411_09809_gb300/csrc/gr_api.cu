@@ -325,7 +325,7 @@ gr_status ensure_records(gr_layout *L, uint64_t R, uint64_t items) {
         g.rec_cap = 0;
         const uint64_t cap = R + R / 4 + 1024;
         if ((st = dalloc(&g.rec, (size_t)cap)) != GR_OK) return st;
-        if ((st = dalloc(&g.rgeo, 3 * (size_t)cap)) != GR_OK) return st;
+        if ((st = dalloc(&g.rgeo, 4 * (size_t)cap)) != GR_OK) return st;
         g.rec_cap = cap;
     }
     if (g.items_cap < items || !g.item_desc) {

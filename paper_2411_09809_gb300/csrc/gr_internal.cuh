@@ -111,7 +111,7 @@ struct GridBuffers {
     uint32_t *item_off = nullptr;  // [C + 1] work items per cell, then offsets
     unsigned long long *cell_fill = nullptr; // [C] short (low 32 bits) and long (high) records placed
     GridRec *rec = nullptr;        // [rec_cap] records sorted by cell: short ones first, then long ones
-    float4 *rgeo = nullptr;        // [3 rec_cap] the records' FP32 cell-relative form (rotation kernel, make_rgeo)
+    float4 *rgeo = nullptr;        // [4 rec_cap] the records' FP32 (make_rgeo) and FP16 (make_hgeo) forms
     uint64_t rec_cap = 0;
     uint4 *item_desc = nullptr;    // [2 items_cap] {record offset, records, short records, ti << 16 | tj}, {cell}
     uint64_t items_cap = 0;

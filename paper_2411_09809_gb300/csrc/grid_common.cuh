@@ -4,6 +4,8 @@
 // tests with the owner-cell rules.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "gr_internal.cuh"
 #include "pair_math.cuh"
 
@@ -571,6 +573,45 @@ __device__ __forceinline__ void make_rgeo(SegRec s, int x0, int y0, int w, float
     c = make_float4(fmaf(t0, fux, fax), fmaf(t0, fuy, fay), fmaf(t1, fux, fax), fmaf(t1, fuy, fay));
 }
 
+// The FP16 form of a record for the rotation kernel's first test, in cell
+// units centred on the cell (the cell is [-1/2, 1/2]^2): the signed distance
+// to its line
+//   f(p) = hx p_y + hy p_x + hc,  hx = u_x / |u|, hy = -u_y / |u|,
+//   hc = nk / (|u| w) + (hx + hy) / 2,
+// and its clipped part E0, E1 as E / w - 1/2, as eight halves
+// {hx, hy, hc, E0x, E0y, E1x, E1y, 0} (two per word, the first in the low
+// half).  The line meets the closed cell, so |hc| <= sqrt(2) / 2 (the
+// distance from the centre).  Error of f at the true clipped part, evaluated
+// as two fused FP16 multiply-adds fma(hx, E_y, fma(hy, E_x, hc)) (round to
+// nearest; |inner| <= 1.25 and |f| <= 1.75, so each rounding is <= 2^-11):
+//   coefficients rounded to FP16 (|hx|, |hy| <= 1 against |p| <= 1/2,
+//   |hc| < 1; FP32 errors below 2^-20)                          <= 2^-12 + 2^-12 + 2^-20;
+//   clip points: FP32 error 2^-6 / w plus FP16 rounding 2^-13, times
+//   |hx| + |hy| <= sqrt(2)                                      <= sqrt(2) (2^-13 + 2^-6 / w);
+//   the two roundings of the multiply-adds                      <= 2 2^-11;
+// in all below 0.00165 + 0.0221 / w, under half_margin(w) = 2^-9 + 2^-4 / w.
+// A zero-length line or a border record (NaN clip points) gets NaN halves,
+// which leave every pair with it to the FP32 test.
+__host__ __device__ __forceinline__ float half_margin(int w) { return 0.001953125f + 0.0625f / (float)w; }
+
+__device__ __forceinline__ uint32_t pack_halves(float lo, float hi) {
+    return (uint32_t)__half_as_ushort(__float2half_rn(lo)) | ((uint32_t)__half_as_ushort(__float2half_rn(hi)) << 16);
+}
+
+__device__ __forceinline__ uint4 make_hgeo(const float4 &b, const float4 &c, int w) {
+    const float inv_w = 1.f / (float)w;  // exact: w is a power of two
+    const float len = sqrtf(b.x * b.x + b.y * b.y);
+    const float hx = b.x / len, hy = -b.y / len;
+    const float hc = b.z * inv_w / len + 0.5f * (hx + hy);
+    if (!(len > 0.f) || !(fabsf(hc) <= 0.75f)) {
+        const uint32_t nan2 = 0x7e007e00u;
+        return make_uint4(nan2, nan2, nan2, nan2);
+    }
+    return make_uint4(pack_halves(hx, hy), pack_halves(hc, fmaf(c.x, inv_w, -0.5f)),
+                      pack_halves(fmaf(c.y, inv_w, -0.5f), fmaf(c.z, inv_w, -0.5f)),
+                      pack_halves(fmaf(c.w, inv_w, -0.5f), 0.f));
+}
+
 // The clip test of a pair: the row's clipped part against the column's line
 // (s0, s1) and the column's clipped part against the row's line (s2, s3).
 // The error of s0, s1 is the column line's FP32 error at the row's clip
@@ -585,8 +626,10 @@ __device__ __forceinline__ void make_rgeo(SegRec s, int x0, int y0, int w, float
 // strictly straddles the column's line, so an intersection point on the row's
 // segment lies strictly inside it, hence in the open cell (the open part of
 // a segment that does not run along the border lies in the cell's interior).
+// both: each part strictly straddles the other's line, so the parts meet in
+// one point inside both: a proper crossing of the segments, in the open cell.
 struct ClipTest {
-    bool out, in;
+    bool out, in, both;
 };
 
 __device__ __forceinline__ ClipTest clip_test(const float4 &rb, const float4 &rc, float r_pts, const float4 &cb,
@@ -600,6 +643,7 @@ __device__ __forceinline__ ClipTest clip_test(const float4 &rb, const float4 &rc
     ClipTest t;
     t.out = (lo01 > M01) | (hi01 < -M01) | (lo23 > M23) | (hi23 < -M23);
     t.in = (lo01 < -M01) & (hi01 > M01);
+    t.both = t.in & (lo23 < -M23) & (hi23 > M23);
     return t;
 }
 

@@ -434,9 +434,10 @@ __global__ void __launch_bounds__(GP_WARPS * 32, 4) k_grid_pairs(const GridRec *
     flush_counts(pc, acc, shu);
 }
 
-// The FP32 cell-relative form of every record (make_rgeo) for the rotation
-// kernel, in record order: coalesced reads of the records (their cell id in
-// .x.z) and coalesced writes of the three geometry arrays.
+// The FP32 cell-relative form of every record (make_rgeo) and its FP16 form
+// (make_hgeo) for the rotation kernel, in record order: coalesced reads of
+// the records (their cell id in .x.z) and coalesced writes of the four
+// geometry arrays.
 __global__ void __launch_bounds__(256) k_rec_geo(const GridRec *__restrict__ rec, const DevAcc *__restrict__ acc,
                                                  uint64_t cap, int k, float4 *__restrict__ geo) {
     const uint64_t R = acc->records;
@@ -450,24 +451,31 @@ __global__ void __launch_bounds__(256) k_rec_geo(const GridRec *__restrict__ rec
         geo[p] = a;
         geo[cap + p] = b;
         geo[2 * cap + p] = c;
+        reinterpret_cast<uint4 *>(geo + 3 * cap)[p] = make_hgeo(b, c, 1 << k);
     }
 }
 
 // a6, rotation form -- one warp per rotation work item (rot_item_count):
-// each lane keeps one row record of the cell in registers; the item's column
-// window (RWIN records) is staged in shared memory, so lane l meets slot
-// l + t at the item's t-th offset.  Records are read as FP32 cell-relative
-// geometry (geo_a = {ax, ay, bx, by}, geo_b = {ux, uy, nk, v}, geo_c = the
-// clipped part; three arrays of rec_cap float4, see make_rgeo).  A pair is
-// queued unless the clip test shows it cannot count in this cell; the queued
-// pairs are settled 32 at a time by the whole warp (settle_pair) after each
-// item, so the rare cases never run with idle lanes.
-constexpr int CP_WARPS = 8;                    // warps per block
-constexpr int CP_QUEUE = 32 * RQ_HALF + 32;    // queued pairs per warp: up to 31 left + 32 per offset
+// each lane keeps one row record of the cell in registers and meets the
+// item's column window, staged in shared memory, at slots l + t.  The first
+// test runs in FP16 (make_hgeo) on two offsets at once: window slot u holds
+// the halves of its record and of the next one interleaved, so one half2
+// operation tests the pairs of offsets t and t + 1.  With the margin above
+// the FP16 error (half_margin), a pair is dropped when one clipped part lies
+// beyond it on one side of the other's line, and counted at once as a proper
+// crossing of this cell when each part straddles the other's line by more
+// than it (only the edges' directions are then read, for the crossing
+// angle's term).  Of the undecided pairs, those that share a vertex are
+// dropped and the rest queued, to be settled 32 at a time by the whole warp
+// (settle_pair, on the FP32 records), so the rare cases never run with idle
+// lanes.
+constexpr int CP_WARPS = 8;   // warps per block
+constexpr int CP_QUEUE = 64;  // queued pairs per warp: up to 31 left + 32 pushed in one round
 
-// Settles one queued pair (row | clip-in flag << 31, col) of a cell of side w:
-// shared vertex ids skip it; the FP32 orientations decide it when they are
-// exact or clear of the filter, else the exact int64 test does; a pair in E_c
+// Settles one queued pair (row, col) of a cell of side w: shared vertex ids
+// skip it; the FP32 clip test drops it, or counts it as a proper crossing of
+// this cell; else the FP32 orientations decide it when they are exact or
+// clear of the filter, or the exact int64 test does, and a pair in E_c
 // counts if its intersection point lies in this cell (decided by the clip
 // test, else by the exact test), a collinear overlap if this cell holds the
 // smallest point of the overlap.
@@ -475,36 +483,41 @@ template <bool PER_EDGE>
 __device__ __forceinline__ void settle_pair(const float4 *__restrict__ geo, uint64_t cap,
                                             const GridRec *__restrict__ rec, uint2 e, int w, uint32_t ideal,
                                             PairCounts &pc, PerEdge pe) {
-    const uint32_t row = e.x & 0x7fffffffu, col = e.y;
-    const bool clip_in = (e.x >> 31) != 0;
+    const uint32_t row = e.x, col = e.y;
     const uint2 rid = *(const uint2 *)&rec[row].s.z, cid = *(const uint2 *)&rec[col].s.z;
     if ((rid.x == cid.x) | (rid.x == cid.y) | (rid.y == cid.x) | (rid.y == cid.y)) return;
-    const float4 ra = geo[row], rb = geo[cap + row], ca = geo[col], cb = geo[cap + col];
-    const Orient4 o = orient4(ra, rb, ca, cb);
-    const float F = fmaxf(rb.w, cb.w) > kClipExact ? kRotFilter : 0.f;  // a filtered record takes part
-    const float mn = fminf(fminf(fabsf(o.o1), fabsf(o.o2)), fminf(fabsf(o.o3), fabsf(o.o4)));
-    int kind;
-    if ((F == 0.f || mn > F) && !(o.o1 == 0.f && o.o2 == 0.f)) {
-        const float p12 = o.o1 * o.o2, p34 = o.o3 * o.o4;
-        kind = (p12 <= 0.f && p34 <= 0.f) ? ((p12 < 0.f && p34 < 0.f) ? PAIR_PROPER : PAIR_TOUCHING) : PAIR_NONE;
-    } else {
-        kind = classify_rel(ra, ca, rid.x, rid.y, cid.x, cid.y);
-    }
-    if (kind == PAIR_NONE) return;
-    if (kind == PAIR_COLLINEAR) {
-        if (!owns_collinear_rel(ra, ca, w)) return;
-        ++pc.collinear;
-        if (PER_EDGE) {
-            atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)rec[row].x.x + 2], 1ull);
-            atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)rec[col].x.x + 2], 1ull);
+    const float4 rb = geo[cap + row], cb = geo[cap + col];
+    const ClipTest ct = clip_test(rb, geo[2 * cap + row], fminf(rb.w, kClipExact), cb, geo[2 * cap + col]);
+    if (ct.out) return;
+    int kind = PAIR_PROPER;
+    if (!ct.both) {
+        const float4 ra = geo[row], ca = geo[col];
+        const Orient4 o = orient4(ra, rb, ca, cb);
+        const float F = fmaxf(rb.w, cb.w) > kClipExact ? kRotFilter : 0.f;  // a filtered record takes part
+        const float mn = fminf(fminf(fabsf(o.o1), fabsf(o.o2)), fminf(fabsf(o.o3), fabsf(o.o4)));
+        if ((F == 0.f || mn > F) && !(o.o1 == 0.f && o.o2 == 0.f)) {
+            const float p12 = o.o1 * o.o2, p34 = o.o3 * o.o4;
+            kind = (p12 <= 0.f && p34 <= 0.f) ? ((p12 < 0.f && p34 < 0.f) ? PAIR_PROPER : PAIR_TOUCHING)
+                                              : PAIR_NONE;
+        } else {
+            kind = classify_rel(ra, ca, rid.x, rid.y, cid.x, cid.y);
         }
-        return;
-    }
-    if (!clip_in) {
-        const int iax = (int)ra.x, iay = (int)ra.y, icx = (int)ca.x, icy = (int)ca.y;
-        if (!owns_crossing(iax, iay, (int)ra.z - iax, (int)ra.w - iay, icx, icy, (int)ca.z - icx, (int)ca.w - icy,
-                           w))
+        if (kind == PAIR_NONE) return;
+        if (kind == PAIR_COLLINEAR) {
+            if (!owns_collinear_rel(ra, ca, w)) return;
+            ++pc.collinear;
+            if (PER_EDGE) {
+                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)rec[row].x.x + 2], 1ull);
+                atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)rec[col].x.x + 2], 1ull);
+            }
             return;
+        }
+        if (!ct.in) {
+            const int iax = (int)ra.x, iay = (int)ra.y, icx = (int)ca.x, icy = (int)ca.y;
+            if (!owns_crossing(iax, iay, (int)ra.z - iax, (int)ra.w - iay, icx, icy, (int)ca.z - icx,
+                               (int)ca.w - icy, w))
+                return;
+        }
     }
     const uint2 rx = *(const uint2 *)&rec[row].x, cx = *(const uint2 *)&rec[col].x;  // edge id, direction
     const uint32_t qd = dev_term(rx.y, cx.y, ideal);
@@ -536,30 +549,50 @@ __device__ __forceinline__ void settle_queue(const float4 *__restrict__ geo, uin
     __syncwarp();
 }
 
+__device__ __forceinline__ __half2 as_half2(uint32_t u) {
+    __half2 h;
+    memcpy(&h, &u, sizeof(h));
+    return h;
+}
+
+// x mod n for the window's rows (x below 2 n but for the smallest cells).
+__device__ __forceinline__ uint32_t wrap_row(uint32_t x, uint32_t n) {
+    if (x >= n) x -= n;
+    return x < n ? x : x % n;
+}
+
+// The offset of bit b of a lane's masks: bit j holds offset 2 j, bit 16 + j
+// offset 2 j + 1 (the low and high halves of the j-th half2 test).
+__device__ __forceinline__ int mask_offset(int b) { return b < 16 ? 2 * b : 2 * (b - 16) + 1; }
+
 template <bool PER_EDGE>
 __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *__restrict__ geo,
                                                                  const GridRec *__restrict__ rec,
                                                                  const uint4 *__restrict__ descs,
                                                                  const uint32_t *__restrict__ n_items_p,
                                                                  uint64_t rec_cap, uint64_t items_cap, int k,
-                                                                 DevAcc *acc, uint32_t ideal, PerEdge pe) {
-    __shared__ float4 win_b[CP_WARPS][RWIN], win_c[CP_WARPS][RWIN];
-    __shared__ uint32_t win_i[CP_WARPS][RWIN];
+                                                                 float margin, DevAcc *acc, uint32_t ideal,
+                                                                 PerEdge pe) {
+    __shared__ uint4 win_h[CP_WARPS][2][RWIN];  // slot u: halves of records u and u + 1, interleaved
+    __shared__ uint32_t win_i[CP_WARPS][RWIN];  // slot u's record
+    __shared__ uint2 win_x[CP_WARPS][RWIN];     // its edge id and direction
+    __shared__ uint2 win_v[CP_WARPS][RWIN];     // its vertex ids
     __shared__ uint2 qbuf[CP_WARPS][CP_QUEUE];
     __shared__ uint64_t shu[32];
+    __shared__ uint32_t part_sh[2];
     const uint32_t n_items = *n_items_p;
     if (acc->records > rec_cap || n_items > items_cap) return;  // overflow raised by the scatter or descriptors
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int w = 1 << k;
     const unsigned lt = lanemask_lt();
-    const float4 *__restrict__ geo_b = geo + rec_cap;
-    const float4 *__restrict__ geo_c = geo + 2 * rec_cap;
-    float4 *wb = win_b[wid], *wc = win_c[wid];
+    const uint4 *__restrict__ geo_h = reinterpret_cast<const uint4 *>(geo + 3 * rec_cap);
+    uint4 *wh0 = win_h[wid][0], *wh1 = win_h[wid][1];
     uint32_t *wi = win_i[wid];
+    uint2 *wx = win_x[wid], *wv = win_v[wid];
     uint2 *q = qbuf[wid];
+    const __half2 hm = __half2half2(__float2half_ru(margin)), nhm = __hneg2(hm);
     int qn = 0;
     PairCounts pc;
-    __shared__ uint32_t part_sh[2];
     uint32_t lo, i_end;  // this evaluation's share of the items
     part_items(acc, descs, n_items, part_sh, lo, i_end);
     const uint32_t stride = gridDim.x * CP_WARPS;
@@ -575,30 +608,87 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
         const int span = rl.m + RQ - 1, slots = rl.s * span;
         __syncwarp();
         for (int u = lane; u < slots; u += 32) {
-            const int sig = u / span;
-            const uint32_t r = base + (rl.first + (uint32_t)(sig * RQ + (u - sig * span))) % n;
-            wb[u] = geo_b[r];
-            wc[u] = geo_c[r];
-            wi[u] = r;
+            const int sig = rl.s == 1 ? 0 : u / span;
+            const uint32_t x = rl.first + (uint32_t)(sig * RQ + (u - sig * span));
+            const uint32_t r0 = base + wrap_row(x, n), r1 = base + wrap_row(x + 1, n);
+            const uint4 A = geo_h[r0], B = geo_h[r1];
+            wh0[u] = make_uint4(__byte_perm(A.x, B.x, 0x5410), __byte_perm(A.x, B.x, 0x7632),
+                                __byte_perm(A.y, B.y, 0x5410), __byte_perm(A.y, B.y, 0x7632));
+            wh1[u] = make_uint4(__byte_perm(A.z, B.z, 0x5410), __byte_perm(A.z, B.z, 0x7632),
+                                __byte_perm(A.w, B.w, 0x5410), 0u);
+            wi[u] = r0;
+            wx[u] = *(const uint2 *)&rec[r0].x;
+            wv[u] = *(const uint2 *)&rec[r0].s.z;
         }
         const uint32_t row = base + (uint32_t)rl.i;
-        const float4 rb = geo_b[row], rc = geo_c[row];
-        const float r_pts = fminf(rb.w, kClipExact);
-        const uint32_t rowq = row;
+        const uint4 R = geo_h[row];
+        const __half2 rhx = as_half2(__byte_perm(R.x, R.x, 0x1010)), rhy = as_half2(__byte_perm(R.x, R.x, 0x3232));
+        const __half2 rhc = as_half2(__byte_perm(R.y, R.y, 0x1010)), r0x = as_half2(__byte_perm(R.y, R.y, 0x3232));
+        const __half2 r0y = as_half2(__byte_perm(R.z, R.z, 0x1010)), r1x = as_half2(__byte_perm(R.z, R.z, 0x3232));
+        const __half2 r1y = as_half2(__byte_perm(R.w, R.w, 0x1010));
+        const uint2 rx = *(const uint2 *)&rec[row].x, rv = *(const uint2 *)&rec[row].s.z;
         __syncwarp();
-        for (int h = 0; h < RQ; h += RQ_HALF) {
+        const int jn = (int)((__reduce_max_sync(0xffffffffu, (unsigned)rl.cnt) + 1u) >> 1);  // half2 steps
+        uint32_t mo = 0, ms = 0;  // dropped, counted
 #pragma unroll
-            for (int tt = 0; tt < RQ_HALF; ++tt) {
-                const int t = h + tt, u = rl.slot + t;
-                const ClipTest ct = clip_test(rb, rc, r_pts, wb[u], wc[u]);
-                const bool keep = t < rl.cnt && !ct.out;
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
-                if (m) {
-                    if (keep) q[qn + __popc(m & lt)] = make_uint2(rowq | (ct.in ? 0x80000000u : 0u), wi[u]);
-                    qn += __popc(m);
+        for (int j = 0; j < RQ / 2; ++j) {
+            if (j >= jn) break;
+            const int u = rl.slot + 2 * j;
+            const uint4 c0 = wh0[u], c1 = wh1[u];
+            const __half2 chx = as_half2(c0.x), chy = as_half2(c0.y), chc = as_half2(c0.z);
+            const __half2 c0x = as_half2(c0.w), c0y = as_half2(c1.x), c1x = as_half2(c1.y), c1y = as_half2(c1.z);
+            // the column's line at the row's clipped part, the row's line at the column's
+            const __half2 s0 = __hfma2(chx, r0y, __hfma2(chy, r0x, chc));
+            const __half2 s1 = __hfma2(chx, r1y, __hfma2(chy, r1x, chc));
+            const __half2 s2 = __hfma2(rhx, c0y, __hfma2(rhy, c0x, rhc));
+            const __half2 s3 = __hfma2(rhx, c1y, __hfma2(rhy, c1x, rhc));
+            // t > 0: both values on one side, by t; t < 0: a strict straddle, by -t
+            const __half2 t01 = __hmax2(__hmin2(s0, s1), __hneg2(__hmax2(s0, s1)));
+            const __half2 t23 = __hmax2(__hmin2(s2, s3), __hneg2(__hmax2(s2, s3)));
+            const __half2 tt = __hmax2_nan(t01, t23);  // NaN (a border record): undecided
+            const uint32_t bit = 0x10001u << j;
+            mo |= __hgt2_mask(tt, hm) & bit;
+            ms |= __hlt2_mask(tt, nhm) & bit;
+        }
+        const int ce = (rl.cnt + 1) >> 1, co = rl.cnt >> 1;  // the lane's even and odd offsets
+        const uint32_t valid = ((1u << ce) - 1u) | (((1u << co) - 1u) << 16);
+        ms &= valid;
+        uint32_t mk = ~(mo | ms) & valid;
+        // one pair of each kind per lane a round: a counted pair adds the
+        // crossing angle's term; an undecided one is dropped if it shares a
+        // vertex, else queued
+        const int n_counted = __popc(ms);
+        pc.proper += n_counted;
+        uint64_t rdev = 0;
+        while (__any_sync(0xffffffffu, (ms | mk) != 0)) {
+            if (ms) {
+                const uint2 cx = wx[rl.slot + mask_offset(__ffs(ms) - 1)];
+                ms &= ms - 1;
+                const uint32_t qd = dev_term(rx.y, cx.y, ideal);
+                pc.dev += qd;
+                if (PER_EDGE) {
+                    rdev += qd;
+                    atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)cx.x], 1ull);
+                    atomicAdd((unsigned long long *)&pe.dev[(int32_t)cx.x], (unsigned long long)qd);
                 }
             }
+            bool push = false;
+            uint2 e = make_uint2(0u, 0u);
+            if (mk) {
+                const int u = rl.slot + mask_offset(__ffs(mk) - 1);
+                mk &= mk - 1;
+                const uint2 cv = wv[u];
+                push = !((rv.x == cv.x) | (rv.x == cv.y) | (rv.y == cv.x) | (rv.y == cv.y));
+                e = make_uint2(row, wi[u]);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, push);
+            if (push) q[qn + __popc(m & lt)] = e;
+            qn += __popc(m);
             settle_queue<PER_EDGE>(geo, rec_cap, rec, q, qn, lane, w, ideal, pc, pe);
+        }
+        if (PER_EDGE && n_counted) {
+            atomicAdd((unsigned long long *)&pe.counts[3 * (int64_t)(int32_t)rx.x], (unsigned long long)n_counted);
+            atomicAdd((unsigned long long *)&pe.dev[(int32_t)rx.x], (unsigned long long)rdev);
         }
     }
     __syncwarp();
@@ -660,10 +750,12 @@ void launch_grid_pairs(const Buffers &b, const GridBuffers &g, int k, bool split
         count_launches(1);
         if (pe.counts)
             k_cell_pairs<true><<<blocks, CP_WARPS * 32, 0, s>>>(g.rgeo, g.rec, g.item_desc, g.item_off + C,
-                                                               g.rec_cap, g.items_cap, k, b.acc, ideal, pe);
+                                                               g.rec_cap, g.items_cap, k, half_margin(1 << k), b.acc,
+                                                               ideal, pe);
         else
             k_cell_pairs<false><<<blocks, CP_WARPS * 32, 0, s>>>(g.rgeo, g.rec, g.item_desc, g.item_off + C,
-                                                                g.rec_cap, g.items_cap, k, b.acc, ideal, pe);
+                                                                g.rec_cap, g.items_cap, k, half_margin(1 << k), b.acc,
+                                                                ideal, pe);
         return;
     }
     const int blocks = n_items_hint ? grid_for((int64_t)n_items_hint, GP_WARPS, 152 * 8) : 152 * 8;

@@ -366,3 +366,118 @@ def test_clip_test_never_drops_a_pair_this_cell_owns():
             inside += 1
             assert own, (trial, r, c, w)
     assert owned > 500 and rejected > 500 and inside > 300
+
+
+def half_margin(w):
+    src = source("grid_common.cuh")
+    a, b = re.search(r"half_margin\(int w\) \{ return ([0-9.]+)f \+ ([0-9.]+)f / \(float\)w; \}", src).groups()
+    m = float(np.float32(np.float32(a) + np.float32(b) / np.float32(w)))
+    h = np.float16(m)
+    if float(h) < m:  # rounded up to FP16, as the kernel takes it
+        h = np.nextafter(h, np.float16(np.inf))
+    return float(h)
+
+
+def make_half(line, clip, w):
+    # grid_common.cuh make_hgeo, in FP32 then rounded to FP16, centred on the
+    # cell (NaN records: None)
+    f = np.float32
+    ux, uy, nk = f(line[0]), f(line[1]), f(line[2])
+    inv_w = f(1.0) / f(w)
+    ln = np.sqrt(ux * ux + uy * uy)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        hx, hy = ux / ln, -uy / ln
+        hc = nk * inv_w / ln + f(0.5) * (hx + hy)
+    if not ln > 0 or not abs(hc) <= 0.75 or any(map(math.isnan, clip)):
+        return None
+    h = lambda v: float(np.float16(v))
+    return (h(hx), h(hy), h(hc)), tuple(h(f(v) * inv_w - f(0.5)) for v in clip)
+
+
+def hfma(a, b, c):
+    # one rounding of a * b + c to FP16 (exact in FP64 for FP16 operands)
+    return float(np.float16(a * b + c))
+
+
+def half_test(r, c, M):
+    # k_cell_pairs' FP16 test of one pair: (dropped, counted); None records: undecided
+    if r is None or c is None:
+        return False, False
+    def s(line, p):
+        return hfma(line[0], p[1], hfma(line[1], p[0], line[2]))
+    (rl, rp), (cl, cp) = r, c
+    s0, s1, s2, s3 = s(cl, rp[:2]), s(cl, rp[2:]), s(rl, cp[:2]), s(rl, cp[2:])
+    t01 = fmax(fmin(s0, s1), -fmax(s0, s1))
+    t23 = fmax(fmin(s2, s3), -fmax(s2, s3))
+    tt = max(t01, t23)
+    return tt > M, tt < -M
+
+
+def proper(r, c):
+    def o(p, q, s):
+        return (q[0] - p[0]) * (s[1] - p[1]) - (q[1] - p[1]) * (s[0] - p[0])
+    a, b, p, q = r[:2], r[2:], c[:2], c[2:]
+    return o(a, b, p) * o(a, b, q) < 0 and o(p, q, a) * o(p, q, b) < 0
+
+
+def test_half_test_is_sound():
+    # pairs of segments meeting one cell: crossing, touching, sharing an
+    # endpoint, nearly touching, collinear, long ones reaching far outside
+    # the cell, points on its corners and border lines.  The FP16 first test
+    # of the pair kernel never drops a pair that counts in this cell (a
+    # crossing or touching whose exact intersection point lies in the
+    # half-open cell, or a collinear overlap), and every pair it counts at
+    # once is a proper crossing whose point lies in the cell.
+    rng = np.random.default_rng(321)
+    dropped = counted = kept_owned = 0
+    for trial in range(9000):
+        k = int(rng.choice([3, 5, 8, 10, 12]))
+        w = 1 << k
+        M = half_margin(w)
+        x0 = int(rng.integers(1, 65536 // w - 1)) * w
+        y0 = int(rng.integers(1, 65536 // w - 1)) * w
+        P = rng.uniform(-0.25 * w, 1.25 * w, size=2)
+        u = rng.random()
+        if u < 0.25:
+            P = np.array([float(rng.choice([0, w])), float(rng.choice([0, w]))])
+        elif u < 0.5:
+            P[int(rng.integers(0, 2))] = float(rng.choice([0, w]))
+
+        def seg(off):
+            th = rng.uniform(0, math.pi)
+            if rng.random() < 0.15:
+                th = float(rng.choice([0.0, math.pi / 2]))
+            d = np.array([math.cos(th), math.sin(th)])
+            nrm = np.array([-d[1], d[0]])
+            la, lb = (rng.uniform(0, 40000, size=2) if rng.random() < 0.3 else rng.uniform(0, 1.5 * w, size=2))
+            if rng.random() < 0.25:
+                la = 0.0  # the segment ends at P
+            Q = P + off * nrm
+            p = np.rint(np.concatenate([Q - la * d, Q + lb * d]) + [x0, y0, x0, y0])
+            p = np.clip(p, 0, 65535).astype(np.int64)
+            return tuple(int(v) for v in (p[0] - x0, p[1] - y0, p[2] - x0, p[3] - y0))
+        off = 0.0 if rng.random() < 0.5 else float(rng.choice([-1, 1])) * rng.uniform(0, 4) * w / 256
+        r, c = seg(0.0), seg(off)
+        if rng.random() < 0.1:
+            c = (r[0], r[1], c[2], c[3])  # an endpoint shared
+        if rng.random() < 0.05:
+            t = int(rng.integers(-3, 4))  # collinear, overlapping or not
+            c = (r[0] + t * (r[2] - r[0]) // 4, r[1] + t * (r[3] - r[1]) // 4, r[2], r[3])
+        if (r[0], r[1]) == (r[2], r[3]) or (c[0], c[1]) == (c[2], c[3]):
+            continue
+        if not (meets_cell(r, w) and meets_cell(c, w)):
+            continue
+        rc, rb = make_clip(*r, w, rng)
+        cc, cb = make_clip(*c, w, rng)
+        out, sure = half_test(make_half(rb, rc, w), make_half(cb, cc, w), M)
+        ux, uy, vx, vy = r[2] - r[0], r[3] - r[1], c[2] - c[0], c[3] - c[1]
+        par = ux * vy - uy * vx == 0
+        counts = crossing(r, c) and (par or exact_owner(r, c, w))
+        if out:
+            dropped += 1
+            assert not counts, (trial, r, c, w)
+        if sure:
+            counted += 1
+            assert proper(r, c) and exact_owner(r, c, w), (trial, r, c, w)
+        kept_owned += counts and not sure
+    assert dropped > 1000 and counted > 500 and kept_owned > 100
