@@ -450,7 +450,10 @@ constexpr int RWIN = 75;               // window slots: max over m of s (m + RQ 
 
 // Streams of a chunk of m rows in a cell with P offset pieces.
 __host__ __device__ __forceinline__ int rot_streams(int m, int P) {
-    return m >= 32 ? 1 : min(min(RSTREAMS, max(1, 32 / m)), max(1, P));
+    int s = 1;  // min(RSTREAMS, 32 / m) for m < 32, without a division
+#pragma unroll
+    for (int k = 2; k <= RSTREAMS; ++k) s += (m < 32 && k * m <= 32) ? 1 : 0;
+    return min(s, max(1, P));
 }
 
 // Work items of a cell with n records; overflow when the item word cannot
@@ -498,7 +501,12 @@ __device__ __forceinline__ RotLane rot_lane(int n, uint32_t w, int lane) {
     RotLane r;
     r.m = min(32, n - 32 * c);
     r.s = rot_streams(r.m, min(P, RSTREAMS));
-    const int sig = lane / r.m, row = lane - sig * r.m;
+    // the lane's stream: lane / m where below s, at least s otherwise (then
+    // the lane takes no offsets), without a division
+    int sig = 0;
+#pragma unroll
+    for (int k = 1; k <= RSTREAMS; ++k) sig += lane >= k * r.m ? 1 : 0;
+    const int row = lane - sig * r.m;
     const int piece = (r.m == 32 ? p : p * r.s) + sig;
     r.i = 32 * c + row;
     r.q0 = 1 + piece * RQ;

@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
         const int span = rl.m + RQ - 1, slots = rl.s * span;
         __syncwarp();
         for (int u = lane; u < slots; u += 32) {
-            const int sig = rl.s == 1 ? 0 : u / span;
+            const int sig = (u >= span ? 1 : 0) + (u >= 2 * span ? 1 : 0);  // s <= 3 streams
             const uint32_t x = rl.first + (uint32_t)(sig * RQ + (u - sig * span));
             const uint32_t r0 = base + wrap_row(x, n), r1 = base + wrap_row(x + 1, n);
             const uint4 A = geo_h[r0], B = geo_h[r1];
