@@ -339,21 +339,29 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
         }
         __syncthreads();
         const bool diag = bi == bj;
-        // pass 1: classify and tally; pass 2 (when pairs are kept): classify
-        // again and write the E_c pairs at offsets reserved with one atomic
-        // per tile (per-pair atomics on one counter serialise)
+        // classify and tally, keeping the E_c columns of the row as bits; when
+        // pairs are kept, write them at offsets reserved with one atomic per
+        // tile (per-pair atomics on one counter serialise)
         uint32_t mine = 0;
-        for (int jj = 0; jj < nc; ++jj) {
-            const bool valid = row_ok && (!diag || jj > (int)threadIdx.x);
-            const int kind = valid ? classify_f32(r, ri, cs[jj], cid[jj]) : PAIR_NONE;
-            const bool ec = kind == PAIR_PROPER || kind == PAIR_TOUCHING;
-            if (kind == PAIR_PROPER) ++pc.proper;
-            else if (kind == PAIR_TOUCHING) ++pc.touching;
-            else if (kind == PAIR_COLLINEAR) ++pc.collinear;
-            if (ec) {
-                pc.dev += dev_term(rth, cth[jj], ideal);
-                ++mine;
+        uint32_t hit[DF_COLS / 32];
+#pragma unroll
+        for (int h = 0; h < DF_COLS / 32; ++h) {
+            uint32_t bits = 0;
+            for (int b = 0; b < 32; ++b) {
+                const int jj = 32 * h + b;
+                const bool valid = row_ok && jj < nc && (!diag || jj > (int)threadIdx.x);
+                const int kind = valid ? classify_f32(r, ri, cs[jj], cid[jj]) : PAIR_NONE;
+                const bool ec = kind == PAIR_PROPER || kind == PAIR_TOUCHING;
+                if (kind == PAIR_PROPER) ++pc.proper;
+                else if (kind == PAIR_TOUCHING) ++pc.touching;
+                else if (kind == PAIR_COLLINEAR) ++pc.collinear;
+                if (ec) {
+                    pc.dev += dev_term(rth, cth[jj], ideal);
+                    bits |= 1u << b;
+                }
             }
+            hit[h] = bits;
+            mine += __popc(bits);
         }
         if (pairs) {
             uint32_t total;
@@ -361,15 +369,12 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
             if (threadIdx.x == 0) tile_base = total ? atomicAdd((unsigned long long *)&acc->records, (unsigned long long)total) : 0ull;
             __syncthreads();
             uint64_t pos = tile_base + off;
-            for (int jj = 0; jj < nc && mine; ++jj) {
-                const bool valid = row_ok && (!diag || jj > (int)threadIdx.x);
-                const int kind = valid ? classify_f32(r, ri, cs[jj], cid[jj]) : PAIR_NONE;
-                if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) {
-                    if (pos < cap) pairs[pos] = make_uint2(rix, cix[jj]);
+#pragma unroll
+            for (int h = 0; h < DF_COLS / 32; ++h)
+                for (uint32_t bits = hit[h]; bits; bits &= bits - 1) {
+                    if (pos < cap) pairs[pos] = make_uint2(rix, cix[32 * h + __ffs(bits) - 1]);
                     ++pos;
-                    --mine;
                 }
-            }
         }
     }
     flush_counts(pc, acc, shu);
@@ -577,19 +582,49 @@ __device__ __forceinline__ void tally(int kind, uint32_t ta, uint32_t tb, uint32
     if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) pc.dev += dev_term(ta, tb, ideal);
 }
 
+constexpr uint32_t PB_CAP = 256;  // E_c pairs a warp buffers in shared memory before writing them
+
+// Writes a warp's buffered E_c pairs at offsets reserved with one atomic
+// (per-pair atomics on one counter serialise).  Every lane must call it.
+__device__ __forceinline__ void flush_pairs(uint2 *wbuf, uint32_t &wn, int lane, DevAcc *acc,
+                                            uint2 *__restrict__ pairs, uint64_t cap) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0 && wn) base = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)wn);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t e = lane; e < wn; e += 32)
+        if (base + e < cap) pairs[base + e] = wbuf[e];
+    wn = 0;
+    __syncwarp();
+}
+
+// Appends the pair of each lane with `ec` set to the warp's buffer, flushing
+// it first if the round might not fit.  Every lane must call it.
+__device__ __forceinline__ void append_pair(bool ec, uint2 pr, uint2 *wbuf, uint32_t &wn, int lane, DevAcc *acc,
+                                            uint2 *__restrict__ pairs, uint64_t cap) {
+    const unsigned m = __ballot_sync(0xffffffffu, ec);
+    if (!m) return;
+    if (wn + __popc(m) > PB_CAP) flush_pairs(wbuf, wn, lane, acc, pairs, cap);
+    if (ec) wbuf[wn + __popc(m & lanemask_lt())] = pr;
+    wn += __popc(m);
+}
+
 // Short x short: one thread per record (row), against the later records of
 // its cell; a pair counts only in the smallest cell of both boxes.  Consecutive
 // records belong to the same or neighbouring cells, so a warp's rows are
-// short loops of similar length.  Two passes: tally and count, then (when
-// pairs are kept) write at offsets reserved once per warp and chunk.
+// short loops of similar length.  One pass: the E_c pairs (when kept) gather
+// in a per-warp buffer in shared memory (append_pair).
 __global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
                                                      const uint32_t *__restrict__ off, const FRec *__restrict__ rec,
                                                      const uint32_t *__restrict__ rec_cell, DevAcc *acc,
                                                      uint32_t ideal, uint2 *__restrict__ pairs, uint64_t cap) {
     __shared__ uint64_t shu[32];
+    __shared__ uint2 pbuf[256 / 32][PB_CAP];
     const FGrid g = *gp;
     const int lane = threadIdx.x & 31;
+    uint2 *wbuf = pbuf[threadIdx.x >> 5];
+    uint32_t wn = 0;  // E_c pairs waiting in the warp's buffer
     const uint32_t total = off[g.G * g.G];
     const uint32_t stride = gridDim.x * blockDim.x;
     PairCounts pc;
@@ -614,35 +649,28 @@ __global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ 
             tested += end - p - 1;
         }
         const int cxc = (int)(c % (uint32_t)g.G), cyc = (int)(c / (uint32_t)g.G);
-        auto visit = [&](auto &&hit) {
-            if (!ok) return;
-            for (uint32_t q = p + 1; q < end; ++q) {
-                const FRec fq = rec[q];
+        // one later record of the cell per lane a round (the warp's rounds
+        // end with its longest row)
+        uint32_t q = p + 1;
+        while (__any_sync(0xffffffffu, ok && q < end)) {
+            bool ec = false;
+            uint2 pr = make_uint2(0u, 0u);
+            if (ok && q < end) {
+                const FRec fq = rec[q++];
                 const int kind = classify_f32(r, rid, fq.s, fq.ids);
-                if (kind == PAIR_NONE) continue;
-                const CellBox qb = cell_box(fq.s, g);
-                if (max(rb.x0, qb.x0) != cxc || max(rb.y0, qb.y0) != cyc) continue;  // not the owner cell
-                hit(kind, ri, fq.i, rth, fq.th);
+                if (kind != PAIR_NONE) {
+                    const CellBox qb = cell_box(fq.s, g);
+                    if (max(rb.x0, qb.x0) == cxc && max(rb.y0, qb.y0) == cyc) {  // the owner cell
+                        tally(kind, rth, fq.th, ideal, pc);
+                        ec = kind == PAIR_PROPER || kind == PAIR_TOUCHING;
+                        pr = make_uint2(ri, fq.i);
+                    }
+                }
             }
-        };
-        uint32_t mine = 0;
-        visit([&](int kind, uint32_t, uint32_t, uint32_t ta, uint32_t tb) {
-            tally(kind, ta, tb, ideal, pc);
-            mine += (kind == PAIR_PROPER || kind == PAIR_TOUCHING) ? 1u : 0u;
-        });
-        if (pairs && __any_sync(0xffffffffu, mine != 0)) {
-            uint32_t wt;
-            const uint32_t lo = warp_excl_scan(mine, &wt);
-            unsigned long long wb = 0;
-            if (lane == 0 && wt) wb = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)wt);
-            uint64_t pos = __shfl_sync(0xffffffffu, wb, 0) + lo;
-            visit([&](int kind, uint32_t ia, uint32_t ib, uint32_t, uint32_t) {
-                if (kind != PAIR_PROPER && kind != PAIR_TOUCHING) return;
-                if (pos < cap) pairs[pos] = make_uint2(ia, ib);
-                ++pos;
-            });
+            if (pairs) append_pair(ec, pr, wbuf, wn, lane, acc, pairs, cap);
         }
     }
+    if (pairs) flush_pairs(wbuf, wn, lane, acc, pairs, cap);
     flush_counts(pc, acc, shu);
     tested = block_sum<uint64_t>(tested, shu);
     if (threadIdx.x == 0 && tested) atomic_add_u64(&acc->grid_work, tested);
@@ -692,8 +720,8 @@ __device__ __forceinline__ int2 line_range(const int2 *__restrict__ wl, uint64_t
 // spreads the (line, short record) pairs of their cells over its lanes, so
 // that every lane tests a pair in every round.  A pair counts only in the
 // first cell of the short's box (in row-major order) that the walk covers.
-// Two passes as in k_f32_grid_ss: tally and count, then (when pairs are
-// kept) write at offsets reserved once per warp and chunk.
+// One pass: the E_c pairs (when kept) gather in a per-warp buffer in shared
+// memory (append_pair).
 __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
                                                      const uint32_t *__restrict__ off, const FRec *__restrict__ rec,
@@ -703,8 +731,11 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                                                      uint64_t wl_cap, DevAcc *acc, uint32_t ideal,
                                                      uint2 *__restrict__ pairs, uint64_t cap) {
     __shared__ uint64_t shu[32];
+    __shared__ uint2 pbuf[256 / 32][PB_CAP];
     const FGrid g = *gp;
     const int lane = threadIdx.x & 31;
+    uint2 *wbuf = pbuf[threadIdx.x >> 5];
+    uint32_t wn = 0;  // E_c pairs waiting in the warp's buffer
     const uint32_t n_long = acc->n_long;
     const uint32_t total = n_long ? line_off[line_total_at] : 0u;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -743,84 +774,74 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
         tested += cnt;
         uint32_t chunk_total;
         const uint32_t pre = warp_excl_scan(cnt, &chunk_total);
-        auto visit = [&](auto &&hit) {
-            for (uint32_t b0 = 0; b0 < chunk_total; b0 += 32) {
-                const uint32_t q = b0 + lane;
-                int o = 0;  // the lane whose line holds pair q
+        for (uint32_t b0 = 0; b0 < chunk_total; b0 += 32) {
+            const uint32_t q = b0 + lane;
+            int o = 0;  // the lane whose line holds pair q
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint32_t pp = __shfl_sync(0xffffffffu, pre, o + step);
-                    if (pp <= q) o += step;
-                }
-                const uint32_t pre_o = __shfl_sync(0xffffffffu, pre, o);
-                const uint32_t li_o = __shfl_sync(0xffffffffu, li, o);
-                const uint32_t off_o = __shfl_sync(0xffffffffu, off_t, o);
-                const int lo_o = __shfl_sync(0xffffffffu, lo, o), hi_o = __shfl_sync(0xffffffffu, hi, o);
-                const int i_o = __shfl_sync(0xffffffffu, i, o), xm_o = __shfl_sync(0xffffffffu, xmaj, o);
-                const int a_o = __shfl_sync(0xffffffffu, ab.x, o);
-                float4 Lo;
-                Lo.x = __shfl_sync(0xffffffffu, L.x, o);
-                Lo.y = __shfl_sync(0xffffffffu, L.y, o);
-                Lo.z = __shfl_sync(0xffffffffu, L.z, o);
-                Lo.w = __shfl_sync(0xffffffffu, L.w, o);
-                uint2 lid_o;
-                lid_o.x = __shfl_sync(0xffffffffu, lid.x, o);
-                lid_o.y = __shfl_sync(0xffffffffu, lid.y, o);
-                const uint32_t lth_o = __shfl_sync(0xffffffffu, lth, o);
-                if (q >= chunk_total) continue;
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t pp = __shfl_sync(0xffffffffu, pre, o + step);
+                if (pp <= q) o += step;
+            }
+            const uint32_t pre_o = __shfl_sync(0xffffffffu, pre, o);
+            const uint32_t li_o = __shfl_sync(0xffffffffu, li, o);
+            const uint32_t off_o = __shfl_sync(0xffffffffu, off_t, o);
+            const int lo_o = __shfl_sync(0xffffffffu, lo, o), hi_o = __shfl_sync(0xffffffffu, hi, o);
+            const int i_o = __shfl_sync(0xffffffffu, i, o), xm_o = __shfl_sync(0xffffffffu, xmaj, o);
+            const int a_o = __shfl_sync(0xffffffffu, ab.x, o);
+            float4 Lo;
+            Lo.x = __shfl_sync(0xffffffffu, L.x, o);
+            Lo.y = __shfl_sync(0xffffffffu, L.y, o);
+            Lo.z = __shfl_sync(0xffffffffu, L.z, o);
+            Lo.w = __shfl_sync(0xffffffffu, L.w, o);
+            uint2 lid_o;
+            lid_o.x = __shfl_sync(0xffffffffu, lid.x, o);
+            lid_o.y = __shfl_sync(0xffffffffu, lid.y, o);
+            const uint32_t lth_o = __shfl_sync(0xffffffffu, lth, o);
+            bool ec = false;
+            uint2 pr = make_uint2(0u, 0u);
+            if (q < chunk_total) {
                 // the cell and record of pair q within the line
                 uint32_t k = q - pre_o;
                 int j = a_o, c = 0;
-                uint32_t p;
                 for (;; ++j) {
                     c = xm_o ? j * g.G + i_o : i_o * g.G + j;
                     const uint32_t n_c = off[c + 1] - off[c];
                     if (k < n_c) break;
                     k -= n_c;
                 }
-                p = off[c] + k;
+                const uint32_t p = off[c] + k;
                 const int cx = xm_o ? i_o : j, cy = xm_o ? j : i_o;
                 const FRec fs = rec[p];
                 const float4 S = fs.s;
                 const int kind = classify_f32(Lo, lid_o, S, fs.ids);
-                if (kind == PAIR_NONE) continue;
-                // owner: the first cell of the short's box (row-major) on the
-                // walk; this cell is on it, so only the cells before it matter
-                const CellBox sb = cell_box(S, g);
-                bool earlier = false;
-                for (int y = sb.y0; y <= cy && !earlier; ++y)
-                    for (int x = sb.x0; x <= sb.x1; ++x) {
-                        if (y == cy && x == cx) break;
-                        const int l2 = xm_o ? x : y, m2 = xm_o ? y : x;
-                        if (l2 < lo_o || l2 > hi_o) continue;
-                        const int2 r2 = line_range(wl, wl_cap, off_o, lo_o, l2, Lo, g);
-                        if (r2.x <= m2 && m2 <= r2.y) {
-                            earlier = true;
-                            break;
+                if (kind != PAIR_NONE) {
+                    // owner: the first cell of the short's box (row-major) on
+                    // the walk; this cell is on it, so only the cells before
+                    // it matter
+                    const CellBox sb = cell_box(S, g);
+                    bool earlier = false;
+                    for (int y = sb.y0; y <= cy && !earlier; ++y)
+                        for (int x = sb.x0; x <= sb.x1; ++x) {
+                            if (y == cy && x == cx) break;
+                            const int l2 = xm_o ? x : y, m2 = xm_o ? y : x;
+                            if (l2 < lo_o || l2 > hi_o) continue;
+                            const int2 r2 = line_range(wl, wl_cap, off_o, lo_o, l2, Lo, g);
+                            if (r2.x <= m2 && m2 <= r2.y) {
+                                earlier = true;
+                                break;
+                            }
                         }
+                    if (!earlier) {
+                        tally(kind, lth_o, fs.th, ideal, pc);
+                        ec = kind == PAIR_PROPER || kind == PAIR_TOUCHING;
+                        pr = make_uint2(li_o, fs.i);
                     }
-                if (earlier) continue;
-                hit(kind, li_o, fs.i, lth_o, fs.th);
+                }
             }
-        };
-        uint32_t mine = 0;
-        visit([&](int kind, uint32_t, uint32_t, uint32_t ta, uint32_t tb) {
-            tally(kind, ta, tb, ideal, pc);
-            mine += (kind == PAIR_PROPER || kind == PAIR_TOUCHING) ? 1u : 0u;
-        });
-        if (pairs && __any_sync(0xffffffffu, mine != 0)) {
-            uint32_t wt;
-            const uint32_t lo_off = warp_excl_scan(mine, &wt);
-            unsigned long long wb = 0;
-            if (lane == 0 && wt) wb = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)wt);
-            uint64_t pos = __shfl_sync(0xffffffffu, wb, 0) + lo_off;
-            visit([&](int kind, uint32_t ia, uint32_t ib, uint32_t, uint32_t) {
-                if (kind != PAIR_PROPER && kind != PAIR_TOUCHING) return;
-                if (pos < cap) pairs[pos] = make_uint2(ia, ib);
-                ++pos;
-            });
+            if (pairs) append_pair(ec, pr, wbuf, wn, lane, acc, pairs, cap);
         }
     }
+    if (pairs) flush_pairs(wbuf, wn, lane, acc, pairs, cap);
     flush_counts(pc, acc, shu);
     tested = block_sum<uint64_t>(tested, shu);
     if (threadIdx.x == 0 && tested) atomic_add_u64(&acc->grid_work, tested);
