@@ -488,15 +488,6 @@ __device__ __forceinline__ void walk_line(const Walk &k, int i, int &a, int &b) 
     b = fcell((float)(v1 + k.m_min), k.o_min_f, k.inv_w, k.G);
 }
 
-// Whether the walk covers cell (cx, cy).
-__device__ __forceinline__ bool walk_covers(const Walk &k, int cx, int cy) {
-    const int i = k.xmajor ? cx : cy, j = k.xmajor ? cy : cx;
-    if (i < k.lo || i > k.hi) return false;
-    int a, b;
-    walk_line(k, i, a, b);
-    return a <= j && j <= b;
-}
-
 __device__ __forceinline__ double ulp32(double v) {  // a unit in the last place of FP32 at |v|
     const float f = fabsf((float)v);
     return (double)(nextafterf(f, INFINITY) - f);
@@ -982,41 +973,68 @@ __device__ __forceinline__ void atomic_add2(float *g, int64_t v, float x, float 
 // d E_ca: a_c is the acute angle between the lines of directions theta_u,
 // theta_v; the fold (d = theta_u - theta_v mod pi, a_c = d or pi - d) and the
 // sign of a_c - ideal are read from the same integer directions the forward
-// used.  First the adjoint of every segment's direction is summed over its
-// E_c pairs (FP64, two atomics per pair); then each segment turns it into its
-// endpoints' gradients: d theta / d q = (-dy, dx) / |q - p|^2 for the vector
-// q - p.
+// used.  Every E_c pair adds the same magnitude, scale = -gout / (ideal
+// E_c), to the adjoints of its two directions, with signs +-1 or 0; so first
+// each segment's signed count is summed over its E_c pairs (exact int32
+// atomics, two per pair), then each segment turns scale times its count into
+// its endpoints' gradients: d theta / d q = (-dy, dx) / |q - p|^2 for the
+// vector q - p.
 __global__ void __launch_bounds__(256) k_grad_theta(const uint2 *const *__restrict__ pairs_slot,
                                                     const uint32_t *__restrict__ theta,
                                                     const DiffState *__restrict__ st, const float *__restrict__ gout,
-                                                    uint32_t ideal_u, double *__restrict__ adj) {
+                                                    uint32_t ideal_u, int32_t *__restrict__ cnt) {
     const DiffState d = *st;
     const uint2 *__restrict__ pairs = *pairs_slot;
     const uint64_t n = min((uint64_t)d.pairs, (uint64_t)d.ec);
     if (d.ec == 0) return;
-    const double scale = -(double)gout[0] / (d.ideal * (double)d.ec);
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
-        const uint2 pr = pairs[p];
-        const uint32_t dd = theta[pr.x] - theta[pr.y];
-        const bool folded = dd > 0x80000000u;           // a_c = pi - d
-        const uint32_t a = folded ? 0u - dd : dd;
-        const double sgn = a > ideal_u ? 1.0 : (a < ideal_u ? -1.0 : 0.0);
-        const double coef = scale * sgn * (folded ? -1.0 : 1.0);  // d E_ca / d theta_u = -d E_ca / d theta_v
-        if (coef != 0.0) {
-            atomicAdd(&adj[pr.x], coef);
-            atomicAdd(&adj[pr.y], -coef);
+    const int lane = threadIdx.x & 31;
+    // whole warps walk the list (the bound is uniform per warp), so the row
+    // side can be summed over runs of equal rows: a row's pairs are written
+    // one after another by the forward kernels
+    const uint64_t n_w = (n + 31) & ~(uint64_t)31;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_w; p += (uint64_t)gridDim.x * blockDim.x) {
+        uint2 pr = make_uint2(0xffffffffu, 0xffffffffu);
+        int c = 0;
+        if (p < n) {
+            pr = pairs[p];
+            const uint32_t dd = theta[pr.x] - theta[pr.y];
+            const bool folded = dd > 0x80000000u;  // a_c = pi - d
+            const uint32_t a = folded ? 0u - dd : dd;
+            const int sgn = a > ideal_u ? 1 : (a < ideal_u ? -1 : 0);
+            c = folded ? -sgn : sgn;  // d E_ca / d theta_u = -d E_ca / d theta_v
+            if (c != 0) atomicAdd(&cnt[pr.y], -c);
         }
+        // segmented sum of c over runs of equal pr.x ending at this lane
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, pr.x, 1);
+        const bool head = lane == 0 || prev != pr.x;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // this run's first lane
+        int sum = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, sum, o);
+            if (lane - o >= start) sum += t;
+        }
+        const uint32_t next = __shfl_down_sync(0xffffffffu, pr.x, 1);
+        const bool tail = lane == 31 || next != pr.x;
+        if (tail && p < n && sum != 0) atomicAdd(&cnt[pr.x], sum);
     }
 }
 
 __global__ void __launch_bounds__(256) k_grad_theta_scatter(const float4 *__restrict__ seg,
                                                             const uint2 *__restrict__ ids,
                                                             const DevAcc *__restrict__ acc,
-                                                            const double *__restrict__ adj, float *__restrict__ grad) {
+                                                            const DiffState *__restrict__ st,
+                                                            const float *__restrict__ gout,
+                                                            const int32_t *__restrict__ cnt, float *__restrict__ grad) {
+    const DiffState d = *st;
+    if (d.ec == 0) return;
+    const double scale = -(double)gout[0] / (d.ideal * (double)d.ec);
     const int64_t n = acc->n_seg;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double c = adj[i];
-        if (c == 0.0) continue;
+        const int32_t k = cnt[i];
+        if (k == 0) continue;
+        const double c = scale * (double)k;
         const float4 r = seg[i];
         const uint2 v = ids[i];
         const double ux = (double)r.z - r.x, uy = (double)r.w - r.y;
@@ -1173,11 +1191,14 @@ void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *c
                           const DiffState *st, const float *gout, uint32_t ideal_u, double *adj, float *grad,
                           cudaStream_t s) {
     cudaMemsetAsync(grad, 0, sizeof(float) * 2 * V, s);
-    cudaMemsetAsync(adj, 0, sizeof(double) * (E > 0 ? E : 1), s);
+    // the adjoint buffer (E doubles) holds the int32 signed counts
+    int32_t *cnt = reinterpret_cast<int32_t *>(adj);
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (E > 0 ? E : 1), s);
     count_launches(4);
     // the pair count is known on the device only: a grid-stride launch of fixed size
-    k_grad_theta<<<152 * 8, 256, 0, s>>>(pairs_slot, b.seg_theta, st, gout, ideal_u, adj);
-    k_grad_theta_scatter<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const float4 *)b.seg, b.seg_ids, b.acc, adj, grad);
+    k_grad_theta<<<152 * 8, 256, 0, s>>>(pairs_slot, b.seg_theta, st, gout, ideal_u, cnt);
+    k_grad_theta_scatter<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const float4 *)b.seg, b.seg_ids, b.acc, st, gout,
+                                                                    cnt, grad);
     k_grad_elv<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.edges, (const float2 *)b.xy, E, st, gout,
                                                          grad);
     k_grad_min_angle<<<grid_for(V, 256, 152 * 8), 256, 0, s>>>(arg, b.deg, (const float2 *)b.xy, V, st, gout, grad);
