@@ -464,11 +464,13 @@ __global__ void __launch_bounds__(256) k_rec_geo(const GridRec *__restrict__ rec
 // the FP16 error (half_margin), a pair is dropped when one clipped part lies
 // beyond it on one side of the other's line, and counted at once as a proper
 // crossing of this cell when each part straddles the other's line by more
-// than it (only the edges' directions are then read, for the crossing
-// angle's term).  Of the undecided pairs, those that share a vertex are
-// dropped and the rest queued, to be settled 32 at a time by the whole warp
-// (settle_pair, on the FP32 records), so the rare cases never run with idle
-// lanes.
+// than it; in the same step a pair sharing a vertex is dropped (the window
+// holds both records' vertex ids) and a counted pair adds its crossing
+// angle's term (from the staged directions).  The undecided rest, about 2 %
+// of the pairs, are queued by per-lane rounds and settled 32 at a time by the
+// whole warp (settle_pair, on the FP32 records), so the rare cases never run
+// with idle lanes.  The per-edge form takes its counted pairs in the rounds
+// too (their tallies are atomics on both edges).
 constexpr int CP_WARPS = 8;   // warps per block
 constexpr int CP_QUEUE = 64;  // queued pairs per warp: up to 31 left + 32 pushed in one round
 
@@ -575,8 +577,9 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
                                                                  PerEdge pe) {
     __shared__ uint4 win_h[CP_WARPS][2][RWIN];  // slot u: halves of records u and u + 1, interleaved
     __shared__ uint32_t win_i[CP_WARPS][RWIN];  // slot u's record
-    __shared__ uint2 win_x[CP_WARPS][RWIN];     // its edge id and direction
-    __shared__ uint2 win_v[CP_WARPS][RWIN];     // its vertex ids
+    __shared__ uint2 win_d[CP_WARPS][RWIN];     // the directions of records u and u + 1
+    __shared__ uint4 win_v[CP_WARPS][RWIN];     // the vertex ids of records u and u + 1
+    __shared__ uint2 win_x[CP_WARPS][PER_EDGE ? RWIN : 1];  // slot u's edge id and direction (per-edge form)
     __shared__ uint2 qbuf[CP_WARPS][CP_QUEUE];
     __shared__ uint64_t shu[32];
     __shared__ uint32_t part_sh[2];
@@ -588,7 +591,8 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
     const uint4 *__restrict__ geo_h = reinterpret_cast<const uint4 *>(geo + 3 * rec_cap);
     uint4 *wh0 = win_h[wid][0], *wh1 = win_h[wid][1];
     uint32_t *wi = win_i[wid];
-    uint2 *wx = win_x[wid], *wv = win_v[wid];
+    uint2 *wd = win_d[wid], *wx = win_x[wid];
+    uint4 *wv = win_v[wid];
     uint2 *q = qbuf[wid];
     const __half2 hm = __half2half2(__float2half_ru(margin)), nhm = __hneg2(hm);
     int qn = 0;
@@ -617,8 +621,11 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
             wh1[u] = make_uint4(__byte_perm(A.z, B.z, 0x5410), __byte_perm(A.z, B.z, 0x7632),
                                 __byte_perm(A.w, B.w, 0x5410), 0u);
             wi[u] = r0;
-            wx[u] = *(const uint2 *)&rec[r0].x;
-            wv[u] = *(const uint2 *)&rec[r0].s.z;
+            const uint2 x0 = *(const uint2 *)&rec[r0].x, v0 = *(const uint2 *)&rec[r0].s.z;
+            const uint2 v1 = *(const uint2 *)&rec[r1].s.z;
+            wd[u] = make_uint2(x0.y, rec[r1].x.y);
+            wv[u] = make_uint4(v0.x, v0.y, v1.x, v1.y);
+            if (PER_EDGE) wx[u] = x0;
         }
         const uint32_t row = base + (uint32_t)rl.i;
         const uint4 R = geo_h[row];
@@ -629,6 +636,8 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
         const uint2 rx = *(const uint2 *)&rec[row].x, rv = *(const uint2 *)&rec[row].s.z;
         __syncwarp();
         const int jn = (int)((__reduce_max_sync(0xffffffffu, (unsigned)rl.cnt) + 1u) >> 1);  // half2 steps
+        const int ce = (rl.cnt + 1) >> 1, co = rl.cnt >> 1;  // the lane's even and odd offsets
+        const uint32_t valid = ((1u << ce) - 1u) | (((1u << co) - 1u) << 16);
         uint32_t mo = 0, ms = 0;  // dropped, counted
 #pragma unroll
         for (int j = 0; j < RQ / 2; ++j) {
@@ -646,22 +655,31 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
             const __half2 t01 = __hmax2(__hmin2(s0, s1), __hneg2(__hmax2(s0, s1)));
             const __half2 t23 = __hmax2(__hmin2(s2, s3), __hneg2(__hmax2(s2, s3)));
             const __half2 tt = __hmax2_nan(t01, t23);  // NaN (a border record): undecided
-            const uint32_t bit = 0x10001u << j;
-            mo |= __hgt2_mask(tt, hm) & bit;
-            ms |= __hlt2_mask(tt, nhm) & bit;
+            const uint32_t lo_bit = 1u << j, hi_bit = 0x10000u << j, vj = valid & (lo_bit | hi_bit);
+            const uint32_t sb = __hlt2_mask(tt, nhm) & vj;  // counted
+            // dropped: apart in this cell, or sharing a vertex (never counted)
+            const uint4 vv = wv[u];
+            const bool sh0 = (rv.x == vv.x) | (rv.x == vv.y) | (rv.y == vv.x) | (rv.y == vv.y);
+            const bool sh1 = (rv.x == vv.z) | (rv.x == vv.w) | (rv.y == vv.z) | (rv.y == vv.w);
+            mo |= (__hgt2_mask(tt, hm) & (lo_bit | hi_bit)) | (sh0 ? lo_bit : 0u) | (sh1 ? hi_bit : 0u);
+            ms |= sb;
+            if (!PER_EDGE) {  // the crossing angle's terms of the counted pairs
+                const uint2 dd = wd[u];
+                const uint32_t q0 = (sb & lo_bit) ? dev_term(rx.y, dd.x, ideal) : 0u;
+                const uint32_t q1 = (sb & hi_bit) ? dev_term(rx.y, dd.y, ideal) : 0u;
+                pc.dev += (uint64_t)q0 + q1;
+            }
         }
-        const int ce = (rl.cnt + 1) >> 1, co = rl.cnt >> 1;  // the lane's even and odd offsets
-        const uint32_t valid = ((1u << ce) - 1u) | (((1u << co) - 1u) << 16);
         ms &= valid;
         uint32_t mk = ~(mo | ms) & valid;
-        // one pair of each kind per lane a round: a counted pair adds the
-        // crossing angle's term; an undecided one is dropped if it shares a
-        // vertex, else queued
         const int n_counted = __popc(ms);
         pc.proper += n_counted;
+        if (!PER_EDGE) ms = 0;  // their terms are in
+        // one pair of each kind per lane a round: a counted pair (per-edge
+        // form) adds its tallies; an undecided one is queued
         uint64_t rdev = 0;
         while (__any_sync(0xffffffffu, (ms | mk) != 0)) {
-            if (ms) {
+            if (PER_EDGE && ms) {
                 const uint2 cx = wx[rl.slot + mask_offset(__ffs(ms) - 1)];
                 ms &= ms - 1;
                 const uint32_t qd = dev_term(rx.y, cx.y, ideal);
@@ -677,8 +695,7 @@ __global__ void __launch_bounds__(CP_WARPS * 32, 4) k_cell_pairs(const float4 *_
             if (mk) {
                 const int u = rl.slot + mask_offset(__ffs(mk) - 1);
                 mk &= mk - 1;
-                const uint2 cv = wv[u];
-                push = !((rv.x == cv.x) | (rv.x == cv.y) | (rv.y == cv.x) | (rv.y == cv.y));
+                push = true;
                 e = make_uint2(row, wi[u]);
             }
             const unsigned m = __ballot_sync(0xffffffffu, push);
