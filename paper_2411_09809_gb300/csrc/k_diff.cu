@@ -149,6 +149,38 @@ __device__ __forceinline__ int classify_f32(float4 r, uint2 ri, float4 c, uint2 
     return (o1 != 0 && o2 != 0 && o3 != 0 && o4 != 0) ? PAIR_PROPER : PAIR_TOUCHING;
 }
 
+// The FP32 filter stage of orient_f32 alone, for a line given by a point p
+// and its direction u = q - p (rounded as orient_f32 rounds it): +-1 when the
+// filter decides the sign, 0 when the FP64 stage would be needed.
+__device__ __forceinline__ int orient_f32_filter(float ux, float uy, float px, float py, float rx, float ry) {
+    const float e32 = 5.9604645e-08f;  // 2^-24
+    const float t1 = ux * (ry - py), t2 = uy * (rx - px), d = t1 - t2;
+    const float mag = fabsf(t1) + fabsf(t2);
+    const float b32 = (3.0f + 16.0f * e32) * e32 * mag;
+    return mag >= 0x1p-100f ? (d > b32 ? 1 : (-d > b32 ? -1 : 0)) : 0;
+}
+
+__device__ __noinline__ int classify_f32_slow(float4 r, uint2 ri, float4 c, uint2 ci) {
+    return classify_f32(r, ri, c, ci);
+}
+
+// classify_f32 with the four orientations evaluated without branches by the
+// FP32 filter (the row's direction ru given): a pair whose four signs the
+// filter decides is settled here, any other goes to classify_f32.  Same
+// result: a decided sign is the exact one.
+__device__ __forceinline__ int classify_f32_fast(const float4 &r, float rux, float ruy, uint2 ri, const float4 &c,
+                                                 uint2 ci) {
+    if ((ri.x == ci.x) | (ri.x == ci.y) | (ri.y == ci.x) | (ri.y == ci.y)) return PAIR_NONE;
+    const float cux = c.z - c.x, cuy = c.w - c.y;
+    const int s1 = orient_f32_filter(rux, ruy, r.x, r.y, c.x, c.y);
+    const int s2 = orient_f32_filter(rux, ruy, r.x, r.y, c.z, c.w);
+    const int s3 = orient_f32_filter(cux, cuy, c.x, c.y, r.x, r.y);
+    const int s4 = orient_f32_filter(cux, cuy, c.x, c.y, r.z, r.w);
+    if (s1 * s2 > 0 || s3 * s4 > 0) return PAIR_NONE;  // one segment strictly on one side of the other's line
+    if (s1 != 0 && s2 != 0 && s3 != 0 && s4 != 0) return PAIR_PROPER;
+    return classify_f32_slow(r, ri, c, ci);
+}
+
 // ------------------------------------------------------------------ gather
 // Direction of the line through (dx, dy) (FP64), in units of pi / 2^32.
 __device__ __forceinline__ uint32_t line_direction_d(double dx, double dy) {
@@ -337,6 +369,7 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
             ri = ids[rix];
             rth = theta[rix];
         }
+        const float rux = r.z - r.x, ruy = r.w - r.y;
         __syncthreads();
         const bool diag = bi == bj;
         // classify and tally, keeping the E_c columns of the row as bits; when
@@ -350,7 +383,7 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
             for (int b = 0; b < 32; ++b) {
                 const int jj = 32 * h + b;
                 const bool valid = row_ok && jj < nc && (!diag || jj > (int)threadIdx.x);
-                const int kind = valid ? classify_f32(r, ri, cs[jj], cid[jj]) : PAIR_NONE;
+                const int kind = valid ? classify_f32_fast(r, rux, ruy, ri, cs[jj], cid[jj]) : PAIR_NONE;
                 const bool ec = kind == PAIR_PROPER || kind == PAIR_TOUCHING;
                 if (kind == PAIR_PROPER) ++pc.proper;
                 else if (kind == PAIR_TOUCHING) ++pc.touching;
@@ -648,7 +681,7 @@ __global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ 
             uint2 pr = make_uint2(0u, 0u);
             if (ok && q < end) {
                 const FRec fq = rec[q++];
-                const int kind = classify_f32(r, rid, fq.s, fq.ids);
+                const int kind = classify_f32_fast(r, r.z - r.x, r.w - r.y, rid, fq.s, fq.ids);
                 if (kind != PAIR_NONE) {
                     const CellBox qb = cell_box(fq.s, g);
                     if (max(rb.x0, qb.x0) == cxc && max(rb.y0, qb.y0) == cyc) {  // the owner cell
@@ -804,7 +837,7 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                 const int cx = xm_o ? i_o : j, cy = xm_o ? j : i_o;
                 const FRec fs = rec[p];
                 const float4 S = fs.s;
-                const int kind = classify_f32(Lo, lid_o, S, fs.ids);
+                const int kind = classify_f32_fast(Lo, Lo.z - Lo.x, Lo.w - Lo.y, lid_o, S, fs.ids);
                 if (kind != PAIR_NONE) {
                     // owner: the first cell of the short's box (row-major) on
                     // the walk; this cell is on it, so only the cells before
