@@ -637,8 +637,10 @@ __device__ __forceinline__ void append_pair(bool ec, uint2 pr, uint2 *wbuf, uint
 // its cell; a pair counts only in the smallest cell of both boxes.  Consecutive
 // records belong to the same or neighbouring cells, so a warp's rows are
 // short loops of similar length.  One pass: the E_c pairs (when kept) gather
-// in a per-warp buffer in shared memory (append_pair).
-__global__ void __launch_bounds__(256) k_f32_grid_ss(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
+// in a per-warp buffer in shared memory (append_pair).  Three blocks an SM
+// (at most 85 registers): more warps to hide the record loads than the
+// unbounded 96 registers allow.
+__global__ void __launch_bounds__(256, 3) k_f32_grid_ss(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
                                                      const uint32_t *__restrict__ off, const FRec *__restrict__ rec,
                                                      const uint32_t *__restrict__ rec_cell, DevAcc *acc,
