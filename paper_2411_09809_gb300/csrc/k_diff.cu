@@ -710,17 +710,24 @@ __global__ void __launch_bounds__(256) k_f32_walk_lines(const float4 *__restrict
                                                         const uint32_t *__restrict__ line_off, uint32_t line_total_at,
                                                         const DevAcc *__restrict__ acc, uint64_t cap,
                                                         int2 *__restrict__ wl) {
+    // one warp per long segment: its walk is set up once per lane (the FP64
+    // set-up per line, and a binary search for the line's segment, made the
+    // FP64 pipe the bound), then its lines are spread over the lanes
     const FGrid g = *gp;
     const uint32_t n_long = acc->n_long;
-    const uint32_t total = n_long ? line_off[line_total_at] : 0u;
-    const uint32_t end = (uint32_t)min((uint64_t)total, cap);
-    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < end; u += gridDim.x * blockDim.x) {
-        const uint32_t t = (uint32_t)find_segment_u32(line_off, n_long, u);
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < n_long; t += warps) {
+        const uint32_t u0 = line_off[t], u1 = (uint32_t)min((uint64_t)line_off[t + 1], cap);
+        if (u0 >= u1) continue;
         const Walk k = make_walk(seg[long_idx[t]], g);
-        int a, b;
-        walk_line(k, k.lo + (int)(u - line_off[t]), a, b);
-        wl[u] = make_int2(a, b);
+        for (uint32_t u = u0 + lane; u < u1; u += 32) {
+            int a, b;
+            walk_line(k, k.lo + (int)(u - u0), a, b);
+            wl[u] = make_int2(a, b);
+        }
     }
+    (void)line_total_at;
 }
 
 // Line i of a walk recomputed (kept out of line: a rare path whose FP64
@@ -741,6 +748,19 @@ __device__ __forceinline__ int2 line_range(const int2 *__restrict__ wl, uint64_t
     return line_range_slow(L, g, i);
 }
 
+// A line of a walk as the lanes of k_f32_grid_ls read it: its long segment,
+// the line's place in the walk and the record offset and count prefix of each
+// of its first LS_CELLS cells (a line meets few cells: its minor extent is at
+// most one cell plus the margins).
+constexpr int LS_CELLS = 4;
+struct LsLine {
+    float4 L;
+    uint2 lid;
+    uint32_t li, lth, off_t, pre;
+    int lo, hi, i, xmaj, j0, ncell;
+    uint32_t cstart[LS_CELLS], cum[LS_CELLS + 1];
+};
+
 // Long x short: a warp takes 32 consecutive lines of the walks (line u
 // belongs to the long segment t with line_off[t] <= u < line_off[t + 1]) and
 // spreads the (line, short record) pairs of their cells over its lanes, so
@@ -758,9 +778,11 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                                                      uint2 *__restrict__ pairs, uint64_t cap) {
     __shared__ uint64_t shu[32];
     __shared__ uint2 pbuf[256 / 32][PB_CAP];
+    __shared__ LsLine lines[256 / 32][32];
     const FGrid g = *gp;
     const int lane = threadIdx.x & 31;
     uint2 *wbuf = pbuf[threadIdx.x >> 5];
+    LsLine *wl_sh = lines[threadIdx.x >> 5];
     uint32_t wn = 0;  // E_c pairs waiting in the warp's buffer
     const uint32_t n_long = acc->n_long;
     const uint32_t total = n_long ? line_off[line_total_at] : 0u;
@@ -779,6 +801,8 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
         uint32_t lth = 0;
         int2 ab = make_int2(0, -1);
         uint32_t cnt = 0;
+        LsLine &me = wl_sh[lane];
+        __syncwarp();
         if (ok) {
             const uint32_t t = (uint32_t)find_segment_u32(line_off, n_long, u);
             off_t = line_off[t];
@@ -792,14 +816,35 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
             xmaj = m.y;
             i = lo + (int)(u - off_t);
             ab = line_range(wl, wl_cap, off_t, lo, i, L, g);
+            me.cum[0] = 0;
             for (int j = ab.x; j <= ab.y; ++j) {
                 const int c = xmaj ? j * g.G + i : i * g.G + j;
-                cnt += off[c + 1] - off[c];
+                const uint32_t c0 = off[c], n_c = off[c + 1] - c0;
+                if (j - ab.x < LS_CELLS) {
+                    me.cstart[j - ab.x] = c0;
+                    me.cum[j - ab.x + 1] = cnt + n_c;
+                }
+                cnt += n_c;
             }
         }
         tested += cnt;
         uint32_t chunk_total;
         const uint32_t pre = warp_excl_scan(cnt, &chunk_total);
+        if (ok) {
+            me.L = L;
+            me.lid = lid;
+            me.li = li;
+            me.lth = lth;
+            me.off_t = off_t;
+            me.pre = pre;
+            me.lo = lo;
+            me.hi = hi;
+            me.i = i;
+            me.xmaj = xmaj;
+            me.j0 = ab.x;
+            me.ncell = ab.y - ab.x + 1;
+        }
+        __syncwarp();
         for (uint32_t b0 = 0; b0 < chunk_total; b0 += 32) {
             const uint32_t q = b0 + lane;
             int o = 0;  // the lane whose line holds pair q
@@ -808,34 +853,36 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                 const uint32_t pp = __shfl_sync(0xffffffffu, pre, o + step);
                 if (pp <= q) o += step;
             }
-            const uint32_t pre_o = __shfl_sync(0xffffffffu, pre, o);
-            const uint32_t li_o = __shfl_sync(0xffffffffu, li, o);
-            const uint32_t off_o = __shfl_sync(0xffffffffu, off_t, o);
-            const int lo_o = __shfl_sync(0xffffffffu, lo, o), hi_o = __shfl_sync(0xffffffffu, hi, o);
-            const int i_o = __shfl_sync(0xffffffffu, i, o), xm_o = __shfl_sync(0xffffffffu, xmaj, o);
-            const int a_o = __shfl_sync(0xffffffffu, ab.x, o);
-            float4 Lo;
-            Lo.x = __shfl_sync(0xffffffffu, L.x, o);
-            Lo.y = __shfl_sync(0xffffffffu, L.y, o);
-            Lo.z = __shfl_sync(0xffffffffu, L.z, o);
-            Lo.w = __shfl_sync(0xffffffffu, L.w, o);
-            uint2 lid_o;
-            lid_o.x = __shfl_sync(0xffffffffu, lid.x, o);
-            lid_o.y = __shfl_sync(0xffffffffu, lid.y, o);
-            const uint32_t lth_o = __shfl_sync(0xffffffffu, lth, o);
             bool ec = false;
             uint2 pr = make_uint2(0u, 0u);
             if (q < chunk_total) {
-                // the cell and record of pair q within the line
-                uint32_t k = q - pre_o;
-                int j = a_o, c = 0;
-                for (;; ++j) {
-                    c = xm_o ? j * g.G + i_o : i_o * g.G + j;
-                    const uint32_t n_c = off[c + 1] - off[c];
-                    if (k < n_c) break;
-                    k -= n_c;
+                const LsLine &ln = wl_sh[o];
+                const uint32_t li_o = ln.li, off_o = ln.off_t, lth_o = ln.lth;
+                const int lo_o = ln.lo, hi_o = ln.hi, i_o = ln.i, xm_o = ln.xmaj;
+                const float4 Lo = ln.L;
+                const uint2 lid_o = ln.lid;
+                // the cell and record of pair q within the line: from the
+                // staged offsets, or past LS_CELLS cells from the offsets table
+                uint32_t k = q - ln.pre;
+                int j = ln.j0;
+                uint32_t p;
+                if (ln.ncell <= LS_CELLS || k < ln.cum[LS_CELLS]) {
+                    int x = 0;
+                    while (k >= ln.cum[x + 1]) ++x;
+                    j += x;
+                    p = ln.cstart[x] + (k - ln.cum[x]);
+                } else {
+                    k -= ln.cum[LS_CELLS];
+                    j += LS_CELLS;
+                    int c = 0;
+                    for (;; ++j) {
+                        c = xm_o ? j * g.G + i_o : i_o * g.G + j;
+                        const uint32_t n_c = off[c + 1] - off[c];
+                        if (k < n_c) break;
+                        k -= n_c;
+                    }
+                    p = off[c] + k;
                 }
-                const uint32_t p = off[c] + k;
                 const int cx = xm_o ? i_o : j, cy = xm_o ? j : i_o;
                 const FRec fs = rec[p];
                 const float4 S = fs.s;
