@@ -1,11 +1,14 @@
-"""CPU: the integer arithmetic of three kernels restated in Python with the
-constants read from their sources, checked against plain definitions: the
-Barrett-reduced visiting order of the DDA passes (a bijection equal to
-i * (2^31 - 1) mod n), the cells each thread of the offsets cluster reads and
-writes (every cell of [0, C) exactly once, 16-byte accesses aligned), and the
-integer scaling of a line direction to units of pi / 2^32 (the FP64 product
-rounded to the nearest integer); and the minimum angle's table-driven FP64
-gap against atan2 (with NumPy's FP32 atan2 standing in for the device's)."""
+"""CPU: the integer and filtered floating-point arithmetic of the kernels
+restated in Python with the constants read from their sources, checked
+against plain definitions: the Barrett-reduced visiting order of the DDA
+passes (a bijection equal to i * (2^31 - 1) mod n), the cells each thread of
+the offsets cluster reads and writes (every cell of [0, C) exactly once,
+16-byte accesses aligned), the integer scaling of a line direction to units
+of pi / 2^32 (the FP64 product rounded to the nearest integer), the minimum
+angle's table-driven FP64 gap against atan2 (with NumPy's FP32 atan2 standing
+in for the device's), the rotation work items (every pair of a cell once),
+the FP32 and FP16 clip tests of the pair kernel and the FP32 orientation
+filter of the differentiable kernels against exact rational arithmetic."""
 import math
 import os
 import re
@@ -481,3 +484,50 @@ def test_half_test_is_sound():
             assert proper(r, c) and exact_owner(r, c, w), (trial, r, c, w)
         kept_owned += counts and not sure
     assert dropped > 1000 and counted > 500 and kept_owned > 100
+
+
+def orient_filter(ux, uy, px, py, rx, ry):
+    # k_diff.cu orient_f32_filter in FP32 (products and differences rounded
+    # one by one; the device may fuse the last subtraction, which only makes
+    # d more accurate): +-1 when decided, 0 otherwise
+    f = np.float32
+    t1 = f(ux) * (f(ry) - f(py))
+    t2 = f(uy) * (f(rx) - f(px))
+    d = t1 - t2
+    mag = abs(t1) + abs(t2)
+    e32 = f(5.9604645e-08)
+    b32 = (f(3.0) + f(16.0) * e32) * e32 * mag
+    if not mag >= f(2.0 ** -100):
+        return 0
+    return 1 if d > b32 else (-1 if -d > b32 else 0)
+
+
+def test_fp32_orientation_filter_decides_only_exact_signs():
+    # FP32 points near and on common lines (collinear up to a few ulp, wide
+    # exponent ranges, shared coordinates): whenever the branch-free FP32 filter
+    # of the differentiable pair kernels decides a sign, it is the sign of the
+    # exact orientation of the FP32 inputs
+    from fractions import Fraction
+    rng = np.random.default_rng(77)
+    decided = undecided = 0
+    for trial in range(20000):
+        scale = float(2.0 ** rng.integers(-20, 20))
+        p = rng.uniform(-1, 1, 2) * scale
+        q = rng.uniform(-1, 1, 2) * scale
+        t = rng.uniform(-2, 3)
+        r = p + t * (q - p)
+        if rng.random() < 0.7:  # nudge off the line by a few ulp
+            r = r + rng.integers(-4, 5, 2) * np.spacing(np.abs(r).astype(np.float32)).astype(np.float64)
+        else:
+            r = r + rng.normal(0, 1e-3 * scale, 2)
+        p, q, r = (np.asarray(v, np.float32) for v in (p, q, r))
+        ux, uy = np.float32(q[0] - p[0]), np.float32(q[1] - p[1])
+        s = orient_filter(ux, uy, p[0], p[1], r[0], r[1])
+        F = lambda v: Fraction(float(v))
+        exact = (F(q[0]) - F(p[0])) * (F(r[1]) - F(p[1])) - (F(q[1]) - F(p[1])) * (F(r[0]) - F(p[0]))
+        if s == 0:
+            undecided += 1
+            continue
+        decided += 1
+        assert (exact > 0 and s == 1) or (exact < 0 and s == -1), (trial, p, q, r, s, exact)
+    assert decided > 5000 and undecided > 1000
