@@ -264,8 +264,9 @@ gr_status gr_move_vertices(gr_layout *layout, int64_t n, const int32_t *ids, con
  *
  * gr_diff_forward evaluates E_ca (ideal `ideal_rad`, <= 0 for 70 deg), M_l
  * and M_a (Sec. 2.1, Algorithms 2, 3, 5) into out3 = {E_ca, M_l, M_a} (host or
- * device memory), keeps the crossing pairs and every vertex's smallest gap,
- * and synchronises the host (it sizes its buffers from counts it reads back).
+ * device memory), keeps what the gradient needs (for every segment the
+ * signed count of its crossing pairs' angle terms, for every vertex its
+ * smallest gap) and synchronises the host (it reads back the status).
  * gr_diff_backward then writes to d_grad_xy ([V][2] FP32, DEVICE memory,
  * overwritten) the gradient of
  *   gout3[0] * E_ca + gout3[1] * M_l + gout3[2] * M_a
@@ -282,7 +283,7 @@ gr_status gr_move_vertices(gr_layout *layout, int64_t n, const int32_t *ids, con
  * while `stream` is being captured it adds its kernels to the caller's graph
  * (gout3 must then be device memory), and each replay of that graph computes
  * the gradient of the last gr_diff_forward that completed before the replay
- * (the crossing pairs are read through the layout at replay time).  Replays,
+ * (the counts and gaps are read from the layout at replay time).  Replays,
  * backward calls and forwards of one layout share its scratch buffers, so
  * they must not overlap on the GPU.  GR_ENOTSUP also when the layout's own
  * stream is being captured while `stream` names another one. */

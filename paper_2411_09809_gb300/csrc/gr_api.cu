@@ -79,9 +79,6 @@ struct gr_layout {
     DevAcc *h_acc = nullptr;        // pinned
     gr_coord_type coord = GR_COORD_I32;
     // differentiable form (FP32 layouts)
-    uint2 *pairs = nullptr;         // E_c pairs of the last forward
-    uint64_t pairs_cap = 0, n_pairs = 0;
-    uint2 **pairs_slot = nullptr;   // device copy of `pairs`: a captured backward reads the current buffer
     bool part_dirty = false;        // the device accumulators hold a share (gr_evaluate_part) other than all
     bool seg_canonical = false;     // the compacted segments are in edge order (gr_evaluate_part)
     uint32_t *canon_flags = nullptr;  // [E + 1] and [E] x 3: workspace of the canonical order
@@ -93,10 +90,9 @@ struct gr_layout {
     int2 *arg = nullptr;            // [V] smallest gap of every vertex
     DiffState *st = nullptr;
     float *out3 = nullptr, *gout3 = nullptr;
-    uint32_t diff_ideal_u = 0;
     bool diff_ready = false;
     void *f32_work = nullptr;       // FP32 crossing grid workspace
-    double *theta_adj = nullptr;    // [E] adjoint of each segment's direction
+    int32_t *theta_cnt = nullptr;   // [E] signed count of each segment's E_c pairs (the E_ca adjoint / scale)
     int f32_G = 0;                  // its grid side (0: all-pairs tiles)
     bool f32_planned = false;
     bool stats_stale = true;        // h_acc's layout part predates the last update
@@ -188,9 +184,9 @@ void free_layout(gr_layout *L) {
     Buffers &b = L->b;
     void *ptrs[] = {b.xy, b.edges, b.seg, b.seg_eid, b.seg_theta, b.len2, b.acc, b.elv_part, b.elv_len, b.ma_part,
                     b.ma_cnt, b.deg, b.deg_fill, b.dirs, b.scan_tmp, b.scan_tmp_side, b.result,
-                    b.seg_ids, b.dir_ang, b.dir_other, L->pairs, L->pairs_slot, L->canon_flags, L->canon_seg,
+                    b.seg_ids, b.dir_ang, b.dir_other, L->canon_flags, L->canon_seg,
                     L->canon_eid, L->canon_theta, L->arg, L->st, L->out3, L->gout3,
-                    L->f32_work, L->theta_adj, L->moved, L->affected, L->dacc, L->mv_ids, L->mv_xy,
+                    L->f32_work, L->theta_cnt, L->moved, L->affected, L->dacc, L->mv_ids, L->mv_xy,
                     L->dirty.flag, L->dirty.list, L->dirty.n, L->mp_dev, b.adj_off, b.adj, b.ma_nz, b.ma_dv, b.ma_touch,
                     b.ma_flag};
     for (void *p : ptrs)
@@ -269,8 +265,7 @@ gr_status alloc_layout(gr_layout *L) {
         GR_TRY(dalloc(&L->st, 1));
         GR_TRY(dalloc(&L->out3, 3));
         GR_TRY(dalloc(&L->gout3, 3));
-        GR_TRY(dalloc(&L->theta_adj, (size_t)E));
-        GR_TRY(dalloc(&L->pairs_slot, 1));
+        GR_TRY(dalloc(&L->theta_cnt, (size_t)E));
     }
 #undef GR_TRY
     GR_CU(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
@@ -579,62 +574,41 @@ gr_status plan_f32_grid(gr_layout *L) {
     return dalloc((char **)&L->f32_work, f32_grid_bytes(best_G, L->E));
 }
 
-// The FP32 forward: E_ca and the crossing counts (E_c pairs saved when
-// `pairs` is set), M_l, M_a (smallest gaps saved), folded into L->st/out3.
-gr_status forward_f32(gr_layout *L, uint32_t metrics, double ideal, bool save_pairs) {
+// The FP32 forward: E_ca and the crossing counts (with `save`, each
+// segment's signed count of E_c pairs for the backward), M_l, M_a (smallest
+// gaps saved), folded into L->st/out3.
+gr_status forward_f32(gr_layout *L, uint32_t metrics, double ideal, bool save) {
     cudaStream_t s = L->stream;
     Buffers &b = L->b;
     const int64_t V = L->V, E = L->E;
     const uint32_t ideal_u = ideal_units(ideal);
     gr_status pst = plan_f32_grid(L);
     if (pst != GR_OK) return pst;
-    if (save_pairs && !L->pairs) {  // the kernels count the E_c pairs only into a buffer
-        const uint64_t cap0 = 4 * (uint64_t)E + 1024;
-        if ((pst = dalloc(&L->pairs, (size_t)cap0)) != GR_OK) return pst;
-        L->pairs_cap = cap0;
-        GR_CU(cudaMemcpyAsync(L->pairs_slot, &L->pairs, sizeof L->pairs, cudaMemcpyHostToDevice, s));
-    }
-    for (int attempt = 0; attempt < 3; ++attempt) {
-        GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
-                              sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
-        phase_begin(L, GR_PHASE_EDGE_LENGTH);
-        if (metrics & GR_METRIC_EDGE_LENGTH) launch_elv(b, E, s, true);
-        phase_end(L, GR_PHASE_EDGE_LENGTH);
-        phase_begin(L, GR_PHASE_MIN_ANGLE);
-        if (metrics & GR_METRIC_MIN_ANGLE) launch_min_angle_f32(b, V, E, L->arg, s);
-        phase_end(L, GR_PHASE_MIN_ANGLE);
-        phase_begin(L, GR_PHASE_CROSS_PAIRS);
-        if ((metrics & GR_METRIC_CROSSINGS) && L->f32_G > 0 && L->opt.crossing_path != GR_PATH_ALLPAIRS)
-            launch_crossings_f32_grid(b, E, L->f32_G, L->f32_work, ideal_u, save_pairs ? L->pairs : nullptr,
-                                      save_pairs ? L->pairs_cap : 0, s);
-        else if (metrics & GR_METRIC_CROSSINGS)
-            launch_crossings_f32(b, E, ideal_u, save_pairs ? L->pairs : nullptr, save_pairs ? L->pairs_cap : 0, s);
-        phase_end(L, GR_PHASE_CROSS_PAIRS);
-        phase_begin(L, GR_PHASE_FINALIZE);
-        if (save_pairs) launch_diff_state(b, V, E, ideal, L->st, L->out3, s);
-        GR_CU(cudaGetLastError());
-        GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
-        L->io_d2h += (int64_t)sizeof(DevAcc);
-        phase_end(L, GR_PHASE_FINALIZE);
-        GR_CU(cudaStreamSynchronize(s));
-        phase_collect(L);
-        gr_status st = status_to_error(L->h_acc->status | L->h_acc->eval_status);
-        if (st != GR_OK) return st;
-        const uint64_t np = L->h_acc->records;
-        if (!save_pairs || np <= L->pairs_cap) {
-            L->n_pairs = save_pairs ? np : 0;
-            L->diff_ideal_u = ideal_u;
-            return GR_OK;
-        }
-        // more E_c pairs than the buffer holds: grow it and run again
-        if (L->pairs) cudaFree(L->pairs);
-        L->pairs = nullptr;
-        L->pairs_cap = 0;
-        if ((st = dalloc(&L->pairs, (size_t)(np + np / 4 + 1024))) != GR_OK) return st;
-        L->pairs_cap = np + np / 4 + 1024;
-        GR_CU(cudaMemcpyAsync(L->pairs_slot, &L->pairs, sizeof L->pairs, cudaMemcpyHostToDevice, s));
-    }
-    return fail(GR_ENOMEM, "crossing pair buffer could not be sized");
+    int32_t *cnt = save ? L->theta_cnt : nullptr;
+    GR_CU(cudaMemsetAsync((char *)b.acc + offsetof(DevAcc, eval_status), 0,
+                          sizeof(DevAcc) - offsetof(DevAcc, eval_status), s));
+    if (cnt) GR_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (E > 0 ? E : 1), s));
+    phase_begin(L, GR_PHASE_EDGE_LENGTH);
+    if (metrics & GR_METRIC_EDGE_LENGTH) launch_elv(b, E, s, true);
+    phase_end(L, GR_PHASE_EDGE_LENGTH);
+    phase_begin(L, GR_PHASE_MIN_ANGLE);
+    if (metrics & GR_METRIC_MIN_ANGLE) launch_min_angle_f32(b, V, E, L->arg, s);
+    phase_end(L, GR_PHASE_MIN_ANGLE);
+    phase_begin(L, GR_PHASE_CROSS_PAIRS);
+    if ((metrics & GR_METRIC_CROSSINGS) && L->f32_G > 0 && L->opt.crossing_path != GR_PATH_ALLPAIRS)
+        launch_crossings_f32_grid(b, E, L->f32_G, L->f32_work, ideal_u, cnt, s);
+    else if (metrics & GR_METRIC_CROSSINGS)
+        launch_crossings_f32(b, E, ideal_u, cnt, s);
+    phase_end(L, GR_PHASE_CROSS_PAIRS);
+    phase_begin(L, GR_PHASE_FINALIZE);
+    if (save) launch_diff_state(b, V, E, ideal, L->st, L->out3, s);
+    GR_CU(cudaGetLastError());
+    GR_CU(cudaMemcpyAsync(L->h_acc, b.acc, sizeof(DevAcc), cudaMemcpyDeviceToHost, s));
+    L->io_d2h += (int64_t)sizeof(DevAcc);
+    phase_end(L, GR_PHASE_FINALIZE);
+    GR_CU(cudaStreamSynchronize(s));
+    phase_collect(L);
+    return status_to_error(L->h_acc->status | L->h_acc->eval_status);
 }
 
 gr_status evaluate_f32(gr_layout *L, uint32_t metrics, double ideal, gr_result *out) {
@@ -1748,12 +1722,11 @@ gr_status gr_diff_backward(gr_layout *L, const float *gout3, float *d_grad_xy, g
     const bool host_g = !is_device_pointer(gout3);
     if (capturing) {
         // the kernels become nodes of the caller's graph; a replay reads the
-        // crossing pairs of the last forward before it through pairs_slot
+        // signed counts and state of the last forward before it
         if (host_g) return fail(GR_EINVAL, "while its stream is being captured, gout3 must be device memory");
         const int64_t l0 = gr_kernel_launches();
         if (L->V > 0)
-            launch_diff_backward(L->b, L->V, L->E, L->pairs_slot, L->arg, L->st, gout3, L->diff_ideal_u,
-                                 L->theta_adj, d_grad_xy, cs);
+            launch_diff_backward(L->b, L->V, L->E, L->arg, L->st, gout3, L->theta_cnt, d_grad_xy, cs);
         count_launches((int)(l0 - gr_kernel_launches()));  // nothing ran yet
         GR_CU(cudaGetLastError());
         return GR_OK;
@@ -1770,8 +1743,7 @@ gr_status gr_diff_backward(gr_layout *L, const float *gout3, float *d_grad_xy, g
     }
     phase_begin(L, GR_PHASE_DIFF_BACKWARD);
     if (L->V > 0)
-        launch_diff_backward(L->b, L->V, L->E, L->pairs_slot, L->arg, L->st, g, L->diff_ideal_u, L->theta_adj,
-                             d_grad_xy, L->stream);
+        launch_diff_backward(L->b, L->V, L->E, L->arg, L->st, g, L->theta_cnt, d_grad_xy, L->stream);
     phase_end(L, GR_PHASE_DIFF_BACKWARD);
     GR_CU(cudaGetLastError());
     if (cs != L->stream) {  // what follows on the caller's stream sees the gradient

@@ -376,7 +376,6 @@ void launch_delta_combine(const DeltaCounts *last, const DeltaAcc *d, Buffers &b
 // What the backward needs from the forward, on the device.
 struct DiffState {
     int64_t ec;        // E_c
-    uint64_t pairs;    // E_c pairs emitted
     double ideal;      // radians
     double E_ca;
     double mu, S, M_l; // mean length, sum (l - mu)^2, M_l
@@ -386,27 +385,26 @@ struct DiffState {
 
 // a1 for FP32 coordinates (finite values; ids checked).
 void launch_gather_f32(const float *xy, int64_t V, const int32_t *edges, int64_t E, Buffers &b, cudaStream_t s);
-// a7 on FP32 coordinates with exact predicates; E_c pairs (compacted segment
-// indices) to `pairs` (at most `cap`; the total goes to acc->records).
-// The same through a G x G grid over the segments' bounding box (short x
-// short pairs in cells, long x short along the long segments' walks, long x
-// long on all-pairs tiles); `work` holds f32_grid_bytes(G, E) bytes.
+// a7 on FP32 coordinates with exact predicates.  With `cnt` (zeroed by the
+// caller, one int32 per compacted segment), every E_c pair also adds the sign
+// of its crossing angle's term (diff_sign: +-1 or 0) to its first segment's
+// count and subtracts it from the second's, the E_ca adjoint the backward
+// scales.  The same through a G x G grid over the segments' bounding box
+// (short x short pairs in cells, long x short along the long segments' walks,
+// long x long on all-pairs tiles); `work` holds f32_grid_bytes(G, E) bytes.
 size_t f32_grid_bytes(int G, int64_t E);
-void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, uint32_t ideal, uint2 *pairs,
-                               uint64_t cap, cudaStream_t s);
-void launch_crossings_f32(const Buffers &b, int64_t n_bound, uint32_t ideal, uint2 *pairs, uint64_t cap,
-                          cudaStream_t s);
+void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, uint32_t ideal, int32_t *cnt,
+                               cudaStream_t s);
+void launch_crossings_f32(const Buffers &b, int64_t n_bound, uint32_t ideal, int32_t *cnt, cudaStream_t s);
 // a9 on FP32 coordinates; each vertex's smallest gap (far vertices) to `arg`.
 void launch_min_angle_f32(Buffers &b, int64_t V, int64_t E, int2 *arg, cudaStream_t s);
 // Folds the forward into `st` and the three values (E_ca, M_l, M_a) into out3.
 void launch_diff_state(const Buffers &b, int64_t V, int64_t E, double ideal, DiffState *st, float *out3,
                        cudaStream_t s);
-// grad[V][2] = gout[0] dE_ca + gout[1] dM_l + gout[2] dM_a (overwritten).
-// The E_c pairs are read through *pairs_slot (their count from st), so a
-// captured launch follows the pair buffer of the last forward before it.
-void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *const *pairs_slot, const int2 *arg,
-                          const DiffState *st, const float *gout, uint32_t ideal_u, double *adj, float *grad,
-                          cudaStream_t s);
+// grad[V][2] = gout[0] dE_ca + gout[1] dM_l + gout[2] dM_a (overwritten),
+// from the signed counts `cnt` and the state `st` of the last forward.
+void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const int2 *arg, const DiffState *st,
+                          const float *gout, const int32_t *cnt, float *grad, cudaStream_t s);
 
 // ------------------------------------------------------------------ batches
 // Device view of a batch of layouts packed one after another: layout l owns

@@ -181,6 +181,26 @@ __device__ __forceinline__ int classify_f32_fast(const float4 &r, float rux, flo
     return classify_f32_slow(r, ri, c, ci);
 }
 
+__device__ __forceinline__ void tally(int kind, uint32_t ta, uint32_t tb, uint32_t ideal, PairCounts &pc) {
+    if (kind == PAIR_COLLINEAR) ++pc.collinear;
+    else if (kind == PAIR_PROPER) ++pc.proper;
+    else if (kind == PAIR_TOUCHING) ++pc.touching;
+    if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) pc.dev += dev_term(ta, tb, ideal);
+}
+
+// The sign of an E_c pair's term in d E_ca / d theta for the pair's first
+// direction ta (the second gets the opposite): a_c is the acute angle
+// between the lines (d = ta - tb mod pi, a_c = d or pi - d) and d|a_c -
+// ideal| / d theta_a = sign(a_c - ideal) (negated when folded).  Read from the
+// same integer directions the forward's terms use.
+__device__ __forceinline__ int diff_sign(uint32_t ta, uint32_t tb, uint32_t ideal_u) {
+    const uint32_t dd = ta - tb;
+    const bool folded = dd > 0x80000000u;  // a_c = pi - d
+    const uint32_t a = folded ? 0u - dd : dd;
+    const int sgn = a > ideal_u ? 1 : (a < ideal_u ? -1 : 0);
+    return folded ? -sgn : sgn;
+}
+
 // ------------------------------------------------------------------ gather
 // Direction of the line through (dx, dy) (FP64), in units of pi / 2^32.
 __device__ __forceinline__ uint32_t line_direction_d(double dx, double dy) {
@@ -298,28 +318,6 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t *total) 
     return inc - v;
 }
 
-// Exclusive prefix of v over the block; *total = the block's sum.  Every
-// thread must call it; sh holds 33 words.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, uint32_t *total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t wt;
-    const uint32_t in_warp = warp_excl_scan(v, &wt);
-    __syncthreads();
-    if (lane == 0) sh[wid] = wt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int w = 0; w < nw; ++w) {
-            const uint32_t t = sh[w];
-            sh[w] = run;
-            run += t;
-        }
-        sh[32] = run;
-    }
-    __syncthreads();
-    *total = sh[32];
-    return sh[wid] + in_warp;
-}
 
 // All-pairs tiles over n FP32 segments (n = *n_p on the device): the
 // compacted segments themselves, or those listed in idx.  E_c pairs
@@ -330,14 +328,13 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
                                                        const uint32_t *__restrict__ theta,
                                                        const uint32_t *__restrict__ idx, const uint32_t *__restrict__ n_p,
                                                        DevAcc *acc, uint32_t ideal, int64_t tiles,
-                                                       uint2 *__restrict__ pairs, uint64_t cap) {
+                                                       int32_t *__restrict__ cnt) {
     __shared__ float4 cs[DF_COLS];
     __shared__ uint2 cid[DF_COLS];
     __shared__ uint32_t cth[DF_COLS];
     __shared__ uint32_t cix[DF_COLS];
+    __shared__ int ccnt[DF_COLS];  // the columns' signed counts in this tile
     __shared__ uint64_t shu[32];
-    __shared__ uint32_t scan_sh[33];
-    __shared__ unsigned long long tile_base;
     const int n_seg = (int)*n_p;
     if (tiles < 0) {
         const int64_t nb = (n_seg + DF_ROWS - 1) / DF_ROWS;
@@ -357,6 +354,7 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
             cid[threadIdx.x] = ids[q];
             cth[threadIdx.x] = theta[q];
             cix[threadIdx.x] = q;
+            ccnt[threadIdx.x] = 0;
         }
         const int i = bi * DF_ROWS + threadIdx.x;
         const bool row_ok = i < n_seg;
@@ -372,42 +370,25 @@ __global__ void __launch_bounds__(DF_ROWS) k_cross_f32(const float4 *__restrict_
         const float rux = r.z - r.x, ruy = r.w - r.y;
         __syncthreads();
         const bool diag = bi == bj;
-        // classify and tally, keeping the E_c columns of the row as bits; when
-        // pairs are kept, write them at offsets reserved with one atomic per
-        // tile (per-pair atomics on one counter serialise)
-        uint32_t mine = 0;
-        uint32_t hit[DF_COLS / 32];
-#pragma unroll
-        for (int h = 0; h < DF_COLS / 32; ++h) {
-            uint32_t bits = 0;
-            for (int b = 0; b < 32; ++b) {
-                const int jj = 32 * h + b;
-                const bool valid = row_ok && jj < nc && (!diag || jj > (int)threadIdx.x);
-                const int kind = valid ? classify_f32_fast(r, rux, ruy, ri, cs[jj], cid[jj]) : PAIR_NONE;
-                const bool ec = kind == PAIR_PROPER || kind == PAIR_TOUCHING;
-                if (kind == PAIR_PROPER) ++pc.proper;
-                else if (kind == PAIR_TOUCHING) ++pc.touching;
-                else if (kind == PAIR_COLLINEAR) ++pc.collinear;
-                if (ec) {
-                    pc.dev += dev_term(rth, cth[jj], ideal);
-                    bits |= 1u << b;
-                }
+        // classify and tally; with `cnt`, each E_c pair's sign (diff_sign)
+        // goes to the row's count (a register) and its column's (shared
+        // memory), written once per tile
+        int rsum = 0;
+        for (int jj = 0; jj < nc; ++jj) {
+            const bool valid = row_ok && (!diag || jj > (int)threadIdx.x);
+            const int kind = valid ? classify_f32_fast(r, rux, ruy, ri, cs[jj], cid[jj]) : PAIR_NONE;
+            if (kind == PAIR_NONE) continue;
+            tally(kind, rth, cth[jj], ideal, pc);
+            if (cnt && (kind == PAIR_PROPER || kind == PAIR_TOUCHING)) {
+                const int sg = diff_sign(rth, cth[jj], ideal);
+                rsum += sg;
+                if (sg) atomicAdd(&ccnt[jj], -sg);
             }
-            hit[h] = bits;
-            mine += __popc(bits);
         }
-        if (pairs) {
-            uint32_t total;
-            const uint32_t off = block_excl_scan(mine, scan_sh, &total);
-            if (threadIdx.x == 0) tile_base = total ? atomicAdd((unsigned long long *)&acc->records, (unsigned long long)total) : 0ull;
+        if (cnt) {
+            if (rsum) atomicAdd(&cnt[rix], rsum);
             __syncthreads();
-            uint64_t pos = tile_base + off;
-#pragma unroll
-            for (int h = 0; h < DF_COLS / 32; ++h)
-                for (uint32_t bits = hit[h]; bits; bits &= bits - 1) {
-                    if (pos < cap) pairs[pos] = make_uint2(rix, cix[32 * h + __ffs(bits) - 1]);
-                    ++pos;
-                }
+            if (threadIdx.x < nc && ccnt[threadIdx.x]) atomicAdd(&cnt[cix[threadIdx.x]], ccnt[threadIdx.x]);
         }
     }
     flush_counts(pc, acc, shu);
@@ -599,58 +580,24 @@ __global__ void __launch_bounds__(256) k_f32_grid_fill(const float4 *__restrict_
     }
 }
 
-__device__ __forceinline__ void tally(int kind, uint32_t ta, uint32_t tb, uint32_t ideal, PairCounts &pc) {
-    if (kind == PAIR_COLLINEAR) ++pc.collinear;
-    else if (kind == PAIR_PROPER) ++pc.proper;
-    else if (kind == PAIR_TOUCHING) ++pc.touching;
-    if (kind == PAIR_PROPER || kind == PAIR_TOUCHING) pc.dev += dev_term(ta, tb, ideal);
-}
 
-constexpr uint32_t PB_CAP = 256;  // E_c pairs a warp buffers in shared memory before writing them
-
-// Writes a warp's buffered E_c pairs at offsets reserved with one atomic
-// (per-pair atomics on one counter serialise).  Every lane must call it.
-__device__ __forceinline__ void flush_pairs(uint2 *wbuf, uint32_t &wn, int lane, DevAcc *acc,
-                                            uint2 *__restrict__ pairs, uint64_t cap) {
-    __syncwarp();
-    unsigned long long base = 0;
-    if (lane == 0 && wn) base = atomicAdd((unsigned long long *)&acc->records, (unsigned long long)wn);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (uint32_t e = lane; e < wn; e += 32)
-        if (base + e < cap) pairs[base + e] = wbuf[e];
-    wn = 0;
-    __syncwarp();
-}
-
-// Appends the pair of each lane with `ec` set to the warp's buffer, flushing
-// it first if the round might not fit.  Every lane must call it.
-__device__ __forceinline__ void append_pair(bool ec, uint2 pr, uint2 *wbuf, uint32_t &wn, int lane, DevAcc *acc,
-                                            uint2 *__restrict__ pairs, uint64_t cap) {
-    const unsigned m = __ballot_sync(0xffffffffu, ec);
-    if (!m) return;
-    if (wn + __popc(m) > PB_CAP) flush_pairs(wbuf, wn, lane, acc, pairs, cap);
-    if (ec) wbuf[wn + __popc(m & lanemask_lt())] = pr;
-    wn += __popc(m);
-}
 
 // Short x short: one thread per record (row), against the later records of
 // its cell; a pair counts only in the smallest cell of both boxes.  Consecutive
 // records belong to the same or neighbouring cells, so a warp's rows are
-// short loops of similar length.  One pass: the E_c pairs (when kept) gather
-// in a per-warp buffer in shared memory (append_pair).  Three blocks an SM
+// short loops of similar length.  With `cnt`, each E_c pair's sign
+// (diff_sign) goes to its segments' counts: the row's summed in a register,
+// the column's by an atomic.  Three blocks an SM
 // (at most 85 registers): more warps to hide the record loads than the
 // unbounded 96 registers allow.
 __global__ void __launch_bounds__(256, 3) k_f32_grid_ss(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
                                                      const uint32_t *__restrict__ off, const FRec *__restrict__ rec,
                                                      const uint32_t *__restrict__ rec_cell, DevAcc *acc,
-                                                     uint32_t ideal, uint2 *__restrict__ pairs, uint64_t cap) {
+                                                     uint32_t ideal, int32_t *__restrict__ cnt) {
     __shared__ uint64_t shu[32];
-    __shared__ uint2 pbuf[256 / 32][PB_CAP];
     const FGrid g = *gp;
     const int lane = threadIdx.x & 31;
-    uint2 *wbuf = pbuf[threadIdx.x >> 5];
-    uint32_t wn = 0;  // E_c pairs waiting in the warp's buffer
     const uint32_t total = off[g.G * g.G];
     const uint32_t stride = gridDim.x * blockDim.x;
     PairCounts pc;
@@ -675,28 +622,22 @@ __global__ void __launch_bounds__(256, 3) k_f32_grid_ss(const float4 *__restrict
             tested += end - p - 1;
         }
         const int cxc = (int)(c % (uint32_t)g.G), cyc = (int)(c / (uint32_t)g.G);
-        // one later record of the cell per lane a round (the warp's rounds
-        // end with its longest row)
-        uint32_t q = p + 1;
-        while (__any_sync(0xffffffffu, ok && q < end)) {
-            bool ec = false;
-            uint2 pr = make_uint2(0u, 0u);
-            if (ok && q < end) {
-                const FRec fq = rec[q++];
-                const int kind = classify_f32_fast(r, r.z - r.x, r.w - r.y, rid, fq.s, fq.ids);
-                if (kind != PAIR_NONE) {
-                    const CellBox qb = cell_box(fq.s, g);
-                    if (max(rb.x0, qb.x0) == cxc && max(rb.y0, qb.y0) == cyc) {  // the owner cell
-                        tally(kind, rth, fq.th, ideal, pc);
-                        ec = kind == PAIR_PROPER || kind == PAIR_TOUCHING;
-                        pr = make_uint2(ri, fq.i);
-                    }
-                }
+        int rsum = 0;  // the row's signed count
+        for (uint32_t q = p + 1; ok && q < end; ++q) {
+            const FRec fq = rec[q];
+            const int kind = classify_f32_fast(r, r.z - r.x, r.w - r.y, rid, fq.s, fq.ids);
+            if (kind == PAIR_NONE) continue;
+            const CellBox qb = cell_box(fq.s, g);
+            if (max(rb.x0, qb.x0) != cxc || max(rb.y0, qb.y0) != cyc) continue;  // not the owner cell
+            tally(kind, rth, fq.th, ideal, pc);
+            if (cnt && (kind == PAIR_PROPER || kind == PAIR_TOUCHING)) {
+                const int sg = diff_sign(rth, fq.th, ideal);
+                rsum += sg;
+                if (sg) atomicAdd(&cnt[fq.i], -sg);
             }
-            if (pairs) append_pair(ec, pr, wbuf, wn, lane, acc, pairs, cap);
         }
+        if (cnt && rsum) atomicAdd(&cnt[ri], rsum);
     }
-    if (pairs) flush_pairs(wbuf, wn, lane, acc, pairs, cap);
     flush_counts(pc, acc, shu);
     tested = block_sum<uint64_t>(tested, shu);
     if (threadIdx.x == 0 && tested) atomic_add_u64(&acc->grid_work, tested);
@@ -766,8 +707,7 @@ struct LsLine {
 // spreads the (line, short record) pairs of their cells over its lanes, so
 // that every lane tests a pair in every round.  A pair counts only in the
 // first cell of the short's box (in row-major order) that the walk covers.
-// One pass: the E_c pairs (when kept) gather in a per-warp buffer in shared
-// memory (append_pair).
+// With `cnt`, each E_c pair's sign (diff_sign) goes to both segments' counts.
 __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ seg, const uint2 *__restrict__ ids,
                                                      const uint32_t *__restrict__ theta, const FGrid *__restrict__ gp,
                                                      const uint32_t *__restrict__ off, const FRec *__restrict__ rec,
@@ -775,15 +715,12 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                                                      const uint32_t *__restrict__ line_off, uint32_t line_total_at,
                                                      const int2 *__restrict__ walk_meta, const int2 *__restrict__ wl,
                                                      uint64_t wl_cap, DevAcc *acc, uint32_t ideal,
-                                                     uint2 *__restrict__ pairs, uint64_t cap) {
+                                                     int32_t *__restrict__ sign_cnt) {
     __shared__ uint64_t shu[32];
-    __shared__ uint2 pbuf[256 / 32][PB_CAP];
     __shared__ LsLine lines[256 / 32][32];
     const FGrid g = *gp;
     const int lane = threadIdx.x & 31;
-    uint2 *wbuf = pbuf[threadIdx.x >> 5];
     LsLine *wl_sh = lines[threadIdx.x >> 5];
-    uint32_t wn = 0;  // E_c pairs waiting in the warp's buffer
     const uint32_t n_long = acc->n_long;
     const uint32_t total = n_long ? line_off[line_total_at] : 0u;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -853,8 +790,6 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                 const uint32_t pp = __shfl_sync(0xffffffffu, pre, o + step);
                 if (pp <= q) o += step;
             }
-            bool ec = false;
-            uint2 pr = make_uint2(0u, 0u);
             if (q < chunk_total) {
                 const LsLine &ln = wl_sh[o];
                 const uint32_t li_o = ln.li, off_o = ln.off_t, lth_o = ln.lth;
@@ -906,15 +841,18 @@ __global__ void __launch_bounds__(256) k_f32_grid_ls(const float4 *__restrict__ 
                         }
                     if (!earlier) {
                         tally(kind, lth_o, fs.th, ideal, pc);
-                        ec = kind == PAIR_PROPER || kind == PAIR_TOUCHING;
-                        pr = make_uint2(li_o, fs.i);
+                        if (sign_cnt && (kind == PAIR_PROPER || kind == PAIR_TOUCHING)) {
+                            const int sg = diff_sign(lth_o, fs.th, ideal);
+                            if (sg) {
+                                atomicAdd(&sign_cnt[li_o], sg);
+                                atomicAdd(&sign_cnt[fs.i], -sg);
+                            }
+                        }
                     }
                 }
             }
-            if (pairs) append_pair(ec, pr, wbuf, wn, lane, acc, pairs, cap);
         }
     }
-    if (pairs) flush_pairs(wbuf, wn, lane, acc, pairs, cap);
     flush_counts(pc, acc, shu);
     tested = block_sum<uint64_t>(tested, shu);
     if (threadIdx.x == 0 && tested) atomic_add_u64(&acc->grid_work, tested);
@@ -1039,7 +977,6 @@ __global__ void k_diff_state(const DevAcc *__restrict__ acc, const double *__res
     d.M_l = (E > 1 && d.mu > 0.0) ? sqrt(sv / ((double)E * d.mu * d.mu)) / sqrt((double)E - 1.0) : 0.0;
     d.n_ma = (int64_t)mn;
     d.M_a = mn > 0 ? 1.0 - ms / (double)mn : 1.0;
-    d.pairs = acc->records;
     *st = d;
     out3[0] = (float)d.E_ca;
     out3[1] = (float)d.M_l;
@@ -1052,57 +989,11 @@ __device__ __forceinline__ void atomic_add2(float *g, int64_t v, float x, float 
     atomicAdd(&g[2 * v + 1], y);
 }
 
-// d E_ca: a_c is the acute angle between the lines of directions theta_u,
-// theta_v; the fold (d = theta_u - theta_v mod pi, a_c = d or pi - d) and the
-// sign of a_c - ideal are read from the same integer directions the forward
-// used.  Every E_c pair adds the same magnitude, scale = -gout / (ideal
-// E_c), to the adjoints of its two directions, with signs +-1 or 0; so first
-// each segment's signed count is summed over its E_c pairs (exact int32
-// atomics, two per pair), then each segment turns scale times its count into
-// its endpoints' gradients: d theta / d q = (-dy, dx) / |q - p|^2 for the
-// vector q - p.
-__global__ void __launch_bounds__(256) k_grad_theta(const uint2 *const *__restrict__ pairs_slot,
-                                                    const uint32_t *__restrict__ theta,
-                                                    const DiffState *__restrict__ st, const float *__restrict__ gout,
-                                                    uint32_t ideal_u, int32_t *__restrict__ cnt) {
-    const DiffState d = *st;
-    const uint2 *__restrict__ pairs = *pairs_slot;
-    const uint64_t n = min((uint64_t)d.pairs, (uint64_t)d.ec);
-    if (d.ec == 0) return;
-    const int lane = threadIdx.x & 31;
-    // whole warps walk the list (the bound is uniform per warp), so the row
-    // side can be summed over runs of equal rows: a row's pairs are written
-    // one after another by the forward kernels
-    const uint64_t n_w = (n + 31) & ~(uint64_t)31;
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_w; p += (uint64_t)gridDim.x * blockDim.x) {
-        uint2 pr = make_uint2(0xffffffffu, 0xffffffffu);
-        int c = 0;
-        if (p < n) {
-            pr = pairs[p];
-            const uint32_t dd = theta[pr.x] - theta[pr.y];
-            const bool folded = dd > 0x80000000u;  // a_c = pi - d
-            const uint32_t a = folded ? 0u - dd : dd;
-            const int sgn = a > ideal_u ? 1 : (a < ideal_u ? -1 : 0);
-            c = folded ? -sgn : sgn;  // d E_ca / d theta_u = -d E_ca / d theta_v
-            if (c != 0) atomicAdd(&cnt[pr.y], -c);
-        }
-        // segmented sum of c over runs of equal pr.x ending at this lane
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, pr.x, 1);
-        const bool head = lane == 0 || prev != pr.x;
-        const unsigned heads = __ballot_sync(0xffffffffu, head);
-        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // this run's first lane
-        int sum = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, sum, o);
-            if (lane - o >= start) sum += t;
-        }
-        const uint32_t next = __shfl_down_sync(0xffffffffu, pr.x, 1);
-        const bool tail = lane == 31 || next != pr.x;
-        if (tail && p < n && sum != 0) atomicAdd(&cnt[pr.x], sum);
-    }
-}
-
+// d E_ca: every E_c pair adds the same magnitude, scale = -gout / (ideal E_c),
+// to the adjoints of its two directions with signs +-1 or 0 (diff_sign); the
+// forward summed them into each segment's signed count (exact int32), so each
+// segment turns scale times its count into its endpoints' gradients:
+// d theta / d q = (-dy, dx) / |q - p|^2 for the vector q - p.
 __global__ void __launch_bounds__(256) k_grad_theta_scatter(const float4 *__restrict__ seg,
                                                             const uint2 *__restrict__ ids,
                                                             const DevAcc *__restrict__ acc,
@@ -1185,15 +1076,14 @@ void launch_gather_f32(const float *xy, int64_t V, const int32_t *edges, int64_t
                                                             b.len2, b.acc);
 }
 
-void launch_crossings_f32(const Buffers &b, int64_t n_bound, uint32_t ideal, uint2 *pairs, uint64_t cap,
-                          cudaStream_t s) {
+void launch_crossings_f32(const Buffers &b, int64_t n_bound, uint32_t ideal, int32_t *cnt, cudaStream_t s) {
     if (n_bound < 2) return;
     const int64_t nb = (n_bound + DF_ROWS - 1) / DF_ROWS;
     const int64_t tiles = nb * (nb + 1) / 2;
     const unsigned grid = (unsigned)(tiles < (int64_t(1) << 30) ? tiles : (int64_t(1) << 30));
     count_launches(1);
     k_cross_f32<<<grid, DF_ROWS, 0, s>>>((const float4 *)b.seg, b.seg_ids, b.seg_theta, nullptr, &b.acc->n_seg,
-                                         b.acc, ideal, tiles, pairs, cap);
+                                         b.acc, ideal, tiles, cnt);
 }
 
 // Lines of the walk table: up to 16 per edge (more are recomputed when needed).
@@ -1205,8 +1095,8 @@ size_t f32_grid_bytes(int G, int64_t E) {
            sizeof(int2) * ((size_t)E + f32_walk_lines_cap(E)) + 256 * 10;
 }
 
-void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, uint32_t ideal, uint2 *pairs,
-                               uint64_t cap, cudaStream_t s) {
+void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, uint32_t ideal, int32_t *sign_cnt,
+                               cudaStream_t s) {
     if (E < 2) return;
     const size_t C = (size_t)G * G;
     char *p = (char *)work;
@@ -1240,12 +1130,12 @@ void launch_crossings_f32_grid(const Buffers &b, int64_t E, int G, void *work, u
     launch_scan_u32(cnt, cnt, (int64_t)C, b.scan_tmp, &b.acc->scan_sink, &b.acc->eval_status, s);
     k_f32_grid_fill<<<gb, 256, 0, s>>>(seg, b.acc, g, cnt, fill, b.seg_ids, b.seg_theta, rec, rec_cell);
     count_launches(3);
-    k_f32_grid_ss<<<152 * 8, 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, rec_cell, b.acc, ideal, pairs,
-                                          cap);
+    k_f32_grid_ss<<<152 * 8, 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, rec_cell, b.acc, ideal,
+                                          sign_cnt);
     k_f32_grid_ls<<<152 * 8, 256, 0, s>>>(seg, b.seg_ids, b.seg_theta, g, cnt, rec, long_idx, long_lines,
-                                          (uint32_t)E, walk_meta, wl, wl_cap, b.acc, ideal, pairs, cap);
+                                          (uint32_t)E, walk_meta, wl, wl_cap, b.acc, ideal, sign_cnt);
     k_cross_f32<<<152 * 8, DF_ROWS, 0, s>>>(seg, b.seg_ids, b.seg_theta, long_idx, &b.acc->n_long, b.acc, ideal, -1,
-                                            pairs, cap);
+                                            sign_cnt);
 }
 
 void launch_min_angle_f32(Buffers &b, int64_t V, int64_t E, int2 *arg, cudaStream_t s) {
@@ -1269,16 +1159,10 @@ void launch_diff_state(const Buffers &b, int64_t V, int64_t E, double ideal, Dif
                                    st, out3);
 }
 
-void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const uint2 *const *pairs_slot, const int2 *arg,
-                          const DiffState *st, const float *gout, uint32_t ideal_u, double *adj, float *grad,
-                          cudaStream_t s) {
+void launch_diff_backward(const Buffers &b, int64_t V, int64_t E, const int2 *arg, const DiffState *st,
+                          const float *gout, const int32_t *cnt, float *grad, cudaStream_t s) {
     cudaMemsetAsync(grad, 0, sizeof(float) * 2 * V, s);
-    // the adjoint buffer (E doubles) holds the int32 signed counts
-    int32_t *cnt = reinterpret_cast<int32_t *>(adj);
-    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (E > 0 ? E : 1), s);
-    count_launches(4);
-    // the pair count is known on the device only: a grid-stride launch of fixed size
-    k_grad_theta<<<152 * 8, 256, 0, s>>>(pairs_slot, b.seg_theta, st, gout, ideal_u, cnt);
+    count_launches(3);
     k_grad_theta_scatter<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const float4 *)b.seg, b.seg_ids, b.acc, st, gout,
                                                                     cnt, grad);
     k_grad_elv<<<grid_for(E, 256, 152 * 8), 256, 0, s>>>((const int2 *)b.edges, (const float2 *)b.xy, E, st, gout,

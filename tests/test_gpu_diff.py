@@ -129,8 +129,9 @@ def test_diff_forward_and_gradients_match_oracle(seed):
         grad_close(d.cpu().numpy(), w[0] * g_eca + w[1] * g_ml + w[2] * g_ma, "combination")
 
 
-def test_diff_pair_buffer_grows_and_update_invalidates():
-    # many crossings (long random edges) so the first forward outgrows its pair buffer
+def test_diff_many_crossings_and_update_invalidates():
+    # many crossings (long random edges, far more than edges), then an update
+    # that invalidates the forward the backward would use
     rng = np.random.default_rng(7)
     V = 1500
     xy = rng.random((V, 2)).astype(np.float32)
@@ -254,7 +255,7 @@ def test_fp32_grid_gradients_equal_allpairs_gradients():
 def test_diff_calls_on_a_caller_stream_and_in_a_captured_graph():
     # the backward ordered on another stream without a host synchronisation, and
     # captured into a CUDA graph whose replays follow the last forward before them,
-    # also after that forward regrew the crossing-pair buffer
+    # also after a forward with far more crossings
     import torch
     xy, e = random_float_layout(55, 3000, 6500, 300)
     V = len(xy)
@@ -282,7 +283,7 @@ def test_diff_calls_on_a_caller_stream_and_in_a_captured_graph():
         torch.cuda.synchronize()
         grad_close(gd.cpu().numpy(), want, "graph replay")
         # random positions turn the nearest-neighbour edges into long ones: millions of
-        # crossings, far more than the pair buffer was sized for
+        # crossings
         xy2 = np.random.default_rng(56).random((V, 2)).astype(np.float32)
         L.update(cuda(xy2))
         gr.gr_diff_forward(L.handle, IDEAL, None)
@@ -290,7 +291,7 @@ def test_diff_calls_on_a_caller_stream_and_in_a_captured_graph():
         gd.fill_(float("nan"))
         g.replay()
         torch.cuda.synchronize()
-        grad_close(gd.cpu().numpy(), -h_eca + h_ml - h_ma, "graph replay after the pair buffer grew")
+        grad_close(gd.cpu().numpy(), -h_eca + h_ml - h_ma, "graph replay after a forward with millions of crossings")
         with pytest.raises(gr.GrError) as ei:
             with torch.cuda.graph(torch.cuda.CUDAGraph(), stream=s, capture_error_mode="relaxed"):
                 gr.gr_diff_forward(L.handle, IDEAL, out, torch.cuda.current_stream().cuda_stream)
